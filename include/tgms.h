@@ -1,0 +1,182 @@
+/*
+ * tgms.h -- C ABI of libtgms: a two-grid preconditioned conjugate-gradient
+ * solver for the lowest-order Raviart-Thomas / P0 mixed discretisation of
+ * Darcy flow, -div(kappa grad p) = f, with an adaptive spectral (GMsFEM)
+ * coarse space, for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Yang, Fu & Chung, "A two-grid preconditioner with an adaptive
+ * coarse space for flow simulations in highly heterogeneous media"
+ * (arXiv 1807.07220).  Each entry point below cites the section / equation
+ * whose operation it performs.
+ *
+ * Conventions (all arrays x-fastest, row-major in y, FP64):
+ *   - the domain is the unit square split into n x n square cells, h = 1/n;
+ *     coarse blocks K_i are b x b cells (b divides n);
+ *   - cell arrays (kappa, f, p): n*n entries, cell (i, j) at j*n + i;
+ *   - ux: (n+1)*n normal velocities of the x-faces, face (i, j) at x = i h,
+ *     y in [j h, (j+1) h], index j*(n+1) + i, positive along +x;
+ *   - uy: n*(n+1) normal velocities of the y-faces, face (i, j) at y = j h,
+ *     x in [i h, (i+1) h], index j*n + i, positive along +y;
+ *   - bflux: 4n OUTWARD normal velocities on the boundary faces: left
+ *     (j = 0..n-1), right (j), bottom (i = 0..n-1), top (i);
+ *   - "psi vectors" (operator-level entry points): n*n stream-function
+ *     values at the nodes (i h, j h), node (i, j) at j*n + i; entries with
+ *     i == 0 or j == 0 are boundary nodes and must be zero (the nodes
+ *     i == n or j == n are implicit zeros).  A divergence-free face field with
+ *     no boundary flux is u_x(i,j) = (psi(i,j+1)-psi(i,j))/h,
+ *     u_y(i,j) = -(psi(i+1,j)-psi(i,j))/h.
+ *
+ * Ownership: the caller owns every buffer it passes.  tg_setup copies what it
+ * keeps; the handle owns its device memory until tg_destroy.  With
+ * TG_PTR_HOST the solver copies host arrays to and from the device inside
+ * the call; with TG_PTR_DEVICE all array pointers must be device pointers
+ * (e.g. torch CUDA tensors).  Operator-level entry points always take device
+ * pointers.  All work is issued on the stream given to tg_setup; entry points
+ * return after synchronising that stream.
+ *
+ * Errors: every int-returning function returns TG_OK (0) or a negative
+ * TG_ERR_* code and never aborts; tg_strerror gives a message.
+ */
+#ifndef TGMS_H
+#define TGMS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TG_OK                       0
+#define TG_ERR_INVALID_ARG         -1  /* sizes, b does not divide n, kappa <= 0 or not finite, NULL */
+#define TG_ERR_INCOMPATIBLE_SOURCE -2  /* |sum F - boundary outflow| > 1e-12 * (sum |F| + outflow) */
+#define TG_ERR_BREAKDOWN           -3  /* PCG: p^T K p <= 0 or non-finite alpha/beta */
+#define TG_ERR_MAXITER             -4  /* not converged in max_iter; outputs still written */
+#define TG_ERR_DEVICE_TIMEOUT      -5  /* a bounded device-side wait expired */
+#define TG_ERR_CUDA                -6  /* CUDA runtime error (launch, copy, no device) */
+#define TG_ERR_OOM                 -7  /* device allocation failed */
+#define TG_ERR_UNSUPPORTED         -8  /* valid but not implemented configuration */
+#define TG_ERR_DEGENERATE_BASIS    -9  /* a coarse face has no selected function with net flux */
+
+/* precision of the preconditioner (patch inverses, coarse basis tiles and
+ * inner residuals); the outer PCG vectors, dot products, fine operator and
+ * the coarse matrix are always FP64. */
+#define TG_PREC_F64  0
+#define TG_PREC_F32  1
+#define TG_PREC_BF16 2   /* BF16 storage, FP32 arithmetic */
+
+#define TG_PTR_HOST   0
+#define TG_PTR_DEVICE 1
+
+#define TG_COARSE_GMSFEM 0   /* adaptive spectral space, Section 4.2 */
+#define TG_COARSE_MSFEM  1   /* one MsFEM function per coarse face, eq. msfem */
+#define TG_COARSE_RT0    2   /* coarse RT0 space */
+
+typedef struct tg_handle tg_handle;
+
+typedef struct tg_grid {
+  int nx, ny;     /* fine cells per side; this release requires nx == ny */
+  int bx, by;     /* fine cells per coarse block side; bx == by, 2 <= b <= 16 */
+  int overlap;    /* oversampling of K_i^+ in fine cells (Section 6: 2), 0..2 */
+} tg_grid;
+
+typedef struct tg_options {
+  double eta;        /* smoother weight, eq. smooth (Section 6: 0.2) */
+  int m1, m2;        /* pre / post smoothing steps (Section 6: 1, 1) */
+  int precision;     /* TG_PREC_* */
+  int flexible;      /* 1: flexible CG beta = -alpha (z, K p) / (r, z)_old */
+  int max_iter;      /* PCG iteration cap */
+  int pointer_mode;  /* TG_PTR_HOST or TG_PTR_DEVICE for tg_setup / tg_solve */
+  int coarse_space;  /* TG_COARSE_* */
+  int max_basis;     /* cap on functions kept per coarse face; 0 = no cap */
+} tg_options;
+
+typedef struct tg_report {
+  int iters;              /* PCG iterations (applications of the fine operator) */
+  int converged;          /* 1 if ||C^T r|| <= rtol ||C^T r_0|| */
+  double rel_residual;    /* final ||C^T r|| / ||C^T r_0|| */
+  double cond_estimate;   /* Lanczos estimate of cond(M K) from the PCG coefficients */
+  int coarse_dim;         /* velocity basis + coarse cells + 1 (the paper's "Dim") */
+  int velocity_basis;     /* number of coarse velocity functions, sum of l_i */
+  int coarse_unknowns;    /* size of the SPD coarse system actually factored */
+  double max_div_error;   /* max over cells of |int_c div u - F_c| / max |F_c| */
+  double preprocess_ms;   /* device time of Section 3 (inside tg_solve) */
+  double pcg_ms;          /* device time of the PCG loop */
+  double epilogue_ms;     /* device time of v = vbar + vtilde and the pressure */
+} tg_report;
+
+/* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
+ * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap. */
+int tg_default_options(tg_options* opt);
+
+/* Step 2 of Section 5 (and the setup half of Section 3): builds everything
+ * that depends only on kappa.
+ *   kappa   n*n cell permeabilities (> 0, finite), host or device per opt;
+ *   grid    geometry; eig_tol the eigenvalue tolerance of Section 4.2
+ *           (functions with lambda < eig_tol kept, at least one per face);
+ *   stream  cudaStream_t (NULL = legacy default stream).
+ * Builds: oversampled patch inverses L_i^{+-1} (eq. smooth) in the requested
+ * precision; per-block snapshot spaces (eq. snapshot_eqn); per-face spectral
+ * problems (eqs. spectral_1, spectral_eqn); the coarse basis and the FP64
+ * coarse matrix R_H L_h R_H^T (eq. coarsepre) and its inverse; the coarse RT0
+ * matrix used by the preprocessing.  *out receives the handle. */
+int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol,
+             const tg_options* opt, void* stream, tg_handle** out);
+
+/* Steps 1, 3 and 4 of Section 5: preprocessing (Section 3, eq. subproblem),
+ * PCG on the reduced problem (eq. reduced_fine_system) preconditioned by the
+ * two-grid cycle (eqs. smooth, coarsepre), then v = vbar + vtilde and the
+ * pressure.
+ *   f      n*n cell-average source densities (F_c = h^2 f_c);
+ *   bflux  4n outward boundary normal velocities, or NULL for no flow (the
+ *          paper's case); sum F must equal the net outflow;
+ *   rtol   stop when ||C^T r||_2 <= rtol ||C^T r_0||_2 (Section 6: 1e-7);
+ *   ux, uy, p  outputs (p physical sign, zero mean, obtained by integrating
+ *          the discrete Darcy law A u = B^T p along grid lines with
+ *          least-squares row offsets);
+ *   iters  may be NULL; rep may be NULL.
+ * Returns TG_ERR_MAXITER (outputs written) if not converged. */
+int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol,
+             double* ux, double* uy, double* p, int* iters, tg_report* rep);
+
+/* Frees all device memory of the handle.  NULL is allowed. */
+void tg_destroy(tg_handle* h);
+
+/* Static message for an error code. */
+const char* tg_strerror(int code);
+
+/* ---- operator-level entry points (device pointers, psi vectors) ----------
+ * These expose single steps of the PCG iteration for verification; they run
+ * exactly the kernels tg_solve runs. */
+
+/* Fine operator of the reduced problem in stream-function form:
+ * out = C^T A_h C psi (A_h of eq. fine_system), in FP64 (precision 0) or
+ * FP32 arithmetic (precision 1). */
+int tg_apply_operator(tg_handle* h, const double* psi, double* out, int precision);
+
+/* Smoother of eq. smooth applied to the stream-function residual
+ * rho = C^T r: z = eta * sum_i E_i (K_i^+)^{-1} E_i^T rho, K_i^+ the
+ * oversampled local operator, in the handle's precision. */
+int tg_apply_smoother(tg_handle* h, const double* rho, double* z);
+
+/* Coarse correction of eq. coarsepre in stream-function form:
+ * z = Psi (Psi^T K Psi)^{-1} Psi^T rho, Psi spanning the divergence-free part
+ * of the coarse space. */
+int tg_apply_coarse(tg_handle* h, const double* rho, double* z);
+
+/* The two-grid preconditioner (Section 5: m1 smoothing steps, one coarse
+ * step, m2 smoothing steps, residual recomputed after each). */
+int tg_apply_preconditioner(tg_handle* h, const double* rho, double* z);
+
+/* Spectral data of the coarse space (Section 4.2), host arrays:
+ * nsel[nfaces] functions kept per coarse face, lambda[nfaces*b] all
+ * eigenvalues ascending.  Coarse faces are ordered vertical (x = I H,
+ * I = 1..nc-1, J = 0..nc-1, J-major) then horizontal (y = J H, J = 1..nc-1,
+ * I = 0..nc-1, J-major).  Any pointer may be NULL. */
+int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, double* lambda);
+
+/* Preprocessing of Section 3 alone: writes vbar (face arrays, device
+ * pointers) with B_h vbar = F_h and the given boundary flux. */
+int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TGMS_H */

@@ -1,0 +1,735 @@
+// C ABI of libtgms (declared in include/tgms.h): handle management, host-side
+// index tables of the coarse space, and the orchestration of the setup
+// (Step 2 of Section 5) and solve (Steps 1, 3, 4) kernels on one stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/tgms.h"
+#include "common.cuh"
+
+using namespace tg;
+
+struct tg_handle {
+  int n = 0, b = 0, nc = 0, ov = 0, nblocks = 0, npatch = 0, nfaces = 0;
+  double h = 0, H = 0, eig_tol = 0;
+  tg_options opt{};
+  cudaStream_t stream = nullptr;
+  // permeability
+  double* kinv = nullptr;
+  float* kinv32 = nullptr;
+  int* d_status = nullptr;
+  // smoother
+  PatchGeo* d_pgeo = nullptr;
+  void* pinv = nullptr;
+  // block factors (preprocessing)
+  double* blk_band = nullptr;
+  // spectral data
+  double* lam = nullptr;
+  std::vector<int> nsel;
+  std::vector<double> lam_h;
+  int velocity_basis = 0;
+  // coarse spaces: preconditioner and coarse RT0 (preprocessing)
+  CoarseSpace cs, rt;
+  // solve work
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rho = nullptr, *phi = nullptr;
+  void *zacc = nullptr, *rin = nullptr;
+  double *ux = nullptr, *uy = nullptr, *fd = nullptr, *bd = nullptr, *pd = nullptr, *pw = nullptr;
+  double *part = nullptr, *gx = nullptr, *gy = nullptr, *FH = nullptr, *absF = nullptr, *diverr = nullptr;
+  double* tmpd = nullptr;   // n*n scratch (operator hooks)
+  PcgState* st = nullptr;
+  int* h_flag = nullptr;    // pinned
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return TG_OK;
+  return (e == cudaErrorMemoryAllocation) ? TG_ERR_OOM : TG_ERR_CUDA;
+}
+
+#define TG_CK(call)                        \
+  do {                                     \
+    const int _rc = cuda_err((call));      \
+    if (_rc != TG_OK) return _rc;          \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cuda_err(cudaMalloc((void**)p, sizeof(T) * count));
+}
+
+void free_space(CoarseSpace& c) {
+  cudaFree(c.slot_ptr);
+  cudaFree(c.slots);
+  cudaFree(c.gather);
+  cudaFree(c.closed);
+  cudaFree(c.owned);
+  cudaFree(c.Kinv);
+  cudaFree(c.part);
+  cudaFree(c.coefs);
+  c = CoarseSpace{};
+}
+
+size_t ts_size(int precision) {
+  return precision == TG_PREC_F64 ? 8 : precision == TG_PREC_F32 ? 4 : 2;
+}
+
+int status_to_err(int st) {
+  if (st & kStBadKappa) return TG_ERR_INVALID_ARG;
+  if (st & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
+  if (st & kStNotSpd) return TG_ERR_BREAKDOWN;
+  if (st & kStDegenerate) return TG_ERR_DEGENERATE_BASIS;
+  if (st & kStBreakdown) return TG_ERR_BREAKDOWN;
+  if (st & kStMaxIter) return TG_ERR_MAXITER;
+  return TG_OK;
+}
+
+int read_status(tg_handle* h, int* out) {
+  TG_CK(cudaMemcpyAsync(h->h_flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  TG_CK(cudaStreamSynchronize(h->stream));
+  *out = *h->h_flag;
+  return TG_OK;
+}
+
+// Host-side index tables of a coarse space in per-block slot form.
+//   theta unknowns: interior coarse nodes (mI, mJ), 1 <= mI, mJ <= nc-1,
+//     index (mJ-1)(nc-1) + (mI-1);
+//   z unknowns: nsel[f]-1 per coarse face f, after all theta unknowns.
+int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool rt_only) {
+  const int nc = h->nc, b = h->b;
+  const int nV = nc * (nc - 1), nfaces = 2 * nc * (nc - 1);
+  const int ntheta = (nc - 1) * (nc - 1);
+  std::vector<int> zbase(nfaces + 1, ntheta);
+  for (int f = 0; f < nfaces; ++f) zbase[f + 1] = zbase[f] + (rt_only ? 0 : std::max(0, nsel[f] - 1));
+  c.D = zbase[nfaces];
+  std::vector<Slot> slots;
+  std::vector<int> ptr(h->nblocks + 1, 0);
+  auto face_of_side = [&](int side, int I, int J) {
+    if (side == 0) return J * (nc - 1) + (I - 1);
+    if (side == 1) return J * (nc - 1) + I;
+    if (side == 2) return nV + (J - 1) * nc + I;
+    return nV + J * nc + I;
+  };
+  for (int blk = 0; blk < h->nblocks; ++blk) {
+    const int I = blk % nc, J = blk / nc;
+    ptr[blk] = (int)slots.size();
+    const int cI[4] = {I, I + 1, I, I + 1}, cJ[4] = {J, J, J + 1, J + 1};
+    for (int k = 0; k < 4; ++k)
+      if (cI[k] >= 1 && cI[k] <= nc - 1 && cJ[k] >= 1 && cJ[k] <= nc - 1)
+        slots.push_back(Slot{blk, 0, k, 0, -1, (cJ[k] - 1) * (nc - 1) + (cI[k] - 1)});
+    if (!rt_only) {
+      const bool inner[4] = {I >= 1, I + 1 < nc, J >= 1, J + 1 < nc};
+      for (int s = 0; s < 4; ++s) {
+        if (!inner[s]) continue;
+        const int f = face_of_side(s, I, J);
+        for (int k = 1; k < nsel[f]; ++k) slots.push_back(Slot{blk, 1, s, k, f, zbase[f] + k - 1});
+      }
+    }
+  }
+  ptr[h->nblocks] = (int)slots.size();
+  c.nslots = (int)slots.size();
+  std::vector<int> gather((size_t)std::max(c.D, 1) * 4, -1);
+  for (int s = 0; s < c.nslots; ++s) {
+    int* g = &gather[(size_t)slots[s].coef * 4];
+    int k = 0;
+    while (k < 4 && g[k] >= 0) ++k;
+    if (k == 4) return TG_ERR_UNSUPPORTED;
+    g[k] = s;
+  }
+  c.max_slots_per_block = 0;
+  for (int blk = 0; blk < h->nblocks; ++blk)
+    c.max_slots_per_block = std::max(c.max_slots_per_block, ptr[blk + 1] - ptr[blk]);
+  const size_t ts = ts_size(h->opt.precision);
+  if (dalloc(&c.slot_ptr, ptr.size()) || dalloc(&c.slots, slots.size()) || dalloc(&c.gather, gather.size()) ||
+      dalloc(&c.closed, (size_t)c.nslots * (b + 1) * (b + 1)) || dalloc(&c.part, c.nslots) ||
+      dalloc(&c.coefs, c.D) || dalloc(&c.Kinv, (size_t)c.D * c.D))
+    return TG_ERR_OOM;
+  const size_t tsz = rt_only ? 8 : ts;  // the RT0 space of the preprocessing is FP64
+  TG_CK(cudaMalloc(&c.owned, std::max<size_t>(1, (size_t)c.nslots * b * b * tsz)));
+  TG_CK(cudaMemcpyAsync(c.slot_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, h->stream));
+  if (!slots.empty())
+    TG_CK(cudaMemcpyAsync(c.slots, slots.data(), sizeof(Slot) * slots.size(), cudaMemcpyHostToDevice,
+                          h->stream));
+  TG_CK(cudaMemcpyAsync(c.gather, gather.data(), sizeof(int) * gather.size(), cudaMemcpyHostToDevice,
+                        h->stream));
+  TG_CK(cudaStreamSynchronize(h->stream));  // host vectors go out of scope
+  return TG_OK;
+}
+
+// tiles, Galerkin matrix and its inverse
+int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double* fcoef, const double* zcoef,
+                 bool rt_only) {
+  const int b = h->b, n = h->n;
+  if (c.nslots > 0) {
+    if (rt_only || h->opt.precision == TG_PREC_F64)
+      launch_build_tiles<double>(c, psiS, fcoef, zcoef, rt_only ? 1 : 0, n, b, h->stream);
+    else if (h->opt.precision == TG_PREC_F32)
+      launch_build_tiles<float>(c, psiS, fcoef, zcoef, 0, n, b, h->stream);
+    else
+      launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, 0, n, b, h->stream);
+  }
+  if (c.D == 0) return cuda_err(cudaGetLastError());
+  // pair energy offsets
+  std::vector<int> ptr(h->nblocks + 1);
+  TG_CK(cudaMemcpy(ptr.data(), c.slot_ptr, sizeof(int) * ptr.size(), cudaMemcpyDeviceToHost));
+  std::vector<long long> pptr(h->nblocks + 1, 0);
+  for (int k = 0; k < h->nblocks; ++k) {
+    const long long m = ptr[k + 1] - ptr[k];
+    pptr[k + 1] = pptr[k] + m * m;
+  }
+  long long* d_pptr = nullptr;
+  double *pairE = nullptr, *tmp = nullptr;
+  int rc = TG_OK;
+  if ((rc = dalloc(&d_pptr, pptr.size())) || (rc = dalloc(&pairE, (size_t)pptr.back())) ||
+      (rc = dalloc(&tmp, (size_t)c.D * c.D))) {
+    cudaFree(d_pptr);
+    cudaFree(pairE);
+    return rc;
+  }
+  cudaMemcpyAsync(d_pptr, pptr.data(), sizeof(long long) * pptr.size(), cudaMemcpyHostToDevice, h->stream);
+  launch_galerkin(c, h->kinv, h->nblocks, n, b, pairE, d_pptr, c.Kinv, h->stream);
+  launch_gauss_jordan(c.Kinv, tmp, c.D, h->d_status, h->stream);
+  rc = cuda_err(cudaStreamSynchronize(h->stream));
+  cudaFree(d_pptr);
+  cudaFree(pairE);
+  cudaFree(tmp);
+  if (rc == TG_OK) rc = cuda_err(cudaGetLastError());
+  return rc;
+}
+
+// ---- the two-grid preconditioner (Section 5), zacc must be zero on entry ----
+template <typename TC, typename TS>
+void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st) {
+  const int n = h->n;
+  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
+  TC* rin = (TC*)h->rin;
+  const TS* pinv = (const TS*)h->pinv;
+  const double eta = h->opt.eta;
+  for (int k = 0; k < h->opt.m1; ++k) {
+    if (k == 0) {
+      launch_smoother<TC, TS, double>(h->d_pgeo, pinv, h->npatch, r, zacc, eta, n, st, h->stream);
+    } else {
+      launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, h->stream);
+    }
+  }
+  if (h->cs.D > 0) {
+    launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
+    launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, st, h->stream);
+    launch_coarse_solve(h->cs, st, h->stream);
+    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, st, h->stream);
+  }
+  for (int k = 0; k < h->opt.m2; ++k) {
+    launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, h->stream);
+  }
+}
+
+template <typename TC, typename TS>
+int run_pcg(tg_handle* h, double rtol) {
+  const int n = h->n;
+  const long long nn = (long long)n * n;
+  TC* zacc = (TC*)h->zacc;
+  // scalar head of PcgState
+  PcgState head{};
+  head.rtol2 = rtol * rtol;
+  head.maxit = std::min(h->opt.max_iter, kMaxHist);
+  head.flexible = h->opt.flexible;
+  TG_CK(cudaMemcpyAsync(h->st, &head, offsetof(PcgState, alphas), cudaMemcpyHostToDevice, h->stream));
+  TG_CK(cudaMemcpyAsync(h->r, h->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+  launch_pcg_init(h->x, h->r, h->part, h->st, n, h->stream);
+  TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
+  precondition<TC, TS>(h, h->r, zacc, h->st);
+  launch_pcg_init_rz<TC>(h->r, zacc, h->p, h->part, h->st, n, h->stream);
+  const int check = 2;
+  for (int it = 0; it < head.maxit; ++it) {
+    launch_pcg_apply_dot(h->p, h->kinv, h->q, h->part, h->st, n, h->stream);
+    launch_pcg_update_xr<TC>(h->x, h->r, h->p, h->q, zacc, h->part, h->st, n, h->stream);
+    precondition<TC, TS>(h, h->r, zacc, h->st);
+    launch_pcg_dots<TC>(h->r, zacc, h->q, h->part, h->st, n, h->stream);
+    launch_pcg_update_p<TC>(h->p, zacc, h->st, n, h->stream);
+    if ((it + 1) % check == 0 || it + 1 == head.maxit) {
+      TG_CK(cudaMemcpyAsync(h->h_flag, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      TG_CK(cudaStreamSynchronize(h->stream));
+      if (*h->h_flag) break;
+    }
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+int dispatch_pcg(tg_handle* h, double rtol) {
+  switch (h->opt.precision) {
+    case TG_PREC_F64: return run_pcg<double, double>(h, rtol);
+    case TG_PREC_F32: return run_pcg<float, float>(h, rtol);
+    default: return run_pcg<float, __nv_bfloat16>(h, rtol);
+  }
+}
+
+// Section 3: vbar into (ux, uy), and rho = C^T(-A vbar) (the PCG right-hand side)
+int preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
+  const int n = h->n, b = h->b;
+  const long long nn = (long long)n * n;
+  cudaStream_t s = h->stream;
+  launch_lift(bflux, ux, uy, n, s);
+  launch_block_sources(f, ux, uy, h->FH, h->absF, n, b, s);
+  launch_rt_particular(h->FH, h->absF, h->gx, h->gy, h->nc, h->H, h->nblocks, h->st, s);
+  launch_add_rt_field(h->gx, h->gy, ux, uy, n, b, s);
+  if (h->rt.D > 0) {
+    launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
+    launch_restrict<double, double>(h->rt, h->nblocks, h->nc, b, n, h->rho, nullptr, s);
+    launch_coarse_solve(h->rt, nullptr, s);
+    TG_CK(cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s));
+    launch_prolong<double, double>(h->rt, h->nblocks, h->nc, b, n, h->phi, nullptr, s);
+    launch_add_curl(h->phi, ux, uy, n, s);
+  }
+  launch_block_particular(f, ux, uy, n, b, s);
+  if (b >= 2) {
+    launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
+    TG_CK(cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s));
+    launch_block_solve(h->blk_band, h->rho, h->phi, n, b, s);
+    launch_add_curl(h->phi, ux, uy, n, s);
+  }
+  launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
+  return cuda_err(cudaGetLastError());
+}
+
+// extreme eigenvalues of the Lanczos tridiagonal by Sturm bisection (report only)
+double lanczos_cond(const PcgState& st) {
+  const int m = std::min(st.iter, kMaxHist);
+  if (m <= 0) return 1.0;
+  std::vector<double> d(m), e(m > 1 ? m - 1 : 1, 0.0);
+  for (int j = 0; j < m; ++j) d[j] = 1.0 / st.alphas[j] + (j > 0 ? st.betas[j - 1] / st.alphas[j - 1] : 0.0);
+  for (int j = 0; j + 1 < m; ++j) e[j] = std::sqrt(std::max(0.0, st.betas[j])) / st.alphas[j];
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < m; ++j) {
+    const double rad = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < m ? std::fabs(e[j]) : 0.0);
+    lo = std::min(lo, d[j] - rad);
+    hi = std::max(hi, d[j] + rad);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int j = 1; j < m; ++j) {
+      if (q == 0.0) q = 1e-300;
+      q = d[j] - x - e[j - 1] * e[j - 1] / q;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  auto kth = [&](int k) {  // k-th smallest (0-based)
+    double a = lo, c = hi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + c);
+      if (count_below(mid) > k) c = mid;
+      else a = mid;
+    }
+    return 0.5 * (a + c);
+  };
+  const double lmin = kth(0), lmax = kth(m - 1);
+  return (lmin > 0) ? lmax / lmin : INFINITY;
+}
+
+int validate_grid(const tg_grid* g) {
+  if (!g) return TG_ERR_INVALID_ARG;
+  if (g->nx != g->ny || g->bx != g->by) return TG_ERR_UNSUPPORTED;
+  if (g->nx < 2 || g->bx < 2 || g->nx % g->bx != 0) return TG_ERR_INVALID_ARG;
+  if (g->bx > kMaxB) return TG_ERR_UNSUPPORTED;
+  if (g->overlap < 0 || g->overlap > kMaxOverlap) return TG_ERR_UNSUPPORTED;
+  if ((long long)g->nx * g->nx > (1LL << 30)) return TG_ERR_UNSUPPORTED;
+  return TG_OK;
+}
+
+int setup_impl(tg_handle* h, const double* kappa) {
+  const int n = h->n, b = h->b, nc = h->nc;
+  const long long nn = (long long)n * n;
+  cudaStream_t s = h->stream;
+  TG_CK(cudaMallocHost(&h->h_flag, sizeof(int)));
+  for (auto& e : h->ev) TG_CK(cudaEventCreate(&e));
+  TG_CK(cudaMalloc(&h->d_status, sizeof(int)));
+  TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
+  if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn)) return TG_ERR_OOM;
+  const double* kd = kappa;
+  double* kcopy = nullptr;
+  if (h->opt.pointer_mode == TG_PTR_HOST) {
+    if (dalloc(&kcopy, nn)) return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(kcopy, kappa, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    kd = kcopy;
+  }
+  launch_kinv(kd, h->kinv, h->kinv32, h->d_status, n, s);
+  int st = 0;
+  int rc = read_status(h, &st);
+  cudaFree(kcopy);
+  if (rc) return rc;
+  if (st) return status_to_err(st);
+
+  // ---- oversampled patches: local operators, band Cholesky, inverses ----
+  std::vector<int4> prect(h->npatch);
+  std::vector<PatchGeo> geo(h->npatch);
+  long long off = 0;
+  int wmax = 0, nmax = 0;
+  for (int J = 0; J < nc; ++J)
+    for (int I = 0; I < nc; ++I) {
+      const int k = J * nc + I;
+      const int x0 = std::max(0, I * b - h->ov), x1 = std::min(n, (I + 1) * b + h->ov);
+      const int y0 = std::max(0, J * b - h->ov), y1 = std::min(n, (J + 1) * b + h->ov);
+      PatchGeo g{};
+      g.x0 = x0; g.y0 = y0; g.nx = x1 - x0 - 1; g.ny = y1 - y0 - 1;
+      g.nloc = g.nx * g.ny;
+      g.ld = ((g.nloc + 7) / 8) * 8;
+      g.off = off;
+      off += (long long)g.nloc * g.ld;
+      geo[k] = g;
+      prect[k] = make_int4(x0, y0, g.nx, g.ny);
+      wmax = std::max(wmax, g.nx + 1);
+      nmax = std::max(nmax, g.nloc);
+    }
+  int4* d_prect = nullptr;
+  double *band = nullptr, *scratch = nullptr;
+  if (dalloc(&h->d_pgeo, geo.size()) || dalloc(&d_prect, prect.size()) ||
+      dalloc(&band, (size_t)h->npatch * nmax * (wmax + 1)))
+    return TG_ERR_OOM;
+  TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
+  TG_CK(cudaMemcpyAsync(h->d_pgeo, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, s));
+  TG_CK(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
+  launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
+  launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
+  const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
+  if (dalloc(&scratch, (size_t)batch * nmax * nmax)) return TG_ERR_OOM;
+  for (int first = 0; first < h->npatch; first += batch) {
+    const int cnt = std::min(batch, h->npatch - first);
+    launch_band_inverse(band, d_prect, first, cnt, wmax, nmax, scratch, s);
+    if (h->opt.precision == TG_PREC_F64)
+      launch_store_inverse<double>(scratch, h->d_pgeo, first, cnt, nmax, (double*)h->pinv, s);
+    else if (h->opt.precision == TG_PREC_F32)
+      launch_store_inverse<float>(scratch, h->d_pgeo, first, cnt, nmax, (float*)h->pinv, s);
+    else
+      launch_store_inverse<__nv_bfloat16>(scratch, h->d_pgeo, first, cnt, nmax, (__nv_bfloat16*)h->pinv, s);
+  }
+  rc = cuda_err(cudaStreamSynchronize(s));
+  cudaFree(scratch);
+  cudaFree(band);
+  cudaFree(d_prect);
+  if (rc) return rc;
+  TG_CK(cudaGetLastError());
+
+  // ---- coarse blocks: local operators and band Cholesky factors ----
+  {
+    std::vector<int4> brect(h->nblocks);
+    for (int J = 0; J < nc; ++J)
+      for (int I = 0; I < nc; ++I) brect[J * nc + I] = make_int4(I * b, J * b, b - 1, b - 1);
+    int4* d_brect = nullptr;
+    const int bw = b, bn = (b - 1) * (b - 1);
+    if (dalloc(&d_brect, brect.size()) || dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1)))
+      return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(d_brect, brect.data(), sizeof(int4) * brect.size(), cudaMemcpyHostToDevice, s));
+    if (bn > 0) {
+      launch_assemble_band(h->kinv, d_brect, h->blk_band, h->nblocks, bw, bn, n, s);
+      launch_band_cholesky(h->blk_band, d_brect, h->nblocks, bw, bn, h->d_status, s);
+    }
+    rc = cuda_err(cudaStreamSynchronize(s));
+    cudaFree(d_brect);
+    if (rc) return rc;
+  }
+
+  // ---- snapshot spaces and local spectral problems (Section 4) ----
+  h->nsel.assign(h->nfaces, 1);
+  double *psiS = nullptr, *gram = nullptr, *fcoef = nullptr, *zcoef = nullptr;
+  int* d_nsel = nullptr;
+  if (h->nfaces > 0 && h->opt.coarse_space != TG_COARSE_RT0) {
+    if (dalloc(&psiS, (size_t)h->nblocks * 4 * b * (b + 1) * (b + 1)) ||
+        dalloc(&gram, (size_t)h->nblocks * 4 * b * b) || dalloc(&h->lam, (size_t)h->nfaces * b) ||
+        dalloc(&d_nsel, h->nfaces) || dalloc(&fcoef, (size_t)h->nfaces * b) ||
+        dalloc(&zcoef, (size_t)h->nfaces * (b - 1) * b))
+      return TG_ERR_OOM;
+    TG_CK(cudaMemsetAsync(zcoef, 0, sizeof(double) * (size_t)h->nfaces * (b - 1) * b, s));
+    launch_snapshots(h->kinv, h->blk_band, psiS, gram, n, b, s);
+    const int mode = (h->opt.coarse_space == TG_COARSE_MSFEM) ? 1 : 0;
+    launch_face_eigen(h->kinv, gram, h->eig_tol, h->opt.max_basis, mode, n, b, h->lam, d_nsel, fcoef, zcoef,
+                      h->d_status, s);
+    TG_CK(cudaMemcpyAsync(h->nsel.data(), d_nsel, sizeof(int) * h->nfaces, cudaMemcpyDeviceToHost, s));
+    h->lam_h.resize((size_t)h->nfaces * b);
+    TG_CK(cudaMemcpyAsync(h->lam_h.data(), h->lam, sizeof(double) * h->lam_h.size(), cudaMemcpyDeviceToHost, s));
+    if ((rc = read_status(h, &st))) return rc;
+    if (st) return status_to_err(st);
+  }
+  h->velocity_basis = 0;
+  for (int v : h->nsel) h->velocity_basis += v;
+
+  // ---- coarse spaces: preconditioner (GMsFEM / MsFEM / RT0) and RT0 ----
+  const bool rt_mode = (h->opt.coarse_space == TG_COARSE_RT0);
+  if ((rc = build_space(h, h->cs, h->nsel, rt_mode))) return rc;
+  if ((rc = finish_space(h, h->cs, psiS, fcoef, zcoef, rt_mode))) return rc;
+  std::vector<int> ones(h->nfaces, 1);
+  if ((rc = build_space(h, h->rt, ones, true))) return rc;
+  if ((rc = finish_space(h, h->rt, nullptr, nullptr, nullptr, true))) return rc;
+  cudaFree(psiS);
+  cudaFree(gram);
+  cudaFree(fcoef);
+  cudaFree(zcoef);
+  cudaFree(d_nsel);
+  if ((rc = read_status(h, &st))) return rc;
+  if (st) return status_to_err(st);
+
+  // ---- solve work space ----
+  const size_t tc = (h->opt.precision == TG_PREC_F64) ? 8 : 4;
+  const long long nf = (long long)(n + 1) * n;
+  if (dalloc(&h->x, nn) || dalloc(&h->r, nn) || dalloc(&h->p, nn) || dalloc(&h->q, nn) ||
+      dalloc(&h->rho, nn) || dalloc(&h->phi, nn) || dalloc(&h->tmpd, nn) || dalloc(&h->ux, nf) ||
+      dalloc(&h->uy, nf) || dalloc(&h->fd, nn) || dalloc(&h->bd, 4 * n) || dalloc(&h->pd, nn) ||
+      dalloc(&h->pw, nn + 2 * n + 2) || dalloc(&h->part, 4 * kRedGrid) || dalloc(&h->gx, (nc + 1) * nc) ||
+      dalloc(&h->gy, (nc + 1) * nc) || dalloc(&h->FH, h->nblocks) || dalloc(&h->absF, h->nblocks) ||
+      dalloc(&h->diverr, 2) || dalloc(&h->st, 1))
+    return TG_ERR_OOM;
+  TG_CK(cudaMalloc(&h->zacc, tc * nn));
+  TG_CK(cudaMalloc(&h->rin, tc * nn));
+  TG_CK(cudaMemsetAsync(h->st, 0, sizeof(PcgState), s));
+  TG_CK(cudaStreamSynchronize(s));
+  return cuda_err(cudaGetLastError());
+}
+
+template <typename TC, typename TS>
+int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
+  const int n = h->n;
+  const long long nn = (long long)n * n;
+  TC* zacc = (TC*)h->zacc;
+  TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
+  if (which == 0) {
+    launch_smoother<TC, TS, double>(h->d_pgeo, (const TS*)h->pinv, h->npatch, rho, zacc, h->opt.eta, n, nullptr,
+                                    h->stream);
+  } else if (which == 1) {
+    if (h->cs.D > 0) {
+      TC* rin = (TC*)h->rin;
+      if (std::is_same<TC, double>::value)
+        TG_CK(cudaMemcpyAsync(rin, rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+      else
+        launch_convert<double, float>(rho, (float*)rin, nn, h->stream);
+      launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, nullptr, h->stream);
+      launch_coarse_solve(h->cs, nullptr, h->stream);
+      launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
+    }
+  } else {
+    precondition<TC, TS>(h, rho, zacc, nullptr);
+  }
+  if (std::is_same<TC, double>::value)
+    TG_CK(cudaMemcpyAsync(z, zacc, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+  else
+    launch_convert<float, double>((const float*)zacc, z, nn, h->stream);
+  TG_CK(cudaStreamSynchronize(h->stream));
+  return cuda_err(cudaGetLastError());
+}
+
+int hook_dispatch(tg_handle* h, const double* rho, double* z, int which) {
+  if (!h || !rho || !z) return TG_ERR_INVALID_ARG;
+  switch (h->opt.precision) {
+    case TG_PREC_F64: return hook_precond<double, double>(h, rho, z, which);
+    case TG_PREC_F32: return hook_precond<float, float>(h, rho, z, which);
+    default: return hook_precond<float, __nv_bfloat16>(h, rho, z, which);
+  }
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int tg_default_options(tg_options* opt) {
+  if (!opt) return TG_ERR_INVALID_ARG;
+  opt->eta = 0.2;
+  opt->m1 = 1;
+  opt->m2 = 1;
+  opt->precision = TG_PREC_F64;
+  opt->flexible = 0;
+  opt->max_iter = 1000;
+  opt->pointer_mode = TG_PTR_DEVICE;
+  opt->coarse_space = TG_COARSE_GMSFEM;
+  opt->max_basis = 0;
+  return TG_OK;
+}
+
+const char* tg_strerror(int code) {
+  switch (code) {
+    case TG_OK: return "success";
+    case TG_ERR_INVALID_ARG: return "invalid argument (sizes, block size, kappa <= 0 or not finite, NULL)";
+    case TG_ERR_INCOMPATIBLE_SOURCE: return "incompatible source: sum of F differs from the net boundary outflow";
+    case TG_ERR_BREAKDOWN: return "breakdown: a matrix that must be positive definite is not (PCG or a factor)";
+    case TG_ERR_MAXITER: return "PCG did not converge within max_iter";
+    case TG_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait expired";
+    case TG_ERR_CUDA: return "CUDA runtime error";
+    case TG_ERR_OOM: return "device memory allocation failed";
+    case TG_ERR_UNSUPPORTED: return "configuration not supported by this build";
+    case TG_ERR_DEGENERATE_BASIS: return "a coarse face has no selected function with net flux";
+    default: return "unknown error code";
+  }
+}
+
+int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_options* opt, void* stream,
+             tg_handle** out) {
+  if (!out) return TG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!kappa || !opt) return TG_ERR_INVALID_ARG;
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (!(opt->eta > 0) || opt->m1 < 0 || opt->m2 < 0 || opt->m1 + opt->m2 < 1 || opt->max_iter < 1 ||
+      opt->precision < 0 || opt->precision > 2 || opt->coarse_space < 0 || opt->coarse_space > 2 ||
+      !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
+    return TG_ERR_INVALID_ARG;
+  if (opt->m1 < 1) return TG_ERR_UNSUPPORTED;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TG_ERR_CUDA;
+  tg_handle* h = new (std::nothrow) tg_handle();
+  if (!h) return TG_ERR_OOM;
+  h->n = grid->nx;
+  h->b = grid->bx;
+  h->nc = h->n / h->b;
+  h->ov = grid->overlap;
+  h->nblocks = h->nc * h->nc;
+  h->npatch = h->nblocks;
+  h->nfaces = 2 * h->nc * (h->nc - 1);
+  h->h = 1.0 / h->n;
+  h->H = (double)h->b / h->n;
+  h->eig_tol = eig_tol;
+  h->opt = *opt;
+  h->stream = (cudaStream_t)stream;
+  rc = setup_impl(h, kappa);
+  if (rc) {
+    tg_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return TG_OK;
+}
+
+int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
+             int* iters, tg_report* rep) {
+  if (!h || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
+  const int n = h->n;
+  const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
+  cudaStream_t s = h->stream;
+  const bool host = (h->opt.pointer_mode == TG_PTR_HOST);
+  const double* fdev = f;
+  const double* bdev = bflux;
+  if (host) {
+    TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    fdev = h->fd;
+    if (bflux) {
+      TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, s));
+      bdev = h->bd;
+    }
+  }
+  double* uxd = host ? h->ux : ux;
+  double* uyd = host ? h->uy : uy;
+  double* pdv = host ? h->pd : p;
+  TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
+  TG_CK(cudaMemsetAsync(h->st, 0, offsetof(PcgState, alphas), s));
+  cudaEventRecord(h->ev[0], s);
+  int rc = preprocess(h, fdev, bdev, uxd, uyd);
+  if (rc) return rc;
+  // incompatible source check (set by the coarse RT0 step)
+  PcgState head{};
+  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  if (head.status & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
+  cudaEventRecord(h->ev[1], s);
+  if ((rc = dispatch_pcg(h, rtol))) return rc;
+  cudaEventRecord(h->ev[2], s);
+  launch_add_curl(h->x, uxd, uyd, n, s);
+  launch_pressure(uxd, uyd, h->kinv, pdv, h->pw, n, s);
+  cudaEventRecord(h->ev[3], s);
+  launch_div_error(uxd, uyd, fdev, h->part, h->diverr, n, s);
+  if (host) {
+    TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+    TG_CK(cudaMemcpyAsync(p, h->pd, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+  }
+  PcgState* full = new (std::nothrow) PcgState();
+  if (!full) return TG_ERR_OOM;
+  double diverr = 0.0;
+  rc = cuda_err(cudaMemcpyAsync(full, h->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(&diverr, h->diverr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  if (!rc) rc = cuda_err(cudaGetLastError());
+  if (rc) {
+    delete full;
+    return rc;
+  }
+  if (iters) *iters = full->iter;
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->iters = full->iter;
+    rep->rel_residual = (full->rr0 > 0) ? std::sqrt(full->rr / full->rr0) : 0.0;
+    rep->converged = (full->rr <= full->rtol2 * full->rr0) ? 1 : 0;
+    rep->cond_estimate = lanczos_cond(*full);
+    rep->velocity_basis = h->velocity_basis;
+    rep->coarse_dim = h->velocity_basis + h->nc * h->nc + 1;
+    rep->coarse_unknowns = h->cs.D;
+    rep->max_div_error = diverr;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+    rep->preprocess_ms = ms;
+    cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
+    rep->pcg_ms = ms;
+    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+    rep->epilogue_ms = ms;
+  }
+  const int status = full->status;
+  delete full;
+  return status_to_err(status);
+}
+
+void tg_destroy(tg_handle* h) {
+  if (!h) return;
+  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->pinv, h->blk_band, h->lam,
+                  h->x, h->r, h->p, h->q, h->rho, h->phi, h->zacc, h->rin, h->ux, h->uy, h->fd,
+                  h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st};
+  for (void* ptr : ptrs) cudaFree(ptr);
+  free_space(h->cs);
+  free_space(h->rt);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+int tg_apply_operator(tg_handle* h, const double* psi, double* out, int precision) {
+  if (!h || !psi || !out || precision < 0 || precision > 1) return TG_ERR_INVALID_ARG;
+  if (precision == 0) launch_apply_operator(psi, h->kinv, out, h->n, h->stream);
+  else launch_apply_operator_f32(psi, h->kinv32, out, h->n, h->stream);
+  TG_CK(cudaStreamSynchronize(h->stream));
+  return cuda_err(cudaGetLastError());
+}
+
+int tg_apply_smoother(tg_handle* h, const double* rho, double* z) { return hook_dispatch(h, rho, z, 0); }
+int tg_apply_coarse(tg_handle* h, const double* rho, double* z) { return hook_dispatch(h, rho, z, 1); }
+int tg_apply_preconditioner(tg_handle* h, const double* rho, double* z) { return hook_dispatch(h, rho, z, 2); }
+
+int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, double* lambda) {
+  if (!h) return TG_ERR_INVALID_ARG;
+  if (nfaces) *nfaces = h->nfaces;
+  if (velocity_basis) *velocity_basis = h->velocity_basis;
+  if (nsel) std::memcpy(nsel, h->nsel.data(), sizeof(int) * h->nsel.size());
+  if (lambda && !h->lam_h.empty()) std::memcpy(lambda, h->lam_h.data(), sizeof(double) * h->lam_h.size());
+  return TG_OK;
+}
+
+int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
+  if (!h || !f || !ux || !uy) return TG_ERR_INVALID_ARG;
+  TG_CK(cudaMemsetAsync(h->st, 0, offsetof(PcgState, alphas), h->stream));
+  int rc = preprocess(h, f, bflux, ux, uy);
+  if (rc) return rc;
+  PcgState head{};
+  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, h->stream));
+  TG_CK(cudaStreamSynchronize(h->stream));
+  if (head.status & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
+  return TG_OK;
+}
+
+}  // extern "C"

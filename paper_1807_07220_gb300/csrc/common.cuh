@@ -1,0 +1,233 @@
+// Internal declarations shared by the libtgms translation units.
+//
+// Device data layout (n x n fine cells, h = 1/n, blocks of b x b cells,
+// nc = n/b blocks per side):
+//   node vectors ("psi vectors"): n*n, node (i, j) at j*n + i; nodes with
+//     i == 0 or j == 0 are boundary nodes and are kept at zero; nodes with
+//     i == n or j == n are implicit zeros;
+//   cell arrays: n*n, cell (i, j) at j*n + i;
+//   face arrays: ux (n+1)*n at j*(n+1)+i, uy n*(n+1) at j*n+i;
+//   block (I, J) owns the nodes [I b, (I+1) b) x [J b, (J+1) b); its closed
+//     node set [I b, (I+1) b] x [J b, (J+1) b] is stored locally as
+//     (a, c) -> c*(b+1) + a; its interior nodes a, c in [1, b-1] as
+//     (c-1)*(b-1) + (a-1);
+//   patch (= oversampled block K_i^+) interior nodes: x0 < i < x1,
+//     y0 < j < y1 for the clipped cell rectangle [x0, x1) x [y0, y1),
+//     local index (j-y0-1)*nx + (i-x0-1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace tg {
+
+constexpr int kMaxB = 16;                 // largest supported block size b
+constexpr int kMaxOverlap = 2;
+constexpr int kMaxPatchSide = kMaxB + 2 * kMaxOverlap - 1;   // interior nodes per side
+constexpr int kMaxPatchNodes = kMaxPatchSide * kMaxPatchSide;
+constexpr int kMaxHist = 4096;            // PCG coefficient history
+constexpr int kRedGrid = 512;             // CTAs of grid-stride reduction kernels
+
+// status bits raised by device code
+enum : int {
+  kStOk = 0,
+  kStBadKappa = 1,
+  kStNotSpd = 2,
+  kStBreakdown = 4,
+  kStIncompatible = 8,
+  kStDegenerate = 16,
+  kStMaxIter = 32,
+};
+
+struct PatchGeo {
+  int x0, y0;      // lower-left cell of the clipped patch rectangle
+  int nx, ny;      // interior nodes per side
+  int nloc;        // nx * ny
+  int ld;          // row stride of the stored inverse (multiple of 8)
+  long long off;   // element offset of the stored inverse
+};
+
+// Scalars of the PCG iteration, updated only by the last CTA of a
+// reduction kernel (so no CTA reads a value written in its own kernel).
+struct PcgState {
+  double rz;        // (r, z) of the current iterate
+  double rz_prev;   // (r, z) of the previous iterate (flexible beta)
+  double rr0;       // ||r_0||^2
+  double rr;        // ||r||^2
+  double rtol2;     // rtol^2
+  double alpha, beta, pq, zq;
+  int iter;         // completed iterations
+  int maxit;
+  int done;         // 1: stop (converged, breakdown or max_iter)
+  int status;       // kSt* bits
+  int flexible;
+  unsigned int counter[4];   // arrival counters of last-CTA reductions
+  double alphas[kMaxHist];
+  double betas[kMaxHist];
+};
+
+// One coarse-space slot: a basis function restricted to one block.
+struct Slot {
+  int block;
+  int kind;        // 0: nodal function theta_m (corner), 1: zero-flux function z_{E,k}
+  int which;       // corner (0 BL, 1 BR, 2 TL, 3 TR) or side (0 L, 1 R, 2 B, 3 T)
+  int k;           // zero-flux index (1..nsel-1)
+  int face;        // coarse face of the side (kind 1) or -1
+  int coef;        // coarse unknown
+};
+
+// Coarse space in per-block slot form.
+struct CoarseSpace {
+  int D = 0;                 // coarse unknowns
+  int nslots = 0;
+  int* slot_ptr = nullptr;   // nblocks+1, CSR over blocks (device)
+  Slot* slots = nullptr;     // device
+  int* gather = nullptr;     // D*4 global slot ids (-1 = none) (device)
+  double* closed = nullptr;  // nslots*(b+1)^2 FP64 tiles (device)
+  void* owned = nullptr;     // nslots*b*b tiles in storage precision (device)
+  double* Kinv = nullptr;    // D*D inverse of the Galerkin matrix (device)
+  double* part = nullptr;    // nslots partial restrictions (device)
+  double* coefs = nullptr;   // D coarse solution (device)
+  int max_slots_per_block = 0;
+};
+
+// ---- small device helpers --------------------------------------------------
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double to_f(double x) { return x; }
+
+template <typename T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double x) {
+  return __float2bfloat16_rn((float)x);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// 9-point stencil of K = C^T A_h C at interior node (i, j) (1 <= i, j < n),
+// written with the inverse permeabilities of the four cells around the node:
+// k00 = (i-1, j-1), k10 = (i, j-1), k01 = (i-1, j), k11 = (i, j).
+template <typename TV, typename TK, typename TA>
+__device__ __forceinline__ TA stencil_apply(const TV* __restrict__ psi, const TK* __restrict__ kinv,
+                                            int n, int i, int j) {
+  const long long c = (long long)j * n + i;
+  const bool e = (i + 1 < n), N = (j + 1 < n);
+  const TA p0 = (TA)psi[c];
+  const TA pw = (TA)psi[c - 1];
+  const TA ps = (TA)psi[c - n];
+  const TA psw = (TA)psi[c - n - 1];
+  const TA pe = e ? (TA)psi[c + 1] : (TA)0;
+  const TA pse = e ? (TA)psi[c - n + 1] : (TA)0;
+  const TA pn = N ? (TA)psi[c + n] : (TA)0;
+  const TA pnw = N ? (TA)psi[c + n - 1] : (TA)0;
+  const TA pne = (e && N) ? (TA)psi[c + n + 1] : (TA)0;
+  const TA k11 = (TA)kinv[c], k01 = (TA)kinv[c - 1];
+  const TA k10 = (TA)kinv[c - n], k00 = (TA)kinv[c - n - 1];
+  const TA third = (TA)(1.0 / 3.0), sixth = (TA)(1.0 / 6.0);
+  TA out = (TA)(2.0 / 3.0) * (k00 + k10 + k01 + k11) * p0;
+  out -= sixth * ((k00 + k10) * ps + (k01 + k11) * pn + (k00 + k01) * pw + (k10 + k11) * pe);
+  out -= third * (k00 * psw + k10 * pse + k01 * pnw + k11 * pne);
+  return out;
+}
+
+// Sum of a partial array by one warp in a fixed order (deterministic).
+__device__ __forceinline__ double warp_sum_array(const double* a, int m) {
+  double s = 0.0;
+  for (int k = threadIdx.x & 31; k < m; k += 32) s += a[k];
+  return warp_sum(s);
+}
+
+}  // namespace tg
+
+// ---- launchers (host functions, implemented in the kernel files) ----------
+namespace tg {
+
+// fine operator / vectors (fine.cu)
+void launch_apply_operator(const double* psi, const double* kinv, double* out, int n, cudaStream_t s);
+void launch_apply_operator_f32(const double* psi, const float* kinv, double* out, int n, cudaStream_t s);
+
+template <typename TC>
+void launch_residual(const double* r, const TC* z, const TC* kinv, TC* out, int n, const PcgState* st,
+                     cudaStream_t s);
+
+void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part,
+                          PcgState* st, int n, cudaStream_t s);
+template <typename TC>
+void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
+                          double* part, PcgState* st, int n, cudaStream_t s);
+template <typename TC>
+void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st,
+                     int n, cudaStream_t s);
+template <typename TC>
+void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s);
+void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s);
+template <typename TC>
+void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,
+                        cudaStream_t s);
+
+template <typename TC, typename TS, typename TR>
+void launch_smoother(const PatchGeo* geo, const TS* pinv, int npatch, const TR* r, TC* zacc,
+                     double eta, int n, const PcgState* st, cudaStream_t s);
+
+template <typename TC, typename TS>
+void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
+                     const PcgState* st, cudaStream_t s);
+void launch_coarse_solve(const CoarseSpace& cs, const PcgState* st, cudaStream_t s);
+template <typename TC, typename TS>
+void launch_prolong(const CoarseSpace& cs, int nblocks, int nc, int b, int n, TC* v,
+                    const PcgState* st, cudaStream_t s);
+
+template <typename TA, typename TB>
+void launch_convert(const TA* a, TB* b, long long m, cudaStream_t s);
+
+// preprocessing and epilogue (pre.cu)
+void launch_lift(const double* bflux, double* ux, double* uy, int n, cudaStream_t s);
+void launch_block_sources(const double* f, const double* ux, const double* uy, double* FH,
+                          double* absF, int n, int b, cudaStream_t s);
+void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc,
+                          double H, int nblocks, PcgState* st, cudaStream_t s);
+void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
+                         cudaStream_t s);
+void launch_face_residual(const double* ux, const double* uy, const double* kinv, double* rho,
+                          int n, cudaStream_t s);
+void launch_add_curl(const double* psi, double* ux, double* uy, int n, cudaStream_t s);
+void launch_block_particular(const double* f, double* ux, double* uy, int n, int b, cudaStream_t s);
+void launch_block_solve(const double* chol, const double* rho, double* phi, int n, int b,
+                        cudaStream_t s);
+void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p,
+                     double* work, int n, cudaStream_t s);
+void launch_div_error(const double* ux, const double* uy, const double* f, double* part,
+                      double* out, int n, cudaStream_t s);
+
+// setup (setup.cu)
+void launch_kinv(const double* kappa, double* kinv, float* kinv32, int* status, int n,
+                 cudaStream_t s);
+void launch_assemble_band(const double* kinv, const int4* rects, double* band, int nmat, int wmax,
+                          int nmax, int n, cudaStream_t s);
+void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, int nmax,
+                          int* status, cudaStream_t s);
+void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax,
+                         int nmax, double* scratch, cudaStream_t s);
+template <typename TS>
+void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count,
+                          int nmax, TS* pinv, cudaStream_t s);
+void launch_snapshots(const double* kinv, const double* blk_band, double* psiS, double* gram,
+                      int n, int b, cudaStream_t s);
+void launch_face_eigen(const double* kinv, const double* gram, double eig_tol, int max_basis,
+                       int mode, int n, int b, double* lam, int* nsel, double* fcoef,
+                       double* zcoef, int* status, cudaStream_t s);
+template <typename TS>
+void launch_build_tiles(const CoarseSpace& cs, const double* psiS, const double* fcoef,
+                        const double* zcoef, int rt_only, int n, int b, cudaStream_t s);
+void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b,
+                     double* pairE, const long long* pair_ptr, double* K, cudaStream_t s);
+void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s);  // result in A
+
+}  // namespace tg

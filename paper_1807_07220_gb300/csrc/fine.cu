@@ -1,0 +1,560 @@
+// Kernels of one PCG iteration on the reduced (divergence-free) problem in
+// stream-function form: fine operator, vector updates with on-device
+// scalars, patch smoother (eq. smooth), coarse restriction / solve /
+// prolongation (eq. coarsepre).
+//
+// Scalar reductions use the "last CTA" pattern: every CTA writes its partial
+// sum, fences, and bumps an arrival counter; the CTA that arrives last sums
+// the partials in a fixed order and updates PcgState.  Consumers read the
+// scalars in the next kernel, so no CTA ever reads a value written in its own
+// launch.  Every kernel of the loop returns at once when PcgState::done is set.
+#include "common.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// Writes this CTA's partial and returns true in every thread of the CTA that
+// arrived last (whose threads may then read all partials of the launch).
+__device__ __forceinline__ bool arrive_last(double partial, double* part, unsigned int* counter) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = partial;
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ double sum_partials(const double* part, int m) {
+  double s = 0.0;
+  for (int k = threadIdx.x & 31; k < m; k += 32) s += __ldcg(part + k);
+  return warp_sum(s);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_apply_operator(const double* __restrict__ psi,
+                                                             const double* __restrict__ kinv,
+                                                             double* __restrict__ out, int n) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    out[t] = (i == 0 || j == 0) ? 0.0 : stencil_apply<double, double, double>(psi, kinv, n, i, j);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply_operator_f32(const double* __restrict__ psi,
+                                                                 const float* __restrict__ kinv,
+                                                                 double* __restrict__ out, int n) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    out[t] = (i == 0 || j == 0) ? 0.0 : (double)stencil_apply<double, float, float>(psi, kinv, n, i, j);
+  }
+}
+
+// out = r - K z  (inner residual of the two-grid cycle, precision TC)
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_residual(const double* __restrict__ r,
+                                                       const TC* __restrict__ z,
+                                                       const TC* __restrict__ kinv,
+                                                       TC* __restrict__ out, int n,
+                                                       const PcgState* st) {
+  if (st && st->done) return;
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    TC v = (TC)0;
+    if (i != 0 && j != 0) v = (TC)r[t] - stencil_apply<TC, TC, TC>(z, kinv, n, i, j);
+    out[t] = v;
+  }
+}
+
+// q = K p, alpha = rz / (p, q)
+__global__ void __launch_bounds__(kThreads) k_pcg_apply_dot(const double* __restrict__ p,
+                                                            const double* __restrict__ kinv,
+                                                            double* __restrict__ q,
+                                                            double* part, PcgState* st, int n) {
+  if (st->done) return;
+  __shared__ double sh[32];
+  const long long nn = (long long)n * n;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    double v = 0.0;
+    if (i != 0 && j != 0) v = stencil_apply<double, double, double>(p, kinv, n, i, j);
+    q[t] = v;
+    acc += v * p[t];
+  }
+  acc = block_sum(acc, sh);
+  if (arrive_last(acc, part, &st->counter[0]) && threadIdx.x < 32) {
+    const double pq = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[0] = 0;
+      st->pq = pq;
+      const double alpha = st->rz / pq;
+      if (!(pq > 0.0) || !isfinite(alpha)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+        st->alpha = 0.0;
+      } else {
+        st->alpha = alpha;
+        if (st->iter < kMaxHist) st->alphas[st->iter] = alpha;
+      }
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, zacc = 0, rr = (r, r); convergence decision
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_pcg_update_xr(double* __restrict__ x,
+                                                            double* __restrict__ r,
+                                                            const double* __restrict__ p,
+                                                            const double* __restrict__ q,
+                                                            TC* __restrict__ zacc, double* part,
+                                                            PcgState* st, int n) {
+  if (st->done) return;
+  __shared__ double sh[32];
+  const double alpha = st->alpha;
+  const long long nn = (long long)n * n;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] += alpha * p[t];
+    const double rv = r[t] - alpha * q[t];
+    r[t] = rv;
+    zacc[t] = (TC)0;
+    acc += rv * rv;
+  }
+  acc = block_sum(acc, sh);
+  if (arrive_last(acc, part, &st->counter[1]) && threadIdx.x < 32) {
+    const double rr = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[1] = 0;
+      st->rr = rr;
+      st->iter += 1;
+      if (rr <= st->rtol2 * st->rr0) {
+        st->done = 1;
+      } else if (!isfinite(rr)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+      } else if (st->iter >= st->maxit) {
+        st->status |= kStMaxIter;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// (r, z) and (z, q); beta
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict__ r,
+                                                       const TC* __restrict__ z,
+                                                       const double* __restrict__ q,
+                                                       double* part, PcgState* st, int n) {
+  if (st->done) return;
+  __shared__ double sh[32];
+  const long long nn = (long long)n * n;
+  double a = 0.0, b = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double zv = (double)z[t];
+    a += r[t] * zv;
+    b += zv * q[t];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  // two partial arrays: part[0..grid) and part[grid..2 grid)
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = b;
+  if (arrive_last(a, part, &st->counter[2]) && threadIdx.x < 32) {
+    const double rz = sum_partials(part, gridDim.x);
+    const double zq = sum_partials(part + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[2] = 0;
+      const double beta = st->flexible ? (-st->alpha * zq / st->rz) : (rz / st->rz);
+      if (!(rz > 0.0) || !isfinite(beta)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+      }
+      st->zq = zq;
+      st->beta = beta;
+      if (st->iter - 1 < kMaxHist) st->betas[st->iter - 1] = beta;
+      st->rz_prev = st->rz;
+      st->rz = rz;
+    }
+  }
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_pcg_update_p(double* __restrict__ p,
+                                                           const TC* __restrict__ z,
+                                                           const PcgState* st, int n) {
+  if (st->done) return;
+  const double beta = st->beta;
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x)
+    p[t] = (double)z[t] + beta * p[t];
+}
+
+// x = 0, rr0 = (r, r)
+__global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
+                                                       const double* __restrict__ r, double* part,
+                                                       PcgState* st, int n) {
+  __shared__ double sh[32];
+  const long long nn = (long long)n * n;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] = 0.0;
+    acc += r[t] * r[t];
+  }
+  acc = block_sum(acc, sh);
+  if (arrive_last(acc, part, &st->counter[3]) && threadIdx.x < 32) {
+    const double rr = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[3] = 0;
+      st->rr0 = rr;
+      st->rr = rr;
+      st->iter = 0;
+      st->done = (rr == 0.0) ? 1 : 0;
+      if (!isfinite(rr)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// p = z, rz = (r, z)
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restrict__ r,
+                                                          const TC* __restrict__ z,
+                                                          double* __restrict__ p, double* part,
+                                                          PcgState* st, int n) {
+  if (st->done) return;
+  __shared__ double sh[32];
+  const long long nn = (long long)n * n;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double zv = (double)z[t];
+    p[t] = zv;
+    acc += r[t] * zv;
+  }
+  acc = block_sum(acc, sh);
+  if (arrive_last(acc, part, &st->counter[3]) && threadIdx.x < 32) {
+    const double rz = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[3] = 0;
+      st->rz = rz;
+      st->rz_prev = rz;
+      if (!(rz > 0.0) || !isfinite(rz)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Smoother: one CTA per oversampled patch.  Gather the residual on the
+// patch's interior nodes, multiply by the stored inverse of the local
+// operator (row per warp, vectorised loads), scatter eta * result with
+// atomics (patches overlap).
+template <typename TS> struct Vec;
+template <> struct Vec<double> { static constexpr int W = 2; };
+template <> struct Vec<float> { static constexpr int W = 4; };
+template <> struct Vec<__nv_bfloat16> { static constexpr int W = 8; };
+
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk(const double* m, const TC* x) {
+  const double2 v = *reinterpret_cast<const double2*>(m);
+  return (TC)(v.x * (double)x[0] + v.y * (double)x[1]);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk(const float* m, const TC* x) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(m));
+  return (TC)(v.x * x[0] + v.y * x[1] + v.z * x[2] + v.w * x[3]);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk(const __nv_bfloat16* m, const TC* x) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(m));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+  TC acc = (TC)0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    acc += f.x * x[2 * k] + f.y * x[2 * k + 1];
+  }
+  return acc;
+}
+
+constexpr int kPatchLd = ((kMaxPatchNodes + 7) / 8) * 8;
+
+template <typename TC, typename TS, typename TR>
+__global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
+                                                       const TS* __restrict__ pinv,
+                                                       const TR* __restrict__ r,
+                                                       TC* __restrict__ zacc, TC eta, int n,
+                                                       const PcgState* st) {
+  if (st && st->done) return;
+  __shared__ __align__(16) TC xs[kPatchLd];
+  __shared__ TC ys[kPatchLd];
+  const PatchGeo g = geo[blockIdx.x];
+  for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
+    TC v = (TC)0;
+    if (q < g.nloc) {
+      const int a = q % g.nx, c = q / g.nx;
+      v = (TC)r[(long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a)];
+    }
+    xs[q] = v;
+  }
+  __syncthreads();
+  constexpr int W = Vec<TS>::W;
+  const TS* M = pinv + g.off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < g.nloc; row += nw) {
+    const TS* mr = M + (long long)row * g.ld;
+    TC acc = (TC)0;
+    for (int col = lane * W; col < g.ld; col += 32 * W) acc += dot_chunk<TC>(mr + col, xs + col);
+    acc = warp_sum(acc);
+    if (lane == 0) ys[row] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < g.nloc; q += blockDim.x) {
+    const int a = q % g.nx, c = q / g.nx;
+    atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * ys[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse restriction: per block, the partial inner products of the residual
+// with each basis function restricted to the block's owned nodes.
+template <typename TC, typename TS>
+__global__ void __launch_bounds__(kThreads) k_restrict(const int* __restrict__ slot_ptr,
+                                                       const TS* __restrict__ owned,
+                                                       const TC* __restrict__ v,
+                                                       double* __restrict__ part, int nc, int b,
+                                                       int n, const PcgState* st) {
+  if (st && st->done) return;
+  __shared__ TC sh[32];
+  const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int bb = b * b, t = threadIdx.x;
+  TC val = (TC)0;
+  if (t < bb) val = v[(long long)(J * b + t / b) * n + I * b + t % b];
+  const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
+  for (int s = s0; s < s1; ++s) {
+    TC prod = (t < bb) ? val * (TC)to_f(owned[(long long)s * bb + t]) : (TC)0;
+    prod = warp_sum(prod);
+    if ((t & 31) == 0) sh[t >> 5] = prod;
+    __syncthreads();
+    if (t < 32) {
+      TC x = (t < (int)(blockDim.x >> 5)) ? sh[t] : (TC)0;
+      x = warp_sum(x);
+      if (t == 0) part[s] = (double)x;
+    }
+    __syncthreads();
+  }
+}
+
+// Coarse solve d = K_H^{-1} c, c[u] = sum of the partials of u's slots.
+__global__ void __launch_bounds__(kThreads) k_coarse_solve(const double* __restrict__ part,
+                                                           const int* __restrict__ gather,
+                                                           const double* __restrict__ Kinv,
+                                                           double* __restrict__ d, int D,
+                                                           const PcgState* st) {
+  if (st && st->done) return;
+  extern __shared__ double cvec[];
+  for (int u = threadIdx.x; u < D; u += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = gather[4 * u + k];
+      if (g >= 0) s += part[g];
+    }
+    cvec[u] = s;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = blockIdx.x * nw + warp; row < D; row += gridDim.x * nw) {
+    const double* kr = Kinv + (long long)row * D;
+    double acc = 0.0;
+    for (int col = lane; col < D; col += 32) acc += kr[col] * cvec[col];
+    acc = warp_sum(acc);
+    if (lane == 0) d[row] = acc;
+  }
+}
+
+// Coarse prolongation: v += sum_s d[coef(s)] * tile_s on each block's owned nodes.
+template <typename TC, typename TS>
+__global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ slot_ptr,
+                                                      const Slot* __restrict__ slots,
+                                                      const TS* __restrict__ owned,
+                                                      const double* __restrict__ d,
+                                                      TC* __restrict__ v, int nc, int b, int n,
+                                                      const PcgState* st) {
+  if (st && st->done) return;
+  const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int bb = b * b, t = threadIdx.x;
+  if (t >= bb) return;
+  TC acc = (TC)0;
+  const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
+  for (int s = s0; s < s1; ++s) acc += (TC)d[slots[s].coef] * (TC)to_f(owned[(long long)s * bb + t]);
+  v[(long long)(J * b + t / b) * n + I * b + t % b] += acc;
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, long long m) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x)
+    b[t] = (TB)a[t];
+}
+
+inline int grid_for(long long m) {
+  long long g = (m + kThreads - 1) / kThreads;
+  if (g > kRedGrid) g = kRedGrid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------
+void launch_apply_operator(const double* psi, const double* kinv, double* out, int n, cudaStream_t s) {
+  k_apply_operator<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
+}
+void launch_apply_operator_f32(const double* psi, const float* kinv, double* out, int n, cudaStream_t s) {
+  k_apply_operator_f32<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
+}
+
+template <typename TC>
+void launch_residual(const double* r, const TC* z, const TC* kinv, TC* out, int n, const PcgState* st,
+                     cudaStream_t s) {
+  k_residual<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, kinv, out, n, st);
+}
+template void launch_residual<double>(const double*, const double*, const double*, double*, int,
+                                      const PcgState*, cudaStream_t);
+template void launch_residual<float>(const double*, const float*, const float*, float*, int,
+                                     const PcgState*, cudaStream_t);
+
+void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part, PcgState* st,
+                          int n, cudaStream_t s) {
+  k_pcg_apply_dot<<<grid_for((long long)n * n), kThreads, 0, s>>>(p, kinv, q, part, st, n);
+}
+template <typename TC>
+void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
+                          double* part, PcgState* st, int n, cudaStream_t s) {
+  k_pcg_update_xr<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, p, q, zacc, part, st, n);
+}
+template <typename TC>
+void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
+                     cudaStream_t s) {
+  k_pcg_dots<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, q, part, st, n);
+}
+template <typename TC>
+void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s) {
+  k_pcg_update_p<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(p, z, st, n);
+}
+void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
+  k_pcg_init<<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, part, st, n);
+}
+template <typename TC>
+void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,
+                        cudaStream_t s) {
+  k_pcg_init_rz<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, p, part, st, n);
+}
+#define TG_INST_TC(TC)                                                                              \
+  template void launch_pcg_update_xr<TC>(double*, double*, const double*, const double*, TC*,      \
+                                         double*, PcgState*, int, cudaStream_t);                    \
+  template void launch_pcg_dots<TC>(const double*, const TC*, const double*, double*, PcgState*,   \
+                                    int, cudaStream_t);                                             \
+  template void launch_pcg_update_p<TC>(double*, const TC*, const PcgState*, int, cudaStream_t);   \
+  template void launch_pcg_init_rz<TC>(const double*, const TC*, double*, double*, PcgState*, int, \
+                                       cudaStream_t);
+TG_INST_TC(double)
+TG_INST_TC(float)
+
+template <typename TC, typename TS, typename TR>
+void launch_smoother(const PatchGeo* geo, const TS* pinv, int npatch, const TR* r, TC* zacc,
+                     double eta, int n, const PcgState* st, cudaStream_t s) {
+  k_smoother<TC, TS, TR><<<npatch, kThreads, 0, s>>>(geo, pinv, r, zacc, (TC)eta, n, st);
+}
+template void launch_smoother<double, double, double>(const PatchGeo*, const double*, int,
+                                                      const double*, double*, double, int,
+                                                      const PcgState*, cudaStream_t);
+template void launch_smoother<float, float, double>(const PatchGeo*, const float*, int, const double*,
+                                                    float*, double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, float, float>(const PatchGeo*, const float*, int, const float*,
+                                                   float*, double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const __nv_bfloat16*, int,
+                                                            const double*, float*, double, int,
+                                                            const PcgState*, cudaStream_t);
+template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const __nv_bfloat16*, int,
+                                                           const float*, float*, double, int,
+                                                           const PcgState*, cudaStream_t);
+
+template <typename TC, typename TS>
+void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
+                     const PcgState* st, cudaStream_t s) {
+  k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, cs.part, nc, b,
+                                                   n, st);
+}
+void launch_coarse_solve(const CoarseSpace& cs, const PcgState* st, cudaStream_t s) {
+  const size_t shm = sizeof(double) * (size_t)cs.D;
+  int grid = (cs.D + 7) / 8;
+  if (grid > 2 * 152) grid = 2 * 152;
+  if (grid < 1) grid = 1;
+  k_coarse_solve<<<grid, kThreads, shm, s>>>(cs.part, cs.gather, cs.Kinv, cs.coefs, cs.D, st);
+}
+template <typename TC, typename TS>
+void launch_prolong(const CoarseSpace& cs, int nblocks, int nc, int b, int n, TC* v, const PcgState* st,
+                    cudaStream_t s) {
+  k_prolong<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, cs.slots, (const TS*)cs.owned, cs.coefs,
+                                                  v, nc, b, n, st);
+}
+template void launch_restrict<double, double>(const CoarseSpace&, int, int, int, int, const double*,
+                                              const PcgState*, cudaStream_t);
+template void launch_restrict<float, float>(const CoarseSpace&, int, int, int, int, const float*,
+                                            const PcgState*, cudaStream_t);
+template void launch_restrict<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, const float*,
+                                                    const PcgState*, cudaStream_t);
+template void launch_prolong<double, double>(const CoarseSpace&, int, int, int, int, double*,
+                                             const PcgState*, cudaStream_t);
+template void launch_prolong<float, float>(const CoarseSpace&, int, int, int, int, float*,
+                                           const PcgState*, cudaStream_t);
+template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, float*,
+                                                   const PcgState*, cudaStream_t);
+
+template <typename TA, typename TB>
+void launch_convert(const TA* a, TB* b, long long m, cudaStream_t s) {
+  k_convert<TA, TB><<<grid_for(m), kThreads, 0, s>>>(a, b, m);
+}
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
+
+}  // namespace tg

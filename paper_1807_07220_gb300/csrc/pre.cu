@@ -1,0 +1,458 @@
+// Section 3 preprocessing (a discrete flux vbar with B_h vbar = F_h built from
+// a coarse RT0 solve and per-block zero-flux Neumann solves), the residual of
+// the reduced system in stream-function form, the final velocity update and
+// the pressure recovery.  Face arrays ux, uy hold physical normal velocities
+// including the prescribed boundary values.
+#include "common.cuh"
+
+namespace tg {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long long m) {
+  long long g = (m + kThreads - 1) / kThreads;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// boundary lift: outward normal velocity bflux -> face values; interior 0
+__global__ void k_lift(const double* __restrict__ bflux, double* __restrict__ ux,
+                       double* __restrict__ uy, int n) {
+  const long long m = (long long)(n + 1) * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    {  // x-face (i, j), index j*(n+1)+i
+      const int i = (int)(t % (n + 1)), j = (int)(t / (n + 1));
+      double v = 0.0;
+      if (bflux) {
+        if (i == 0) v = -bflux[j];
+        else if (i == n) v = bflux[n + j];
+      }
+      ux[t] = v;
+    }
+    {  // y-face (i, j), index j*n+i
+      const int i = (int)(t % n), j = (int)(t / n);
+      double v = 0.0;
+      if (bflux) {
+        if (j == 0) v = -bflux[2 * n + i];
+        else if (j == n) v = bflux[3 * n + i];
+      }
+      uy[t] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ double cell_outflow(const double* ux, const double* uy, int n, int i, int j,
+                                               double h) {
+  return h * (ux[(long long)j * (n + 1) + i + 1] - ux[(long long)j * (n + 1) + i] +
+              uy[(long long)(j + 1) * n + i] - uy[(long long)j * n + i]);
+}
+
+// per block: FH = sum_c (h^2 f_c - outflow_c), absF = sum_c (|h^2 f_c| + |outflow_c| terms)
+__global__ void k_block_sources(const double* __restrict__ f, const double* __restrict__ ux,
+                                const double* __restrict__ uy, double* __restrict__ FH,
+                                double* __restrict__ absF, int n, int b) {
+  __shared__ double sa[32], sb[32];
+  const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const double h = 1.0 / n;
+  double a = 0.0, s = 0.0;
+  for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+    const int i = I * b + t % b, j = J * b + t / b;
+    const double F = h * h * f[(long long)j * n + i];
+    a += F - cell_outflow(ux, uy, n, i, j, h);
+    s += fabs(F) + h * (fabs(ux[(long long)j * (n + 1) + i + 1]) + fabs(ux[(long long)j * (n + 1) + i]) +
+                        fabs(uy[(long long)(j + 1) * n + i]) + fabs(uy[(long long)j * n + i]));
+  }
+  a = warp_sum(a);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ta += sa[w];
+      tb += sb[w];
+    }
+    FH[blk] = ta;
+    absF[blk] = tb;
+  }
+}
+
+// Particular coarse RT0 coefficients with B_H g = F_H: all vertical transport
+// in the first block column (cumulative row totals), then horizontal transport
+// along each block row (cumulative remaining sources).  gx[(J)*(nc+1) + I] is
+// the normal value on the vertical coarse edge x = I H of block row J, gy[J*nc+I]
+// on the horizontal edge y = J H of block column I (boundary edges zero).
+__global__ void k_rt_particular(const double* __restrict__ FH, const double* __restrict__ absF,
+                                double* __restrict__ gx, double* __restrict__ gy, int nc, double H,
+                                int nblocks, PcgState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tot = 0.0, ab = 0.0;
+  for (int k = 0; k < nblocks; ++k) {
+    tot += FH[k];
+    ab += absF[k];
+  }
+  if (fabs(tot) > 1e-12 * fmax(ab, 1e-300)) st->status |= kStIncompatible;
+  for (int k = 0; k < (nc + 1) * nc; ++k) {
+    gx[k] = 0.0;
+    gy[k] = 0.0;
+  }
+  double below = 0.0;  // flux through the horizontal edge under block row J, column 0
+  for (int J = 0; J < nc; ++J) {
+    double row = 0.0;
+    for (int I = 0; I < nc; ++I) row += FH[J * nc + I];
+    const double above = (J + 1 < nc) ? below + row : 0.0;
+    if (J + 1 < nc) gy[(J + 1) * nc + 0] = above / H;
+    double run = 0.0;
+    for (int I = 0; I + 1 < nc; ++I) {
+      double s = FH[J * nc + I];
+      if (I == 0) s -= (above - below);
+      run += s;
+      gx[J * (nc + 1) + I + 1] = run / H;
+    }
+    below = above;
+  }
+}
+
+// u += interpolation of the coarse RT0 field g onto the interior fine faces
+__global__ void k_add_rt_field(const double* __restrict__ gx, const double* __restrict__ gy,
+                               double* __restrict__ ux, double* __restrict__ uy, int n, int b) {
+  const int nc = n / b;
+  const long long m = (long long)(n + 1) * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    {
+      const int i = (int)(t % (n + 1)), j = (int)(t / (n + 1));
+      if (i > 0 && i < n) {
+        const int I0 = i / b, J = j / b;
+        const double w = (double)(i - I0 * b) / b;
+        const double a0 = gx[J * (nc + 1) + I0];
+        const double a1 = (I0 + 1 <= nc) ? gx[J * (nc + 1) + I0 + 1] : 0.0;
+        ux[t] += (1.0 - w) * a0 + (w > 0.0 ? w * a1 : 0.0);
+      }
+    }
+    {
+      const int i = (int)(t % n), j = (int)(t / n);
+      if (j > 0 && j < n) {
+        const int J0 = j / b, I = i / b;
+        const double w = (double)(j - J0 * b) / b;
+        const double a0 = gy[J0 * nc + I];
+        const double a1 = (J0 + 1 <= nc) ? gy[(J0 + 1) * nc + I] : 0.0;
+        uy[t] += (1.0 - w) * a0 + (w > 0.0 ? w * a1 : 0.0);
+      }
+    }
+  }
+}
+
+// (A u)_f / h on x-face (i, j) and y-face (i, j) (exact RT0 mass, cell kinv)
+__device__ __forceinline__ double Au_x(const double* ux, const double* kinv, int n, int i, int j) {
+  const double kL = (i > 0) ? kinv[(long long)j * n + i - 1] : 0.0;
+  const double kR = (i < n) ? kinv[(long long)j * n + i] : 0.0;
+  const double* u = ux + (long long)j * (n + 1) + i;
+  double v = (kL + kR) * (1.0 / 3.0) * u[0];
+  if (i > 0) v += kL * (1.0 / 6.0) * u[-1];
+  if (i < n) v += kR * (1.0 / 6.0) * u[1];
+  return v * (1.0 / n);  // h^2 / h
+}
+__device__ __forceinline__ double Au_y(const double* uy, const double* kinv, int n, int i, int j) {
+  const double kB = (j > 0) ? kinv[(long long)(j - 1) * n + i] : 0.0;
+  const double kT = (j < n) ? kinv[(long long)j * n + i] : 0.0;
+  const double* u = uy + (long long)j * n + i;
+  double v = (kB + kT) * (1.0 / 3.0) * u[0];
+  if (j > 0) v += kB * (1.0 / 6.0) * u[-n];
+  if (j < n) v += kT * (1.0 / 6.0) * u[n];
+  return v * (1.0 / n);
+}
+
+// rho = C^T (-A u) at the interior nodes (the residual of the reduced system)
+__global__ void k_face_residual(const double* __restrict__ ux, const double* __restrict__ uy,
+                                const double* __restrict__ kinv, double* __restrict__ rho, int n) {
+  // Au_x / Au_y already carry the 1/h of C^T: rho = sum of (-A u)/h over the four faces
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    double v = 0.0;
+    if (i > 0 && j > 0) {
+      v = -Au_x(ux, kinv, n, i, j - 1) + Au_x(ux, kinv, n, i, j) + Au_y(uy, kinv, n, i - 1, j) -
+          Au_y(uy, kinv, n, i, j);
+    }
+    rho[t] = v;
+  }
+}
+
+// u += C psi on the interior faces
+__global__ void k_add_curl(const double* __restrict__ psi, double* __restrict__ ux,
+                           double* __restrict__ uy, int n) {
+  const long long m = (long long)(n + 1) * n;
+  const double inv_h = (double)n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    {
+      const int i = (int)(t % (n + 1)), j = (int)(t / (n + 1));
+      if (i > 0 && i < n) {
+        const double top = (j + 1 < n) ? psi[(long long)(j + 1) * n + i] : 0.0;
+        ux[t] += (top - psi[(long long)j * n + i]) * inv_h;
+      }
+    }
+    {
+      const int i = (int)(t % n), j = (int)(t / n);
+      if (j > 0 && j < n) {
+        const double right = (i + 1 < n) ? psi[(long long)j * n + i + 1] : 0.0;
+        uy[t] -= (right - psi[(long long)j * n + i]) * inv_h;
+      }
+    }
+  }
+}
+
+// Particular zero-flux field on each block carrying the block's remaining
+// divergence s_c = h^2 f_c - outflow_c (zero mean per block after the coarse
+// RT0 step): vertical transport in the block's first column, then horizontal
+// transport along each row.
+__global__ void k_block_particular(const double* __restrict__ f, double* __restrict__ ux,
+                                   double* __restrict__ uy, int n, int b) {
+  __shared__ double s[kMaxB * kMaxB];
+  __shared__ double up[kMaxB + 1];
+  const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const double h = 1.0 / n;
+  for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+    const int i = I * b + t % b, j = J * b + t / b;
+    s[t] = h * h * f[(long long)j * n + i] - cell_outflow(ux, uy, n, i, j, h);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    up[0] = 0.0;
+    for (int c = 0; c < b; ++c) {
+      double row = 0.0;
+      for (int a = 0; a < b; ++a) row += s[c * b + a];
+      up[c + 1] = up[c] + row;
+    }
+    up[b] = 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < b) {
+    // vertical flux through y-face (I b, J b + c), c >= 1, column 0 of the block
+    if (c >= 1) uy[(long long)(J * b + c) * n + I * b] += up[c] / h;
+    double run = 0.0;
+    for (int a = 0; a + 1 < b; ++a) {
+      double v = s[c * b + a];
+      if (a == 0) v -= (up[c + 1] - up[c]);
+      run += v;
+      ux[(long long)(J * b + c) * (n + 1) + I * b + a + 1] += run / h;
+    }
+  }
+}
+
+// Band forward/back substitution for one matrix by one warp (column
+// oriented), x overwritten in shared memory.  band row j: L[j*(w+1) + d] =
+// L_{j, j-d}.
+__device__ void warp_band_solve(const double* L, int ldb, int nloc, int w, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < nloc; ++j) {
+    double yj = 0.0;
+    if (lane == 0) {
+      yj = x[j] / L[(long long)j * ldb];
+      x[j] = yj;
+    }
+    yj = __shfl_sync(0xffffffffu, yj, 0);
+    __syncwarp();
+    for (int d = 1 + lane; d <= w; d += 32)
+      if (j + d < nloc) x[j + d] -= L[(long long)(j + d) * ldb + d] * yj;
+    __syncwarp();
+  }
+  for (int j = nloc - 1; j >= 0; --j) {
+    double xj = 0.0;
+    if (lane == 0) {
+      xj = x[j] / L[(long long)j * ldb];
+      x[j] = xj;
+    }
+    xj = __shfl_sync(0xffffffffu, xj, 0);
+    __syncwarp();
+    for (int d = 1 + lane; d <= w; d += 32)
+      if (j - d >= 0) x[j - d] -= L[(long long)j * ldb + d] * xj;
+    __syncwarp();
+  }
+}
+
+// per block: phi = K_K^{-1} rho on the block's interior nodes (one warp)
+__global__ void k_block_solve(const double* __restrict__ chol, const double* __restrict__ rho,
+                              double* __restrict__ phi, int n, int b) {
+  __shared__ double x[(kMaxB - 1) * (kMaxB - 1)];
+  const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int nx = b - 1, nloc = nx * nx, w = nx + 1, ldb = b + 1;  // band width of the block
+  for (int q = threadIdx.x; q < nloc; q += 32)
+    x[q] = rho[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx];
+  __syncwarp();
+  warp_band_solve(chol + (long long)blk * nloc * ldb, ldb, nloc, w, x);
+  for (int q = threadIdx.x; q < nloc; q += 32)
+    phi[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx] = x[q];
+}
+
+// pressure: integrate A u = B^T p along each row (x-faces), then fit one
+// offset per row to the y-face equations in least squares, zero mean.
+__global__ void k_pressure_rows(const double* __restrict__ ux, const double* __restrict__ kinv,
+                                double* __restrict__ rowp, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double p = 0.0;
+  rowp[(long long)j * n] = 0.0;
+  for (int i = 1; i < n; ++i) {
+    p -= Au_x(ux, kinv, n, i, j);
+    rowp[(long long)j * n + i] = p;
+  }
+}
+
+__global__ void k_pressure_steps(const double* __restrict__ uy, const double* __restrict__ kinv,
+                                 const double* __restrict__ rowp, double* __restrict__ step,
+                                 double* __restrict__ rowsum, int n) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;  // row j -> j+1 (j < n-1); row sums for all rows
+  double a = 0.0, rs = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    rs += rowp[(long long)j * n + i];
+    if (j + 1 < n)
+      a += rowp[(long long)j * n + i] - rowp[(long long)(j + 1) * n + i] - Au_y(uy, kinv, n, i, j + 1);
+  }
+  a = warp_sum(a);
+  rs = warp_sum(rs);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    step[j] = (j + 1 < n) ? t / n : 0.0;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = rs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    rowsum[j] = t;
+  }
+}
+
+__global__ void k_pressure_offsets(double* __restrict__ step, const double* __restrict__ rowsum,
+                                   int n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // step[j] becomes the offset of row j; step[n] the mean
+  double c = 0.0, tot = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double sj = step[j];
+    step[j] = c;
+    tot += rowsum[j] + c * n;
+    c += sj;
+  }
+  step[n] = tot / ((double)n * n);
+}
+
+__global__ void k_pressure_final(const double* __restrict__ rowp, const double* __restrict__ off,
+                                 double* __restrict__ p, int n) {
+  const long long nn = (long long)n * n;
+  const double mean = off[n];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x)
+    p[t] = rowp[t] + off[t / n] - mean;
+}
+
+// max_c |outflow_c - h^2 f_c| and max_c |h^2 f_c| per CTA
+__global__ void k_div_error(const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ f, double* __restrict__ part, int n) {
+  __shared__ double sa[32], sb[32];
+  const long long nn = (long long)n * n;
+  const double h = 1.0 / n;
+  double a = 0.0, m = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    const double F = h * h * f[t];
+    a = fmax(a, fabs(cell_outflow(ux, uy, n, i, j, h) - F));
+    m = fmax(m, fabs(F));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a = fmax(a, sa[w]);
+      m = fmax(m, sb[w]);
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = m;
+  }
+}
+
+__global__ void k_div_error_final(const double* __restrict__ part, int g, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, m = 0.0;
+  for (int k = 0; k < g; ++k) {
+    a = fmax(a, part[2 * k]);
+    m = fmax(m, part[2 * k + 1]);
+  }
+  out[0] = (m > 0.0) ? a / m : a;
+}
+
+}  // namespace
+
+void launch_lift(const double* bflux, double* ux, double* uy, int n, cudaStream_t s) {
+  k_lift<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(bflux, ux, uy, n);
+}
+void launch_block_sources(const double* f, const double* ux, const double* uy, double* FH, double* absF,
+                          int n, int b, cudaStream_t s) {
+  const int nc = n / b;
+  k_block_sources<<<nc * nc, kThreads, 0, s>>>(f, ux, uy, FH, absF, n, b);
+}
+void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
+                          int nblocks, PcgState* st, cudaStream_t s) {
+  k_rt_particular<<<1, 32, 0, s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
+}
+void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
+                         cudaStream_t s) {
+  k_add_rt_field<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(gx, gy, ux, uy, n, b);
+}
+void launch_face_residual(const double* ux, const double* uy, const double* kinv, double* rho, int n,
+                          cudaStream_t s) {
+  k_face_residual<<<grid_for((long long)n * n), kThreads, 0, s>>>(ux, uy, kinv, rho, n);
+}
+void launch_add_curl(const double* psi, double* ux, double* uy, int n, cudaStream_t s) {
+  k_add_curl<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(psi, ux, uy, n);
+}
+void launch_block_particular(const double* f, double* ux, double* uy, int n, int b, cudaStream_t s) {
+  const int nc = n / b;
+  k_block_particular<<<nc * nc, 32, 0, s>>>(f, ux, uy, n, b);
+}
+void launch_block_solve(const double* chol, const double* rho, double* phi, int n, int b,
+                        cudaStream_t s) {
+  const int nc = n / b;
+  k_block_solve<<<nc * nc, 32, 0, s>>>(chol, rho, phi, n, b);
+}
+void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p, double* work,
+                     int n, cudaStream_t s) {
+  double* rowp = work;
+  double* step = work + (long long)n * n;
+  double* rowsum = step + n + 1;
+  k_pressure_rows<<<(n + 127) / 128, 128, 0, s>>>(ux, kinv, rowp, n);
+  k_pressure_steps<<<n, 128, 0, s>>>(uy, kinv, rowp, step, rowsum, n);
+  k_pressure_offsets<<<1, 32, 0, s>>>(step, rowsum, n);
+  k_pressure_final<<<grid_for((long long)n * n), kThreads, 0, s>>>(rowp, step, p, n);
+}
+void launch_div_error(const double* ux, const double* uy, const double* f, double* part, double* out,
+                      int n, cudaStream_t s) {
+  const int g = grid_for((long long)n * n) > kRedGrid ? kRedGrid : grid_for((long long)n * n);
+  k_div_error<<<g, kThreads, 0, s>>>(ux, uy, f, part, n);
+  k_div_error_final<<<1, 32, 0, s>>>(part, g, out);
+}
+
+}  // namespace tg

@@ -1,0 +1,753 @@
+// Setup kernels (Step 2 of Section 5): local operators and their factors,
+// snapshot spaces (eq. snapshot_eqn), local spectral problems (eqs.
+// spectral_1, spectral_eqn), coarse basis tiles and the FP64 coarse matrix.
+//
+// Local operators are principal submatrices of K = C^T A_h C on the interior
+// nodes of a cell rectangle (a block K_i or an oversampled block K_i^+): the
+// zero-flux local saddle problems of the paper restricted to their
+// divergence-free subspace.  Rectangles are given as int4 {x0, y0, nx, ny}:
+// cell origin and interior node counts; local node (a, c) is global node
+// (x0+1+a, y0+1+c), index c*nx + a, and the natural ordering gives band width
+// w = nx + 1.  Band storage: row j holds L_{j, j-d} at j*(wmax+1) + d.
+#include "common.cuh"
+
+namespace tg {
+namespace {
+
+__device__ __forceinline__ double kat(const double* kinv, int n, int i, int j) {
+  return kinv[(long long)j * n + i];
+}
+
+__global__ void k_kinv(const double* __restrict__ kappa, double* __restrict__ kinv,
+                       float* __restrict__ kinv32, int* status, int n) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double k = kappa[t];
+    double v = 1.0;
+    if (!(k > 0.0) || !isfinite(k)) atomicOr(status, kStBadKappa);
+    else v = 1.0 / k;
+    kinv[t] = v;
+    kinv32[t] = (float)v;
+  }
+}
+
+// lower band rows of the local operator of each rectangle
+__global__ void k_assemble_band(const double* __restrict__ kinv, const int4* __restrict__ rects,
+                                double* __restrict__ band, int wmax, int nmax, int n) {
+  const int4 r = rects[blockIdx.x];
+  const int nx = r.z, nloc = r.z * r.w, ldb = wmax + 1;
+  double* B = band + (long long)blockIdx.x * nmax * ldb;
+  for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+    const int a = q % nx, c = q / nx;
+    const int i = r.x + 1 + a, j = r.y + 1 + c;
+    const double k00 = kat(kinv, n, i - 1, j - 1), k10 = kat(kinv, n, i, j - 1);
+    const double k01 = kat(kinv, n, i - 1, j), k11 = kat(kinv, n, i, j);
+    double* row = B + (long long)q * ldb;
+    for (int d = 0; d <= wmax; ++d) row[d] = 0.0;
+    row[0] = (2.0 / 3.0) * (k00 + k10 + k01 + k11);
+    if (a >= 1) row[1] = -(1.0 / 6.0) * (k00 + k01);                 // west
+    if (c >= 1) {
+      row[nx] = -(1.0 / 6.0) * (k00 + k10);                          // south
+      if (a >= 1) row[nx + 1] = -(1.0 / 3.0) * k00;                  // south-west
+      if (a + 1 < nx) row[nx - 1] = -(1.0 / 3.0) * k10;              // south-east
+    }
+  }
+}
+
+// right-looking band Cholesky, one CTA per matrix, band in shared memory
+__global__ void k_band_cholesky(double* __restrict__ band, const int4* __restrict__ rects, int wmax,
+                                int nmax, int* status) {
+  extern __shared__ double L[];
+  const int4 r = rects[blockIdx.x];
+  const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1;
+  double* B = band + (long long)blockIdx.x * nmax * ldb;
+  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = B[t];
+  __syncthreads();
+  const int npair = w * (w + 1) / 2;
+  for (int j = 0; j < nloc; ++j) {
+    if (threadIdx.x == 0) {
+      double piv = L[(long long)j * ldb];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        atomicOr(status, kStNotSpd);
+        piv = 1.0;
+      }
+      L[(long long)j * ldb] = sqrt(piv);
+    }
+    __syncthreads();
+    const double ljj = L[(long long)j * ldb];
+    for (int d = 1 + threadIdx.x; d <= w; d += blockDim.x)
+      if (j + d < nloc) L[(long long)(j + d) * ldb + d] /= ljj;
+    __syncthreads();
+    for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+      // t -> (d1, d2), 1 <= d2 <= d1 <= w
+      int d1 = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((d1 + 1) * (d1 + 2) / 2 <= t) ++d1;
+      while (d1 * (d1 + 1) / 2 > t) --d1;
+      const int d2 = t - d1 * (d1 + 1) / 2;  // 0..d1
+      const int D1 = d1 + 1, D2 = d2 + 1;     // 1..w
+      if (j + D1 < nloc)
+        L[(long long)(j + D1) * ldb + (D1 - D2)] -=
+            L[(long long)(j + D1) * ldb + D1] * L[(long long)(j + D2) * ldb + D2];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) B[t] = L[t];
+}
+
+// columns of the inverse from the band factor: thread t solves L L^T x = e_t.
+// scratch (row-major, rows j, columns t) holds nloc x nloc per matrix.
+__global__ void k_band_inverse(const double* __restrict__ band, const int4* __restrict__ rects,
+                               int first, int wmax, int nmax, double* __restrict__ scratch) {
+  extern __shared__ double L[];
+  const int m = first + blockIdx.x;
+  const int4 r = rects[m];
+  const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1;
+  const double* B = band + (long long)m * nmax * ldb;
+  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = B[t];
+  __syncthreads();
+  double* X = scratch + (long long)blockIdx.x * nmax * nmax;
+  for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+    for (int j = 0; j < t; ++j) X[(long long)j * nloc + t] = 0.0;
+    for (int j = t; j < nloc; ++j) {
+      double acc = (j == t) ? 1.0 : 0.0;
+      const int dmax = min(w, j - t);
+      for (int d = 1; d <= dmax; ++d) acc -= L[(long long)j * ldb + d] * X[(long long)(j - d) * nloc + t];
+      X[(long long)j * nloc + t] = acc / L[(long long)j * ldb];
+    }
+    for (int j = nloc - 1; j >= 0; --j) {
+      double acc = X[(long long)j * nloc + t];
+      const int dmax = min(w, nloc - 1 - j);
+      for (int d = 1; d <= dmax; ++d)
+        acc -= L[(long long)(j + d) * ldb + d] * X[(long long)(j + d) * nloc + t];
+      X[(long long)j * nloc + t] = acc / L[(long long)j * ldb];
+    }
+  }
+}
+
+template <typename TS>
+__global__ void k_store_inverse(const double* __restrict__ scratch, const PatchGeo* __restrict__ geo,
+                                int first, int nmax, TS* __restrict__ pinv) {
+  const PatchGeo g = geo[first + blockIdx.x];
+  const double* X = scratch + (long long)blockIdx.x * nmax * nmax;
+  TS* M = pinv + g.off;
+  const long long tot = (long long)g.nloc * g.ld;
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int row = (int)(t / g.ld), col = (int)(t % g.ld);
+    const double v = (col < g.nloc) ? X[(long long)row * g.nloc + col] : 0.0;
+    M[t] = from_d<TS>(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Snapshot spaces.  For block K = (I, J) and an interior side s (0 L, 1 R,
+// 2 B, 3 T) the snapshot space of Section 4.1 restricted to K is spanned by
+//   fn 0:    the unit-flux function RT_s + C psi (coarse RT0 half-function of
+//            side s plus the energy-minimising divergence-free correction,
+//            psi = 0 on dK) -- the MsFEM function of eq. msfem on K;
+//   fn k>=1: C psi with psi = 1 at the k-th interior node of side s, zero on
+//            the rest of dK, discrete-harmonic (K psi = 0) inside K.
+// (Any delta_l snapshot is (1/b) fn0 plus a combination of the fn k >= 1;
+// the span is the same.)  Outputs the closed-block psi of every function and
+// the Gram matrix int_K kappa^{-1} u_a . u_b.
+
+// normal value of RT_s at fine x-face column i' (local 0..b) / y-face row
+__device__ __forceinline__ double rt_value(int side, int t, int b) {
+  const double x = (double)t / b;
+  return (side == 0 || side == 2) ? 1.0 - x : x;
+}
+
+__device__ __forceinline__ void side_node(int side, int k, int b, int& a, int& c) {
+  if (side == 0) { a = 0; c = k; }
+  else if (side == 1) { a = b; c = k; }
+  else if (side == 2) { a = k; c = 0; }
+  else { a = k; c = b; }
+}
+
+__device__ __forceinline__ bool side_interior(int side, int I, int J, int nc) {
+  return (side == 0) ? I >= 1 : (side == 1) ? I + 1 < nc : (side == 2) ? J >= 1 : J + 1 < nc;
+}
+
+__device__ __forceinline__ void warp_band_solve_s(const double* L, int ldb, int nloc, int w, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < nloc; ++j) {
+    double yj = 0.0;
+    if (lane == 0) {
+      yj = x[j] / L[j * ldb];
+      x[j] = yj;
+    }
+    yj = __shfl_sync(0xffffffffu, yj, 0);
+    __syncwarp();
+    for (int d = 1 + lane; d <= w; d += 32)
+      if (j + d < nloc) x[j + d] -= L[(j + d) * ldb + d] * yj;
+    __syncwarp();
+  }
+  for (int j = nloc - 1; j >= 0; --j) {
+    double xj = 0.0;
+    if (lane == 0) {
+      xj = x[j] / L[j * ldb];
+      x[j] = xj;
+    }
+    xj = __shfl_sync(0xffffffffu, xj, 0);
+    __syncwarp();
+    for (int d = 1 + lane; d <= w; d += 32)
+      if (j - d >= 0) x[j - d] -= L[j * ldb + d] * xj;
+    __syncwarp();
+  }
+}
+
+// Dynamic shared memory: L[(b-1)^2 (b+1)] | psi[b (b+1)^2] | kloc[b^2]
+__global__ void k_snapshots(const double* __restrict__ kinv, const double* __restrict__ blk_band,
+                            double* __restrict__ psiS, double* __restrict__ gram, int n, int b) {
+  extern __shared__ double sm[];
+  const int nc = n / b;
+  const int blk = blockIdx.x >> 2, side = blockIdx.x & 3;
+  const int I = blk % nc, J = blk / nc;
+  if (!side_interior(side, I, J, nc)) return;
+  const int nx = b - 1, nloc = nx * nx, ldb = b + 1, w = b;  // block band width w = nx + 1
+  const int nb1 = b + 1, ncl = nb1 * nb1;
+  double* L = sm;
+  double* psi = L + nloc * ldb;
+  double* kl = psi + b * ncl;
+  const double h = 1.0 / n;
+  const double* Bg = blk_band + (long long)blk * nloc * ldb;
+  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = Bg[t];
+  for (int t = threadIdx.x; t < b * b; t += blockDim.x)
+    kl[t] = kinv[(long long)(J * b + t / b) * n + I * b + t % b];
+  // closed psi: boundary data, interior = right-hand side
+  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) {
+    const int fn = t / ncl, node = t % ncl, a = node % nb1, c = node / nb1;
+    double v = 0.0;
+    const bool interior = (a >= 1 && a <= b - 1 && c >= 1 && c <= b - 1);
+    if (!interior) {
+      if (fn >= 1) {
+        int ba, bc;
+        side_node(side, fn, b, ba, bc);
+        v = (a == ba && c == bc) ? 1.0 : 0.0;
+      }
+    }
+    psi[t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) {
+    const int fn = t / ncl, node = t % ncl, a = node % nb1, c = node / nb1;
+    if (!(a >= 1 && a <= b - 1 && c >= 1 && c <= b - 1)) continue;
+    const double k00 = kl[(c - 1) * b + a - 1], k10 = kl[(c - 1) * b + a];
+    const double k01 = kl[c * b + a - 1], k11 = kl[c * b + a];
+    double rhs = 0.0;
+    if (fn == 0) {
+      // -C^T A RT_s at node (a, c); A RT_s / h on a face = h * (...) with RT values
+      if (side <= 1) {
+        // x-faces (a, c-1) [node on top] and (a, c) [node at bottom]; cells row c-1 / c
+        auto ax = [&](double kL, double kR) {
+          return h * ((kL + kR) / 3.0 * rt_value(side, a, b) +
+                      (kL * rt_value(side, a - 1, b) + kR * rt_value(side, a + 1, b)) / 6.0);
+        };
+        rhs = -(ax(k00, k10) - ax(k01, k11));
+      } else {
+        auto ay = [&](double kB, double kT) {
+          return h * ((kB + kT) / 3.0 * rt_value(side, c, b) +
+                      (kB * rt_value(side, c - 1, b) + kT * rt_value(side, c + 1, b)) / 6.0);
+        };
+        // y-faces (a-1, c) [node on the right] and (a, c) [node on the left]
+        rhs = -(-ay(k00, k01) + ay(k10, k11));
+      }
+    } else {
+      // boundary data only: interior entries of P are being overwritten with
+      // right-hand sides by other threads, and the data field is zero there
+      const double* P = psi + fn * ncl;
+      auto at = [&](int da, int dc) {
+        const int aa = a + da, cc = c + dc;
+        const bool in = (aa >= 1 && aa <= b - 1 && cc >= 1 && cc <= b - 1);
+        return in ? 0.0 : P[cc * nb1 + aa];
+      };
+      double kp = (2.0 / 3.0) * (k00 + k10 + k01 + k11) * at(0, 0);
+      kp -= (1.0 / 6.0) * ((k00 + k10) * at(0, -1) + (k01 + k11) * at(0, 1) + (k00 + k01) * at(-1, 0) +
+                           (k10 + k11) * at(1, 0));
+      kp -= (1.0 / 3.0) * (k00 * at(-1, -1) + k10 * at(1, -1) + k01 * at(-1, 1) + k11 * at(1, 1));
+      rhs = -kp;
+    }
+    psi[t] = rhs;  // interior slot used as right-hand side
+  }
+  __syncthreads();
+  // solve: warp per function, in a compact interior vector stored in the
+  // function's own interior slots (copied to a temporary line first)
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* tmp = kl + b * b;  // nw * nloc scratch
+    double* x = tmp + warp * nloc;
+    for (int fn = warp; fn < b; fn += nw) {
+      double* P = psi + fn * ncl;
+      for (int q = lane; q < nloc; q += 32) x[q] = P[(1 + q / nx) * nb1 + 1 + q % nx];
+      __syncwarp();
+      warp_band_solve_s(L, ldb, nloc, w, x);
+      for (int q = lane; q < nloc; q += 32) P[(1 + q / nx) * nb1 + 1 + q % nx] = x[q];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double* outp = psiS + ((long long)blk * 4 + side) * b * ncl;
+  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) outp[t] = psi[t];
+  // Gram: thread per pair (fa <= fb), energy summed over the block's cells
+  double* G = gram + ((long long)blk * 4 + side) * b * b;
+  const int npair = b * (b + 1) / 2;
+  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+    int fa = 0, rem = t;
+    while (rem >= b - fa) { rem -= b - fa; ++fa; }
+    const int fb = fa + rem;
+    const double* Pa = psi + fa * ncl;
+    const double* Pb = psi + fb * ncl;
+    double e = 0.0;
+    for (int cell = 0; cell < b * b; ++cell) {
+      const int a = cell % b, c = cell / b;
+      const int n00 = c * nb1 + a, n10 = n00 + 1, n01 = n00 + nb1, n11 = n01 + 1;
+      // w = h * normal velocity: x-faces left/right, y-faces bottom/top
+      double aL = Pa[n01] - Pa[n00], aR = Pa[n11] - Pa[n10];
+      double aB = -(Pa[n10] - Pa[n00]), aT = -(Pa[n11] - Pa[n01]);
+      double bL = Pb[n01] - Pb[n00], bR = Pb[n11] - Pb[n10];
+      double bB = -(Pb[n10] - Pb[n00]), bT = -(Pb[n11] - Pb[n01]);
+      if (fa == 0) {
+        if (side <= 1) { aL += h * rt_value(side, a, b); aR += h * rt_value(side, a + 1, b); }
+        else { aB += h * rt_value(side, c, b); aT += h * rt_value(side, c + 1, b); }
+      }
+      if (fb == 0) {
+        if (side <= 1) { bL += h * rt_value(side, a, b); bR += h * rt_value(side, a + 1, b); }
+        else { bB += h * rt_value(side, c, b); bT += h * rt_value(side, c + 1, b); }
+      }
+      const double k = kl[cell];
+      e += k * ((aL * bL + aR * bR + aB * bB + aT * bT) / 3.0 +
+                (aL * bR + aR * bL + aB * bT + aT * bB) / 6.0);
+    }
+    G[fa * b + fb] = e;
+    G[fb * b + fa] = e;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per coarse face: local spectral problem a c = lambda s c (eq. spectral_1)
+// in the basis {m, d_1..d_{b-1}} of the snapshot space (m: unit-flux MsFEM
+// function on omega_i, d_k: harmonic extensions of psi = e_k on E_i).
+//   s = H^{-1} (Gram_{K1} + Gram_{K2} + div term), div term 2 on (m, m);
+//   a = N diag(kappa_e^{-1}) N^T with N the normal values on the fine faces
+//       of E_i (fine-face trace product, kappa_e^{-1} the mean of the two
+//       adjacent cells).
+// Solved as L_a^{-1} s L_a^{-T} y = mu y (a = L_a L_a^T, mu = 1/lambda) by
+// cyclic Jacobi, so the selected (small lambda = large mu) pairs carry full
+// relative accuracy.  Then the selected span is split into one function with
+// unit m-coefficient (unit flux through E_i, min-norm combination) and
+// nsel-1 zero-flux functions (a Householder complement of the m-coefficients).
+constexpr int kJ = kMaxB;
+
+__device__ void jacobi_serial(double (*A)[kJ], double (*V)[kJ], int m) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) scale += A[i][j] * A[i][j];
+  scale = sqrt(scale);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j)
+        if (i != j) off += A[i][j] * A[i][j];
+    if (sqrt(off) <= 1e-15 * scale) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p][q];
+        if (apq == 0.0) continue;
+        const double diff = A[q][q] - A[p][p];
+        double t;
+        if (fabs(diff) > 1e150 * fabs(apq)) {
+          t = apq / diff;
+        } else {
+          const double tau = diff / (2.0 * apq);
+          t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+        }
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        A[p][q] = A[q][p] = 0.0;
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+__device__ bool cholesky_serial(double (*A)[kJ], int m) {  // lower factor in place
+  for (int j = 0; j < m; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    if (!(d > 0.0)) return false;
+    d = sqrt(d);
+    A[j][j] = d;
+    for (int i = j + 1; i < m; ++i) {
+      double v = A[i][j];
+      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+      A[i][j] = v / d;
+    }
+    for (int k = j + 1; k < m; ++k) A[j][k] = 0.0;
+  }
+  return true;
+}
+
+__global__ void k_face_eigen(const double* __restrict__ kinv, const double* __restrict__ gram,
+                             double eig_tol, int max_basis, int mode, int n, int b,
+                             double* __restrict__ lam, int* __restrict__ nsel,
+                             double* __restrict__ fcoef, double* __restrict__ zcoef, int* status) {
+  if (threadIdx.x != 0) return;
+  __shared__ double S[kJ][kJ], Aa[kJ][kJ], V[kJ][kJ], C[kJ][kJ];
+  __shared__ double mu[kJ], lamv[kJ];
+  __shared__ int ord[kJ];
+  const int nc = n / b, nV = nc * (nc - 1);
+  const int f = blockIdx.x;
+  int kind, I, J;
+  if (f < nV) { kind = 0; I = f % (nc - 1) + 1; J = f / (nc - 1); }
+  else { kind = 1; I = (f - nV) % nc; J = (f - nV) / nc + 1; }
+  int blk1, side1, blk2, side2;
+  if (kind == 0) { blk1 = J * nc + I - 1; side1 = 1; blk2 = J * nc + I; side2 = 0; }
+  else { blk1 = (J - 1) * nc + I; side1 = 3; blk2 = J * nc + I; side2 = 2; }
+  const double h = 1.0 / n, H = b * h;
+  const double* G1 = gram + ((long long)blk1 * 4 + side1) * b * b;
+  const double* G2 = gram + ((long long)blk2 * 4 + side2) * b * b;
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < b; ++j) S[i][j] = (G1[i * b + j] + G2[i * b + j]) / H;
+  S[0][0] += 2.0 / H;
+  // a = N D N^T
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < b; ++j) Aa[i][j] = 0.0;
+  for (int l = 0; l < b; ++l) {
+    double kl, kr;
+    if (kind == 0) { kl = kinv[(long long)(J * b + l) * n + I * b - 1]; kr = kinv[(long long)(J * b + l) * n + I * b]; }
+    else { kl = kinv[(long long)(J * b - 1) * n + I * b + l]; kr = kinv[(long long)(J * b) * n + I * b + l]; }
+    const double ke = 0.5 * (kl + kr);
+    double Nl[kJ];
+    for (int k = 0; k < b; ++k) Nl[k] = 0.0;
+    Nl[0] = 1.0;
+    // d_k: +-1/h on faces k-1 (node k above/right) and k
+    const double sg = (kind == 0) ? 1.0 : -1.0;
+    if (l + 1 <= b - 1) Nl[l + 1] = sg / h;        // face l has node l+1 as its upper/right end
+    if (l >= 1) Nl[l] = -sg / h;                   // and node l as its lower/left end
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) Aa[i][j] += ke * Nl[i] * Nl[j];
+  }
+  if (!cholesky_serial(Aa, b)) {
+    atomicOr(status, kStNotSpd);
+    return;
+  }
+  // S <- L^{-1} S L^{-T}
+  for (int col = 0; col < b; ++col)
+    for (int i = 0; i < b; ++i) {
+      double v = S[i][col];
+      for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[k][col];
+      S[i][col] = v / Aa[i][i];
+    }
+  for (int row = 0; row < b; ++row)
+    for (int i = 0; i < b; ++i) {
+      double v = S[row][i];
+      for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[row][k];
+      S[row][i] = v / Aa[i][i];
+    }
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double v = 0.5 * (S[i][j] + S[j][i]);
+      S[i][j] = S[j][i] = v;
+    }
+  jacobi_serial(S, V, b);
+  for (int k = 0; k < b; ++k) { mu[k] = S[k][k]; ord[k] = k; }
+  // descending mu = ascending lambda (stable insertion sort)
+  for (int i = 1; i < b; ++i) {
+    const int o = ord[i];
+    int j = i - 1;
+    while (j >= 0 && mu[ord[j]] < mu[o]) { ord[j + 1] = ord[j]; --j; }
+    ord[j + 1] = o;
+  }
+  for (int k = 0; k < b; ++k) {
+    lamv[k] = 1.0 / mu[ord[k]];
+    lam[(long long)f * b + k] = lamv[k];
+  }
+  int m = 0;
+  while (m < b && lamv[m] < eig_tol) ++m;
+  if (m < 1) m = 1;
+  if (max_basis > 0 && m > max_basis) m = max_basis;
+  if (mode != 0) m = 1;
+  nsel[f] = m;
+  // coefficient vectors c_k = L^{-T} y_k / sqrt(mu_k) (s-orthonormal)
+  for (int k = 0; k < m; ++k) {
+    const int o = ord[k];
+    for (int i = b - 1; i >= 0; --i) {
+      double v = V[i][o];
+      for (int r = i + 1; r < b; ++r) v -= Aa[r][i] * C[r][k];
+      C[i][k] = v / Aa[i][i];
+    }
+    const double sc = 1.0 / sqrt(mu[o]);
+    for (int i = 0; i < b; ++i) C[i][k] *= sc;
+  }
+  double* fc = fcoef + (long long)f * b;
+  double* zc = zcoef + (long long)f * (b - 1) * b;
+  if (mode != 0) {  // MsFEM / RT0: the unit-flux MsFEM function alone
+    for (int i = 0; i < b; ++i) fc[i] = (i == 0) ? 1.0 : 0.0;
+    return;
+  }
+  double tn = 0.0, cmax = 0.0;
+  for (int k = 0; k < m; ++k) tn += C[0][k] * C[0][k];
+  for (int k = 0; k < m; ++k)
+    for (int i = 0; i < b; ++i) cmax = fmax(cmax, fabs(C[i][k]));
+  if (!(sqrt(tn) > 1e-12 * cmax)) {
+    atomicOr(status, kStDegenerate);
+    for (int i = 0; i < b; ++i) fc[i] = (i == 0) ? 1.0 : 0.0;
+    return;
+  }
+  for (int i = 0; i < b; ++i) {
+    double v = 0.0;
+    for (int k = 0; k < m; ++k) v += C[i][k] * C[0][k] / tn;
+    fc[i] = v;
+  }
+  fc[0] = 1.0;
+  if (m > 1) {
+    // Householder H = I - 2 v v^T / v^T v with v = t + sign(t0) |t| e0 maps t to -sign |t| e0;
+    // columns 1..m-1 of H span t^perp.
+    double v[kJ];
+    for (int k = 0; k < m; ++k) v[k] = C[0][k];
+    const double tnorm = sqrt(tn);
+    v[0] += (v[0] >= 0.0 ? tnorm : -tnorm);
+    double vv = 0.0;
+    for (int k = 0; k < m; ++k) vv += v[k] * v[k];
+    for (int q = 1; q < m; ++q) {
+      for (int i = 0; i < b; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) {
+          const double Hkq = ((k == q) ? 1.0 : 0.0) - 2.0 * v[k] * v[q] / vv;
+          acc += C[i][k] * Hkq;
+        }
+        zc[(long long)(q - 1) * b + i] = (i == 0) ? 0.0 : acc;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Basis tiles.  For a slot of block K = (I, J):
+//   theta_m (corner m): Hat_m + sum over the two sides E of K at m of
+//       c_{E,m} (psi_m(E) + sum_j fcoef_E[j] psi_dj(E)),  c = +-1/H the
+//       coarse curl of the nodal delta at m;
+//   z_{E,k}: sum_j zcoef_E[k-1][j] psi_dj(E).
+// rt_only: theta_m = Hat_m (coarse RT0 space).
+__device__ __forceinline__ int face_of_side(int side, int I, int J, int nc) {
+  const int nV = nc * (nc - 1);
+  if (side == 0) return J * (nc - 1) + (I - 1);
+  if (side == 1) return J * (nc - 1) + I;
+  if (side == 2) return nV + (J - 1) * nc + I;
+  return nV + J * nc + I;
+}
+
+template <typename TS>
+__global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __restrict__ psiS,
+                              const double* __restrict__ fcoef, const double* __restrict__ zcoef,
+                              double* __restrict__ closed, TS* __restrict__ owned, int rt_only, int n,
+                              int b) {
+  const int nc = n / b, nb1 = b + 1, ncl = nb1 * nb1;
+  const Slot sl = slots[blockIdx.x];
+  const int I = sl.block % nc, J = sl.block / nc;
+  const double H = (double)b / n;
+  for (int t = threadIdx.x; t < ncl; t += blockDim.x) {
+    const int a = t % nb1, c = t / nb1;
+    const double x = (double)a / b, y = (double)c / b;
+    double v = 0.0;
+    if (sl.kind == 0) {
+      int sA, sB;
+      double cA, cB;
+      switch (sl.which) {
+        case 0: v = (1 - x) * (1 - y); sA = 0; cA = -1.0; sB = 2; cB = +1.0; break;   // BL
+        case 1: v = x * (1 - y);       sA = 1; cA = -1.0; sB = 2; cB = -1.0; break;   // BR
+        case 2: v = (1 - x) * y;       sA = 0; cA = +1.0; sB = 3; cB = +1.0; break;   // TL
+        default: v = x * y;            sA = 1; cA = +1.0; sB = 3; cB = -1.0; break;   // TR
+      }
+      if (!rt_only) {
+        const int sides[2] = {sA, sB};
+        const double cs[2] = {cA / H, cB / H};
+        for (int e = 0; e < 2; ++e) {
+          const int face = face_of_side(sides[e], I, J, nc);
+          const double* P = psiS + ((long long)sl.block * 4 + sides[e]) * b * ncl;
+          const double* fc = fcoef + (long long)face * b;
+          double xi = P[t];
+          for (int jj = 1; jj < b; ++jj) xi += fc[jj] * P[(long long)jj * ncl + t];
+          v += cs[e] * xi;
+        }
+      }
+    } else {
+      const double* P = psiS + ((long long)sl.block * 4 + sl.which) * b * ncl;
+      const double* zc = zcoef + ((long long)sl.face * (b - 1) + (sl.k - 1)) * b;
+      for (int jj = 1; jj < b; ++jj) v += zc[jj] * P[(long long)jj * ncl + t];
+    }
+    closed[(long long)blockIdx.x * ncl + t] = v;
+    if (a < b && c < b) owned[(long long)blockIdx.x * b * b + c * b + a] = from_d<TS>(v);
+  }
+}
+
+// energies of all slot pairs of a block: int_K kappa^{-1} (C psi_s).(C psi_t)
+__global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __restrict__ closed,
+                              const double* __restrict__ kinv, const long long* __restrict__ pair_ptr,
+                              double* __restrict__ pairE, int n, int b) {
+  const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
+  const int nb1 = b + 1, ncl = nb1 * nb1;
+  double* E = pairE + pair_ptr[blk];
+  const int npair = m * (m + 1) / 2;
+  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+    int sa = 0, rem = t;
+    while (rem >= m - sa) { rem -= m - sa; ++sa; }
+    const int sb = sa + rem;
+    const double* Pa = closed + (long long)(s0 + sa) * ncl;
+    const double* Pb = closed + (long long)(s0 + sb) * ncl;
+    double e = 0.0;
+    for (int cell = 0; cell < b * b; ++cell) {
+      const int a = cell % b, c = cell / b;
+      const int n00 = c * nb1 + a, n10 = n00 + 1, n01 = n00 + nb1, n11 = n01 + 1;
+      const double aL = Pa[n01] - Pa[n00], aR = Pa[n11] - Pa[n10];
+      const double aB = Pa[n00] - Pa[n10], aT = Pa[n01] - Pa[n11];
+      const double bL = Pb[n01] - Pb[n00], bR = Pb[n11] - Pb[n10];
+      const double bB = Pb[n00] - Pb[n10], bT = Pb[n01] - Pb[n11];
+      const double k = kinv[(long long)(J * b + c) * n + I * b + a];
+      e += k * ((aL * bL + aR * bR + aB * bB + aT * bT) / 3.0 +
+                (aL * bR + aR * bL + aB * bT + aT * bB) / 6.0);
+    }
+    E[sa * m + sb] = e;
+    E[sb * m + sa] = e;
+  }
+}
+
+// K[u][*] += pair energies of u's slots (one thread per row: deterministic)
+__global__ void k_assemble_coarse(const int* __restrict__ slot_ptr, const Slot* __restrict__ slots,
+                                  const int* __restrict__ gather, const long long* __restrict__ pair_ptr,
+                                  const double* __restrict__ pairE, double* __restrict__ K, int D) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= D) return;
+  double* row = K + (long long)u * D;
+  for (int g = 0; g < 4; ++g) {
+    const int s = gather[4 * u + g];
+    if (s < 0) continue;
+    const int blk = slots[s].block, s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
+    const double* E = pairE + pair_ptr[blk] + (long long)(s - s0) * m;
+    for (int t = 0; t < m; ++t) row[slots[s0 + t].coef] += E[t];
+  }
+}
+
+// one Gauss-Jordan elimination step on an SPD matrix: B = GJ_k(A)
+__global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int D, int k,
+                          int* status) {
+  const long long m = (long long)D * D;
+  const double p = A[(long long)k * D + k];
+  if (!(p > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStNotSpd);
+  }
+  const double ip = 1.0 / p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / D), j = (int)(t % D);
+    double v;
+    if (i == k && j == k) v = ip;
+    else if (i == k) v = A[t] * ip;
+    else if (j == k) v = -A[t] * ip;
+    else v = A[t] - A[(long long)i * D + k] * A[(long long)k * D + j] * ip;
+    B[t] = v;
+  }
+}
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------
+void launch_kinv(const double* kappa, double* kinv, float* kinv32, int* status, int n, cudaStream_t s) {
+  long long nn = (long long)n * n;
+  int g = (int)((nn + 255) / 256);
+  if (g > 4096) g = 4096;
+  k_kinv<<<g, 256, 0, s>>>(kappa, kinv, kinv32, status, n);
+}
+void launch_assemble_band(const double* kinv, const int4* rects, double* band, int nmat, int wmax, int nmax,
+                          int n, cudaStream_t s) {
+  k_assemble_band<<<nmat, 128, 0, s>>>(kinv, rects, band, wmax, nmax, n);
+}
+void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, int nmax, int* status,
+                          cudaStream_t s) {
+  const size_t shm = sizeof(double) * (size_t)nmax * (wmax + 1);
+  cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  k_band_cholesky<<<nmat, 256, shm, s>>>(band, rects, wmax, nmax, status);
+}
+void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax, int nmax,
+                         double* scratch, cudaStream_t s) {
+  const size_t shm = sizeof(double) * (size_t)nmax * (wmax + 1);
+  cudaFuncSetAttribute(k_band_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  k_band_inverse<<<count, 128, shm, s>>>(band, rects, first, wmax, nmax, scratch);
+}
+template <typename TS>
+void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count, int nmax,
+                          TS* pinv, cudaStream_t s) {
+  k_store_inverse<TS><<<count, 256, 0, s>>>(scratch, geo, first, nmax, pinv);
+}
+template void launch_store_inverse<double>(const double*, const PatchGeo*, int, int, int, double*,
+                                           cudaStream_t);
+template void launch_store_inverse<float>(const double*, const PatchGeo*, int, int, int, float*,
+                                          cudaStream_t);
+template void launch_store_inverse<__nv_bfloat16>(const double*, const PatchGeo*, int, int, int,
+                                                  __nv_bfloat16*, cudaStream_t);
+
+void launch_snapshots(const double* kinv, const double* blk_band, double* psiS, double* gram, int n, int b,
+                      cudaStream_t s) {
+  const int nc = n / b, nloc = (b - 1) * (b - 1), threads = 256;
+  const size_t shm = sizeof(double) * ((size_t)nloc * (b + 1) + (size_t)b * (b + 1) * (b + 1) +
+                                       (size_t)b * b + (size_t)(threads / 32) * nloc);
+  cudaFuncSetAttribute(k_snapshots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  k_snapshots<<<nc * nc * 4, threads, shm, s>>>(kinv, blk_band, psiS, gram, n, b);
+}
+void launch_face_eigen(const double* kinv, const double* gram, double eig_tol, int max_basis, int mode,
+                       int n, int b, double* lam, int* nsel, double* fcoef, double* zcoef, int* status,
+                       cudaStream_t s) {
+  const int nc = n / b, nfaces = 2 * nc * (nc - 1);
+  if (nfaces == 0) return;
+  k_face_eigen<<<nfaces, 32, 0, s>>>(kinv, gram, eig_tol, max_basis, mode, n, b, lam, nsel, fcoef, zcoef,
+                                     status);
+}
+template <typename TS>
+void launch_build_tiles(const CoarseSpace& cs, const double* psiS, const double* fcoef, const double* zcoef,
+                        int rt_only, int n, int b, cudaStream_t s) {
+  if (cs.nslots == 0) return;
+  k_build_tiles<TS><<<cs.nslots, 128, 0, s>>>(cs.slots, psiS, fcoef, zcoef, cs.closed, (TS*)cs.owned,
+                                               rt_only, n, b);
+}
+template void launch_build_tiles<double>(const CoarseSpace&, const double*, const double*, const double*,
+                                         int, int, int, cudaStream_t);
+template void launch_build_tiles<float>(const CoarseSpace&, const double*, const double*, const double*,
+                                        int, int, int, cudaStream_t);
+template void launch_build_tiles<__nv_bfloat16>(const CoarseSpace&, const double*, const double*,
+                                                const double*, int, int, int, cudaStream_t);
+
+void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b, double* pairE,
+                     const long long* pair_ptr, double* K, cudaStream_t s) {
+  if (cs.D == 0) return;
+  k_pair_energy<<<nblocks, 128, 0, s>>>(cs.slot_ptr, cs.closed, kinv, pair_ptr, pairE, n, b);
+  cudaMemsetAsync(K, 0, sizeof(double) * (size_t)cs.D * cs.D, s);
+  k_assemble_coarse<<<(cs.D + 127) / 128, 128, 0, s>>>(cs.slot_ptr, cs.slots, cs.gather, pair_ptr, pairE,
+                                                        K, cs.D);
+}
+void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s) {
+  long long m = (long long)D * D;
+  int g = (int)((m + 255) / 256);
+  if (g > 2048) g = 2048;
+  for (int k = 0; k < D; ++k) {
+    if (k % 2 == 0) k_gj_step<<<g, 256, 0, s>>>(A, B, D, k, status);
+    else k_gj_step<<<g, 256, 0, s>>>(B, A, D, k, status);
+  }
+  if (D % 2 == 1) cudaMemcpyAsync(A, B, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace tg

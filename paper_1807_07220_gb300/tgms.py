@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libtgms (include/tgms.h): same entry-point names,
+argument marshalling only.  Every step of the solver runs in the library's
+CUDA kernels; nothing here computes.
+
+Device arrays are passed as torch CUDA tensors (float64, contiguous) through
+their data pointers; host arrays (TG_PTR_HOST mode) as C-contiguous float64
+numpy arrays.  The library must have been built (``build.build_library``);
+``lib()`` raises if it is missing -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtgms.so")
+
+TG_OK = 0
+ERRORS = {
+    -1: "TG_ERR_INVALID_ARG", -2: "TG_ERR_INCOMPATIBLE_SOURCE", -3: "TG_ERR_BREAKDOWN",
+    -4: "TG_ERR_MAXITER", -5: "TG_ERR_DEVICE_TIMEOUT", -6: "TG_ERR_CUDA", -7: "TG_ERR_OOM",
+    -8: "TG_ERR_UNSUPPORTED", -9: "TG_ERR_DEGENERATE_BASIS",
+}
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2}
+PTR_HOST, PTR_DEVICE = 0, 1
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+c_int_p, c_double_p = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+
+
+class tg_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("bx", c_int), ("by", c_int), ("overlap", c_int)]
+
+
+class tg_options(ctypes.Structure):
+    _fields_ = [("eta", c_double), ("m1", c_int), ("m2", c_int), ("precision", c_int),
+                ("flexible", c_int), ("max_iter", c_int), ("pointer_mode", c_int),
+                ("coarse_space", c_int), ("max_basis", c_int)]
+
+
+class tg_report(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("converged", c_int), ("rel_residual", c_double),
+                ("cond_estimate", c_double), ("coarse_dim", c_int), ("velocity_basis", c_int),
+                ("coarse_unknowns", c_int), ("max_div_error", c_double),
+                ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TgmsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.tg_strerror(code).decode() if _lib is not None else ""
+        super().__init__("%s failed: %s (%s)" % (where, ERRORS.get(code, code), msg))
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "tg_default_options": (c_int, [ctypes.POINTER(tg_options)]),
+    "tg_setup": (c_int, [c_void_p, ctypes.POINTER(tg_grid), c_double, ctypes.POINTER(tg_options),
+                         c_void_p, ctypes.POINTER(c_void_p)]),
+    "tg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p,
+                         c_int_p, ctypes.POINTER(tg_report)]),
+    "tg_destroy": (None, [c_void_p]),
+    "tg_strerror": (ctypes.c_char_p, [c_int]),
+    "tg_apply_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "tg_apply_smoother": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "tg_apply_coarse": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "tg_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "tg_coarse_info": (c_int, [c_void_p, c_int_p, c_int_p, c_void_p, c_void_p]),
+    "tg_preprocess": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+}
+
+
+def lib():
+    """Load libtgms.so from the package tree (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtgms.so not built: run paper_1807_07220_gb300.build.build_library()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, where):
+    if rc != TG_OK:
+        raise TgmsError(rc, where)
+
+
+def default_options(**kw):
+    o = tg_options()
+    _check(lib().tg_default_options(ctypes.byref(o)), "tg_default_options")
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        if k == "coarse_space" and isinstance(v, str):
+            v = COARSE[v]
+        setattr(o, k, v)
+    return o
+
+
+def tg_setup(kappa, n, b, eig_tol, overlap=2, options=None, stream=0):
+    """Returns an opaque handle (c_void_p).  kappa: n*n float64 (device tensor
+    or host array per options.pointer_mode)."""
+    g = tg_grid(n, n, b, b, overlap)
+    o = options if options is not None else default_options()
+    h = ctypes.c_void_p()
+    _check(lib().tg_setup(_ptr(kappa), ctypes.byref(g), float(eig_tol), ctypes.byref(o),
+                          ctypes.c_void_p(stream), ctypes.byref(h)), "tg_setup")
+    return h
+
+
+def tg_solve(h, f, bflux, rtol, ux, uy, p, allow_maxiter=False):
+    it = ctypes.c_int(0)
+    rep = tg_report()
+    rc = lib().tg_solve(h, _ptr(f), _ptr(bflux), float(rtol), _ptr(ux), _ptr(uy), _ptr(p),
+                        ctypes.byref(it), ctypes.byref(rep))
+    if not (allow_maxiter and rc == -4):
+        _check(rc, "tg_solve")
+    return it.value, rep
+
+
+def tg_destroy(h):
+    if h is not None:
+        lib().tg_destroy(h)
+
+
+def tg_strerror(code):
+    return lib().tg_strerror(code).decode()
+
+
+def tg_apply_operator(h, psi, out, precision=0):
+    _check(lib().tg_apply_operator(h, _ptr(psi), _ptr(out), int(precision)), "tg_apply_operator")
+
+
+def tg_apply_smoother(h, rho, z):
+    _check(lib().tg_apply_smoother(h, _ptr(rho), _ptr(z)), "tg_apply_smoother")
+
+
+def tg_apply_coarse(h, rho, z):
+    _check(lib().tg_apply_coarse(h, _ptr(rho), _ptr(z)), "tg_apply_coarse")
+
+
+def tg_apply_preconditioner(h, rho, z):
+    _check(lib().tg_apply_preconditioner(h, _ptr(rho), _ptr(z)), "tg_apply_preconditioner")
+
+
+def tg_coarse_info(h, b):
+    """Returns (nsel per face, eigenvalues (nfaces, b), velocity basis count)."""
+    import numpy as np
+    nf, vb = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().tg_coarse_info(h, ctypes.byref(nf), ctypes.byref(vb), None, None), "tg_coarse_info")
+    nsel = np.zeros(nf.value, dtype=np.int32)
+    lam = np.zeros((nf.value, b), dtype=np.float64)
+    _check(lib().tg_coarse_info(h, None, None, _ptr(nsel), _ptr(lam)), "tg_coarse_info")
+    return nsel, lam, vb.value
+
+
+def tg_preprocess(h, f, bflux, ux, uy):
+    _check(lib().tg_preprocess(h, _ptr(f), _ptr(bflux), _ptr(ux), _ptr(uy)), "tg_preprocess")
+
+
+class Solver:
+    """Convenience owner of a handle plus output buffers on one CUDA device.
+
+    Inputs and outputs are torch float64 CUDA tensors; arrays are (n, n)
+    [j, i], ux (n, n+1), uy (n+1, n)."""
+
+    def __init__(self, kappa, b, eig_tol, overlap=2, device="cuda", stream=None, **opts):
+        import torch
+        self.torch = torch
+        n = kappa.shape[0]
+        self.n, self.b = n, b
+        self.device = torch.device(device)
+        self.kappa = torch.as_tensor(kappa, dtype=torch.float64, device=self.device).contiguous()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = tg_setup(self.kappa, n, b, eig_tol, overlap, default_options(**opts),
+                          self.stream.cuda_stream)
+        z = lambda *s: torch.zeros(*s, dtype=torch.float64, device=self.device)
+        self.ux, self.uy, self.p = z(n, n + 1), z(n + 1, n), z(n, n)
+
+    def solve(self, f, bflux=None, rtol=1e-8, allow_maxiter=False):
+        t = self.torch
+        f = t.as_tensor(f, dtype=t.float64, device=self.device).contiguous()
+        bf = None if bflux is None else t.as_tensor(bflux, dtype=t.float64, device=self.device).contiguous()
+        it, rep = tg_solve(self.h, f, bf, rtol, self.ux, self.uy, self.p, allow_maxiter)
+        return it, rep
+
+    def close(self):
+        if self.h is not None:
+            tg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

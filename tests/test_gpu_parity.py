@@ -1,0 +1,219 @@
+"""GPU parity of libtgms against the FP64 CPU oracle (same seeded inputs).
+
+The CUDA path works in stream-function form (psi on the interior nodes,
+u = C psi); the oracle works in the paper's saddle-point form on faces.  Each
+operator is compared through the discrete curl C of the oracle:
+  K psi          vs  C^T A C psi
+  C S_psi C^T r  vs  the oracle smoother S r           (eq. smooth)
+  C P_psi C^T r  vs  the oracle coarse correction P r  (eq. coarsepre)
+  C M_psi C^T r  vs  the oracle two-grid preconditioner
+and the full solve against the sparse direct solve of the saddle system.
+Tolerance: 1e-8 relative error in velocity and pressure for solves (run at
+rtol 1e-12), 1e-9 relative for single FP64 operators.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.fine import Grid, solve_direct, assemble, curl_matrix  # noqa: E402
+from oracle.twogrid import TwoGridSolver  # noqa: E402
+from paper_1807_07220_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import os
+    from paper_1807_07220_gb300 import build, tgms
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(tgms.LIB_PATH):
+        build.build_library()
+    tgms.lib()
+    return tgms
+
+
+DEV = "cuda"
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def psi_from_interior(n, v):
+    full = np.zeros((n, n))
+    full[1:, 1:] = v.reshape(n - 1, n - 1)
+    return full
+
+
+def interior_from_psi(n, full):
+    return np.asarray(full).reshape(n, n)[1:, 1:].ravel()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+CASES = {
+    "32x32_b8_channels": (32, 8, lambda n: inputs.channel_field(n, 1e4, 3)),
+    "24x24_b8_lognormal": (24, 8, lambda n: inputs.lognormal_field(n, 5, sigma=2.0)),
+    "20x20_b4_channels": (20, 4, lambda n: inputs.channel_field(n, 1e6, 9)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, tg):
+    n, b, kf = CASES[request.param]
+    kappa = kf(n)
+    tol = 10.0
+    oracle = TwoGridSolver(n, b, kappa, tol=tol)
+    solver = tg.Solver(kappa, b, tol)
+    yield dict(n=n, b=b, kappa=kappa, tol=tol, oracle=oracle, solver=solver, name=request.param)
+    solver.close()
+
+
+def test_fine_operator(case, tg):
+    n, o, s = case["n"], case["oracle"], case["solver"]
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal((n - 1) ** 2)
+    ref = o.C.T @ (o.AII @ (o.C @ v))
+    out = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+    tg.tg_apply_operator(s.h, dev(psi_from_interior(n, v)), out, 0)
+    got = out.cpu().numpy()
+    assert rel(interior_from_psi(n, got), ref) < 1e-13
+    assert np.all(got[0, :] == 0) and np.all(got[:, 0] == 0)
+    tg.tg_apply_operator(s.h, dev(psi_from_interior(n, v)), out, 1)
+    assert rel(interior_from_psi(n, out.cpu().numpy()), ref) < 1e-5
+
+
+@pytest.mark.parametrize("which", ["smoother", "coarse", "precondition"])
+def test_preconditioner_parts(case, tg, which):
+    n, o, s = case["n"], case["oracle"], case["solver"]
+    rng = np.random.default_rng(2)
+    r = o.project(rng.standard_normal(o.If.size))
+    rho = o.C.T @ r
+    ref = {"smoother": o.smoother, "coarse": o.coarse_correction, "precondition": o.precondition}[which](r)
+    z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+    fn = {"smoother": tg.tg_apply_smoother, "coarse": tg.tg_apply_coarse,
+          "precondition": tg.tg_apply_preconditioner}[which]
+    fn(s.h, dev(psi_from_interior(n, rho)), z)
+    got = o.C @ interior_from_psi(n, z.cpu().numpy())
+    assert rel(got, ref) < 1e-9, (case["name"], which, rel(got, ref))
+
+
+def test_spectra_and_selection(case, tg):
+    o, s, b = case["oracle"], case["solver"], case["b"]
+    nsel, lam, vb = tg.tg_coarse_info(s.h, b)
+    lam_o = np.array(o.info["lam"])
+    np.testing.assert_array_equal(nsel, np.array(o.info["nsel"]))
+    assert vb == int(np.sum(o.info["nsel"]))
+    small = lam_o < 1e3
+    np.testing.assert_allclose(lam[small], lam_o[small], rtol=1e-8)
+    np.testing.assert_allclose(lam, lam_o, rtol=1e-5)
+
+
+def test_preprocessing(case, tg):
+    n, o, s = case["n"], case["oracle"], case["solver"]
+    f = inputs.random_pairs(n, 3, 7)
+    ux = torch.zeros(n, n + 1, dtype=torch.float64, device=DEV)
+    uy = torch.zeros(n + 1, n, dtype=torch.float64, device=DEV)
+    tg.tg_preprocess(s.h, dev(f), None, ux, uy)
+    got = np.concatenate([ux.cpu().numpy().ravel(), uy.cpu().numpy().ravel()])
+    F = (1.0 / n) ** 2 * f.ravel()
+    ref = o.preprocess(F, np.zeros(o.If.size))
+    assert rel(got[o.If], ref) < 1e-10
+    assert np.abs(o.B @ got - F).max() <= 1e-12 * np.abs(F).max()
+
+
+def test_full_solve_matches_direct_solve(case, tg):
+    n, b, o, s = case["n"], case["b"], case["oracle"], case["solver"]
+    f = inputs.quarter_five_spot(n)
+    g = Grid(n, b)
+    u_ref, p_ref = solve_direct(g, case["kappa"], f)
+    it, rep = s.solve(f, rtol=1e-12)
+    got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+    got_p = s.p.cpu().numpy().ravel()
+    assert rep.converged == 1
+    assert rel(got_u, u_ref) < 1e-8, rel(got_u, u_ref)
+    assert rel(got_p, p_ref) < 1e-8, rel(got_p, p_ref)
+    assert rep.max_div_error < 1e-12
+    # iteration count and condition estimate at the paper's tolerance
+    it8, rep8 = s.solve(f, rtol=1e-8)
+    ora = o.solve(f, rtol=1e-8)
+    assert abs(it8 - ora["iters"]) <= 1, (it8, ora["iters"])
+    assert abs(rep8.cond_estimate / ora["cond"] - 1) < 0.05
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_mixed_precision_solve(case, tg, prec):
+    n, b = case["n"], case["b"]
+    f = inputs.quarter_five_spot(n)
+    u_ref, p_ref = solve_direct(Grid(n, b), case["kappa"], f)
+    s = tg.Solver(case["kappa"], b, case["tol"], precision=prec, flexible=1)
+    try:
+        it, rep = s.solve(f, rtol=1e-12)
+        got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert rel(got_u, u_ref) < 1e-8
+        assert rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+        assert rep.max_div_error < 1e-12
+    finally:
+        s.close()
+
+
+def test_boundary_flux_closed_form(tg):
+    """Layered medium with prescribed inflow/outflow: u_x = -kappa(row), p = x."""
+    n, b = 16, 4
+    rng = np.random.default_rng(1)
+    krow = np.exp(rng.standard_normal(n) * 2)
+    kappa = np.repeat(krow[:, None], n, axis=1)
+    bflux = np.concatenate([krow, -krow, np.zeros(n), np.zeros(n)])
+    s = tg.Solver(kappa, b, 10.0)
+    try:
+        s.solve(np.zeros((n, n)), bflux=bflux, rtol=1e-13)
+        ux = s.ux.cpu().numpy()
+        np.testing.assert_allclose(ux, -np.repeat(krow[:, None], n + 1, axis=1), rtol=1e-9)
+        xc = (np.arange(n) + 0.5) / n
+        np.testing.assert_allclose(s.p.cpu().numpy(), np.tile(xc - xc.mean(), (n, 1)), atol=1e-9)
+    finally:
+        s.close()
+
+
+def test_error_codes(tg):
+    n = 16
+    kappa = np.ones((n, n))
+    bad = kappa.copy()
+    bad[3, 4] = -1.0
+    with pytest.raises(tg.TgmsError) as e:
+        tg.Solver(bad, 4, 10.0)
+    assert e.value.code == -1
+    with pytest.raises(tg.TgmsError) as e:
+        tg.Solver(np.ones((18, 18)), 4, 10.0)
+    assert e.value.code == -1
+    s = tg.Solver(kappa, 4, 10.0)
+    try:
+        f = np.zeros((n, n))
+        f[0, 0] = 1.0
+        with pytest.raises(tg.TgmsError) as e:
+            s.solve(f)
+        assert e.value.code == -2
+        it, rep = s.solve(inputs.quarter_five_spot(n), rtol=1e-8)
+        assert rep.converged == 1
+    finally:
+        s.close()
+
+
+def test_host_pointer_mode(tg):
+    n, b = 16, 4
+    kappa = inputs.lognormal_field(n, 2)
+    f = inputs.quarter_five_spot(n)
+    u_ref, p_ref = solve_direct(Grid(n, b), kappa, f)
+    h = tg.tg_setup(np.ascontiguousarray(kappa), n, b, 10.0, 2, tg.default_options(pointer_mode=0))
+    try:
+        ux, uy, p = np.zeros((n, n + 1)), np.zeros((n + 1, n)), np.zeros((n, n))
+        tg.tg_solve(h, np.ascontiguousarray(f), None, 1e-12, ux, uy, p)
+        assert rel(np.concatenate([ux.ravel(), uy.ravel()]), u_ref) < 1e-8
+        assert rel(p.ravel(), p_ref) < 1e-8
+    finally:
+        tg.tg_destroy(h)
