@@ -1,0 +1,402 @@
+"""Benchmark: fine DOF-solves/s of the two-grid GMsFEM-preconditioned PCG.
+
+Workload (one "step" = one solve: Section 3 preprocessing + PCG to relative
+residual 1e-8 + velocity update and pressure):
+  256 x 256 RT0/P0 grid, 16 x 16-cell coarse blocks, kappa = exp(Gaussian field,
+  variance 4, correlation length 0.05) with horizontal channels at 1e6,
+  quarter five-spot source, eigenvalue tolerance 10, eta 0.2, overlap 2.
+The headline arm runs the mixed-precision preconditioner (FP32 patch inverses
+and coarse basis, FP32 arithmetic inside the two-grid cycle, flexible CG);
+outer vectors, dot products, fine operator and coarse matrix are FP64.  The
+plain FP64 arm runs the same code with FP64 everywhere.  DOF per solve =
+2n(n-1) + n^2 + 1 (interior faces + cells + one pressure constraint).
+
+Inputs are resident on the device when a timed step starts; L2 is flushed
+(256 MiB write) before every timed step, outside the timed interval.  Every
+step is timed with CUDA events on the solver's stream.  `e2e` repeats the
+headline arm through the host-pointer C ABI (host -> device copy of f and
+device -> host copy of ux, uy, p inside every timed call).
+
+--impl reference times the FP64 CPU oracle (test infrastructure of this
+repository) on the host cores: each step is one oracle PCG iteration on the
+same workload, and the throughput uses the oracle's own preprocessing,
+iteration count and pressure times measured once in warm-up.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine DOF-solves/s to 1e-8 rel. residual vs plain FP64; PCG iters; HBM %"
+N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
+
+
+def dof(n):
+    return 2 * n * (n - 1) + n * n + 1
+
+
+def workload(n, seed):
+    from paper_1807_07220_gb300 import inputs
+    return inputs.grf_channel_field(n, CONTRAST, seed), inputs.quarter_five_spot(n)
+
+
+def workload_name(n, b):
+    return ("%dx%d RT0/P0, %dx%d-cell coarse blocks, kappa = exp(GRF var 4, corr 0.05) + channels 1e6, "
+            "quarter five-spot, eig tol 10, rtol 1e-8" % (n, n, b, b))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.lines = gpu, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def time_solves(solver, f, steps, warmup, flush, torch):
+    """Per-step CUDA-event times (ms) of steps solves; L2 flushed before each."""
+    stream = solver.stream
+    for _ in range(warmup):
+        solver.solve(f, rtol=RTOL)
+    times, reps = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rep = solver.solve(f, rtol=RTOL)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps.append(rep)
+    return times, reps
+
+
+def smoother_bytes(n, b, ov, ts_bytes, tc_bytes):
+    """Algorithmic bytes of one smoother launch: every patch inverse read once
+    (nloc^2 entries), the residual gathered (FP64 or TC) and the correction
+    scattered (read + write, TC)."""
+    total = 0
+    nc = n // b
+    for J in range(nc):
+        for I in range(nc):
+            nx = min(n, (I + 1) * b + ov) - max(0, I * b - ov) - 1
+            ny = min(n, (J + 1) * b + ov) - max(0, J * b - ov) - 1
+            m = nx * ny
+            total += m * m * ts_bytes + m * 8 + 2 * m * tc_bytes
+    return total
+
+
+def run_ncu_target(args):
+    """Setup, warm-up and timed solves of the headline arm only (the command
+    profiled by ncu; prints the solver report of the last solve)."""
+    import torch
+    from paper_1807_07220_gb300 import tgms
+    n, b = args.n, args.b
+    kappa, f = workload(n, 5)
+    s = tgms.Solver(kappa, b, EIG_TOL, precision=args.precision, flexible=int(args.precision != "f64"))
+    for _ in range(args.warmup + args.steps):
+        it, rep = s.solve(f, rtol=RTOL)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps(rep.as_dict()))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1807_07220_gb300 import build, tgms
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if not os.path.exists(tgms.LIB_PATH):
+        if rank == 0:
+            build.build_library()
+        if dist:
+            dist.barrier()
+    n, b = args.n, args.b
+    kappa, f = workload(n, 5 + rank)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+    prec = args.precision
+
+    def make(precision, flexible, profile=0, pointer_mode=1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = tgms.Solver(kappa, b, EIG_TOL, precision=precision, flexible=flexible, profile=profile,
+                        pointer_mode=pointer_mode)
+        torch.cuda.synchronize()
+        return s, (time.perf_counter() - t0) * 1e3
+
+    # plain FP64 reference arm of the metric
+    plain, plain_setup_ms = make("f64", 0)
+    p_times, p_reps = time_solves(plain, f, args.steps, args.warmup, flush, torch)
+    plain.close()
+    # headline mixed-precision arm, timed region with clock sampling
+    head, setup_ms = make(prec, 1)
+    for _ in range(args.warmup):
+        head.solve(f, rtol=RTOL)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, reps = time_solves(head, f, args.steps, 0, flush, torch)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    head.close()
+    # roofline of the dominant kernel (patch smoother): events around every launch
+    prof, _ = make(prec, 1, profile=1)
+    _, prof_reps = time_solves(prof, f, args.steps, args.warmup, flush, torch)
+    prof.close()
+    sm_ms = sum(r.smoother_ms for r in prof_reps)
+    sm_n = sum(r.smoother_launches for r in prof_reps)
+    ts_bytes = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    tc_bytes = 8 if prec == "f64" else 4
+    alg_bytes = smoother_bytes(n, b, 2, ts_bytes, tc_bytes)
+    # end to end through the host-pointer ABI (copies inside the timed call)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h = tgms.tg_setup(pin(kappa), n, b, EIG_TOL, 2,
+                      tgms.default_options(precision=prec, flexible=1, pointer_mode=tgms.PTR_HOST),
+                      torch.cuda.current_stream().cuda_stream)
+    hf = pin(f)
+    hux, huy, hp = pin(np.zeros((n, n + 1))), pin(np.zeros((n + 1, n))), pin(np.zeros((n, n)))
+    for _ in range(args.warmup):
+        tgms.tg_solve(h, hf, None, RTOL, hux, huy, hp)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tgms.tg_solve(h, hf, None, RTOL, hux, huy, hp)
+        e2e_t.append((time.perf_counter() - t0) * 1e3)
+    tgms.tg_destroy(h)
+
+    def agg(ms_list):
+        """Whole-job DOF-solves/s: all ranks' solves over the slowest rank's time."""
+        total_ms = sum(ms_list)
+        if dist:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return world * len(ms_list) * dof(n) / (total_ms / 1e3), total_ms / len(ms_list)
+
+    value, ms_step = agg(times)
+    p_value, p_ms = agg(p_times)
+    e_value, e_ms = agg(e2e_t)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    achieved = alg_bytes / (sm_ms / sm_n / 1e3) / 1e9 if sm_n else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+%s" % prec, "data": "synthetic",
+        "config": {"workload": workload_name(n, b), "n": n, "b": b, "precision": prec, "flexible_cg": True,
+                   "dof_per_solve": dof(n), "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "iters": reps[-1].iters, "cond_estimate": reps[-1].cond_estimate,
+        "rel_residual": reps[-1].rel_residual, "max_div_error": reps[-1].max_div_error,
+        "coarse_dim": reps[-1].coarse_dim, "setup_ms": setup_ms,
+        "plain_f64": {"value": p_value, "ms_per_step": p_ms, "iters": p_reps[-1].iters,
+                      "setup_ms": plain_setup_ms},
+        "speedup_vs_plain_f64": value / p_value,
+        "gpu_launches": sum(r.kernel_launches for r in reps),
+        "gpu_launches_per_step": reps[-1].kernel_launches,
+        "roofline": {"bound": "hbm", "kernel": "k_smoother (patch inverse apply)",
+                     "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": None,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None,
+                     "launches_timed": sm_n, "peak_source": peak_src},
+        "e2e": {"value": e_value, "unit": "DOF-solves/s", "ms_per_step": e_ms,
+                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * (n + 1) + n * n)},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, b)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle arms
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle.twogrid import TwoGridSolver
+from oracle.fine import boundary_lift
+from paper_1807_07220_gb300 import inputs
+n, b, mode, steps, warmup = %(n)d, %(b)d, %(mode)r, %(steps)d, %(warmup)d
+kappa = inputs.grf_channel_field(n, 1e6, 5)
+f = inputs.quarter_five_spot(n)
+t0 = time.perf_counter()
+s = TwoGridSolver(n, b, kappa, tol=10.0)
+setup = time.perf_counter() - t0
+out = {"setup_s": setup}
+if mode == "full":
+    t0 = time.perf_counter()
+    res = s.solve(f, rtol=1e-8)
+    out.update(solve_s=time.perf_counter() - t0, iters=res["iters"])
+else:
+    g = s.g
+    F = g.h ** 2 * f.ravel()
+    t0 = time.perf_counter(); vbar = s.preprocess(F, np.zeros(s.If.size)); t_pre = time.perf_counter() - t0
+    res = s.solve(f, rtol=1e-8)
+    t0 = time.perf_counter(); s.pressure(res["u"]); t_post = time.perf_counter() - t0
+    r = s.project(-(s.AII @ vbar)); z = s.precondition(r); p = z.copy(); rz = r @ z
+    x = np.zeros_like(r)
+    it_times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        q = s.project(s.AII @ p); a = rz / (p @ q)
+        x += a * p; r = r - a * q
+        s.residual_norm(r)
+        z = s.precondition(r); rz_new = r @ z; p = z + (rz_new / rz) * p; rz = rz_new
+        if k >= warmup:
+            it_times.append(time.perf_counter() - t0)
+    out.update(t_pre=t_pre, t_post=t_post, iters=res["iters"], it_times=it_times)
+print("ORACLE_JSON " + json.dumps(out))
+"""
+
+
+def run_oracle(n, b, mode, steps=0, warmup=0, timeout=900):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET % {"root": ROOT, "n": n, "b": b, "mode": mode, "steps": steps, "warmup": warmup}
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    for ln in r.stdout.splitlines():
+        if ln.startswith("ORACLE_JSON "):
+            return json.loads(ln[len("ORACLE_JSON "):])
+    raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+
+
+def cpu_baseline(n, b):
+    try:
+        o = run_oracle(n, b, "full")
+    except Exception as e:  # reported, never fatal for the GPU line
+        return {"value": None, "error": str(e)[:200]}
+    return {"value": dof(n) / o["solve_s"], "unit": "DOF-solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one full oracle solve (preprocessing + %d PCG iterations + pressure) of the same "
+                      "workload, single-threaded BLAS; oracle setup (%.0f s) excluded" % (o["iters"], o["setup_s"]),
+            "solve_s": o["solve_s"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n, b = args.n, args.b
+    o = run_oracle(n, b, "iter", steps=args.steps, warmup=args.warmup, timeout=3000)
+    t_iter = statistics.mean(o["it_times"])
+    t_solve = o["t_pre"] + o["iters"] * t_iter + o["t_post"]
+    value = dof(n) / t_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_iter, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n, b), "n": n, "b": b, "precision": "f64",
+                   "dof_per_solve": dof(n)},
+        "cpu_baseline": {"value": value, "unit": "DOF-solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step = one oracle PCG iteration (operator, two preconditioner "
+                                   "applications for the scalars, vector updates) on the same workload; "
+                                   "solve time = preprocessing %.2f s + %d iterations + pressure %.2f s"
+                                   % (o["t_pre"], o["iters"], o["t_post"])},
+        "e2e": {"value": value, "unit": "DOF-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--b", type=int, default=B_DEFAULT)
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")
+    args = ap.parse_args()
+    if args.ncu_target:
+        return run_ncu_target(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

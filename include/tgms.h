@@ -86,6 +86,9 @@ typedef struct tg_options {
   int pointer_mode;  /* TG_PTR_HOST or TG_PTR_DEVICE for tg_setup / tg_solve */
   int coarse_space;  /* TG_COARSE_* */
   int max_basis;     /* cap on functions kept per coarse face; 0 = no cap */
+  int profile;       /* 0: tg_solve runs one instantiated CUDA graph (PCG loop in a
+                        device-side while node); 1: host-driven loop with CUDA
+                        events around every smoother launch (timings in tg_report) */
 } tg_options;
 
 typedef struct tg_report {
@@ -100,10 +103,14 @@ typedef struct tg_report {
   double preprocess_ms;   /* device time of Section 3 (inside tg_solve) */
   double pcg_ms;          /* device time of the PCG loop */
   double epilogue_ms;     /* device time of v = vbar + vtilde and the pressure */
+  int kernel_launches;    /* kernels of this library launched by the call */
+  int smoother_launches;  /* profile == 1: smoother launches timed ... */
+  double smoother_ms;     /* ... and their summed device time */
+  int graph;              /* 1 if the call ran as one CUDA graph */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
- * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap. */
+ * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything

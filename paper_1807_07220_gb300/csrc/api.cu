@@ -13,6 +13,10 @@
 
 using namespace tg;
 
+namespace tg {
+unsigned long long g_kernel_launches = 0;
+}
+
 struct tg_handle {
   int n = 0, b = 0, nc = 0, ov = 0, nblocks = 0, npatch = 0, nfaces = 0;
   double h = 0, H = 0, eig_tol = 0;
@@ -42,7 +46,17 @@ struct tg_handle {
   double* tmpd = nullptr;   // n*n scratch (operator hooks)
   PcgState* st = nullptr;
   int* h_flag = nullptr;    // pinned
+  double* h_rtol = nullptr; // pinned
+  double* d_rtol = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // one-graph solve: prefix -> while(PCG body) -> epilogue
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long k_prefix = 0, k_body = 0, k_epi = 0;
+  // profiling: events around smoother launches (profile == 1)
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0;
 };
 
 namespace {
@@ -205,8 +219,12 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
 }
 
 // ---- the two-grid preconditioner (Section 5), zacc must be zero on entry ----
+void prof_mark(tg_handle* h, cudaStream_t s) {
+  if (h->opt.profile && h->prof_used < (int)h->prof_ev.size()) cudaEventRecord(h->prof_ev[h->prof_used++], s);
+}
+
 template <typename TC, typename TS>
-void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st) {
+void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st, cudaStream_t s) {
   const int n = h->n;
   const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
   TC* rin = (TC*)h->rin;
@@ -214,69 +232,35 @@ void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st) {
   const double eta = h->opt.eta;
   for (int k = 0; k < h->opt.m1; ++k) {
     if (k == 0) {
-      launch_smoother<TC, TS, double>(h->d_pgeo, pinv, h->npatch, r, zacc, eta, n, st, h->stream);
+      prof_mark(h, s);
+      launch_smoother<TC, TS, double>(h->d_pgeo, pinv, h->npatch, r, zacc, eta, n, st, s);
+      prof_mark(h, s);
     } else {
-      launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, h->stream);
+      launch_residual<TC>(r, zacc, kin, rin, n, st, s);
+      prof_mark(h, s);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, s);
+      prof_mark(h, s);
     }
   }
   if (h->cs.D > 0) {
-    launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
-    launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, st, h->stream);
-    launch_coarse_solve(h->cs, st, h->stream);
-    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, st, h->stream);
+    launch_residual<TC>(r, zacc, kin, rin, n, st, s);
+    launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, st, s);
+    launch_coarse_solve(h->cs, st, s);
+    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
-    launch_residual<TC>(r, zacc, kin, rin, n, st, h->stream);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, h->stream);
-  }
-}
-
-template <typename TC, typename TS>
-int run_pcg(tg_handle* h, double rtol) {
-  const int n = h->n;
-  const long long nn = (long long)n * n;
-  TC* zacc = (TC*)h->zacc;
-  // scalar head of PcgState
-  PcgState head{};
-  head.rtol2 = rtol * rtol;
-  head.maxit = std::min(h->opt.max_iter, kMaxHist);
-  head.flexible = h->opt.flexible;
-  TG_CK(cudaMemcpyAsync(h->st, &head, offsetof(PcgState, alphas), cudaMemcpyHostToDevice, h->stream));
-  TG_CK(cudaMemcpyAsync(h->r, h->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
-  launch_pcg_init(h->x, h->r, h->part, h->st, n, h->stream);
-  TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
-  precondition<TC, TS>(h, h->r, zacc, h->st);
-  launch_pcg_init_rz<TC>(h->r, zacc, h->p, h->part, h->st, n, h->stream);
-  const int check = 2;
-  for (int it = 0; it < head.maxit; ++it) {
-    launch_pcg_apply_dot(h->p, h->kinv, h->q, h->part, h->st, n, h->stream);
-    launch_pcg_update_xr<TC>(h->x, h->r, h->p, h->q, zacc, h->part, h->st, n, h->stream);
-    precondition<TC, TS>(h, h->r, zacc, h->st);
-    launch_pcg_dots<TC>(h->r, zacc, h->q, h->part, h->st, n, h->stream);
-    launch_pcg_update_p<TC>(h->p, zacc, h->st, n, h->stream);
-    if ((it + 1) % check == 0 || it + 1 == head.maxit) {
-      TG_CK(cudaMemcpyAsync(h->h_flag, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-      TG_CK(cudaStreamSynchronize(h->stream));
-      if (*h->h_flag) break;
-    }
-  }
-  return cuda_err(cudaGetLastError());
-}
-
-int dispatch_pcg(tg_handle* h, double rtol) {
-  switch (h->opt.precision) {
-    case TG_PREC_F64: return run_pcg<double, double>(h, rtol);
-    case TG_PREC_F32: return run_pcg<float, float>(h, rtol);
-    default: return run_pcg<float, __nv_bfloat16>(h, rtol);
+    launch_residual<TC>(r, zacc, kin, rin, n, st, s);
+    prof_mark(h, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, s);
+    prof_mark(h, s);
   }
 }
 
 // Section 3: vbar into (ux, uy), and rho = C^T(-A vbar) (the PCG right-hand side)
-int preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
+void enqueue_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy,
+                        cudaStream_t s) {
   const int n = h->n, b = h->b;
   const long long nn = (long long)n * n;
-  cudaStream_t s = h->stream;
   launch_lift(bflux, ux, uy, n, s);
   launch_block_sources(f, ux, uy, h->FH, h->absF, n, b, s);
   launch_rt_particular(h->FH, h->absF, h->gx, h->gy, h->nc, h->H, h->nblocks, h->st, s);
@@ -285,19 +269,126 @@ int preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, d
     launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
     launch_restrict<double, double>(h->rt, h->nblocks, h->nc, b, n, h->rho, nullptr, s);
     launch_coarse_solve(h->rt, nullptr, s);
-    TG_CK(cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s));
+    cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s);
     launch_prolong<double, double>(h->rt, h->nblocks, h->nc, b, n, h->phi, nullptr, s);
     launch_add_curl(h->phi, ux, uy, n, s);
   }
   launch_block_particular(f, ux, uy, n, b, s);
-  if (b >= 2) {
-    launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
-    TG_CK(cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s));
-    launch_block_solve(h->blk_band, h->rho, h->phi, n, b, s);
-    launch_add_curl(h->phi, ux, uy, n, s);
-  }
   launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
+  cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s);
+  launch_block_solve(h->blk_band, h->rho, h->phi, n, b, s);
+  launch_add_curl(h->phi, ux, uy, n, s);
+  launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
+}
+
+// reset + preprocessing + PCG start (r = rho, x = 0, z = M r, p = z)
+template <typename TC, typename TS>
+void enqueue_prefix(tg_handle* h, cudaStream_t s) {
+  const int n = h->n;
+  const long long nn = (long long)n * n;
+  launch_pcg_reset(h->st, h->d_rtol, std::min(h->opt.max_iter, kMaxHist), h->opt.flexible, s);
+  enqueue_preprocess(h, h->fd, h->bd, h->ux, h->uy, s);
+  cudaMemcpyAsync(h->r, h->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+  launch_pcg_init(h->x, h->r, h->part, h->st, n, s);
+  cudaMemsetAsync(h->zacc, 0, sizeof(TC) * nn, s);
+  precondition<TC, TS>(h, h->r, (TC*)h->zacc, h->st, s);
+  launch_pcg_init_rz<TC>(h->r, (const TC*)h->zacc, h->p, h->part, h->st, n, s);
+}
+
+// one PCG iteration (every kernel returns at once when st->done is set)
+template <typename TC, typename TS>
+void enqueue_body(tg_handle* h, cudaStream_t s) {
+  const int n = h->n;
+  TC* zacc = (TC*)h->zacc;
+  launch_pcg_apply_dot(h->p, h->kinv, h->q, h->part, h->st, n, s);
+  launch_pcg_update_xr<TC>(h->x, h->r, h->p, h->q, zacc, h->part, h->st, n, s);
+  precondition<TC, TS>(h, h->r, zacc, h->st, s);
+  launch_pcg_dots<TC>(h->r, zacc, h->q, h->part, h->st, n, s);
+  launch_pcg_update_p<TC>(h->p, zacc, h->st, n, s);
+}
+
+// Step 4: v = vbar + C x, pressure, conservation check
+void enqueue_epilogue(tg_handle* h, cudaStream_t s) {
+  launch_add_curl(h->x, h->ux, h->uy, h->n, s);
+  launch_pressure(h->ux, h->uy, h->kinv, h->pd, h->pw, h->n, s);
+  launch_div_error(h->ux, h->uy, h->fd, h->part, h->diverr, h->n, s);
+}
+
+template <typename TC, typename TS>
+int build_graph_t(tg_handle* h) {
+  cudaStream_t cs = h->cap;
+  cudaGraph_t prefix = nullptr, epi = nullptr;
+  unsigned long long k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  enqueue_prefix<TC, TS>(h, cs);
+  TG_CK(cudaStreamEndCapture(cs, &prefix));
+  h->k_prefix = g_kernel_launches - k0;
+  TG_CK(cudaGraphCreate(&h->graph, 0));
+  cudaGraphNode_t n1, n2, n3;
+  TG_CK(cudaGraphAddChildGraphNode(&n1, h->graph, nullptr, 0, prefix));
+  cudaGraphConditionalHandle cond;
+  TG_CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  TG_CK(cudaGraphAddNode(&n2, h->graph, &n1, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_body<TC, TS>(h, cs);
+  launch_set_condition(cond, h->st, cs);
+  TG_CK(cudaStreamEndCapture(cs, &body));
+  h->k_body = g_kernel_launches - k0;
+  k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  enqueue_epilogue(h, cs);
+  TG_CK(cudaStreamEndCapture(cs, &epi));
+  h->k_epi = g_kernel_launches - k0;
+  TG_CK(cudaGraphAddChildGraphNode(&n3, h->graph, &n2, 1, epi));
+  TG_CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  cudaGraphDestroy(prefix);
+  cudaGraphDestroy(epi);
+  return TG_OK;
+}
+
+int build_graph(tg_handle* h) {
+  switch (h->opt.precision) {
+    case TG_PREC_F64: return build_graph_t<double, double>(h);
+    case TG_PREC_F32: return build_graph_t<float, float>(h);
+    default: return build_graph_t<float, __nv_bfloat16>(h);
+  }
+}
+
+// host-driven loop (profile mode): same kernels, events around the smoother
+template <typename TC, typename TS>
+int run_loop_t(tg_handle* h, unsigned long long* launches) {
+  cudaStream_t s = h->stream;
+  const unsigned long long k0 = g_kernel_launches;
+  enqueue_prefix<TC, TS>(h, s);
+  cudaEventRecord(h->ev[1], s);
+  const int maxit = std::min(h->opt.max_iter, kMaxHist);
+  for (int it = 0; it < maxit; ++it) {
+    enqueue_body<TC, TS>(h, s);
+    if ((it + 1) % 2 == 0 || it + 1 == maxit) {
+      TG_CK(cudaMemcpyAsync(h->h_flag, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TG_CK(cudaStreamSynchronize(s));
+      if (*h->h_flag) break;
+    }
+  }
+  cudaEventRecord(h->ev[2], s);
+  enqueue_epilogue(h, s);
+  *launches = g_kernel_launches - k0;
   return cuda_err(cudaGetLastError());
+}
+
+int run_loop(tg_handle* h, unsigned long long* launches) {
+  switch (h->opt.precision) {
+    case TG_PREC_F64: return run_loop_t<double, double>(h, launches);
+    case TG_PREC_F32: return run_loop_t<float, float>(h, launches);
+    default: return run_loop_t<float, __nv_bfloat16>(h, launches);
+  }
 }
 
 // extreme eigenvalues of the Lanczos tridiagonal by Sturm bisection (report only)
@@ -488,6 +579,14 @@ int setup_impl(tg_handle* h, const double* kappa) {
       dalloc(&h->gy, (nc + 1) * nc) || dalloc(&h->FH, h->nblocks) || dalloc(&h->absF, h->nblocks) ||
       dalloc(&h->diverr, 2) || dalloc(&h->st, 1))
     return TG_ERR_OOM;
+  configure_kernels(std::max(h->cs.D, h->rt.D));
+  TG_CK(cudaMallocHost(&h->h_rtol, sizeof(double)));
+  if (dalloc(&h->d_rtol, 1)) return TG_ERR_OOM;
+  TG_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  if (h->opt.profile) {
+    h->prof_ev.resize(2048);
+    for (auto& e : h->prof_ev) TG_CK(cudaEventCreate(&e));
+  }
   TG_CK(cudaMalloc(&h->zacc, tc * nn));
   TG_CK(cudaMalloc(&h->rin, tc * nn));
   TG_CK(cudaMemsetAsync(h->st, 0, sizeof(PcgState), s));
@@ -516,7 +615,7 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
       launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
     }
   } else {
-    precondition<TC, TS>(h, rho, zacc, nullptr);
+    precondition<TC, TS>(h, rho, zacc, nullptr, h->stream);
   }
   if (std::is_same<TC, double>::value)
     TG_CK(cudaMemcpyAsync(z, zacc, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
@@ -613,42 +712,29 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
   cudaStream_t s = h->stream;
-  const bool host = (h->opt.pointer_mode == TG_PTR_HOST);
-  const double* fdev = f;
-  const double* bdev = bflux;
-  if (host) {
-    TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
-    fdev = h->fd;
-    if (bflux) {
-      TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, s));
-      bdev = h->bd;
-    }
-  }
-  double* uxd = host ? h->ux : ux;
-  double* uyd = host ? h->uy : uy;
-  double* pdv = host ? h->pd : p;
-  TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
-  TG_CK(cudaMemsetAsync(h->st, 0, offsetof(PcgState, alphas), s));
+  const cudaMemcpyKind in = (h->opt.pointer_mode == TG_PTR_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind out = (h->opt.pointer_mode == TG_PTR_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  // stage inputs into handle buffers (the instantiated graph only references those)
+  TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, in, s));
+  if (bflux) TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, in, s));
+  else TG_CK(cudaMemsetAsync(h->bd, 0, sizeof(double) * 4 * n, s));
+  *h->h_rtol = rtol;
+  TG_CK(cudaMemcpyAsync(h->d_rtol, h->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+  unsigned long long launches = 0;
+  int rc = TG_OK;
   cudaEventRecord(h->ev[0], s);
-  int rc = preprocess(h, fdev, bdev, uxd, uyd);
-  if (rc) return rc;
-  // incompatible source check (set by the coarse RT0 step)
-  PcgState head{};
-  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, s));
-  TG_CK(cudaStreamSynchronize(s));
-  if (head.status & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
-  cudaEventRecord(h->ev[1], s);
-  if ((rc = dispatch_pcg(h, rtol))) return rc;
-  cudaEventRecord(h->ev[2], s);
-  launch_add_curl(h->x, uxd, uyd, n, s);
-  launch_pressure(uxd, uyd, h->kinv, pdv, h->pw, n, s);
-  cudaEventRecord(h->ev[3], s);
-  launch_div_error(uxd, uyd, fdev, h->part, h->diverr, n, s);
-  if (host) {
-    TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
-    TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
-    TG_CK(cudaMemcpyAsync(p, h->pd, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+  if (h->opt.profile) {
+    h->prof_used = 0;
+    rc = run_loop(h, &launches);
+  } else {
+    if (!h->exec && (rc = build_graph(h))) return rc;
+    TG_CK(cudaGraphLaunch(h->exec, s));
   }
+  cudaEventRecord(h->ev[3], s);
+  if (rc) return rc;
+  TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, out, s));
+  TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, out, s));
+  TG_CK(cudaMemcpyAsync(p, h->pd, sizeof(double) * nn, out, s));
   PcgState* full = new (std::nothrow) PcgState();
   if (!full) return TG_ERR_OOM;
   double diverr = 0.0;
@@ -659,6 +745,12 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
   if (rc) {
     delete full;
     return rc;
+  }
+  if (!h->opt.profile) {
+    // the while node ran the body once per completed iteration (the pass that
+    // sets done is the last one)
+    const unsigned long long passes = (unsigned long long)std::max(full->iter, 1);
+    launches = h->k_prefix + passes * h->k_body + h->k_epi;
   }
   if (iters) *iters = full->iter;
   if (rep) {
@@ -671,13 +763,27 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
     rep->coarse_dim = h->velocity_basis + h->nc * h->nc + 1;
     rep->coarse_unknowns = h->cs.D;
     rep->max_div_error = diverr;
+    rep->kernel_launches = (int)launches;
+    rep->graph = h->opt.profile ? 0 : 1;
     float ms = 0;
-    cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
-    rep->preprocess_ms = ms;
-    cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
-    rep->pcg_ms = ms;
-    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
-    rep->epilogue_ms = ms;
+    if (h->opt.profile) {
+      cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+      rep->preprocess_ms = ms;
+      cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
+      rep->pcg_ms = ms;
+      cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+      rep->epilogue_ms = ms;
+      double sm = 0.0;
+      for (int k = 0; k + 1 < h->prof_used; k += 2) {
+        cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]);
+        sm += ms;
+      }
+      rep->smoother_ms = sm;
+      rep->smoother_launches = h->prof_used / 2;
+    } else {
+      cudaEventElapsedTime(&ms, h->ev[0], h->ev[3]);
+      rep->pcg_ms = ms;  // whole graph
+    }
   }
   const int status = full->status;
   delete full;
@@ -686,15 +792,22 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
 
 void tg_destroy(tg_handle* h) {
   if (!h) return;
-  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap) cudaStreamDestroy(h->cap);
   void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->pinv, h->blk_band, h->lam,
                   h->x, h->r, h->p, h->q, h->rho, h->phi, h->zacc, h->rin, h->ux, h->uy, h->fd,
-                  h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st};
+                  h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st,
+                  h->d_rtol};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);
   if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->h_rtol) cudaFreeHost(h->h_rtol);
   for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
   delete h;
 }
@@ -722,12 +835,22 @@ int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, do
 
 int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
   if (!h || !f || !ux || !uy) return TG_ERR_INVALID_ARG;
-  TG_CK(cudaMemsetAsync(h->st, 0, offsetof(PcgState, alphas), h->stream));
-  int rc = preprocess(h, f, bflux, ux, uy);
-  if (rc) return rc;
+  const int n = h->n;
+  const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
+  cudaStream_t s = h->stream;
+  TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if (bflux) TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s));
+  else TG_CK(cudaMemsetAsync(h->bd, 0, sizeof(double) * 4 * n, s));
+  *h->h_rtol = 0.5;
+  TG_CK(cudaMemcpyAsync(h->d_rtol, h->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_pcg_reset(h->st, h->d_rtol, 1, 0, s);
+  enqueue_preprocess(h, h->fd, h->bd, h->ux, h->uy, s);
+  TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+  TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
   PcgState head{};
-  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, h->stream));
-  TG_CK(cudaStreamSynchronize(h->stream));
+  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  TG_CK(cudaGetLastError());
   if (head.status & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
   return TG_OK;
 }

@@ -149,6 +149,14 @@ __device__ __forceinline__ double warp_sum_array(const double* a, int m) {
 // ---- launchers (host functions, implemented in the kernel files) ----------
 namespace tg {
 
+// number of kernels enqueued by the launchers below (host counter)
+extern unsigned long long g_kernel_launches;
+#define TG_COUNT(k) (::tg::g_kernel_launches += (unsigned long long)(k))
+
+void configure_kernels(int max_coarse_dim);
+void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s);
+void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s);
+
 // fine operator / vectors (fine.cu)
 void launch_apply_operator(const double* psi, const double* kinv, double* out, int n, cudaStream_t s);
 void launch_apply_operator_f32(const double* psi, const float* kinv, double* out, int n, cudaStream_t s);

@@ -220,6 +220,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update_p(double* __restrict__ 
     p[t] = (double)z[t] + beta * p[t];
 }
 
+// scalar state at the start of a solve (rtol read from device memory so that
+// an instantiated graph serves every tolerance)
+__global__ void k_pcg_reset(PcgState* st, const double* __restrict__ rtol, int maxit, int flexible) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->rz = st->rz_prev = st->rr0 = st->rr = 0.0;
+  st->alpha = st->beta = st->pq = st->zq = 0.0;
+  st->rtol2 = rtol[0] * rtol[0];
+  st->iter = 0;
+  st->maxit = maxit;
+  st->done = 0;
+  st->status = 0;
+  st->flexible = flexible;
+  for (int k = 0; k < 4; ++k) st->counter[k] = 0u;
+}
+
+// loop condition of the graph's while node: continue while not done
+__global__ void k_set_condition(cudaGraphConditionalHandle cond, const PcgState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
 // x = 0, rr0 = (r, r)
 __global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
                                                        const double* __restrict__ r, double* part,
@@ -240,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
       st->rr0 = rr;
       st->rr = rr;
       st->iter = 0;
-      st->done = (rr == 0.0) ? 1 : 0;
+      if (rr == 0.0) st->done = 1;
       if (!isfinite(rr)) {
         st->status |= kStBreakdown;
         st->done = 1;
@@ -445,15 +465,18 @@ inline int grid_for(long long m) {
 
 // ---- launchers ---------------------------------------------------------------
 void launch_apply_operator(const double* psi, const double* kinv, double* out, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_apply_operator<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
 }
 void launch_apply_operator_f32(const double* psi, const float* kinv, double* out, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_apply_operator_f32<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
 }
 
 template <typename TC>
 void launch_residual(const double* r, const TC* z, const TC* kinv, TC* out, int n, const PcgState* st,
                      cudaStream_t s) {
+  TG_COUNT(1);
   k_residual<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, kinv, out, n, st);
 }
 template void launch_residual<double>(const double*, const double*, const double*, double*, int,
@@ -463,28 +486,34 @@ template void launch_residual<float>(const double*, const float*, const float*, 
 
 void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part, PcgState* st,
                           int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_apply_dot<<<grid_for((long long)n * n), kThreads, 0, s>>>(p, kinv, q, part, st, n);
 }
 template <typename TC>
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
                           double* part, PcgState* st, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_update_xr<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, p, q, zacc, part, st, n);
 }
 template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
                      cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_dots<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, q, part, st, n);
 }
 template <typename TC>
 void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_update_p<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(p, z, st, n);
 }
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_init<<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, part, st, n);
 }
 template <typename TC>
 void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,
                         cudaStream_t s) {
+  TG_COUNT(1);
   k_pcg_init_rz<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, p, part, st, n);
 }
 #define TG_INST_TC(TC)                                                                              \
@@ -501,6 +530,7 @@ TG_INST_TC(float)
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const TS* pinv, int npatch, const TR* r, TC* zacc,
                      double eta, int n, const PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
   k_smoother<TC, TS, TR><<<npatch, kThreads, 0, s>>>(geo, pinv, r, zacc, (TC)eta, n, st);
 }
 template void launch_smoother<double, double, double>(const PatchGeo*, const double*, int,
@@ -520,19 +550,35 @@ template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, cons
 template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
   k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, cs.part, nc, b,
                                                    n, st);
+}
+void configure_kernels(int max_coarse_dim) {
+  const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
+  if (shm > 48 * 1024)
+    cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+}
+void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s) {
+  TG_COUNT(1);
+  k_pcg_reset<<<1, 32, 0, s>>>(st, rtol, maxit, flexible);
+}
+void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
+  k_set_condition<<<1, 32, 0, s>>>(cond, st);
 }
 void launch_coarse_solve(const CoarseSpace& cs, const PcgState* st, cudaStream_t s) {
   const size_t shm = sizeof(double) * (size_t)cs.D;
   int grid = (cs.D + 7) / 8;
   if (grid > 2 * 152) grid = 2 * 152;
   if (grid < 1) grid = 1;
+  TG_COUNT(1);
   k_coarse_solve<<<grid, kThreads, shm, s>>>(cs.part, cs.gather, cs.Kinv, cs.coefs, cs.D, st);
 }
 template <typename TC, typename TS>
 void launch_prolong(const CoarseSpace& cs, int nblocks, int nc, int b, int n, TC* v, const PcgState* st,
                     cudaStream_t s) {
+  TG_COUNT(1);
   k_prolong<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, cs.slots, (const TS*)cs.owned, cs.coefs,
                                                   v, nc, b, n, st);
 }
@@ -551,6 +597,7 @@ template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, int, int,
 
 template <typename TA, typename TB>
 void launch_convert(const TA* a, TB* b, long long m, cudaStream_t s) {
+  TG_COUNT(1);
   k_convert<TA, TB><<<grid_for(m), kThreads, 0, s>>>(a, b, m);
 }
 template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);

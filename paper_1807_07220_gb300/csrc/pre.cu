@@ -97,7 +97,10 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
     tot += FH[k];
     ab += absF[k];
   }
-  if (fabs(tot) > 1e-12 * fmax(ab, 1e-300)) st->status |= kStIncompatible;
+  if (fabs(tot) > 1e-12 * fmax(ab, 1e-300)) {
+    st->status |= kStIncompatible;
+    st->done = 1;
+  }
   for (int k = 0; k < (nc + 1) * nc; ++k) {
     gx[k] = 0.0;
     gy[k] = 0.0;
@@ -407,35 +410,43 @@ __global__ void k_div_error_final(const double* __restrict__ part, int g, double
 }  // namespace
 
 void launch_lift(const double* bflux, double* ux, double* uy, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_lift<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(bflux, ux, uy, n);
 }
 void launch_block_sources(const double* f, const double* ux, const double* uy, double* FH, double* absF,
                           int n, int b, cudaStream_t s) {
   const int nc = n / b;
+  TG_COUNT(1);
   k_block_sources<<<nc * nc, kThreads, 0, s>>>(f, ux, uy, FH, absF, n, b);
 }
 void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
                           int nblocks, PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
   k_rt_particular<<<1, 32, 0, s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
 }
 void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
                          cudaStream_t s) {
+  TG_COUNT(1);
   k_add_rt_field<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(gx, gy, ux, uy, n, b);
 }
 void launch_face_residual(const double* ux, const double* uy, const double* kinv, double* rho, int n,
                           cudaStream_t s) {
+  TG_COUNT(1);
   k_face_residual<<<grid_for((long long)n * n), kThreads, 0, s>>>(ux, uy, kinv, rho, n);
 }
 void launch_add_curl(const double* psi, double* ux, double* uy, int n, cudaStream_t s) {
+  TG_COUNT(1);
   k_add_curl<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(psi, ux, uy, n);
 }
 void launch_block_particular(const double* f, double* ux, double* uy, int n, int b, cudaStream_t s) {
   const int nc = n / b;
+  TG_COUNT(1);
   k_block_particular<<<nc * nc, 32, 0, s>>>(f, ux, uy, n, b);
 }
 void launch_block_solve(const double* chol, const double* rho, double* phi, int n, int b,
                         cudaStream_t s) {
   const int nc = n / b;
+  TG_COUNT(1);
   k_block_solve<<<nc * nc, 32, 0, s>>>(chol, rho, phi, n, b);
 }
 void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p, double* work,
@@ -443,15 +454,21 @@ void launch_pressure(const double* ux, const double* uy, const double* kinv, dou
   double* rowp = work;
   double* step = work + (long long)n * n;
   double* rowsum = step + n + 1;
+  TG_COUNT(1);
   k_pressure_rows<<<(n + 127) / 128, 128, 0, s>>>(ux, kinv, rowp, n);
+  TG_COUNT(1);
   k_pressure_steps<<<n, 128, 0, s>>>(uy, kinv, rowp, step, rowsum, n);
+  TG_COUNT(1);
   k_pressure_offsets<<<1, 32, 0, s>>>(step, rowsum, n);
+  TG_COUNT(1);
   k_pressure_final<<<grid_for((long long)n * n), kThreads, 0, s>>>(rowp, step, p, n);
 }
 void launch_div_error(const double* ux, const double* uy, const double* f, double* part, double* out,
                       int n, cudaStream_t s) {
   const int g = grid_for((long long)n * n) > kRedGrid ? kRedGrid : grid_for((long long)n * n);
+  TG_COUNT(1);
   k_div_error<<<g, kThreads, 0, s>>>(ux, uy, f, part, n);
+  TG_COUNT(1);
   k_div_error_final<<<1, 32, 0, s>>>(part, g, out);
 }
 

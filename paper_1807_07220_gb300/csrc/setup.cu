@@ -590,8 +590,12 @@ __global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __re
       const double* zc = zcoef + ((long long)sl.face * (b - 1) + (sl.k - 1)) * b;
       for (int jj = 1; jj < b; ++jj) v += zc[jj] * P[(long long)jj * ncl + t];
     }
-    closed[(long long)blockIdx.x * ncl + t] = v;
-    if (a < b && c < b) owned[(long long)blockIdx.x * b * b + c * b + a] = from_d<TS>(v);
+    // the Galerkin matrix is assembled from the rounded values, so that the
+    // coarse step is the exact K-orthogonal projection onto the span that the
+    // restriction and prolongation actually use
+    const TS vr = from_d<TS>(v);
+    closed[(long long)blockIdx.x * ncl + t] = (double)to_f(vr);
+    if (a < b && c < b) owned[(long long)blockIdx.x * b * b + c * b + a] = vr;
   }
 }
 

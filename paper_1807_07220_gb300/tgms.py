@@ -35,14 +35,16 @@ class tg_grid(ctypes.Structure):
 class tg_options(ctypes.Structure):
     _fields_ = [("eta", c_double), ("m1", c_int), ("m2", c_int), ("precision", c_int),
                 ("flexible", c_int), ("max_iter", c_int), ("pointer_mode", c_int),
-                ("coarse_space", c_int), ("max_basis", c_int)]
+                ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int)]
 
 
 class tg_report(ctypes.Structure):
     _fields_ = [("iters", c_int), ("converged", c_int), ("rel_residual", c_double),
                 ("cond_estimate", c_double), ("coarse_dim", c_int), ("velocity_basis", c_int),
                 ("coarse_unknowns", c_int), ("max_div_error", c_double),
-                ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double)]
+                ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double),
+                ("kernel_launches", c_int), ("smoother_launches", c_int), ("smoother_ms", c_double),
+                ("graph", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -189,6 +191,8 @@ class Solver:
 
     def __init__(self, kappa, b, eig_tol, overlap=2, device="cuda", stream=None, **opts):
         import torch
+        if opts.get("pointer_mode", PTR_DEVICE) != PTR_DEVICE:
+            raise ValueError("Solver passes device tensors; use tg_setup/tg_solve for host pointers")
         self.torch = torch
         n = kappa.shape[0]
         self.n, self.b = n, b
