@@ -153,7 +153,8 @@ def run_ncu_target(args):
     from paper_1807_07220_gb300 import tgms
     n, b = args.n, args.b
     kappa, f = workload(n, 5)
-    s = tgms.Solver(kappa, b, EIG_TOL, precision=args.precision, flexible=int(args.precision != "f64"))
+    s = tgms.Solver(kappa, b, EIG_TOL, precision=args.precision, flexible=int(args.precision != "f64"),
+                    profile=int(args.profile_loop))
     for _ in range(args.warmup + args.steps):
         it, rep = s.solve(f, rtol=RTOL)
     torch.cuda.synchronize()
@@ -387,6 +388,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")
+    ap.add_argument("--profile-loop", action="store_true",
+                    help="with --ncu-target: host-driven PCG loop instead of the graph (ncu sees each launch)")
     args = ap.parse_args()
     if args.ncu_target:
         return run_ncu_target(args)
