@@ -183,6 +183,35 @@ int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, do
  * pointers) with B_h vbar = F_h and the given boundary flux. */
 int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy);
 
+/* ---- allocation-free entry point --------------------------------------
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- code recorded inside a CUDA stream capture
+ * (cudaMalloc is not capturable), processes whose device memory is owned by
+ * another allocator (a framework's caching allocator or a fixed arena), and
+ * latency-critical paths that must not take cudaMalloc's implicit device
+ * synchronisation.  It needs no handle and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Pressure recovery, the same computation as the pressure output of tg_solve:
+ * with kappa (n*n, > 0), and a face velocity (ux, uy) in the layout above,
+ * writes p (n*n, physical sign, zero mean) by integrating the discrete Darcy
+ * law A u = B^T p along grid rows and fitting one offset per row to the
+ * y-face equations in least squares.  All pointers are device pointers;
+ * work runs on `stream` (cudaStream_t, NULL = legacy default stream) and the
+ * call returns after synchronising it.
+ *
+ * Scratch: one statically sized device array compiled into the library
+ * (about 20 MiB, held by every GPU that loads the library until the process
+ * exits) serves grids up to n = 1024; larger n returns TG_ERR_UNSUPPORTED,
+ * n < 2 or a NULL pointer TG_ERR_INVALID_ARG, kappa <= 0 or not finite
+ * TG_ERR_INVALID_ARG (p is then unspecified).  Every call on a device shares
+ * that array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (a one-time set-up per device);
+ * make that first call before any stream capture. */
+int tg_pressure_noalloc(const double* kappa, const double* ux, const double* uy, double* p, int n,
+                        void* stream);
+
 #ifdef __cplusplus
 }
 #endif

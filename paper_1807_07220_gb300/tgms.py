@@ -74,6 +74,7 @@ SIGNATURES = {
     "tg_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p]),
     "tg_coarse_info": (c_int, [c_void_p, c_int_p, c_int_p, c_void_p, c_void_p]),
     "tg_preprocess": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tg_pressure_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
 }
 
 
@@ -181,6 +182,12 @@ def tg_coarse_info(h, b):
 
 def tg_preprocess(h, f, bflux, ux, uy):
     _check(lib().tg_preprocess(h, _ptr(f), _ptr(bflux), _ptr(ux), _ptr(uy)), "tg_preprocess")
+
+
+def tg_pressure_noalloc(kappa, ux, uy, p, n, stream=0):
+    """Allocation-free pressure recovery (device tensors; see include/tgms.h)."""
+    _check(lib().tg_pressure_noalloc(_ptr(kappa), _ptr(ux), _ptr(uy), _ptr(p), int(n),
+                                     ctypes.c_void_p(stream)), "tg_pressure_noalloc")
 
 
 class Solver:
