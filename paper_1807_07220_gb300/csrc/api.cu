@@ -28,6 +28,8 @@ struct tg_handle {
   int* d_status = nullptr;
   // smoother
   PatchGeo* d_pgeo = nullptr;
+  int* d_gofs = nullptr;    // first row group of each patch (+ total)
+  int ngroups = 0;
   void* pinv = nullptr;
   // block factors (preprocessing)
   double* blk_band = nullptr;
@@ -233,25 +235,24 @@ void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st, c
   for (int k = 0; k < h->opt.m1; ++k) {
     if (k == 0) {
       prof_mark(h, s);
-      launch_smoother<TC, TS, double>(h->d_pgeo, pinv, h->npatch, r, zacc, eta, n, st, s);
+      launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s);
       prof_mark(h, s);
     } else {
       launch_residual<TC>(r, zacc, kin, rin, n, st, s);
       prof_mark(h, s);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, s);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
       prof_mark(h, s);
     }
   }
   if (h->cs.D > 0) {
-    launch_residual<TC>(r, zacc, kin, rin, n, st, s);
-    launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, st, s);
+    launch_resid_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
     launch_coarse_solve(h->cs, st, s);
     launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r, zacc, kin, rin, n, st, s);
     prof_mark(h, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, pinv, h->npatch, rin, zacc, eta, n, st, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
     prof_mark(h, s);
   }
 }
@@ -482,6 +483,11 @@ int setup_impl(tg_handle* h, const double* kappa) {
       wmax = std::max(wmax, g.nx + 1);
       nmax = std::max(nmax, g.nloc);
     }
+  std::vector<int> gofs(h->npatch + 1, 0);
+  for (int k = 0; k < h->npatch; ++k) gofs[k + 1] = gofs[k] + (geo[k].nloc + kRowsPerGroup - 1) / kRowsPerGroup;
+  h->ngroups = gofs[h->npatch];
+  if (dalloc(&h->d_gofs, gofs.size())) return TG_ERR_OOM;
+  TG_CK(cudaMemcpyAsync(h->d_gofs, gofs.data(), sizeof(int) * gofs.size(), cudaMemcpyHostToDevice, s));
   int4* d_prect = nullptr;
   double *band = nullptr, *scratch = nullptr;
   if (dalloc(&h->d_pgeo, geo.size()) || dalloc(&d_prect, prect.size()) ||
@@ -601,8 +607,8 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
   TC* zacc = (TC*)h->zacc;
   TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
   if (which == 0) {
-    launch_smoother<TC, TS, double>(h->d_pgeo, (const TS*)h->pinv, h->npatch, rho, zacc, h->opt.eta, n, nullptr,
-                                    h->stream);
+    launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rho, zacc,
+                                    h->opt.eta, n, nullptr, h->stream);
   } else if (which == 1) {
     if (h->cs.D > 0) {
       TC* rin = (TC*)h->rin;
@@ -796,7 +802,7 @@ void tg_destroy(tg_handle* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
-  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->pinv, h->blk_band, h->lam,
+  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->blk_band, h->lam,
                   h->x, h->r, h->p, h->q, h->rho, h->phi, h->zacc, h->rin, h->ux, h->uy, h->fd,
                   h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st,
                   h->d_rtol};

@@ -181,8 +181,12 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
                         cudaStream_t s);
 
 template <typename TC, typename TS, typename TR>
-void launch_smoother(const PatchGeo* geo, const TS* pinv, int npatch, const TR* r, TC* zacc,
-                     double eta, int n, const PcgState* st, cudaStream_t s);
+void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s);
+template <typename TC, typename TS>
+void launch_resid_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const double* r, const TC* z,
+                           const TC* kinv, const PcgState* st, cudaStream_t s);
+constexpr int kRowsPerGroup = 4;   // rows of a patch inverse streamed together by one warp
 
 template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,

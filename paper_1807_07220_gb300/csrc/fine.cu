@@ -334,40 +334,109 @@ __device__ __forceinline__ TC dot_chunk(const __nv_bfloat16* m, const TC* x) {
 }
 
 constexpr int kPatchLd = ((kMaxPatchNodes + 7) / 8) * 8;
+constexpr int kRowsPerWarp = kRowsPerGroup;
 
+// The rows of all patch inverses are cut into groups of kRowsPerWarp rows;
+// gofs[p] is the first group of patch p.  The grid is one wave of CTAs and
+// CTA k owns the contiguous group range [k G/grid, (k+1) G/grid): for each
+// patch it touches it gathers the patch residual into shared memory, then its
+// warps stream their groups (vector loads, the rows of a group in flight
+// together) and scatter eta * (M x) with atomics (patches overlap).
 template <typename TC, typename TS, typename TR>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
+                                                       const int* __restrict__ gofs, int npatch,
                                                        const TS* __restrict__ pinv,
                                                        const TR* __restrict__ r,
                                                        TC* __restrict__ zacc, TC eta, int n,
                                                        const PcgState* st) {
   if (st && st->done) return;
   __shared__ __align__(16) TC xs[kPatchLd];
-  __shared__ TC ys[kPatchLd];
-  const PatchGeo g = geo[blockIdx.x];
-  for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
-    TC v = (TC)0;
-    if (q < g.nloc) {
-      const int a = q % g.nx, c = q / g.nx;
-      v = (TC)r[(long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a)];
-    }
-    xs[q] = v;
+  const int G = gofs[npatch];
+  const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
+  const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
+  if (g0 >= g1) return;
+  int p = 0, hi = npatch - 1;  // last patch with gofs[p] <= g0
+  while (p < hi) {
+    const int mid = (p + hi + 1) >> 1;
+    if (gofs[mid] <= g0) p = mid;
+    else hi = mid - 1;
   }
-  __syncthreads();
   constexpr int W = Vec<TS>::W;
-  const TS* M = pinv + g.off;
+  constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int row = warp; row < g.nloc; row += nw) {
-    const TS* mr = M + (long long)row * g.ld;
-    TC acc = (TC)0;
-    for (int col = lane * W; col < g.ld; col += 32 * W) acc += dot_chunk<TC>(mr + col, xs + col);
-    acc = warp_sum(acc);
-    if (lane == 0) ys[row] = acc;
+  for (; p < npatch && gofs[p] < g1; ++p) {
+    const PatchGeo g = geo[p];
+    __syncthreads();
+    for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
+      TC v = (TC)0;
+      if (q < g.nloc) {
+        const int a = q % g.nx, c = q / g.nx;
+        v = (TC)r[(long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a)];
+      }
+      xs[q] = v;
+    }
+    __syncthreads();
+    const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
+    const TS* M = pinv + g.off;
+    for (int grp = ga + warp; grp < gb; grp += nw) {
+      const int row0 = grp * kRowsPerWarp;
+      TC acc[kRowsPerWarp];
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k) acc[k] = (TC)0;
+#pragma unroll
+      for (int it = 0; it < kIter; ++it) {
+        const int col = (it * 32 + lane) * W;
+        if (col < g.ld) {
+#pragma unroll
+          for (int k = 0; k < kRowsPerWarp; ++k)
+            if (row0 + k < g.nloc) acc[k] += dot_chunk<TC>(M + (long long)(row0 + k) * g.ld + col, xs + col);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k) acc[k] = warp_sum(acc[k]);
+      if (lane < kRowsPerWarp && row0 + lane < g.nloc) {
+        TC v = acc[0];
+#pragma unroll
+        for (int k = 1; k < kRowsPerWarp; ++k)
+          if (lane == k) v = acc[k];
+        const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
+        atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
+      }
+    }
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < g.nloc; q += blockDim.x) {
-    const int a = q % g.nx, c = q / g.nx;
-    atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * ys[q]);
+}
+
+// Inner residual r - K z on each block's owned nodes fused with the coarse
+// restriction (partial inner products with the block's basis tiles).
+template <typename TC, typename TS>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(const int* __restrict__ slot_ptr,
+                                                             const TS* __restrict__ owned,
+                                                             const double* __restrict__ r,
+                                                             const TC* __restrict__ z,
+                                                             const TC* __restrict__ kinv,
+                                                             double* __restrict__ part, int nc, int b,
+                                                             int n, const PcgState* st) {
+  if (st && st->done) return;
+  __shared__ TC sh[32];
+  const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int bb = b * b, t = threadIdx.x;
+  TC val = (TC)0;
+  if (t < bb) {
+    const int i = I * b + t % b, j = J * b + t / b;
+    if (i != 0 && j != 0) val = (TC)r[(long long)j * n + i] - stencil_apply<TC, TC, TC>(z, kinv, n, i, j);
+  }
+  const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
+  for (int s = s0; s < s1; ++s) {
+    TC prod = (t < bb) ? val * (TC)to_f(owned[(long long)s * bb + t]) : (TC)0;
+    prod = warp_sum(prod);
+    if ((t & 31) == 0) sh[t >> 5] = prod;
+    __syncthreads();
+    if (t < 32) {
+      TC x = (t < (int)(blockDim.x >> 5)) ? sh[t] : (TC)0;
+      x = warp_sum(x);
+      if (t == 0) part[s] = (double)x;
+    }
+    __syncthreads();
   }
 }
 
@@ -527,25 +596,62 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 TG_INST_TC(double)
 TG_INST_TC(float)
 
-template <typename TC, typename TS, typename TR>
-void launch_smoother(const PatchGeo* geo, const TS* pinv, int npatch, const TR* r, TC* zacc,
-                     double eta, int n, const PcgState* st, cudaStream_t s) {
-  TG_COUNT(1);
-  k_smoother<TC, TS, TR><<<npatch, kThreads, 0, s>>>(geo, pinv, r, zacc, (TC)eta, n, st);
+int sm_count() {
+  static int cnt = 0;
+  if (!cnt) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev);
+    if (cnt <= 0) cnt = 1;
+  }
+  return cnt;
 }
-template void launch_smoother<double, double, double>(const PatchGeo*, const double*, int,
-                                                      const double*, double*, double, int,
-                                                      const PcgState*, cudaStream_t);
-template void launch_smoother<float, float, double>(const PatchGeo*, const float*, int, const double*,
-                                                    float*, double, int, const PcgState*, cudaStream_t);
-template void launch_smoother<float, float, float>(const PatchGeo*, const float*, int, const float*,
-                                                   float*, double, int, const PcgState*, cudaStream_t);
-template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const __nv_bfloat16*, int,
-                                                            const double*, float*, double, int,
-                                                            const PcgState*, cudaStream_t);
-template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const __nv_bfloat16*, int,
-                                                           const float*, float*, double, int,
-                                                           const PcgState*, cudaStream_t);
+
+// resident CTAs per SM of a smoother instantiation (queried once, at setup)
+template <typename TC, typename TS, typename TR>
+int smoother_per_sm() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR>, kThreads, 0);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  return per_sm;
+}
+
+template <typename TC, typename TS, typename TR>
+void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s) {
+  int grid = smoother_per_sm<TC, TS, TR>() * sm_count();
+  const int min_groups_per_cta = 8;   // keep every warp busy with at least one group
+  if (grid * min_groups_per_cta > ngroups) grid = (ngroups + min_groups_per_cta - 1) / min_groups_per_cta;
+  if (grid < 1) grid = 1;
+  TG_COUNT(1);
+  k_smoother<TC, TS, TR><<<grid, kThreads, 0, s>>>(geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st);
+}
+template void launch_smoother<double, double, double>(const PatchGeo*, const int*, int, int, const double*, const double*, double*,
+                                      double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, float, double>(const PatchGeo*, const int*, int, int, const float*, const double*, float*,
+                                      double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, float, float>(const PatchGeo*, const int*, int, int, const float*, const float*, float*,
+                                      double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const double*, float*,
+                                      double, int, const PcgState*, cudaStream_t);
+template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const float*, float*,
+                                      double, int, const PcgState*, cudaStream_t);
+
+template <typename TC, typename TS>
+void launch_resid_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const double* r, const TC* z,
+                           const TC* kinv, const PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
+  k_resid_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, r, z, kinv, cs.part, nc,
+                                                         b, n, st);
+}
+template void launch_resid_restrict<double, double>(const CoarseSpace&, int, int, int, int, const double*,
+                                                    const double*, const double*, const PcgState*, cudaStream_t);
+template void launch_resid_restrict<float, float>(const CoarseSpace&, int, int, int, int, const double*,
+                                                  const float*, const float*, const PcgState*, cudaStream_t);
+template void launch_resid_restrict<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, const double*,
+                                                          const float*, const float*, const PcgState*, cudaStream_t);
 
 template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
@@ -554,7 +660,15 @@ void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, c
   k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, cs.part, nc, b,
                                                    n, st);
 }
+int sm_count();
+template <typename TC, typename TS, typename TR> int smoother_per_sm();
 void configure_kernels(int max_coarse_dim) {
+  sm_count();
+  smoother_per_sm<double, double, double>();
+  smoother_per_sm<float, float, double>();
+  smoother_per_sm<float, float, float>();
+  smoother_per_sm<float, __nv_bfloat16, double>();
+  smoother_per_sm<float, __nv_bfloat16, float>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
   if (shm > 48 * 1024)
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

@@ -17,6 +17,51 @@ inline int grid_for(long long m) {
   return (int)g;
 }
 
+// In-place inclusive prefix sum of v[0..m) by one CTA (each thread scans a
+// contiguous chunk, then the chunk totals are scanned by warp 0).
+__device__ void block_inclusive_scan(double* v, int m) {
+  __shared__ double tot[1024];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int chunk = (m + T - 1) / T, lo = min(m, t * chunk), hi = min(m, lo + chunk);
+  double run = 0.0;
+  for (int k = lo; k < hi; ++k) {
+    run += v[k];
+    v[k] = run;
+  }
+  tot[t] = run;
+  __syncthreads();
+  if (t == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < T; ++k) {
+      const double x = tot[k];
+      tot[k] = acc;  // exclusive offsets
+      acc += x;
+    }
+  }
+  __syncthreads();
+  const double off = tot[t];
+  for (int k = lo; k < hi; ++k) v[k] += off;
+  __syncthreads();
+}
+
+__device__ double block_reduce_sum(double v) {
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
 // boundary lift: outward normal velocity bflux -> face values; interior 0
 __global__ void k_lift(const double* __restrict__ bflux, double* __restrict__ ux,
                        double* __restrict__ uy, int n) {
@@ -91,25 +136,32 @@ __global__ void k_block_sources(const double* __restrict__ f, const double* __re
 __global__ void k_rt_particular(const double* __restrict__ FH, const double* __restrict__ absF,
                                 double* __restrict__ gx, double* __restrict__ gy, int nc, double H,
                                 int nblocks, PcgState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double tot = 0.0, ab = 0.0;
-  for (int k = 0; k < nblocks; ++k) {
-    tot += FH[k];
+  extern __shared__ double sm[];
+  double* rowt = sm;            // nc row totals -> flux above each block row (column 0)
+  double a = 0.0, ab = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+    a += FH[k];
     ab += absF[k];
   }
-  if (fabs(tot) > 1e-12 * fmax(ab, 1e-300)) {
+  const double tot = block_reduce_sum(a), abt = block_reduce_sum(ab);
+  if (threadIdx.x == 0 && fabs(tot) > 1e-12 * fmax(abt, 1e-300)) {
     st->status |= kStIncompatible;
     st->done = 1;
   }
-  for (int k = 0; k < (nc + 1) * nc; ++k) {
+  for (int k = threadIdx.x; k < (nc + 1) * nc; k += blockDim.x) {
     gx[k] = 0.0;
     gy[k] = 0.0;
   }
-  double below = 0.0;  // flux through the horizontal edge under block row J, column 0
-  for (int J = 0; J < nc; ++J) {
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) {
     double row = 0.0;
     for (int I = 0; I < nc; ++I) row += FH[J * nc + I];
-    const double above = (J + 1 < nc) ? below + row : 0.0;
+    rowt[J] = row;
+  }
+  __syncthreads();
+  block_inclusive_scan(rowt, nc);   // rowt[J] = flux through the edge above row J (column 0)
+  for (int J = threadIdx.x; J < nc; J += blockDim.x) {
+    const double below = (J > 0) ? rowt[J - 1] : 0.0;
+    const double above = (J + 1 < nc) ? rowt[J] : 0.0;
     if (J + 1 < nc) gy[(J + 1) * nc + 0] = above / H;
     double run = 0.0;
     for (int I = 0; I + 1 < nc; ++I) {
@@ -118,7 +170,6 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
       run += s;
       gx[J * (nc + 1) + I + 1] = run / H;
     }
-    below = above;
   }
 }
 
@@ -254,13 +305,13 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
 
 // Band forward/back substitution for one matrix by one warp (column
 // oriented), x overwritten in shared memory.  band row j: L[j*(w+1) + d] =
-// L_{j, j-d}.
-__device__ void warp_band_solve(const double* L, int ldb, int nloc, int w, double* x) {
+// L_{j, j-d}; rinv[j] = 1 / L_{jj}.
+__device__ void warp_band_solve(const double* L, const double* rinv, int ldb, int nloc, int w, double* x) {
   const int lane = threadIdx.x & 31;
   for (int j = 0; j < nloc; ++j) {
     double yj = 0.0;
     if (lane == 0) {
-      yj = x[j] / L[(long long)j * ldb];
+      yj = x[j] * rinv[j];
       x[j] = yj;
     }
     yj = __shfl_sync(0xffffffffu, yj, 0);
@@ -272,7 +323,7 @@ __device__ void warp_band_solve(const double* L, int ldb, int nloc, int w, doubl
   for (int j = nloc - 1; j >= 0; --j) {
     double xj = 0.0;
     if (lane == 0) {
-      xj = x[j] / L[(long long)j * ldb];
+      xj = x[j] * rinv[j];
       x[j] = xj;
     }
     xj = __shfl_sync(0xffffffffu, xj, 0);
@@ -287,12 +338,16 @@ __device__ void warp_band_solve(const double* L, int ldb, int nloc, int w, doubl
 __global__ void k_block_solve(const double* __restrict__ chol, const double* __restrict__ rho,
                               double* __restrict__ phi, int n, int b) {
   __shared__ double x[(kMaxB - 1) * (kMaxB - 1)];
+  __shared__ double rinv[(kMaxB - 1) * (kMaxB - 1)];
   const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int nx = b - 1, nloc = nx * nx, w = nx + 1, ldb = b + 1;  // band width of the block
-  for (int q = threadIdx.x; q < nloc; q += 32)
+  const double* L = chol + (long long)blk * nloc * ldb;
+  for (int q = threadIdx.x; q < nloc; q += 32) {
     x[q] = rho[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx];
+    rinv[q] = 1.0 / L[(long long)q * ldb];
+  }
   __syncwarp();
-  warp_band_solve(chol + (long long)blk * nloc * ldb, ldb, nloc, w, x);
+  warp_band_solve(L, rinv, ldb, nloc, w, x);
   for (int q = threadIdx.x; q < nloc; q += 32)
     phi[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx] = x[q];
 }
@@ -301,14 +356,11 @@ __global__ void k_block_solve(const double* __restrict__ chol, const double* __r
 // offset per row to the y-face equations in least squares, zero mean.
 __global__ void k_pressure_rows(const double* __restrict__ ux, const double* __restrict__ kinv,
                                 double* __restrict__ rowp, int n) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double p = 0.0;
-  rowp[(long long)j * n] = 0.0;
-  for (int i = 1; i < n; ++i) {
-    p -= Au_x(ux, kinv, n, i, j);
-    rowp[(long long)j * n + i] = p;
-  }
+  const int j = blockIdx.x;
+  double* row = rowp + (long long)j * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = (i == 0) ? 0.0 : -Au_x(ux, kinv, n, i, j);
+  __syncthreads();
+  block_inclusive_scan(row, n);
 }
 
 __global__ void k_pressure_steps(const double* __restrict__ uy, const double* __restrict__ kinv,
@@ -341,18 +393,21 @@ __global__ void k_pressure_steps(const double* __restrict__ uy, const double* __
   }
 }
 
+// step[j] (row j -> j+1) becomes the offset c_j = sum_{k<j} step[k] of row j;
+// step[n] receives the mean of the pressure.
 __global__ void k_pressure_offsets(double* __restrict__ step, const double* __restrict__ rowsum,
                                    int n) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  // step[j] becomes the offset of row j; step[n] the mean
-  double c = 0.0, tot = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const double sj = step[j];
-    step[j] = c;
-    tot += rowsum[j] + c * n;
-    c += sj;
+  extern __shared__ double c[];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = (j == 0) ? 0.0 : step[j - 1];
+  __syncthreads();
+  block_inclusive_scan(c, n);
+  double part = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    step[j] = c[j];
+    part += rowsum[j] + (double)n * c[j];
   }
-  step[n] = tot / ((double)n * n);
+  const double tot = block_reduce_sum(part);
+  if (threadIdx.x == 0) step[n] = tot / ((double)n * n);
 }
 
 __global__ void k_pressure_final(const double* __restrict__ rowp, const double* __restrict__ off,
@@ -398,13 +453,16 @@ __global__ void k_div_error(const double* __restrict__ ux, const double* __restr
 }
 
 __global__ void k_div_error_final(const double* __restrict__ part, int g, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double a = 0.0, m = 0.0;
-  for (int k = 0; k < g; ++k) {
+  for (int k = threadIdx.x; k < g; k += 32) {
     a = fmax(a, part[2 * k]);
     m = fmax(m, part[2 * k + 1]);
   }
-  out[0] = (m > 0.0) ? a / m : a;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if (threadIdx.x == 0) out[0] = (m > 0.0) ? a / m : a;
 }
 
 }  // namespace
@@ -422,7 +480,7 @@ void launch_block_sources(const double* f, const double* ux, const double* uy, d
 void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
                           int nblocks, PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_rt_particular<<<1, 32, 0, s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
+  k_rt_particular<<<1, 256, sizeof(double) * (size_t)nc, s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
 }
 void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
                          cudaStream_t s) {
@@ -455,11 +513,11 @@ void launch_pressure(const double* ux, const double* uy, const double* kinv, dou
   double* step = work + (long long)n * n;
   double* rowsum = step + n + 1;
   TG_COUNT(1);
-  k_pressure_rows<<<(n + 127) / 128, 128, 0, s>>>(ux, kinv, rowp, n);
+  k_pressure_rows<<<n, 256, 0, s>>>(ux, kinv, rowp, n);
   TG_COUNT(1);
   k_pressure_steps<<<n, 128, 0, s>>>(uy, kinv, rowp, step, rowsum, n);
   TG_COUNT(1);
-  k_pressure_offsets<<<1, 32, 0, s>>>(step, rowsum, n);
+  k_pressure_offsets<<<1, 256, sizeof(double) * (size_t)n, s>>>(step, rowsum, n);
   TG_COUNT(1);
   k_pressure_final<<<grid_for((long long)n * n), kThreads, 0, s>>>(rowp, step, p, n);
 }
