@@ -25,14 +25,19 @@ struct tg_handle {
   // permeability
   double* kinv = nullptr;
   float* kinv32 = nullptr;
+  double* kcoef = nullptr;  // 5 n^2 node coefficients of the FP64 outer operator
   int* d_status = nullptr;
   // smoother
   PatchGeo* d_pgeo = nullptr;
   int* d_gofs = nullptr;    // first row group of each patch (+ total)
   int ngroups = 0;
   void* pinv = nullptr;
-  // block factors (preprocessing)
+  // block factors (snapshots) and dense block inverses (preprocessing)
   double* blk_band = nullptr;
+  PatchGeo* d_bgeo = nullptr;
+  int* d_bgofs = nullptr;
+  int bgroups = 0;
+  double* binv = nullptr;
   // spectral data
   double* lam = nullptr;
   std::vector<int> nsel;
@@ -43,6 +48,8 @@ struct tg_handle {
   // solve work
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rho = nullptr, *phi = nullptr;
   void *zacc = nullptr, *rin = nullptr;
+  double *p2 = nullptr, *r2 = nullptr;   // ping-pong partners of p and r
+  void* zacc2 = nullptr;                 // ping-pong partner of zacc
   double *ux = nullptr, *uy = nullptr, *fd = nullptr, *bd = nullptr, *pd = nullptr, *pw = nullptr;
   double *part = nullptr, *gx = nullptr, *gy = nullptr, *FH = nullptr, *absF = nullptr, *diverr = nullptr;
   double* tmpd = nullptr;   // n*n scratch (operator hooks)
@@ -277,7 +284,10 @@ void enqueue_preprocess(tg_handle* h, const double* f, const double* bflux, doub
   launch_block_particular(f, ux, uy, n, b, s);
   launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
   cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s);
-  launch_block_solve(h->blk_band, h->rho, h->phi, n, b, s);
+  // phi = K_K^{-1} rho on every block's interior nodes: the smoother's GEMV
+  // with the dense block inverses (blocks do not overlap, eta = 1)
+  launch_smoother<double, double, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv, h->rho, h->phi,
+                                          1.0, n, nullptr, s);
   launch_add_curl(h->phi, ux, uy, n, s);
   launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
 }
@@ -296,16 +306,50 @@ void enqueue_prefix(tg_handle* h, cudaStream_t s) {
   launch_pcg_init_rz<TC>(h->r, (const TC*)h->zacc, h->p, h->part, h->st, n, s);
 }
 
-// one PCG iteration (every kernel returns at once when st->done is set)
+// one PCG iteration (every kernel returns at once when st->done is set).
+// parity 0 reads (p, r, zacc) and writes (p2, r2, zacc2); parity 1 the reverse.
+//   q = K p_new, p_new = z_prev + beta p_old            (operator kernel)
+//   r_new = r_old - alpha q, x += alpha p_new, z = S r_new  (first smoothing)
+//   z += P (r_new - K z)                                (coarse correction)
+//   z += S (r_new - K z)                                (post-smoothing)
+//   beta from (r_new, z) and (z, q)
 template <typename TC, typename TS>
-void enqueue_body(tg_handle* h, cudaStream_t s) {
+void enqueue_iteration(tg_handle* h, int parity, cudaStream_t s) {
   const int n = h->n;
-  TC* zacc = (TC*)h->zacc;
-  launch_pcg_apply_dot(h->p, h->kinv, h->q, h->part, h->st, n, s);
-  launch_pcg_update_xr<TC>(h->x, h->r, h->p, h->q, zacc, h->part, h->st, n, s);
-  precondition<TC, TS>(h, h->r, zacc, h->st, s);
-  launch_pcg_dots<TC>(h->r, zacc, h->q, h->part, h->st, n, s);
-  launch_pcg_update_p<TC>(h->p, zacc, h->st, n, s);
+  double* p_old = parity ? h->p2 : h->p;
+  double* p_new = parity ? h->p : h->p2;
+  double* r_old = parity ? h->r2 : h->r;
+  double* r_new = parity ? h->r : h->r2;
+  TC* z_prev = (TC*)(parity ? h->zacc2 : h->zacc);
+  TC* z_cur = (TC*)(parity ? h->zacc : h->zacc2);
+  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
+  TC* rin = (TC*)h->rin;
+  const TS* pinv = (const TS*)h->pinv;
+  const double eta = h->opt.eta;
+  PcgState* st = h->st;
+  launch_pcg_apply_p<TC>(z_prev, p_old, p_new, h->q, z_cur, h->kcoef, h->part, st, n, s);
+  prof_mark(h, s);
+  launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, h->q, h->x,
+                                 p_new, z_cur, eta, n, h->nc, h->b, h->part, st, s);
+  prof_mark(h, s);
+  for (int k = 1; k < h->opt.m1; ++k) {
+    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
+    prof_mark(h, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    prof_mark(h, s);
+  }
+  if (h->cs.D > 0) {
+    launch_resid_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
+    launch_coarse_solve(h->cs, st, s);
+    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
+  }
+  for (int k = 0; k < h->opt.m2; ++k) {
+    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
+    prof_mark(h, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    prof_mark(h, s);
+  }
+  launch_pcg_dots<TC>(r_new, z_cur, h->q, h->part, st, n, s);
 }
 
 // Step 4: v = vbar + C x, pressure, conservation check
@@ -338,7 +382,8 @@ int build_graph_t(tg_handle* h) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   k0 = g_kernel_launches;
   TG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  enqueue_body<TC, TS>(h, cs);
+  enqueue_iteration<TC, TS>(h, 0, cs);
+  enqueue_iteration<TC, TS>(h, 1, cs);
   launch_set_condition(cond, h->st, cs);
   TG_CK(cudaStreamEndCapture(cs, &body));
   h->k_body = g_kernel_launches - k0;
@@ -371,7 +416,7 @@ int run_loop_t(tg_handle* h, unsigned long long* launches) {
   cudaEventRecord(h->ev[1], s);
   const int maxit = std::min(h->opt.max_iter, kMaxHist);
   for (int it = 0; it < maxit; ++it) {
-    enqueue_body<TC, TS>(h, s);
+    enqueue_iteration<TC, TS>(h, it & 1, s);
     if ((it + 1) % 2 == 0 || it + 1 == maxit) {
       TG_CK(cudaMemcpyAsync(h->h_flag, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
       TG_CK(cudaStreamSynchronize(s));
@@ -456,6 +501,8 @@ int setup_impl(tg_handle* h, const double* kappa) {
     kd = kcopy;
   }
   launch_kinv(kd, h->kinv, h->kinv32, h->d_status, n, s);
+  if (dalloc(&h->kcoef, 5 * nn)) return TG_ERR_OOM;
+  launch_stencil_coefs(h->kinv, h->kcoef, n, s);
   int st = 0;
   int rc = read_status(h, &st);
   cudaFree(kcopy);
@@ -527,11 +574,39 @@ int setup_impl(tg_handle* h, const double* kappa) {
     if (dalloc(&d_brect, brect.size()) || dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1)))
       return TG_ERR_OOM;
     TG_CK(cudaMemcpyAsync(d_brect, brect.data(), sizeof(int4) * brect.size(), cudaMemcpyHostToDevice, s));
+    // dense inverses of the block operators (preprocessing), smoother layout
+    std::vector<PatchGeo> bgeo(h->nblocks);
+    std::vector<int> bgofs(h->nblocks + 1, 0);
+    long long boff = 0;
+    for (int k = 0; k < h->nblocks; ++k) {
+      PatchGeo g{};
+      g.x0 = brect[k].x; g.y0 = brect[k].y; g.nx = g.ny = b - 1;
+      g.nloc = bn;
+      g.ld = ((bn + 7) / 8) * 8;
+      g.off = boff;
+      boff += (long long)g.nloc * g.ld;
+      bgeo[k] = g;
+      bgofs[k + 1] = bgofs[k] + (bn + kRowsPerGroup - 1) / kRowsPerGroup;
+    }
+    h->bgroups = bgofs[h->nblocks];
+    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) || dalloc(&h->binv, (size_t)boff))
+      return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
+    TG_CK(cudaMemcpyAsync(h->d_bgofs, bgofs.data(), sizeof(int) * bgofs.size(), cudaMemcpyHostToDevice, s));
+    double* bscratch = nullptr;
+    const int bbatch = std::max(1, std::min(h->nblocks, (int)((256LL << 20) / (8LL * std::max(bn, 1) * std::max(bn, 1)))));
+    if (dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1))) return TG_ERR_OOM;
     if (bn > 0) {
       launch_assemble_band(h->kinv, d_brect, h->blk_band, h->nblocks, bw, bn, n, s);
       launch_band_cholesky(h->blk_band, d_brect, h->nblocks, bw, bn, h->d_status, s);
+      for (int first = 0; first < h->nblocks; first += bbatch) {
+        const int cnt = std::min(bbatch, h->nblocks - first);
+        launch_band_inverse(h->blk_band, d_brect, first, cnt, bw, bn, bscratch, s);
+        launch_store_inverse<double>(bscratch, h->d_bgeo, first, cnt, bn, h->binv, s);
+      }
     }
     rc = cuda_err(cudaStreamSynchronize(s));
+    cudaFree(bscratch);
     cudaFree(d_brect);
     if (rc) return rc;
   }
@@ -581,7 +656,7 @@ int setup_impl(tg_handle* h, const double* kappa) {
   if (dalloc(&h->x, nn) || dalloc(&h->r, nn) || dalloc(&h->p, nn) || dalloc(&h->q, nn) ||
       dalloc(&h->rho, nn) || dalloc(&h->phi, nn) || dalloc(&h->tmpd, nn) || dalloc(&h->ux, nf) ||
       dalloc(&h->uy, nf) || dalloc(&h->fd, nn) || dalloc(&h->bd, 4 * n) || dalloc(&h->pd, nn) ||
-      dalloc(&h->pw, nn + 2 * n + 2) || dalloc(&h->part, 4 * kRedGrid) || dalloc(&h->gx, (nc + 1) * nc) ||
+      dalloc(&h->pw, nn + 2 * n + 2) || dalloc(&h->part, 4 * std::max<long long>(kRedGrid, (long long)((n + 31) / 32) * ((n + 7) / 8))) || dalloc(&h->gx, (nc + 1) * nc) ||
       dalloc(&h->gy, (nc + 1) * nc) || dalloc(&h->FH, h->nblocks) || dalloc(&h->absF, h->nblocks) ||
       dalloc(&h->diverr, 2) || dalloc(&h->st, 1))
     return TG_ERR_OOM;
@@ -594,6 +669,8 @@ int setup_impl(tg_handle* h, const double* kappa) {
     for (auto& e : h->prof_ev) TG_CK(cudaEventCreate(&e));
   }
   TG_CK(cudaMalloc(&h->zacc, tc * nn));
+  TG_CK(cudaMalloc(&h->zacc2, tc * nn));
+  if (dalloc(&h->p2, nn) || dalloc(&h->r2, nn)) return TG_ERR_OOM;
   TG_CK(cudaMalloc(&h->rin, tc * nn));
   TG_CK(cudaMemsetAsync(h->st, 0, sizeof(PcgState), s));
   TG_CK(cudaStreamSynchronize(s));
@@ -755,7 +832,7 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
   if (!h->opt.profile) {
     // the while node ran the body once per completed iteration (the pass that
     // sets done is the last one)
-    const unsigned long long passes = (unsigned long long)std::max(full->iter, 1);
+    const unsigned long long passes = (unsigned long long)std::max((full->iter + 1) / 2, 1);
     launches = h->k_prefix + passes * h->k_body + h->k_epi;
   }
   if (iters) *iters = full->iter;
@@ -803,9 +880,10 @@ void tg_destroy(tg_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
   void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->blk_band, h->lam,
+                  h->d_bgeo, h->d_bgofs, h->binv, h->kcoef,
                   h->x, h->r, h->p, h->q, h->rho, h->phi, h->zacc, h->rin, h->ux, h->uy, h->fd,
                   h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st,
-                  h->d_rtol};
+                  h->d_rtol, h->p2, h->r2, h->zacc2};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);

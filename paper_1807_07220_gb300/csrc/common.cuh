@@ -184,6 +184,15 @@ template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                      TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s);
 template <typename TC, typename TS>
+void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                            const double* r_old, double* r_new, const double* q, double* x, const double* p,
+                            TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
+                            cudaStream_t s);
+template <typename TC>
+void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
+                        const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);
+void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s);
+template <typename TC, typename TS>
 void launch_resid_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const double* r, const TC* z,
                            const TC* kinv, const PcgState* st, cudaStream_t s);
 constexpr int kRowsPerGroup = 4;   // rows of a patch inverse streamed together by one warp
@@ -211,8 +220,6 @@ void launch_face_residual(const double* ux, const double* uy, const double* kinv
                           int n, cudaStream_t s);
 void launch_add_curl(const double* psi, double* ux, double* uy, int n, cudaStream_t s);
 void launch_block_particular(const double* f, double* ux, double* uy, int n, int b, cudaStream_t s);
-void launch_block_solve(const double* chol, const double* rho, double* phi, int n, int b,
-                        cudaStream_t s);
 void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p,
                      double* work, int n, cudaStream_t s);
 void launch_div_error(const double* ux, const double* uy, const double* f, double* part,

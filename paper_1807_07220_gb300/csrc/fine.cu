@@ -45,6 +45,20 @@ __device__ __forceinline__ bool arrive_last(double partial, double* part, unsign
   return last;
 }
 
+__device__ __forceinline__ bool arrive_last_linear(double partial, double* part, unsigned int* counter,
+                                                   unsigned int bid, unsigned int nblk) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[bid] = partial;
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
 __device__ __forceinline__ double sum_partials(const double* part, int m) {
   double s = 0.0;
   for (int k = threadIdx.x & 31; k < m; k += 32) s += __ldcg(part + k);
@@ -112,6 +126,85 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_dot(const double* __rest
   acc = block_sum(acc, sh);
   if (arrive_last(acc, part, &st->counter[0]) && threadIdx.x < 32) {
     const double pq = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[0] = 0;
+      st->pq = pq;
+      const double alpha = st->rz / pq;
+      if (!(pq > 0.0) || !isfinite(alpha)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+        st->alpha = 0.0;
+      } else {
+        st->alpha = alpha;
+        if (st->iter < kMaxHist) st->alphas[st->iter] = alpha;
+      }
+    }
+  }
+}
+
+// q = K p_new with p_new = z_prev + beta p_old formed on the fly in a shared
+// (32+2) x (8+2) halo tile (each p_new value computed once), p_new and q
+// written, z_next zeroed for the coming smoother accumulation, and
+// alpha = rz / (p_new, q) by the last CTA.
+constexpr int kTx = 32, kTy = 8;
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__ zprev,
+                                                          const double* __restrict__ pold,
+                                                          double* __restrict__ pnew, double* __restrict__ q,
+                                                          TC* __restrict__ znext,
+                                                          const double* __restrict__ kcoef, double* part,
+                                                          PcgState* st, int n) {
+  if (st->done) return;
+  __shared__ double P[kTy + 2][kTx + 2];
+  __shared__ double sh[32];
+  const double beta = st->beta;
+  const int i0 = blockIdx.x * kTx, j0 = blockIdx.y * kTy;
+  for (int t = threadIdx.x; t < (kTx + 2) * (kTy + 2); t += blockDim.x) {
+    const int a = t % (kTx + 2), c = t / (kTx + 2);
+    const int i = i0 - 1 + a, j = j0 - 1 + c;
+    double v = 0.0;
+    if (i >= 1 && j >= 1 && i < n && j < n) {
+      const long long id = (long long)j * n + i;
+      v = (double)zprev[id] + beta * pold[id];
+    }
+    P[c][a] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kTx, ty = threadIdx.x / kTx;
+  const int i = i0 + tx, j = j0 + ty;
+  double acc = 0.0;
+  if (i < n && j < n) {
+    const long long id = (long long)j * n + i, nn = (long long)n * n;
+    const double p0 = P[ty + 1][tx + 1];
+    double qv = 0.0;
+    if (i >= 1 && j >= 1) {
+      // K p with the node coefficients (c0, cE, cN, cNE, cNW); the west, south,
+      // south-west and south-east couplings are the neighbours' east, north,
+      // north-east and north-west ones (K is symmetric)
+      const double* c0 = kcoef;
+      const double* cE = kcoef + nn;
+      const double* cN = kcoef + 2 * nn;
+      const double* cNE = kcoef + 3 * nn;
+      const double* cNW = kcoef + 4 * nn;
+      qv = c0[id] * p0;
+      qv = fma(cE[id], P[ty + 1][tx + 2], qv);
+      qv = fma(cN[id], P[ty + 2][tx + 1], qv);
+      qv = fma(cNE[id], P[ty + 2][tx + 2], qv);
+      qv = fma(cNW[id], P[ty + 2][tx], qv);
+      qv = fma(cE[id - 1], P[ty + 1][tx], qv);
+      qv = fma(cN[id - n], P[ty][tx + 1], qv);
+      qv = fma(cNE[id - n - 1], P[ty][tx], qv);
+      qv = fma(cNW[id - n + 1], P[ty][tx + 2], qv);
+    }
+    pnew[id] = p0;
+    q[id] = qv;
+    znext[id] = (TC)0;
+    acc = p0 * qv;
+  }
+  acc = block_sum(acc, sh);
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
+  if (arrive_last_linear(acc, part, &st->counter[0], bid, nblk) && threadIdx.x < 32) {
+    const double pq = sum_partials(part, nblk);
     if (threadIdx.x == 0) {
       st->counter[0] = 0;
       st->pq = pq;
@@ -292,6 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restri
       st->counter[3] = 0;
       st->rz = rz;
       st->rz_prev = rz;
+      st->beta = 0.0;
       if (!(rz > 0.0) || !isfinite(rz)) {
         st->status |= kStBreakdown;
         st->done = 1;
@@ -309,6 +403,37 @@ template <typename TS> struct Vec;
 template <> struct Vec<double> { static constexpr int W = 2; };
 template <> struct Vec<float> { static constexpr int W = 4; };
 template <> struct Vec<__nv_bfloat16> { static constexpr int W = 8; };
+
+// raw vector chunk of W storage elements (16 bytes) and its dot product
+template <typename TS> struct Chunk;
+template <> struct Chunk<double> { using T = double2; };
+template <> struct Chunk<float> { using T = float4; };
+template <> struct Chunk<__nv_bfloat16> { using T = uint4; };
+template <typename TS>
+__device__ __forceinline__ typename Chunk<TS>::T load_chunk(const TS* m) {
+  return __ldg(reinterpret_cast<const typename Chunk<TS>::T*>(m));
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_raw(const double2& v, const TC* x) {
+  return (TC)(v.x * (double)x[0] + v.y * (double)x[1]);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_raw(const float4& v, const TC* x) {
+  return (TC)(v.x * x[0] + v.y * x[1] + v.z * x[2] + v.w * x[3]);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_raw(const uint4& v, const TC* x) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+  TC acc = (TC)0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    acc += f.x * x[2 * k] + f.y * x[2 * k + 1];
+  }
+  return acc;
+}
+template <typename TS> struct RowsPerPass { static constexpr int R = 4; };
+template <> struct RowsPerPass<double> { static constexpr int R = 2; };
 
 template <typename TC>
 __device__ __forceinline__ TC dot_chunk(const double* m, const TC* x) {
@@ -342,19 +467,37 @@ constexpr int kRowsPerWarp = kRowsPerGroup;
 // patch it touches it gathers the patch residual into shared memory, then its
 // warps stream their groups (vector loads, the rows of a group in flight
 // together) and scatter eta * (M x) with atomics (patches overlap).
-template <typename TC, typename TS, typename TR>
+// With kFused the sweep also performs the PCG update: the residual it
+// smooths is r_new = r_old - alpha q, formed at gather time; the CTA that owns
+// the first row group of patch p writes r_new and x += alpha p on the nodes of
+// block p (blocks partition the nodes, and r_old is never written here), and
+// the last CTA takes (r_new, r_new) and decides convergence.
+struct FuseArgs {
+  const double* r_old;
+  double* r_new;
+  const double* q;
+  double* x;
+  const double* p;
+  double* part;
+  PcgState* st;
+  int nc, b;
+};
+
+template <typename TC, typename TS, typename TR, bool kFused>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
                                                        const int* __restrict__ gofs, int npatch,
                                                        const TS* __restrict__ pinv,
                                                        const TR* __restrict__ r,
                                                        TC* __restrict__ zacc, TC eta, int n,
-                                                       const PcgState* st) {
+                                                       const PcgState* st, FuseArgs fa) {
   if (st && st->done) return;
   __shared__ __align__(16) TC xs[kPatchLd];
+  __shared__ double shr[32];
+  const double alpha = kFused ? fa.st->alpha : 0.0;
+  double rr = 0.0;
   const int G = gofs[npatch];
   const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
   const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
-  if (g0 >= g1) return;
   int p = 0, hi = npatch - 1;  // last patch with gofs[p] <= g0
   while (p < hi) {
     const int mid = (p + hi + 1) >> 1;
@@ -364,43 +507,92 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
   constexpr int W = Vec<TS>::W;
   constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (; p < npatch && gofs[p] < g1; ++p) {
+  for (; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
     const PatchGeo g = geo[p];
     __syncthreads();
     for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
       TC v = (TC)0;
       if (q < g.nloc) {
         const int a = q % g.nx, c = q / g.nx;
-        v = (TC)r[(long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a)];
+        const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
+        if (kFused) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+        else v = (TC)r[id];
       }
       xs[q] = v;
+    }
+    if (kFused && gofs[p] >= g0) {   // this CTA owns block p
+      const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+      for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+        const double rv = fa.r_old[id] - alpha * fa.q[id];
+        fa.r_new[id] = rv;
+        fa.x[id] += alpha * fa.p[id];
+        rr += rv * rv;
+      }
     }
     __syncthreads();
     const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
     const TS* M = pinv + g.off;
+    constexpr int R = RowsPerPass<TS>::R;
+    using V = typename Chunk<TS>::T;
     for (int grp = ga + warp; grp < gb; grp += nw) {
-      const int row0 = grp * kRowsPerWarp;
-      TC acc[kRowsPerWarp];
 #pragma unroll
-      for (int k = 0; k < kRowsPerWarp; ++k) acc[k] = (TC)0;
+      for (int pass = 0; pass < kRowsPerWarp / R; ++pass) {
+        const int row0 = grp * kRowsPerWarp + pass * R;
+        // issue every load of the R rows first (predicated, zero-filled) ...
+        V buf[R][kIter];
 #pragma unroll
-      for (int it = 0; it < kIter; ++it) {
-        const int col = (it * 32 + lane) * W;
-        if (col < g.ld) {
+        for (int it = 0; it < kIter; ++it) {
+          const int col = (it * 32 + lane) * W;
 #pragma unroll
-          for (int k = 0; k < kRowsPerWarp; ++k)
-            if (row0 + k < g.nloc) acc[k] += dot_chunk<TC>(M + (long long)(row0 + k) * g.ld + col, xs + col);
+          for (int k = 0; k < R; ++k) {
+            if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_chunk<TS>(M + (long long)(row0 + k) * g.ld + col);
+            else buf[k][it] = V{};
+          }
+        }
+        // ... then the arithmetic
+        TC acc[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = (TC)0;
+#pragma unroll
+        for (int it = 0; it < kIter; ++it) {
+          const int col = (it * 32 + lane) * W;
+          if (col < g.ld) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) acc[k] += dot_raw<TC>(buf[k][it], xs + col);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = warp_sum(acc[k]);
+        if (lane < R && row0 + lane < g.nloc) {
+          TC v = acc[0];
+#pragma unroll
+          for (int k = 1; k < R; ++k)
+            if (lane == k) v = acc[k];
+          const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
+          atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
         }
       }
-#pragma unroll
-      for (int k = 0; k < kRowsPerWarp; ++k) acc[k] = warp_sum(acc[k]);
-      if (lane < kRowsPerWarp && row0 + lane < g.nloc) {
-        TC v = acc[0];
-#pragma unroll
-        for (int k = 1; k < kRowsPerWarp; ++k)
-          if (lane == k) v = acc[k];
-        const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
-        atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
+    }
+  }
+  if (kFused) {
+    rr = block_sum(rr, shr);
+    if (arrive_last(rr, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
+      const double tot = sum_partials(fa.part, gridDim.x);
+      if (threadIdx.x == 0) {
+        PcgState* S = fa.st;
+        S->counter[1] = 0;
+        S->rr = tot;
+        S->iter += 1;
+        if (tot <= S->rtol2 * S->rr0) {
+          S->done = 1;
+        } else if (!isfinite(tot)) {
+          S->status |= kStBreakdown;
+          S->done = 1;
+        } else if (S->iter >= S->maxit) {
+          S->status |= kStMaxIter;
+          S->done = 1;
+        }
       }
     }
   }
@@ -516,6 +708,22 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ sl
   v[(long long)(J * b + t / b) * n + I * b + t % b] += acc;
 }
 
+// node coefficients of K (FP64): c0, cE, cN, cNE, cNW, cells outside the domain as 0
+__global__ void k_stencil_coefs(const double* __restrict__ kinv, double* __restrict__ kcoef, int n) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    auto cell = [&](int ci, int cj) { return (ci >= 0 && cj >= 0 && ci < n && cj < n) ? kinv[(long long)cj * n + ci] : 0.0; };
+    const double k00 = cell(i - 1, j - 1), k10 = cell(i, j - 1), k01 = cell(i - 1, j), k11 = cell(i, j);
+    kcoef[t] = (2.0 / 3.0) * (k00 + k10 + k01 + k11);
+    kcoef[nn + t] = -(1.0 / 6.0) * (k10 + k11);
+    kcoef[2 * nn + t] = -(1.0 / 6.0) * (k01 + k11);
+    kcoef[3 * nn + t] = -(1.0 / 3.0) * k11;
+    kcoef[4 * nn + t] = -(1.0 / 3.0) * k01;
+  }
+}
+
 template <typename TA, typename TB>
 __global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, long long m) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
@@ -612,22 +820,63 @@ template <typename TC, typename TS, typename TR>
 int smoother_per_sm() {
   static int per_sm = 0;
   if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR, false>, kThreads, 0);
     if (per_sm <= 0) per_sm = 1;
   }
   return per_sm;
 }
 
 template <typename TC, typename TS, typename TR>
-void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s) {
+int smoother_grid(int ngroups) {
   int grid = smoother_per_sm<TC, TS, TR>() * sm_count();
   const int min_groups_per_cta = 8;   // keep every warp busy with at least one group
   if (grid * min_groups_per_cta > ngroups) grid = (ngroups + min_groups_per_cta - 1) / min_groups_per_cta;
-  if (grid < 1) grid = 1;
-  TG_COUNT(1);
-  k_smoother<TC, TS, TR><<<grid, kThreads, 0, s>>>(geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st);
+  return grid < 1 ? 1 : grid;
 }
+
+template <typename TC, typename TS, typename TR>
+void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s) {
+  TG_COUNT(1);
+  k_smoother<TC, TS, TR, false><<<smoother_grid<TC, TS, TR>(ngroups), kThreads, 0, s>>>(
+      geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st, FuseArgs{});
+}
+
+template <typename TC, typename TS>
+void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                            const double* r_old, double* r_new, const double* q, double* x, const double* p,
+                            TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
+                            cudaStream_t s) {
+  TG_COUNT(1);
+  FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b};
+  k_smoother<TC, TS, double, true><<<smoother_grid<TC, TS, double>(ngroups), kThreads, 0, s>>>(
+      geo, gofs, npatch, pinv, r_old, zacc, (TC)eta, n, st, fa);
+}
+template void launch_smoother_update<double, double>(const PatchGeo*, const int*, int, int, const double*,
+                                                     const double*, double*, const double*, double*,
+                                                     const double*, double*, double, int, int, int, double*,
+                                                     PcgState*, cudaStream_t);
+template void launch_smoother_update<float, float>(const PatchGeo*, const int*, int, int, const float*,
+                                                   const double*, double*, const double*, double*,
+                                                   const double*, float*, double, int, int, int, double*,
+                                                   PcgState*, cudaStream_t);
+template void launch_smoother_update<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
+                                                           const __nv_bfloat16*, const double*, double*,
+                                                           const double*, double*, const double*, float*, double,
+                                                           int, int, int, double*, PcgState*, cudaStream_t);
+
+template <typename TC>
+void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
+                        const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s) {
+  TG_COUNT(1);
+  dim3 grid((n + kTx - 1) / kTx, (n + kTy - 1) / kTy);
+  k_pcg_apply_p<TC><<<grid, kThreads, 0, s>>>(zprev, pold, pnew, q, znext, kcoef, part, st, n);
+}
+template void launch_pcg_apply_p<double>(const double*, const double*, double*, double*, double*, const double*,
+                                         double*, PcgState*, int, cudaStream_t);
+template void launch_pcg_apply_p<float>(const float*, const double*, double*, double*, float*, const double*,
+                                        double*, PcgState*, int, cudaStream_t);
+
 template void launch_smoother<double, double, double>(const PatchGeo*, const int*, int, int, const double*, const double*, double*,
                                       double, int, const PcgState*, cudaStream_t);
 template void launch_smoother<float, float, double>(const PatchGeo*, const int*, int, int, const float*, const double*, float*,
@@ -708,6 +957,11 @@ template void launch_prolong<float, float>(const CoarseSpace&, int, int, int, in
                                            const PcgState*, cudaStream_t);
 template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, float*,
                                                    const PcgState*, cudaStream_t);
+
+void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s) {
+  TG_COUNT(1);
+  k_stencil_coefs<<<grid_for((long long)n * n), kThreads, 0, s>>>(kinv, kcoef, n);
+}
 
 template <typename TA, typename TB>
 void launch_convert(const TA* a, TB* b, long long m, cudaStream_t s) {

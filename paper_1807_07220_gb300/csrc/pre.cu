@@ -28,16 +28,29 @@ __device__ void block_inclusive_scan(double* v, int m) {
     run += v[k];
     v[k] = run;
   }
-  tot[t] = run;
-  __syncthreads();
-  if (t == 0) {
-    double acc = 0.0;
-    for (int k = 0; k < T; ++k) {
-      const double x = tot[k];
-      tot[k] = acc;  // exclusive offsets
-      acc += x;
-    }
+  // exclusive scan of the chunk totals: shuffle scan inside each warp, then
+  // the warp totals by warp 0
+  __shared__ double wtot[32];
+  const int lane = t & 31, w = t >> 5;
+  double x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) wtot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    double v = (lane < (T >> 5)) ? wtot[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wtot[lane] = v - ((lane < (T >> 5)) ? wtot[lane] : 0.0);   // exclusive warp offsets
+  }
+  __syncthreads();
+  tot[t] = wtot[w] + x - run;   // exclusive offset of thread t
   __syncthreads();
   const double off = tot[t];
   for (int k = lo; k < hi; ++k) v[k] += off;
@@ -138,9 +151,12 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
                                 int nblocks, PcgState* st) {
   extern __shared__ double sm[];
   double* rowt = sm;            // nc row totals -> flux above each block row (column 0)
+  double* fh = sm + nc;         // block sources staged in shared memory
   double a = 0.0, ab = 0.0;
   for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
-    a += FH[k];
+    const double v = FH[k];
+    fh[k] = v;
+    a += v;
     ab += absF[k];
   }
   const double tot = block_reduce_sum(a), abt = block_reduce_sum(ab);
@@ -154,7 +170,7 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
   }
   for (int J = threadIdx.x; J < nc; J += blockDim.x) {
     double row = 0.0;
-    for (int I = 0; I < nc; ++I) row += FH[J * nc + I];
+    for (int I = 0; I < nc; ++I) row += fh[J * nc + I];
     rowt[J] = row;
   }
   __syncthreads();
@@ -165,7 +181,7 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
     if (J + 1 < nc) gy[(J + 1) * nc + 0] = above / H;
     double run = 0.0;
     for (int I = 0; I + 1 < nc; ++I) {
-      double s = FH[J * nc + I];
+      double s = fh[J * nc + I];
       if (I == 0) s -= (above - below);
       run += s;
       gx[J * (nc + 1) + I + 1] = run / H;
@@ -279,13 +295,15 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
     s[t] = h * h * f[(long long)j * n + i] - cell_outflow(ux, uy, n, i, j, h);
   }
   __syncthreads();
+  if (threadIdx.x < b) {
+    double row = 0.0;
+    for (int a = 0; a < b; ++a) row += s[threadIdx.x * b + a];
+    up[threadIdx.x + 1] = row;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     up[0] = 0.0;
-    for (int c = 0; c < b; ++c) {
-      double row = 0.0;
-      for (int a = 0; a < b; ++a) row += s[c * b + a];
-      up[c + 1] = up[c] + row;
-    }
+    for (int c = 1; c <= b; ++c) up[c] += up[c - 1];
     up[b] = 0.0;
   }
   __syncthreads();
@@ -301,55 +319,6 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
       ux[(long long)(J * b + c) * (n + 1) + I * b + a + 1] += run / h;
     }
   }
-}
-
-// Band forward/back substitution for one matrix by one warp (column
-// oriented), x overwritten in shared memory.  band row j: L[j*(w+1) + d] =
-// L_{j, j-d}; rinv[j] = 1 / L_{jj}.
-__device__ void warp_band_solve(const double* L, const double* rinv, int ldb, int nloc, int w, double* x) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < nloc; ++j) {
-    double yj = 0.0;
-    if (lane == 0) {
-      yj = x[j] * rinv[j];
-      x[j] = yj;
-    }
-    yj = __shfl_sync(0xffffffffu, yj, 0);
-    __syncwarp();
-    for (int d = 1 + lane; d <= w; d += 32)
-      if (j + d < nloc) x[j + d] -= L[(long long)(j + d) * ldb + d] * yj;
-    __syncwarp();
-  }
-  for (int j = nloc - 1; j >= 0; --j) {
-    double xj = 0.0;
-    if (lane == 0) {
-      xj = x[j] * rinv[j];
-      x[j] = xj;
-    }
-    xj = __shfl_sync(0xffffffffu, xj, 0);
-    __syncwarp();
-    for (int d = 1 + lane; d <= w; d += 32)
-      if (j - d >= 0) x[j - d] -= L[(long long)j * ldb + d] * xj;
-    __syncwarp();
-  }
-}
-
-// per block: phi = K_K^{-1} rho on the block's interior nodes (one warp)
-__global__ void k_block_solve(const double* __restrict__ chol, const double* __restrict__ rho,
-                              double* __restrict__ phi, int n, int b) {
-  __shared__ double x[(kMaxB - 1) * (kMaxB - 1)];
-  __shared__ double rinv[(kMaxB - 1) * (kMaxB - 1)];
-  const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
-  const int nx = b - 1, nloc = nx * nx, w = nx + 1, ldb = b + 1;  // band width of the block
-  const double* L = chol + (long long)blk * nloc * ldb;
-  for (int q = threadIdx.x; q < nloc; q += 32) {
-    x[q] = rho[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx];
-    rinv[q] = 1.0 / L[(long long)q * ldb];
-  }
-  __syncwarp();
-  warp_band_solve(L, rinv, ldb, nloc, w, x);
-  for (int q = threadIdx.x; q < nloc; q += 32)
-    phi[(long long)(J * b + 1 + q / nx) * n + I * b + 1 + q % nx] = x[q];
 }
 
 // pressure: integrate A u = B^T p along each row (x-faces), then fit one
@@ -480,7 +449,7 @@ void launch_block_sources(const double* f, const double* ux, const double* uy, d
 void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
                           int nblocks, PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_rt_particular<<<1, 256, sizeof(double) * (size_t)nc, s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
+  k_rt_particular<<<1, 256, sizeof(double) * (size_t)(nc + nblocks), s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
 }
 void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
                          cudaStream_t s) {
@@ -500,12 +469,6 @@ void launch_block_particular(const double* f, double* ux, double* uy, int n, int
   const int nc = n / b;
   TG_COUNT(1);
   k_block_particular<<<nc * nc, 32, 0, s>>>(f, ux, uy, n, b);
-}
-void launch_block_solve(const double* chol, const double* rho, double* phi, int n, int b,
-                        cudaStream_t s) {
-  const int nc = n / b;
-  TG_COUNT(1);
-  k_block_solve<<<nc * nc, 32, 0, s>>>(chol, rho, phi, n, b);
 }
 void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p, double* work,
                      int n, cudaStream_t s) {
