@@ -105,6 +105,7 @@ size_t ts_size(int precision) {
 }
 
 int status_to_err(int st) {
+  if (st & kStTimeout) return TG_ERR_DEVICE_TIMEOUT;
   if (st & kStBadKappa) return TG_ERR_INVALID_ARG;
   if (st & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
   if (st & kStNotSpd) return TG_ERR_BREAKDOWN;
@@ -705,7 +706,8 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
   else
     launch_convert<float, double>((const float*)zacc, z, nn, h->stream);
   TG_CK(cudaStreamSynchronize(h->stream));
-  return cuda_err(cudaGetLastError());
+  TG_CK(cudaGetLastError());
+  return read_and_clear_timeout() ? TG_ERR_DEVICE_TIMEOUT : TG_OK;
 }
 
 int hook_dispatch(tg_handle* h, const double* rho, double* z, int which) {
@@ -868,8 +870,9 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
       rep->pcg_ms = ms;  // whole graph
     }
   }
-  const int status = full->status;
+  int status = full->status;
   delete full;
+  if (read_and_clear_timeout()) status |= kStTimeout;
   return status_to_err(status);
 }
 

@@ -38,6 +38,7 @@ enum : int {
   kStIncompatible = 8,
   kStDegenerate = 16,
   kStMaxIter = 32,
+  kStTimeout = 64,      // a bounded device-side wait expired
 };
 
 struct PatchGeo {
@@ -154,6 +155,7 @@ extern unsigned long long g_kernel_launches;
 #define TG_COUNT(k) (::tg::g_kernel_launches += (unsigned long long)(k))
 
 void configure_kernels(int max_coarse_dim);
+int read_and_clear_timeout();   // 1 if a bounded device wait expired since the last call
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s);
 void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s);
 

@@ -8,6 +8,8 @@
 // the partials in a fixed order and updates PcgState.  Consumers read the
 // scalars in the next kernel, so no CTA ever reads a value written in its own
 // launch.  Every kernel of the loop returns at once when PcgState::done is set.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace tg {
@@ -432,6 +434,18 @@ __device__ __forceinline__ TC dot_raw(const uint4& v, const TC* x) {
   }
   return acc;
 }
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk_smem(const double* m, const TC* x) {
+  return dot_raw<TC>(*reinterpret_cast<const double2*>(m), x);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk_smem(const float* m, const TC* x) {
+  return dot_raw<TC>(*reinterpret_cast<const float4*>(m), x);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_chunk_smem(const __nv_bfloat16* m, const TC* x) {
+  return dot_raw<TC>(*reinterpret_cast<const uint4*>(m), x);
+}
 template <typename TS> struct RowsPerPass { static constexpr int R = 4; };
 template <> struct RowsPerPass<double> { static constexpr int R = 2; };
 
@@ -580,6 +594,210 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
     if (arrive_last(rr, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
       const double tot = sum_partials(fa.part, gridDim.x);
       if (threadIdx.x == 0) {
+        PcgState* S = fa.st;
+        S->counter[1] = 0;
+        S->rr = tot;
+        S->iter += 1;
+        if (tot <= S->rtol2 * S->rr0) {
+          S->done = 1;
+        } else if (!isfinite(tot)) {
+          S->status |= kStBreakdown;
+          S->done = 1;
+        } else if (S->iter >= S->maxit) {
+          S->status |= kStMaxIter;
+          S->done = 1;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA variant of the smoother: the CTA's rows are streamed into a ring of
+// shared-memory stages by 1-D bulk copies (cp.async.bulk, completion counted
+// on one mbarrier per stage); a stage holds up to 8 consecutive rows of one
+// patch (contiguous in memory) and each warp reduces one row of it.  Every
+// wait on an mbarrier is bounded; on expiry the kernel raises kStTimeout,
+// drains its own copies (bounded again) and returns.
+__device__ int g_timeout_flag;   // raised by any expired bounded wait (read and cleared by the host)
+constexpr int kStageRows = 8;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+template <typename TS> struct Stages { static constexpr int N = 4; };
+template <> struct Stages<double> { static constexpr int N = 3; };
+template <> struct Stages<__nv_bfloat16> { static constexpr int N = 6; };
+
+// stage k of the CTA's row list: patch, first row, row count
+struct StageDesc {
+  int patch, row0, rows;
+};
+__device__ __forceinline__ StageDesc stage_of(int k, int p0, int npatch, int g0, int g1,
+                                              const int* __restrict__ gofs, const PatchGeo* __restrict__ geo) {
+  for (int p = p0; p < npatch && gofs[p] < g1; ++p) {
+    const int ra = kRowsPerGroup * (max(g0, gofs[p]) - gofs[p]);
+    const int rb = min(geo[p].nloc, kRowsPerGroup * (min(g1, gofs[p + 1]) - gofs[p]));
+    const int ns = (rb - ra + kStageRows - 1) / kStageRows;
+    if (k < ns) return StageDesc{p, ra + k * kStageRows, min(kStageRows, rb - ra - k * kStageRows)};
+    k -= ns;
+  }
+  return StageDesc{-1, 0, 0};
+}
+
+template <typename TC, typename TS, typename TR, bool kFused>
+__global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __restrict__ geo,
+                                                           const int* __restrict__ gofs, int npatch,
+                                                           const TS* __restrict__ pinv,
+                                                           const TR* __restrict__ r,
+                                                           TC* __restrict__ zacc, TC eta, int n,
+                                                           PcgState* st, FuseArgs fa) {
+  if (st && st->done) return;
+  constexpr int NS = Stages<TS>::N;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(16) TC xs[kPatchLd];
+  __shared__ __align__(8) unsigned long long bars[NS];
+  __shared__ double shr[32];
+  __shared__ int s_nst, s_p0;
+  TS* buf = reinterpret_cast<TS*>(dsm);
+  const int stage_elems = kStageRows * kPatchLd;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double alpha = kFused ? fa.st->alpha : 0.0;
+  const int G = gofs[npatch];
+  const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
+  const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
+  if (tid == 0) {
+    int p = 0, hi = npatch - 1;  // last patch with gofs[p] <= g0
+    while (p < hi) {
+      const int mid = (p + hi + 1) >> 1;
+      if (gofs[mid] <= g0) p = mid;
+      else hi = mid - 1;
+    }
+    int cnt = 0;
+    for (int q = p; g0 < g1 && q < npatch && gofs[q] < g1; ++q) {
+      const int ra = kRowsPerGroup * (max(g0, gofs[q]) - gofs[q]);
+      const int rb = min(geo[q].nloc, kRowsPerGroup * (min(g1, gofs[q + 1]) - gofs[q]));
+      cnt += (rb - ra + kStageRows - 1) / kStageRows;
+    }
+    s_nst = cnt;
+    s_p0 = p;
+    for (int b = 0; b < NS; ++b) mbar_init(smem_addr(&bars[b]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int nst = s_nst, p0 = s_p0;
+  auto issue = [&](int k) {
+    const StageDesc d = stage_of(k, p0, npatch, g0, g1, gofs, geo);
+    const PatchGeo g = geo[d.patch];
+    const unsigned bytes = (unsigned)(d.rows * g.ld * (int)sizeof(TS));
+    const unsigned bar = smem_addr(&bars[k % NS]);
+    mbar_expect_tx(bar, bytes);
+    bulk_copy(smem_addr(buf + (size_t)(k % NS) * stage_elems), pinv + g.off + (long long)d.row0 * g.ld, bytes, bar);
+  };
+  if (tid == 0)
+    for (int k = 0; k < NS && k < nst; ++k) issue(k);
+  int cur = -1;
+  PatchGeo g{};
+  bool ok = true;
+  int k = 0;
+  for (; k < nst; ++k) {
+    const StageDesc d = stage_of(k, p0, npatch, g0, g1, gofs, geo);
+    if (d.patch != cur) {
+      __syncthreads();
+      cur = d.patch;
+      g = geo[cur];
+      for (int q = tid; q < g.ld; q += blockDim.x) {
+        TC v = (TC)0;
+        if (q < g.nloc) {
+          const long long id = (long long)(g.y0 + 1 + q / g.nx) * n + (g.x0 + 1 + q % g.nx);
+          if (kFused) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+          else v = (TC)r[id];
+        }
+        xs[q] = v;
+      }
+      __syncthreads();
+    }
+    // every thread observes the stage's completion; the CTA leaves together if
+    // any thread's bounded wait expired
+    const int mine = mbar_wait(smem_addr(&bars[k % NS]), (unsigned)((k / NS) & 1)) ? 1 : 0;
+    if (!__syncthreads_and(mine)) {
+      ok = false;
+      break;
+    }
+    if (warp < d.rows) {
+      const TS* row = buf + (size_t)(k % NS) * stage_elems + (size_t)warp * g.ld;
+      constexpr int W = Vec<TS>::W;
+      TC acc = (TC)0;
+      for (int col = lane * W; col < g.ld; col += 32 * W) acc += dot_chunk_smem<TC>(row + col, xs + col);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const int q = d.row0 + warp;
+        atomicAdd(zacc + (long long)(g.y0 + 1 + q / g.nx) * n + (g.x0 + 1 + q % g.nx), eta * acc);
+      }
+    }
+    __syncthreads();   // stage buffer free again
+    if (tid == 0 && k + NS < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + NS);
+    }
+  }
+  if (!ok) {
+    // raise the status, then drain this CTA's own copies (bounded) before leaving
+    if (tid == 0) {
+      atomicOr(&g_timeout_flag, 1);
+      if (st) {
+        atomicOr(&st->status, kStTimeout);
+        st->done = 1;
+      }
+      for (int j = k; j < nst && j < k + NS; ++j) mbar_wait(smem_addr(&bars[j % NS]), (unsigned)((j / NS) & 1));
+    }
+    return;
+  }
+  if (kFused) {
+    // block owners: r_new = r_old - alpha q and x += alpha p on their block's nodes
+    double rr = 0.0;
+    for (int p = p0; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
+      if (gofs[p] < g0) continue;
+      const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+      for (int t = tid; t < b * b; t += blockDim.x) {
+        const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+        const double rv = fa.r_old[id] - alpha * fa.q[id];
+        fa.r_new[id] = rv;
+        fa.x[id] += alpha * fa.p[id];
+        rr += rv * rv;
+      }
+    }
+    rr = block_sum(rr, shr);
+    if (arrive_last(rr, fa.part, &fa.st->counter[1]) && tid < 32) {
+      const double tot = sum_partials(fa.part, gridDim.x);
+      if (tid == 0) {
         PcgState* S = fa.st;
         S->counter[1] = 0;
         S->rr = tot;
@@ -834,10 +1052,35 @@ int smoother_grid(int ngroups) {
   return grid < 1 ? 1 : grid;
 }
 
+// TMA smoother: dynamic shared memory of the stage ring, resident CTAs per SM
+template <typename TS>
+size_t tma_smem() { return (size_t)Stages<TS>::N * kStageRows * kPatchLd * sizeof(TS); }
+
+template <typename TC, typename TS, typename TR, bool kFused>
+int tma_per_sm() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    const size_t shm = tma_smem<TS>();
+    cudaFuncSetAttribute(k_smoother_tma<TC, TS, TR, kFused>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother_tma<TC, TS, TR, kFused>, kThreads, shm);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  return per_sm;
+}
+
+int g_use_tma = 0;   // smoother streaming through TMA bulk copies (0: register-staged loads)
+
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                      TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
+  if (g_use_tma) {
+    int grid = tma_per_sm<TC, TS, TR, false>() * sm_count();
+    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
+    k_smoother_tma<TC, TS, TR, false><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
+        geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), FuseArgs{});
+    return;
+  }
   k_smoother<TC, TS, TR, false><<<smoother_grid<TC, TS, TR>(ngroups), kThreads, 0, s>>>(
       geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st, FuseArgs{});
 }
@@ -849,6 +1092,13 @@ void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, in
                             cudaStream_t s) {
   TG_COUNT(1);
   FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b};
+  if (g_use_tma) {
+    int grid = tma_per_sm<TC, TS, double, true>() * sm_count();
+    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
+    k_smoother_tma<TC, TS, double, true><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
+        geo, gofs, npatch, pinv, r_old, zacc, (TC)eta, n, st, fa);
+    return;
+  }
   k_smoother<TC, TS, double, true><<<smoother_grid<TC, TS, double>(ngroups), kThreads, 0, s>>>(
       geo, gofs, npatch, pinv, r_old, zacc, (TC)eta, n, st, fa);
 }
@@ -911,8 +1161,32 @@ void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, c
 }
 int sm_count();
 template <typename TC, typename TS, typename TR> int smoother_per_sm();
+template <typename TC, typename TS, typename TR, bool kFused> int tma_per_sm();
+int read_and_clear_timeout() {
+  int v = 0;
+  cudaMemcpyFromSymbol(&v, g_timeout_flag, sizeof(int));
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_timeout_flag, &zero, sizeof(int));
+  }
+  return v;
+}
+
 void configure_kernels(int max_coarse_dim) {
+  // smoother streaming: register-staged loads (default, measured faster on
+  // GB300) or TMA bulk copies into a shared-memory ring (TGMS_SMOOTHER=tma);
+  // a tuning switch, same arithmetic
+  const char* v = getenv("TGMS_SMOOTHER");
+  g_use_tma = (v && v[0] == 't') ? 1 : 0;
   sm_count();
+  tma_per_sm<double, double, double, false>();
+  tma_per_sm<float, float, double, false>();
+  tma_per_sm<float, float, float, false>();
+  tma_per_sm<float, __nv_bfloat16, double, false>();
+  tma_per_sm<float, __nv_bfloat16, float, false>();
+  tma_per_sm<double, double, double, true>();
+  tma_per_sm<float, float, double, true>();
+  tma_per_sm<float, __nv_bfloat16, double, true>();
   smoother_per_sm<double, double, double>();
   smoother_per_sm<float, float, double>();
   smoother_per_sm<float, float, float>();
