@@ -5,10 +5,11 @@ residual 1e-8 + velocity update and pressure):
   256 x 256 RT0/P0 grid, 16 x 16-cell coarse blocks, kappa = exp(Gaussian field,
   variance 4, correlation length 0.05) with horizontal channels at 1e6,
   quarter five-spot source, eigenvalue tolerance 10, eta 0.2, overlap 2.
-The headline arm runs the mixed-precision preconditioner (FP32 patch inverses
+The headline arm runs the mixed-precision preconditioner (BF16 patch inverses
 and coarse basis, FP32 arithmetic inside the two-grid cycle, flexible CG);
 outer vectors, dot products, fine operator and coarse matrix are FP64.  The
-plain FP64 arm runs the same code with FP64 everywhere.  DOF per solve =
+FP32 arm (FP32 storage) and the plain FP64 arm (the same code with FP64
+everywhere) are reported beside it.  DOF per solve =
 2n(n-1) + n^2 + 1 (interior faces + cells + one pressure constraint).
 
 Inputs are resident on the device when a timed step starts; L2 is flushed
@@ -37,6 +38,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fine DOF-solves/s to 1e-8 rel. residual vs plain FP64; PCG iters; HBM %"
 N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
+# DRAM bytes (read + write) per smoother launch at the default workload, mean of
+# the fused and plain sweeps, from the ncu capture summarised in
+# profiles/k_smoother_256x256.md (valid for the kernel version profiled there)
+SMOOTHER_TRAFFIC = {"f32": 134.42e6, "bf16": 66.24e6}
 
 
 def dof(n):
@@ -74,7 +79,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
         except Exception:
@@ -193,10 +198,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         return s, (time.perf_counter() - t0) * 1e3
 
-    # plain FP64 reference arm of the metric
+    # plain FP64 reference arm of the metric, and the other mixed arm
     plain, plain_setup_ms = make("f64", 0)
     p_times, p_reps = time_solves(plain, f, args.steps, args.warmup, flush, torch)
     plain.close()
+    other = "f32" if prec == "bf16" else "bf16"
+    oth, oth_setup_ms = make(other, 1)
+    o_times, o_reps = time_solves(oth, f, args.steps, args.warmup, flush, torch)
+    oth.close()
     # headline mixed-precision arm, timed region with clock sampling
     head, setup_ms = make(prec, 1)
     for _ in range(args.warmup):
@@ -250,6 +259,7 @@ def run_ours(args):
 
     value, ms_step = agg(times)
     p_value, p_ms = agg(p_times)
+    o_value, o_ms = agg(o_times)
     e_value, e_ms = agg(e2e_t)
     if rank != 0:
         if dist:
@@ -269,12 +279,14 @@ def run_ours(args):
         "coarse_dim": reps[-1].coarse_dim, "setup_ms": setup_ms,
         "plain_f64": {"value": p_value, "ms_per_step": p_ms, "iters": p_reps[-1].iters,
                       "setup_ms": plain_setup_ms},
+        other: {"value": o_value, "ms_per_step": o_ms, "iters": o_reps[-1].iters, "setup_ms": oth_setup_ms},
         "speedup_vs_plain_f64": value / p_value,
         "gpu_launches": sum(r.kernel_launches for r in reps),
         "gpu_launches_per_step": reps[-1].kernel_launches,
         "roofline": {"bound": "hbm", "kernel": "k_smoother (patch inverse apply)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": None,
+                     "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+                     "traffic": SMOOTHER_TRAFFIC.get(prec),
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None,
                      "launches_timed": sm_n, "peak_source": peak_src},
         "e2e": {"value": e_value, "unit": "DOF-solves/s", "ms_per_step": e_ms,
@@ -385,7 +397,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--b", type=int, default=B_DEFAULT)
-    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")
     ap.add_argument("--profile-loop", action="store_true",
