@@ -300,6 +300,103 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched workload
+def batch_specs(ninst, seed=2024):
+    """64 instances: side n from {64, 128, 256, 512}, block b from {8, 16},
+    contrast 10^U(4, 6), own channel field; blocks are widened to 16 where
+    n / b would exceed 32 (the dense coarse inverse's range)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(ninst):
+        n = int(rng.choice([64, 128, 256, 512]))
+        b = int(rng.choice([8, 16]))
+        if n // b > 32:
+            b = 16
+        out.append((n, b, float(10.0 ** rng.uniform(4, 6)), 1000 + i))
+    return out
+
+
+def run_batch(args):
+    """One step = tg_solve_batch over all instances x right-hand sides (one
+    CUDA graph launch); compared with the same problems solved one by one."""
+    import numpy as np
+    import torch
+    from paper_1807_07220_gb300 import inputs, tgms
+    torch.cuda.set_device(0)
+    dev = "cuda"
+    specs = batch_specs(args.batch_instances)
+    nrhs = args.batch_rhs
+    prec = args.precision
+    kappas = [torch.as_tensor(inputs.channel_field(n, c, seed), dtype=torch.float64, device=dev).contiguous()
+              for n, b, c, seed in specs]
+    opts = tgms.default_options(precision=prec, flexible=1)
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = tgms.tg_setup_batch(kappas, [s[0] for s in specs], [s[1] for s in specs], EIG_TOL, nrhs, options=opts,
+                                stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    fs, ux, uy, pp = [], [], [], []
+    for (n, b, c, seed) in specs:
+        for r in range(nrhs):
+            fs.append(torch.as_tensor(inputs.random_pairs(n, 1, 7 * seed + r), dtype=torch.float64,
+                                      device=dev).contiguous())
+            ux.append(torch.zeros(n, n + 1, dtype=torch.float64, device=dev))
+            uy.append(torch.zeros(n + 1, n, dtype=torch.float64, device=dev))
+            pp.append(torch.zeros(n, n, dtype=torch.float64, device=dev))
+    total_dof = sum(dof(n) for (n, b, c, seed) in specs) * nrhs
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        tgms.tg_solve_batch(batch, fs, None, RTOL, ux, uy, pp)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        iters, status = tgms.tg_solve_batch(batch, fs, None, RTOL, ux, uy, pp)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    tgms.tg_destroy_batch(batch)
+    # the same problems one solve at a time (one graph launch each)
+    seq_ms = 0.0
+    seq_iters = []
+    j = 0
+    for (n, b, c, seed), k in zip(specs, kappas):
+        s = tgms.Solver(k, b, EIG_TOL, precision=prec, flexible=1)
+        for r in range(nrhs):
+            for _ in range(2):
+                s.solve(fs[j], rtol=RTOL)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            it, _ = s.solve(fs[j], rtol=RTOL)
+            e1.record()
+            e1.synchronize()
+            seq_ms += e0.elapsed_time(e1)
+            seq_iters.append(it)
+            j += 1
+        s.close()
+    ms = statistics.mean(times)
+    line = {
+        "metric": METRIC + " (batched)", "value": total_dof / (ms / 1e3), "unit": "DOF-solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+%s" % prec, "data": "synthetic",
+        "config": {"workload": "%d instances x %d right-hand sides, n in {64,128,256,512}, b in {8,16} "
+                               "(n/b <= 32), channels at 10^U(4,6), random source/sink pair per rhs, "
+                               "one CUDA graph launch per step" % (len(specs), nrhs),
+                   "instances": [[n, b] for (n, b, c, seed) in specs], "dof_per_step": total_dof},
+        "iters_min_mean_max": [int(iters.min()), float(iters.mean()), int(iters.max())],
+        "all_converged": bool((status == 0).all()),
+        "setup_s": setup_s,
+        "sequential": {"value": total_dof / (seq_ms / 1e3), "ms_per_step": seq_ms,
+                       "note": "same problems, one tg_solve graph launch each"},
+        "speedup_vs_sequential": seq_ms / ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- oracle arms
 ORACLE_SNIPPET = r"""
 import json, os, sys, time
@@ -399,6 +496,9 @@ def main():
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")
     ap.add_argument("--profile-loop", action="store_true",
                     help="with --ncu-target: host-driven PCG loop instead of the graph (ncu sees each launch)")
@@ -409,6 +509,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -183,6 +183,33 @@ int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, do
  * pointers) with B_h vbar = F_h and the given boundary flux. */
 int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy);
 
+/* ---- batched solves ------------------------------------------------------
+ * Many independent problems -- kappa realisations on grids of different sizes,
+ * each with several right-hand sides -- solved by ONE CUDA graph launch whose
+ * ninst * nrhs PCG chains (Section 5, Steps 1, 3, 4 each) run concurrently on
+ * the device.  All instances share options and eigenvalue tolerance; device
+ * pointers only (pointer_mode TG_PTR_DEVICE, profile 0). */
+typedef struct tg_batch tg_batch;
+
+/* Step 2 of Section 5 for every instance: kappa[i] (device, n_i * n_i) on
+ * grids[i]; nrhs right-hand sides per instance.  The batch owns the handles. */
+int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, double eig_tol,
+                   const tg_options* opt, int nrhs, void* stream, tg_batch** out);
+
+/* Solves all ninst * nrhs problems; every array holds ninst * nrhs device
+ * pointers, instance-major (entry i * nrhs + k).  bflux may be NULL (all no
+ * flow) or hold NULL entries.  iters and status (per problem TG_OK or a
+ * TG_ERR_* code) may be NULL.  Returns TG_OK if every problem converged, else
+ * the most severe per-problem code. */
+int tg_solve_batch(tg_batch* batch, const double* const* f, const double* const* bflux, double rtol,
+                   double* const* ux, double* const* uy, double* const* p, int* iters, int* status);
+
+/* Number of instances and right-hand sides per instance. */
+int tg_batch_size(tg_batch* batch, int* ninst, int* nrhs);
+
+/* Frees the batch and its handles.  NULL is allowed. */
+void tg_destroy_batch(tg_batch* batch);
+
 /* ---- allocation-free entry point --------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory -- code recorded inside a CUDA stream capture

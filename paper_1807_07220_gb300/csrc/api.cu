@@ -1,6 +1,14 @@
 // C ABI of libtgms (declared in include/tgms.h): handle management, host-side
 // index tables of the coarse space, and the orchestration of the setup
-// (Step 2 of Section 5) and solve (Steps 1, 3, 4) kernels on one stream.
+// (Step 2 of Section 5) and solve (Steps 1, 3, 4) kernels.
+//
+// A handle holds everything that depends on kappa only (setup) plus one
+// solve context; a context holds the vectors, the PCG scalars and the coarse
+// scratch of one right-hand side.  A solve is one CUDA graph: for each
+// context a chain  prefix (preprocessing, PCG start) -> while node (two PCG
+// iterations per pass) -> epilogue.  A batch puts the chains of many contexts
+// (several handles, several right-hand sides each) into one graph, where they
+// run concurrently.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -15,6 +23,10 @@ using namespace tg;
 
 namespace tg {
 unsigned long long g_kernel_launches = 0;
+}
+
+namespace {
+struct Ctx;
 }
 
 struct tg_handle {
@@ -45,30 +57,33 @@ struct tg_handle {
   int velocity_basis = 0;
   // coarse spaces: preconditioner and coarse RT0 (preprocessing)
   CoarseSpace cs, rt;
-  // solve work
+  int* h_flag = nullptr;    // pinned
+  Ctx* ctx = nullptr;       // default solve context (tg_solve and the operator hooks)
+};
+
+namespace {
+
+// per right-hand-side solve state
+struct Ctx {
+  tg_handle* h = nullptr;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *rho = nullptr, *phi = nullptr;
-  void *zacc = nullptr, *rin = nullptr;
   double *p2 = nullptr, *r2 = nullptr;   // ping-pong partners of p and r
-  void* zacc2 = nullptr;                 // ping-pong partner of zacc
+  void *zacc = nullptr, *zacc2 = nullptr, *rin = nullptr;
   double *ux = nullptr, *uy = nullptr, *fd = nullptr, *bd = nullptr, *pd = nullptr, *pw = nullptr;
   double *part = nullptr, *gx = nullptr, *gy = nullptr, *FH = nullptr, *absF = nullptr, *diverr = nullptr;
-  double* tmpd = nullptr;   // n*n scratch (operator hooks)
+  double *cs_part = nullptr, *cs_coefs = nullptr, *rt_part = nullptr, *rt_coefs = nullptr;
   PcgState* st = nullptr;
-  int* h_flag = nullptr;    // pinned
-  double* h_rtol = nullptr; // pinned
   double* d_rtol = nullptr;
+  double* h_rtol = nullptr;   // pinned
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  // one-graph solve: prefix -> while(PCG body) -> epilogue
+  // one-chain graph of tg_solve
   cudaStream_t cap = nullptr;
-  cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long k_prefix = 0, k_body = 0, k_epi = 0;
   // profiling: events around smoother launches (profile == 1)
   std::vector<cudaEvent_t> prof_ev;
   int prof_used = 0;
 };
-
-namespace {
 
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return TG_OK;
@@ -95,8 +110,6 @@ void free_space(CoarseSpace& c) {
   cudaFree(c.closed);
   cudaFree(c.owned);
   cudaFree(c.Kinv);
-  cudaFree(c.part);
-  cudaFree(c.coefs);
   c = CoarseSpace{};
 }
 
@@ -172,8 +185,7 @@ int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool
     c.max_slots_per_block = std::max(c.max_slots_per_block, ptr[blk + 1] - ptr[blk]);
   const size_t ts = ts_size(h->opt.precision);
   if (dalloc(&c.slot_ptr, ptr.size()) || dalloc(&c.slots, slots.size()) || dalloc(&c.gather, gather.size()) ||
-      dalloc(&c.closed, (size_t)c.nslots * (b + 1) * (b + 1)) || dalloc(&c.part, c.nslots) ||
-      dalloc(&c.coefs, c.D) || dalloc(&c.Kinv, (size_t)c.D * c.D))
+      dalloc(&c.closed, (size_t)c.nslots * (b + 1) * (b + 1)) || dalloc(&c.Kinv, (size_t)c.D * c.D))
     return TG_ERR_OOM;
   const size_t tsz = rt_only ? 8 : ts;  // the RT0 space of the preprocessing is FP64
   TG_CK(cudaMalloc(&c.owned, std::max<size_t>(1, (size_t)c.nslots * b * b * tsz)));
@@ -228,216 +240,6 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
   return rc;
 }
 
-// ---- the two-grid preconditioner (Section 5), zacc must be zero on entry ----
-void prof_mark(tg_handle* h, cudaStream_t s) {
-  if (h->opt.profile && h->prof_used < (int)h->prof_ev.size()) cudaEventRecord(h->prof_ev[h->prof_used++], s);
-}
-
-template <typename TC, typename TS>
-void precondition(tg_handle* h, const double* r, TC* zacc, const PcgState* st, cudaStream_t s) {
-  const int n = h->n;
-  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
-  TC* rin = (TC*)h->rin;
-  const TS* pinv = (const TS*)h->pinv;
-  const double eta = h->opt.eta;
-  for (int k = 0; k < h->opt.m1; ++k) {
-    if (k == 0) {
-      prof_mark(h, s);
-      launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s);
-      prof_mark(h, s);
-    } else {
-      launch_residual<TC>(r, zacc, kin, rin, n, st, s);
-      prof_mark(h, s);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
-      prof_mark(h, s);
-    }
-  }
-  if (h->cs.D > 0) {
-    launch_resid_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
-    launch_coarse_solve(h->cs, st, s);
-    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, st, s);
-  }
-  for (int k = 0; k < h->opt.m2; ++k) {
-    launch_residual<TC>(r, zacc, kin, rin, n, st, s);
-    prof_mark(h, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
-    prof_mark(h, s);
-  }
-}
-
-// Section 3: vbar into (ux, uy), and rho = C^T(-A vbar) (the PCG right-hand side)
-void enqueue_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy,
-                        cudaStream_t s) {
-  const int n = h->n, b = h->b;
-  const long long nn = (long long)n * n;
-  launch_lift(bflux, ux, uy, n, s);
-  launch_block_sources(f, ux, uy, h->FH, h->absF, n, b, s);
-  launch_rt_particular(h->FH, h->absF, h->gx, h->gy, h->nc, h->H, h->nblocks, h->st, s);
-  launch_add_rt_field(h->gx, h->gy, ux, uy, n, b, s);
-  if (h->rt.D > 0) {
-    launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
-    launch_restrict<double, double>(h->rt, h->nblocks, h->nc, b, n, h->rho, nullptr, s);
-    launch_coarse_solve(h->rt, nullptr, s);
-    cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s);
-    launch_prolong<double, double>(h->rt, h->nblocks, h->nc, b, n, h->phi, nullptr, s);
-    launch_add_curl(h->phi, ux, uy, n, s);
-  }
-  launch_block_particular(f, ux, uy, n, b, s);
-  launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
-  cudaMemsetAsync(h->phi, 0, sizeof(double) * nn, s);
-  // phi = K_K^{-1} rho on every block's interior nodes: the smoother's GEMV
-  // with the dense block inverses (blocks do not overlap, eta = 1)
-  launch_smoother<double, double, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv, h->rho, h->phi,
-                                          1.0, n, nullptr, s);
-  launch_add_curl(h->phi, ux, uy, n, s);
-  launch_face_residual(ux, uy, h->kinv, h->rho, n, s);
-}
-
-// reset + preprocessing + PCG start (r = rho, x = 0, z = M r, p = z)
-template <typename TC, typename TS>
-void enqueue_prefix(tg_handle* h, cudaStream_t s) {
-  const int n = h->n;
-  const long long nn = (long long)n * n;
-  launch_pcg_reset(h->st, h->d_rtol, std::min(h->opt.max_iter, kMaxHist), h->opt.flexible, s);
-  enqueue_preprocess(h, h->fd, h->bd, h->ux, h->uy, s);
-  cudaMemcpyAsync(h->r, h->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
-  launch_pcg_init(h->x, h->r, h->part, h->st, n, s);
-  cudaMemsetAsync(h->zacc, 0, sizeof(TC) * nn, s);
-  precondition<TC, TS>(h, h->r, (TC*)h->zacc, h->st, s);
-  launch_pcg_init_rz<TC>(h->r, (const TC*)h->zacc, h->p, h->part, h->st, n, s);
-}
-
-// one PCG iteration (every kernel returns at once when st->done is set).
-// parity 0 reads (p, r, zacc) and writes (p2, r2, zacc2); parity 1 the reverse.
-//   q = K p_new, p_new = z_prev + beta p_old            (operator kernel)
-//   r_new = r_old - alpha q, x += alpha p_new, z = S r_new  (first smoothing)
-//   z += P (r_new - K z)                                (coarse correction)
-//   z += S (r_new - K z)                                (post-smoothing)
-//   beta from (r_new, z) and (z, q)
-template <typename TC, typename TS>
-void enqueue_iteration(tg_handle* h, int parity, cudaStream_t s) {
-  const int n = h->n;
-  double* p_old = parity ? h->p2 : h->p;
-  double* p_new = parity ? h->p : h->p2;
-  double* r_old = parity ? h->r2 : h->r;
-  double* r_new = parity ? h->r : h->r2;
-  TC* z_prev = (TC*)(parity ? h->zacc2 : h->zacc);
-  TC* z_cur = (TC*)(parity ? h->zacc : h->zacc2);
-  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
-  TC* rin = (TC*)h->rin;
-  const TS* pinv = (const TS*)h->pinv;
-  const double eta = h->opt.eta;
-  PcgState* st = h->st;
-  launch_pcg_apply_p<TC>(z_prev, p_old, p_new, h->q, z_cur, h->kcoef, h->part, st, n, s);
-  prof_mark(h, s);
-  launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, h->q, h->x,
-                                 p_new, z_cur, eta, n, h->nc, h->b, h->part, st, s);
-  prof_mark(h, s);
-  for (int k = 1; k < h->opt.m1; ++k) {
-    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
-    prof_mark(h, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
-    prof_mark(h, s);
-  }
-  if (h->cs.D > 0) {
-    launch_resid_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
-    launch_coarse_solve(h->cs, st, s);
-    launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
-  }
-  for (int k = 0; k < h->opt.m2; ++k) {
-    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
-    prof_mark(h, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
-    prof_mark(h, s);
-  }
-  launch_pcg_dots<TC>(r_new, z_cur, h->q, h->part, st, n, s);
-}
-
-// Step 4: v = vbar + C x, pressure, conservation check
-void enqueue_epilogue(tg_handle* h, cudaStream_t s) {
-  launch_add_curl(h->x, h->ux, h->uy, h->n, s);
-  launch_pressure(h->ux, h->uy, h->kinv, h->pd, h->pw, h->n, s);
-  launch_div_error(h->ux, h->uy, h->fd, h->part, h->diverr, h->n, s);
-}
-
-template <typename TC, typename TS>
-int build_graph_t(tg_handle* h) {
-  cudaStream_t cs = h->cap;
-  cudaGraph_t prefix = nullptr, epi = nullptr;
-  unsigned long long k0 = g_kernel_launches;
-  TG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  enqueue_prefix<TC, TS>(h, cs);
-  TG_CK(cudaStreamEndCapture(cs, &prefix));
-  h->k_prefix = g_kernel_launches - k0;
-  TG_CK(cudaGraphCreate(&h->graph, 0));
-  cudaGraphNode_t n1, n2, n3;
-  TG_CK(cudaGraphAddChildGraphNode(&n1, h->graph, nullptr, 0, prefix));
-  cudaGraphConditionalHandle cond;
-  TG_CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  TG_CK(cudaGraphAddNode(&n2, h->graph, &n1, nullptr, 1, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  k0 = g_kernel_launches;
-  TG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  enqueue_iteration<TC, TS>(h, 0, cs);
-  enqueue_iteration<TC, TS>(h, 1, cs);
-  launch_set_condition(cond, h->st, cs);
-  TG_CK(cudaStreamEndCapture(cs, &body));
-  h->k_body = g_kernel_launches - k0;
-  k0 = g_kernel_launches;
-  TG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  enqueue_epilogue(h, cs);
-  TG_CK(cudaStreamEndCapture(cs, &epi));
-  h->k_epi = g_kernel_launches - k0;
-  TG_CK(cudaGraphAddChildGraphNode(&n3, h->graph, &n2, 1, epi));
-  TG_CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
-  cudaGraphDestroy(prefix);
-  cudaGraphDestroy(epi);
-  return TG_OK;
-}
-
-int build_graph(tg_handle* h) {
-  switch (h->opt.precision) {
-    case TG_PREC_F64: return build_graph_t<double, double>(h);
-    case TG_PREC_F32: return build_graph_t<float, float>(h);
-    default: return build_graph_t<float, __nv_bfloat16>(h);
-  }
-}
-
-// host-driven loop (profile mode): same kernels, events around the smoother
-template <typename TC, typename TS>
-int run_loop_t(tg_handle* h, unsigned long long* launches) {
-  cudaStream_t s = h->stream;
-  const unsigned long long k0 = g_kernel_launches;
-  enqueue_prefix<TC, TS>(h, s);
-  cudaEventRecord(h->ev[1], s);
-  const int maxit = std::min(h->opt.max_iter, kMaxHist);
-  for (int it = 0; it < maxit; ++it) {
-    enqueue_iteration<TC, TS>(h, it & 1, s);
-    if ((it + 1) % 2 == 0 || it + 1 == maxit) {
-      TG_CK(cudaMemcpyAsync(h->h_flag, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TG_CK(cudaStreamSynchronize(s));
-      if (*h->h_flag) break;
-    }
-  }
-  cudaEventRecord(h->ev[2], s);
-  enqueue_epilogue(h, s);
-  *launches = g_kernel_launches - k0;
-  return cuda_err(cudaGetLastError());
-}
-
-int run_loop(tg_handle* h, unsigned long long* launches) {
-  switch (h->opt.precision) {
-    case TG_PREC_F64: return run_loop_t<double, double>(h, launches);
-    case TG_PREC_F32: return run_loop_t<float, float>(h, launches);
-    default: return run_loop_t<float, __nv_bfloat16>(h, launches);
-  }
-}
-
 // extreme eigenvalues of the Lanczos tridiagonal by Sturm bisection (report only)
 double lanczos_cond(const PcgState& st) {
   const int m = std::min(st.iter, kMaxHist);
@@ -485,12 +287,283 @@ int validate_grid(const tg_grid* g) {
   return TG_OK;
 }
 
+
+// ---- solve contexts ---------------------------------------------------------
+void ctx_free(Ctx* c) {
+  if (!c) return;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  void* ptrs[] = {c->x, c->r, c->p, c->q, c->rho, c->phi, c->p2, c->r2, c->zacc, c->zacc2, c->rin, c->ux, c->uy,
+                  c->fd, c->bd, c->pd, c->pw, c->part, c->gx, c->gy, c->FH, c->absF, c->diverr, c->cs_part,
+                  c->cs_coefs, c->rt_part, c->rt_coefs, c->st, c->d_rtol};
+  for (void* ptr : ptrs) cudaFree(ptr);
+  if (c->h_rtol) cudaFreeHost(c->h_rtol);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->prof_ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+int ctx_alloc(tg_handle* h, Ctx** out) {
+  *out = nullptr;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return TG_ERR_OOM;
+  c->h = h;
+  const int n = h->n, nc = h->nc;
+  const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
+  const size_t tc = (h->opt.precision == TG_PREC_F64) ? 8 : 4;
+  const long long npart = 4 * std::max<long long>(kRedGrid, (long long)((n + 31) / 32) * ((n + 7) / 8));
+  int rc = TG_OK;
+  if (dalloc(&c->x, nn) || dalloc(&c->r, nn) || dalloc(&c->p, nn) || dalloc(&c->q, nn) || dalloc(&c->rho, nn) ||
+      dalloc(&c->phi, nn) || dalloc(&c->p2, nn) || dalloc(&c->r2, nn) || dalloc(&c->ux, nf) || dalloc(&c->uy, nf) ||
+      dalloc(&c->fd, nn) || dalloc(&c->bd, 4 * n) || dalloc(&c->pd, nn) || dalloc(&c->pw, nn + 2 * n + 2) ||
+      dalloc(&c->part, npart) || dalloc(&c->gx, (nc + 1) * nc) || dalloc(&c->gy, (nc + 1) * nc) ||
+      dalloc(&c->FH, h->nblocks) || dalloc(&c->absF, h->nblocks) || dalloc(&c->diverr, 2) ||
+      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, h->cs.D) || dalloc(&c->rt_part, h->rt.nslots) ||
+      dalloc(&c->rt_coefs, h->rt.D) || dalloc(&c->st, 1) || dalloc(&c->d_rtol, 1))
+    rc = TG_ERR_OOM;
+  if (!rc) rc = cuda_err(cudaMalloc(&c->zacc, tc * nn));
+  if (!rc) rc = cuda_err(cudaMalloc(&c->zacc2, tc * nn));
+  if (!rc) rc = cuda_err(cudaMalloc(&c->rin, tc * nn));
+  if (!rc) rc = cuda_err(cudaMallocHost(&c->h_rtol, sizeof(double)));
+  for (auto& e : c->ev)
+    if (!rc) rc = cuda_err(cudaEventCreate(&e));
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (!rc && h->opt.profile) {
+    c->prof_ev.resize(2048);
+    for (auto& e : c->prof_ev)
+      if (!rc) rc = cuda_err(cudaEventCreate(&e));
+  }
+  if (!rc) rc = cuda_err(cudaMemsetAsync(c->st, 0, sizeof(PcgState), h->stream));
+  if (rc) {
+    ctx_free(c);
+    return rc;
+  }
+  *out = c;
+  return TG_OK;
+}
+
+// ---- the two-grid preconditioner (Section 5), zacc must be zero on entry ----
+void prof_mark(Ctx* c, cudaStream_t s) {
+  if (c->h->opt.profile && c->prof_used < (int)c->prof_ev.size()) cudaEventRecord(c->prof_ev[c->prof_used++], s);
+}
+
+template <typename TC, typename TS>
+void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStream_t s) {
+  tg_handle* h = c->h;
+  const int n = h->n;
+  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
+  TC* rin = (TC*)c->rin;
+  const TS* pinv = (const TS*)h->pinv;
+  const double eta = h->opt.eta;
+  for (int k = 0; k < h->opt.m1; ++k) {
+    if (k == 0) {
+      prof_mark(c, s);
+      launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s);
+      prof_mark(c, s);
+    } else {
+      launch_residual<TC>(r, zacc, kin, rin, n, st, s);
+      prof_mark(c, s);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
+      prof_mark(c, s);
+    }
+  }
+  if (h->cs.D > 0) {
+    launch_resid_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
+    launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
+    launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
+  }
+  for (int k = 0; k < h->opt.m2; ++k) {
+    launch_residual<TC>(r, zacc, kin, rin, n, st, s);
+    prof_mark(c, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
+    prof_mark(c, s);
+  }
+}
+
+// Section 3: vbar into (ux, uy), and rho = C^T(-A vbar) (the PCG right-hand side)
+void enqueue_preprocess(Ctx* c, const double* f, const double* bflux, double* ux, double* uy, cudaStream_t s) {
+  tg_handle* h = c->h;
+  const int n = h->n, b = h->b;
+  const long long nn = (long long)n * n;
+  launch_lift(bflux, ux, uy, n, s);
+  launch_block_sources(f, ux, uy, c->FH, c->absF, n, b, s);
+  launch_rt_particular(c->FH, c->absF, c->gx, c->gy, h->nc, h->H, h->nblocks, c->st, s);
+  launch_add_rt_field(c->gx, c->gy, ux, uy, n, b, s);
+  if (h->rt.D > 0) {
+    launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
+    launch_restrict<double, double>(h->rt, c->rt_part, h->nblocks, h->nc, b, n, c->rho, nullptr, s);
+    launch_coarse_solve(h->rt, c->rt_part, c->rt_coefs, nullptr, s);
+    cudaMemsetAsync(c->phi, 0, sizeof(double) * nn, s);
+    launch_prolong<double, double>(h->rt, c->rt_coefs, h->nblocks, h->nc, b, n, c->phi, nullptr, s);
+    launch_add_curl(c->phi, ux, uy, n, s);
+  }
+  launch_block_particular(f, ux, uy, n, b, s);
+  launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
+  cudaMemsetAsync(c->phi, 0, sizeof(double) * nn, s);
+  // phi = K_K^{-1} rho on every block's interior nodes: the smoother's GEMV
+  // with the dense block inverses (blocks do not overlap, eta = 1)
+  launch_smoother<double, double, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv, c->rho, c->phi,
+                                          1.0, n, nullptr, s);
+  launch_add_curl(c->phi, ux, uy, n, s);
+  launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
+}
+
+// reset + preprocessing + PCG start (r = rho, x = 0, z = M r, p = z)
+template <typename TC, typename TS>
+void enqueue_prefix(Ctx* c, cudaStream_t s) {
+  tg_handle* h = c->h;
+  const int n = h->n;
+  const long long nn = (long long)n * n;
+  launch_pcg_reset(c->st, c->d_rtol, std::min(h->opt.max_iter, kMaxHist), h->opt.flexible, s);
+  enqueue_preprocess(c, c->fd, c->bd, c->ux, c->uy, s);
+  cudaMemcpyAsync(c->r, c->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+  launch_pcg_init(c->x, c->r, c->part, c->st, n, s);
+  cudaMemsetAsync(c->zacc, 0, sizeof(TC) * nn, s);
+  precondition<TC, TS>(c, c->r, (TC*)c->zacc, c->st, s);
+  launch_pcg_init_rz<TC>(c->r, (const TC*)c->zacc, c->p, c->part, c->st, n, s);
+}
+
+// one PCG iteration (every kernel returns at once when st->done is set).
+// parity 0 reads (p, r, zacc) and writes (p2, r2, zacc2); parity 1 the reverse.
+//   q = K p_new, p_new = z_prev + beta p_old                (operator kernel)
+//   r_new = r_old - alpha q, x += alpha p_new, z = S r_new  (first smoothing)
+//   z += P (r_new - K z)                                    (coarse correction)
+//   z += S (r_new - K z)                                    (post-smoothing)
+//   beta from (r_new, z) and (z, q)
+template <typename TC, typename TS>
+void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
+  tg_handle* h = c->h;
+  const int n = h->n;
+  double* p_old = parity ? c->p2 : c->p;
+  double* p_new = parity ? c->p : c->p2;
+  double* r_old = parity ? c->r2 : c->r;
+  double* r_new = parity ? c->r : c->r2;
+  TC* z_prev = (TC*)(parity ? c->zacc2 : c->zacc);
+  TC* z_cur = (TC*)(parity ? c->zacc : c->zacc2);
+  const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
+  TC* rin = (TC*)c->rin;
+  const TS* pinv = (const TS*)h->pinv;
+  const double eta = h->opt.eta;
+  PcgState* st = c->st;
+  launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
+  prof_mark(c, s);
+  launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
+                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s);
+  prof_mark(c, s);
+  for (int k = 1; k < h->opt.m1; ++k) {
+    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
+    prof_mark(c, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    prof_mark(c, s);
+  }
+  if (h->cs.D > 0) {
+    launch_resid_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
+    launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
+    launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
+  }
+  for (int k = 0; k < h->opt.m2; ++k) {
+    launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
+    prof_mark(c, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    prof_mark(c, s);
+  }
+  launch_pcg_dots<TC>(r_new, z_cur, c->q, c->part, st, n, s);
+}
+
+// Step 4: v = vbar + C x, pressure, conservation check
+void enqueue_epilogue(Ctx* c, cudaStream_t s) {
+  tg_handle* h = c->h;
+  launch_add_curl(c->x, c->ux, c->uy, h->n, s);
+  launch_pressure(c->ux, c->uy, h->kinv, c->pd, c->pw, h->n, s);
+  launch_div_error(c->ux, c->uy, c->fd, c->part, c->diverr, h->n, s);
+}
+
+// Appends the chain  prefix -> while(two iterations) -> epilogue  of one
+// context to `graph` (roots: no dependencies), captured on stream cs.
+template <typename TC, typename TS>
+int add_chain_t(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaStreamCaptureStatus cst;
+  unsigned long long k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_prefix<TC, TS>(c, cs);
+  TG_CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+  cudaGraph_t g2 = nullptr;
+  TG_CK(cudaStreamEndCapture(cs, &g2));
+  c->k_prefix = g_kernel_launches - k0;
+  cudaGraphConditionalHandle cond;
+  TG_CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  TG_CK(cudaGraphAddNode(&wnode, graph, tail.data(), nullptr, tail.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_iteration<TC, TS>(c, 0, cs);
+  enqueue_iteration<TC, TS>(c, 1, cs);
+  launch_set_condition(cond, c->st, cs);
+  TG_CK(cudaStreamEndCapture(cs, &body));
+  c->k_body = g_kernel_launches - k0;
+  k0 = g_kernel_launches;
+  TG_CK(cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  enqueue_epilogue(c, cs);
+  TG_CK(cudaStreamEndCapture(cs, &g2));
+  c->k_epi = g_kernel_launches - k0;
+  return TG_OK;
+}
+
+int add_chain(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
+  switch (c->h->opt.precision) {
+    case TG_PREC_F64: return add_chain_t<double, double>(c, graph, cs);
+    case TG_PREC_F32: return add_chain_t<float, float>(c, graph, cs);
+    default: return add_chain_t<float, __nv_bfloat16>(c, graph, cs);
+  }
+}
+
+// host-driven loop (profile mode): same kernels, events around the smoother
+template <typename TC, typename TS>
+int run_loop_t(Ctx* c, unsigned long long* launches) {
+  tg_handle* h = c->h;
+  cudaStream_t s = h->stream;
+  const unsigned long long k0 = g_kernel_launches;
+  enqueue_prefix<TC, TS>(c, s);
+  cudaEventRecord(c->ev[1], s);
+  const int maxit = std::min(h->opt.max_iter, kMaxHist);
+  for (int it = 0; it < maxit; ++it) {
+    enqueue_iteration<TC, TS>(c, it & 1, s);
+    if ((it + 1) % 2 == 0 || it + 1 == maxit) {
+      TG_CK(cudaMemcpyAsync(h->h_flag, &c->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TG_CK(cudaStreamSynchronize(s));
+      if (*h->h_flag) break;
+    }
+  }
+  cudaEventRecord(c->ev[2], s);
+  enqueue_epilogue(c, s);
+  *launches = g_kernel_launches - k0;
+  return cuda_err(cudaGetLastError());
+}
+
+int run_loop(Ctx* c, unsigned long long* launches) {
+  switch (c->h->opt.precision) {
+    case TG_PREC_F64: return run_loop_t<double, double>(c, launches);
+    case TG_PREC_F32: return run_loop_t<float, float>(c, launches);
+    default: return run_loop_t<float, __nv_bfloat16>(c, launches);
+  }
+}
+
 int setup_impl(tg_handle* h, const double* kappa) {
   const int n = h->n, b = h->b, nc = h->nc;
   const long long nn = (long long)n * n;
   cudaStream_t s = h->stream;
   TG_CK(cudaMallocHost(&h->h_flag, sizeof(int)));
-  for (auto& e : h->ev) TG_CK(cudaEventCreate(&e));
   TG_CK(cudaMalloc(&h->d_status, sizeof(int)));
   TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
   if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn)) return TG_ERR_OOM;
@@ -651,55 +724,35 @@ int setup_impl(tg_handle* h, const double* kappa) {
   if ((rc = read_status(h, &st))) return rc;
   if (st) return status_to_err(st);
 
-  // ---- solve work space ----
-  const size_t tc = (h->opt.precision == TG_PREC_F64) ? 8 : 4;
-  const long long nf = (long long)(n + 1) * n;
-  if (dalloc(&h->x, nn) || dalloc(&h->r, nn) || dalloc(&h->p, nn) || dalloc(&h->q, nn) ||
-      dalloc(&h->rho, nn) || dalloc(&h->phi, nn) || dalloc(&h->tmpd, nn) || dalloc(&h->ux, nf) ||
-      dalloc(&h->uy, nf) || dalloc(&h->fd, nn) || dalloc(&h->bd, 4 * n) || dalloc(&h->pd, nn) ||
-      dalloc(&h->pw, nn + 2 * n + 2) || dalloc(&h->part, 4 * std::max<long long>(kRedGrid, (long long)((n + 31) / 32) * ((n + 7) / 8))) || dalloc(&h->gx, (nc + 1) * nc) ||
-      dalloc(&h->gy, (nc + 1) * nc) || dalloc(&h->FH, h->nblocks) || dalloc(&h->absF, h->nblocks) ||
-      dalloc(&h->diverr, 2) || dalloc(&h->st, 1))
-    return TG_ERR_OOM;
   configure_kernels(std::max(h->cs.D, h->rt.D));
-  TG_CK(cudaMallocHost(&h->h_rtol, sizeof(double)));
-  if (dalloc(&h->d_rtol, 1)) return TG_ERR_OOM;
-  TG_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-  if (h->opt.profile) {
-    h->prof_ev.resize(2048);
-    for (auto& e : h->prof_ev) TG_CK(cudaEventCreate(&e));
-  }
-  TG_CK(cudaMalloc(&h->zacc, tc * nn));
-  TG_CK(cudaMalloc(&h->zacc2, tc * nn));
-  if (dalloc(&h->p2, nn) || dalloc(&h->r2, nn)) return TG_ERR_OOM;
-  TG_CK(cudaMalloc(&h->rin, tc * nn));
-  TG_CK(cudaMemsetAsync(h->st, 0, sizeof(PcgState), s));
+  if ((rc = ctx_alloc(h, &h->ctx))) return rc;
   TG_CK(cudaStreamSynchronize(s));
   return cuda_err(cudaGetLastError());
 }
 
 template <typename TC, typename TS>
 int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
+  Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n;
-  TC* zacc = (TC*)h->zacc;
+  TC* zacc = (TC*)c->zacc;
   TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
   if (which == 0) {
     launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rho, zacc,
                                     h->opt.eta, n, nullptr, h->stream);
   } else if (which == 1) {
     if (h->cs.D > 0) {
-      TC* rin = (TC*)h->rin;
+      TC* rin = (TC*)c->rin;
       if (std::is_same<TC, double>::value)
         TG_CK(cudaMemcpyAsync(rin, rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
       else
         launch_convert<double, float>(rho, (float*)rin, nn, h->stream);
-      launch_restrict<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, rin, nullptr, h->stream);
-      launch_coarse_solve(h->cs, nullptr, h->stream);
-      launch_prolong<TC, TS>(h->cs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
+      launch_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, rin, nullptr, h->stream);
+      launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, nullptr, h->stream);
+      launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
     }
   } else {
-    precondition<TC, TS>(h, rho, zacc, nullptr, h->stream);
+    precondition<TC, TS>(c, rho, zacc, nullptr, h->stream);
   }
   if (std::is_same<TC, double>::value)
     TG_CK(cudaMemcpyAsync(z, zacc, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
@@ -719,6 +772,46 @@ int hook_dispatch(tg_handle* h, const double* rho, double* z, int which) {
   }
 }
 
+// ---- batches ------------------------------------------------------------------
+}  // namespace
+
+struct tg_batch {
+  std::vector<tg_handle*> handles;   // owned
+  std::vector<Ctx*> ctx;             // ninst * nrhs, instance-major (owned)
+  int nrhs = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // device tables: per context the staging buffers and sizes
+  double** d_src = nullptr;    // 5 m caller pointers: f, bflux, ux, uy, p
+  double** d_buf = nullptr;    // 5 m context buffers: fd, bd, ux, uy, pd
+  long long* d_cnt = nullptr;  // 5 m element counts
+  double** h_src = nullptr;    // pinned staging of the caller pointers
+  double* d_rtol = nullptr;    // shared tolerance; each context's d_rtol is set from it
+  double** d_ctx_rtol = nullptr;
+  PcgState** d_ctx_state = nullptr;  // PCG state per context
+  int* d_out = nullptr;         // 2 m: iter, status
+  int* h_out = nullptr;         // pinned
+  double* h_rtol = nullptr;     // pinned
+};
+
+namespace {
+
+void batch_free(tg_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (Ctx* c : b->ctx) ctx_free(c);
+  for (tg_handle* h : b->handles) tg_destroy(h);
+  void* ptrs[] = {b->d_src, b->d_buf, b->d_cnt, b->d_rtol, b->d_ctx_rtol, b->d_ctx_state, b->d_out};
+  for (void* p : ptrs) cudaFree(p);
+  if (b->h_src) cudaFreeHost(b->h_src);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->h_rtol) cudaFreeHost(b->h_rtol);
+  delete b;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -735,6 +828,7 @@ int tg_default_options(tg_options* opt) {
   opt->pointer_mode = TG_PTR_DEVICE;
   opt->coarse_space = TG_COARSE_GMSFEM;
   opt->max_basis = 0;
+  opt->profile = 0;
   return TG_OK;
 }
 
@@ -794,37 +888,45 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
 int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
              int* iters, tg_report* rep) {
   if (!h || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
+  Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
   cudaStream_t s = h->stream;
   const cudaMemcpyKind in = (h->opt.pointer_mode == TG_PTR_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind out = (h->opt.pointer_mode == TG_PTR_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  // stage inputs into handle buffers (the instantiated graph only references those)
-  TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, in, s));
-  if (bflux) TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, in, s));
-  else TG_CK(cudaMemsetAsync(h->bd, 0, sizeof(double) * 4 * n, s));
-  *h->h_rtol = rtol;
-  TG_CK(cudaMemcpyAsync(h->d_rtol, h->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+  // stage inputs into context buffers (the instantiated graph only references those)
+  TG_CK(cudaMemcpyAsync(c->fd, f, sizeof(double) * nn, in, s));
+  if (bflux) TG_CK(cudaMemcpyAsync(c->bd, bflux, sizeof(double) * 4 * n, in, s));
+  else TG_CK(cudaMemsetAsync(c->bd, 0, sizeof(double) * 4 * n, s));
+  *c->h_rtol = rtol;
+  TG_CK(cudaMemcpyAsync(c->d_rtol, c->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
   unsigned long long launches = 0;
   int rc = TG_OK;
-  cudaEventRecord(h->ev[0], s);
+  cudaEventRecord(c->ev[0], s);
   if (h->opt.profile) {
-    h->prof_used = 0;
-    rc = run_loop(h, &launches);
+    c->prof_used = 0;
+    rc = run_loop(c, &launches);
   } else {
-    if (!h->exec && (rc = build_graph(h))) return rc;
-    TG_CK(cudaGraphLaunch(h->exec, s));
+    if (!c->exec) {
+      cudaGraph_t g = nullptr;
+      TG_CK(cudaGraphCreate(&g, 0));
+      rc = add_chain(c, g, c->cap);
+      if (!rc) rc = cuda_err(cudaGraphInstantiate(&c->exec, g, 0));
+      cudaGraphDestroy(g);
+      if (rc) return rc;
+    }
+    TG_CK(cudaGraphLaunch(c->exec, s));
   }
-  cudaEventRecord(h->ev[3], s);
+  cudaEventRecord(c->ev[3], s);
   if (rc) return rc;
-  TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, out, s));
-  TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, out, s));
-  TG_CK(cudaMemcpyAsync(p, h->pd, sizeof(double) * nn, out, s));
+  TG_CK(cudaMemcpyAsync(ux, c->ux, sizeof(double) * nf, out, s));
+  TG_CK(cudaMemcpyAsync(uy, c->uy, sizeof(double) * nf, out, s));
+  TG_CK(cudaMemcpyAsync(p, c->pd, sizeof(double) * nn, out, s));
   PcgState* full = new (std::nothrow) PcgState();
   if (!full) return TG_ERR_OOM;
   double diverr = 0.0;
-  rc = cuda_err(cudaMemcpyAsync(full, h->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  if (!rc) rc = cuda_err(cudaMemcpyAsync(&diverr, h->diverr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  rc = cuda_err(cudaMemcpyAsync(full, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(&diverr, c->diverr, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
   if (!rc) rc = cuda_err(cudaGetLastError());
   if (rc) {
@@ -832,10 +934,9 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
     return rc;
   }
   if (!h->opt.profile) {
-    // the while node ran the body once per completed iteration (the pass that
-    // sets done is the last one)
+    // the while node ran the two-iteration body once per pair of iterations
     const unsigned long long passes = (unsigned long long)std::max((full->iter + 1) / 2, 1);
-    launches = h->k_prefix + passes * h->k_body + h->k_epi;
+    launches = c->k_prefix + passes * c->k_body + c->k_epi;
   }
   if (iters) *iters = full->iter;
   if (rep) {
@@ -852,21 +953,21 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
     rep->graph = h->opt.profile ? 0 : 1;
     float ms = 0;
     if (h->opt.profile) {
-      cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+      cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
       rep->preprocess_ms = ms;
-      cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
+      cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
       rep->pcg_ms = ms;
-      cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+      cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
       rep->epilogue_ms = ms;
       double sm = 0.0;
-      for (int k = 0; k + 1 < h->prof_used; k += 2) {
-        cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]);
+      for (int k = 0; k + 1 < c->prof_used; k += 2) {
+        cudaEventElapsedTime(&ms, c->prof_ev[k], c->prof_ev[k + 1]);
         sm += ms;
       }
       rep->smoother_ms = sm;
-      rep->smoother_launches = h->prof_used / 2;
+      rep->smoother_launches = c->prof_used / 2;
     } else {
-      cudaEventElapsedTime(&ms, h->ev[0], h->ev[3]);
+      cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
       rep->pcg_ms = ms;  // whole graph
     }
   }
@@ -879,23 +980,13 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
 void tg_destroy(tg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  if (h->exec) cudaGraphExecDestroy(h->exec);
-  if (h->graph) cudaGraphDestroy(h->graph);
-  if (h->cap) cudaStreamDestroy(h->cap);
+  ctx_free(h->ctx);
   void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->blk_band, h->lam,
-                  h->d_bgeo, h->d_bgofs, h->binv, h->kcoef,
-                  h->x, h->r, h->p, h->q, h->rho, h->phi, h->zacc, h->rin, h->ux, h->uy, h->fd,
-                  h->bd, h->pd, h->pw, h->part, h->gx, h->gy, h->FH, h->absF, h->diverr, h->tmpd, h->st,
-                  h->d_rtol, h->p2, h->r2, h->zacc2};
+                  h->d_bgeo, h->d_bgofs, h->binv, h->kcoef};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);
   if (h->h_flag) cudaFreeHost(h->h_flag);
-  if (h->h_rtol) cudaFreeHost(h->h_rtol);
-  for (auto& e : h->ev)
-    if (e) cudaEventDestroy(e);
-  for (auto& e : h->prof_ev)
-    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -922,23 +1013,146 @@ int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, do
 
 int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
   if (!h || !f || !ux || !uy) return TG_ERR_INVALID_ARG;
+  Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
   cudaStream_t s = h->stream;
-  TG_CK(cudaMemcpyAsync(h->fd, f, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  if (bflux) TG_CK(cudaMemcpyAsync(h->bd, bflux, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s));
-  else TG_CK(cudaMemsetAsync(h->bd, 0, sizeof(double) * 4 * n, s));
-  *h->h_rtol = 0.5;
-  TG_CK(cudaMemcpyAsync(h->d_rtol, h->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
-  launch_pcg_reset(h->st, h->d_rtol, 1, 0, s);
-  enqueue_preprocess(h, h->fd, h->bd, h->ux, h->uy, s);
-  TG_CK(cudaMemcpyAsync(ux, h->ux, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
-  TG_CK(cudaMemcpyAsync(uy, h->uy, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+  TG_CK(cudaMemcpyAsync(c->fd, f, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if (bflux) TG_CK(cudaMemcpyAsync(c->bd, bflux, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, s));
+  else TG_CK(cudaMemsetAsync(c->bd, 0, sizeof(double) * 4 * n, s));
+  *c->h_rtol = 0.5;
+  TG_CK(cudaMemcpyAsync(c->d_rtol, c->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_pcg_reset(c->st, c->d_rtol, 1, 0, s);
+  enqueue_preprocess(c, c->fd, c->bd, c->ux, c->uy, s);
+  TG_CK(cudaMemcpyAsync(ux, c->ux, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+  TG_CK(cudaMemcpyAsync(uy, c->uy, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
   PcgState head{};
-  TG_CK(cudaMemcpyAsync(&head, h->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaMemcpyAsync(&head, c->st, offsetof(PcgState, alphas), cudaMemcpyDeviceToHost, s));
   TG_CK(cudaStreamSynchronize(s));
   TG_CK(cudaGetLastError());
   if (head.status & kStIncompatible) return TG_ERR_INCOMPATIBLE_SOURCE;
+  return TG_OK;
+}
+
+int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, double eig_tol,
+                   const tg_options* opt, int nrhs, void* stream, tg_batch** out) {
+  if (!out) return TG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (ninst < 1 || nrhs < 1 || !kappa || !grids || !opt || opt->pointer_mode != TG_PTR_DEVICE || opt->profile)
+    return TG_ERR_INVALID_ARG;
+  tg_batch* B = new (std::nothrow) tg_batch();
+  if (!B) return TG_ERR_OOM;
+  B->nrhs = nrhs;
+  B->stream = (cudaStream_t)stream;
+  int rc = TG_OK;
+  for (int i = 0; i < ninst && !rc; ++i) {
+    tg_handle* h = nullptr;
+    rc = tg_setup(kappa[i], &grids[i], eig_tol, opt, stream, &h);
+    if (!rc) B->handles.push_back(h);
+  }
+  // contexts: the handle's own context serves its first right-hand side
+  for (int i = 0; i < ninst && !rc; ++i) {
+    for (int k = 0; k < nrhs && !rc; ++k) {
+      Ctx* c = nullptr;
+      if (k == 0) {
+        c = B->handles[i]->ctx;
+        B->handles[i]->ctx = nullptr;   // now owned by the batch
+        rc = ctx_alloc(B->handles[i], &B->handles[i]->ctx);
+      } else {
+        rc = ctx_alloc(B->handles[i], &c);
+      }
+      if (!rc) B->ctx.push_back(c);
+    }
+  }
+  const int m = ninst * nrhs;
+  if (!rc && (dalloc(&B->d_src, 5 * m) || dalloc(&B->d_buf, 5 * m) || dalloc(&B->d_cnt, 5 * m) ||
+              dalloc(&B->d_rtol, 1) || dalloc(&B->d_ctx_rtol, m) || dalloc(&B->d_ctx_state, m) ||
+              dalloc(&B->d_out, 2 * m)))
+    rc = TG_ERR_OOM;
+  if (!rc) rc = cuda_err(cudaMallocHost(&B->h_src, sizeof(double*) * 5 * m));
+  if (!rc) rc = cuda_err(cudaMallocHost(&B->h_out, sizeof(int) * 2 * m));
+  if (!rc) rc = cuda_err(cudaMallocHost(&B->h_rtol, sizeof(double)));
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  if (!rc) {
+    std::vector<double*> buf(5 * m), rt(m);
+    std::vector<long long> cnt(5 * m);
+    std::vector<PcgState*> stp(m);
+    for (int j = 0; j < m; ++j) {
+      Ctx* c = B->ctx[j];
+      const long long n = c->h->n, nn = n * n, nf = (n + 1) * n;
+      double* bufs[5] = {c->fd, c->bd, c->ux, c->uy, c->pd};
+      const long long cn[5] = {nn, 4 * n, nf, nf, nn};
+      for (int t = 0; t < 5; ++t) {
+        buf[5 * j + t] = bufs[t];
+        cnt[5 * j + t] = cn[t];
+      }
+      rt[j] = c->d_rtol;
+      stp[j] = c->st;
+    }
+    rc = cuda_err(cudaMemcpy(B->d_buf, buf.data(), sizeof(double*) * buf.size(), cudaMemcpyHostToDevice));
+    if (!rc) rc = cuda_err(cudaMemcpy(B->d_cnt, cnt.data(), sizeof(long long) * cnt.size(), cudaMemcpyHostToDevice));
+    if (!rc) rc = cuda_err(cudaMemcpy(B->d_ctx_rtol, rt.data(), sizeof(double*) * m, cudaMemcpyHostToDevice));
+    if (!rc) rc = cuda_err(cudaMemcpy(B->d_ctx_state, stp.data(), sizeof(PcgState*) * m, cudaMemcpyHostToDevice));
+  }
+  if (!rc) {
+    // one graph: the chains of all contexts, independent of each other
+    cudaGraph_t g = nullptr;
+    rc = cuda_err(cudaGraphCreate(&g, 0));
+    for (size_t j = 0; j < B->ctx.size() && !rc; ++j) rc = add_chain(B->ctx[j], g, B->cap);
+    if (!rc) rc = cuda_err(cudaGraphInstantiate(&B->exec, g, 0));
+    if (g) cudaGraphDestroy(g);
+  }
+  if (rc) {
+    batch_free(B);
+    return rc;
+  }
+  *out = B;
+  return TG_OK;
+}
+
+int tg_solve_batch(tg_batch* B, const double* const* f, const double* const* bflux, double rtol,
+                   double* const* ux, double* const* uy, double* const* p, int* iters, int* status) {
+  if (!B || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
+  const int m = (int)B->ctx.size();
+  cudaStream_t s = B->stream;
+  for (int j = 0; j < m; ++j) {
+    if (!f[j] || !ux[j] || !uy[j] || !p[j]) return TG_ERR_INVALID_ARG;
+    B->h_src[5 * j + 0] = const_cast<double*>(f[j]);
+    B->h_src[5 * j + 1] = bflux ? const_cast<double*>(bflux[j]) : nullptr;
+    B->h_src[5 * j + 2] = ux[j];
+    B->h_src[5 * j + 3] = uy[j];
+    B->h_src[5 * j + 4] = p[j];
+  }
+  *B->h_rtol = rtol;
+  TG_CK(cudaMemcpyAsync(B->d_src, B->h_src, sizeof(double*) * 5 * m, cudaMemcpyHostToDevice, s));
+  TG_CK(cudaMemcpyAsync(B->d_rtol, B->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
+  // inputs: caller -> context buffers (f, bflux or zeros), tolerances
+  launch_copy_table((const double* const*)B->d_src, B->d_buf, B->d_cnt, m, 0, 2, 1, s);
+  launch_fill_scalars(B->d_rtol, B->d_ctx_rtol, m, s);
+  TG_CK(cudaGraphLaunch(B->exec, s));
+  // outputs: context buffers -> caller (ux, uy, p), then iterations and status
+  launch_copy_table((const double* const*)B->d_buf, (double* const*)B->d_src, B->d_cnt, m, 2, 5, 0, s);
+  launch_gather_states(B->d_ctx_state, B->d_out, m, s);
+  TG_CK(cudaMemcpyAsync(B->h_out, B->d_out, sizeof(int) * 2 * m, cudaMemcpyDeviceToHost, s));
+  TG_CK(cudaStreamSynchronize(s));
+  TG_CK(cudaGetLastError());
+  int worst = TG_OK;
+  for (int j = 0; j < m; ++j) {
+    if (iters) iters[j] = B->h_out[2 * j];
+    if (status) status[j] = status_to_err(B->h_out[2 * j + 1]);
+    const int e = status_to_err(B->h_out[2 * j + 1]);
+    if (e != TG_OK && (worst == TG_OK || e > worst)) worst = e;   // MAXITER (-4) before harder errors
+  }
+  if (read_and_clear_timeout()) worst = TG_ERR_DEVICE_TIMEOUT;
+  return worst;
+}
+
+void tg_destroy_batch(tg_batch* B) { batch_free(B); }
+
+int tg_batch_size(tg_batch* B, int* ninst, int* nrhs) {
+  if (!B) return TG_ERR_INVALID_ARG;
+  if (ninst) *ninst = (int)B->handles.size();
+  if (nrhs) *nrhs = B->nrhs;
   return TG_OK;
 }
 

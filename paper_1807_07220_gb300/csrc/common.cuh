@@ -88,8 +88,6 @@ struct CoarseSpace {
   double* closed = nullptr;  // nslots*(b+1)^2 FP64 tiles (device)
   void* owned = nullptr;     // nslots*b*b tiles in storage precision (device)
   double* Kinv = nullptr;    // D*D inverse of the Galerkin matrix (device)
-  double* part = nullptr;    // nslots partial restrictions (device)
-  double* coefs = nullptr;   // D coarse solution (device)
   int max_slots_per_block = 0;
 };
 
@@ -155,6 +153,11 @@ extern unsigned long long g_kernel_launches;
 #define TG_COUNT(k) (::tg::g_kernel_launches += (unsigned long long)(k))
 
 void configure_kernels(int max_coarse_dim);
+// batched solves (batch.cu)
+void launch_copy_table(const double* const* src, double* const* dst, const long long* cnt, int m, int t0, int t1,
+                       int zero_if_null, cudaStream_t s);
+void launch_fill_scalars(const double* v, double* const* dst, int m, cudaStream_t s);
+void launch_gather_states(PcgState* const* st, int* out, int m, cudaStream_t s);
 int read_and_clear_timeout();   // 1 if a bounded device wait expired since the last call
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s);
 void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s);
@@ -195,16 +198,18 @@ void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, doubl
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);
 void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s);
 template <typename TC, typename TS>
-void launch_resid_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const double* r, const TC* z,
-                           const TC* kinv, const PcgState* st, cudaStream_t s);
+void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,
+                           const TC* z, const TC* kinv, const PcgState* st, cudaStream_t s);
 constexpr int kRowsPerGroup = 4;   // rows of a patch inverse streamed together by one warp
 
+// per-solve scratch of the coarse step: part (one entry per slot), coefs (D)
 template <typename TC, typename TS>
-void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
+void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s);
-void launch_coarse_solve(const CoarseSpace& cs, const PcgState* st, cudaStream_t s);
+void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
+                         cudaStream_t s);
 template <typename TC, typename TS>
-void launch_prolong(const CoarseSpace& cs, int nblocks, int nc, int b, int n, TC* v,
+void launch_prolong(const CoarseSpace& cs, const double* coefs, int nblocks, int nc, int b, int n, TC* v,
                     const PcgState* st, cudaStream_t s);
 
 template <typename TA, typename TB>

@@ -1139,25 +1139,24 @@ template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, cons
                                       double, int, const PcgState*, cudaStream_t);
 
 template <typename TC, typename TS>
-void launch_resid_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const double* r, const TC* z,
-                           const TC* kinv, const PcgState* st, cudaStream_t s) {
+void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,
+                           const TC* z, const TC* kinv, const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_resid_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, r, z, kinv, cs.part, nc,
+  k_resid_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, r, z, kinv, part, nc,
                                                          b, n, st);
 }
-template void launch_resid_restrict<double, double>(const CoarseSpace&, int, int, int, int, const double*,
+template void launch_resid_restrict<double, double>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                                     const double*, const double*, const PcgState*, cudaStream_t);
-template void launch_resid_restrict<float, float>(const CoarseSpace&, int, int, int, int, const double*,
+template void launch_resid_restrict<float, float>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                                   const float*, const float*, const PcgState*, cudaStream_t);
-template void launch_resid_restrict<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, const double*,
+template void launch_resid_restrict<float, __nv_bfloat16>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                                           const float*, const float*, const PcgState*, cudaStream_t);
 
 template <typename TC, typename TS>
-void launch_restrict(const CoarseSpace& cs, int nblocks, int nc, int b, int n, const TC* v,
+void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, cs.part, nc, b,
-                                                   n, st);
+  k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, part, nc, b, n, st);
 }
 int sm_count();
 template <typename TC, typename TS, typename TR> int smoother_per_sm();
@@ -1204,32 +1203,33 @@ void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, c
   TG_COUNT(1);
   k_set_condition<<<1, 32, 0, s>>>(cond, st);
 }
-void launch_coarse_solve(const CoarseSpace& cs, const PcgState* st, cudaStream_t s) {
+void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
+                         cudaStream_t s) {
   const size_t shm = sizeof(double) * (size_t)cs.D;
   int grid = (cs.D + 7) / 8;
   if (grid > 2 * 152) grid = 2 * 152;
   if (grid < 1) grid = 1;
   TG_COUNT(1);
-  k_coarse_solve<<<grid, kThreads, shm, s>>>(cs.part, cs.gather, cs.Kinv, cs.coefs, cs.D, st);
+  k_coarse_solve<<<grid, kThreads, shm, s>>>(part, cs.gather, cs.Kinv, coefs, cs.D, st);
 }
 template <typename TC, typename TS>
-void launch_prolong(const CoarseSpace& cs, int nblocks, int nc, int b, int n, TC* v, const PcgState* st,
-                    cudaStream_t s) {
+void launch_prolong(const CoarseSpace& cs, const double* coefs, int nblocks, int nc, int b, int n, TC* v,
+                    const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_prolong<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, cs.slots, (const TS*)cs.owned, cs.coefs,
-                                                  v, nc, b, n, st);
+  k_prolong<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, cs.slots, (const TS*)cs.owned, coefs, v, nc, b, n,
+                                                  st);
 }
-template void launch_restrict<double, double>(const CoarseSpace&, int, int, int, int, const double*,
+template void launch_restrict<double, double>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                               const PcgState*, cudaStream_t);
-template void launch_restrict<float, float>(const CoarseSpace&, int, int, int, int, const float*,
+template void launch_restrict<float, float>(const CoarseSpace&, double*, int, int, int, int, const float*,
                                             const PcgState*, cudaStream_t);
-template void launch_restrict<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, const float*,
+template void launch_restrict<float, __nv_bfloat16>(const CoarseSpace&, double*, int, int, int, int, const float*,
                                                     const PcgState*, cudaStream_t);
-template void launch_prolong<double, double>(const CoarseSpace&, int, int, int, int, double*,
+template void launch_prolong<double, double>(const CoarseSpace&, const double*, int, int, int, int, double*,
                                              const PcgState*, cudaStream_t);
-template void launch_prolong<float, float>(const CoarseSpace&, int, int, int, int, float*,
+template void launch_prolong<float, float>(const CoarseSpace&, const double*, int, int, int, int, float*,
                                            const PcgState*, cudaStream_t);
-template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, int, int, int, int, float*,
+template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, const double*, int, int, int, int, float*,
                                                    const PcgState*, cudaStream_t);
 
 void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s) {

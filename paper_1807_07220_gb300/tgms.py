@@ -75,6 +75,12 @@ SIGNATURES = {
     "tg_coarse_info": (c_int, [c_void_p, c_int_p, c_int_p, c_void_p, c_void_p]),
     "tg_preprocess": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "tg_pressure_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "tg_setup_batch": (c_int, [c_int, c_void_p, c_void_p, c_double, ctypes.POINTER(tg_options), c_int, c_void_p,
+                               ctypes.POINTER(c_void_p)]),
+    "tg_solve_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p]),
+    "tg_batch_size": (c_int, [c_void_p, c_int_p, c_int_p]),
+    "tg_destroy_batch": (None, [c_void_p]),
 }
 
 
@@ -182,6 +188,50 @@ def tg_coarse_info(h, b):
 
 def tg_preprocess(h, f, bflux, ux, uy):
     _check(lib().tg_preprocess(h, _ptr(f), _ptr(bflux), _ptr(ux), _ptr(uy)), "tg_preprocess")
+
+
+def _ptr_array(arrs):
+    """C array of data pointers (None entries -> NULL)."""
+    arr = (c_void_p * len(arrs))()
+    for k, a in enumerate(arrs):
+        arr[k] = None if a is None else _ptr(a).value
+    return arr
+
+
+def tg_setup_batch(kappas, ns, bs, eig_tol, nrhs, overlap=2, options=None, stream=0):
+    """kappas: list of device tensors (n_i, n_i); returns an opaque batch handle."""
+    ninst = len(kappas)
+    grids = (tg_grid * ninst)(*[tg_grid(n, n, b, b, overlap) for n, b in zip(ns, bs)])
+    o = options if options is not None else default_options()
+    h = ctypes.c_void_p()
+    _check(lib().tg_setup_batch(ninst, _ptr_array(kappas), grids, float(eig_tol), ctypes.byref(o), int(nrhs),
+                                ctypes.c_void_p(stream), ctypes.byref(h)), "tg_setup_batch")
+    return h
+
+
+def tg_solve_batch(batch, f, bflux, rtol, ux, uy, p, allow_maxiter=False):
+    """Lists of device tensors (instance-major, nrhs per instance); bflux may be None.
+    Returns (iterations, status codes) per problem."""
+    import numpy as np
+    m = len(f)
+    iters = np.zeros(m, dtype=np.int32)
+    status = np.zeros(m, dtype=np.int32)
+    rc = lib().tg_solve_batch(batch, _ptr_array(f), None if bflux is None else _ptr_array(bflux), float(rtol),
+                              _ptr_array(ux), _ptr_array(uy), _ptr_array(p), _ptr(iters), _ptr(status))
+    if not (allow_maxiter and rc == -4):
+        _check(rc, "tg_solve_batch")
+    return iters, status
+
+
+def tg_destroy_batch(batch):
+    if batch is not None:
+        lib().tg_destroy_batch(batch)
+
+
+def tg_batch_size(batch):
+    ni, nr = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().tg_batch_size(batch, ctypes.byref(ni), ctypes.byref(nr)), "tg_batch_size")
+    return ni.value, nr.value
 
 
 def tg_pressure_noalloc(kappa, ux, uy, p, n, stream=0):

@@ -1,0 +1,72 @@
+"""Batched solves (one CUDA graph for many instances and right-hand sides)
+against the oracle's direct solves and against single solves (GPU)."""
+
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.fine import Grid, solve_direct  # noqa: E402
+from paper_1807_07220_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def tg():
+    from paper_1807_07220_gb300 import build, tgms
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(tgms.LIB_PATH):
+        build.build_library()
+    tgms.lib()
+    return tgms
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16"])
+def test_batch_matches_direct_and_single_solves(tg, prec):
+    specs = [(32, 8, 1e4, 1), (24, 4, 1e6, 2), (48, 16, 1e5, 3)]
+    nrhs = 2
+    dev = "cuda"
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device=dev).contiguous() for k in kappas]
+    opts = tg.default_options(precision=prec, flexible=int(prec != "f64"))
+    stream = torch.cuda.current_stream().cuda_stream
+    batch = tg.tg_setup_batch(kd, [s[0] for s in specs], [s[1] for s in specs], 10.0, nrhs, options=opts,
+                              stream=stream)
+    try:
+        assert tg.tg_batch_size(batch) == (len(specs), nrhs)
+        fs, outs = [], []
+        for (n, b, c, seed), k in zip(specs, kappas):
+            for r in range(nrhs):
+                f = inputs.random_pairs(n, 2, 100 * seed + r)
+                fs.append(f)
+                outs.append((torch.zeros(n, n + 1, dtype=torch.float64, device=dev),
+                             torch.zeros(n + 1, n, dtype=torch.float64, device=dev),
+                             torch.zeros(n, n, dtype=torch.float64, device=dev)))
+        fd = [torch.as_tensor(f, dtype=torch.float64, device=dev).contiguous() for f in fs]
+        for rep in range(2):   # the batch graph is replayed
+            iters, status = tg.tg_solve_batch(batch, fd, None, 1e-12, [o[0] for o in outs], [o[1] for o in outs],
+                                              [o[2] for o in outs])
+            assert (status == 0).all() and (iters > 0).all()
+        j = 0
+        for (n, b, c, seed), k in zip(specs, kappas):
+            s = tg.Solver(k, b, 10.0, precision=prec, flexible=int(prec != "f64"))
+            try:
+                for r in range(nrhs):
+                    u_ref, p_ref = solve_direct(Grid(n, b), k, fs[j])
+                    got_u = np.concatenate([outs[j][0].cpu().numpy().ravel(), outs[j][1].cpu().numpy().ravel()])
+                    got_p = outs[j][2].cpu().numpy().ravel()
+                    assert rel(got_u, u_ref) < 1e-8 and rel(got_p, p_ref) < 1e-8
+                    it1, _ = s.solve(fs[j], rtol=1e-12)
+                    assert abs(it1 - iters[j]) <= 1
+                    j += 1
+            finally:
+                s.close()
+    finally:
+        tg.tg_destroy_batch(batch)
