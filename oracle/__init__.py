@@ -18,6 +18,10 @@ written with numpy/scipy sparse matrices in the paper's own saddle-point form:
                      by the package's own cyclic Jacobi eigensolver, basis
                      selection; plus the MsFEM (eq. msfem) and RT0 comparator
                      coarse spaces.
+* ``learned``     -- the learned coarse basis: face input map, labels from
+                     the spectral problems of Section 4.2, the subspace loss,
+                     a perceptron with its backward pass and Adam, and the
+                     Rayleigh-Ritz selection on predicted flux profiles.
 * ``twogrid``     -- Section 5: smoother (eq. smooth), coarse correction
                      (eq. coarsepre), multiplicative two-grid cycle, PCG with
                      the stopping rule of Section 6 and a Lanczos estimate of

@@ -196,12 +196,16 @@ def rt0_interpolation(g, face):
     return np.concatenate(rows), np.concatenate(vals)
 
 
-def build_coarse_space(g, A, B, kappa, kind="gmsfem", tol=10.0, cap=None, blocks=None):
+def build_coarse_space(g, A, B, kappa, kind="gmsfem", tol=10.0, cap=None, blocks=None, profiles=None):
     """Coarse velocity space as a sparse matrix Phi (interior faces x dim).
 
     kind = 'gmsfem': V_ms of Section 4.2 (spectral selection with tolerance
                      tol); 'msfem': one MsFEM basis function per face
-                     (eq. msfem); 'rt0': coarse RT0 interpolation.
+                     (eq. msfem); 'rt0': coarse RT0 interpolation;
+           'learned': the spectral problem restricted to the span of
+                     predicted flux profiles (``profiles``: faces x b x k,
+                     see oracle.learned.ritz_select), with the exact problem
+                     where the selection falls back.
     Returns (Phi, info) where info holds, per coarse face, the spectrum and
     the number of selected functions."""
     I_f = g.interior_faces()
@@ -211,8 +215,8 @@ def build_coarse_space(g, A, B, kappa, kind="gmsfem", tol=10.0, cap=None, blocks
     blocks = blocks or BlockSolvers(g, A, B)
     cols_r, cols_v, col = [], [], 0
     rows_c = []
-    info = {"faces": coarse_faces(g), "lam": [], "nsel": [], "coef": []}
-    for face in info["faces"]:
+    info = {"faces": coarse_faces(g), "lam": [], "nsel": [], "coef": [], "fallback": []}
+    for fidx, face in enumerate(info["faces"]):
         if kind == "rt0":
             sup, v = rt0_interpolation(g, face)
             keep = pos[sup] >= 0
@@ -226,6 +230,16 @@ def build_coarse_space(g, A, B, kappa, kind="gmsfem", tol=10.0, cap=None, blocks
         if kind == "msfem":
             cset = np.ones((g.b, 1))
             info["nsel"].append(1)
+        elif kind == "learned":
+            from .learned import ritz_select
+            a, s = spectral_problem(g, A, B, kinv, face, sup, val)
+            lam, cset, fb = ritz_select(np.asarray(profiles[fidx], float), a, s, tol)
+            if fb:
+                lam, cset = solve_spectral(a, s, tol, cap)
+            info["fallback"].append(fb)
+            info["lam"].append(lam)
+            info["nsel"].append(cset.shape[1])
+            info["coef"].append(cset)
         else:
             a, s = spectral_problem(g, A, B, kinv, face, sup, val)
             lam, cset = solve_spectral(a, s, tol, cap)

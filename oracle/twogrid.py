@@ -49,7 +49,7 @@ class TwoGridSolver:
     'msfem') instead of 'gmsfem'."""
 
     def __init__(self, n, b, kappa, tol=10.0, eta=0.2, overlap=2, m1=1, m2=1,
-                 coarse="gmsfem", cap=None):
+                 coarse="gmsfem", cap=None, profiles=None):
         from .fine import Grid
         self.g = g = Grid(n, b, overlap)
         self.kappa = np.asarray(kappa, float).reshape(n, n)
@@ -71,7 +71,7 @@ class TwoGridSolver:
                                 shape=(n * n, g.nc ** 2))
         # Step 2: coarse space and coarse matrix L_H (eq. coarsepre)
         self.Phi, self.info = build_coarse_space(g, self.A, self.B, self.kappa, coarse, tol, cap,
-                                                 self.blocks)
+                                                 self.blocks, profiles)
         self.coarse_solver = self._galerkin(self.Phi)
         # oversampled local matrices L_i^+ (eq. smooth)
         self.patches = []

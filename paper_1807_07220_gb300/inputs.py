@@ -91,3 +91,24 @@ def lognormal_field(n, seed, sigma=1.0):
     """Cell-wise independent log-normal permeability (for small parity cases)."""
     rng = np.random.default_rng(seed)
     return np.exp(sigma * rng.standard_normal((n, n)))
+
+
+def mlp_init_params(din, dout, hidden, seed):
+    """Initial weights of the three-layer perceptron as one flat float32
+    vector in the layout W1 (hidden x din), b1, W2 (hidden x hidden), b2,
+    W3 (dout x hidden), b3: He-normal weights (std sqrt(2 / fan_in)), zero
+    biases, the output layer scaled by 1/2."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.standard_normal(hidden * din) * np.sqrt(2.0 / din), np.zeros(hidden),
+             rng.standard_normal(hidden * hidden) * np.sqrt(2.0 / hidden), np.zeros(hidden),
+             0.5 * rng.standard_normal(dout * hidden) * np.sqrt(2.0 / hidden), np.zeros(dout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def sample_order(nsamples, nsteps, batch, seed):
+    """Row indices of the training batches: consecutive random permutations of
+    range(nsamples), cut into nsteps batches of ``batch`` (int32)."""
+    rng = np.random.default_rng(seed)
+    need = nsteps * batch
+    reps = -(-need // max(nsamples, 1))
+    return np.concatenate([rng.permutation(nsamples) for _ in range(reps)])[:need].astype(np.int32)
