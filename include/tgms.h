@@ -40,6 +40,8 @@
 #ifndef TGMS_H
 #define TGMS_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -68,8 +70,11 @@ extern "C" {
 #define TG_COARSE_GMSFEM 0   /* adaptive spectral space, Section 4.2 */
 #define TG_COARSE_MSFEM  1   /* one MsFEM function per coarse face, eq. msfem */
 #define TG_COARSE_RT0    2   /* coarse RT0 space */
+#define TG_COARSE_LEARNED 3  /* spectral problem of Section 4.2 restricted to predicted
+                                flux profiles (see "learned coarse basis" below) */
 
 typedef struct tg_handle tg_handle;
+typedef struct tg_mlp tg_mlp;
 
 typedef struct tg_grid {
   int nx, ny;     /* fine cells per side; this release requires nx == ny */
@@ -89,6 +94,17 @@ typedef struct tg_options {
   int profile;       /* 0: tg_solve runs one instantiated CUDA graph (PCG loop in a
                         device-side while node); 1: host-driven loop with CUDA
                         events around every smoother launch (timings in tg_report) */
+  /* TG_COARSE_LEARNED only: the k predicted whitened flux profiles per coarse
+   * face (see "learned coarse basis" below) come from face_profiles (device,
+   * FP32, nfaces x learned_k x b, profile j of face f at f*learned_k*b + j*b
+   * + l, l the fine face along E_i) when it is not
+   * NULL, else from the network `net` (k = its k).  learned_max_iter > 0:
+   * tg_solve rebuilds the coarse space with the exact spectral problems and
+   * solves again when the learned space needed more PCG iterations. */
+  const tg_mlp* net;
+  const float* face_profiles;
+  int learned_k;
+  int learned_max_iter;
 } tg_options;
 
 typedef struct tg_report {
@@ -107,10 +123,14 @@ typedef struct tg_report {
   int smoother_launches;  /* profile == 1: smoother launches timed ... */
   double smoother_ms;     /* ... and their summed device time */
   int graph;              /* 1 if the call ran as one CUDA graph */
+  int snapshot_solves;    /* local block solves of the coarse-space setup (Section 4.1) */
+  int fallback_faces;     /* TG_COARSE_LEARNED: faces that took the exact spectral problem */
+  int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
- * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0. */
+ * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0, no
+ * network or profiles, learned_k 4, learned_max_iter 0. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything
@@ -209,6 +229,77 @@ int tg_batch_size(tg_batch* batch, int* ninst, int* nrhs);
 
 /* Frees the batch and its handles.  NULL is allowed. */
 void tg_destroy_batch(tg_batch* batch);
+
+/* ---- learned coarse basis -------------------------------------------------
+ * The paper selects the coarse functions of each coarse face E_i by a local
+ * spectral problem over its snapshot space (Section 4.2, eqs. spectral_1,
+ * spectral_eqn; snapshots of eq. snapshot_eqn, one per fine face e_l of E_i
+ * with normal component delta_l).  A coefficient vector over the snapshots is
+ * therefore the normal-velocity profile g of the function on e_0..e_{b-1}
+ * (its "flux profile", l running along +y on a vertical edge, +x on a
+ * horizontal one, normal +x / +y).  Predictions are made in whitened
+ * coordinates y_l = a_l^{1/2} g_l, a_l the mean of the two adjacent cells'
+ * 1/kappa (the diagonal of the a-form), in which the spectral problem is
+ * symmetric.  A network maps log kappa around E_i to k such profiles; the
+ * setup extends each to omega_i with one local solve per block (instead of
+ * b), solves the spectral problem on their span (Rayleigh-Ritz), keeps the
+ * Ritz pairs with lambda < eig_tol (at least one) and falls back to the exact
+ * problem of the face when its smallest Ritz value is >= eig_tol, when no
+ * predicted direction is kept, or when the kept functions carry no net flux.
+ *
+ * Network input of face E_i: log10(kappa)/3 rounded to bfloat16 on the
+ * (b + 2) x (2b + 2) cells of omega_i plus a one-cell halo (cells outside the
+ * domain take the nearest cell's value), rows along E_i, columns across it
+ * (K^1 first); a horizontal edge is transposed onto that layout.
+ * Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, weights and hidden
+ * activations bfloat16, accumulation FP32; output entry j*b + l is profile j
+ * at fine face l.  Parameters are one FP32 vector, layout W1 (hidden x din,
+ * row-major), b1, W2 (hidden x hidden), b2, W3 (dout x hidden), b3 with
+ * din = (b + 2)(2b + 2), dout = k b.
+ * Training loss per face: ||G G^T - Q Q^T||_F^2, G the b x k predicted
+ * whitened profiles as columns, Q the label (orthonormal basis of the span of
+ * the whitened profiles of the k eigenfunctions with the smallest
+ * eigenvalues), mean over the batch;
+ * Adam (beta 0.9, 0.999, eps 1e-8).  bfloat16 arrays are passed as uint16_t.
+ * All array pointers are device pointers. */
+
+/* Sizes of the network for block size b (2..16), k profiles (1..8) and
+ * hidden width (1..4096): din, dout, number of FP32 parameters. */
+int tg_mlp_shape(int b, int k, int hidden, int* din, int* dout, long long* nparam);
+
+/* Creates a network with parameters `params` (device, FP32, nparam) and Adam
+ * state zero; work runs on `stream`. */
+int tg_mlp_create(int b, int k, int hidden, const float* params, void* stream, tg_mlp** out);
+
+/* Copies the FP32 parameters out (device, nparam). */
+int tg_mlp_params(const tg_mlp* net, float* params);
+
+/* y (batch x dout, FP32) = network(x (batch x din, bfloat16)). */
+int tg_mlp_forward(tg_mlp* net, int batch, const uint16_t* x, float* y);
+
+/* Loss and gradient of one batch, parameters unchanged: x (batch x din,
+ * bfloat16), q (batch x k x b, FP32 labels, vectors as rows); *loss (host)
+ * the mean loss; grad (device, nparam FP32, parameter layout) may be NULL.
+ * batch <= 4096. */
+int tg_mlp_loss_grad(tg_mlp* net, int batch, const uint16_t* x, const float* q, double* loss, float* grad);
+
+/* nsteps Adam steps with learning rate lr; step s uses the samples
+ * order[s*batch .. s*batch+batch-1] (device int32 indices into the
+ * nsamples rows of x and q).  loss_hist (device, nsteps FP32) may be NULL.
+ * batch <= 4096. */
+int tg_mlp_train(tg_mlp* net, int nsamples, const uint16_t* x, const float* q, const int* order, int nsteps,
+                 int batch, float lr, float* loss_hist);
+
+/* Frees the network.  NULL is allowed. */
+void tg_mlp_destroy(tg_mlp* net);
+
+/* Training data of one field: for every coarse face (order of tg_coarse_info)
+ * the network input x (nfaces x din, bfloat16) and the label q (nfaces x k x
+ * b, FP32) from the exact spectral problems of Section 4.2 with tolerance
+ * eig_tol; nsel (nfaces, the exact selection counts) and lambda (nfaces x b)
+ * may be NULL.  kappa (device, n*n), grid as in tg_setup. */
+int tg_face_data(const double* kappa, const tg_grid* grid, double eig_tol, int k, void* stream,
+                 uint16_t* x, float* q, int* nsel, double* lambda);
 
 /* ---- allocation-free entry point --------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot

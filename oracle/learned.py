@@ -9,7 +9,7 @@ face E_i (Section 4.2, eqs. spectral_1 / spectral_eqn) posed on the snapshot
 space of eq. snapshot_eqn.  The snapshot v_l^i has normal component delta_l on
 the fine faces e_l of E_i, so a coefficient vector over the snapshots is the
 normal-velocity profile of the function on those b fine faces: the "flux
-profile".  The learned variant predicts, from log kappa on omega_i, k flux
+profile".  The learned variant predicts, from log kappa on omega_i, k
 profiles whose span should contain the eigenfunctions the spectral problem
 selects; the profiles are extended to omega_i by the same local solves that
 define the snapshots (linearity: one solve per profile), and the spectral
@@ -24,8 +24,20 @@ Readings (the paper has no learned part; these fix the interface):
     edge is transposed onto the vertical layout; the flux profile keeps its
     coordinates under the transposition (pinned: the spectral problem of the
     transposed field on the transposed face is the same).
-  * label: an orthonormal basis (Euclidean, flux-profile coordinates) of the
-    span of the first min(nsel, k) selected eigenfunctions, zero-padded to k.
+  * coordinates: predictions and labels are "whitened profiles"
+    y_l = a_l^{1/2} g_l, g the flux profile and a_l = kappa_e^{-1} the
+    diagonal of the a-form on fine face l.  In y the spectral problem is the
+    symmetric eigenproblem of D_a^{-1/2} s D_a^{-1/2} (mu = 1/lambda), so a
+    subspace at angle theta from its top eigenvectors gives Ritz values within
+    O(theta^2); in plain flux coordinates the weights a_l span the contrast
+    (1e-6 .. 1e2) and a small Euclidean error on a high-a face ruins the
+    Rayleigh quotient.  a is known from kappa, so g = a^{-1/2} y at inference.
+  * label: an orthonormal basis (Euclidean, y coordinates) of the span of the
+    k eigenfunctions with the smallest eigenvalues (all b when b < k,
+    zero-padded).  The span of the lowest modes varies smoothly with kappa,
+    unlike the tolerance-selected subset, and it contains every selected
+    function when nsel <= k; the tolerance acts at inference, on the Ritz
+    values.
   * loss: ||G G^T - Q Q^T||_F^2 per face (G: b x k predicted profiles as
     columns, Q: label), averaged over the batch.  It depends on G only through
     G G^T, so it is invariant under G -> G R for orthogonal R (signs, order,
@@ -36,7 +48,9 @@ Readings (the paper has no learned part; these fix the interface):
   * selection: directions of span(G) with G^T G eigenvalue above 1/4 (the
     target eigenvalues are 1 and 0), orthonormalised; Ritz pairs of
     a c = lambda s c on that span; keep lambda < tol (at least one); fall
-    back to the exact problem when the smallest Ritz value is >= tol.
+    back to the exact problem when the smallest Ritz value is >= tol, when
+    no direction is kept, or when the kept functions carry no net flux
+    through E_i (mean profile ~ 0: no unit-flux function can be formed).
 """
 
 import numpy as np
@@ -68,14 +82,15 @@ def face_input(kappa, g, face):
     return out.ravel()
 
 
-def face_label(cset, k):
-    """Orthonormal basis (b x k, zero-padded) of the span of the first
-    min(nsel, k) selected coefficient vectors (columns of cset)."""
+def face_label(cset, a, k):
+    """Orthonormal basis (b x k, zero-padded, y coordinates) of the span of
+    the first min(columns, k) coefficient vectors (columns of cset, by
+    ascending eigenvalue); a: the a-form diagonal of the face."""
     b, m = cset.shape
     m = min(m, k)
     Q = np.zeros((b, k))
     if m:
-        q, _ = np.linalg.qr(cset[:, :m])
+        q, _ = np.linalg.qr(np.sqrt(np.asarray(a))[:, None] * cset[:, :m])
         Q[:, :m] = q
     return Q
 
@@ -180,14 +195,16 @@ def adam_step(flat, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # ----------------------------------------------------------------- selection
 def ritz_select(G, a, s, tol, thr=0.25):
     """Rayleigh-Ritz form of eq. spectral_eqn on the span of the predicted
-    profiles G (b x k).  a: the diagonal of the a-form in snapshot
-    coordinates; s: the s-form (b x b).  Returns (Ritz values ascending,
-    selected coefficient vectors b x m, fallback flag)."""
+    whitened profiles G (b x k, y coordinates).  a: the diagonal of the a-form
+    in snapshot coordinates; s: the s-form (b x b).  Returns (Ritz values
+    ascending, selected coefficient vectors b x m in snapshot coordinates,
+    fallback flag)."""
     w, V = jacobi_eigh(G.T @ G)
     keep = w > thr
     if not keep.any():
         return np.array([]), None, True
-    U = G @ (V[:, keep] / np.sqrt(w[keep]))           # orthonormal columns
+    Uy = G @ (V[:, keep] / np.sqrt(w[keep]))          # orthonormal columns (y)
+    U = Uy / np.sqrt(np.asarray(a))[:, None]          # flux profiles g = a^{-1/2} y
     ak = U.T @ (np.asarray(a)[:, None] * U)
     sk = U.T @ s @ U
     L = np.linalg.cholesky(0.5 * (ak + ak.T))
@@ -197,7 +214,13 @@ def ritz_select(G, a, s, tol, thr=0.25):
     Y = Y[:, ::-1]
     nsel = max(1, int(np.sum(lam < tol)))
     c = sla.solve_triangular(L.T, Y[:, :nsel], lower=False)
-    return lam, U @ c, bool(lam[0] >= tol)
+    cset = U @ c
+    if lam[0] >= tol:
+        return lam, cset, True
+    # the kept functions must carry net flux through E_i (the coarse space
+    # needs one unit-flux function per face); otherwise fall back
+    t = cset.mean(axis=0)
+    return lam, cset, bool(np.linalg.norm(t) <= 1e-6 * np.abs(cset).max())
 
 
 def exact_profiles(g, kappa, tol, k, cap=None):
@@ -214,8 +237,9 @@ def exact_profiles(g, kappa, tol, k, cap=None):
         sup, val = snapshots(g, A, B, blocks, face)
         a, s = spectral_problem(g, A, B, kinv, face, sup, val)
         lam, cset = solve_spectral(a, s, tol, cap)
+        _, low = solve_spectral(a, s, np.inf, k)       # the k lowest eigenfunctions
         X.append(face_input(kap, g, face))
-        Q.append(face_label(cset, k).T)
+        Q.append(face_label(low, a, k).T)
         nsel.append(cset.shape[1])
         lams.append(lam)
     return np.array(X), np.array(Q), np.array(nsel), np.array(lams)

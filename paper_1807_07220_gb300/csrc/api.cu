@@ -55,6 +55,8 @@ struct tg_handle {
   std::vector<int> nsel;
   std::vector<double> lam_h;
   int velocity_basis = 0;
+  int snapshot_solves = 0;   // local block solves of the coarse-space setup
+  int fallback_faces = 0;    // learned space: faces that took the exact problem
   // coarse spaces: preconditioner and coarse RT0 (preprocessing)
   CoarseSpace cs, rt;
   int* h_flag = nullptr;    // pinned
@@ -201,15 +203,15 @@ int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool
 
 // tiles, Galerkin matrix and its inverse
 int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double* fcoef, const double* zcoef,
-                 bool rt_only) {
+                 const int* jeff, bool rt_only) {
   const int b = h->b, n = h->n;
   if (c.nslots > 0) {
     if (rt_only || h->opt.precision == TG_PREC_F64)
-      launch_build_tiles<double>(c, psiS, fcoef, zcoef, rt_only ? 1 : 0, n, b, h->stream);
+      launch_build_tiles<double>(c, psiS, fcoef, zcoef, jeff, rt_only ? 1 : 0, n, b, h->stream);
     else if (h->opt.precision == TG_PREC_F32)
-      launch_build_tiles<float>(c, psiS, fcoef, zcoef, 0, n, b, h->stream);
+      launch_build_tiles<float>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
     else
-      launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, 0, n, b, h->stream);
+      launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
   }
   if (c.D == 0) return cuda_err(cudaGetLastError());
   // pair energy offsets
@@ -559,31 +561,26 @@ int run_loop(Ctx* c, unsigned long long* launches) {
   }
 }
 
-int setup_impl(tg_handle* h, const double* kappa) {
-  const int n = h->n, b = h->b, nc = h->nc;
-  const long long nn = (long long)n * n;
+// kappa and the quantities derived from it cell by cell
+int setup_kappa(tg_handle* h, const double* kd) {
+  const long long nn = (long long)h->n * h->n;
   cudaStream_t s = h->stream;
   TG_CK(cudaMallocHost(&h->h_flag, sizeof(int)));
   TG_CK(cudaMalloc(&h->d_status, sizeof(int)));
   TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
-  if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn)) return TG_ERR_OOM;
-  const double* kd = kappa;
-  double* kcopy = nullptr;
-  if (h->opt.pointer_mode == TG_PTR_HOST) {
-    if (dalloc(&kcopy, nn)) return TG_ERR_OOM;
-    TG_CK(cudaMemcpyAsync(kcopy, kappa, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
-    kd = kcopy;
-  }
-  launch_kinv(kd, h->kinv, h->kinv32, h->d_status, n, s);
-  if (dalloc(&h->kcoef, 5 * nn)) return TG_ERR_OOM;
-  launch_stencil_coefs(h->kinv, h->kcoef, n, s);
+  if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn) || dalloc(&h->kcoef, 5 * nn)) return TG_ERR_OOM;
+  launch_kinv(kd, h->kinv, h->kinv32, h->d_status, h->n, s);
+  launch_stencil_coefs(h->kinv, h->kcoef, h->n, s);
   int st = 0;
   int rc = read_status(h, &st);
-  cudaFree(kcopy);
   if (rc) return rc;
-  if (st) return status_to_err(st);
+  return st ? status_to_err(st) : TG_OK;
+}
 
-  // ---- oversampled patches: local operators, band Cholesky, inverses ----
+// oversampled patches K_i^+: local operators, band Cholesky, dense inverses
+int setup_patches(tg_handle* h) {
+  const int n = h->n, b = h->b, nc = h->nc;
+  cudaStream_t s = h->stream;
   std::vector<int4> prect(h->npatch);
   std::vector<PatchGeo> geo(h->npatch);
   long long off = 0;
@@ -612,43 +609,59 @@ int setup_impl(tg_handle* h, const double* kappa) {
   int4* d_prect = nullptr;
   double *band = nullptr, *scratch = nullptr;
   if (dalloc(&h->d_pgeo, geo.size()) || dalloc(&d_prect, prect.size()) ||
-      dalloc(&band, (size_t)h->npatch * nmax * (wmax + 1)))
+      dalloc(&band, (size_t)h->npatch * nmax * (wmax + 1))) {
+    cudaFree(d_prect);
+    cudaFree(band);
     return TG_ERR_OOM;
-  TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
-  TG_CK(cudaMemcpyAsync(h->d_pgeo, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, s));
-  TG_CK(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
-  launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
-  launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
-  const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
-  if (dalloc(&scratch, (size_t)batch * nmax * nmax)) return TG_ERR_OOM;
-  for (int first = 0; first < h->npatch; first += batch) {
-    const int cnt = std::min(batch, h->npatch - first);
-    launch_band_inverse(band, d_prect, first, cnt, wmax, nmax, scratch, s);
-    if (h->opt.precision == TG_PREC_F64)
-      launch_store_inverse<double>(scratch, h->d_pgeo, first, cnt, nmax, (double*)h->pinv, s);
-    else if (h->opt.precision == TG_PREC_F32)
-      launch_store_inverse<float>(scratch, h->d_pgeo, first, cnt, nmax, (float*)h->pinv, s);
-    else
-      launch_store_inverse<__nv_bfloat16>(scratch, h->d_pgeo, first, cnt, nmax, (__nv_bfloat16*)h->pinv, s);
   }
-  rc = cuda_err(cudaStreamSynchronize(s));
+  int rc = cuda_err(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_pgeo, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
+  const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
+  if (!rc) rc = dalloc(&scratch, (size_t)batch * nmax * nmax);
+  if (!rc) {
+    launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
+    launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
+    for (int first = 0; first < h->npatch; first += batch) {
+      const int cnt = std::min(batch, h->npatch - first);
+      launch_band_inverse(band, d_prect, first, cnt, wmax, nmax, scratch, s);
+      if (h->opt.precision == TG_PREC_F64)
+        launch_store_inverse<double>(scratch, h->d_pgeo, first, cnt, nmax, (double*)h->pinv, s);
+      else if (h->opt.precision == TG_PREC_F32)
+        launch_store_inverse<float>(scratch, h->d_pgeo, first, cnt, nmax, (float*)h->pinv, s);
+      else
+        launch_store_inverse<__nv_bfloat16>(scratch, h->d_pgeo, first, cnt, nmax, (__nv_bfloat16*)h->pinv, s);
+    }
+    rc = cuda_err(cudaStreamSynchronize(s));
+  }
   cudaFree(scratch);
   cudaFree(band);
   cudaFree(d_prect);
   if (rc) return rc;
-  TG_CK(cudaGetLastError());
+  return cuda_err(cudaGetLastError());
+}
 
-  // ---- coarse blocks: local operators and band Cholesky factors ----
-  {
-    std::vector<int4> brect(h->nblocks);
-    for (int J = 0; J < nc; ++J)
-      for (int I = 0; I < nc; ++I) brect[J * nc + I] = make_int4(I * b, J * b, b - 1, b - 1);
-    int4* d_brect = nullptr;
-    const int bw = b, bn = (b - 1) * (b - 1);
-    if (dalloc(&d_brect, brect.size()) || dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1)))
-      return TG_ERR_OOM;
-    TG_CK(cudaMemcpyAsync(d_brect, brect.data(), sizeof(int4) * brect.size(), cudaMemcpyHostToDevice, s));
-    // dense inverses of the block operators (preprocessing), smoother layout
+// coarse blocks: band Cholesky factors of the local operators (snapshots) and,
+// with inverses, their dense inverses (preprocessing)
+int setup_blocks(tg_handle* h, bool inverses) {
+  const int b = h->b, nc = h->nc, n = h->n;
+  cudaStream_t s = h->stream;
+  std::vector<int4> brect(h->nblocks);
+  for (int J = 0; J < nc; ++J)
+    for (int I = 0; I < nc; ++I) brect[J * nc + I] = make_int4(I * b, J * b, b - 1, b - 1);
+  int4* d_brect = nullptr;
+  const int bw = b, bn = (b - 1) * (b - 1);
+  if (dalloc(&d_brect, brect.size()) || dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1))) {
+    cudaFree(d_brect);
+    return TG_ERR_OOM;
+  }
+  int rc = cuda_err(cudaMemcpyAsync(d_brect, brect.data(), sizeof(int4) * brect.size(), cudaMemcpyHostToDevice, s));
+  if (!rc && bn > 0) {
+    launch_assemble_band(h->kinv, d_brect, h->blk_band, h->nblocks, bw, bn, n, s);
+    launch_band_cholesky(h->blk_band, d_brect, h->nblocks, bw, bn, h->d_status, s);
+  }
+  if (!rc && inverses) {
+    // dense inverses of the block operators, smoother layout
     std::vector<PatchGeo> bgeo(h->nblocks);
     std::vector<int> bgofs(h->nblocks + 1, 0);
     long long boff = 0;
@@ -663,70 +676,262 @@ int setup_impl(tg_handle* h, const double* kappa) {
       bgofs[k + 1] = bgofs[k] + (bn + kRowsPerGroup - 1) / kRowsPerGroup;
     }
     h->bgroups = bgofs[h->nblocks];
-    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) || dalloc(&h->binv, (size_t)boff))
-      return TG_ERR_OOM;
-    TG_CK(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
-    TG_CK(cudaMemcpyAsync(h->d_bgofs, bgofs.data(), sizeof(int) * bgofs.size(), cudaMemcpyHostToDevice, s));
     double* bscratch = nullptr;
     const int bbatch = std::max(1, std::min(h->nblocks, (int)((256LL << 20) / (8LL * std::max(bn, 1) * std::max(bn, 1)))));
-    if (dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1))) return TG_ERR_OOM;
-    if (bn > 0) {
-      launch_assemble_band(h->kinv, d_brect, h->blk_band, h->nblocks, bw, bn, n, s);
-      launch_band_cholesky(h->blk_band, d_brect, h->nblocks, bw, bn, h->d_status, s);
+    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) || dalloc(&h->binv, (size_t)boff) ||
+        dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1)))
+      rc = TG_ERR_OOM;
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgofs, bgofs.data(), sizeof(int) * bgofs.size(), cudaMemcpyHostToDevice, s));
+    if (!rc && bn > 0) {
       for (int first = 0; first < h->nblocks; first += bbatch) {
         const int cnt = std::min(bbatch, h->nblocks - first);
         launch_band_inverse(h->blk_band, d_brect, first, cnt, bw, bn, bscratch, s);
         launch_store_inverse<double>(bscratch, h->d_bgeo, first, cnt, bn, h->binv, s);
       }
     }
-    rc = cuda_err(cudaStreamSynchronize(s));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
     cudaFree(bscratch);
-    cudaFree(d_brect);
-    if (rc) return rc;
   }
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  cudaFree(d_brect);
+  return rc;
+}
+
+// buffers of the per-face spectral problems (Section 4)
+struct SpectralBufs {
+  double *psiS = nullptr, *gram = nullptr, *fcoef = nullptr, *zcoef = nullptr;
+  int *d_nsel = nullptr, *d_jeff = nullptr;
+};
+
+void free_spectral(SpectralBufs& sb) {
+  cudaFree(sb.psiS);
+  cudaFree(sb.gram);
+  cudaFree(sb.fcoef);
+  cudaFree(sb.zcoef);
+  cudaFree(sb.d_nsel);
+  cudaFree(sb.d_jeff);
+  sb = SpectralBufs{};
+}
+
+int alloc_spectral(tg_handle* h, SpectralBufs& sb) {
+  const int b = h->b, F = h->nfaces;
+  if (!h->lam && dalloc(&h->lam, (size_t)F * b)) return TG_ERR_OOM;
+  if (dalloc(&sb.psiS, (size_t)h->nblocks * 4 * b * (b + 1) * (b + 1)) ||
+      dalloc(&sb.gram, (size_t)h->nblocks * 4 * b * b) || dalloc(&sb.d_nsel, F) || dalloc(&sb.d_jeff, F) ||
+      dalloc(&sb.fcoef, (size_t)F * b) || dalloc(&sb.zcoef, (size_t)F * (b - 1) * b))
+    return TG_ERR_OOM;
+  TG_CK(cudaMemsetAsync(sb.zcoef, 0, sizeof(double) * (size_t)F * (b - 1) * b, h->stream));
+  TG_CK(cudaMemsetAsync(sb.fcoef, 0, sizeof(double) * (size_t)F * b, h->stream));
+  return TG_OK;
+}
+
+SpectralArgs spectral_args(tg_handle* h, SpectralBufs& sb) {
+  SpectralArgs A;
+  A.kinv = h->kinv;
+  A.gram = sb.gram;
+  A.eig_tol = h->eig_tol;
+  A.max_basis = h->opt.max_basis;
+  A.mode = (h->opt.coarse_space == TG_COARSE_MSFEM) ? 1 : 0;
+  A.n = h->n;
+  A.b = h->b;
+  A.lam = h->lam;
+  A.nsel = sb.d_nsel;
+  A.fcoef = sb.fcoef;
+  A.zcoef = sb.zcoef;
+  A.status = h->d_status;
+  A.jeff = sb.d_jeff;
+  return A;
+}
+
+// exact snapshot spaces and spectral problems (all faces, or the masked ones)
+void spectral_exact(tg_handle* h, SpectralBufs& sb, const unsigned char* smask, const unsigned char* fmask,
+                    float* labels, int klab) {
+  launch_snapshots(h->kinv, h->blk_band, nullptr, h->b, smask, sb.psiS, sb.gram, h->n, h->b, h->stream);
+  SpectralArgs A = spectral_args(h, sb);
+  A.fmask = fmask;
+  A.labels = labels;
+  A.klab = klab;
+  launch_face_spectral(A, h->nfaces, h->stream);
+}
+
+// learned space: predicted profiles -> Rayleigh-Ritz on their span; faces whose
+// smallest Ritz value is >= eig_tol take the exact problem
+int spectral_learned(tg_handle* h, const double* kd, SpectralBufs& sb) {
+  const int F = h->nfaces, b = h->b, n = h->n;
+  cudaStream_t s = h->stream;
+  int k = h->opt.learned_k;
+  const float* Y = h->opt.face_profiles;
+  float* ybuf = nullptr;
+  __nv_bfloat16 *x = nullptr, *h1 = nullptr, *h2 = nullptr;
+  double *prof = nullptr, *ccoef = nullptr;
+  int *jpred = nullptr, *fb = nullptr;
+  unsigned char *fmask = nullptr, *smask = nullptr;
+  int rc = TG_OK;
+  if (!Y) {
+    int nb = 0, hid = 0, din = 0, dout = 0;
+    mlp_dims(h->opt.net, &nb, &k, &hid, &din, &dout);
+    if (nb != b) return TG_ERR_INVALID_ARG;
+    if (dalloc(&x, (size_t)F * din) || dalloc(&h1, (size_t)F * hid) || dalloc(&h2, (size_t)F * hid) ||
+        dalloc(&ybuf, (size_t)F * dout))
+      rc = TG_ERR_OOM;
+    if (!rc) {
+      launch_face_inputs(kd, n, b, x, s);
+      mlp_forward(h->opt.net, F, x, ybuf, h1, h2, s);
+      Y = ybuf;
+    }
+  }
+  if (!rc && (dalloc(&prof, (size_t)F * k * b) || dalloc(&ccoef, (size_t)F * k * b) || dalloc(&jpred, F) ||
+              dalloc(&fb, F) || dalloc(&fmask, F) || dalloc(&smask, (size_t)h->nblocks * 4)))
+    rc = TG_ERR_OOM;
+  std::vector<int> hfb(F, 0);
+  if (!rc) {
+    cudaMemsetAsync(fb, 0, sizeof(int) * F, s);
+    launch_pred_basis(Y, h->kinv, k, n, b, 0.25, prof, ccoef, jpred, F, s);
+    launch_snapshots(h->kinv, h->blk_band, ccoef, k, nullptr, sb.psiS, sb.gram, n, b, s);
+    SpectralArgs A = spectral_args(h, sb);
+    A.prof = prof;
+    A.ccoef = ccoef;
+    A.jpred = jpred;
+    A.kmax = k;
+    A.fallback = fb;
+    launch_face_spectral(A, F, s);
+    rc = cuda_err(cudaMemcpyAsync(hfb.data(), fb, sizeof(int) * F, cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  }
+  int nfb = 0;
+  for (int v : hfb) nfb += v;
+  h->fallback_faces = nfb;
+  h->snapshot_solves = 2 * F * k + 2 * nfb * b;
+  if (!rc && nfb > 0) {
+    const int nc = h->nc, nV = nc * (nc - 1);
+    std::vector<unsigned char> hf(F, 0), hs((size_t)h->nblocks * 4, 0);
+    for (int f = 0; f < F; ++f) {
+      if (!hfb[f]) continue;
+      hf[f] = 1;
+      if (f < nV) {
+        const int I = f % (nc - 1) + 1, J = f / (nc - 1);
+        hs[(size_t)(J * nc + I - 1) * 4 + 1] = 1;
+        hs[(size_t)(J * nc + I) * 4 + 0] = 1;
+      } else {
+        const int I = (f - nV) % nc, J = (f - nV) / nc + 1;
+        hs[(size_t)((J - 1) * nc + I) * 4 + 3] = 1;
+        hs[(size_t)(J * nc + I) * 4 + 2] = 1;
+      }
+    }
+    rc = cuda_err(cudaMemcpyAsync(fmask, hf.data(), F, cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(smask, hs.data(), hs.size(), cudaMemcpyHostToDevice, s));
+    if (!rc) {
+      spectral_exact(h, sb, smask, fmask, nullptr, 0);
+      rc = cuda_err(cudaStreamSynchronize(s));
+    }
+  }
+  cudaFree(ybuf); cudaFree(x); cudaFree(h1); cudaFree(h2);
+  cudaFree(prof); cudaFree(ccoef); cudaFree(jpred); cudaFree(fb); cudaFree(fmask); cudaFree(smask);
+  if (rc) return rc;
+  return cuda_err(cudaGetLastError());
+}
+
+int read_spectral(tg_handle* h, SpectralBufs& sb) {
+  cudaStream_t s = h->stream;
+  TG_CK(cudaMemcpyAsync(h->nsel.data(), sb.d_nsel, sizeof(int) * h->nfaces, cudaMemcpyDeviceToHost, s));
+  h->lam_h.resize((size_t)h->nfaces * h->b);
+  TG_CK(cudaMemcpyAsync(h->lam_h.data(), h->lam, sizeof(double) * h->lam_h.size(), cudaMemcpyDeviceToHost, s));
+  int st = 0;
+  int rc = read_status(h, &st);
+  if (rc) return rc;
+  if (st) return status_to_err(st);
+  h->velocity_basis = 0;
+  for (int v : h->nsel) h->velocity_basis += v;
+  return TG_OK;
+}
+
+// preconditioner coarse space from the spectral data (or RT0)
+int setup_coarse(tg_handle* h, SpectralBufs& sb) {
+  const bool rt_mode = (h->opt.coarse_space == TG_COARSE_RT0);
+  int rc = build_space(h, h->cs, h->nsel, rt_mode);
+  if (!rc) rc = finish_space(h, h->cs, sb.psiS, sb.fcoef, sb.zcoef, sb.d_jeff, rt_mode);
+  return rc;
+}
+
+int setup_impl(tg_handle* h, const double* kappa) {
+  const long long nn = (long long)h->n * h->n;
+  cudaStream_t s = h->stream;
+  const double* kd = kappa;
+  double* kcopy = nullptr;
+  struct Guard {
+    double*& p;
+    ~Guard() { cudaFree(p); }
+  } guard{kcopy};
+  if (h->opt.pointer_mode == TG_PTR_HOST) {
+    if (dalloc(&kcopy, nn)) return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(kcopy, kappa, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    kd = kcopy;
+  }
+  int rc = setup_kappa(h, kd);
+  if (!rc) rc = setup_patches(h);
+  if (!rc) rc = setup_blocks(h, true);
+  if (rc) return rc;
 
   // ---- snapshot spaces and local spectral problems (Section 4) ----
   h->nsel.assign(h->nfaces, 1);
-  double *psiS = nullptr, *gram = nullptr, *fcoef = nullptr, *zcoef = nullptr;
-  int* d_nsel = nullptr;
+  SpectralBufs sb{};
   if (h->nfaces > 0 && h->opt.coarse_space != TG_COARSE_RT0) {
-    if (dalloc(&psiS, (size_t)h->nblocks * 4 * b * (b + 1) * (b + 1)) ||
-        dalloc(&gram, (size_t)h->nblocks * 4 * b * b) || dalloc(&h->lam, (size_t)h->nfaces * b) ||
-        dalloc(&d_nsel, h->nfaces) || dalloc(&fcoef, (size_t)h->nfaces * b) ||
-        dalloc(&zcoef, (size_t)h->nfaces * (b - 1) * b))
-      return TG_ERR_OOM;
-    TG_CK(cudaMemsetAsync(zcoef, 0, sizeof(double) * (size_t)h->nfaces * (b - 1) * b, s));
-    launch_snapshots(h->kinv, h->blk_band, psiS, gram, n, b, s);
-    const int mode = (h->opt.coarse_space == TG_COARSE_MSFEM) ? 1 : 0;
-    launch_face_eigen(h->kinv, gram, h->eig_tol, h->opt.max_basis, mode, n, b, h->lam, d_nsel, fcoef, zcoef,
-                      h->d_status, s);
-    TG_CK(cudaMemcpyAsync(h->nsel.data(), d_nsel, sizeof(int) * h->nfaces, cudaMemcpyDeviceToHost, s));
-    h->lam_h.resize((size_t)h->nfaces * b);
-    TG_CK(cudaMemcpyAsync(h->lam_h.data(), h->lam, sizeof(double) * h->lam_h.size(), cudaMemcpyDeviceToHost, s));
-    if ((rc = read_status(h, &st))) return rc;
-    if (st) return status_to_err(st);
+    rc = alloc_spectral(h, sb);
+    if (!rc) {
+      if (h->opt.coarse_space == TG_COARSE_LEARNED) {
+        rc = spectral_learned(h, kd, sb);
+      } else {
+        spectral_exact(h, sb, nullptr, nullptr, nullptr, 0);
+        h->snapshot_solves = 2 * h->nfaces * h->b;
+      }
+    }
+    if (!rc) rc = read_spectral(h, sb);
+  } else {
+    h->velocity_basis = h->nfaces;
   }
-  h->velocity_basis = 0;
-  for (int v : h->nsel) h->velocity_basis += v;
-
-  // ---- coarse spaces: preconditioner (GMsFEM / MsFEM / RT0) and RT0 ----
-  const bool rt_mode = (h->opt.coarse_space == TG_COARSE_RT0);
-  if ((rc = build_space(h, h->cs, h->nsel, rt_mode))) return rc;
-  if ((rc = finish_space(h, h->cs, psiS, fcoef, zcoef, rt_mode))) return rc;
+  // ---- coarse spaces: preconditioner (GMsFEM / MsFEM / RT0 / learned) and RT0 ----
+  if (!rc) rc = setup_coarse(h, sb);
+  free_spectral(sb);
+  if (rc) return rc;
   std::vector<int> ones(h->nfaces, 1);
   if ((rc = build_space(h, h->rt, ones, true))) return rc;
-  if ((rc = finish_space(h, h->rt, nullptr, nullptr, nullptr, true))) return rc;
-  cudaFree(psiS);
-  cudaFree(gram);
-  cudaFree(fcoef);
-  cudaFree(zcoef);
-  cudaFree(d_nsel);
+  if ((rc = finish_space(h, h->rt, nullptr, nullptr, nullptr, nullptr, true))) return rc;
+  int st = 0;
   if ((rc = read_status(h, &st))) return rc;
   if (st) return status_to_err(st);
 
   configure_kernels(std::max(h->cs.D, h->rt.D));
   if ((rc = ctx_alloc(h, &h->ctx))) return rc;
   TG_CK(cudaStreamSynchronize(s));
+  return cuda_err(cudaGetLastError());
+}
+
+// replaces a learned coarse space by the exact one of Section 4.2 and
+// re-creates the default solve context
+int rebuild_exact(tg_handle* h) {
+  SpectralBufs sb{};
+  const int saved = h->opt.coarse_space;
+  h->opt.coarse_space = TG_COARSE_GMSFEM;
+  int rc = alloc_spectral(h, sb);
+  if (!rc) {
+    spectral_exact(h, sb, nullptr, nullptr, nullptr, 0);
+    rc = read_spectral(h, sb);
+  }
+  if (!rc) {
+    free_space(h->cs);
+    rc = setup_coarse(h, sb);
+  }
+  free_spectral(sb);
+  h->opt.coarse_space = saved;
+  if (rc) return rc;
+  h->snapshot_solves += 2 * h->nfaces * h->b;
+  h->fallback_faces = h->nfaces;
+  ctx_free(h->ctx);
+  h->ctx = nullptr;
+  configure_kernels(std::max(h->cs.D, h->rt.D));
+  if ((rc = ctx_alloc(h, &h->ctx))) return rc;
+  TG_CK(cudaStreamSynchronize(h->stream));
   return cuda_err(cudaGetLastError());
 }
 
@@ -829,6 +1034,10 @@ int tg_default_options(tg_options* opt) {
   opt->coarse_space = TG_COARSE_GMSFEM;
   opt->max_basis = 0;
   opt->profile = 0;
+  opt->net = nullptr;
+  opt->face_profiles = nullptr;
+  opt->learned_k = 4;
+  opt->learned_max_iter = 0;
   return TG_OK;
 }
 
@@ -856,10 +1065,15 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
   int rc = validate_grid(grid);
   if (rc) return rc;
   if (!(opt->eta > 0) || opt->m1 < 0 || opt->m2 < 0 || opt->m1 + opt->m2 < 1 || opt->max_iter < 1 ||
-      opt->precision < 0 || opt->precision > 2 || opt->coarse_space < 0 || opt->coarse_space > 2 ||
+      opt->precision < 0 || opt->precision > 2 || opt->coarse_space < 0 || opt->coarse_space > 3 ||
       !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
     return TG_ERR_INVALID_ARG;
   if (opt->m1 < 1) return TG_ERR_UNSUPPORTED;
+  if (opt->coarse_space == TG_COARSE_LEARNED) {
+    if (!opt->face_profiles && !opt->net) return TG_ERR_INVALID_ARG;
+    if (opt->face_profiles && (opt->learned_k < 1 || opt->learned_k > 8)) return TG_ERR_INVALID_ARG;
+    if (opt->learned_max_iter < 0) return TG_ERR_INVALID_ARG;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TG_ERR_CUDA;
   tg_handle* h = new (std::nothrow) tg_handle();
@@ -885,9 +1099,12 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
   return TG_OK;
 }
 
-int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
-             int* iters, tg_report* rep) {
-  if (!h || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
+               int* iters, tg_report* rep) {
   Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
@@ -951,6 +1168,8 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
     rep->max_div_error = diverr;
     rep->kernel_launches = (int)launches;
     rep->graph = h->opt.profile ? 0 : 1;
+    rep->snapshot_solves = h->snapshot_solves;
+    rep->fallback_faces = h->fallback_faces;
     float ms = 0;
     if (h->opt.profile) {
       cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
@@ -975,6 +1194,29 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, do
   delete full;
   if (read_and_clear_timeout()) status |= kStTimeout;
   return status_to_err(status);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
+             int* iters, tg_report* rep) {
+  if (!h || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
+  int it = 0;
+  int rc = solve_impl(h, f, bflux, rtol, ux, uy, p, &it, rep);
+  int refit = 0;
+  if ((rc == TG_OK || rc == TG_ERR_MAXITER) && h->opt.coarse_space == TG_COARSE_LEARNED &&
+      h->opt.learned_max_iter > 0 && it > h->opt.learned_max_iter && h->fallback_faces < h->nfaces) {
+    // the learned space needed too many iterations: exact space, solve again
+    int rb = rebuild_exact(h);
+    if (rb) return rb;
+    rc = solve_impl(h, f, bflux, rtol, ux, uy, p, &it, rep);
+    refit = 1;
+  }
+  if (iters) *iters = it;
+  if (rep) rep->learned_fallback = refit;
+  return rc;
 }
 
 void tg_destroy(tg_handle* h) {
@@ -1154,6 +1396,48 @@ int tg_batch_size(tg_batch* B, int* ninst, int* nrhs) {
   if (ninst) *ninst = (int)B->handles.size();
   if (nrhs) *nrhs = B->nrhs;
   return TG_OK;
+}
+
+int tg_face_data(const double* kappa, const tg_grid* grid, double eig_tol, int k, void* stream, uint16_t* x,
+                 float* q, int* nsel, double* lambda) {
+  if (!kappa || !x || !q || k < 1 || k > 8 || !(eig_tol > 0)) return TG_ERR_INVALID_ARG;
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TG_ERR_CUDA;
+  tg_handle* h = new (std::nothrow) tg_handle();
+  if (!h) return TG_ERR_OOM;
+  h->n = grid->nx;
+  h->b = grid->bx;
+  h->nc = h->n / h->b;
+  h->ov = grid->overlap;
+  h->nblocks = h->nc * h->nc;
+  h->npatch = h->nblocks;
+  h->nfaces = 2 * h->nc * (h->nc - 1);
+  h->h = 1.0 / h->n;
+  h->H = (double)h->b / h->n;
+  h->eig_tol = eig_tol;
+  tg_default_options(&h->opt);
+  h->stream = (cudaStream_t)stream;
+  SpectralBufs sb{};
+  rc = setup_kappa(h, kappa);
+  if (!rc) rc = setup_blocks(h, false);
+  if (!rc && h->nfaces > 0) {
+    h->nsel.assign(h->nfaces, 1);
+    rc = alloc_spectral(h, sb);
+    if (!rc) {
+      spectral_exact(h, sb, nullptr, nullptr, q, k);
+      launch_face_inputs(kappa, h->n, h->b, reinterpret_cast<__nv_bfloat16*>(x), h->stream);
+      rc = read_spectral(h, sb);
+    }
+    if (!rc && nsel) rc = cuda_err(cudaMemcpyAsync(nsel, sb.d_nsel, sizeof(int) * h->nfaces, cudaMemcpyDeviceToDevice, h->stream));
+    if (!rc && lambda)
+      rc = cuda_err(cudaMemcpyAsync(lambda, h->lam, sizeof(double) * h->nfaces * h->b, cudaMemcpyDeviceToDevice, h->stream));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(h->stream));
+  }
+  free_spectral(sb);
+  tg_destroy(h);
+  return rc;
 }
 
 }  // extern "C"

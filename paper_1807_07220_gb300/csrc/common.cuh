@@ -20,6 +20,8 @@
 #include <cstdint>
 #include <cstddef>
 
+struct tg_mlp;   // network of the learned coarse basis (learned.cu)
+
 namespace tg {
 
 constexpr int kMaxB = 16;                 // largest supported block size b
@@ -244,16 +246,57 @@ void launch_band_inverse(const double* band, const int4* rects, int first, int c
 template <typename TS>
 void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count,
                           int nmax, TS* pinv, cudaStream_t s);
-void launch_snapshots(const double* kinv, const double* blk_band, double* psiS, double* gram,
-                      int n, int b, cudaStream_t s);
-void launch_face_eigen(const double* kinv, const double* gram, double eig_tol, int max_basis,
-                       int mode, int n, int b, double* lam, int* nsel, double* fcoef,
-                       double* zcoef, int* status, cudaStream_t s);
+// Snapshot functions of every (block, side): nfn functions per side whose
+// coefficient vectors over {m, d_1..d_{b-1}} are coef[face][fn][0..b-1]
+// (coef NULL: the unit vectors, nfn = b).  Sides with mask[blk*4+side] == 0
+// are skipped (mask NULL: all).  psiS keeps b functions per side, gram b x b.
+void launch_snapshots(const double* kinv, const double* blk_band, const double* coef, int nfn,
+                      const unsigned char* mask, double* psiS, double* gram, int n, int b, cudaStream_t s);
+
+// Arguments of the per-face spectral problems.
+struct SpectralArgs {
+  const double* kinv = nullptr;
+  const double* gram = nullptr;
+  double eig_tol = 0;
+  int max_basis = 0;
+  int mode = 0;                 // 0 spectral selection, 1 the unit-flux MsFEM function alone
+  int n = 0, b = 0;
+  double* lam = nullptr;        // [F][b] eigen- or Ritz values ascending (INFINITY padded)
+  int* nsel = nullptr;          // [F]
+  double* fcoef = nullptr;      // [F][b] unit-flux combination of the face's functions
+  double* zcoef = nullptr;      // [F][b-1][b] zero-flux combinations
+  int* status = nullptr;
+  // learned mode (prof != NULL): the face's functions are jpred[f] predicted
+  // ones with orthonormal flux profiles prof[f][i][.] and coefficients
+  // ccoef[f][i][.] over {m, d_j}; Ritz pairs on their span
+  const double* prof = nullptr;
+  const double* ccoef = nullptr;
+  const int* jpred = nullptr;
+  int kmax = 0;
+  int* fallback = nullptr;      // [F] out: 1 when the smallest Ritz value is >= eig_tol
+  const unsigned char* fmask = nullptr;   // [F] faces to process (NULL: all)
+  int* jeff = nullptr;          // [F] out: functions behind fcoef / zcoef
+  float* labels = nullptr;      // [F][klab][b] out (exact mode): orthonormal profiles of the klab lowest modes
+  int klab = 0;
+};
+void launch_face_spectral(const SpectralArgs& a, int nfaces, cudaStream_t s);
+// predicted whitened profiles (network output y, faces x k x b FP32) ->
+// flux profiles of an orthonormal basis of their span, their coefficients
+// over {m, d_j}, and the count kept per face
+void launch_pred_basis(const float* y, const double* kinv, int k, int n, int b, double thr, double* prof,
+                       double* ccoef, int* jpred, int nfaces, cudaStream_t s);
 template <typename TS>
 void launch_build_tiles(const CoarseSpace& cs, const double* psiS, const double* fcoef,
-                        const double* zcoef, int rt_only, int n, int b, cudaStream_t s);
+                        const double* zcoef, const int* jeff, int rt_only, int n, int b, cudaStream_t s);
 void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b,
                      double* pairE, const long long* pair_ptr, double* K, cudaStream_t s);
 void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s);  // result in A
+
+// learned coarse basis (learned.cu)
+void launch_face_inputs(const double* kappa, int n, int b, __nv_bfloat16* x, cudaStream_t s);
+// network dimensions; y (batch x dout) = net(x) with caller scratch h1, h2 (batch x hidden)
+void mlp_dims(const tg_mlp* net, int* b, int* k, int* hidden, int* din, int* dout);
+void mlp_forward(const tg_mlp* net, int batch, const __nv_bfloat16* x, float* y, __nv_bfloat16* h1,
+                 __nv_bfloat16* h2, cudaStream_t s);
 
 }  // namespace tg

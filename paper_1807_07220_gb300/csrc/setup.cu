@@ -196,46 +196,68 @@ __device__ __forceinline__ void warp_band_solve_s(const double* L, int ldb, int 
   }
 }
 
-// Dynamic shared memory: L[(b-1)^2 (b+1)] | psi[b (b+1)^2] | kloc[b^2]
+// position k (1..b-1) of closed-block node (a, c) among the interior nodes of
+// side s, or 0 if the node is not one of them
+__device__ __forceinline__ int side_position(int side, int a, int c, int b) {
+  if (side == 0) return (a == 0 && c >= 1 && c <= b - 1) ? c : 0;
+  if (side == 1) return (a == b && c >= 1 && c <= b - 1) ? c : 0;
+  if (side == 2) return (c == 0 && a >= 1 && a <= b - 1) ? a : 0;
+  return (c == b && a >= 1 && a <= b - 1) ? a : 0;
+}
+
+__device__ __forceinline__ int face_of_side(int side, int I, int J, int nc) {
+  const int nV = nc * (nc - 1);
+  if (side == 0) return J * (nc - 1) + (I - 1);
+  if (side == 1) return J * (nc - 1) + I;
+  if (side == 2) return nV + (J - 1) * nc + I;
+  return nV + J * nc + I;
+}
+
+// Function fn of a side is sum_j coef_j f_j over the snapshot functions above
+// (coef = e_fn when the coefficient array is NULL): boundary data
+// psi = coef_j on the j-th interior node of the side, forcing coef_0 times the
+// RT_s forcing, interior solved with the block's band factor.
+// Dynamic shared memory: L[(b-1)^2 (b+1)] | psi[nfn (b+1)^2] | kloc[b^2] |
+// coefficient rows [nfn b] | solve lines [warps (b-1)^2]
 __global__ void k_snapshots(const double* __restrict__ kinv, const double* __restrict__ blk_band,
+                            const double* __restrict__ coef, int nfn, const unsigned char* __restrict__ mask,
                             double* __restrict__ psiS, double* __restrict__ gram, int n, int b) {
   extern __shared__ double sm[];
   const int nc = n / b;
   const int blk = blockIdx.x >> 2, side = blockIdx.x & 3;
   const int I = blk % nc, J = blk / nc;
   if (!side_interior(side, I, J, nc)) return;
+  if (mask && !mask[blockIdx.x]) return;
   const int nx = b - 1, nloc = nx * nx, ldb = b + 1, w = b;  // block band width w = nx + 1
   const int nb1 = b + 1, ncl = nb1 * nb1;
   double* L = sm;
   double* psi = L + nloc * ldb;
-  double* kl = psi + b * ncl;
+  double* kl = psi + nfn * ncl;
+  double* cf = kl + b * b;
   const double h = 1.0 / n;
   const double* Bg = blk_band + (long long)blk * nloc * ldb;
   for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = Bg[t];
   for (int t = threadIdx.x; t < b * b; t += blockDim.x)
     kl[t] = kinv[(long long)(J * b + t / b) * n + I * b + t % b];
+  const double* crow = coef ? coef + (long long)face_of_side(side, I, J, nc) * nfn * b : nullptr;
+  for (int t = threadIdx.x; t < nfn * b; t += blockDim.x)
+    cf[t] = crow ? crow[t] : ((t / b == t % b) ? 1.0 : 0.0);
+  __syncthreads();
   // closed psi: boundary data, interior = right-hand side
-  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nfn * ncl; t += blockDim.x) {
     const int fn = t / ncl, node = t % ncl, a = node % nb1, c = node / nb1;
-    double v = 0.0;
-    const bool interior = (a >= 1 && a <= b - 1 && c >= 1 && c <= b - 1);
-    if (!interior) {
-      if (fn >= 1) {
-        int ba, bc;
-        side_node(side, fn, b, ba, bc);
-        v = (a == ba && c == bc) ? 1.0 : 0.0;
-      }
-    }
-    psi[t] = v;
+    const int pos = side_position(side, a, c, b);
+    psi[t] = pos ? cf[fn * b + pos] : 0.0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nfn * ncl; t += blockDim.x) {
     const int fn = t / ncl, node = t % ncl, a = node % nb1, c = node / nb1;
     if (!(a >= 1 && a <= b - 1 && c >= 1 && c <= b - 1)) continue;
     const double k00 = kl[(c - 1) * b + a - 1], k10 = kl[(c - 1) * b + a];
     const double k01 = kl[c * b + a - 1], k11 = kl[c * b + a];
     double rhs = 0.0;
-    if (fn == 0) {
+    const double c0 = cf[fn * b];
+    if (c0 != 0.0) {
       // -C^T A RT_s at node (a, c); A RT_s / h on a face = h * (...) with RT values
       if (side <= 1) {
         // x-faces (a, c-1) [node on top] and (a, c) [node at bottom]; cells row c-1 / c
@@ -243,40 +265,38 @@ __global__ void k_snapshots(const double* __restrict__ kinv, const double* __res
           return h * ((kL + kR) / 3.0 * rt_value(side, a, b) +
                       (kL * rt_value(side, a - 1, b) + kR * rt_value(side, a + 1, b)) / 6.0);
         };
-        rhs = -(ax(k00, k10) - ax(k01, k11));
+        rhs = -c0 * (ax(k00, k10) - ax(k01, k11));
       } else {
         auto ay = [&](double kB, double kT) {
           return h * ((kB + kT) / 3.0 * rt_value(side, c, b) +
                       (kB * rt_value(side, c - 1, b) + kT * rt_value(side, c + 1, b)) / 6.0);
         };
         // y-faces (a-1, c) [node on the right] and (a, c) [node on the left]
-        rhs = -(-ay(k00, k01) + ay(k10, k11));
+        rhs = -c0 * (-ay(k00, k01) + ay(k10, k11));
       }
-    } else {
-      // boundary data only: interior entries of P are being overwritten with
-      // right-hand sides by other threads, and the data field is zero there
-      const double* P = psi + fn * ncl;
-      auto at = [&](int da, int dc) {
-        const int aa = a + da, cc = c + dc;
-        const bool in = (aa >= 1 && aa <= b - 1 && cc >= 1 && cc <= b - 1);
-        return in ? 0.0 : P[cc * nb1 + aa];
-      };
-      double kp = (2.0 / 3.0) * (k00 + k10 + k01 + k11) * at(0, 0);
-      kp -= (1.0 / 6.0) * ((k00 + k10) * at(0, -1) + (k01 + k11) * at(0, 1) + (k00 + k01) * at(-1, 0) +
-                           (k10 + k11) * at(1, 0));
-      kp -= (1.0 / 3.0) * (k00 * at(-1, -1) + k10 * at(1, -1) + k01 * at(-1, 1) + k11 * at(1, 1));
-      rhs = -kp;
     }
-    psi[t] = rhs;  // interior slot used as right-hand side
+    // boundary data: interior entries of P are being overwritten with
+    // right-hand sides by other threads, and the data field is zero there
+    const double* P = psi + fn * ncl;
+    auto at = [&](int da, int dc) {
+      const int aa = a + da, cc = c + dc;
+      const bool in = (aa >= 1 && aa <= b - 1 && cc >= 1 && cc <= b - 1);
+      return in ? 0.0 : P[cc * nb1 + aa];
+    };
+    double kp = (2.0 / 3.0) * (k00 + k10 + k01 + k11) * at(0, 0);
+    kp -= (1.0 / 6.0) * ((k00 + k10) * at(0, -1) + (k01 + k11) * at(0, 1) + (k00 + k01) * at(-1, 0) +
+                         (k10 + k11) * at(1, 0));
+    kp -= (1.0 / 3.0) * (k00 * at(-1, -1) + k10 * at(1, -1) + k01 * at(-1, 1) + k11 * at(1, 1));
+    psi[t] = rhs - kp;  // interior slot used as right-hand side
   }
   __syncthreads();
   // solve: warp per function, in a compact interior vector stored in the
   // function's own interior slots (copied to a temporary line first)
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double* tmp = kl + b * b;  // nw * nloc scratch
+    double* tmp = cf + nfn * b;  // nw * nloc scratch
     double* x = tmp + warp * nloc;
-    for (int fn = warp; fn < b; fn += nw) {
+    for (int fn = warp; fn < nfn; fn += nw) {
       double* P = psi + fn * ncl;
       for (int q = lane; q < nloc; q += 32) x[q] = P[(1 + q / nx) * nb1 + 1 + q % nx];
       __syncwarp();
@@ -287,16 +307,18 @@ __global__ void k_snapshots(const double* __restrict__ kinv, const double* __res
   }
   __syncthreads();
   double* outp = psiS + ((long long)blk * 4 + side) * b * ncl;
-  for (int t = threadIdx.x; t < b * ncl; t += blockDim.x) outp[t] = psi[t];
-  // Gram: thread per pair (fa <= fb), energy summed over the block's cells
+  for (int t = threadIdx.x; t < nfn * ncl; t += blockDim.x) outp[t] = psi[t];
+  // Gram: thread per pair (fa <= fb), energy summed over the block's cells;
+  // the velocity of function f is coef_{f,0} RT_s + C psi_f
   double* G = gram + ((long long)blk * 4 + side) * b * b;
-  const int npair = b * (b + 1) / 2;
+  const int npair = nfn * (nfn + 1) / 2;
   for (int t = threadIdx.x; t < npair; t += blockDim.x) {
     int fa = 0, rem = t;
-    while (rem >= b - fa) { rem -= b - fa; ++fa; }
+    while (rem >= nfn - fa) { rem -= nfn - fa; ++fa; }
     const int fb = fa + rem;
     const double* Pa = psi + fa * ncl;
     const double* Pb = psi + fb * ncl;
+    const double ca = cf[fa * b], cb = cf[fb * b];
     double e = 0.0;
     for (int cell = 0; cell < b * b; ++cell) {
       const int a = cell % b, c = cell / b;
@@ -306,13 +328,12 @@ __global__ void k_snapshots(const double* __restrict__ kinv, const double* __res
       double aB = -(Pa[n10] - Pa[n00]), aT = -(Pa[n11] - Pa[n01]);
       double bL = Pb[n01] - Pb[n00], bR = Pb[n11] - Pb[n10];
       double bB = -(Pb[n10] - Pb[n00]), bT = -(Pb[n11] - Pb[n01]);
-      if (fa == 0) {
-        if (side <= 1) { aL += h * rt_value(side, a, b); aR += h * rt_value(side, a + 1, b); }
-        else { aB += h * rt_value(side, c, b); aT += h * rt_value(side, c + 1, b); }
-      }
-      if (fb == 0) {
-        if (side <= 1) { bL += h * rt_value(side, a, b); bR += h * rt_value(side, a + 1, b); }
-        else { bB += h * rt_value(side, c, b); bT += h * rt_value(side, c + 1, b); }
+      if (side <= 1) {
+        aL += ca * h * rt_value(side, a, b); aR += ca * h * rt_value(side, a + 1, b);
+        bL += cb * h * rt_value(side, a, b); bR += cb * h * rt_value(side, a + 1, b);
+      } else {
+        aB += ca * h * rt_value(side, c, b); aT += ca * h * rt_value(side, c + 1, b);
+        bB += cb * h * rt_value(side, c, b); bT += cb * h * rt_value(side, c + 1, b);
       }
       const double k = kl[cell];
       e += k * ((aL * bL + aR * bR + aB * bB + aT * bT) / 3.0 +
@@ -401,124 +422,202 @@ __device__ bool cholesky_serial(double (*A)[kJ], int m) {  // lower factor in pl
   return true;
 }
 
-__global__ void k_face_eigen(const double* __restrict__ kinv, const double* __restrict__ gram,
-                             double eig_tol, int max_basis, int mode, int n, int b,
-                             double* __restrict__ lam, int* __restrict__ nsel,
-                             double* __restrict__ fcoef, double* __restrict__ zcoef, int* status) {
-  if (threadIdx.x != 0) return;
-  __shared__ double S[kJ][kJ], Aa[kJ][kJ], V[kJ][kJ], C[kJ][kJ];
-  __shared__ double mu[kJ], lamv[kJ];
-  __shared__ int ord[kJ];
-  const int nc = n / b, nV = nc * (nc - 1);
-  const int f = blockIdx.x;
-  int kind, I, J;
+__device__ __forceinline__ void face_geometry(int f, int nc, int& kind, int& I, int& J) {
+  const int nV = nc * (nc - 1);
   if (f < nV) { kind = 0; I = f % (nc - 1) + 1; J = f / (nc - 1); }
   else { kind = 1; I = (f - nV) % nc; J = (f - nV) / nc + 1; }
+}
+
+// mean inverse permeability of the two cells at fine face l of coarse face (kind, I, J)
+__device__ __forceinline__ double face_kinv(const double* kinv, int n, int b, int kind, int I, int J, int l) {
+  double kl, kr;
+  if (kind == 0) { kl = kinv[(long long)(J * b + l) * n + I * b - 1]; kr = kinv[(long long)(J * b + l) * n + I * b]; }
+  else { kl = kinv[(long long)(J * b - 1) * n + I * b + l]; kr = kinv[(long long)(J * b) * n + I * b + l]; }
+  return 0.5 * (kl + kr);
+}
+
+// normal values on fine faces l of E_i of {m, d_1..d_{b-1}}: Nl[0] = 1;
+// d_k = +-1/h on faces k-1 (node k above / right) and k
+__device__ __forceinline__ void normal_values(int kind, int l, int b, double h, double* Nl) {
+  for (int k = 0; k < b; ++k) Nl[k] = 0.0;
+  Nl[0] = 1.0;
+  const double sg = (kind == 0) ? 1.0 : -1.0;
+  if (l + 1 <= b - 1) Nl[l + 1] = sg / h;   // face l has node l+1 as its upper/right end
+  if (l >= 1) Nl[l] = -sg / h;              // and node l as its lower/left end
+}
+
+__global__ void k_face_spectral(SpectralArgs A) {
+  if (threadIdx.x != 0) return;
+  __shared__ double S[kJ][kJ], Aa[kJ][kJ], V[kJ][kJ], C[kJ][kJ];
+  __shared__ double mu[kJ], lamv[kJ], wv[kJ];
+  __shared__ int ord[kJ];
+  const int n = A.n, b = A.b, nc = n / b;
+  const int f = blockIdx.x;
+  if (A.fmask && !A.fmask[f]) return;
+  int kind, I, J;
+  face_geometry(f, nc, kind, I, J);
   int blk1, side1, blk2, side2;
   if (kind == 0) { blk1 = J * nc + I - 1; side1 = 1; blk2 = J * nc + I; side2 = 0; }
   else { blk1 = (J - 1) * nc + I; side1 = 3; blk2 = J * nc + I; side2 = 2; }
   const double h = 1.0 / n, H = b * h;
-  const double* G1 = gram + ((long long)blk1 * 4 + side1) * b * b;
-  const double* G2 = gram + ((long long)blk2 * 4 + side2) * b * b;
-  for (int i = 0; i < b; ++i)
-    for (int j = 0; j < b; ++j) S[i][j] = (G1[i * b + j] + G2[i * b + j]) / H;
-  S[0][0] += 2.0 / H;
-  // a = N D N^T
-  for (int i = 0; i < b; ++i)
-    for (int j = 0; j < b; ++j) Aa[i][j] = 0.0;
-  for (int l = 0; l < b; ++l) {
-    double kl, kr;
-    if (kind == 0) { kl = kinv[(long long)(J * b + l) * n + I * b - 1]; kr = kinv[(long long)(J * b + l) * n + I * b]; }
-    else { kl = kinv[(long long)(J * b - 1) * n + I * b + l]; kr = kinv[(long long)(J * b) * n + I * b + l]; }
-    const double ke = 0.5 * (kl + kr);
-    double Nl[kJ];
-    for (int k = 0; k < b; ++k) Nl[k] = 0.0;
-    Nl[0] = 1.0;
-    // d_k: +-1/h on faces k-1 (node k above/right) and k
-    const double sg = (kind == 0) ? 1.0 : -1.0;
-    if (l + 1 <= b - 1) Nl[l + 1] = sg / h;        // face l has node l+1 as its upper/right end
-    if (l >= 1) Nl[l] = -sg / h;                   // and node l as its lower/left end
-    for (int i = 0; i < b; ++i)
-      for (int j = 0; j < b; ++j) Aa[i][j] += ke * Nl[i] * Nl[j];
+  const bool learned = (A.prof != nullptr);
+  const int m_fn = learned ? A.jpred[f] : b;    // functions of the face
+  if (A.jeff) A.jeff[f] = m_fn;
+  for (int k = 0; k < b; ++k) A.lam[(long long)f * b + k] = INFINITY;
+  if (learned && m_fn < 1) {                     // nothing predicted: exact problem
+    A.fallback[f] = 1;
+    return;
   }
-  if (!cholesky_serial(Aa, b)) {
-    atomicOr(status, kStNotSpd);
+  // flux weights: coefficient of m in each function
+  for (int i = 0; i < m_fn; ++i) wv[i] = learned ? A.ccoef[((long long)f * A.kmax + i) * b] : (i == 0 ? 1.0 : 0.0);
+  const double* G1 = A.gram + ((long long)blk1 * 4 + side1) * b * b;
+  const double* G2 = A.gram + ((long long)blk2 * 4 + side2) * b * b;
+  // s = H^{-1} (Gram_{K1} + Gram_{K2} + div term), div term 2 w_i w_j
+  for (int i = 0; i < m_fn; ++i)
+    for (int j = 0; j < m_fn; ++j) S[i][j] = (G1[i * b + j] + G2[i * b + j] + 2.0 * wv[i] * wv[j]) / H;
+  // a = N diag(kappa_e^{-1}) N^T, N the normal values of the functions on E_i
+  for (int i = 0; i < m_fn; ++i)
+    for (int j = 0; j < m_fn; ++j) Aa[i][j] = 0.0;
+  for (int l = 0; l < b; ++l) {
+    const double ke = face_kinv(A.kinv, n, b, kind, I, J, l);
+    double Nl[kJ];
+    if (learned) {
+      for (int i = 0; i < m_fn; ++i) Nl[i] = A.prof[((long long)f * A.kmax + i) * b + l];
+    } else {
+      normal_values(kind, l, b, h, Nl);
+    }
+    for (int i = 0; i < m_fn; ++i)
+      for (int j = 0; j < m_fn; ++j) Aa[i][j] += ke * Nl[i] * Nl[j];
+  }
+  if (!cholesky_serial(Aa, m_fn)) {
+    atomicOr(A.status, kStNotSpd);
     return;
   }
   // S <- L^{-1} S L^{-T}
-  for (int col = 0; col < b; ++col)
-    for (int i = 0; i < b; ++i) {
+  for (int col = 0; col < m_fn; ++col)
+    for (int i = 0; i < m_fn; ++i) {
       double v = S[i][col];
       for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[k][col];
       S[i][col] = v / Aa[i][i];
     }
-  for (int row = 0; row < b; ++row)
-    for (int i = 0; i < b; ++i) {
+  for (int row = 0; row < m_fn; ++row)
+    for (int i = 0; i < m_fn; ++i) {
       double v = S[row][i];
       for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[row][k];
       S[row][i] = v / Aa[i][i];
     }
-  for (int i = 0; i < b; ++i)
+  for (int i = 0; i < m_fn; ++i)
     for (int j = 0; j < i; ++j) {
       const double v = 0.5 * (S[i][j] + S[j][i]);
       S[i][j] = S[j][i] = v;
     }
-  jacobi_serial(S, V, b);
-  for (int k = 0; k < b; ++k) { mu[k] = S[k][k]; ord[k] = k; }
+  jacobi_serial(S, V, m_fn);
+  for (int k = 0; k < m_fn; ++k) { mu[k] = S[k][k]; ord[k] = k; }
   // descending mu = ascending lambda (stable insertion sort)
-  for (int i = 1; i < b; ++i) {
+  for (int i = 1; i < m_fn; ++i) {
     const int o = ord[i];
     int j = i - 1;
     while (j >= 0 && mu[ord[j]] < mu[o]) { ord[j + 1] = ord[j]; --j; }
     ord[j + 1] = o;
   }
-  for (int k = 0; k < b; ++k) {
+  for (int k = 0; k < m_fn; ++k) {
     lamv[k] = 1.0 / mu[ord[k]];
-    lam[(long long)f * b + k] = lamv[k];
+    A.lam[(long long)f * b + k] = lamv[k];
   }
   int m = 0;
-  while (m < b && lamv[m] < eig_tol) ++m;
+  while (m < m_fn && lamv[m] < A.eig_tol) ++m;
   if (m < 1) m = 1;
-  if (max_basis > 0 && m > max_basis) m = max_basis;
-  if (mode != 0) m = 1;
-  nsel[f] = m;
-  // coefficient vectors c_k = L^{-T} y_k / sqrt(mu_k) (s-orthonormal)
-  for (int k = 0; k < m; ++k) {
+  if (A.max_basis > 0 && m > A.max_basis) m = A.max_basis;
+  if (A.mode != 0) m = 1;
+  if (learned) {
+    const int fb = (lamv[0] >= A.eig_tol) ? 1 : 0;
+    A.fallback[f] = fb;
+    if (fb) return;
+  }
+  if (!learned) A.nsel[f] = m;
+  // coefficient vectors c_k = L^{-T} y_k / sqrt(mu_k) (s-orthonormal); the
+  // labels need the klab lowest modes, selected or not
+  const int mc = A.labels ? max(m, min(A.klab, m_fn)) : m;
+  for (int k = 0; k < mc; ++k) {
     const int o = ord[k];
-    for (int i = b - 1; i >= 0; --i) {
+    for (int i = m_fn - 1; i >= 0; --i) {
       double v = V[i][o];
-      for (int r = i + 1; r < b; ++r) v -= Aa[r][i] * C[r][k];
+      for (int r = i + 1; r < m_fn; ++r) v -= Aa[r][i] * C[r][k];
       C[i][k] = v / Aa[i][i];
     }
     const double sc = 1.0 / sqrt(mu[o]);
-    for (int i = 0; i < b; ++i) C[i][k] *= sc;
+    for (int i = 0; i < m_fn; ++i) C[i][k] *= sc;
   }
-  double* fc = fcoef + (long long)f * b;
-  double* zc = zcoef + (long long)f * (b - 1) * b;
-  if (mode != 0) {  // MsFEM / RT0: the unit-flux MsFEM function alone
+  if (A.labels) {
+    // whitened profiles y_k = a^{1/2} N^T c_k of the min(klab, b) lowest modes,
+    // orthonormalised by modified Gram-Schmidt (twice), zero-padded
+    const int ml = min(A.klab, m_fn);
+    float* out = A.labels + (long long)f * A.klab * b;
+    double P[kJ][kJ];
+    for (int k = 0; k < ml; ++k)
+      for (int l = 0; l < b; ++l) {
+        double Nl[kJ];
+        normal_values(kind, l, b, h, Nl);
+        double g = 0.0;
+        for (int i = 0; i < m_fn; ++i) g += Nl[i] * C[i][k];
+        P[k][l] = sqrt(face_kinv(A.kinv, n, b, kind, I, J, l)) * g;   // whitened y = a^{1/2} g
+      }
+    for (int k = 0; k < ml; ++k) {
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = 0; q < k; ++q) {
+          double d = 0.0;
+          for (int l = 0; l < b; ++l) d += P[q][l] * P[k][l];
+          for (int l = 0; l < b; ++l) P[k][l] -= d * P[q][l];
+        }
+      double nr = 0.0;
+      for (int l = 0; l < b; ++l) nr += P[k][l] * P[k][l];
+      nr = sqrt(nr);
+      for (int l = 0; l < b; ++l) P[k][l] = (nr > 0.0) ? P[k][l] / nr : 0.0;
+    }
+    for (int k = 0; k < A.klab; ++k)
+      for (int l = 0; l < b; ++l) out[k * b + l] = (k < ml) ? (float)P[k][l] : 0.0f;
+  }
+  double* fc = A.fcoef + (long long)f * b;
+  double* zc = A.zcoef + (long long)f * (b - 1) * b;
+  if (A.mode != 0) {  // MsFEM / RT0: the unit-flux MsFEM function alone
     for (int i = 0; i < b; ++i) fc[i] = (i == 0) ? 1.0 : 0.0;
     return;
   }
+  // net flux of each selected function: t_k = sum_i w_i C[i][k]
+  double t[kJ];
   double tn = 0.0, cmax = 0.0;
-  for (int k = 0; k < m; ++k) tn += C[0][k] * C[0][k];
+  for (int k = 0; k < m; ++k) {
+    double v = 0.0;
+    for (int i = 0; i < m_fn; ++i) v += wv[i] * C[i][k];
+    t[k] = v;
+    tn += v * v;
+  }
   for (int k = 0; k < m; ++k)
-    for (int i = 0; i < b; ++i) cmax = fmax(cmax, fabs(C[i][k]));
-  if (!(sqrt(tn) > 1e-12 * cmax)) {
-    atomicOr(status, kStDegenerate);
-    for (int i = 0; i < b; ++i) fc[i] = (i == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < m_fn; ++i) cmax = fmax(cmax, fabs(C[i][k]));
+  if (learned && !(sqrt(tn) > 1e-6 * cmax)) {
+    // the kept predicted functions carry no net flux through E_i: exact problem
+    A.fallback[f] = 1;
     return;
   }
+  if (!(sqrt(tn) > 1e-12 * cmax)) {
+    atomicOr(A.status, kStDegenerate);
+    for (int i = 0; i < b; ++i) fc[i] = (!learned && i == 0) ? 1.0 : 0.0;
+    return;
+  }
+  if (learned) A.nsel[f] = m;
+  // unit-flux function: the min-norm combination with sum_k t_k a_k = 1
   for (int i = 0; i < b; ++i) {
     double v = 0.0;
-    for (int k = 0; k < m; ++k) v += C[i][k] * C[0][k] / tn;
+    if (i < m_fn)
+      for (int k = 0; k < m; ++k) v += C[i][k] * t[k] / tn;
     fc[i] = v;
   }
-  fc[0] = 1.0;
+  if (!learned) fc[0] = 1.0;
   if (m > 1) {
     // Householder H = I - 2 v v^T / v^T v with v = t + sign(t0) |t| e0 maps t to -sign |t| e0;
-    // columns 1..m-1 of H span t^perp.
+    // columns 1..m-1 of H span t^perp: the zero-flux functions
     double v[kJ];
-    for (int k = 0; k < m; ++k) v[k] = C[0][k];
+    for (int k = 0; k < m; ++k) v[k] = t[k];
     const double tnorm = sqrt(tn);
     v[0] += (v[0] >= 0.0 ? tnorm : -tnorm);
     double vv = 0.0;
@@ -526,12 +625,75 @@ __global__ void k_face_eigen(const double* __restrict__ kinv, const double* __re
     for (int q = 1; q < m; ++q) {
       for (int i = 0; i < b; ++i) {
         double acc = 0.0;
-        for (int k = 0; k < m; ++k) {
-          const double Hkq = ((k == q) ? 1.0 : 0.0) - 2.0 * v[k] * v[q] / vv;
-          acc += C[i][k] * Hkq;
-        }
-        zc[(long long)(q - 1) * b + i] = (i == 0) ? 0.0 : acc;
+        if (i < m_fn)
+          for (int k = 0; k < m; ++k) {
+            const double Hkq = ((k == q) ? 1.0 : 0.0) - 2.0 * v[k] * v[q] / vv;
+            acc += C[i][k] * Hkq;
+          }
+        zc[(long long)(q - 1) * b + i] = (!learned && i == 0) ? 0.0 : acc;
       }
+    }
+  }
+}
+
+// Predicted whitened profiles of a face (network output, k x b, y_l =
+// a_l^{1/2} g_l) -> an orthonormal basis of the directions of their span with
+// G^T G eigenvalue > thr, converted to flux profiles g = a^{-1/2} y, and each
+// direction's coefficients over {m, d_1..d_{b-1}}: c_0 = the mean normal
+// value, d_j = sg h sum_{l<j} (g_l - c_0) (inverse of the normal-value map).
+__global__ void k_pred_basis(const float* __restrict__ y, const double* __restrict__ kinv, int k, int n, int b,
+                             double thr, double* __restrict__ prof, double* __restrict__ ccoef,
+                             int* __restrict__ jpred, int nfaces) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfaces) return;
+  const int nc = n / b;
+  int kind, I, J;
+  face_geometry(f, nc, kind, I, J);
+  const double h = 1.0 / n, sg = (kind == 0) ? 1.0 : -1.0;
+  constexpr int kK = 8;
+  double Gm[kJ][kJ], Vm[kJ][kJ];
+  const float* Y = y + (long long)f * k * b;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double v = 0.0;
+      for (int l = 0; l < b; ++l) v += (double)Y[i * b + l] * (double)Y[j * b + l];
+      Gm[i][j] = v;
+    }
+  jacobi_serial(Gm, Vm, k);
+  int order[kK];
+  int r = 0;
+  for (int i = 0; i < k; ++i)
+    if (Gm[i][i] > thr) order[r++] = i;
+  // largest eigenvalue first
+  for (int i = 1; i < r; ++i) {
+    const int o = order[i];
+    int j = i - 1;
+    while (j >= 0 && Gm[order[j]][order[j]] < Gm[o][o]) { order[j + 1] = order[j]; --j; }
+    order[j + 1] = o;
+  }
+  jpred[f] = r;
+  for (int q = 0; q < k; ++q) {
+    double* P = prof + ((long long)f * k + q) * b;
+    double* Cc = ccoef + ((long long)f * k + q) * b;
+    if (q >= r) {
+      for (int l = 0; l < b; ++l) { P[l] = 0.0; Cc[l] = 0.0; }
+      continue;
+    }
+    const int o = order[q];
+    const double sc = 1.0 / sqrt(Gm[o][o]);
+    double mean = 0.0;
+    for (int l = 0; l < b; ++l) {
+      double g = 0.0;
+      for (int i = 0; i < k; ++i) g += (double)Y[i * b + l] * Vm[i][o];
+      P[l] = g * sc / sqrt(face_kinv(kinv, n, b, kind, I, J, l));
+      mean += P[l];
+    }
+    mean /= b;
+    Cc[0] = mean;
+    double run = 0.0;
+    for (int j = 1; j < b; ++j) {
+      run += P[j - 1] - mean;
+      Cc[j] = sg * h * run;
     }
   }
 }
@@ -543,19 +705,14 @@ __global__ void k_face_eigen(const double* __restrict__ kinv, const double* __re
 //       coarse curl of the nodal delta at m;
 //   z_{E,k}: sum_j zcoef_E[k-1][j] psi_dj(E).
 // rt_only: theta_m = Hat_m (coarse RT0 space).
-__device__ __forceinline__ int face_of_side(int side, int I, int J, int nc) {
-  const int nV = nc * (nc - 1);
-  if (side == 0) return J * (nc - 1) + (I - 1);
-  if (side == 1) return J * (nc - 1) + I;
-  if (side == 2) return nV + (J - 1) * nc + I;
-  return nV + J * nc + I;
-}
-
+// A face's functions are the first jeff[face] functions of its sides (b
+// snapshot functions, or the predicted ones of the learned space); fcoef and
+// zcoef are combinations of them.
 template <typename TS>
 __global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __restrict__ psiS,
                               const double* __restrict__ fcoef, const double* __restrict__ zcoef,
-                              double* __restrict__ closed, TS* __restrict__ owned, int rt_only, int n,
-                              int b) {
+                              const int* __restrict__ jeff, double* __restrict__ closed, TS* __restrict__ owned,
+                              int rt_only, int n, int b) {
   const int nc = n / b, nb1 = b + 1, ncl = nb1 * nb1;
   const Slot sl = slots[blockIdx.x];
   const int I = sl.block % nc, J = sl.block / nc;
@@ -580,15 +737,17 @@ __global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __re
           const int face = face_of_side(sides[e], I, J, nc);
           const double* P = psiS + ((long long)sl.block * 4 + sides[e]) * b * ncl;
           const double* fc = fcoef + (long long)face * b;
-          double xi = P[t];
-          for (int jj = 1; jj < b; ++jj) xi += fc[jj] * P[(long long)jj * ncl + t];
+          const int nf = jeff ? jeff[face] : b;
+          double xi = 0.0;
+          for (int jj = 0; jj < nf; ++jj) xi += fc[jj] * P[(long long)jj * ncl + t];
           v += cs[e] * xi;
         }
       }
     } else {
       const double* P = psiS + ((long long)sl.block * 4 + sl.which) * b * ncl;
       const double* zc = zcoef + ((long long)sl.face * (b - 1) + (sl.k - 1)) * b;
-      for (int jj = 1; jj < b; ++jj) v += zc[jj] * P[(long long)jj * ncl + t];
+      const int nf = jeff ? jeff[sl.face] : b;
+      for (int jj = 0; jj < nf; ++jj) v += zc[jj] * P[(long long)jj * ncl + t];
     }
     // the Galerkin matrix is assembled from the rounded values, so that the
     // coarse step is the exact K-orthogonal projection onto the span that the
@@ -705,35 +864,37 @@ template void launch_store_inverse<float>(const double*, const PatchGeo*, int, i
 template void launch_store_inverse<__nv_bfloat16>(const double*, const PatchGeo*, int, int, int,
                                                   __nv_bfloat16*, cudaStream_t);
 
-void launch_snapshots(const double* kinv, const double* blk_band, double* psiS, double* gram, int n, int b,
-                      cudaStream_t s) {
+void launch_snapshots(const double* kinv, const double* blk_band, const double* coef, int nfn,
+                      const unsigned char* mask, double* psiS, double* gram, int n, int b, cudaStream_t s) {
   const int nc = n / b, nloc = (b - 1) * (b - 1), threads = 256;
-  const size_t shm = sizeof(double) * ((size_t)nloc * (b + 1) + (size_t)b * (b + 1) * (b + 1) +
-                                       (size_t)b * b + (size_t)(threads / 32) * nloc);
+  if (!coef) nfn = b;
+  const size_t shm = sizeof(double) * ((size_t)nloc * (b + 1) + (size_t)nfn * (b + 1) * (b + 1) +
+                                       (size_t)b * b + (size_t)nfn * b + (size_t)(threads / 32) * nloc);
   cudaFuncSetAttribute(k_snapshots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  k_snapshots<<<nc * nc * 4, threads, shm, s>>>(kinv, blk_band, psiS, gram, n, b);
+  k_snapshots<<<nc * nc * 4, threads, shm, s>>>(kinv, blk_band, coef, nfn, mask, psiS, gram, n, b);
 }
-void launch_face_eigen(const double* kinv, const double* gram, double eig_tol, int max_basis, int mode,
-                       int n, int b, double* lam, int* nsel, double* fcoef, double* zcoef, int* status,
-                       cudaStream_t s) {
-  const int nc = n / b, nfaces = 2 * nc * (nc - 1);
+void launch_face_spectral(const SpectralArgs& a, int nfaces, cudaStream_t s) {
   if (nfaces == 0) return;
-  k_face_eigen<<<nfaces, 32, 0, s>>>(kinv, gram, eig_tol, max_basis, mode, n, b, lam, nsel, fcoef, zcoef,
-                                     status);
+  k_face_spectral<<<nfaces, 32, 0, s>>>(a);
+}
+void launch_pred_basis(const float* y, const double* kinv, int k, int n, int b, double thr, double* prof,
+                       double* ccoef, int* jpred, int nfaces, cudaStream_t s) {
+  if (nfaces == 0) return;
+  k_pred_basis<<<(nfaces + 63) / 64, 64, 0, s>>>(y, kinv, k, n, b, thr, prof, ccoef, jpred, nfaces);
 }
 template <typename TS>
 void launch_build_tiles(const CoarseSpace& cs, const double* psiS, const double* fcoef, const double* zcoef,
-                        int rt_only, int n, int b, cudaStream_t s) {
+                        const int* jeff, int rt_only, int n, int b, cudaStream_t s) {
   if (cs.nslots == 0) return;
-  k_build_tiles<TS><<<cs.nslots, 128, 0, s>>>(cs.slots, psiS, fcoef, zcoef, cs.closed, (TS*)cs.owned,
+  k_build_tiles<TS><<<cs.nslots, 128, 0, s>>>(cs.slots, psiS, fcoef, zcoef, jeff, cs.closed, (TS*)cs.owned,
                                                rt_only, n, b);
 }
 template void launch_build_tiles<double>(const CoarseSpace&, const double*, const double*, const double*,
-                                         int, int, int, cudaStream_t);
+                                         const int*, int, int, int, cudaStream_t);
 template void launch_build_tiles<float>(const CoarseSpace&, const double*, const double*, const double*,
-                                        int, int, int, cudaStream_t);
+                                        const int*, int, int, int, cudaStream_t);
 template void launch_build_tiles<__nv_bfloat16>(const CoarseSpace&, const double*, const double*,
-                                                const double*, int, int, int, cudaStream_t);
+                                                const double*, const int*, int, int, int, cudaStream_t);
 
 void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b, double* pairE,
                      const long long* pair_ptr, double* K, cudaStream_t s) {

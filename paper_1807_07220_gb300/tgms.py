@@ -21,7 +21,7 @@ ERRORS = {
     -8: "TG_ERR_UNSUPPORTED", -9: "TG_ERR_DEGENERATE_BASIS",
 }
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
-COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2}
+COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2, "learned": 3}
 PTR_HOST, PTR_DEVICE = 0, 1
 
 c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -35,7 +35,9 @@ class tg_grid(ctypes.Structure):
 class tg_options(ctypes.Structure):
     _fields_ = [("eta", c_double), ("m1", c_int), ("m2", c_int), ("precision", c_int),
                 ("flexible", c_int), ("max_iter", c_int), ("pointer_mode", c_int),
-                ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int)]
+                ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
+                ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
+                ("learned_max_iter", c_int)]
 
 
 class tg_report(ctypes.Structure):
@@ -44,7 +46,8 @@ class tg_report(ctypes.Structure):
                 ("coarse_unknowns", c_int), ("max_div_error", c_double),
                 ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double),
                 ("kernel_launches", c_int), ("smoother_launches", c_int), ("smoother_ms", c_double),
-                ("graph", c_int)]
+                ("graph", c_int), ("snapshot_solves", c_int), ("fallback_faces", c_int),
+                ("learned_fallback", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +84,16 @@ SIGNATURES = {
                                c_void_p]),
     "tg_batch_size": (c_int, [c_void_p, c_int_p, c_int_p]),
     "tg_destroy_batch": (None, [c_void_p]),
+    "tg_mlp_shape": (c_int, [c_int, c_int, c_int, c_int_p, c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "tg_mlp_create": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
+    "tg_mlp_params": (c_int, [c_void_p, c_void_p]),
+    "tg_mlp_forward": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "tg_mlp_loss_grad": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double_p, c_void_p]),
+    "tg_mlp_train": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, ctypes.c_float,
+                             c_void_p]),
+    "tg_mlp_destroy": (None, [c_void_p]),
+    "tg_face_data": (c_int, [c_void_p, ctypes.POINTER(tg_grid), c_double, c_int, c_void_p, c_void_p, c_void_p,
+                             c_void_p, c_void_p]),
 }
 
 
@@ -118,6 +131,8 @@ def _check(rc, where):
 
 
 def default_options(**kw):
+    """tg_default_options plus overrides; ``net`` takes an Mlp (or a raw
+    handle), ``face_profiles`` a device tensor."""
     o = tg_options()
     _check(lib().tg_default_options(ctypes.byref(o)), "tg_default_options")
     for k, v in kw.items():
@@ -125,6 +140,11 @@ def default_options(**kw):
             v = PREC[v]
         if k == "coarse_space" and isinstance(v, str):
             v = COARSE[v]
+        if k == "net":
+            v = getattr(v, "handle", v)
+            v = v.value if isinstance(v, ctypes.c_void_p) else v
+        if k == "face_profiles":
+            v = _ptr(v).value if v is not None else None
         setattr(o, k, v)
     return o
 
@@ -238,6 +258,66 @@ def tg_pressure_noalloc(kappa, ux, uy, p, n, stream=0):
     """Allocation-free pressure recovery (device tensors; see include/tgms.h)."""
     _check(lib().tg_pressure_noalloc(_ptr(kappa), _ptr(ux), _ptr(uy), _ptr(p), int(n),
                                      ctypes.c_void_p(stream)), "tg_pressure_noalloc")
+
+
+# ---------------------------------------------------------------- learned coarse basis
+def tg_mlp_shape(b, k, hidden):
+    din, dout, npar = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0)
+    _check(lib().tg_mlp_shape(int(b), int(k), int(hidden), ctypes.byref(din), ctypes.byref(dout),
+                              ctypes.byref(npar)), "tg_mlp_shape")
+    return din.value, dout.value, npar.value
+
+
+class Mlp:
+    """Owner of a tg_mlp handle.  Tensors are torch CUDA tensors: parameters
+    float32, inputs bfloat16 (passed as uint16 bit patterns), labels float32."""
+
+    def __init__(self, b, k, hidden, params, stream=0):
+        self.b, self.k, self.hidden = b, k, hidden
+        self.din, self.dout, self.nparam = tg_mlp_shape(b, k, hidden)
+        if params.numel() != self.nparam:
+            raise ValueError("parameter vector has %d entries, expected %d" % (params.numel(), self.nparam))
+        self.handle = ctypes.c_void_p()
+        _check(lib().tg_mlp_create(b, k, hidden, _ptr(params), ctypes.c_void_p(stream),
+                                   ctypes.byref(self.handle)), "tg_mlp_create")
+
+    def params(self, out):
+        _check(lib().tg_mlp_params(self.handle, _ptr(out)), "tg_mlp_params")
+        return out
+
+    def forward(self, x, y):
+        _check(lib().tg_mlp_forward(self.handle, int(x.shape[0]), _ptr(x), _ptr(y)), "tg_mlp_forward")
+        return y
+
+    def loss_grad(self, x, q, grad=None):
+        loss = ctypes.c_double(0.0)
+        _check(lib().tg_mlp_loss_grad(self.handle, int(x.shape[0]), _ptr(x), _ptr(q), ctypes.byref(loss),
+                                      _ptr(grad)), "tg_mlp_loss_grad")
+        return loss.value
+
+    def train(self, x, q, order, nsteps, batch, lr, loss_hist=None):
+        _check(lib().tg_mlp_train(self.handle, int(x.shape[0]), _ptr(x), _ptr(q), _ptr(order), int(nsteps),
+                                  int(batch), float(lr), _ptr(loss_hist)), "tg_mlp_train")
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().tg_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tg_face_data(kappa, n, b, eig_tol, k, x, q, nsel=None, lam=None, overlap=2, stream=0):
+    """Training data of one field (device tensors): x (faces x din, uint16 =
+    bfloat16 bits), q (faces x k x b float32), nsel (faces int32), lam
+    (faces x b float64)."""
+    g = tg_grid(n, n, b, b, overlap)
+    _check(lib().tg_face_data(_ptr(kappa), ctypes.byref(g), float(eig_tol), int(k), ctypes.c_void_p(stream),
+                              _ptr(x), _ptr(q), _ptr(nsel), _ptr(lam)), "tg_face_data")
 
 
 class Solver:

@@ -49,6 +49,19 @@ def test_host_only_calls(lib):
     for code in [0] + list(tgms.ERRORS):
         assert isinstance(tgms.tg_strerror(code), str) and tgms.tg_strerror(code)
     assert lib.tg_default_options(None) == -1
+    assert o.learned_k == 4 and o.learned_max_iter == 0 and not o.net and not o.face_profiles
+
+
+def test_network_shape_matches_the_oracle_layout(lib):
+    """tg_mlp_shape (host-only) agrees with the parameter layout of the oracle."""
+    from oracle.learned import input_shape, param_layout
+    from paper_1807_07220_gb300 import tgms
+    for b, k, hidden in ((16, 4, 512), (8, 4, 64), (2, 1, 3)):
+        R, C = input_shape(b)
+        _, total = param_layout(b, k, hidden)
+        assert tgms.tg_mlp_shape(b, k, hidden) == (R * C, k * b, total)
+    assert lib.tg_mlp_shape(17, 4, 8, None, None, None) == -1
+    assert lib.tg_mlp_shape(16, 9, 8, None, None, None) == -1
 
 
 def test_structs_match_header_layout():
@@ -57,6 +70,7 @@ def test_structs_match_header_layout():
     text = open(HEADER).read()
     for struct in (tgms.tg_grid, tgms.tg_options, tgms.tg_report):
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct.__name__, struct.__name__), text, re.S)
-        fields = re.findall(r"\b(?:int|double)\s+([^;]+);", re.sub(r"/\*.*?\*/", "", body.group(1), flags=re.S))
+        fields = re.findall(r"\b(?:const\s+)?(?:int|double|float|tg_mlp)\s*\*?\s*([A-Za-z_][^;]*);",
+                            re.sub(r"/\*.*?\*/", "", body.group(1), flags=re.S))
         names = [x.strip() for f in fields for x in f.split(",")]
         assert names == [f for f, _ in struct._fields_], struct.__name__

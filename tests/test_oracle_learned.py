@@ -159,7 +159,7 @@ def test_ritz_on_the_exact_span_reproduces_the_selection(channel_problem):
     for face in coarse_faces(g):
         a, s, (lam, c) = _spectral(g, kap, face, blocks, A, B, 10.0)
         G = np.zeros((g.b, 4))
-        G[:, :c.shape[1]] = np.linalg.qr(c)[0]
+        G[:, :c.shape[1]] = np.linalg.qr(np.sqrt(a)[:, None] * c)[0]      # whitened coordinates
         rl, rc, fb = L.ritz_select(G, a, s, 10.0)
         m = c.shape[1]
         np.testing.assert_allclose(rl[:m], lam[:m], rtol=1e-9)
@@ -177,7 +177,8 @@ def test_ritz_values_bound_the_eigenvalues_from_above(channel_problem):
         rl, _, _ = L.ritz_select(G, a, s, 1e300)
         assert rl.size == 3
         assert np.all(rl >= lam[:3] * (1 - 1e-10))
-        ref = sla.eigh(G.T @ (a[:, None] * G), G.T @ s @ G, eigvals_only=True)
+        Gg = G / np.sqrt(a)[:, None]                               # flux profiles of the span
+        ref = sla.eigh(Gg.T @ (a[:, None] * Gg), Gg.T @ s @ Gg, eigvals_only=True)
         np.testing.assert_allclose(rl, np.sort(ref), rtol=1e-9)
 
 
