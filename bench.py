@@ -303,16 +303,13 @@ def run_ours(args):
 # ---------------------------------------------------------------- batched workload
 def batch_specs(ninst, seed=2024):
     """64 instances: side n from {64, 128, 256, 512}, block b from {8, 16},
-    contrast 10^U(4, 6), own channel field; blocks are widened to 16 where
-    n / b would exceed 32 (the dense coarse inverse's range)."""
+    contrast 10^U(4, 6), own channel field."""
     import numpy as np
     rng = np.random.default_rng(seed)
     out = []
     for i in range(ninst):
         n = int(rng.choice([64, 128, 256, 512]))
         b = int(rng.choice([8, 16]))
-        if n // b > 32:
-            b = 16
         out.append((n, b, float(10.0 ** rng.uniform(4, 6)), 1000 + i))
     return out
 
@@ -383,8 +380,8 @@ def run_batch(args):
         "metric": METRIC + " (batched)", "value": total_dof / (ms / 1e3), "unit": "DOF-solves/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+%s" % prec, "data": "synthetic",
-        "config": {"workload": "%d instances x %d right-hand sides, n in {64,128,256,512}, b in {8,16} "
-                               "(n/b <= 32), channels at 10^U(4,6), random source/sink pair per rhs, "
+        "config": {"workload": "%d instances x %d right-hand sides, n in {64,128,256,512}, b in {8,16}, "
+                               "channels at 10^U(4,6), random source/sink pair per rhs, "
                                "one CUDA graph launch per step" % (len(specs), nrhs),
                    "instances": [[n, b] for (n, b, c, seed) in specs], "dof_per_step": total_dof},
         "iters_min_mean_max": [int(iters.min()), float(iters.mean()), int(iters.max())],
@@ -393,6 +390,82 @@ def run_batch(args):
         "sequential": {"value": total_dof / (seq_ms / 1e3), "ms_per_step": seq_ms,
                        "note": "same problems, one tg_solve graph launch each"},
         "speedup_vs_sequential": seq_ms / ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- learned coarse space
+def run_learned(args):
+    """Learned coarse space at 1024 x 1024 with 16 x 16 blocks: labels from the
+    exact spectral problems of ``--train-fields`` seeded fields, GPU training
+    with the library's kernels, then setup and solves on a held-out field with
+    the exact and the learned coarse space (BF16 preconditioner) and the plain
+    FP64 exact path."""
+    import numpy as np
+    import torch
+    from paper_1807_07220_gb300 import inputs, tgms
+    torch.cuda.set_device(0)
+    dev = "cuda"
+    n, b, k, hidden, tol = args.n, args.b, 4, args.hidden, EIG_TOL
+    stream = torch.cuda.current_stream().cuda_stream
+    nc = n // b
+    F = 2 * nc * (nc - 1)
+    din, dout, npar = tgms.tg_mlp_shape(b, k, hidden)
+    # ---- training data
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = torch.empty((args.train_fields * F, din), dtype=torch.bfloat16, device=dev)
+    Q = torch.empty((args.train_fields * F, k, b), dtype=torch.float32, device=dev)
+    for i in range(args.train_fields):
+        kap = torch.as_tensor(inputs.grf_channel_field(n, CONTRAST, 5000 + i), dtype=torch.float64, device=dev)
+        tgms.tg_face_data(kap, n, b, tol, k, X[i * F:(i + 1) * F], Q[i * F:(i + 1) * F], stream=stream)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    # ---- training
+    params = torch.as_tensor(inputs.mlp_init_params(din, dout, hidden, 17), device=dev)
+    net = tgms.Mlp(b, k, hidden, params, stream=stream)
+    nsteps, batch = args.train_steps, 1024
+    order = torch.as_tensor(inputs.sample_order(X.shape[0], nsteps, batch, 23), device=dev)
+    hist = torch.zeros(nsteps, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.train(X, Q, order, nsteps, batch, 1e-3, hist)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    h = hist.cpu().numpy()
+    # ---- held-out field
+    kappa, f = workload(n, 4242)
+    kd = torch.as_tensor(kappa, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    arms = {}
+    for name, kw in (("exact_bf16", dict(precision="bf16", flexible=1, coarse_space="gmsfem")),
+                     ("learned_bf16", dict(precision="bf16", flexible=1, coarse_space="learned", net=net)),
+                     ("exact_plain_f64", dict(precision="f64", flexible=0, coarse_space="gmsfem"))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = tgms.Solver(kd, b, tol, **kw)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        times, reps = time_solves(s, f, args.steps, args.warmup, flush, torch)
+        ms = statistics.mean(times)
+        r = reps[-1]
+        arms[name] = {"value": dof(n) / (ms / 1e3), "ms_per_solve": ms, "iters": r.iters, "setup_ms": setup_ms,
+                      "coarse_unknowns": r.coarse_unknowns, "velocity_basis": r.velocity_basis,
+                      "snapshot_solves": r.snapshot_solves, "fallback_faces": r.fallback_faces,
+                      "rel_residual": r.rel_residual}
+        s.close()
+    net.close()
+    line = {
+        "metric": METRIC + " (learned coarse space)", "value": arms["learned_bf16"]["value"], "unit": "DOF-solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms["learned_bf16"]["ms_per_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
+        "config": {"workload": workload_name(n, b) + "; network %d-%d-%d-%d trained on %d fields (%d faces)"
+                   % (din, hidden, hidden, dout, args.train_fields, X.shape[0]), "l2": "flushed between solves"},
+        "arms": arms, "faces": F,
+        "training": {"samples": int(X.shape[0]), "steps": nsteps, "batch": batch, "label_s": data_s,
+                     "train_s": train_s, "loss_first": float(h[:20].mean()), "loss_last": float(h[-50:].mean())},
+        "vs_exact_bf16": arms["learned_bf16"]["value"] / arms["exact_bf16"]["value"],
+        "vs_plain_f64": arms["learned_bf16"]["value"] / arms["exact_plain_f64"]["value"],
     }
     print(json.dumps(line), flush=True)
 
@@ -496,7 +569,10 @@ def main():
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned"])
+    ap.add_argument("--train-fields", type=int, default=25)
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--hidden", type=int, default=512)
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")
@@ -511,6 +587,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 
