@@ -40,8 +40,9 @@ METRIC = "fine DOF-solves/s to 1e-8 rel. residual vs plain FP64; PCG iters; HBM 
 N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
 # DRAM bytes (read + write) per smoother launch at the default workload, mean of
 # the fused and plain sweeps, from the ncu capture summarised in
-# profiles/k_smoother_256x256.md (valid for the kernel version profiled there)
-SMOOTHER_TRAFFIC = {"f32": 134.42e6, "bf16": 66.24e6}
+# profiles/k_smoother_256x256.md, keyed by (storage precision, tile shape);
+# valid only for the kernel version and shape profiled there
+SMOOTHER_TRAFFIC = {("f32", 0): 134.42e6, ("bf16", 0): 66.24e6}
 
 
 def dof(n):
@@ -190,11 +191,11 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
     prec = args.precision
 
-    def make(precision, flexible, profile=0, pointer_mode=1):
+    def make(precision, flexible, profile=0, pointer_mode=1, **kw):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = tgms.Solver(kappa, b, EIG_TOL, precision=precision, flexible=flexible, profile=profile,
-                        pointer_mode=pointer_mode)
+                        pointer_mode=pointer_mode, **kw)
         torch.cuda.synchronize()
         return s, (time.perf_counter() - t0) * 1e3
 
@@ -222,7 +223,8 @@ def run_ours(args):
         dist.barrier()
     head.close()
     # roofline of the dominant kernel (patch smoother): events around every launch
-    prof, _ = make(prec, 1, profile=1)
+    shape = reps[-1].smoother_shape
+    prof, _ = make(prec, 1, profile=1, smoother_shape=shape)
     _, prof_reps = time_solves(prof, f, args.steps, args.warmup, flush, torch)
     prof.close()
     sm_ms = sum(r.smoother_ms for r in prof_reps)
@@ -286,7 +288,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_smoother (patch inverse apply)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
-                     "traffic": SMOOTHER_TRAFFIC.get(prec),
+                     "traffic": SMOOTHER_TRAFFIC.get((prec, shape)),
+                     "tile_shape": shape, "autotuner_us_per_shape": reps[-1].shape_times(),
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None,
                      "launches_timed": sm_n, "peak_source": peak_src},
         "e2e": {"value": e_value, "unit": "DOF-solves/s", "ms_per_step": e_ms,

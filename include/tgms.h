@@ -105,6 +105,13 @@ typedef struct tg_options {
   const float* face_profiles;
   int learned_k;
   int learned_max_iter;
+  /* smoother tile shape: -1 = autotune at setup (time every shape on the
+   * handle's own patch inverses, keep the fastest); 0 = 16-byte loads, 4 rows
+   * per pass (2 for FP64 storage); 1 = 16-byte loads, 2 rows; 2 = 8-byte
+   * loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
+   * shared-memory ring.  FP64 storage runs shape 0 for 1..3.  Same arithmetic
+   * in every shape. */
+  int smoother_shape;
 } tg_options;
 
 typedef struct tg_report {
@@ -126,11 +133,13 @@ typedef struct tg_report {
   int snapshot_solves;    /* local block solves of the coarse-space setup (Section 4.1) */
   int fallback_faces;     /* TG_COARSE_LEARNED: faces that took the exact spectral problem */
   int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
+  int smoother_shape;     /* smoother tile shape in use */
+  float shape_us[5];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
  * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0, no
- * network or profiles, learned_k 4, learned_max_iter 0. */
+ * network or profiles, learned_k 4, learned_max_iter 0, smoother_shape -1. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything

@@ -57,6 +57,8 @@ struct tg_handle {
   int velocity_basis = 0;
   int snapshot_solves = 0;   // local block solves of the coarse-space setup
   int fallback_faces = 0;    // learned space: faces that took the exact problem
+  int shape = 0;             // smoother tile shape (autotuned or from the options)
+  float shape_us[kSmootherShapes] = {};   // autotuner: time per smoother launch of each shape (0: not tried)
   // coarse spaces: preconditioner and coarse RT0 (preprocessing)
   CoarseSpace cs, rt;
   int* h_flag = nullptr;    // pinned
@@ -362,12 +364,13 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
   for (int k = 0; k < h->opt.m1; ++k) {
     if (k == 0) {
       prof_mark(c, s);
-      launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s);
+      launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s,
+                                      h->shape);
       prof_mark(c, s);
     } else {
       launch_residual<TC>(r, zacc, kin, rin, n, st, s);
       prof_mark(c, s);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape);
       prof_mark(c, s);
     }
   }
@@ -379,7 +382,7 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r, zacc, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape);
     prof_mark(c, s);
   }
 }
@@ -452,12 +455,12 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
   prof_mark(c, s);
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
-                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s);
+                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape);
   prof_mark(c, s);
   for (int k = 1; k < h->opt.m1; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape);
     prof_mark(c, s);
   }
   if (h->cs.D > 0) {
@@ -468,7 +471,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape);
     prof_mark(c, s);
   }
   launch_pcg_dots<TC>(r_new, z_cur, c->q, c->part, st, n, s);
@@ -854,6 +857,67 @@ int setup_coarse(tg_handle* h, SpectralBufs& sb) {
   return rc;
 }
 
+// Smoother autotuner: times every tile shape on this handle's own patch
+// inverses (one warm-up and five timed launches each, CUDA events on the
+// handle's stream, scratch vectors of its own) and keeps the fastest.
+template <typename TC, typename TS>
+int autotune_smoother_t(tg_handle* h) {
+  const long long nn = (long long)h->n * h->n;
+  cudaStream_t s = h->stream;
+  TC *rin = nullptr, *z = nullptr;
+  if (dalloc(&rin, nn) || dalloc(&z, nn)) {
+    cudaFree(rin);
+    return TG_ERR_OOM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_err(cudaEventCreate(&e0));
+  if (!rc) rc = cuda_err(cudaEventCreate(&e1));
+  if (!rc) rc = cuda_err(cudaMemsetAsync(rin, 0, sizeof(TC) * nn, s));
+  if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
+  const bool f64 = std::is_same<TS, double>::value;
+  const int cand_all[] = {0, 1, 2, 3, 4}, cand_f64[] = {0, 4};
+  const int* cand = f64 ? cand_f64 : cand_all;
+  const int ncand = f64 ? 2 : 5;
+  float best = 1e30f;
+  int best_shape = 0;
+  for (int i = 0; i < ncand && !rc; ++i) {
+    const int shape = cand[i];
+    auto go = [&]() {
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rin, z,
+                                  h->opt.eta, h->n, nullptr, s, shape);
+    };
+    go();
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < 5; ++k) go();
+    cudaEventRecord(e1, s);
+    rc = cuda_err(cudaEventSynchronize(e1));
+    if (!rc) rc = cuda_err(cudaGetLastError());
+    float ms = 0.0f;
+    if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+    h->shape_us[shape] = ms * 1000.0f / 5.0f;
+    if (!rc && h->shape_us[shape] < best) {
+      best = h->shape_us[shape];
+      best_shape = shape;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(rin);
+  cudaFree(z);
+  if (!rc) h->shape = best_shape;
+  return rc;
+}
+
+int choose_smoother_shape(tg_handle* h) {
+  if (h->opt.smoother_shape >= 0) {
+    h->shape = h->opt.smoother_shape;
+    return TG_OK;
+  }
+  if (h->opt.precision == TG_PREC_F64) return autotune_smoother_t<double, double>(h);
+  if (h->opt.precision == TG_PREC_F32) return autotune_smoother_t<float, float>(h);
+  return autotune_smoother_t<float, __nv_bfloat16>(h);
+}
+
 int setup_impl(tg_handle* h, const double* kappa) {
   const long long nn = (long long)h->n * h->n;
   cudaStream_t s = h->stream;
@@ -902,6 +966,7 @@ int setup_impl(tg_handle* h, const double* kappa) {
   if (st) return status_to_err(st);
 
   configure_kernels(std::max(h->cs.D, h->rt.D));
+  if ((rc = choose_smoother_shape(h))) return rc;
   if ((rc = ctx_alloc(h, &h->ctx))) return rc;
   TG_CK(cudaStreamSynchronize(s));
   return cuda_err(cudaGetLastError());
@@ -944,7 +1009,7 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
   TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
   if (which == 0) {
     launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rho, zacc,
-                                    h->opt.eta, n, nullptr, h->stream);
+                                    h->opt.eta, n, nullptr, h->stream, h->shape);
   } else if (which == 1) {
     if (h->cs.D > 0) {
       TC* rin = (TC*)c->rin;
@@ -1038,6 +1103,7 @@ int tg_default_options(tg_options* opt) {
   opt->face_profiles = nullptr;
   opt->learned_k = 4;
   opt->learned_max_iter = 0;
+  opt->smoother_shape = -1;
   return TG_OK;
 }
 
@@ -1069,6 +1135,7 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
       !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
     return TG_ERR_INVALID_ARG;
   if (opt->m1 < 1) return TG_ERR_UNSUPPORTED;
+  if (opt->smoother_shape < -1 || opt->smoother_shape >= kSmootherShapes) return TG_ERR_INVALID_ARG;
   if (opt->coarse_space == TG_COARSE_LEARNED) {
     if (!opt->face_profiles && !opt->net) return TG_ERR_INVALID_ARG;
     if (opt->face_profiles && (opt->learned_k < 1 || opt->learned_k > 8)) return TG_ERR_INVALID_ARG;
@@ -1170,6 +1237,8 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
     rep->graph = h->opt.profile ? 0 : 1;
     rep->snapshot_solves = h->snapshot_solves;
     rep->fallback_faces = h->fallback_faces;
+    rep->smoother_shape = h->shape;
+    for (int k = 0; k < kSmootherShapes; ++k) rep->shape_us[k] = h->shape_us[k];
     float ms = 0;
     if (h->opt.profile) {
       cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);

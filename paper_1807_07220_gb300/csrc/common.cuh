@@ -187,14 +187,19 @@ template <typename TC>
 void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,
                         cudaStream_t s);
 
+// Smoother tile shapes (chosen per handle by the autotuner): 0 = 16-byte
+// loads, 4 rows per pass (2 for FP64); 1 = 16-byte loads, 2 rows; 2 = 8-byte
+// loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
+// shared-memory ring.  FP64 storage uses shape 0 for 1..3.
+constexpr int kSmootherShapes = 5;
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s);
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape = 0);
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s);
+                            cudaStream_t s, int shape = 0);
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);

@@ -9,6 +9,7 @@
 // scalars in the next kernel, so no CTA ever reads a value written in its own
 // launch.  Every kernel of the loop returns at once when PcgState::done is set.
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -449,6 +450,36 @@ __device__ __forceinline__ TC dot_chunk_smem(const __nv_bfloat16* m, const TC* x
 template <typename TS> struct RowsPerPass { static constexpr int R = 4; };
 template <> struct RowsPerPass<double> { static constexpr int R = 2; };
 
+// Register-staged smoother tiles: kCB bytes per lane load (8 or 16) and kR
+// rows reduced together per pass.  A 368-entry bfloat16 row is 46 16-byte
+// chunks (two passes of 32 lanes, 72% of the slots used) or 92 8-byte chunks
+// (three passes, 96%); the autotuner picks per handle.
+template <typename TS, int kCB> struct LdChunk;
+template <> struct LdChunk<double, 16> { using T = double2; };
+template <> struct LdChunk<float, 16> { using T = float4; };
+template <> struct LdChunk<float, 8> { using T = float2; };
+template <> struct LdChunk<__nv_bfloat16, 16> { using T = uint4; };
+template <> struct LdChunk<__nv_bfloat16, 8> { using T = uint2; };
+template <typename TS, int kCB>
+__device__ __forceinline__ typename LdChunk<TS, kCB>::T load_tile(const TS* m) {
+  return __ldg(reinterpret_cast<const typename LdChunk<TS, kCB>::T*>(m));
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_raw(const float2& v, const TC* x) {
+  return (TC)(v.x * x[0] + v.y * x[1]);
+}
+template <typename TC>
+__device__ __forceinline__ TC dot_raw(const uint2& v, const TC* x) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+  TC acc = (TC)0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    acc += f.x * x[2 * k] + f.y * x[2 * k + 1];
+  }
+  return acc;
+}
+
 template <typename TC>
 __device__ __forceinline__ TC dot_chunk(const double* m, const TC* x) {
   const double2 v = *reinterpret_cast<const double2*>(m);
@@ -497,7 +528,7 @@ struct FuseArgs {
   int nc, b;
 };
 
-template <typename TC, typename TS, typename TR, bool kFused>
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
                                                        const int* __restrict__ gofs, int npatch,
                                                        const TS* __restrict__ pinv,
@@ -518,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
     if (gofs[mid] <= g0) p = mid;
     else hi = mid - 1;
   }
-  constexpr int W = Vec<TS>::W;
+  constexpr int W = kCB / (int)sizeof(TS);
   constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
@@ -547,8 +578,8 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
     __syncthreads();
     const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
     const TS* M = pinv + g.off;
-    constexpr int R = RowsPerPass<TS>::R;
-    using V = typename Chunk<TS>::T;
+    constexpr int R = kR;
+    using V = typename LdChunk<TS, kCB>::T;
     for (int grp = ga + warp; grp < gb; grp += nw) {
 #pragma unroll
       for (int pass = 0; pass < kRowsPerWarp / R; ++pass) {
@@ -560,7 +591,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
           const int col = (it * 32 + lane) * W;
 #pragma unroll
           for (int k = 0; k < R; ++k) {
-            if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_chunk<TS>(M + (long long)(row0 + k) * g.ld + col);
+            if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_tile<TS, kCB>(M + (long long)(row0 + k) * g.ld + col);
             else buf[k][it] = V{};
           }
         }
@@ -1034,20 +1065,20 @@ int sm_count() {
 }
 
 // resident CTAs per SM of a smoother instantiation (queried once, at setup)
-template <typename TC, typename TS, typename TR>
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
 int smoother_per_sm() {
   static int per_sm = 0;
   if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR, false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR, kFused, kCB, kR>, kThreads, 0);
     if (per_sm <= 0) per_sm = 1;
   }
   return per_sm;
 }
 
-template <typename TC, typename TS, typename TR>
-int smoother_grid(int ngroups) {
-  int grid = smoother_per_sm<TC, TS, TR>() * sm_count();
-  const int min_groups_per_cta = 8;   // keep every warp busy with at least one group
+// one wave of CTAs, but at least 8 row groups per CTA (every warp busy)
+inline int wave_grid(int per_sm, int ngroups) {
+  int grid = per_sm * sm_count();
+  const int min_groups_per_cta = 8;
   if (grid * min_groups_per_cta > ngroups) grid = (ngroups + min_groups_per_cta - 1) / min_groups_per_cta;
   return grid < 1 ? 1 : grid;
 }
@@ -1068,52 +1099,82 @@ int tma_per_sm() {
   return per_sm;
 }
 
-int g_use_tma = 0;   // smoother streaming through TMA bulk copies (0: register-staged loads)
+// Smoother tile shapes: 0 = 16-byte loads, default rows per pass (4; 2 for
+// FP64); 1 = 16-byte loads, 2 rows; 2 = 8-byte loads, 4 rows; 3 = 8-byte
+// loads, 2 rows; 4 = TMA bulk copies into a shared-memory ring.  FP64 storage
+// has shapes 0 and 4 only (others map to 0).
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
+void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
+                 TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa, cudaStream_t s) {
+  const int grid = wave_grid(smoother_per_sm<TC, TS, TR, kFused, kCB, kR>(), ngroups);
+  k_smoother<TC, TS, TR, kFused, kCB, kR><<<grid, kThreads, 0, s>>>(geo, gofs, npatch, pinv, r, zacc, (TC)eta, n,
+                                                                     st, fa);
+}
+
+template <typename TC, typename TS, typename TR, bool kFused>
+void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                    const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
+                    cudaStream_t s) {
+  TG_COUNT(1);
+  if (shape == 4) {
+    int grid = tma_per_sm<TC, TS, TR, kFused>() * sm_count();
+    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
+    k_smoother_tma<TC, TS, TR, kFused><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
+        geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
+    return;
+  }
+  if constexpr (std::is_same<TS, double>::value) {
+    smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s);
+  } else {
+    switch (shape) {
+      case 1: smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
+      case 2: smoother_go<TC, TS, TR, kFused, 8, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
+      case 3: smoother_go<TC, TS, TR, kFused, 8, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
+      default: smoother_go<TC, TS, TR, kFused, 16, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
+    }
+  }
+}
+
+// occupancy queries of every shape of one instantiation (outside any capture)
+template <typename TC, typename TS, typename TR, bool kFused>
+void smoother_prepare() {
+  tma_per_sm<TC, TS, TR, kFused>();
+  if constexpr (std::is_same<TS, double>::value) {
+    smoother_per_sm<TC, TS, TR, kFused, 16, 2>();
+  } else {
+    smoother_per_sm<TC, TS, TR, kFused, 16, 4>();
+    smoother_per_sm<TC, TS, TR, kFused, 16, 2>();
+    smoother_per_sm<TC, TS, TR, kFused, 8, 4>();
+    smoother_per_sm<TC, TS, TR, kFused, 8, 2>();
+  }
+}
 
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s) {
-  TG_COUNT(1);
-  if (g_use_tma) {
-    int grid = tma_per_sm<TC, TS, TR, false>() * sm_count();
-    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
-    k_smoother_tma<TC, TS, TR, false><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
-        geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), FuseArgs{});
-    return;
-  }
-  k_smoother<TC, TS, TR, false><<<smoother_grid<TC, TS, TR>(ngroups), kThreads, 0, s>>>(
-      geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st, FuseArgs{});
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape) {
+  smoother_shape<TC, TS, TR, false>(shape, geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, FuseArgs{}, s);
 }
 
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s) {
-  TG_COUNT(1);
+                            cudaStream_t s, int shape) {
   FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b};
-  if (g_use_tma) {
-    int grid = tma_per_sm<TC, TS, double, true>() * sm_count();
-    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
-    k_smoother_tma<TC, TS, double, true><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
-        geo, gofs, npatch, pinv, r_old, zacc, (TC)eta, n, st, fa);
-    return;
-  }
-  k_smoother<TC, TS, double, true><<<smoother_grid<TC, TS, double>(ngroups), kThreads, 0, s>>>(
-      geo, gofs, npatch, pinv, r_old, zacc, (TC)eta, n, st, fa);
+  smoother_shape<TC, TS, double, true>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa, s);
 }
 template void launch_smoother_update<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                      const double*, double*, const double*, double*,
                                                      const double*, double*, double, int, int, int, double*,
-                                                     PcgState*, cudaStream_t);
+                                                     PcgState*, cudaStream_t, int);
 template void launch_smoother_update<float, float>(const PatchGeo*, const int*, int, int, const float*,
                                                    const double*, double*, const double*, double*,
                                                    const double*, float*, double, int, int, int, double*,
-                                                   PcgState*, cudaStream_t);
+                                                   PcgState*, cudaStream_t, int);
 template void launch_smoother_update<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
                                                            const __nv_bfloat16*, const double*, double*,
                                                            const double*, double*, const double*, float*, double,
-                                                           int, int, int, double*, PcgState*, cudaStream_t);
+                                                           int, int, int, double*, PcgState*, cudaStream_t, int);
 
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
@@ -1128,15 +1189,15 @@ template void launch_pcg_apply_p<float>(const float*, const double*, double*, do
                                         double*, PcgState*, int, cudaStream_t);
 
 template void launch_smoother<double, double, double>(const PatchGeo*, const int*, int, int, const double*, const double*, double*,
-                                      double, int, const PcgState*, cudaStream_t);
+                                      double, int, const PcgState*, cudaStream_t, int);
 template void launch_smoother<float, float, double>(const PatchGeo*, const int*, int, int, const float*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t);
+                                      double, int, const PcgState*, cudaStream_t, int);
 template void launch_smoother<float, float, float>(const PatchGeo*, const int*, int, int, const float*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t);
+                                      double, int, const PcgState*, cudaStream_t, int);
 template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t);
+                                      double, int, const PcgState*, cudaStream_t, int);
 template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t);
+                                      double, int, const PcgState*, cudaStream_t, int);
 
 template <typename TC, typename TS>
 void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,
@@ -1159,8 +1220,7 @@ void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, i
   k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, part, nc, b, n, st);
 }
 int sm_count();
-template <typename TC, typename TS, typename TR> int smoother_per_sm();
-template <typename TC, typename TS, typename TR, bool kFused> int tma_per_sm();
+template <typename TC, typename TS, typename TR, bool kFused> void smoother_prepare();
 int read_and_clear_timeout() {
   int v = 0;
   cudaMemcpyFromSymbol(&v, g_timeout_flag, sizeof(int));
@@ -1172,25 +1232,15 @@ int read_and_clear_timeout() {
 }
 
 void configure_kernels(int max_coarse_dim) {
-  // smoother streaming: register-staged loads (default, measured faster on
-  // GB300) or TMA bulk copies into a shared-memory ring (TGMS_SMOOTHER=tma);
-  // a tuning switch, same arithmetic
-  const char* v = getenv("TGMS_SMOOTHER");
-  g_use_tma = (v && v[0] == 't') ? 1 : 0;
   sm_count();
-  tma_per_sm<double, double, double, false>();
-  tma_per_sm<float, float, double, false>();
-  tma_per_sm<float, float, float, false>();
-  tma_per_sm<float, __nv_bfloat16, double, false>();
-  tma_per_sm<float, __nv_bfloat16, float, false>();
-  tma_per_sm<double, double, double, true>();
-  tma_per_sm<float, float, double, true>();
-  tma_per_sm<float, __nv_bfloat16, double, true>();
-  smoother_per_sm<double, double, double>();
-  smoother_per_sm<float, float, double>();
-  smoother_per_sm<float, float, float>();
-  smoother_per_sm<float, __nv_bfloat16, double>();
-  smoother_per_sm<float, __nv_bfloat16, float>();
+  smoother_prepare<double, double, double, false>();
+  smoother_prepare<float, float, double, false>();
+  smoother_prepare<float, float, float, false>();
+  smoother_prepare<float, __nv_bfloat16, double, false>();
+  smoother_prepare<float, __nv_bfloat16, float, false>();
+  smoother_prepare<double, double, double, true>();
+  smoother_prepare<float, float, double, true>();
+  smoother_prepare<float, __nv_bfloat16, double, true>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
   if (shm > 48 * 1024)
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

@@ -103,6 +103,49 @@ def test_preconditioner_parts(case, tg, which):
     assert rel(got, ref) < 1e-9, (case["name"], which, rel(got, ref))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_smoother_tile_shapes(tg, prec):
+    """Every smoother tile shape (16- or 8-byte loads, 2 or 4 rows per pass,
+    TMA ring) computes the same smoother: against shape 0 to FP32 summation
+    order (same stored inverses), against the oracle to the storage
+    precision; a solve with each shape matches the direct solve; the
+    autotuner reports a timed shape."""
+    n, b, kf = CASES["32x32_b8_channels"]
+    kappa = kf(n)
+    o = TwoGridSolver(n, b, kappa, tol=10.0)
+    rng = np.random.default_rng(12)
+    r = o.project(rng.standard_normal(o.If.size))
+    rho = dev(psi_from_interior(n, o.C.T @ r))
+    ref = o.smoother(r)
+    f = inputs.quarter_five_spot(n)
+    u_ref, _ = solve_direct(Grid(n, b), kappa, f)
+    tol_oracle = {"f64": 1e-9, "f32": 2e-5, "bf16": 2e-2}[prec]
+    outs = {}
+    for shape in range(5):
+        s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), smoother_shape=shape)
+        try:
+            z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+            tg.tg_apply_smoother(s.h, rho, z)
+            outs[shape] = o.C @ interior_from_psi(n, z.cpu().numpy())
+            assert rel(outs[shape], ref) < tol_oracle, (prec, shape, rel(outs[shape], ref))
+            it, rep = s.solve(f, rtol=1e-12)
+            got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+            assert rel(got_u, u_ref) < 1e-8 and rep.smoother_shape == shape
+        finally:
+            s.close()
+    for shape in range(1, 5):
+        assert rel(outs[shape], outs[0]) < (1e-12 if prec == "f64" else 2e-6), (prec, shape)
+    s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"))
+    try:
+        it, rep = s.solve(f, rtol=1e-8)
+        times = rep.shape_times()
+        tried = [0, 4] if prec == "f64" else [0, 1, 2, 3, 4]
+        assert all(times[k] > 0 for k in tried)
+        assert rep.smoother_shape in tried and times[rep.smoother_shape] == min(times[k] for k in tried)
+    finally:
+        s.close()
+
+
 def test_spectra_and_selection(case, tg):
     o, s, b = case["oracle"], case["solver"], case["b"]
     nsel, lam, vb = tg.tg_coarse_info(s.h, b)

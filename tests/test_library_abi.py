@@ -72,5 +72,5 @@ def test_structs_match_header_layout():
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct.__name__, struct.__name__), text, re.S)
         fields = re.findall(r"\b(?:const\s+)?(?:int|double|float|tg_mlp)\s*\*?\s*([A-Za-z_][^;]*);",
                             re.sub(r"/\*.*?\*/", "", body.group(1), flags=re.S))
-        names = [x.strip() for f in fields for x in f.split(",")]
+        names = [re.sub(r"\[.*\]", "", x).strip() for f in fields for x in f.split(",")]
         assert names == [f for f, _ in struct._fields_], struct.__name__
