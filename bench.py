@@ -203,10 +203,14 @@ def run_ours(args):
     plain, plain_setup_ms = make("f64", 0)
     p_times, p_reps = time_solves(plain, f, args.steps, args.warmup, flush, torch)
     plain.close()
-    other = "f32" if prec == "bf16" else "bf16"
-    oth, oth_setup_ms = make(other, 1)
-    o_times, o_reps = time_solves(oth, f, args.steps, args.warmup, flush, torch)
-    oth.close()
+    others = {}
+    for other in ("f32", "bf16", "f16"):
+        if other == prec:
+            continue
+        oth, oth_setup_ms = make(other, 1)
+        o_times, o_reps = time_solves(oth, f, args.steps, args.warmup, flush, torch)
+        oth.close()
+        others[other] = (o_times, o_reps, oth_setup_ms)
     # headline mixed-precision arm, timed region with clock sampling
     head, setup_ms = make(prec, 1)
     for _ in range(args.warmup):
@@ -229,7 +233,7 @@ def run_ours(args):
     prof.close()
     sm_ms = sum(r.smoother_ms for r in prof_reps)
     sm_n = sum(r.smoother_launches for r in prof_reps)
-    ts_bytes = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    ts_bytes = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[prec]
     tc_bytes = 8 if prec == "f64" else 4
     alg_bytes = smoother_bytes(n, b, 2, ts_bytes, tc_bytes)
     # end to end through the host-pointer ABI (copies inside the timed call)
@@ -261,7 +265,11 @@ def run_ours(args):
 
     value, ms_step = agg(times)
     p_value, p_ms = agg(p_times)
-    o_value, o_ms = agg(o_times)
+    other_arms = {}
+    for other, (o_times, o_reps, oth_setup_ms) in others.items():
+        o_value, o_ms = agg(o_times)
+        other_arms[other] = {"value": o_value, "ms_per_step": o_ms, "iters": o_reps[-1].iters,
+                             "setup_ms": oth_setup_ms, "tile_shape": o_reps[-1].smoother_shape}
     e_value, e_ms = agg(e2e_t)
     if rank != 0:
         if dist:
@@ -281,7 +289,7 @@ def run_ours(args):
         "coarse_dim": reps[-1].coarse_dim, "setup_ms": setup_ms,
         "plain_f64": {"value": p_value, "ms_per_step": p_ms, "iters": p_reps[-1].iters,
                       "setup_ms": plain_setup_ms},
-        other: {"value": o_value, "ms_per_step": o_ms, "iters": o_reps[-1].iters, "setup_ms": oth_setup_ms},
+        "other_precisions": other_arms,
         "speedup_vs_plain_f64": value / p_value,
         "gpu_launches": sum(r.kernel_launches for r in reps),
         "gpu_launches_per_step": reps[-1].kernel_launches,
@@ -441,8 +449,9 @@ def run_learned(args):
     kd = torch.as_tensor(kappa, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     arms = {}
-    for name, kw in (("exact_bf16", dict(precision="bf16", flexible=1, coarse_space="gmsfem")),
-                     ("learned_bf16", dict(precision="bf16", flexible=1, coarse_space="learned", net=net)),
+    lp = args.learned_precision
+    for name, kw in (("exact_" + lp, dict(precision=lp, flexible=1, coarse_space="gmsfem")),
+                     ("learned_" + lp, dict(precision=lp, flexible=1, coarse_space="learned", net=net)),
                      ("exact_plain_f64", dict(precision="f64", flexible=0, coarse_space="gmsfem"))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -459,16 +468,16 @@ def run_learned(args):
         s.close()
     net.close()
     line = {
-        "metric": METRIC + " (learned coarse space)", "value": arms["learned_bf16"]["value"], "unit": "DOF-solves/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms["learned_bf16"]["ms_per_solve"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
+        "metric": METRIC + " (learned coarse space)", "value": arms["learned_" + lp]["value"], "unit": "DOF-solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms["learned_" + lp]["ms_per_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + lp, "data": "synthetic",
         "config": {"workload": workload_name(n, b) + "; network %d-%d-%d-%d trained on %d fields (%d faces)"
                    % (din, hidden, hidden, dout, args.train_fields, X.shape[0]), "l2": "flushed between solves"},
         "arms": arms, "faces": F,
         "training": {"samples": int(X.shape[0]), "steps": nsteps, "batch": batch, "label_s": data_s,
                      "train_s": train_s, "loss_first": float(h[:20].mean()), "loss_last": float(h[-50:].mean())},
-        "vs_exact_bf16": arms["learned_bf16"]["value"] / arms["exact_bf16"]["value"],
-        "vs_plain_f64": arms["learned_bf16"]["value"] / arms["exact_plain_f64"]["value"],
+        "vs_exact_same_precision": arms["learned_" + lp]["value"] / arms["exact_" + lp]["value"],
+        "vs_plain_f64": arms["learned_" + lp]["value"] / arms["exact_plain_f64"]["value"],
     }
     print(json.dumps(line), flush=True)
 
@@ -570,12 +579,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--b", type=int, default=B_DEFAULT)
-    ap.add_argument("--precision", default="bf16", choices=["f32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "learned"])
     ap.add_argument("--train-fields", type=int, default=25)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--learned-precision", default="f16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")

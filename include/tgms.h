@@ -63,6 +63,10 @@ extern "C" {
 #define TG_PREC_F64  0
 #define TG_PREC_F32  1
 #define TG_PREC_BF16 2   /* BF16 storage, FP32 arithmetic */
+#define TG_PREC_F16  3   /* FP16 patch inverses, each row scaled by a power of two that puts its
+                            largest magnitude in [2^14, 2^15) (the factor is undone after the row's
+                            FP32 dot product); FP32 coarse tiles; FP32 arithmetic.  Same bytes as
+                            BF16 with three more mantissa bits. */
 
 #define TG_PTR_HOST   0
 #define TG_PTR_DEVICE 1
@@ -109,8 +113,8 @@ typedef struct tg_options {
    * handle's own patch inverses, keep the fastest); 0 = 16-byte loads, 4 rows
    * per pass (2 for FP64 storage); 1 = 16-byte loads, 2 rows; 2 = 8-byte
    * loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
-   * shared-memory ring.  FP64 storage runs shape 0 for 1..3.  Same arithmetic
-   * in every shape. */
+   * shared-memory ring.  FP64 storage runs shape 0 for 1..3, FP16 storage
+   * shape 0 for 4.  Same arithmetic in every shape. */
   int smoother_shape;
 } tg_options;
 

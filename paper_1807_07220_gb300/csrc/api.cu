@@ -44,6 +44,7 @@ struct tg_handle {
   int* d_gofs = nullptr;    // first row group of each patch (+ total)
   int ngroups = 0;
   void* pinv = nullptr;
+  float* rscale = nullptr;  // FP16 storage: inverse row scales
   // block factors (snapshots) and dense block inverses (preprocessing)
   double* blk_band = nullptr;
   PatchGeo* d_bgeo = nullptr;
@@ -117,8 +118,12 @@ void free_space(CoarseSpace& c) {
   c = CoarseSpace{};
 }
 
+// bytes per stored patch-inverse entry and per coarse-tile entry
 size_t ts_size(int precision) {
   return precision == TG_PREC_F64 ? 8 : precision == TG_PREC_F32 ? 4 : 2;
+}
+size_t tile_size(int precision) {
+  return precision == TG_PREC_F64 ? 8 : precision == TG_PREC_BF16 ? 2 : 4;
 }
 
 int status_to_err(int st) {
@@ -187,7 +192,7 @@ int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool
   c.max_slots_per_block = 0;
   for (int blk = 0; blk < h->nblocks; ++blk)
     c.max_slots_per_block = std::max(c.max_slots_per_block, ptr[blk + 1] - ptr[blk]);
-  const size_t ts = ts_size(h->opt.precision);
+  const size_t ts = tile_size(h->opt.precision);
   if (dalloc(&c.slot_ptr, ptr.size()) || dalloc(&c.slots, slots.size()) || dalloc(&c.gather, gather.size()) ||
       dalloc(&c.closed, (size_t)c.nslots * (b + 1) * (b + 1)) || dalloc(&c.Kinv, (size_t)c.D * c.D))
     return TG_ERR_OOM;
@@ -210,7 +215,7 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
   if (c.nslots > 0) {
     if (rt_only || h->opt.precision == TG_PREC_F64)
       launch_build_tiles<double>(c, psiS, fcoef, zcoef, jeff, rt_only ? 1 : 0, n, b, h->stream);
-    else if (h->opt.precision == TG_PREC_F32)
+    else if (h->opt.precision == TG_PREC_F32 || h->opt.precision == TG_PREC_F16)
       launch_build_tiles<float>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
     else
       launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
@@ -365,24 +370,24 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
     if (k == 0) {
       prof_mark(c, s);
       launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s,
-                                      h->shape);
+                                      h->shape, h->rscale);
       prof_mark(c, s);
     } else {
       launch_residual<TC>(r, zacc, kin, rin, n, st, s);
       prof_mark(c, s);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape, h->rscale);
       prof_mark(c, s);
     }
   }
   if (h->cs.D > 0) {
-    launch_resid_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
+    launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
     launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
-    launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
+    launch_prolong<TC, tile_t<TS>>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r, zacc, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape, h->rscale);
     prof_mark(c, s);
   }
 }
@@ -455,23 +460,23 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
   prof_mark(c, s);
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
-                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape);
+                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale);
   prof_mark(c, s);
   for (int k = 1; k < h->opt.m1; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape, h->rscale);
     prof_mark(c, s);
   }
   if (h->cs.D > 0) {
-    launch_resid_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
+    launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
     launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
-    launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
+    launch_prolong<TC, tile_t<TS>>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape, h->rscale);
     prof_mark(c, s);
   }
   launch_pcg_dots<TC>(r_new, z_cur, c->q, c->part, st, n, s);
@@ -529,6 +534,7 @@ int add_chain(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
   switch (c->h->opt.precision) {
     case TG_PREC_F64: return add_chain_t<double, double>(c, graph, cs);
     case TG_PREC_F32: return add_chain_t<float, float>(c, graph, cs);
+    case TG_PREC_F16: return add_chain_t<float, __half>(c, graph, cs);
     default: return add_chain_t<float, __nv_bfloat16>(c, graph, cs);
   }
 }
@@ -560,6 +566,7 @@ int run_loop(Ctx* c, unsigned long long* launches) {
   switch (c->h->opt.precision) {
     case TG_PREC_F64: return run_loop_t<double, double>(c, launches);
     case TG_PREC_F32: return run_loop_t<float, float>(c, launches);
+    case TG_PREC_F16: return run_loop_t<float, __half>(c, launches);
     default: return run_loop_t<float, __nv_bfloat16>(c, launches);
   }
 }
@@ -622,6 +629,7 @@ int setup_patches(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
   const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
   if (!rc) rc = dalloc(&scratch, (size_t)batch * nmax * nmax);
+  if (!rc && h->opt.precision == TG_PREC_F16) rc = dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup);
   if (!rc) {
     launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
     launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
@@ -632,6 +640,8 @@ int setup_patches(tg_handle* h) {
         launch_store_inverse<double>(scratch, h->d_pgeo, first, cnt, nmax, (double*)h->pinv, s);
       else if (h->opt.precision == TG_PREC_F32)
         launch_store_inverse<float>(scratch, h->d_pgeo, first, cnt, nmax, (float*)h->pinv, s);
+      else if (h->opt.precision == TG_PREC_F16)
+        launch_store_inverse_f16(scratch, h->d_pgeo, h->d_gofs, first, cnt, nmax, (__half*)h->pinv, h->rscale, s);
       else
         launch_store_inverse<__nv_bfloat16>(scratch, h->d_pgeo, first, cnt, nmax, (__nv_bfloat16*)h->pinv, s);
     }
@@ -874,17 +884,17 @@ int autotune_smoother_t(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaEventCreate(&e1));
   if (!rc) rc = cuda_err(cudaMemsetAsync(rin, 0, sizeof(TC) * nn, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
-  const bool f64 = std::is_same<TS, double>::value;
+  const bool f64 = std::is_same<TS, double>::value, f16 = std::is_same<TS, __half>::value;
   const int cand_all[] = {0, 1, 2, 3, 4}, cand_f64[] = {0, 4};
   const int* cand = f64 ? cand_f64 : cand_all;
-  const int ncand = f64 ? 2 : 5;
+  const int ncand = f64 ? 2 : f16 ? 4 : 5;   // FP16: no TMA ring
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {
     const int shape = cand[i];
     auto go = [&]() {
       launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rin, z,
-                                  h->opt.eta, h->n, nullptr, s, shape);
+                                  h->opt.eta, h->n, nullptr, s, shape, h->rscale);
     };
     go();
     cudaEventRecord(e0, s);
@@ -911,10 +921,12 @@ int autotune_smoother_t(tg_handle* h) {
 int choose_smoother_shape(tg_handle* h) {
   if (h->opt.smoother_shape >= 0) {
     h->shape = h->opt.smoother_shape;
+    if (h->opt.precision == TG_PREC_F16 && h->shape == 4) h->shape = 0;   // no TMA ring for FP16
     return TG_OK;
   }
   if (h->opt.precision == TG_PREC_F64) return autotune_smoother_t<double, double>(h);
   if (h->opt.precision == TG_PREC_F32) return autotune_smoother_t<float, float>(h);
+  if (h->opt.precision == TG_PREC_F16) return autotune_smoother_t<float, __half>(h);
   return autotune_smoother_t<float, __nv_bfloat16>(h);
 }
 
@@ -1009,7 +1021,7 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
   TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
   if (which == 0) {
     launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rho, zacc,
-                                    h->opt.eta, n, nullptr, h->stream, h->shape);
+                                    h->opt.eta, n, nullptr, h->stream, h->shape, h->rscale);
   } else if (which == 1) {
     if (h->cs.D > 0) {
       TC* rin = (TC*)c->rin;
@@ -1017,9 +1029,9 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
         TG_CK(cudaMemcpyAsync(rin, rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
       else
         launch_convert<double, float>(rho, (float*)rin, nn, h->stream);
-      launch_restrict<TC, TS>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, rin, nullptr, h->stream);
+      launch_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, rin, nullptr, h->stream);
       launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, nullptr, h->stream);
-      launch_prolong<TC, TS>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
+      launch_prolong<TC, tile_t<TS>>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, nullptr, h->stream);
     }
   } else {
     precondition<TC, TS>(c, rho, zacc, nullptr, h->stream);
@@ -1038,6 +1050,7 @@ int hook_dispatch(tg_handle* h, const double* rho, double* z, int which) {
   switch (h->opt.precision) {
     case TG_PREC_F64: return hook_precond<double, double>(h, rho, z, which);
     case TG_PREC_F32: return hook_precond<float, float>(h, rho, z, which);
+    case TG_PREC_F16: return hook_precond<float, __half>(h, rho, z, which);
     default: return hook_precond<float, __nv_bfloat16>(h, rho, z, which);
   }
 }
@@ -1131,7 +1144,7 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
   int rc = validate_grid(grid);
   if (rc) return rc;
   if (!(opt->eta > 0) || opt->m1 < 0 || opt->m2 < 0 || opt->m1 + opt->m2 < 1 || opt->max_iter < 1 ||
-      opt->precision < 0 || opt->precision > 2 || opt->coarse_space < 0 || opt->coarse_space > 3 ||
+      opt->precision < 0 || opt->precision > 3 || opt->coarse_space < 0 || opt->coarse_space > 3 ||
       !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
     return TG_ERR_INVALID_ARG;
   if (opt->m1 < 1) return TG_ERR_UNSUPPORTED;
@@ -1292,7 +1305,7 @@ void tg_destroy(tg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   ctx_free(h->ctx);
-  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->blk_band, h->lam,
+  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->rscale, h->blk_band, h->lam,
                   h->d_bgeo, h->d_bgofs, h->binv, h->kcoef};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);

@@ -17,6 +17,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
 
@@ -105,6 +106,13 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(doubl
   return __float2bfloat16_rn((float)x);
 }
 
+// Coarse basis tiles are stored in the preconditioner precision, except with
+// FP16 patch inverses, whose tiles stay FP32 (they are a small fraction of the
+// bytes and carry no row scale).
+template <typename TS> struct TileOf { using T = TS; };
+template <> struct TileOf<__half> { using T = float; };
+template <typename TS> using tile_t = typename TileOf<TS>::T;
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -192,14 +200,17 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 // loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
 // shared-memory ring.  FP64 storage uses shape 0 for 1..3.
 constexpr int kSmootherShapes = 5;
+// rscale: FP16 storage only, one power-of-two factor per stored row (index
+// gofs[p] * kRowsPerGroup + row) that undoes the row's scaling.
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape = 0);
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape = 0,
+                     const float* rscale = nullptr);
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape = 0);
+                            cudaStream_t s, int shape = 0, const float* rscale = nullptr);
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);
@@ -251,6 +262,10 @@ void launch_band_inverse(const double* band, const int4* rects, int first, int c
 template <typename TS>
 void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count,
                           int nmax, TS* pinv, cudaStream_t s);
+// FP16 storage: each row scaled by a power of two that puts its largest
+// magnitude in [2^14, 2^15); rscale receives the inverse factor
+void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const int* gofs, int first, int count,
+                              int nmax, __half* pinv, float* rscale, cudaStream_t s);
 // Snapshot functions of every (block, side): nfn functions per side whose
 // coefficient vectors over {m, d_1..d_{b-1}} are coef[face][fn][0..b-1]
 // (coef NULL: the unit vectors, nfn = b).  Sides with mask[blk*4+side] == 0

@@ -460,6 +460,8 @@ template <> struct LdChunk<float, 16> { using T = float4; };
 template <> struct LdChunk<float, 8> { using T = float2; };
 template <> struct LdChunk<__nv_bfloat16, 16> { using T = uint4; };
 template <> struct LdChunk<__nv_bfloat16, 8> { using T = uint2; };
+template <> struct LdChunk<__half, 16> { using T = uint4; };
+template <> struct LdChunk<__half, 8> { using T = uint2; };
 template <typename TS, int kCB>
 __device__ __forceinline__ typename LdChunk<TS, kCB>::T load_tile(const TS* m) {
   return __ldg(reinterpret_cast<const typename LdChunk<TS, kCB>::T*>(m));
@@ -478,6 +480,24 @@ __device__ __forceinline__ TC dot_raw(const uint2& v, const TC* x) {
     acc += f.x * x[2 * k] + f.y * x[2 * k + 1];
   }
   return acc;
+}
+// FP16 chunks (8 or 4 halves), products in FP32
+template <typename TC, typename V>
+__device__ __forceinline__ TC dot_half(const V& v, const TC* x) {
+  constexpr int P = (int)(sizeof(V) / sizeof(__half2));
+  const __half2* h = reinterpret_cast<const __half2*>(&v);
+  TC acc = (TC)0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const float2 f = __half22float2(h[k]);
+    acc += f.x * x[2 * k] + f.y * x[2 * k + 1];
+  }
+  return acc;
+}
+template <typename TS, typename TC, typename V>
+__device__ __forceinline__ TC dot_tile(const V& v, const TC* x) {
+  if constexpr (std::is_same<TS, __half>::value) return dot_half<TC>(v, x);
+  else return dot_raw<TC>(v, x);
 }
 
 template <typename TC>
@@ -534,7 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
                                                        const TS* __restrict__ pinv,
                                                        const TR* __restrict__ r,
                                                        TC* __restrict__ zacc, TC eta, int n,
-                                                       const PcgState* st, FuseArgs fa) {
+                                                       const PcgState* st, FuseArgs fa,
+                                                       const float* __restrict__ rscale) {
   if (st && st->done) return;
   __shared__ __align__(16) TC xs[kPatchLd];
   __shared__ double shr[32];
@@ -604,7 +625,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
           const int col = (it * 32 + lane) * W;
           if (col < g.ld) {
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += dot_raw<TC>(buf[k][it], xs + col);
+            for (int k = 0; k < R; ++k) acc[k] += dot_tile<TS, TC>(buf[k][it], xs + col);
           }
         }
 #pragma unroll
@@ -615,6 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
           for (int k = 1; k < R; ++k)
             if (lane == k) v = acc[k];
           const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
+          if constexpr (std::is_same<TS, __half>::value) v *= (TC)rscale[(long long)gofs[p] * kRowsPerWarp + q];
           atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
         }
       }
@@ -1105,32 +1127,37 @@ int tma_per_sm() {
 // has shapes 0 and 4 only (others map to 0).
 template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
 void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                 TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa, cudaStream_t s) {
+                 TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa, const float* rscale,
+                 cudaStream_t s) {
   const int grid = wave_grid(smoother_per_sm<TC, TS, TR, kFused, kCB, kR>(), ngroups);
   k_smoother<TC, TS, TR, kFused, kCB, kR><<<grid, kThreads, 0, s>>>(geo, gofs, npatch, pinv, r, zacc, (TC)eta, n,
-                                                                     st, fa);
+                                                                     st, fa, rscale);
 }
 
 template <typename TC, typename TS, typename TR, bool kFused>
 void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                     const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
-                    cudaStream_t s) {
+                    const float* rscale, cudaStream_t s) {
   TG_COUNT(1);
+  constexpr bool kHalf = std::is_same<TS, __half>::value;
+  if (kHalf && shape == 4) shape = 0;   // the TMA ring has no row scaling
   if (shape == 4) {
-    int grid = tma_per_sm<TC, TS, TR, kFused>() * sm_count();
-    if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
-    k_smoother_tma<TC, TS, TR, kFused><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
-        geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
+    if constexpr (!kHalf) {
+      int grid = tma_per_sm<TC, TS, TR, kFused>() * sm_count();
+      if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
+      k_smoother_tma<TC, TS, TR, kFused><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
+          geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
+    }
     return;
   }
   if constexpr (std::is_same<TS, double>::value) {
-    smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s);
+    smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s);
   } else {
     switch (shape) {
-      case 1: smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
-      case 2: smoother_go<TC, TS, TR, kFused, 8, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
-      case 3: smoother_go<TC, TS, TR, kFused, 8, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
-      default: smoother_go<TC, TS, TR, kFused, 16, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, s); break;
+      case 1: smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
+      case 2: smoother_go<TC, TS, TR, kFused, 8, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
+      case 3: smoother_go<TC, TS, TR, kFused, 8, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
+      default: smoother_go<TC, TS, TR, kFused, 16, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
     }
   }
 }
@@ -1138,7 +1165,7 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
 // occupancy queries of every shape of one instantiation (outside any capture)
 template <typename TC, typename TS, typename TR, bool kFused>
 void smoother_prepare() {
-  tma_per_sm<TC, TS, TR, kFused>();
+  if constexpr (!std::is_same<TS, __half>::value) tma_per_sm<TC, TS, TR, kFused>();
   if constexpr (std::is_same<TS, double>::value) {
     smoother_per_sm<TC, TS, TR, kFused, 16, 2>();
   } else {
@@ -1151,30 +1178,38 @@ void smoother_prepare() {
 
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
-                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape) {
-  smoother_shape<TC, TS, TR, false>(shape, geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, FuseArgs{}, s);
+                     TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape,
+                     const float* rscale) {
+  smoother_shape<TC, TS, TR, false>(shape, geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, FuseArgs{},
+                                    rscale, s);
 }
 
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape) {
+                            cudaStream_t s, int shape, const float* rscale) {
   FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b};
-  smoother_shape<TC, TS, double, true>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa, s);
+  smoother_shape<TC, TS, double, true>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa,
+                                       rscale, s);
 }
 template void launch_smoother_update<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                      const double*, double*, const double*, double*,
                                                      const double*, double*, double, int, int, int, double*,
-                                                     PcgState*, cudaStream_t, int);
+                                                     PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother_update<float, float>(const PatchGeo*, const int*, int, int, const float*,
                                                    const double*, double*, const double*, double*,
                                                    const double*, float*, double, int, int, int, double*,
-                                                   PcgState*, cudaStream_t, int);
+                                                   PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother_update<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
                                                            const __nv_bfloat16*, const double*, double*,
                                                            const double*, double*, const double*, float*, double,
-                                                           int, int, int, double*, PcgState*, cudaStream_t, int);
+                                                           int, int, int, double*, PcgState*, cudaStream_t, int,
+                                                           const float*);
+template void launch_smoother_update<float, __half>(const PatchGeo*, const int*, int, int, const __half*,
+                                                    const double*, double*, const double*, double*, const double*,
+                                                    float*, double, int, int, int, double*, PcgState*, cudaStream_t,
+                                                    int, const float*);
 
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
@@ -1189,15 +1224,19 @@ template void launch_pcg_apply_p<float>(const float*, const double*, double*, do
                                         double*, PcgState*, int, cudaStream_t);
 
 template void launch_smoother<double, double, double>(const PatchGeo*, const int*, int, int, const double*, const double*, double*,
-                                      double, int, const PcgState*, cudaStream_t, int);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother<float, float, double>(const PatchGeo*, const int*, int, int, const float*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother<float, float, float>(const PatchGeo*, const int*, int, int, const float*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+template void launch_smoother<float, __half, double>(const PatchGeo*, const int*, int, int, const __half*, const double*, float*,
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+template void launch_smoother<float, __half, float>(const PatchGeo*, const int*, int, int, const __half*, const float*, float*,
+                                      double, int, const PcgState*, cudaStream_t, int, const float*);
 
 template <typename TC, typename TS>
 void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,
@@ -1241,6 +1280,9 @@ void configure_kernels(int max_coarse_dim) {
   smoother_prepare<double, double, double, true>();
   smoother_prepare<float, float, double, true>();
   smoother_prepare<float, __nv_bfloat16, double, true>();
+  smoother_prepare<float, __half, double, false>();
+  smoother_prepare<float, __half, float, false>();
+  smoother_prepare<float, __half, double, true>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
   if (shm > 48 * 1024)
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

@@ -139,6 +139,34 @@ __global__ void k_store_inverse(const double* __restrict__ scratch, const PatchG
   }
 }
 
+// FP16 storage of the inverses: row q of patch p is multiplied by 2^(15 - e),
+// e the binary exponent of its largest magnitude (frexp: max = m 2^e,
+// m in [1/2, 1)), so the row maximum lands in [2^14, 2^15) below the FP16
+// limit and the smallest entries keep most of their precision; the power-of-
+// two factor is exact and rscale holds its inverse.  One warp per row.
+__global__ void k_store_inverse_f16(const double* __restrict__ scratch, const PatchGeo* __restrict__ geo,
+                                    const int* __restrict__ gofs, int first, int nmax, __half* __restrict__ pinv,
+                                    float* __restrict__ rscale) {
+  const int p = first + blockIdx.x;
+  const PatchGeo g = geo[p];
+  const double* X = scratch + (long long)blockIdx.x * nmax * nmax;
+  __half* M = pinv + g.off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < g.nloc; row += nw) {
+    const double* xr = X + (long long)row * g.nloc;
+    double mx = 0.0;
+    for (int col = lane; col < g.nloc; col += 32) mx = fmax(mx, fabs(xr[col]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    const double sc = ldexp(1.0, 15 - e);
+    for (int col = lane; col < g.ld; col += 32)
+      M[(long long)row * g.ld + col] = __double2half(col < g.nloc ? xr[col] * sc : 0.0);
+    if (lane == 0) rscale[(long long)gofs[p] * kRowsPerGroup + row] = (float)ldexp(1.0, e - 15);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Snapshot spaces.  For block K = (I, J) and an interior side s (0 L, 1 R,
 // 2 B, 3 T) the snapshot space of Section 4.1 restricted to K is spanned by
@@ -864,6 +892,10 @@ template void launch_store_inverse<float>(const double*, const PatchGeo*, int, i
 template void launch_store_inverse<__nv_bfloat16>(const double*, const PatchGeo*, int, int, int,
                                                   __nv_bfloat16*, cudaStream_t);
 
+void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const int* gofs, int first, int count,
+                              int nmax, __half* pinv, float* rscale, cudaStream_t s) {
+  k_store_inverse_f16<<<count, 256, 0, s>>>(scratch, geo, gofs, first, nmax, pinv, rscale);
+}
 void launch_snapshots(const double* kinv, const double* blk_band, const double* coef, int nfn,
                       const unsigned char* mask, double* psiS, double* gram, int n, int b, cudaStream_t s) {
   const int nc = n / b, nloc = (b - 1) * (b - 1), threads = 256;

@@ -20,7 +20,7 @@ ERRORS = {
     -4: "TG_ERR_MAXITER", -5: "TG_ERR_DEVICE_TIMEOUT", -6: "TG_ERR_CUDA", -7: "TG_ERR_OOM",
     -8: "TG_ERR_UNSUPPORTED", -9: "TG_ERR_DEGENERATE_BASIS",
 }
-PREC = {"f64": 0, "f32": 1, "bf16": 2}
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2, "learned": 3}
 PTR_HOST, PTR_DEVICE = 0, 1
 

@@ -103,7 +103,7 @@ def test_preconditioner_parts(case, tg, which):
     assert rel(got, ref) < 1e-9, (case["name"], which, rel(got, ref))
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f16"])
 def test_smoother_tile_shapes(tg, prec):
     """Every smoother tile shape (16- or 8-byte loads, 2 or 4 rows per pass,
     TMA ring) computes the same smoother: against shape 0 to FP32 summation
@@ -119,7 +119,7 @@ def test_smoother_tile_shapes(tg, prec):
     ref = o.smoother(r)
     f = inputs.quarter_five_spot(n)
     u_ref, _ = solve_direct(Grid(n, b), kappa, f)
-    tol_oracle = {"f64": 1e-9, "f32": 2e-5, "bf16": 2e-2}[prec]
+    tol_oracle = {"f64": 1e-9, "f32": 2e-5, "bf16": 2e-2, "f16": 5e-3}[prec]
     outs = {}
     for shape in range(5):
         s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), smoother_shape=shape)
@@ -130,7 +130,8 @@ def test_smoother_tile_shapes(tg, prec):
             assert rel(outs[shape], ref) < tol_oracle, (prec, shape, rel(outs[shape], ref))
             it, rep = s.solve(f, rtol=1e-12)
             got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
-            assert rel(got_u, u_ref) < 1e-8 and rep.smoother_shape == shape
+            ran = 0 if (prec == "f16" and shape == 4) else shape       # FP16 has no TMA ring
+            assert rel(got_u, u_ref) < 1e-8 and rep.smoother_shape == ran
         finally:
             s.close()
     for shape in range(1, 5):
@@ -139,7 +140,7 @@ def test_smoother_tile_shapes(tg, prec):
     try:
         it, rep = s.solve(f, rtol=1e-8)
         times = rep.shape_times()
-        tried = [0, 4] if prec == "f64" else [0, 1, 2, 3, 4]
+        tried = {"f64": [0, 4], "f16": [0, 1, 2, 3]}.get(prec, [0, 1, 2, 3, 4])
         assert all(times[k] > 0 for k in tried)
         assert rep.smoother_shape in tried and times[rep.smoother_shape] == min(times[k] for k in tried)
     finally:
@@ -189,7 +190,7 @@ def test_full_solve_matches_direct_solve(case, tg):
     assert abs(rep8.cond_estimate / ora["cond"] - 1) < 0.05
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
 def test_mixed_precision_solve(case, tg, prec):
     n, b = case["n"], case["b"]
     f = inputs.quarter_five_spot(n)
