@@ -160,7 +160,7 @@ def run_ncu_target(args):
     n, b = args.n, args.b
     kappa, f = workload(n, 5)
     s = tgms.Solver(kappa, b, EIG_TOL, precision=args.precision, flexible=int(args.precision != "f64"),
-                    profile=int(args.profile_loop))
+                    profile=int(args.profile_loop), smoother_shape=args.shape)
     for _ in range(args.warmup + args.steps):
         it, rep = s.solve(f, rtol=RTOL)
     torch.cuda.synchronize()
@@ -212,7 +212,7 @@ def run_ours(args):
         oth.close()
         others[other] = (o_times, o_reps, oth_setup_ms)
     # headline mixed-precision arm, timed region with clock sampling
-    head, setup_ms = make(prec, 1)
+    head, setup_ms = make(prec, 1, smoother_shape=args.shape)
     for _ in range(args.warmup):
         head.solve(f, rtol=RTOL)
     if dist:
@@ -586,6 +586,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--hidden", type=int, default=512)
     ap.add_argument("--learned-precision", default="f16", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--shape", type=int, default=-1, help="smoother tile shape (-1: autotune)")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")

@@ -51,6 +51,7 @@ struct tg_handle {
   int* d_bgofs = nullptr;
   int bgroups = 0;
   double* binv = nullptr;
+  float* binv32 = nullptr;  // mixed precision: FP32 block inverses
   // spectral data
   double* lam = nullptr;
   std::vector<int> nsel;
@@ -329,8 +330,9 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
       dalloc(&c->fd, nn) || dalloc(&c->bd, 4 * n) || dalloc(&c->pd, nn) || dalloc(&c->pw, nn + 2 * n + 2) ||
       dalloc(&c->part, npart) || dalloc(&c->gx, (nc + 1) * nc) || dalloc(&c->gy, (nc + 1) * nc) ||
       dalloc(&c->FH, h->nblocks) || dalloc(&c->absF, h->nblocks) || dalloc(&c->diverr, 2) ||
-      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, h->cs.D) || dalloc(&c->rt_part, h->rt.nslots) ||
-      dalloc(&c->rt_coefs, h->rt.D) || dalloc(&c->st, 1) || dalloc(&c->d_rtol, 1))
+      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, 2 * (size_t)h->cs.D) ||
+      dalloc(&c->rt_part, h->rt.nslots) || dalloc(&c->rt_coefs, 2 * (size_t)h->rt.D) || dalloc(&c->st, 1) ||
+      dalloc(&c->d_rtol, 1))
     rc = TG_ERR_OOM;
   if (!rc) rc = cuda_err(cudaMalloc(&c->zacc, tc * nn));
   if (!rc) rc = cuda_err(cudaMalloc(&c->zacc2, tc * nn));
@@ -411,11 +413,22 @@ void enqueue_preprocess(Ctx* c, const double* f, const double* bflux, double* ux
   }
   launch_block_particular(f, ux, uy, n, b, s);
   launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
-  cudaMemsetAsync(c->phi, 0, sizeof(double) * nn, s);
   // phi = K_K^{-1} rho on every block's interior nodes: the smoother's GEMV
-  // with the dense block inverses (blocks do not overlap, eta = 1)
-  launch_smoother<double, double, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv, c->rho, c->phi,
+  // with the dense block inverses (blocks do not overlap, eta = 1).  phi is a
+  // stream function, so its precision cannot change the divergence of vbar;
+  // it only moves the PCG starting point, and mixed-precision handles use
+  // FP32 inverses and FP32 accumulation (in the free inner-residual buffer).
+  if (h->binv) {
+    cudaMemsetAsync(c->phi, 0, sizeof(double) * nn, s);
+    launch_smoother<double, double, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv, c->rho, c->phi,
+                                            1.0, n, nullptr, s);
+  } else {
+    float* phi32 = (float*)c->rin;
+    cudaMemsetAsync(phi32, 0, sizeof(float) * nn, s);
+    launch_smoother<float, float, double>(h->d_bgeo, h->d_bgofs, h->nblocks, h->bgroups, h->binv32, c->rho, phi32,
                                           1.0, n, nullptr, s);
+    launch_convert<float, double>(phi32, c->phi, nn, s);
+  }
   launch_add_curl(c->phi, ux, uy, n, s);
   launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
 }
@@ -691,7 +704,9 @@ int setup_blocks(tg_handle* h, bool inverses) {
     h->bgroups = bgofs[h->nblocks];
     double* bscratch = nullptr;
     const int bbatch = std::max(1, std::min(h->nblocks, (int)((256LL << 20) / (8LL * std::max(bn, 1) * std::max(bn, 1)))));
-    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) || dalloc(&h->binv, (size_t)boff) ||
+    const bool f64 = (h->opt.precision == TG_PREC_F64);
+    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) ||
+        (f64 ? dalloc(&h->binv, (size_t)boff) : dalloc(&h->binv32, (size_t)boff)) ||
         dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1)))
       rc = TG_ERR_OOM;
     if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
@@ -700,7 +715,8 @@ int setup_blocks(tg_handle* h, bool inverses) {
       for (int first = 0; first < h->nblocks; first += bbatch) {
         const int cnt = std::min(bbatch, h->nblocks - first);
         launch_band_inverse(h->blk_band, d_brect, first, cnt, bw, bn, bscratch, s);
-        launch_store_inverse<double>(bscratch, h->d_bgeo, first, cnt, bn, h->binv, s);
+        if (f64) launch_store_inverse<double>(bscratch, h->d_bgeo, first, cnt, bn, h->binv, s);
+        else launch_store_inverse<float>(bscratch, h->d_bgeo, first, cnt, bn, h->binv32, s);
       }
     }
     if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
@@ -1306,7 +1322,7 @@ void tg_destroy(tg_handle* h) {
   cudaStreamSynchronize(h->stream);
   ctx_free(h->ctx);
   void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->rscale, h->blk_band, h->lam,
-                  h->d_bgeo, h->d_bgofs, h->binv, h->kcoef};
+                  h->d_bgeo, h->d_bgofs, h->binv, h->binv32, h->kcoef};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);

@@ -224,6 +224,7 @@ constexpr int kRowsPerGroup = 4;   // rows of a patch inverse streamed together 
 template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s);
+// coefs: 2 D doubles; d = coefs[0, D), the second half is right-hand-side scratch
 void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
                          cudaStream_t s);
 template <typename TC, typename TS>

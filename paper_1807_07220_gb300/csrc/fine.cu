@@ -18,6 +18,7 @@ namespace tg {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kCoarseSplit = 1024;   // coarse systems larger than this form their right-hand side once
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -961,6 +962,47 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const double* __restr
   }
 }
 
+// Large coarse systems: the right-hand side c[u] = sum of u's slot partials is
+// formed once (k_coarse_rhs), then every CTA copies it into shared memory and
+// streams its rows of K_H^{-1} with four independent accumulators per lane.
+__global__ void k_coarse_rhs(const double* __restrict__ part, const int* __restrict__ gather,
+                             double* __restrict__ c, int D, const PcgState* st) {
+  if (st && st->done) return;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < D; u += gridDim.x * blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = gather[4 * u + k];
+      if (g >= 0) v += part[g];
+    }
+    c[u] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_coarse_gemv(const double* __restrict__ c,
+                                                          const double* __restrict__ Kinv,
+                                                          double* __restrict__ d, int D, const PcgState* st) {
+  if (st && st->done) return;
+  extern __shared__ double cvec[];
+  for (int u = threadIdx.x; u < D; u += blockDim.x) cvec[u] = c[u];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = blockIdx.x * nw + warp; row < D; row += gridDim.x * nw) {
+    const double* kr = Kinv + (long long)row * D;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int col = lane;
+    for (; col + 96 < D; col += 128) {
+      a0 += __ldg(kr + col) * cvec[col];
+      a1 += __ldg(kr + col + 32) * cvec[col + 32];
+      a2 += __ldg(kr + col + 64) * cvec[col + 64];
+      a3 += __ldg(kr + col + 96) * cvec[col + 96];
+    }
+    for (; col < D; col += 32) a0 += __ldg(kr + col) * cvec[col];
+    const double acc = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) d[row] = acc;
+  }
+}
+
 // Coarse prolongation: v += sum_s d[coef(s)] * tile_s on each block's owned nodes.
 template <typename TC, typename TS>
 __global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ slot_ptr,
@@ -1284,8 +1326,10 @@ void configure_kernels(int max_coarse_dim) {
   smoother_prepare<float, __half, float, false>();
   smoother_prepare<float, __half, double, true>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
-  if (shm > 48 * 1024)
+  if (shm > 48 * 1024) {
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_coarse_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  }
 }
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s) {
   TG_COUNT(1);
@@ -1298,6 +1342,15 @@ void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, c
 void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
                          cudaStream_t s) {
   const size_t shm = sizeof(double) * (size_t)cs.D;
+  if (cs.D > kCoarseSplit) {
+    double* rhs = coefs + cs.D;
+    TG_COUNT(2);
+    k_coarse_rhs<<<(cs.D + kThreads - 1) / kThreads, kThreads, 0, s>>>(part, cs.gather, rhs, cs.D, st);
+    int grid = (cs.D + 7) / 8;
+    if (grid > 2 * sm_count()) grid = 2 * sm_count();
+    k_coarse_gemv<<<grid, kThreads, shm, s>>>(rhs, cs.Kinv, coefs, cs.D, st);
+    return;
+  }
   int grid = (cs.D + 7) / 8;
   if (grid > 2 * 152) grid = 2 * 152;
   if (grid < 1) grid = 1;

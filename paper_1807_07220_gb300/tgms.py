@@ -53,7 +53,11 @@ class tg_report(ctypes.Structure):
         return [float(v) for v in self.shape_us]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 class TgmsError(RuntimeError):
