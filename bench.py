@@ -42,7 +42,7 @@ N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
 # the fused and plain sweeps, from the ncu capture summarised in
 # profiles/k_smoother_256x256.md, keyed by (storage precision, tile shape);
 # valid only for the kernel version and shape profiled there
-SMOOTHER_TRAFFIC = {("f32", 0): 134.42e6, ("bf16", 0): 66.24e6}
+SMOOTHER_TRAFFIC = {("f32", 0): 134.42e6, ("bf16", 0): 66.24e6, ("bf16", 2): 66.10e6}
 
 
 def dof(n):
