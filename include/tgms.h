@@ -113,9 +113,18 @@ typedef struct tg_options {
    * handle's own patch inverses, keep the fastest); 0 = 16-byte loads, 4 rows
    * per pass (2 for FP64 storage); 1 = 16-byte loads, 2 rows; 2 = 8-byte
    * loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
-   * shared-memory ring.  FP64 storage runs shape 0 for 1..3, FP16 storage
-   * shape 0 for 4.  Same arithmetic in every shape. */
+   * shared-memory ring; 5 = shape 3 and 6 = shape 1 software-pipelined (the
+   * next pass's rows are loaded while the current pass is reduced).  FP64
+   * storage runs shape 0 for 1..3, 5, 6; FP16 storage shape 0 for 4.  Same
+   * arithmetic in every shape. */
   int smoother_shape;
+  /* 1: launch the kernels of a solve with programmatic dependent launch
+   * (each kernel's launch overlaps the tail of the one before it; it waits
+   * for that kernel's completion before reading its results); 0: plain
+   * stream order.  Same results either way.  Default 0: on GB300 the
+   * overlap measured slower (+14 % per solve at 256^2, +22 % at 1024^2),
+   * the early-launched CTAs competing with the one-wave grids. */
+  int launch_overlap;
 } tg_options;
 
 typedef struct tg_report {
@@ -138,12 +147,13 @@ typedef struct tg_report {
   int fallback_faces;     /* TG_COARSE_LEARNED: faces that took the exact spectral problem */
   int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
   int smoother_shape;     /* smoother tile shape in use */
-  float shape_us[5];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
+  float shape_us[7];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
  * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0, no
- * network or profiles, learned_k 4, learned_max_iter 0, smoother_shape -1. */
+ * network or profiles, learned_k 4, learned_max_iter 0, smoother_shape -1,
+ * launch_overlap 0. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything

@@ -23,6 +23,7 @@ using namespace tg;
 
 namespace tg {
 unsigned long long g_kernel_launches = 0;
+bool g_pdl = false;
 }
 
 namespace {
@@ -901,9 +902,9 @@ int autotune_smoother_t(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaMemsetAsync(rin, 0, sizeof(TC) * nn, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
   const bool f64 = std::is_same<TS, double>::value, f16 = std::is_same<TS, __half>::value;
-  const int cand_all[] = {0, 1, 2, 3, 4}, cand_f64[] = {0, 4};
-  const int* cand = f64 ? cand_f64 : cand_all;
-  const int ncand = f64 ? 2 : f16 ? 4 : 5;   // FP16: no TMA ring
+  const int cand_all[] = {0, 1, 2, 3, 4, 5, 6}, cand_f64[] = {0, 4}, cand_f16[] = {0, 1, 2, 3, 5, 6};
+  const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : cand_all;   // FP16: no TMA ring
+  const int ncand = f64 ? 2 : f16 ? 6 : 7;
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {
@@ -1062,6 +1063,7 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
 }
 
 int hook_dispatch(tg_handle* h, const double* rho, double* z, int which) {
+  g_pdl = (h->opt.launch_overlap != 0);
   if (!h || !rho || !z) return TG_ERR_INVALID_ARG;
   switch (h->opt.precision) {
     case TG_PREC_F64: return hook_precond<double, double>(h, rho, z, which);
@@ -1133,6 +1135,7 @@ int tg_default_options(tg_options* opt) {
   opt->learned_k = 4;
   opt->learned_max_iter = 0;
   opt->smoother_shape = -1;
+  opt->launch_overlap = 0;
   return TG_OK;
 }
 
@@ -1201,6 +1204,7 @@ namespace {
 
 int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
                int* iters, tg_report* rep) {
+  g_pdl = (h->opt.launch_overlap != 0);
   Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
@@ -1353,6 +1357,7 @@ int tg_coarse_info(tg_handle* h, int* nfaces, int* velocity_basis, int* nsel, do
 
 int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux, double* uy) {
   if (!h || !f || !ux || !uy) return TG_ERR_INVALID_ARG;
+  g_pdl = (h->opt.launch_overlap != 0);
   Ctx* c = h->ctx;
   const int n = h->n;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
@@ -1438,6 +1443,7 @@ int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, 
     // one graph: the chains of all contexts, independent of each other
     cudaGraph_t g = nullptr;
     rc = cuda_err(cudaGraphCreate(&g, 0));
+    g_pdl = (opt->launch_overlap != 0);
     for (size_t j = 0; j < B->ctx.size() && !rc; ++j) rc = add_chain(B->ctx[j], g, B->cap);
     if (!rc) rc = cuda_err(cudaGraphInstantiate(&B->exec, g, 0));
     if (g) cudaGraphDestroy(g);

@@ -10,6 +10,7 @@ namespace {
 // of every context are copied; a NULL source writes zeros when zero_if_null
 __global__ void k_copy_table(const double* const* __restrict__ src, double* const* __restrict__ dst,
                              const long long* __restrict__ cnt, int t0, int t1, int zero_if_null) {
+  pdl_entry();
   const int per = t1 - t0;
   const int j = blockIdx.y / per, t = t0 + blockIdx.y % per;
   const int e = 5 * j + t;
@@ -25,11 +26,13 @@ __global__ void k_copy_table(const double* const* __restrict__ src, double* cons
 }
 
 __global__ void k_fill_scalars(const double* __restrict__ v, double* const* __restrict__ dst, int m) {
+  pdl_entry();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < m) dst[j][0] = v[0];
 }
 
 __global__ void k_gather_states(PcgState* const* __restrict__ st, int* __restrict__ out, int m) {
+  pdl_entry();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < m) {
     out[2 * j] = st[j]->iter;
@@ -43,15 +46,15 @@ void launch_copy_table(const double* const* src, double* const* dst, const long 
                        int zero_if_null, cudaStream_t s) {
   TG_COUNT(1);
   dim3 grid(64, m * (t1 - t0));
-  k_copy_table<<<grid, 256, 0, s>>>(src, dst, cnt, t0, t1, zero_if_null);
+  launch(k_copy_table, dim3(grid), dim3(256), 0, s, src, dst, cnt, t0, t1, zero_if_null);
 }
 void launch_fill_scalars(const double* v, double* const* dst, int m, cudaStream_t s) {
   TG_COUNT(1);
-  k_fill_scalars<<<(m + 127) / 128, 128, 0, s>>>(v, dst, m);
+  launch(k_fill_scalars, dim3((m + 127) / 128), dim3(128), 0, s, v, dst, m);
 }
 void launch_gather_states(PcgState* const* st, int* out, int m, cudaStream_t s) {
   TG_COUNT(1);
-  k_gather_states<<<(m + 127) / 128, 128, 0, s>>>(st, out, m);
+  launch(k_gather_states, dim3((m + 127) / 128), dim3(128), 0, s, st, out, m);
 }
 
 }  // namespace tg

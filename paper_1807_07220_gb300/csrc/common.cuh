@@ -146,6 +146,17 @@ __device__ __forceinline__ TA stencil_apply(const TV* __restrict__ psi, const TK
   return out;
 }
 
+// Programmatic dependent launch.  Every solve-path kernel starts here: it
+// waits until the grid it depends on has completed and its writes are visible
+// (a no-op when the launch carried no programmatic dependency), then lets the
+// next grid in the stream begin launching.  The next grid can only launch
+// once every CTA of this one has executed the trigger, so its waiting CTAs
+// never hold resources that this grid still needs.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Sum of a partial array by one warp in a fixed order (deterministic).
 __device__ __forceinline__ double warp_sum_array(const double* a, int m) {
   double s = 0.0;
@@ -161,6 +172,26 @@ namespace tg {
 // number of kernels enqueued by the launchers below (host counter)
 extern unsigned long long g_kernel_launches;
 #define TG_COUNT(k) (::tg::g_kernel_launches += (unsigned long long)(k))
+
+// Solve-path kernels are launched with the programmatic-stream-serialization
+// attribute when g_pdl is set (tg_options.launch_overlap, read at enqueue /
+// capture time), so a kernel's launch overlaps the tail of its predecessor.
+// Off by default: measured slower on GB300 for this kernel chain.
+extern bool g_pdl;
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t shm, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
 
 void configure_kernels(int max_coarse_dim);
 // batched solves (batch.cu)
@@ -198,8 +229,10 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 // Smoother tile shapes (chosen per handle by the autotuner): 0 = 16-byte
 // loads, 4 rows per pass (2 for FP64); 1 = 16-byte loads, 2 rows; 2 = 8-byte
 // loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
-// shared-memory ring.  FP64 storage uses shape 0 for 1..3.
-constexpr int kSmootherShapes = 5;
+// shared-memory ring; 5 = shape 3 and 6 = shape 1, software-pipelined (the
+// next pass's rows in flight while the current one is reduced).  FP64 storage
+// uses shape 0 for 1..3, 5, 6; FP16 storage uses shape 0 for 4.
+constexpr int kSmootherShapes = 7;
 // rscale: FP16 storage only, one power-of-two factor per stored row (index
 // gofs[p] * kRowsPerGroup + row) that undoes the row's scaling.
 template <typename TC, typename TS, typename TR>

@@ -73,6 +73,7 @@ __device__ __forceinline__ double sum_partials(const double* part, int m) {
 __global__ void __launch_bounds__(kThreads) k_apply_operator(const double* __restrict__ psi,
                                                              const double* __restrict__ kinv,
                                                              double* __restrict__ out, int n) {
+  pdl_entry();
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
        t += (long long)gridDim.x * blockDim.x) {
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_operator(const double* __res
 __global__ void __launch_bounds__(kThreads) k_apply_operator_f32(const double* __restrict__ psi,
                                                                  const float* __restrict__ kinv,
                                                                  double* __restrict__ out, int n) {
+  pdl_entry();
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
        t += (long long)gridDim.x * blockDim.x) {
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double* __restrict_
                                                        const TC* __restrict__ kinv,
                                                        TC* __restrict__ out, int n,
                                                        const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_dot(const double* __rest
                                                             const double* __restrict__ kinv,
                                                             double* __restrict__ q,
                                                             double* part, PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   __shared__ double sh[32];
   const long long nn = (long long)n * n;
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
                                                           TC* __restrict__ znext,
                                                           const double* __restrict__ kcoef, double* part,
                                                           PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   __shared__ double P[kTy + 2][kTx + 2];
   __shared__ double sh[32];
@@ -233,6 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update_xr(double* __restrict__
                                                             const double* __restrict__ q,
                                                             TC* __restrict__ zacc, double* part,
                                                             PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   __shared__ double sh[32];
   const double alpha = st->alpha;
@@ -272,6 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
                                                        const TC* __restrict__ z,
                                                        const double* __restrict__ q,
                                                        double* part, PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   __shared__ double sh[32];
   const long long nn = (long long)n * n;
@@ -309,6 +316,7 @@ template <typename TC>
 __global__ void __launch_bounds__(kThreads) k_pcg_update_p(double* __restrict__ p,
                                                            const TC* __restrict__ z,
                                                            const PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   const double beta = st->beta;
   const long long nn = (long long)n * n;
@@ -320,6 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update_p(double* __restrict__ 
 // scalar state at the start of a solve (rtol read from device memory so that
 // an instantiated graph serves every tolerance)
 __global__ void k_pcg_reset(PcgState* st, const double* __restrict__ rtol, int maxit, int flexible) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->rz = st->rz_prev = st->rr0 = st->rr = 0.0;
   st->alpha = st->beta = st->pq = st->zq = 0.0;
@@ -334,6 +343,7 @@ __global__ void k_pcg_reset(PcgState* st, const double* __restrict__ rtol, int m
 
 // loop condition of the graph's while node: continue while not done
 __global__ void k_set_condition(cudaGraphConditionalHandle cond, const PcgState* st) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
 
@@ -341,6 +351,7 @@ __global__ void k_set_condition(cudaGraphConditionalHandle cond, const PcgState*
 __global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
                                                        const double* __restrict__ r, double* part,
                                                        PcgState* st, int n) {
+  pdl_entry();
   __shared__ double sh[32];
   const long long nn = (long long)n * n;
   double acc = 0.0;
@@ -372,6 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restri
                                                           const TC* __restrict__ z,
                                                           double* __restrict__ p, double* part,
                                                           PcgState* st, int n) {
+  pdl_entry();
   if (st->done) return;
   __shared__ double sh[32];
   const long long nn = (long long)n * n;
@@ -549,7 +561,7 @@ struct FuseArgs {
   int nc, b;
 };
 
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
                                                        const int* __restrict__ gofs, int npatch,
                                                        const TS* __restrict__ pinv,
@@ -557,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
                                                        TC* __restrict__ zacc, TC eta, int n,
                                                        const PcgState* st, FuseArgs fa,
                                                        const float* __restrict__ rscale) {
+  pdl_entry();
   if (st && st->done) return;
   __shared__ __align__(16) TC xs[kPatchLd];
   __shared__ double shr[32];
@@ -601,44 +614,68 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
     const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
     const TS* M = pinv + g.off;
     constexpr int R = kR;
+    constexpr int P = kRowsPerWarp / R;   // passes per row group
     using V = typename LdChunk<TS, kCB>::T;
-    for (int grp = ga + warp; grp < gb; grp += nw) {
+    // every load of R rows first (predicated, zero-filled) ...
+    auto load_rows = [&](V (&buf)[R][kIter], int row0) {
 #pragma unroll
-      for (int pass = 0; pass < kRowsPerWarp / R; ++pass) {
-        const int row0 = grp * kRowsPerWarp + pass * R;
-        // issue every load of the R rows first (predicated, zero-filled) ...
-        V buf[R][kIter];
+      for (int it = 0; it < kIter; ++it) {
+        const int col = (it * 32 + lane) * W;
 #pragma unroll
-        for (int it = 0; it < kIter; ++it) {
-          const int col = (it * 32 + lane) * W;
-#pragma unroll
-          for (int k = 0; k < R; ++k) {
-            if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_tile<TS, kCB>(M + (long long)(row0 + k) * g.ld + col);
-            else buf[k][it] = V{};
-          }
+        for (int k = 0; k < R; ++k) {
+          if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_tile<TS, kCB>(M + (long long)(row0 + k) * g.ld + col);
+          else buf[k][it] = V{};
         }
-        // ... then the arithmetic
-        TC acc[R];
+      }
+    };
+    // ... then the arithmetic, the warp reductions and the scatter
+    auto reduce_rows = [&](const V (&buf)[R][kIter], int row0) {
+      TC acc[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = (TC)0;
+      for (int k = 0; k < R; ++k) acc[k] = (TC)0;
 #pragma unroll
-        for (int it = 0; it < kIter; ++it) {
-          const int col = (it * 32 + lane) * W;
-          if (col < g.ld) {
+      for (int it = 0; it < kIter; ++it) {
+        const int col = (it * 32 + lane) * W;
+        if (col < g.ld) {
 #pragma unroll
-            for (int k = 0; k < R; ++k) acc[k] += dot_tile<TS, TC>(buf[k][it], xs + col);
-          }
+          for (int k = 0; k < R; ++k) acc[k] += dot_tile<TS, TC>(buf[k][it], xs + col);
         }
+      }
 #pragma unroll
-        for (int k = 0; k < R; ++k) acc[k] = warp_sum(acc[k]);
-        if (lane < R && row0 + lane < g.nloc) {
-          TC v = acc[0];
+      for (int k = 0; k < R; ++k) acc[k] = warp_sum(acc[k]);
+      if (lane < R && row0 + lane < g.nloc) {
+        TC v = acc[0];
 #pragma unroll
-          for (int k = 1; k < R; ++k)
-            if (lane == k) v = acc[k];
-          const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
-          if constexpr (std::is_same<TS, __half>::value) v *= (TC)rscale[(long long)gofs[p] * kRowsPerWarp + q];
-          atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
+        for (int k = 1; k < R; ++k)
+          if (lane == k) v = acc[k];
+        const int q = row0 + lane, a = q % g.nx, c = q / g.nx;
+        if constexpr (std::is_same<TS, __half>::value) v *= (TC)rscale[(long long)gofs[p] * kRowsPerWarp + q];
+        atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * v);
+      }
+    };
+    if constexpr (!kPipe) {
+      for (int grp = ga + warp; grp < gb; grp += nw) {
+#pragma unroll
+        for (int pass = 0; pass < P; ++pass) {
+          const int row0 = grp * kRowsPerWarp + pass * R;
+          V buf[R][kIter];
+          load_rows(buf, row0);
+          reduce_rows(buf, row0);
+        }
+      }
+    } else {
+      // software pipeline: the rows of pass t+1 are in flight while pass t is reduced
+      const int ngrp = (gb > ga + warp) ? (gb - ga - warp + nw - 1) / nw : 0;
+      const int nseq = ngrp * P;
+      auto row_at = [&](int t) { return (ga + warp + (t / P) * nw) * kRowsPerWarp + (t % P) * R; };
+      V bA[R][kIter], bB[R][kIter];
+      if (nseq > 0) load_rows(bA, row_at(0));
+      for (int t = 0; t < nseq; t += 2) {
+        if (t + 1 < nseq) load_rows(bB, row_at(t + 1));
+        reduce_rows(bA, row_at(t));
+        if (t + 1 < nseq) {
+          if (t + 2 < nseq) load_rows(bA, row_at(t + 2));
+          reduce_rows(bB, row_at(t + 1));
         }
       }
     }
@@ -733,6 +770,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __res
                                                            const TR* __restrict__ r,
                                                            TC* __restrict__ zacc, TC eta, int n,
                                                            PcgState* st, FuseArgs fa) {
+  pdl_entry();
   if (st && st->done) return;
   constexpr int NS = Stages<TS>::N;
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -880,6 +918,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const int* __restri
                                                              const TC* __restrict__ kinv,
                                                              double* __restrict__ part, int nc, int b,
                                                              int n, const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   __shared__ TC sh[32];
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
@@ -913,6 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const int* __restrict__ s
                                                        const TC* __restrict__ v,
                                                        double* __restrict__ part, int nc, int b,
                                                        int n, const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   __shared__ TC sh[32];
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
@@ -940,6 +980,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const double* __restr
                                                            const double* __restrict__ Kinv,
                                                            double* __restrict__ d, int D,
                                                            const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   extern __shared__ double cvec[];
   for (int u = threadIdx.x; u < D; u += blockDim.x) {
@@ -967,6 +1008,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const double* __restr
 // streams its rows of K_H^{-1} with four independent accumulators per lane.
 __global__ void k_coarse_rhs(const double* __restrict__ part, const int* __restrict__ gather,
                              double* __restrict__ c, int D, const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < D; u += gridDim.x * blockDim.x) {
     double v = 0.0;
@@ -982,6 +1024,7 @@ __global__ void k_coarse_rhs(const double* __restrict__ part, const int* __restr
 __global__ void __launch_bounds__(kThreads) k_coarse_gemv(const double* __restrict__ c,
                                                           const double* __restrict__ Kinv,
                                                           double* __restrict__ d, int D, const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   extern __shared__ double cvec[];
   for (int u = threadIdx.x; u < D; u += blockDim.x) cvec[u] = c[u];
@@ -1011,6 +1054,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ sl
                                                       const double* __restrict__ d,
                                                       TC* __restrict__ v, int nc, int b, int n,
                                                       const PcgState* st) {
+  pdl_entry();
   if (st && st->done) return;
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int bb = b * b, t = threadIdx.x;
@@ -1023,6 +1067,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ sl
 
 // node coefficients of K (FP64): c0, cE, cN, cNE, cNW, cells outside the domain as 0
 __global__ void k_stencil_coefs(const double* __restrict__ kinv, double* __restrict__ kcoef, int n) {
+  pdl_entry();
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
        t += (long long)gridDim.x * blockDim.x) {
@@ -1039,6 +1084,7 @@ __global__ void k_stencil_coefs(const double* __restrict__ kinv, double* __restr
 
 template <typename TA, typename TB>
 __global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, long long m) {
+  pdl_entry();
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
        t += (long long)gridDim.x * blockDim.x)
     b[t] = (TB)a[t];
@@ -1056,18 +1102,18 @@ inline int grid_for(long long m) {
 // ---- launchers ---------------------------------------------------------------
 void launch_apply_operator(const double* psi, const double* kinv, double* out, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_apply_operator<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
+  launch(k_apply_operator, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, psi, kinv, out, n);
 }
 void launch_apply_operator_f32(const double* psi, const float* kinv, double* out, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_apply_operator_f32<<<grid_for((long long)n * n), kThreads, 0, s>>>(psi, kinv, out, n);
+  launch(k_apply_operator_f32, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, psi, kinv, out, n);
 }
 
 template <typename TC>
 void launch_residual(const double* r, const TC* z, const TC* kinv, TC* out, int n, const PcgState* st,
                      cudaStream_t s) {
   TG_COUNT(1);
-  k_residual<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, kinv, out, n, st);
+  launch(k_residual<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, kinv, out, n, st);
 }
 template void launch_residual<double>(const double*, const double*, const double*, double*, int,
                                       const PcgState*, cudaStream_t);
@@ -1077,34 +1123,34 @@ template void launch_residual<float>(const double*, const float*, const float*, 
 void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part, PcgState* st,
                           int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_apply_dot<<<grid_for((long long)n * n), kThreads, 0, s>>>(p, kinv, q, part, st, n);
+  launch(k_pcg_apply_dot, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, p, kinv, q, part, st, n);
 }
 template <typename TC>
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
                           double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_update_xr<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, p, q, zacc, part, st, n);
+  launch(k_pcg_update_xr<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, x, r, p, q, zacc, part, st, n);
 }
 template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
                      cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_dots<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, q, part, st, n);
+  launch(k_pcg_dots<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, q, part, st, n);
 }
 template <typename TC>
 void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_update_p<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(p, z, st, n);
+  launch(k_pcg_update_p<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, p, z, st, n);
 }
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_init<<<grid_for((long long)n * n), kThreads, 0, s>>>(x, r, part, st, n);
+  launch(k_pcg_init, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, x, r, part, st, n);
 }
 template <typename TC>
 void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,
                         cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_init_rz<TC><<<grid_for((long long)n * n), kThreads, 0, s>>>(r, z, p, part, st, n);
+  launch(k_pcg_init_rz<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, p, part, st, n);
 }
 #define TG_INST_TC(TC)                                                                              \
   template void launch_pcg_update_xr<TC>(double*, double*, const double*, const double*, TC*,      \
@@ -1129,11 +1175,11 @@ int sm_count() {
 }
 
 // resident CTAs per SM of a smoother instantiation (queried once, at setup)
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe>
 int smoother_per_sm() {
   static int per_sm = 0;
   if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR, kFused, kCB, kR>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother<TC, TS, TR, kFused, kCB, kR, kPipe>, kThreads, 0);
     if (per_sm <= 0) per_sm = 1;
   }
   return per_sm;
@@ -1165,15 +1211,16 @@ int tma_per_sm() {
 
 // Smoother tile shapes: 0 = 16-byte loads, default rows per pass (4; 2 for
 // FP64); 1 = 16-byte loads, 2 rows; 2 = 8-byte loads, 4 rows; 3 = 8-byte
-// loads, 2 rows; 4 = TMA bulk copies into a shared-memory ring.  FP64 storage
-// has shapes 0 and 4 only (others map to 0).
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR>
+// loads, 2 rows; 4 = TMA bulk copies into a shared-memory ring; 5 and 6 =
+// shapes 3 and 1 software-pipelined (the next pass's rows in flight while the
+// current pass is reduced).  FP64 storage has shapes 0 and 4 only (others map
+// to 0).
+template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe = false>
 void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                  TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa, const float* rscale,
                  cudaStream_t s) {
-  const int grid = wave_grid(smoother_per_sm<TC, TS, TR, kFused, kCB, kR>(), ngroups);
-  k_smoother<TC, TS, TR, kFused, kCB, kR><<<grid, kThreads, 0, s>>>(geo, gofs, npatch, pinv, r, zacc, (TC)eta, n,
-                                                                     st, fa, rscale);
+  const int grid = wave_grid(smoother_per_sm<TC, TS, TR, kFused, kCB, kR, kPipe>(), ngroups);
+  launch(k_smoother<TC, TS, TR, kFused, kCB, kR, kPipe>, dim3(grid), dim3(kThreads), 0, s, geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st, fa, rscale);
 }
 
 template <typename TC, typename TS, typename TR, bool kFused>
@@ -1187,8 +1234,8 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
     if constexpr (!kHalf) {
       int grid = tma_per_sm<TC, TS, TR, kFused>() * sm_count();
       if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
-      k_smoother_tma<TC, TS, TR, kFused><<<grid < 1 ? 1 : grid, kThreads, tma_smem<TS>(), s>>>(
-          geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
+      launch(k_smoother_tma<TC, TS, TR, kFused>, dim3(grid < 1 ? 1 : grid), dim3(kThreads), tma_smem<TS>(), s, geo,
+             gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
     }
     return;
   }
@@ -1199,6 +1246,8 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
       case 1: smoother_go<TC, TS, TR, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
       case 2: smoother_go<TC, TS, TR, kFused, 8, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
       case 3: smoother_go<TC, TS, TR, kFused, 8, 2>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
+      case 5: smoother_go<TC, TS, TR, kFused, 8, 2, true>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
+      case 6: smoother_go<TC, TS, TR, kFused, 16, 2, true>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
       default: smoother_go<TC, TS, TR, kFused, 16, 4>(geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, fa, rscale, s); break;
     }
   }
@@ -1209,12 +1258,14 @@ template <typename TC, typename TS, typename TR, bool kFused>
 void smoother_prepare() {
   if constexpr (!std::is_same<TS, __half>::value) tma_per_sm<TC, TS, TR, kFused>();
   if constexpr (std::is_same<TS, double>::value) {
-    smoother_per_sm<TC, TS, TR, kFused, 16, 2>();
+    smoother_per_sm<TC, TS, TR, kFused, 16, 2, false>();
   } else {
-    smoother_per_sm<TC, TS, TR, kFused, 16, 4>();
-    smoother_per_sm<TC, TS, TR, kFused, 16, 2>();
-    smoother_per_sm<TC, TS, TR, kFused, 8, 4>();
-    smoother_per_sm<TC, TS, TR, kFused, 8, 2>();
+    smoother_per_sm<TC, TS, TR, kFused, 16, 4, false>();
+    smoother_per_sm<TC, TS, TR, kFused, 16, 2, false>();
+    smoother_per_sm<TC, TS, TR, kFused, 8, 4, false>();
+    smoother_per_sm<TC, TS, TR, kFused, 8, 2, false>();
+    smoother_per_sm<TC, TS, TR, kFused, 8, 2, true>();
+    smoother_per_sm<TC, TS, TR, kFused, 16, 2, true>();
   }
 }
 
@@ -1258,7 +1309,7 @@ void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, doubl
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
   dim3 grid((n + kTx - 1) / kTx, (n + kTy - 1) / kTy);
-  k_pcg_apply_p<TC><<<grid, kThreads, 0, s>>>(zprev, pold, pnew, q, znext, kcoef, part, st, n);
+  launch(k_pcg_apply_p<TC>, dim3(grid), dim3(kThreads), 0, s, zprev, pold, pnew, q, znext, kcoef, part, st, n);
 }
 template void launch_pcg_apply_p<double>(const double*, const double*, double*, double*, double*, const double*,
                                          double*, PcgState*, int, cudaStream_t);
@@ -1284,8 +1335,7 @@ template <typename TC, typename TS>
 void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,
                            const TC* z, const TC* kinv, const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_resid_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, r, z, kinv, part, nc,
-                                                         b, n, st);
+  launch(k_resid_restrict<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, cs.slot_ptr, (const TS*)cs.owned, r, z, kinv, part, nc, b, n, st);
 }
 template void launch_resid_restrict<double, double>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                                     const double*, const double*, const PcgState*, cudaStream_t);
@@ -1298,7 +1348,7 @@ template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_restrict<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, (const TS*)cs.owned, v, part, nc, b, n, st);
+  launch(k_restrict<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, cs.slot_ptr, (const TS*)cs.owned, v, part, nc, b, n, st);
 }
 int sm_count();
 template <typename TC, typename TS, typename TR, bool kFused> void smoother_prepare();
@@ -1333,11 +1383,11 @@ void configure_kernels(int max_coarse_dim) {
 }
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s) {
   TG_COUNT(1);
-  k_pcg_reset<<<1, 32, 0, s>>>(st, rtol, maxit, flexible);
+  launch(k_pcg_reset, dim3(1), dim3(32), 0, s, st, rtol, maxit, flexible);
 }
 void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_set_condition<<<1, 32, 0, s>>>(cond, st);
+  launch(k_set_condition, dim3(1), dim3(32), 0, s, cond, st);
 }
 void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
                          cudaStream_t s) {
@@ -1345,24 +1395,23 @@ void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coef
   if (cs.D > kCoarseSplit) {
     double* rhs = coefs + cs.D;
     TG_COUNT(2);
-    k_coarse_rhs<<<(cs.D + kThreads - 1) / kThreads, kThreads, 0, s>>>(part, cs.gather, rhs, cs.D, st);
+    launch(k_coarse_rhs, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rhs, cs.D, st);
     int grid = (cs.D + 7) / 8;
     if (grid > 2 * sm_count()) grid = 2 * sm_count();
-    k_coarse_gemv<<<grid, kThreads, shm, s>>>(rhs, cs.Kinv, coefs, cs.D, st);
+    launch(k_coarse_gemv, dim3(grid), dim3(kThreads), shm, s, rhs, cs.Kinv, coefs, cs.D, st);
     return;
   }
   int grid = (cs.D + 7) / 8;
   if (grid > 2 * 152) grid = 2 * 152;
   if (grid < 1) grid = 1;
   TG_COUNT(1);
-  k_coarse_solve<<<grid, kThreads, shm, s>>>(part, cs.gather, cs.Kinv, coefs, cs.D, st);
+  launch(k_coarse_solve, dim3(grid), dim3(kThreads), shm, s, part, cs.gather, cs.Kinv, coefs, cs.D, st);
 }
 template <typename TC, typename TS>
 void launch_prolong(const CoarseSpace& cs, const double* coefs, int nblocks, int nc, int b, int n, TC* v,
                     const PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_prolong<TC, TS><<<nblocks, kThreads, 0, s>>>(cs.slot_ptr, cs.slots, (const TS*)cs.owned, coefs, v, nc, b, n,
-                                                  st);
+  launch(k_prolong<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, cs.slot_ptr, cs.slots, (const TS*)cs.owned, coefs, v, nc, b, n, st);
 }
 template void launch_restrict<double, double>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                               const PcgState*, cudaStream_t);
@@ -1379,13 +1428,13 @@ template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, const dou
 
 void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_stencil_coefs<<<grid_for((long long)n * n), kThreads, 0, s>>>(kinv, kcoef, n);
+  launch(k_stencil_coefs, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, kinv, kcoef, n);
 }
 
 template <typename TA, typename TB>
 void launch_convert(const TA* a, TB* b, long long m, cudaStream_t s) {
   TG_COUNT(1);
-  k_convert<TA, TB><<<grid_for(m), kThreads, 0, s>>>(a, b, m);
+  launch(k_convert<TA, TB>, dim3(grid_for(m)), dim3(kThreads), 0, s, a, b, m);
 }
 template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);

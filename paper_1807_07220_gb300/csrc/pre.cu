@@ -78,6 +78,7 @@ __device__ double block_reduce_sum(double v) {
 // boundary lift: outward normal velocity bflux -> face values; interior 0
 __global__ void k_lift(const double* __restrict__ bflux, double* __restrict__ ux,
                        double* __restrict__ uy, int n) {
+  pdl_entry();
   const long long m = (long long)(n + 1) * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
        t += (long long)gridDim.x * blockDim.x) {
@@ -112,6 +113,7 @@ __device__ __forceinline__ double cell_outflow(const double* ux, const double* u
 __global__ void k_block_sources(const double* __restrict__ f, const double* __restrict__ ux,
                                 const double* __restrict__ uy, double* __restrict__ FH,
                                 double* __restrict__ absF, int n, int b) {
+  pdl_entry();
   __shared__ double sa[32], sb[32];
   const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const double h = 1.0 / n;
@@ -149,6 +151,7 @@ __global__ void k_block_sources(const double* __restrict__ f, const double* __re
 __global__ void k_rt_particular(const double* __restrict__ FH, const double* __restrict__ absF,
                                 double* __restrict__ gx, double* __restrict__ gy, int nc, double H,
                                 int nblocks, PcgState* st) {
+  pdl_entry();
   extern __shared__ double sm[];
   double* rowt = sm;            // nc row totals -> flux above each block row (column 0)
   double* fh = sm + nc;         // block sources staged in shared memory
@@ -192,6 +195,7 @@ __global__ void k_rt_particular(const double* __restrict__ FH, const double* __r
 // u += interpolation of the coarse RT0 field g onto the interior fine faces
 __global__ void k_add_rt_field(const double* __restrict__ gx, const double* __restrict__ gy,
                                double* __restrict__ ux, double* __restrict__ uy, int n, int b) {
+  pdl_entry();
   const int nc = n / b;
   const long long m = (long long)(n + 1) * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
@@ -242,6 +246,7 @@ __device__ __forceinline__ double Au_y(const double* uy, const double* kinv, int
 // rho = C^T (-A u) at the interior nodes (the residual of the reduced system)
 __global__ void k_face_residual(const double* __restrict__ ux, const double* __restrict__ uy,
                                 const double* __restrict__ kinv, double* __restrict__ rho, int n) {
+  pdl_entry();
   // Au_x / Au_y already carry the 1/h of C^T: rho = sum of (-A u)/h over the four faces
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -259,6 +264,7 @@ __global__ void k_face_residual(const double* __restrict__ ux, const double* __r
 // u += C psi on the interior faces
 __global__ void k_add_curl(const double* __restrict__ psi, double* __restrict__ ux,
                            double* __restrict__ uy, int n) {
+  pdl_entry();
   const long long m = (long long)(n + 1) * n;
   const double inv_h = (double)n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
@@ -286,6 +292,7 @@ __global__ void k_add_curl(const double* __restrict__ psi, double* __restrict__ 
 // transport along each row.
 __global__ void k_block_particular(const double* __restrict__ f, double* __restrict__ ux,
                                    double* __restrict__ uy, int n, int b) {
+  pdl_entry();
   __shared__ double s[kMaxB * kMaxB];
   __shared__ double up[kMaxB + 1];
   const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
@@ -325,6 +332,7 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
 // offset per row to the y-face equations in least squares, zero mean.
 __global__ void k_pressure_rows(const double* __restrict__ ux, const double* __restrict__ kinv,
                                 double* __restrict__ rowp, int n) {
+  pdl_entry();
   const int j = blockIdx.x;
   double* row = rowp + (long long)j * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = (i == 0) ? 0.0 : -Au_x(ux, kinv, n, i, j);
@@ -335,6 +343,7 @@ __global__ void k_pressure_rows(const double* __restrict__ ux, const double* __r
 __global__ void k_pressure_steps(const double* __restrict__ uy, const double* __restrict__ kinv,
                                  const double* __restrict__ rowp, double* __restrict__ step,
                                  double* __restrict__ rowsum, int n) {
+  pdl_entry();
   __shared__ double sh[32];
   const int j = blockIdx.x;  // row j -> j+1 (j < n-1); row sums for all rows
   double a = 0.0, rs = 0.0;
@@ -366,6 +375,7 @@ __global__ void k_pressure_steps(const double* __restrict__ uy, const double* __
 // step[n] receives the mean of the pressure.
 __global__ void k_pressure_offsets(double* __restrict__ step, const double* __restrict__ rowsum,
                                    int n) {
+  pdl_entry();
   extern __shared__ double c[];
   for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = (j == 0) ? 0.0 : step[j - 1];
   __syncthreads();
@@ -381,6 +391,7 @@ __global__ void k_pressure_offsets(double* __restrict__ step, const double* __re
 
 __global__ void k_pressure_final(const double* __restrict__ rowp, const double* __restrict__ off,
                                  double* __restrict__ p, int n) {
+  pdl_entry();
   const long long nn = (long long)n * n;
   const double mean = off[n];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -391,6 +402,7 @@ __global__ void k_pressure_final(const double* __restrict__ rowp, const double* 
 // max_c |outflow_c - h^2 f_c| and max_c |h^2 f_c| per CTA
 __global__ void k_div_error(const double* __restrict__ ux, const double* __restrict__ uy,
                             const double* __restrict__ f, double* __restrict__ part, int n) {
+  pdl_entry();
   __shared__ double sa[32], sb[32];
   const long long nn = (long long)n * n;
   const double h = 1.0 / n;
@@ -422,6 +434,7 @@ __global__ void k_div_error(const double* __restrict__ ux, const double* __restr
 }
 
 __global__ void k_div_error_final(const double* __restrict__ part, int g, double* __restrict__ out) {
+  pdl_entry();
   double a = 0.0, m = 0.0;
   for (int k = threadIdx.x; k < g; k += 32) {
     a = fmax(a, part[2 * k]);
@@ -438,37 +451,37 @@ __global__ void k_div_error_final(const double* __restrict__ part, int g, double
 
 void launch_lift(const double* bflux, double* ux, double* uy, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_lift<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(bflux, ux, uy, n);
+  launch(k_lift, dim3(grid_for((long long)(n + 1) * n)), dim3(kThreads), 0, s, bflux, ux, uy, n);
 }
 void launch_block_sources(const double* f, const double* ux, const double* uy, double* FH, double* absF,
                           int n, int b, cudaStream_t s) {
   const int nc = n / b;
   TG_COUNT(1);
-  k_block_sources<<<nc * nc, kThreads, 0, s>>>(f, ux, uy, FH, absF, n, b);
+  launch(k_block_sources, dim3(nc * nc), dim3(kThreads), 0, s, f, ux, uy, FH, absF, n, b);
 }
 void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
                           int nblocks, PcgState* st, cudaStream_t s) {
   TG_COUNT(1);
-  k_rt_particular<<<1, 256, sizeof(double) * (size_t)(nc + nblocks), s>>>(FH, absF, gx, gy, nc, H, nblocks, st);
+  launch(k_rt_particular, dim3(1), dim3(256), sizeof(double) * (size_t)(nc + nblocks), s, FH, absF, gx, gy, nc, H, nblocks, st);
 }
 void launch_add_rt_field(const double* gx, const double* gy, double* ux, double* uy, int n, int b,
                          cudaStream_t s) {
   TG_COUNT(1);
-  k_add_rt_field<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(gx, gy, ux, uy, n, b);
+  launch(k_add_rt_field, dim3(grid_for((long long)(n + 1) * n)), dim3(kThreads), 0, s, gx, gy, ux, uy, n, b);
 }
 void launch_face_residual(const double* ux, const double* uy, const double* kinv, double* rho, int n,
                           cudaStream_t s) {
   TG_COUNT(1);
-  k_face_residual<<<grid_for((long long)n * n), kThreads, 0, s>>>(ux, uy, kinv, rho, n);
+  launch(k_face_residual, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, ux, uy, kinv, rho, n);
 }
 void launch_add_curl(const double* psi, double* ux, double* uy, int n, cudaStream_t s) {
   TG_COUNT(1);
-  k_add_curl<<<grid_for((long long)(n + 1) * n), kThreads, 0, s>>>(psi, ux, uy, n);
+  launch(k_add_curl, dim3(grid_for((long long)(n + 1) * n)), dim3(kThreads), 0, s, psi, ux, uy, n);
 }
 void launch_block_particular(const double* f, double* ux, double* uy, int n, int b, cudaStream_t s) {
   const int nc = n / b;
   TG_COUNT(1);
-  k_block_particular<<<nc * nc, 32, 0, s>>>(f, ux, uy, n, b);
+  launch(k_block_particular, dim3(nc * nc), dim3(32), 0, s, f, ux, uy, n, b);
 }
 void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p, double* work,
                      int n, cudaStream_t s) {
@@ -476,21 +489,21 @@ void launch_pressure(const double* ux, const double* uy, const double* kinv, dou
   double* step = work + (long long)n * n;
   double* rowsum = step + n + 1;
   TG_COUNT(1);
-  k_pressure_rows<<<n, 256, 0, s>>>(ux, kinv, rowp, n);
+  launch(k_pressure_rows, dim3(n), dim3(256), 0, s, ux, kinv, rowp, n);
   TG_COUNT(1);
-  k_pressure_steps<<<n, 128, 0, s>>>(uy, kinv, rowp, step, rowsum, n);
+  launch(k_pressure_steps, dim3(n), dim3(128), 0, s, uy, kinv, rowp, step, rowsum, n);
   TG_COUNT(1);
-  k_pressure_offsets<<<1, 256, sizeof(double) * (size_t)n, s>>>(step, rowsum, n);
+  launch(k_pressure_offsets, dim3(1), dim3(256), sizeof(double) * (size_t)n, s, step, rowsum, n);
   TG_COUNT(1);
-  k_pressure_final<<<grid_for((long long)n * n), kThreads, 0, s>>>(rowp, step, p, n);
+  launch(k_pressure_final, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, rowp, step, p, n);
 }
 void launch_div_error(const double* ux, const double* uy, const double* f, double* part, double* out,
                       int n, cudaStream_t s) {
   const int g = grid_for((long long)n * n) > kRedGrid ? kRedGrid : grid_for((long long)n * n);
   TG_COUNT(1);
-  k_div_error<<<g, kThreads, 0, s>>>(ux, uy, f, part, n);
+  launch(k_div_error, dim3(g), dim3(kThreads), 0, s, ux, uy, f, part, n);
   TG_COUNT(1);
-  k_div_error_final<<<1, 32, 0, s>>>(part, g, out);
+  launch(k_div_error_final, dim3(1), dim3(32), 0, s, part, g, out);
 }
 
 }  // namespace tg

@@ -37,7 +37,7 @@ class tg_options(ctypes.Structure):
                 ("flexible", c_int), ("max_iter", c_int), ("pointer_mode", c_int),
                 ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
                 ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
-                ("learned_max_iter", c_int), ("smoother_shape", c_int)]
+                ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int)]
 
 
 class tg_report(ctypes.Structure):
@@ -47,7 +47,7 @@ class tg_report(ctypes.Structure):
                 ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double),
                 ("kernel_launches", c_int), ("smoother_launches", c_int), ("smoother_ms", c_double),
                 ("graph", c_int), ("snapshot_solves", c_int), ("fallback_faces", c_int),
-                ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 5)]
+                ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 7)]
 
     def shape_times(self):
         return [float(v) for v in self.shape_us]
