@@ -324,7 +324,9 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
   const int n = h->n, nc = h->nc;
   const long long nn = (long long)n * n, nf = (long long)(n + 1) * n;
   const size_t tc = (h->opt.precision == TG_PREC_F64) ? 8 : 4;
-  const long long npart = 4 * std::max<long long>(kRedGrid, (long long)((n + 31) / 32) * ((n + 7) / 8));
+  // partials: reductions over up to max(kRedGrid, stencil tiles) CTAs, and the
+  // last smoothing sweep's two dot products over its one-wave grid
+  const long long npart = 4 * std::max<long long>(2048, (long long)((n + 31) / 32) * ((n + 7) / 8));
   int rc = TG_OK;
   if (dalloc(&c->x, nn) || dalloc(&c->r, nn) || dalloc(&c->p, nn) || dalloc(&c->q, nn) || dalloc(&c->rho, nn) ||
       dalloc(&c->phi, nn) || dalloc(&c->p2, nn) || dalloc(&c->r2, nn) || dalloc(&c->ux, nf) || dalloc(&c->uy, nf) ||
@@ -384,8 +386,7 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
   }
   if (h->cs.D > 0) {
     launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, zacc, kin, st, s);
-    launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
-    launch_prolong<TC, tile_t<TS>>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
+    launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r, zacc, kin, rin, n, st, s);
@@ -407,9 +408,8 @@ void enqueue_preprocess(Ctx* c, const double* f, const double* bflux, double* ux
   if (h->rt.D > 0) {
     launch_face_residual(ux, uy, h->kinv, c->rho, n, s);
     launch_restrict<double, double>(h->rt, c->rt_part, h->nblocks, h->nc, b, n, c->rho, nullptr, s);
-    launch_coarse_solve(h->rt, c->rt_part, c->rt_coefs, nullptr, s);
     cudaMemsetAsync(c->phi, 0, sizeof(double) * nn, s);
-    launch_prolong<double, double>(h->rt, c->rt_coefs, h->nblocks, h->nc, b, n, c->phi, nullptr, s);
+    launch_coarse_correct<double, double>(h->rt, c->rt_part, c->rt_coefs, h->nblocks, h->nc, b, n, c->phi, nullptr, s);
     launch_add_curl(c->phi, ux, uy, n, s);
   }
   launch_block_particular(f, ux, uy, n, b, s);
@@ -464,13 +464,37 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   double* p_new = parity ? c->p : c->p2;
   double* r_old = parity ? c->r2 : c->r;
   double* r_new = parity ? c->r : c->r2;
-  TC* z_prev = (TC*)(parity ? c->zacc2 : c->zacc);
-  TC* z_cur = (TC*)(parity ? c->zacc : c->zacc2);
   const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
   TC* rin = (TC*)c->rin;
   const TS* pinv = (const TS*)h->pinv;
   const double eta = h->opt.eta;
   PcgState* st = c->st;
+  if (h->opt.m1 == 1 && h->opt.m2 == 1) {
+    // The cycle of Section 6 (m1 = m2 = 1) in five kernels.  z ends every
+    // iteration in zacc (A); zacc2 (B) holds the intermediate z.  The first
+    // sweep accumulates into B and clears A (dead once p is formed), the
+    // coarse step adds into B, and the last sweep forms r - K z_B at gather
+    // time and accumulates z_B + S(r - K z_B) into A.
+    TC* zA = (TC*)c->zacc;
+    TC* zB = (TC*)c->zacc2;
+    launch_pcg_apply_p<TC>(zA, p_old, p_new, c->q, zB, h->kcoef, c->part, st, n, s);
+    prof_mark(c, s);
+    launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
+                                   p_new, zB, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, zA);
+    prof_mark(c, s);
+    if (h->cs.D > 0) {
+      launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, zB, kin, st, s);
+      launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, zB, st, s);
+    }
+    prof_mark(c, s);
+    launch_smoother_resid<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_new, zB, kin, zA, eta, n,
+                                  h->nc, h->b, st, s, h->shape, h->rscale);
+    prof_mark(c, s);
+    launch_pcg_dots<TC>(r_new, zA, c->q, c->part, st, n, s);
+    return;
+  }
+  TC* z_prev = (TC*)(parity ? c->zacc2 : c->zacc);
+  TC* z_cur = (TC*)(parity ? c->zacc : c->zacc2);
   launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
   prof_mark(c, s);
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
@@ -484,8 +508,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   }
   if (h->cs.D > 0) {
     launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, z_cur, kin, st, s);
-    launch_coarse_solve(h->cs, c->cs_part, c->cs_coefs, st, s);
-    launch_prolong<TC, tile_t<TS>>(h->cs, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
+    launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
   }
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);

@@ -243,7 +243,13 @@ template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape = 0, const float* rscale = nullptr);
+                            cudaStream_t s, int shape = 0, const float* rscale = nullptr, TC* zclear = nullptr);
+// last smoothing sweep with the residual formed at gather time:
+// zout (zeroed beforehand) = zin + eta sum_i E_i M_i E_i^T (r - K zin)
+template <typename TC, typename TS>
+void launch_smoother_resid(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                           const double* r, const TC* zin, const TC* kin, TC* zout, double eta, int n, int nc, int b,
+                           const PcgState* st, cudaStream_t s, int shape, const float* rscale);
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);
@@ -257,6 +263,11 @@ constexpr int kRowsPerGroup = 4;   // rows of a patch inverse streamed together 
 template <typename TC, typename TS>
 void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const TC* v,
                      const PcgState* st, cudaStream_t s);
+// v += Psi K_H^{-1} c (c formed from the slot partials): one fused kernel for
+// small coarse systems, else the coarse solve then the prolongation
+template <typename TC, typename TS>
+void launch_coarse_correct(const CoarseSpace& cs, const double* part, double* coefs, int nblocks, int nc, int b, int n,
+                           TC* v, const PcgState* st, cudaStream_t s);
 // coefs: 2 D doubles; d = coefs[0, D), the second half is right-hand-side scratch
 void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
                          cudaStream_t s);

@@ -559,9 +559,16 @@ struct FuseArgs {
   double* part;
   PcgState* st;
   int nc, b;
+  void* zclear;         // mode 1: z buffer zeroed on the owned nodes (or NULL)
+  const void* zin;      // mode 2: z before the sweep (TC), read for the residual
+  const void* kin;      // mode 2: inverse permeabilities (TC)
 };
 
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe>
+// kFused: 0 plain sweep z += eta S r; 1 first sweep of an iteration (r - alpha q
+// formed at gather time, r, x updated and (r, r) reduced by the block
+// owners); 2 last sweep with the residual formed at gather time,
+// r_in = r - K z_in, into a z buffer that the owners seed with z_in.
+template <typename TC, typename TS, typename TR, int kFused, int kCB, int kR, bool kPipe>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
                                                        const int* __restrict__ gofs, int npatch,
                                                        const TS* __restrict__ pinv,
@@ -573,17 +580,22 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
   if (st && st->done) return;
   __shared__ __align__(16) TC xs[kPatchLd];
   __shared__ double shr[32];
-  const double alpha = kFused ? fa.st->alpha : 0.0;
+  const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
   double rr = 0.0;
   const int G = gofs[npatch];
   const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
   const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
-  int p = 0, hi = npatch - 1;  // last patch with gofs[p] <= g0
-  while (p < hi) {
-    const int mid = (p + hi + 1) >> 1;
-    if (gofs[mid] <= g0) p = mid;
-    else hi = mid - 1;
-  }
+  // last patch with gofs[p] <= g0: gofs is strictly increasing (every patch
+  // has at least one row group), so exactly one thread finds p with
+  // gofs[p] <= g0 < gofs[p+1] in one round of loads (none when g0 = G: the
+  // CTA is empty and p = npatch - 1 as a bisection would give)
+  __shared__ int sp;
+  if (threadIdx.x == 0) sp = npatch - 1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < npatch; t += blockDim.x)
+    if (gofs[t] <= g0 && gofs[t + 1] > g0) sp = t;
+  __syncthreads();
+  int p = sp;
   constexpr int W = kCB / (int)sizeof(TS);
   constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -595,12 +607,15 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
       if (q < g.nloc) {
         const int a = q % g.nx, c = q / g.nx;
         const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
-        if (kFused) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+        if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+        else if constexpr (kFused == 2)
+          v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
+                                                    g.y0 + 1 + c);
         else v = (TC)r[id];
       }
       xs[q] = v;
     }
-    if (kFused && gofs[p] >= g0) {   // this CTA owns block p
+    if (kFused == 1 && gofs[p] >= g0) {   // this CTA owns block p
       const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
       for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
         const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
@@ -608,6 +623,14 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
         fa.r_new[id] = rv;
         fa.x[id] += alpha * fa.p[id];
         rr += rv * rv;
+        if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
+      }
+    }
+    if (kFused == 2 && gofs[p] >= g0) {   // the owner seeds the output with z_in
+      const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+      for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+        atomicAdd(zacc + id, ((const TC*)fa.zin)[id]);
       }
     }
     __syncthreads();
@@ -680,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
       }
     }
   }
-  if (kFused) {
+  if (kFused == 1) {
     rr = block_sum(rr, shr);
     if (arrive_last(rr, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
       const double tot = sum_partials(fa.part, gridDim.x);
@@ -781,7 +804,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __res
   TS* buf = reinterpret_cast<TS*>(dsm);
   const int stage_elems = kStageRows * kPatchLd;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const double alpha = kFused ? fa.st->alpha : 0.0;
+  const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
   const int G = gofs[npatch];
   const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
   const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
@@ -884,6 +907,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __res
         fa.r_new[id] = rv;
         fa.x[id] += alpha * fa.p[id];
         rr += rv * rv;
+        if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
       }
     }
     rr = block_sum(rr, shr);
@@ -1065,6 +1089,53 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const int* __restrict__ sl
   v[(long long)(J * b + t / b) * n + I * b + t % b] += acc;
 }
 
+// Small coarse systems (D <= kCoarseSplit, at most kFuseSlots slots per block):
+// the coarse solve and the prolongation in one kernel.  Each CTA (one block)
+// forms the whole right-hand side c, computes d_u = (K_H^{-1} c)_u only for
+// the unknowns of its own slots (warp per row, the lane order of
+// k_coarse_solve, so d is bit-identical), then adds sum_s d * tile_s on its
+// owned nodes exactly as k_prolong does.
+constexpr int kFuseSlots = 64;
+template <typename TC, typename TS>
+__global__ void __launch_bounds__(kThreads) k_coarse_prolong(const double* __restrict__ part,
+                                                             const int* __restrict__ gather,
+                                                             const double* __restrict__ Kinv, int D,
+                                                             const int* __restrict__ slot_ptr,
+                                                             const Slot* __restrict__ slots,
+                                                             const TS* __restrict__ owned, TC* __restrict__ v,
+                                                             int nc, int b, int n, const PcgState* st) {
+  pdl_entry();
+  if (st && st->done) return;
+  __shared__ double cvec[kCoarseSplit];
+  __shared__ double dloc[kFuseSlots];
+  for (int u = threadIdx.x; u < D; u += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = gather[4 * u + k];
+      if (g >= 0) sum += part[g];
+    }
+    cvec[u] = sum;
+  }
+  __syncthreads();
+  const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  const int s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < m; j += nw) {
+    const double* kr = Kinv + (long long)slots[s0 + j].coef * D;
+    double acc = 0.0;
+    for (int col = lane; col < D; col += 32) acc += kr[col] * cvec[col];
+    acc = warp_sum(acc);
+    if (lane == 0) dloc[j] = acc;
+  }
+  __syncthreads();
+  const int bb = b * b, t = threadIdx.x;
+  if (t >= bb) return;
+  TC acc = (TC)0;
+  for (int j = 0; j < m; ++j) acc += (TC)dloc[j] * (TC)to_f(owned[(long long)(s0 + j) * bb + t]);
+  v[(long long)(J * b + t / b) * n + I * b + t % b] += acc;
+}
+
 // node coefficients of K (FP64): c0, cE, cN, cNE, cNW, cells outside the domain as 0
 __global__ void k_stencil_coefs(const double* __restrict__ kinv, double* __restrict__ kcoef, int n) {
   pdl_entry();
@@ -1175,7 +1246,7 @@ int sm_count() {
 }
 
 // resident CTAs per SM of a smoother instantiation (queried once, at setup)
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe>
+template <typename TC, typename TS, typename TR, int kFused, int kCB, int kR, bool kPipe>
 int smoother_per_sm() {
   static int per_sm = 0;
   if (!per_sm) {
@@ -1215,7 +1286,7 @@ int tma_per_sm() {
 // shapes 3 and 1 software-pipelined (the next pass's rows in flight while the
 // current pass is reduced).  FP64 storage has shapes 0 and 4 only (others map
 // to 0).
-template <typename TC, typename TS, typename TR, bool kFused, int kCB, int kR, bool kPipe = false>
+template <typename TC, typename TS, typename TR, int kFused, int kCB, int kR, bool kPipe = false>
 void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                  TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa, const float* rscale,
                  cudaStream_t s) {
@@ -1223,19 +1294,20 @@ void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, 
   launch(k_smoother<TC, TS, TR, kFused, kCB, kR, kPipe>, dim3(grid), dim3(kThreads), 0, s, geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, st, fa, rscale);
 }
 
-template <typename TC, typename TS, typename TR, bool kFused>
+template <typename TC, typename TS, typename TR, int kFused>
 void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                     const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
                     const float* rscale, cudaStream_t s) {
   TG_COUNT(1);
   constexpr bool kHalf = std::is_same<TS, __half>::value;
-  if (kHalf && shape == 4) shape = 0;   // the TMA ring has no row scaling
+  // the TMA ring has no row scaling and no residual-fused mode
+  if ((kHalf || kFused == 2) && shape == 4) shape = 0;
   if (shape == 4) {
-    if constexpr (!kHalf) {
-      int grid = tma_per_sm<TC, TS, TR, kFused>() * sm_count();
+    if constexpr (!kHalf && kFused != 2) {
+      int grid = tma_per_sm<TC, TS, TR, kFused == 1>() * sm_count();
       if (grid * 2 > ngroups) grid = (ngroups + 1) / 2;
-      launch(k_smoother_tma<TC, TS, TR, kFused>, dim3(grid < 1 ? 1 : grid), dim3(kThreads), tma_smem<TS>(), s, geo,
-             gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
+      launch(k_smoother_tma<TC, TS, TR, kFused == 1>, dim3(grid < 1 ? 1 : grid), dim3(kThreads), tma_smem<TS>(), s,
+             geo, gofs, npatch, pinv, r, zacc, (TC)eta, n, const_cast<PcgState*>(st), fa);
     }
     return;
   }
@@ -1254,9 +1326,9 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
 }
 
 // occupancy queries of every shape of one instantiation (outside any capture)
-template <typename TC, typename TS, typename TR, bool kFused>
+template <typename TC, typename TS, typename TR, int kFused>
 void smoother_prepare() {
-  if constexpr (!std::is_same<TS, __half>::value) tma_per_sm<TC, TS, TR, kFused>();
+  if constexpr (!std::is_same<TS, __half>::value && kFused != 2) tma_per_sm<TC, TS, TR, kFused == 1>();
   if constexpr (std::is_same<TS, double>::value) {
     smoother_per_sm<TC, TS, TR, kFused, 16, 2, false>();
   } else {
@@ -1281,28 +1353,49 @@ template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape, const float* rscale) {
-  FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b};
-  smoother_shape<TC, TS, double, true>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa,
-                                       rscale, s);
+                            cudaStream_t s, int shape, const float* rscale, TC* zclear) {
+  FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b, zclear, nullptr, nullptr};
+  smoother_shape<TC, TS, double, 1>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa,
+                                    rscale, s);
 }
+
+template <typename TC, typename TS>
+void launch_smoother_resid(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                           const double* r, const TC* zin, const TC* kin, TC* zout, double eta, int n, int nc, int b,
+                           const PcgState* st, cudaStream_t s, int shape, const float* rscale) {
+  FuseArgs fa{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nc, b, nullptr, zin, kin};
+  smoother_shape<TC, TS, double, 2>(shape, geo, gofs, npatch, ngroups, pinv, r, zout, eta, n, st, fa, rscale, s);
+}
+template void launch_smoother_resid<double, double>(const PatchGeo*, const int*, int, int, const double*,
+                                                    const double*, const double*, const double*, double*, double,
+                                                    int, int, int, const PcgState*, cudaStream_t, int, const float*);
+template void launch_smoother_resid<float, float>(const PatchGeo*, const int*, int, int, const float*, const double*,
+                                                  const float*, const float*, float*, double, int, int, int,
+                                                  const PcgState*, cudaStream_t, int, const float*);
+template void launch_smoother_resid<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
+                                                          const __nv_bfloat16*, const double*, const float*,
+                                                          const float*, float*, double, int, int, int,
+                                                          const PcgState*, cudaStream_t, int, const float*);
+template void launch_smoother_resid<float, __half>(const PatchGeo*, const int*, int, int, const __half*,
+                                                   const double*, const float*, const float*, float*, double, int,
+                                                   int, int, const PcgState*, cudaStream_t, int, const float*);
 template void launch_smoother_update<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                      const double*, double*, const double*, double*,
                                                      const double*, double*, double, int, int, int, double*,
-                                                     PcgState*, cudaStream_t, int, const float*);
+                                                     PcgState*, cudaStream_t, int, const float*, double*);
 template void launch_smoother_update<float, float>(const PatchGeo*, const int*, int, int, const float*,
                                                    const double*, double*, const double*, double*,
                                                    const double*, float*, double, int, int, int, double*,
-                                                   PcgState*, cudaStream_t, int, const float*);
+                                                   PcgState*, cudaStream_t, int, const float*, float*);
 template void launch_smoother_update<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
                                                            const __nv_bfloat16*, const double*, double*,
                                                            const double*, double*, const double*, float*, double,
                                                            int, int, int, double*, PcgState*, cudaStream_t, int,
-                                                           const float*);
+                                                           const float*, float*);
 template void launch_smoother_update<float, __half>(const PatchGeo*, const int*, int, int, const __half*,
                                                     const double*, double*, const double*, double*, const double*,
                                                     float*, double, int, int, int, double*, PcgState*, cudaStream_t,
-                                                    int, const float*);
+                                                    int, const float*, float*);
 
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
@@ -1351,7 +1444,7 @@ void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, i
   launch(k_restrict<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, cs.slot_ptr, (const TS*)cs.owned, v, part, nc, b, n, st);
 }
 int sm_count();
-template <typename TC, typename TS, typename TR, bool kFused> void smoother_prepare();
+template <typename TC, typename TS, typename TR, int kFused> void smoother_prepare();
 int read_and_clear_timeout() {
   int v = 0;
   cudaMemcpyFromSymbol(&v, g_timeout_flag, sizeof(int));
@@ -1375,6 +1468,10 @@ void configure_kernels(int max_coarse_dim) {
   smoother_prepare<float, __half, double, false>();
   smoother_prepare<float, __half, float, false>();
   smoother_prepare<float, __half, double, true>();
+  smoother_prepare<double, double, double, 2>();
+  smoother_prepare<float, float, double, 2>();
+  smoother_prepare<float, __nv_bfloat16, double, 2>();
+  smoother_prepare<float, __half, double, 2>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
   if (shm > 48 * 1024) {
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -1413,6 +1510,24 @@ void launch_prolong(const CoarseSpace& cs, const double* coefs, int nblocks, int
   TG_COUNT(1);
   launch(k_prolong<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, cs.slot_ptr, cs.slots, (const TS*)cs.owned, coefs, v, nc, b, n, st);
 }
+template <typename TC, typename TS>
+void launch_coarse_correct(const CoarseSpace& cs, const double* part, double* coefs, int nblocks, int nc, int b, int n,
+                           TC* v, const PcgState* st, cudaStream_t s) {
+  if (cs.D <= kCoarseSplit && cs.max_slots_per_block <= kFuseSlots && b * b <= kThreads) {
+    TG_COUNT(1);
+    launch(k_coarse_prolong<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, part, cs.gather, cs.Kinv, cs.D, cs.slot_ptr,
+           cs.slots, (const TS*)cs.owned, v, nc, b, n, st);
+    return;
+  }
+  launch_coarse_solve(cs, part, coefs, st, s);
+  launch_prolong<TC, TS>(cs, coefs, nblocks, nc, b, n, v, st, s);
+}
+template void launch_coarse_correct<double, double>(const CoarseSpace&, const double*, double*, int, int, int, int,
+                                                    double*, const PcgState*, cudaStream_t);
+template void launch_coarse_correct<float, float>(const CoarseSpace&, const double*, double*, int, int, int, int,
+                                                  float*, const PcgState*, cudaStream_t);
+template void launch_coarse_correct<float, __nv_bfloat16>(const CoarseSpace&, const double*, double*, int, int, int,
+                                                          int, float*, const PcgState*, cudaStream_t);
 template void launch_restrict<double, double>(const CoarseSpace&, double*, int, int, int, int, const double*,
                                               const PcgState*, cudaStream_t);
 template void launch_restrict<float, float>(const CoarseSpace&, double*, int, int, int, int, const float*,
