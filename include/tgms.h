@@ -186,6 +186,18 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol,
 int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol,
              double* ux, double* uy, double* p, int* iters, tg_report* rep);
 
+/* tg_solve from an initial guess (ux0, uy0) of the velocity, e.g. the
+ * previous step of a time-dependent run: PCG starts from the stream function
+ * of the guess minus the preprocessing field vbar (built by integrating its
+ * x-face values up each node column, exact when the guess carries the same
+ * divergence and boundary flux as the solution; uy0 is not read and may be
+ * NULL).  rtol is relative to the residual of the zero guess, as in tg_solve,
+ * so the stopping target is the same and a good guess saves iterations; a
+ * guess already within it returns with 0 iterations.  Pointers follow
+ * pointer_mode like tg_solve's. */
+int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rtol, const double* ux0,
+                  const double* uy0, double* ux, double* uy, double* p, int* iters, tg_report* rep);
+
 /* Frees all device memory of the handle.  NULL is allowed. */
 void tg_destroy(tg_handle* h);
 

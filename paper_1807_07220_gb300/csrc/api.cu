@@ -83,10 +83,12 @@ struct Ctx {
   double* d_rtol = nullptr;
   double* h_rtol = nullptr;   // pinned
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  // one-chain graph of tg_solve
+  // one-chain graphs of tg_solve (zero initial guess) and tg_solve_warm
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  unsigned long long k_prefix = 0, k_body = 0, k_epi = 0;
+  cudaGraphExec_t exec = nullptr, exec_warm = nullptr;
+  unsigned long long k_prefix = 0, k_prefix_warm = 0, k_body = 0, k_epi = 0;
+  bool warm = false;            // enqueue the warm-start prefix
+  double* ux0 = nullptr;        // warm start: staged x-face velocities of the guess
   // profiling: events around smoother launches (profile == 1)
   std::vector<cudaEvent_t> prof_ev;
   int prof_used = 0;
@@ -303,7 +305,9 @@ int validate_grid(const tg_grid* g) {
 void ctx_free(Ctx* c) {
   if (!c) return;
   if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->exec_warm) cudaGraphExecDestroy(c->exec_warm);
   if (c->cap) cudaStreamDestroy(c->cap);
+  cudaFree(c->ux0);
   void* ptrs[] = {c->x, c->r, c->p, c->q, c->rho, c->phi, c->p2, c->r2, c->zacc, c->zacc2, c->rin, c->ux, c->uy,
                   c->fd, c->bd, c->pd, c->pw, c->part, c->gx, c->gy, c->FH, c->absF, c->diverr, c->cs_part,
                   c->cs_coefs, c->rt_part, c->rt_coefs, c->st, c->d_rtol};
@@ -442,8 +446,14 @@ void enqueue_prefix(Ctx* c, cudaStream_t s) {
   const long long nn = (long long)n * n;
   launch_pcg_reset(c->st, c->d_rtol, std::min(h->opt.max_iter, kMaxHist), h->opt.flexible, s);
   enqueue_preprocess(c, c->fd, c->bd, c->ux, c->uy, s);
-  cudaMemcpyAsync(c->r, c->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
-  launch_pcg_init(c->x, c->r, c->part, c->st, n, s);
+  if (c->warm) {
+    // x0 = stream function of the guess minus vbar; r = rho - K x0
+    launch_psi_from_faces(c->ux0, c->ux, c->pw, c->x, n, s);
+    launch_pcg_init_warm(c->x, c->rho, h->kinv, c->r, c->part, c->st, n, s);
+  } else {
+    cudaMemcpyAsync(c->r, c->rho, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+    launch_pcg_init(c->x, c->r, c->part, c->st, n, s);
+  }
   cudaMemsetAsync(c->zacc, 0, sizeof(TC) * nn, s);
   precondition<TC, TS>(c, c->r, (TC*)c->zacc, c->st, s);
   launch_pcg_init_rz<TC>(c->r, (const TC*)c->zacc, c->p, c->part, c->st, n, s);
@@ -541,7 +551,7 @@ int add_chain_t(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
   std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
   cudaGraph_t g2 = nullptr;
   TG_CK(cudaStreamEndCapture(cs, &g2));
-  c->k_prefix = g_kernel_launches - k0;
+  (c->warm ? c->k_prefix_warm : c->k_prefix) = g_kernel_launches - k0;
   cudaGraphConditionalHandle cond;
   TG_CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
@@ -1225,8 +1235,8 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
 
 namespace {
 
-int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
-               int* iters, tg_report* rep) {
+int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, const double* ux0, double* ux,
+               double* uy, double* p, int* iters, tg_report* rep) {
   g_pdl = (h->opt.launch_overlap != 0);
   Ctx* c = h->ctx;
   const int n = h->n;
@@ -1238,6 +1248,11 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
   TG_CK(cudaMemcpyAsync(c->fd, f, sizeof(double) * nn, in, s));
   if (bflux) TG_CK(cudaMemcpyAsync(c->bd, bflux, sizeof(double) * 4 * n, in, s));
   else TG_CK(cudaMemsetAsync(c->bd, 0, sizeof(double) * 4 * n, s));
+  c->warm = (ux0 != nullptr);
+  if (c->warm) {
+    if (!c->ux0 && dalloc(&c->ux0, (size_t)nf)) return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(c->ux0, ux0, sizeof(double) * nf, in, s));
+  }
   *c->h_rtol = rtol;
   TG_CK(cudaMemcpyAsync(c->d_rtol, c->h_rtol, sizeof(double), cudaMemcpyHostToDevice, s));
   unsigned long long launches = 0;
@@ -1247,15 +1262,16 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
     c->prof_used = 0;
     rc = run_loop(c, &launches);
   } else {
-    if (!c->exec) {
+    cudaGraphExec_t& ex = c->warm ? c->exec_warm : c->exec;
+    if (!ex) {
       cudaGraph_t g = nullptr;
       TG_CK(cudaGraphCreate(&g, 0));
       rc = add_chain(c, g, c->cap);
-      if (!rc) rc = cuda_err(cudaGraphInstantiate(&c->exec, g, 0));
+      if (!rc) rc = cuda_err(cudaGraphInstantiate(&ex, g, 0));
       cudaGraphDestroy(g);
       if (rc) return rc;
     }
-    TG_CK(cudaGraphLaunch(c->exec, s));
+    TG_CK(cudaGraphLaunch(ex, s));
   }
   cudaEventRecord(c->ev[3], s);
   if (rc) return rc;
@@ -1276,7 +1292,7 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
   if (!h->opt.profile) {
     // the while node ran the two-iteration body once per pair of iterations
     const unsigned long long passes = (unsigned long long)std::max((full->iter + 1) / 2, 1);
-    launches = c->k_prefix + passes * c->k_body + c->k_epi;
+    launches = (c->warm ? c->k_prefix_warm : c->k_prefix) + passes * c->k_body + c->k_epi;
   }
   if (iters) *iters = full->iter;
   if (rep) {
@@ -1321,27 +1337,39 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
   return status_to_err(status);
 }
 
-}  // namespace
-
-extern "C" {
-
-int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
-             int* iters, tg_report* rep) {
+int solve_entry(tg_handle* h, const double* f, const double* bflux, double rtol, const double* ux0, double* ux,
+                double* uy, double* p, int* iters, tg_report* rep) {
   if (!h || !f || !ux || !uy || !p || !(rtol > 0) || !(rtol < 1)) return TG_ERR_INVALID_ARG;
   int it = 0;
-  int rc = solve_impl(h, f, bflux, rtol, ux, uy, p, &it, rep);
+  int rc = solve_impl(h, f, bflux, rtol, ux0, ux, uy, p, &it, rep);
   int refit = 0;
   if ((rc == TG_OK || rc == TG_ERR_MAXITER) && h->opt.coarse_space == TG_COARSE_LEARNED &&
       h->opt.learned_max_iter > 0 && it > h->opt.learned_max_iter && h->fallback_faces < h->nfaces) {
     // the learned space needed too many iterations: exact space, solve again
     int rb = rebuild_exact(h);
     if (rb) return rb;
-    rc = solve_impl(h, f, bflux, rtol, ux, uy, p, &it, rep);
+    rc = solve_impl(h, f, bflux, rtol, ux0, ux, uy, p, &it, rep);
     refit = 1;
   }
   if (iters) *iters = it;
   if (rep) rep->learned_fallback = refit;
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol, double* ux, double* uy, double* p,
+             int* iters, tg_report* rep) {
+  return solve_entry(h, f, bflux, rtol, nullptr, ux, uy, p, iters, rep);
+}
+
+int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rtol, const double* ux0,
+                  const double* uy0, double* ux, double* uy, double* p, int* iters, tg_report* rep) {
+  (void)uy0;   // the x-face velocities determine the guess's stream function
+  if (!ux0) return TG_ERR_INVALID_ARG;
+  return solve_entry(h, f, bflux, rtol, ux0, ux, uy, p, iters, rep);
 }
 
 void tg_destroy(tg_handle* h) {

@@ -201,6 +201,11 @@ void launch_fill_scalars(const double* v, double* const* dst, int m, cudaStream_
 void launch_gather_states(PcgState* const* st, int* out, int m, cudaStream_t s);
 int read_and_clear_timeout();   // 1 if a bounded device wait expired since the last call
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s);
+// warm start: r = rho - K x, rr = |r|^2, rr0 = |rho|^2 (stopping reference)
+void launch_pcg_init_warm(const double* x, const double* rho, const double* kinv, double* r, double* part,
+                          PcgState* st, int n, cudaStream_t s);
+// warm start: x = stream function of the x-face part of ux0 - vx (colbuf: n*n scratch)
+void launch_psi_from_faces(const double* ux0, const double* vx, double* colbuf, double* psi, int n, cudaStream_t s);
 void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, cudaStream_t s);
 
 // fine operator / vectors (fine.cu)

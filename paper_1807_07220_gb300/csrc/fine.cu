@@ -377,6 +377,47 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
   }
 }
 
+// warm start: r = rho - K x (FP64), rr = (r, r); the stopping reference is the
+// zero-guess residual, rr0 = (rho, rho), so a good guess needs fewer iterations
+// for the same target
+__global__ void __launch_bounds__(kThreads) k_pcg_init_warm(const double* __restrict__ x,
+                                                            const double* __restrict__ rho,
+                                                            const double* __restrict__ kinv,
+                                                            double* __restrict__ r, double* part,
+                                                            PcgState* st, int n) {
+  pdl_entry();
+  __shared__ double sh[32];
+  const long long nn = (long long)n * n;
+  double a = 0.0, b = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    double v = 0.0;
+    if (i != 0 && j != 0) v = rho[t] - stencil_apply<double, double, double>(x, kinv, n, i, j);
+    r[t] = v;
+    a += v * v;
+    b += rho[t] * rho[t];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = b;
+  if (arrive_last(a, part, &st->counter[3]) && threadIdx.x < 32) {
+    const double rr = sum_partials(part, gridDim.x);
+    const double rr0 = sum_partials(part + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->counter[3] = 0;
+      st->rr0 = rr0;
+      st->rr = rr;
+      st->iter = 0;
+      if (rr0 == 0.0 || rr <= st->rtol2 * rr0) st->done = 1;
+      if (!isfinite(rr) || !isfinite(rr0)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+      }
+    }
+  }
+}
+
 // p = z, rz = (r, z)
 template <typename TC>
 __global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restrict__ r,
@@ -1477,6 +1518,11 @@ void configure_kernels(int max_coarse_dim) {
     cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     cudaFuncSetAttribute(k_coarse_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   }
+}
+void launch_pcg_init_warm(const double* x, const double* rho, const double* kinv, double* r, double* part,
+                          PcgState* st, int n, cudaStream_t s) {
+  TG_COUNT(1);
+  launch(k_pcg_init_warm, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, x, rho, kinv, r, part, st, n);
 }
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s) {
   TG_COUNT(1);

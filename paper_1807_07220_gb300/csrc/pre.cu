@@ -330,6 +330,27 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
 
 // pressure: integrate A u = B^T p along each row (x-faces), then fit one
 // offset per row to the y-face equations in least squares, zero mean.
+// Warm start: stream function of the x-face part of w = u0 - vbar, one CTA
+// per node column i: psi(i, 0) = 0, psi(i, j+1) = psi(i, j) + h w_x(i, j)
+// (exact when w is divergence free with zero boundary flux, the form of every
+// PCG iterate); column 0 is boundary.  col: n doubles of scratch per column.
+__global__ void k_psi_from_faces(const double* __restrict__ ux0, const double* __restrict__ vx,
+                                 double* __restrict__ colbuf, double* __restrict__ psi, int n) {
+  pdl_entry();
+  const int i = blockIdx.x;
+  const double h = 1.0 / n;
+  double* col = colbuf + (long long)i * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const long long f = (long long)j * (n + 1) + i;
+    col[j] = (i == 0) ? 0.0 : h * (ux0[f] - vx[f]);
+  }
+  __syncthreads();
+  block_inclusive_scan(col, n);
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    psi[(long long)j * n + i] = (i == 0 || j == 0) ? 0.0 : col[j - 1];
+}
+
 __global__ void k_pressure_rows(const double* __restrict__ ux, const double* __restrict__ kinv,
                                 double* __restrict__ rowp, int n) {
   pdl_entry();
@@ -483,6 +504,11 @@ void launch_block_particular(const double* f, double* ux, double* uy, int n, int
   TG_COUNT(1);
   launch(k_block_particular, dim3(nc * nc), dim3(32), 0, s, f, ux, uy, n, b);
 }
+void launch_psi_from_faces(const double* ux0, const double* vx, double* colbuf, double* psi, int n, cudaStream_t s) {
+  TG_COUNT(1);
+  launch(k_psi_from_faces, dim3(n), dim3(256), 0, s, ux0, vx, colbuf, psi, n);
+}
+
 void launch_pressure(const double* ux, const double* uy, const double* kinv, double* p, double* work,
                      int n, cudaStream_t s) {
   double* rowp = work;

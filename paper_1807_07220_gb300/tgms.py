@@ -77,6 +77,8 @@ SIGNATURES = {
     "tg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p,
                          c_int_p, ctypes.POINTER(tg_report)]),
     "tg_destroy": (None, [c_void_p]),
+    "tg_solve_warm": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_int_p, ctypes.POINTER(tg_report)]),
     "tg_strerror": (ctypes.c_char_p, [c_int]),
     "tg_apply_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "tg_apply_smoother": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -174,6 +176,16 @@ def tg_solve(h, f, bflux, rtol, ux, uy, p, allow_maxiter=False):
                         ctypes.byref(it), ctypes.byref(rep))
     if not (allow_maxiter and rc == -4):
         _check(rc, "tg_solve")
+    return it.value, rep
+
+
+def tg_solve_warm(h, f, bflux, rtol, ux0, uy0, ux, uy, p, allow_maxiter=False):
+    it = ctypes.c_int(0)
+    rep = tg_report()
+    rc = lib().tg_solve_warm(h, _ptr(f), _ptr(bflux), float(rtol), _ptr(ux0), _ptr(uy0), _ptr(ux), _ptr(uy),
+                             _ptr(p), ctypes.byref(it), ctypes.byref(rep))
+    if not (allow_maxiter and rc == -4):
+        _check(rc, "tg_solve_warm")
     return it.value, rep
 
 
@@ -348,10 +360,14 @@ class Solver:
         z = lambda *s: torch.zeros(*s, dtype=torch.float64, device=self.device)
         self.ux, self.uy, self.p = z(n, n + 1), z(n + 1, n), z(n, n)
 
-    def solve(self, f, bflux=None, rtol=1e-8, allow_maxiter=False):
+    def solve(self, f, bflux=None, rtol=1e-8, allow_maxiter=False, ux0=None):
+        """ux0: optional initial guess of the x-face velocities (tg_solve_warm)."""
         t = self.torch
         f = t.as_tensor(f, dtype=t.float64, device=self.device).contiguous()
         bf = None if bflux is None else t.as_tensor(bflux, dtype=t.float64, device=self.device).contiguous()
+        if ux0 is not None:
+            u0 = t.as_tensor(ux0, dtype=t.float64, device=self.device).contiguous()
+            return tg_solve_warm(self.h, f, bf, rtol, u0, None, self.ux, self.uy, self.p, allow_maxiter)
         it, rep = tg_solve(self.h, f, bf, rtol, self.ux, self.uy, self.p, allow_maxiter)
         return it, rep
 

@@ -229,6 +229,39 @@ def test_programmatic_dependent_launch_same_results(tg, prec):
     assert its[0] == its[1]
 
 
+@pytest.mark.parametrize("prec,profile", [("f64", 0), ("bf16", 0), ("bf16", 1)])
+def test_warm_start(tg, prec, profile):
+    """tg_solve_warm: the exact solution as guess needs 0 iterations; a
+    perturbed guess needs fewer iterations than the zero guess; a guess from
+    another source still converges to the direct solution."""
+    n, b, kf = CASES["32x32_b8_channels"]
+    kappa = kf(n)
+    g = Grid(n, b)
+    f = inputs.quarter_five_spot(n)
+    u_ref, p_ref = solve_direct(g, kappa, f)
+    s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), profile=profile)
+    try:
+        it_cold, _ = s.solve(f, rtol=1e-10)
+        exact_x = dev(u_ref[: g.nxf].reshape(n, n + 1))
+        it0, rep0 = s.solve(f, rtol=1e-10, ux0=exact_x)
+        got = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert it0 == 0 and rel(got, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+        rng = np.random.default_rng(8)
+        guess = exact_x + 1e-3 * torch.as_tensor(rng.standard_normal((n, n + 1)), device=DEV) * exact_x.abs().max()
+        it_w, _ = s.solve(f, rtol=1e-10, ux0=guess)
+        got = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert it_w < it_cold and rel(got, u_ref) < 1e-8
+        f2 = inputs.random_pairs(n, 2, 5)
+        u2, p2 = solve_direct(g, kappa, f2)
+        it2, _ = s.solve(f2, rtol=1e-12, ux0=exact_x)
+        got = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert rel(got, u2) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p2) < 1e-8
+        it_c, _ = s.solve(f, rtol=1e-10)            # the cold graph still works after a warm one
+        assert it_c == it_cold
+    finally:
+        s.close()
+
+
 def test_boundary_flux_closed_form(tg):
     """Layered medium with prescribed inflow/outflow: u_x = -kappa(row), p = x."""
     n, b = 16, 4
