@@ -22,6 +22,10 @@ written with numpy/scipy sparse matrices in the paper's own saddle-point form:
                      the spectral problems of Section 4.2, the subspace loss,
                      a perceptron with its backward pass and Adam, and the
                      Rayleigh-Ritz selection on predicted flux profiles.
+* ``impes``       -- Section 6.2: two-phase flow by IMPES, total mobility
+                     and fractional flow (eqs. mobility, fraction) and the
+                     upstream-weighted saturation update (eq.
+                     DisSatEq_Implicit) evaluated explicitly with a CFL step.
 * ``twogrid``     -- Section 5: smoother (eq. smooth), coarse correction
                      (eq. coarsepre), multiplicative two-grid cycle, PCG with
                      the stopping rule of Section 6 and a Lanczos estimate of
