@@ -198,6 +198,18 @@ int tg_solve(tg_handle* h, const double* f, const double* bflux, double rtol,
 int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rtol, const double* ux0,
                   const double* uy0, double* ux, double* uy, double* p, int* iters, tg_report* rep);
 
+/* New permeability for an existing handle (time-dependent runs such as the
+ * two-phase flow of Section 6.2, where the pressure equation's coefficient is
+ * kappa times the total mobility): kappa (n*n, > 0; host or device per
+ * pointer_mode) replaces the setup's.  The smoother's patch inverses, the
+ * block factors and the coarse matrices are recomputed in place.  coarse = 0
+ * keeps the coarse basis of the first setup (the paper keeps the initial
+ * multiscale space) and recomputes only its Galerkin matrix and inverse;
+ * coarse = 1 rebuilds the coarse space by the handle's method (spectral
+ * problems, MsFEM or the learned basis).  Solves after the call use the new
+ * kappa. */
+int tg_update_kappa(tg_handle* h, const double* kappa, int coarse);
+
 /* Frees all device memory of the handle.  NULL is allowed. */
 void tg_destroy(tg_handle* h);
 
@@ -335,6 +347,30 @@ void tg_mlp_destroy(tg_mlp* net);
  * may be NULL.  kappa (device, n*n), grid as in tg_setup. */
 int tg_face_data(const double* kappa, const tg_grid* grid, double eig_tol, int k, void* stream,
                  uint16_t* x, float* q, int* nsel, double* lambda);
+
+/* ---- two-phase flow (Section 6.2) ---------------------------------------
+ * IMPES building blocks, water and oil, porosity 1, relative permeabilities
+ * k_rw = s^2, k_ro = (1 - s)^2.  Cell arrays n*n device pointers; work on
+ * `stream`, the calls return after synchronising it. */
+
+/* kappa_out = kappa * lambda(s), lambda(s) = s^2/mu_w + (1-s)^2/mu_o the total
+ * mobility (eq. mobility): the permeability of the IMPES pressure equation. */
+int tg_total_mobility(const double* kappa, const double* s, int n, double mu_w, double mu_o, double* kappa_out,
+                      void* stream);
+
+/* One explicit upstream-weighted saturation step (eq. DisSatEq_Implicit
+ * evaluated at s^n): s_out = s + dt/h^2 (h^2 f+ - sum over faces of
+ * (u h) f_w(upstream) + f_w(s) h^2 f-), with (ux, uy) the face velocities of
+ * the pressure solve (boundary faces included: inward flow there is water)
+ * and f the cell source densities (f > 0 injects water, f < 0 produces at the
+ * cell's fractional flow).  dt_fixed > 0 is used as the time step; otherwise
+ * dt = cfl h^2 / (F_max sigma), F_max the largest total outflow of a cell
+ * (outgoing face fluxes plus its sink) and sigma the largest slope of f_w on
+ * [0, 1] (20001 samples).  *dt (host, may be NULL) receives the step.  s_out
+ * must not alias s.  The CFL reduction uses a scratch array compiled into the
+ * library: calls that overlap on a device must be serialised. */
+int tg_transport_step(const double* s, const double* ux, const double* uy, const double* f, int n, double cfl,
+                      double dt_fixed, double mu_w, double mu_o, double* s_out, double* dt, void* stream);
 
 /* ---- allocation-free entry point --------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot

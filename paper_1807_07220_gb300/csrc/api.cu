@@ -213,6 +213,8 @@ int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool
 }
 
 // tiles, Galerkin matrix and its inverse
+int galerkin_inverse(tg_handle* h, CoarseSpace& c);
+
 int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double* fcoef, const double* zcoef,
                  const int* jeff, bool rt_only) {
   const int b = h->b, n = h->n;
@@ -224,6 +226,13 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
     else
       launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
   }
+  return galerkin_inverse(h, c);
+}
+
+// Galerkin matrix R_H K R_H^T of a coarse space from its FP64 closed tiles and
+// the handle's current kappa, and its inverse
+int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
+  const int b = h->b, n = h->n;
   if (c.D == 0) return cuda_err(cudaGetLastError());
   // pair energy offsets
   std::vector<int> ptr(h->nblocks + 1);
@@ -619,13 +628,15 @@ int run_loop(Ctx* c, unsigned long long* launches) {
 }
 
 // kappa and the quantities derived from it cell by cell
-int setup_kappa(tg_handle* h, const double* kd) {
+int setup_kappa(tg_handle* h, const double* kd, bool update = false) {
   const long long nn = (long long)h->n * h->n;
   cudaStream_t s = h->stream;
-  TG_CK(cudaMallocHost(&h->h_flag, sizeof(int)));
-  TG_CK(cudaMalloc(&h->d_status, sizeof(int)));
+  if (!update) {
+    TG_CK(cudaMallocHost(&h->h_flag, sizeof(int)));
+    TG_CK(cudaMalloc(&h->d_status, sizeof(int)));
+    if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn) || dalloc(&h->kcoef, 5 * nn)) return TG_ERR_OOM;
+  }
   TG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s));
-  if (dalloc(&h->kinv, nn) || dalloc(&h->kinv32, nn) || dalloc(&h->kcoef, 5 * nn)) return TG_ERR_OOM;
   launch_kinv(kd, h->kinv, h->kinv32, h->d_status, h->n, s);
   launch_stencil_coefs(h->kinv, h->kcoef, h->n, s);
   int st = 0;
@@ -635,7 +646,7 @@ int setup_kappa(tg_handle* h, const double* kd) {
 }
 
 // oversampled patches K_i^+: local operators, band Cholesky, dense inverses
-int setup_patches(tg_handle* h) {
+int setup_patches(tg_handle* h, bool update = false) {
   const int n = h->n, b = h->b, nc = h->nc;
   cudaStream_t s = h->stream;
   std::vector<int4> prect(h->npatch);
@@ -661,22 +672,23 @@ int setup_patches(tg_handle* h) {
   std::vector<int> gofs(h->npatch + 1, 0);
   for (int k = 0; k < h->npatch; ++k) gofs[k + 1] = gofs[k] + (geo[k].nloc + kRowsPerGroup - 1) / kRowsPerGroup;
   h->ngroups = gofs[h->npatch];
-  if (dalloc(&h->d_gofs, gofs.size())) return TG_ERR_OOM;
+  if (!update && dalloc(&h->d_gofs, gofs.size())) return TG_ERR_OOM;
   TG_CK(cudaMemcpyAsync(h->d_gofs, gofs.data(), sizeof(int) * gofs.size(), cudaMemcpyHostToDevice, s));
   int4* d_prect = nullptr;
   double *band = nullptr, *scratch = nullptr;
-  if (dalloc(&h->d_pgeo, geo.size()) || dalloc(&d_prect, prect.size()) ||
+  if ((!update && dalloc(&h->d_pgeo, geo.size())) || dalloc(&d_prect, prect.size()) ||
       dalloc(&band, (size_t)h->npatch * nmax * (wmax + 1))) {
     cudaFree(d_prect);
     cudaFree(band);
     return TG_ERR_OOM;
   }
-  int rc = cuda_err(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
+  int rc = update ? TG_OK
+                  : cuda_err(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
   if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_pgeo, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_err(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
   const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
   if (!rc) rc = dalloc(&scratch, (size_t)batch * nmax * nmax);
-  if (!rc && h->opt.precision == TG_PREC_F16) rc = dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup);
+  if (!rc && !update && h->opt.precision == TG_PREC_F16) rc = dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup);
   if (!rc) {
     launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
     launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
@@ -703,7 +715,7 @@ int setup_patches(tg_handle* h) {
 
 // coarse blocks: band Cholesky factors of the local operators (snapshots) and,
 // with inverses, their dense inverses (preprocessing)
-int setup_blocks(tg_handle* h, bool inverses) {
+int setup_blocks(tg_handle* h, bool inverses, bool update = false) {
   const int b = h->b, nc = h->nc, n = h->n;
   cudaStream_t s = h->stream;
   std::vector<int4> brect(h->nblocks);
@@ -711,7 +723,8 @@ int setup_blocks(tg_handle* h, bool inverses) {
     for (int I = 0; I < nc; ++I) brect[J * nc + I] = make_int4(I * b, J * b, b - 1, b - 1);
   int4* d_brect = nullptr;
   const int bw = b, bn = (b - 1) * (b - 1);
-  if (dalloc(&d_brect, brect.size()) || dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1))) {
+  if (dalloc(&d_brect, brect.size()) ||
+      (!update && dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1)))) {
     cudaFree(d_brect);
     return TG_ERR_OOM;
   }
@@ -739,8 +752,8 @@ int setup_blocks(tg_handle* h, bool inverses) {
     double* bscratch = nullptr;
     const int bbatch = std::max(1, std::min(h->nblocks, (int)((256LL << 20) / (8LL * std::max(bn, 1) * std::max(bn, 1)))));
     const bool f64 = (h->opt.precision == TG_PREC_F64);
-    if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) ||
-        (f64 ? dalloc(&h->binv, (size_t)boff) : dalloc(&h->binv32, (size_t)boff)) ||
+    if ((!update && (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) ||
+                     (f64 ? dalloc(&h->binv, (size_t)boff) : dalloc(&h->binv32, (size_t)boff)))) ||
         dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1)))
       rc = TG_ERR_OOM;
     if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
@@ -1030,6 +1043,66 @@ int setup_impl(tg_handle* h, const double* kappa) {
   configure_kernels(std::max(h->cs.D, h->rt.D));
   if ((rc = choose_smoother_shape(h))) return rc;
   if ((rc = ctx_alloc(h, &h->ctx))) return rc;
+  TG_CK(cudaStreamSynchronize(s));
+  return cuda_err(cudaGetLastError());
+}
+
+// New permeability for an existing handle (time-dependent runs, Section 6.2):
+// everything that depends on kappa is recomputed into the handle's existing
+// buffers (so instantiated solve graphs stay valid), and the preconditioner's
+// coarse space is either kept (coarse == 0: the basis of the first setup,
+// with its Galerkin matrix recomputed for the new kappa, as the paper keeps
+// the initial multiscale space) or rebuilt by the handle's method (coarse ==
+// 1: exact spectral, MsFEM or learned; the solve context is re-created).
+int update_kappa_impl(tg_handle* h, const double* kappa, int coarse) {
+  const long long nn = (long long)h->n * h->n;
+  cudaStream_t s = h->stream;
+  const double* kd = kappa;
+  double* kcopy = nullptr;
+  struct Guard {
+    double*& p;
+    ~Guard() { cudaFree(p); }
+  } guard{kcopy};
+  if (h->opt.pointer_mode == TG_PTR_HOST) {
+    if (dalloc(&kcopy, nn)) return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(kcopy, kappa, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    kd = kcopy;
+  }
+  int rc = setup_kappa(h, kd, true);
+  if (!rc) rc = setup_patches(h, true);
+  if (!rc) rc = setup_blocks(h, true, true);
+  if (rc) return rc;
+  if (coarse == 0 || h->opt.coarse_space == TG_COARSE_RT0 || h->nfaces == 0) {
+    rc = galerkin_inverse(h, h->cs);
+  } else {
+    SpectralBufs sb{};
+    rc = alloc_spectral(h, sb);
+    if (!rc) {
+      if (h->opt.coarse_space == TG_COARSE_LEARNED) {
+        rc = spectral_learned(h, kd, sb);
+      } else {
+        spectral_exact(h, sb, nullptr, nullptr, nullptr, 0);
+        h->snapshot_solves = 2 * h->nfaces * h->b;
+        h->fallback_faces = 0;
+      }
+    }
+    if (!rc) rc = read_spectral(h, sb);
+    if (!rc) {
+      free_space(h->cs);
+      rc = setup_coarse(h, sb);
+    }
+    free_spectral(sb);
+    if (rc) return rc;
+    ctx_free(h->ctx);
+    h->ctx = nullptr;
+    configure_kernels(std::max(h->cs.D, h->rt.D));
+    rc = ctx_alloc(h, &h->ctx);
+  }
+  if (!rc) rc = galerkin_inverse(h, h->rt);
+  if (rc) return rc;
+  int st = 0;
+  if ((rc = read_status(h, &st))) return rc;
+  if (st) return status_to_err(st);
   TG_CK(cudaStreamSynchronize(s));
   return cuda_err(cudaGetLastError());
 }
@@ -1370,6 +1443,11 @@ int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rto
   (void)uy0;   // the x-face velocities determine the guess's stream function
   if (!ux0) return TG_ERR_INVALID_ARG;
   return solve_entry(h, f, bflux, rtol, ux0, ux, uy, p, iters, rep);
+}
+
+int tg_update_kappa(tg_handle* h, const double* kappa, int coarse) {
+  if (!h || !kappa || (coarse != 0 && coarse != 1)) return TG_ERR_INVALID_ARG;
+  return update_kappa_impl(h, kappa, coarse);
 }
 
 void tg_destroy(tg_handle* h) {

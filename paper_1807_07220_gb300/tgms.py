@@ -77,6 +77,10 @@ SIGNATURES = {
     "tg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p,
                          c_int_p, ctypes.POINTER(tg_report)]),
     "tg_destroy": (None, [c_void_p]),
+    "tg_update_kappa": (c_int, [c_void_p, c_void_p, c_int]),
+    "tg_total_mobility": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_void_p, c_void_p]),
+    "tg_transport_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double,
+                                  c_double, c_void_p, c_double_p, c_void_p]),
     "tg_solve_warm": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_int_p, ctypes.POINTER(tg_report)]),
     "tg_strerror": (ctypes.c_char_p, [c_int]),
@@ -187,6 +191,24 @@ def tg_solve_warm(h, f, bflux, rtol, ux0, uy0, ux, uy, p, allow_maxiter=False):
     if not (allow_maxiter and rc == -4):
         _check(rc, "tg_solve_warm")
     return it.value, rep
+
+
+def tg_update_kappa(h, kappa, coarse=0):
+    _check(lib().tg_update_kappa(h, _ptr(kappa), int(coarse)), "tg_update_kappa")
+
+
+def tg_total_mobility(kappa, s, n, mu_w, mu_o, out, stream=0):
+    _check(lib().tg_total_mobility(_ptr(kappa), _ptr(s), int(n), float(mu_w), float(mu_o), _ptr(out),
+                                   ctypes.c_void_p(stream)), "tg_total_mobility")
+
+
+def tg_transport_step(s, ux, uy, f, n, cfl, mu_w, mu_o, s_out, dt_fixed=0.0, stream=0):
+    """Returns the time step taken."""
+    dt = ctypes.c_double(0.0)
+    _check(lib().tg_transport_step(_ptr(s), _ptr(ux), _ptr(uy), _ptr(f), int(n), float(cfl), float(dt_fixed),
+                                   float(mu_w), float(mu_o), _ptr(s_out), ctypes.byref(dt),
+                                   ctypes.c_void_p(stream)), "tg_transport_step")
+    return dt.value
 
 
 def tg_destroy(h):
