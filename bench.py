@@ -482,6 +482,54 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- two-phase IMPES
+def run_impes(args):
+    """Two-phase IMPES (Section 6.2) at 512 x 512 with 16 x 16 blocks:
+    channels at 1e5, water injected in cell (0, 0) and produced in
+    (n-1, n-1), mu_w = 1, mu_o = 5, CFL 0.5, args.impes_steps steps, with the
+    coarse basis of the first setup kept (the paper's choice) and rebuilt
+    exactly every step."""
+    import numpy as np
+    import torch
+    from paper_1807_07220_gb300 import inputs
+    from paper_1807_07220_gb300.impes import Impes
+    torch.cuda.set_device(0)
+    n, b = args.n, args.b
+    kap = torch.as_tensor(inputs.channel_field(n, 1e5, 77), dtype=torch.float64, device="cuda")
+    f = torch.as_tensor(inputs.quarter_five_spot(n), dtype=torch.float64, device="cuda")
+    arms = {}
+    for mode in ("frozen", "rebuild"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, coarse=mode, precision=args.precision, flexible=1)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(args.impes_steps):
+            sim.step()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        hist = np.array(sim.history)
+        water = float(sim.s.sum()) / n ** 2
+        arms[mode] = {"steps": sim.steps, "t_final": sim.t, "wall_s": wall, "steps_per_s": sim.steps / wall,
+                      "setup_s": setup_s, "iters_mean": float(hist[:, 1].mean()), "iters_max": int(hist[:, 1].max()),
+                      "update_ms_mean": float(hist[:, 2].mean()), "solve_ms_mean": float(hist[:, 3].mean()),
+                      "transport_ms_mean": float(hist[:, 4].mean()),
+                      "pressure_dof_solves_per_s": dof(n) / (float(hist[:, 3].mean()) / 1e3),
+                      "water_volume": water, "s_max": float(sim.s.max())}
+        sim.close()
+    line = {
+        "metric": "IMPES steps/s (pressure update + warm-started solve + transport)",
+        "value": arms["frozen"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.impes_steps,
+        "warmup": 0, "ms_per_step": 1e3 / arms["frozen"]["steps_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
+        "config": {"workload": "%dx%d two-phase IMPES, %dx%d-cell blocks, channels 1e5, quarter five-spot, "
+                               "mu_w 1, mu_o 5, CFL 0.5, rtol %g" % (n, n, b, b, RTOL)},
+        "arms": arms,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- oracle arms
 ORACLE_SNIPPET = r"""
 import json, os, sys, time
@@ -581,7 +629,8 @@ def main():
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned", "impes"])
+    ap.add_argument("--impes-steps", type=int, default=200)
     ap.add_argument("--train-fields", type=int, default=25)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--hidden", type=int, default=512)
@@ -603,6 +652,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "impes":
+        run_impes(args)
     else:
         run_ours(args)
 
