@@ -148,6 +148,11 @@ typedef struct tg_report {
   int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
   int smoother_shape;     /* smoother tile shape in use */
   float shape_us[7];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
+  int refactored_patches; /* patch inverses computed by the handle's last setup or tg_update_kappa */
+  int refactored_blocks;  /* coarse-block factors computed by the same call */
+  int update_rank[2];     /* last tg_update_kappa: rank of the low-rank update of the
+                             coarse inverse ([0]) and of the coarse RT0 inverse ([1]);
+                             -1: recomputed in full */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
@@ -201,13 +206,23 @@ int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rto
 /* New permeability for an existing handle (time-dependent runs such as the
  * two-phase flow of Section 6.2, where the pressure equation's coefficient is
  * kappa times the total mobility): kappa (n*n, > 0; host or device per
- * pointer_mode) replaces the setup's.  The smoother's patch inverses, the
- * block factors and the coarse matrices are recomputed in place.  coarse = 0
- * keeps the coarse basis of the first setup (the paper keeps the initial
- * multiscale space) and recomputes only its Galerkin matrix and inverse;
- * coarse = 1 rebuilds the coarse space by the handle's method (spectral
- * problems, MsFEM or the learned basis).  Solves after the call use the new
- * kappa. */
+ * pointer_mode) replaces the setup's.  The smoother's patch inverses and the
+ * block factors are recomputed in place for the patches and blocks that hold
+ * a cell whose 1/kappa changed (the others are bitwise what a fresh setup
+ * would compute; tg_report's refactored_* count them).
+ *   coarse = 0: keeps the coarse basis of the first setup (the paper keeps
+ *     the initial multiscale space).  The Galerkin matrices are linear in
+ *     1/kappa, so their inverses change by a symmetric update of rank |S|,
+ *     S the basis functions whose support meets a changed cell; it is
+ *     applied in O(D^2 |S|) (Sherman-Morrison-Woodbury), or the inverse is
+ *     recomputed in full when |S| > min(1024, D/4), after 64 updates in a row
+ *     or on a non-positive pivot (tg_report's update_rank: |S|, -1 = full);
+ *   coarse = 1: rebuilds the coarse space by the handle's method (spectral
+ *     problems, MsFEM or the learned basis); the coarse RT0 inverse of the
+ *     preprocessing is updated as for 0;
+ *   coarse = 2: as 0 with both inverses recomputed in full.
+ * Solves after the call use the new kappa.  TG_ERR_INVALID_ARG for another
+ * value of coarse. */
 int tg_update_kappa(tg_handle* h, const double* kappa, int coarse);
 
 /* Frees all device memory of the handle.  NULL is allowed. */

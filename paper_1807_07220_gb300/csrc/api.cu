@@ -60,12 +60,18 @@ struct tg_handle {
   int velocity_basis = 0;
   int snapshot_solves = 0;   // local block solves of the coarse-space setup
   int fallback_faces = 0;    // learned space: faces that took the exact problem
+  int refactored_patches = 0, refactored_blocks = 0;   // factored by the last setup or update
+  int update_rank[2] = {-1, -1};   // last update: rows of the low-rank Galerkin-inverse update (cs, rt); -1 full
   int shape = 0;             // smoother tile shape (autotuned or from the options)
   float shape_us[kSmootherShapes] = {};   // autotuner: time per smoother launch of each shape (0: not tried)
   // coarse spaces: preconditioner and coarse RT0 (preprocessing)
   CoarseSpace cs, rt;
   int* h_flag = nullptr;    // pinned
   Ctx* ctx = nullptr;       // default solve context (tg_solve and the operator hooks)
+  // grow-only device scratch of the setup steps, kept between permeability
+  // updates (an update then allocates nothing); released after a setup
+  void* scr[16] = {};
+  size_t scr_cap[16] = {};
 };
 
 namespace {
@@ -110,6 +116,53 @@ int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   return cuda_err(cudaMalloc((void**)p, sizeof(T) * count));
+}
+
+// scratch slots of the setup steps; a function uses only its own slots and
+// those of no caller that is live across the call
+enum Scr {
+  kScrDelta,   // update: change of 1/kappa (n^2)
+  kScrRect,    // rectangles of a compact list
+  kScrFlag,    // per-rectangle or per-row flags
+  kScrGeo,     // layouts of a compact list
+  kScrIds,     // indices of a compact list
+  kScrBand,    // band factors of patches
+  kScrInv,     // dense local inverses of a batch
+  kScrDense,   // D x D Galerkin matrix or its change
+  kScrPPtr,    // pair-energy offsets per block
+  kScrPairE,   // pair energies
+  kScrX,       // low-rank update: B[:, S]
+  kScrT,       // X M
+  kScrSmall,   // four |S| x |S| matrices
+  kScrBad,     // pivot flag
+  kScrBlkMask, // update: blocks with a changed cell
+  kScrCount
+};
+
+template <typename T>
+int scratch(tg_handle* h, Scr slot, size_t count, T** out) {
+  const size_t bytes = sizeof(T) * std::max<size_t>(1, count);
+  if (h->scr_cap[slot] < bytes) {
+    cudaFree(h->scr[slot]);
+    h->scr[slot] = nullptr;
+    h->scr_cap[slot] = 0;
+    if (cudaMalloc(&h->scr[slot], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *out = nullptr;
+      return TG_ERR_OOM;
+    }
+    h->scr_cap[slot] = bytes;
+  }
+  *out = static_cast<T*>(h->scr[slot]);
+  return TG_OK;
+}
+
+void scratch_release(tg_handle* h) {
+  for (int k = 0; k < kScrCount; ++k) {
+    cudaFree(h->scr[k]);
+    h->scr[k] = nullptr;
+    h->scr_cap[k] = 0;
+  }
 }
 
 void free_space(CoarseSpace& c) {
@@ -229,12 +282,12 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
   return galerkin_inverse(h, c);
 }
 
-// Galerkin matrix R_H K R_H^T of a coarse space from its FP64 closed tiles and
-// the handle's current kappa, and its inverse
-int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
+// Galerkin matrix R_H K R_H^T of a coarse space from its FP64 closed tiles,
+// with the cell weights kinv (1/kappa, or a change of it: the matrix is
+// linear in them), into K (D x D, device)
+int assemble_galerkin(tg_handle* h, const CoarseSpace& c, const double* kinv, double* K,
+                      const unsigned char* bmask = nullptr) {
   const int b = h->b, n = h->n;
-  if (c.D == 0) return cuda_err(cudaGetLastError());
-  // pair energy offsets
   std::vector<int> ptr(h->nblocks + 1);
   TG_CK(cudaMemcpy(ptr.data(), c.slot_ptr, sizeof(int) * ptr.size(), cudaMemcpyDeviceToHost));
   std::vector<long long> pptr(h->nblocks + 1, 0);
@@ -243,23 +296,115 @@ int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
     pptr[k + 1] = pptr[k] + m * m;
   }
   long long* d_pptr = nullptr;
-  double *pairE = nullptr, *tmp = nullptr;
-  int rc = TG_OK;
-  if ((rc = dalloc(&d_pptr, pptr.size())) || (rc = dalloc(&pairE, (size_t)pptr.back())) ||
-      (rc = dalloc(&tmp, (size_t)c.D * c.D))) {
-    cudaFree(d_pptr);
-    cudaFree(pairE);
-    return rc;
+  double* pairE = nullptr;
+  int rc = (scratch(h, kScrPPtr, pptr.size(), &d_pptr) || scratch(h, kScrPairE, (size_t)pptr.back(), &pairE))
+               ? TG_ERR_OOM : TG_OK;
+  if (!rc)
+    rc = cuda_err(cudaMemcpyAsync(d_pptr, pptr.data(), sizeof(long long) * pptr.size(), cudaMemcpyHostToDevice,
+                                  h->stream));
+  if (!rc) {
+    launch_galerkin(c, kinv, h->nblocks, n, b, pairE, d_pptr, K, h->stream, bmask);
+    rc = cuda_err(cudaStreamSynchronize(h->stream));
   }
-  cudaMemcpyAsync(d_pptr, pptr.data(), sizeof(long long) * pptr.size(), cudaMemcpyHostToDevice, h->stream);
-  launch_galerkin(c, h->kinv, h->nblocks, n, b, pairE, d_pptr, c.Kinv, h->stream);
-  launch_gauss_jordan(c.Kinv, tmp, c.D, h->d_status, h->stream);
-  rc = cuda_err(cudaStreamSynchronize(h->stream));
-  cudaFree(d_pptr);
-  cudaFree(pairE);
-  cudaFree(tmp);
+  return rc ? rc : cuda_err(cudaGetLastError());
+}
+
+// Galerkin matrix of a coarse space with the handle's current kappa, and its
+// inverse (dense Gauss-Jordan)
+int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
+  if (c.D == 0) return cuda_err(cudaGetLastError());
+  double* tmp = nullptr;
+  if (scratch(h, kScrDense, (size_t)c.D * c.D, &tmp)) return TG_ERR_OOM;
+  int rc = assemble_galerkin(h, c, h->kinv, c.Kinv);
+  if (!rc) {
+    launch_gauss_jordan(c.Kinv, tmp, c.D, h->d_status, h->stream);
+    rc = cuda_err(cudaStreamSynchronize(h->stream));
+  }
+  c.low_rank_updates = 0;
   if (rc == TG_OK) rc = cuda_err(cudaGetLastError());
   return rc;
+}
+
+// The Galerkin inverse after 1/kappa changed by delta (device, n x n; zero on
+// unchanged cells), with the handle's kinv already the new one.  The change
+// of the Galerkin matrix, Galerkin(delta), is nonzero only in the rows and
+// columns S of basis functions that meet a changed cell; with B the current
+// inverse, X = B[:, S] and P = B[S, S]^{-1} the new inverse is
+//   B + X M X^T,  M = -P (P + Delta_SS)^{-1} Delta_SS
+// (the Sherman-Morrison-Woodbury identity written with SPD inverses only:
+// P and P + Delta_SS are the Schur complements on S of the old and new
+// matrices).  O(D^2 |S|) instead of O(D^3).  Falls back to the full inverse
+// when |S| is large, after kMaxLowRankUpdates updates in a row (rounding of
+// the updates accumulates) or when a small inverse meets a non-positive pivot.
+// bmask (device, optional): the blocks that hold a changed cell.
+int galerkin_update(tg_handle* h, CoarseSpace& c, const double* delta, const unsigned char* bmask, int* rank) {
+  constexpr int kMaxLowRankUpdates = 64;
+  *rank = -1;
+  if (c.D == 0) return cuda_err(cudaGetLastError());
+  if (c.low_rank_updates >= kMaxLowRankUpdates) return galerkin_inverse(h, c);
+  cudaStream_t s = h->stream;
+  const int D = c.D;
+  double* dK = nullptr;
+  unsigned char* d_flag = nullptr;
+  if (scratch(h, kScrDense, (size_t)D * D, &dK) || scratch(h, kScrFlag, (size_t)D, &d_flag)) return TG_ERR_OOM;
+  int rc = assemble_galerkin(h, c, delta, dK, bmask);
+  std::vector<unsigned char> flag(D);
+  if (!rc) {
+    launch_row_nonzero(dK, D, d_flag, s);
+    rc = cuda_err(cudaMemcpyAsync(flag.data(), d_flag, D, cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  }
+  std::vector<int> S;
+  for (int i = 0; i < D && !rc; ++i)
+    if (flag[i]) S.push_back(i);
+  const int m = (int)S.size();
+  if (rc || m == 0 || m > kGjSmallMax || 4 * m > D) {
+    if (rc) return rc;
+    if (m == 0) *rank = 0;
+    return m == 0 ? TG_OK : galerkin_inverse(h, c);
+  }
+  int* d_S = nullptr;
+  int* d_bad = nullptr;
+  double *X = nullptr, *P = nullptr, *Q = nullptr, *dS = nullptr, *W = nullptr, *T = nullptr;
+  double* small = nullptr;
+  const size_t mm2 = (size_t)m * m;
+  rc = (scratch(h, kScrIds, (size_t)m, &d_S) || scratch(h, kScrBad, 1, &d_bad) || scratch(h, kScrX, (size_t)D * m, &X) ||
+        scratch(h, kScrSmall, 4 * mm2, &small) || scratch(h, kScrT, (size_t)D * m, &T))
+           ? TG_ERR_OOM : TG_OK;
+  if (!rc) {
+    P = small;
+    Q = small + mm2;
+    dS = small + 2 * mm2;
+    W = small + 3 * mm2;
+  }
+  int bad = 0;
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_S, S.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+  if (!rc) {
+    const long long mm = (long long)m * m;
+    launch_gather_cols(c.Kinv, D, d_S, m, D, true, X, s);      // X = B[:, S]
+    launch_gather_cols(c.Kinv, D, d_S, m, m, false, P, s);     // B_SS
+    launch_gather_cols(dK, D, d_S, m, m, false, dS, s);        // Delta_SS
+    launch_gj_small(P, m, d_bad, s);                           // P = B_SS^{-1}
+    cudaMemcpyAsync(Q, P, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s);
+    launch_add(Q, dS, mm, s);
+    launch_gj_small(Q, m, d_bad, s);                           // Q = (P + Delta_SS)^{-1}
+    launch_dgemm(m, m, m, 1.0, Q, m, 1, dS, m, 1, 0.0, W, m, s);     // W = Q Delta_SS
+    launch_dgemm(m, m, m, -1.0, P, m, 1, W, m, 1, 0.0, Q, m, s);     // M = -P W (into Q)
+    launch_symmetrize(Q, m, s);
+    launch_dgemm(D, m, m, 1.0, X, m, 1, Q, m, 1, 0.0, T, m, s);      // T = X M
+    rc = cuda_err(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+    if (!rc && !bad) {
+      launch_dgemm(D, D, m, 1.0, T, m, 1, X, 1, m, 1.0, c.Kinv, D, s);   // B += T X^T
+      rc = cuda_err(cudaStreamSynchronize(s));
+    }
+  }
+  if (rc) return rc;
+  if (bad) return galerkin_inverse(h, c);
+  ++c.low_rank_updates;
+  *rank = m;
+  return cuda_err(cudaGetLastError());
 }
 
 // extreme eigenvalues of the Lanczos tridiagonal by Sturm bisection (report only)
@@ -645,14 +790,19 @@ int setup_kappa(tg_handle* h, const double* kd, bool update = false) {
   return st ? status_to_err(st) : TG_OK;
 }
 
-// oversampled patches K_i^+: local operators, band Cholesky, dense inverses
-int setup_patches(tg_handle* h, bool update = false) {
-  const int n = h->n, b = h->b, nc = h->nc;
-  cudaStream_t s = h->stream;
-  std::vector<int4> prect(h->npatch);
-  std::vector<PatchGeo> geo(h->npatch);
-  long long off = 0;
+// rectangles and smoother layout of the oversampled patches K_i^+
+struct PatchLayout {
+  std::vector<int4> rect;
+  std::vector<PatchGeo> geo;
+  long long off = 0;   // total stored elements
   int wmax = 0, nmax = 0;
+};
+
+PatchLayout patch_layout(const tg_handle* h) {
+  const int n = h->n, b = h->b, nc = h->nc;
+  PatchLayout L;
+  L.rect.resize(h->npatch);
+  L.geo.resize(h->npatch);
   for (int J = 0; J < nc; ++J)
     for (int I = 0; I < nc; ++I) {
       const int k = J * nc + I;
@@ -662,115 +812,186 @@ int setup_patches(tg_handle* h, bool update = false) {
       g.x0 = x0; g.y0 = y0; g.nx = x1 - x0 - 1; g.ny = y1 - y0 - 1;
       g.nloc = g.nx * g.ny;
       g.ld = ((g.nloc + 7) / 8) * 8;
-      g.off = off;
-      off += (long long)g.nloc * g.ld;
-      geo[k] = g;
-      prect[k] = make_int4(x0, y0, g.nx, g.ny);
-      wmax = std::max(wmax, g.nx + 1);
-      nmax = std::max(nmax, g.nloc);
+      g.off = L.off;
+      L.off += (long long)g.nloc * g.ld;
+      L.geo[k] = g;
+      L.rect[k] = make_int4(x0, y0, g.nx, g.ny);
+      L.wmax = std::max(L.wmax, g.nx + 1);
+      L.nmax = std::max(L.nmax, g.nloc);
     }
-  std::vector<int> gofs(h->npatch + 1, 0);
-  for (int k = 0; k < h->npatch; ++k) gofs[k + 1] = gofs[k] + (geo[k].nloc + kRowsPerGroup - 1) / kRowsPerGroup;
-  h->ngroups = gofs[h->npatch];
-  if (!update && dalloc(&h->d_gofs, gofs.size())) return TG_ERR_OOM;
-  TG_CK(cudaMemcpyAsync(h->d_gofs, gofs.data(), sizeof(int) * gofs.size(), cudaMemcpyHostToDevice, s));
-  int4* d_prect = nullptr;
-  double *band = nullptr, *scratch = nullptr;
-  if ((!update && dalloc(&h->d_pgeo, geo.size())) || dalloc(&d_prect, prect.size()) ||
-      dalloc(&band, (size_t)h->npatch * nmax * (wmax + 1))) {
-    cudaFree(d_prect);
-    cudaFree(band);
-    return TG_ERR_OOM;
-  }
-  int rc = update ? TG_OK
-                  : cuda_err(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)off * ts_size(h->opt.precision))));
-  if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_pgeo, geo.data(), sizeof(PatchGeo) * geo.size(), cudaMemcpyHostToDevice, s));
-  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_prect, prect.data(), sizeof(int4) * prect.size(), cudaMemcpyHostToDevice, s));
-  const int batch = std::max(1, std::min(h->npatch, (int)((256LL << 20) / (8LL * nmax * nmax))));
-  if (!rc) rc = dalloc(&scratch, (size_t)batch * nmax * nmax);
-  if (!rc && !update && h->opt.precision == TG_PREC_F16) rc = dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup);
+  return L;
+}
+
+std::vector<int4> block_rects(const tg_handle* h) {
+  std::vector<int4> r(h->nblocks);
+  for (int J = 0; J < h->nc; ++J)
+    for (int I = 0; I < h->nc; ++I) r[J * h->nc + I] = make_int4(I * h->b, J * h->b, h->b - 1, h->b - 1);
+  return r;
+}
+
+// changed[m] = 1 where a cell of rect[m] gets a new 1/kappa from kappa (device);
+// run before kinv is overwritten
+int changed_rects(tg_handle* h, const double* kappa, const std::vector<int4>& rect,
+                  std::vector<unsigned char>& changed) {
+  cudaStream_t s = h->stream;
+  changed.assign(rect.size(), 1);
+  if (rect.empty()) return TG_OK;
+  int4* d_rect = nullptr;
+  unsigned char* d_flag = nullptr;
+  int rc = (scratch(h, kScrRect, rect.size(), &d_rect) || scratch(h, kScrFlag, rect.size(), &d_flag)) ? TG_ERR_OOM
+                                                                                                      : TG_OK;
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_rect, rect.data(), sizeof(int4) * rect.size(), cudaMemcpyHostToDevice, s));
   if (!rc) {
-    launch_assemble_band(h->kinv, d_prect, band, h->npatch, wmax, nmax, n, s);
-    launch_band_cholesky(band, d_prect, h->npatch, wmax, nmax, h->d_status, s);
-    for (int first = 0; first < h->npatch; first += batch) {
-      const int cnt = std::min(batch, h->npatch - first);
-      launch_band_inverse(band, d_prect, first, cnt, wmax, nmax, scratch, s);
+    launch_rect_changed(kappa, h->kinv, d_rect, (int)rect.size(), h->n, d_flag, s);
+    rc = cuda_err(cudaMemcpyAsync(changed.data(), d_flag, rect.size(), cudaMemcpyDeviceToHost, s));
+  }
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  return rc;
+}
+
+// indices m with sel[m] set (sel NULL: all of 0..count-1)
+std::vector<int> selected(int count, const std::vector<unsigned char>* sel) {
+  std::vector<int> ids;
+  ids.reserve(count);
+  for (int m = 0; m < count; ++m)
+    if (!sel || (*sel)[m]) ids.push_back(m);
+  return ids;
+}
+
+// oversampled patches K_i^+: local operators, band Cholesky, dense inverses.
+// update: the storage exists and only the patches in `changed` (NULL: all)
+// are factored again
+int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned char>* changed = nullptr) {
+  const int n = h->n;
+  cudaStream_t s = h->stream;
+  const PatchLayout L = patch_layout(h);
+  const int wmax = L.wmax, nmax = L.nmax;
+  std::vector<int> gofs(h->npatch + 1, 0);
+  for (int k = 0; k < h->npatch; ++k) gofs[k + 1] = gofs[k] + (L.geo[k].nloc + kRowsPerGroup - 1) / kRowsPerGroup;
+  h->ngroups = gofs[h->npatch];
+  if (!update) {
+    if (dalloc(&h->d_gofs, gofs.size()) || dalloc(&h->d_pgeo, L.geo.size())) return TG_ERR_OOM;
+    TG_CK(cudaMemcpyAsync(h->d_gofs, gofs.data(), sizeof(int) * gofs.size(), cudaMemcpyHostToDevice, s));
+    TG_CK(cudaMemcpyAsync(h->d_pgeo, L.geo.data(), sizeof(PatchGeo) * L.geo.size(), cudaMemcpyHostToDevice, s));
+    TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)L.off * ts_size(h->opt.precision))));
+    if (h->opt.precision == TG_PREC_F16 && dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup))
+      return TG_ERR_OOM;
+  }
+  // the patches to factor, as a compact list: rectangles, layouts, numbers
+  const std::vector<int> ids = selected(h->npatch, update ? changed : nullptr);
+  const int cnt = (int)ids.size();
+  h->refactored_patches = cnt;
+  if (cnt == 0) return TG_OK;
+  std::vector<int4> crect(cnt);
+  std::vector<PatchGeo> cgeo(cnt);
+  for (int c = 0; c < cnt; ++c) {
+    crect[c] = L.rect[ids[c]];
+    cgeo[c] = L.geo[ids[c]];
+  }
+  int4* d_rect = nullptr;
+  PatchGeo* d_geo = nullptr;
+  int* d_ids = nullptr;
+  double *band = nullptr, *inv = nullptr;
+  const int batch = std::max(1, std::min(cnt, (int)((256LL << 20) / (8LL * nmax * nmax))));
+  int rc = (scratch(h, kScrRect, cnt, &d_rect) || scratch(h, kScrGeo, cnt, &d_geo) ||
+            scratch(h, kScrIds, cnt, &d_ids) || scratch(h, kScrBand, (size_t)cnt * nmax * (wmax + 1), &band) ||
+            scratch(h, kScrInv, (size_t)batch * nmax * nmax, &inv))
+               ? TG_ERR_OOM : TG_OK;
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_rect, crect.data(), sizeof(int4) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_geo, cgeo.data(), sizeof(PatchGeo) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) {
+    launch_assemble_band(h->kinv, d_rect, band, cnt, wmax, nmax, n, s);
+    launch_band_cholesky(band, d_rect, cnt, wmax, nmax, h->d_status, s);
+    for (int first = 0; first < cnt; first += batch) {
+      const int m = std::min(batch, cnt - first);
+      launch_band_inverse(band, d_rect, first, m, wmax, nmax, inv, s);
       if (h->opt.precision == TG_PREC_F64)
-        launch_store_inverse<double>(scratch, h->d_pgeo, first, cnt, nmax, (double*)h->pinv, s);
+        launch_store_inverse<double>(inv, d_geo, first, m, nmax, (double*)h->pinv, s);
       else if (h->opt.precision == TG_PREC_F32)
-        launch_store_inverse<float>(scratch, h->d_pgeo, first, cnt, nmax, (float*)h->pinv, s);
+        launch_store_inverse<float>(inv, d_geo, first, m, nmax, (float*)h->pinv, s);
       else if (h->opt.precision == TG_PREC_F16)
-        launch_store_inverse_f16(scratch, h->d_pgeo, h->d_gofs, first, cnt, nmax, (__half*)h->pinv, h->rscale, s);
+        launch_store_inverse_f16(inv, d_geo, h->d_gofs, first, m, nmax, (__half*)h->pinv, h->rscale, s, d_ids);
       else
-        launch_store_inverse<__nv_bfloat16>(scratch, h->d_pgeo, first, cnt, nmax, (__nv_bfloat16*)h->pinv, s);
+        launch_store_inverse<__nv_bfloat16>(inv, d_geo, first, m, nmax, (__nv_bfloat16*)h->pinv, s);
     }
     rc = cuda_err(cudaStreamSynchronize(s));
   }
-  cudaFree(scratch);
-  cudaFree(band);
-  cudaFree(d_prect);
   if (rc) return rc;
   return cuda_err(cudaGetLastError());
 }
 
 // coarse blocks: band Cholesky factors of the local operators (snapshots) and,
-// with inverses, their dense inverses (preprocessing)
-int setup_blocks(tg_handle* h, bool inverses, bool update = false) {
-  const int b = h->b, nc = h->nc, n = h->n;
+// with inverses, their dense inverses (preprocessing).  update: the storage
+// exists and only the blocks in `changed` (NULL: all) are factored again
+int setup_blocks(tg_handle* h, bool inverses, bool update = false,
+                 const std::vector<unsigned char>* changed = nullptr) {
+  const int b = h->b, n = h->n;
   cudaStream_t s = h->stream;
-  std::vector<int4> brect(h->nblocks);
-  for (int J = 0; J < nc; ++J)
-    for (int I = 0; I < nc; ++I) brect[J * nc + I] = make_int4(I * b, J * b, b - 1, b - 1);
-  int4* d_brect = nullptr;
+  const std::vector<int4> brect = block_rects(h);
   const int bw = b, bn = (b - 1) * (b - 1);
-  if (dalloc(&d_brect, brect.size()) ||
-      (!update && dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1)))) {
-    cudaFree(d_brect);
-    return TG_ERR_OOM;
+  std::vector<PatchGeo> bgeo(h->nblocks);
+  std::vector<int> bgofs(h->nblocks + 1, 0);
+  long long boff = 0;
+  for (int k = 0; k < h->nblocks; ++k) {
+    PatchGeo g{};
+    g.x0 = brect[k].x; g.y0 = brect[k].y; g.nx = g.ny = b - 1;
+    g.nloc = bn;
+    g.ld = ((bn + 7) / 8) * 8;
+    g.off = boff;
+    boff += (long long)g.nloc * g.ld;
+    bgeo[k] = g;
+    bgofs[k + 1] = bgofs[k] + (bn + kRowsPerGroup - 1) / kRowsPerGroup;
   }
-  int rc = cuda_err(cudaMemcpyAsync(d_brect, brect.data(), sizeof(int4) * brect.size(), cudaMemcpyHostToDevice, s));
-  if (!rc && bn > 0) {
-    launch_assemble_band(h->kinv, d_brect, h->blk_band, h->nblocks, bw, bn, n, s);
-    launch_band_cholesky(h->blk_band, d_brect, h->nblocks, bw, bn, h->d_status, s);
-  }
-  if (!rc && inverses) {
-    // dense inverses of the block operators, smoother layout
-    std::vector<PatchGeo> bgeo(h->nblocks);
-    std::vector<int> bgofs(h->nblocks + 1, 0);
-    long long boff = 0;
-    for (int k = 0; k < h->nblocks; ++k) {
-      PatchGeo g{};
-      g.x0 = brect[k].x; g.y0 = brect[k].y; g.nx = g.ny = b - 1;
-      g.nloc = bn;
-      g.ld = ((bn + 7) / 8) * 8;
-      g.off = boff;
-      boff += (long long)g.nloc * g.ld;
-      bgeo[k] = g;
-      bgofs[k + 1] = bgofs[k] + (bn + kRowsPerGroup - 1) / kRowsPerGroup;
+  const bool f64 = (h->opt.precision == TG_PREC_F64);
+  if (!update) {
+    if (dalloc(&h->blk_band, (size_t)h->nblocks * std::max(bn, 1) * (bw + 1))) return TG_ERR_OOM;
+    if (inverses) {
+      h->bgroups = bgofs[h->nblocks];
+      if (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) ||
+          (f64 ? dalloc(&h->binv, (size_t)boff) : dalloc(&h->binv32, (size_t)boff)))
+        return TG_ERR_OOM;
+      TG_CK(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
+      TG_CK(cudaMemcpyAsync(h->d_bgofs, bgofs.data(), sizeof(int) * bgofs.size(), cudaMemcpyHostToDevice, s));
     }
-    h->bgroups = bgofs[h->nblocks];
-    double* bscratch = nullptr;
-    const int bbatch = std::max(1, std::min(h->nblocks, (int)((256LL << 20) / (8LL * std::max(bn, 1) * std::max(bn, 1)))));
-    const bool f64 = (h->opt.precision == TG_PREC_F64);
-    if ((!update && (dalloc(&h->d_bgeo, bgeo.size()) || dalloc(&h->d_bgofs, bgofs.size()) ||
-                     (f64 ? dalloc(&h->binv, (size_t)boff) : dalloc(&h->binv32, (size_t)boff)))) ||
-        dalloc(&bscratch, (size_t)bbatch * std::max(bn, 1) * std::max(bn, 1)))
-      rc = TG_ERR_OOM;
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgeo, bgeo.data(), sizeof(PatchGeo) * bgeo.size(), cudaMemcpyHostToDevice, s));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(h->d_bgofs, bgofs.data(), sizeof(int) * bgofs.size(), cudaMemcpyHostToDevice, s));
-    if (!rc && bn > 0) {
-      for (int first = 0; first < h->nblocks; first += bbatch) {
-        const int cnt = std::min(bbatch, h->nblocks - first);
-        launch_band_inverse(h->blk_band, d_brect, first, cnt, bw, bn, bscratch, s);
-        if (f64) launch_store_inverse<double>(bscratch, h->d_bgeo, first, cnt, bn, h->binv, s);
-        else launch_store_inverse<float>(bscratch, h->d_bgeo, first, cnt, bn, h->binv32, s);
+  }
+  // the blocks to factor, as a compact list; their bands stay in the full
+  // numbering (the snapshot solves read them), so the kernels get the slots
+  const std::vector<int> ids = selected(h->nblocks, update ? changed : nullptr);
+  const int cnt = (int)ids.size();
+  h->refactored_blocks = cnt;
+  if (cnt == 0 || bn == 0) return cuda_err(cudaStreamSynchronize(s));
+  std::vector<int4> crect(cnt);
+  std::vector<PatchGeo> cgeo(cnt);
+  for (int c = 0; c < cnt; ++c) {
+    crect[c] = brect[ids[c]];
+    cgeo[c] = bgeo[ids[c]];
+  }
+  int4* d_rect = nullptr;
+  PatchGeo* d_geo = nullptr;
+  int* d_ids = nullptr;
+  double* bscratch = nullptr;
+  const int bbatch = std::max(1, std::min(cnt, (int)((256LL << 20) / (8LL * bn * bn))));
+  int rc = (scratch(h, kScrRect, cnt, &d_rect) || scratch(h, kScrGeo, cnt, &d_geo) || scratch(h, kScrIds, cnt, &d_ids) ||
+            (inverses && scratch(h, kScrInv, (size_t)bbatch * bn * bn, &bscratch)))
+               ? TG_ERR_OOM : TG_OK;
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_rect, crect.data(), sizeof(int4) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_geo, cgeo.data(), sizeof(PatchGeo) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+  if (!rc) {
+    launch_assemble_band(h->kinv, d_rect, h->blk_band, cnt, bw, bn, n, s, d_ids);
+    launch_band_cholesky(h->blk_band, d_rect, cnt, bw, bn, h->d_status, s, d_ids);
+    if (inverses) {
+      // dense inverses of the block operators, smoother layout
+      for (int first = 0; first < cnt; first += bbatch) {
+        const int m = std::min(bbatch, cnt - first);
+        launch_band_inverse(h->blk_band, d_rect, first, m, bw, bn, bscratch, s, d_ids);
+        if (f64) launch_store_inverse<double>(bscratch, d_geo, first, m, bn, h->binv, s);
+        else launch_store_inverse<float>(bscratch, d_geo, first, m, bn, h->binv32, s);
       }
     }
-    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
-    cudaFree(bscratch);
+    rc = cuda_err(cudaStreamSynchronize(s));
   }
-  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
-  cudaFree(d_brect);
   return rc;
 }
 
@@ -1068,12 +1289,29 @@ int update_kappa_impl(tg_handle* h, const double* kappa, int coarse) {
     TG_CK(cudaMemcpyAsync(kcopy, kappa, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
     kd = kcopy;
   }
-  int rc = setup_kappa(h, kd, true);
-  if (!rc) rc = setup_patches(h, true);
-  if (!rc) rc = setup_blocks(h, true, true);
+  // only patches and blocks with a cell whose 1/kappa changed get new
+  // factors: their operators depend on kappa through 1/kappa alone, so the
+  // others are bitwise what a fresh setup computes (in two-phase flow most of
+  // the domain away from the front keeps its saturation and mobility)
+  std::vector<unsigned char> pchg, bchg;
+  double* delta = nullptr;   // change of 1/kappa, for the low-rank updates of the coarse inverses
+  if (scratch(h, kScrDelta, nn, &delta)) return TG_ERR_OOM;
+  launch_kinv_delta(kd, h->kinv, delta, h->n, s);
+  int rc = changed_rects(h, kd, patch_layout(h).rect, pchg);
+  if (!rc) rc = changed_rects(h, kd, block_rects(h), bchg);
+  unsigned char* d_bmask = nullptr;
+  if (!rc) rc = scratch(h, kScrBlkMask, bchg.size(), &d_bmask);
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(d_bmask, bchg.data(), bchg.size(), cudaMemcpyHostToDevice, s));
+  if (!rc) rc = setup_kappa(h, kd, true);
+  if (!rc) rc = setup_patches(h, true, &pchg);
+  if (!rc) rc = setup_blocks(h, true, true, &bchg);
   if (rc) return rc;
-  if (coarse == 0 || h->opt.coarse_space == TG_COARSE_RT0 || h->nfaces == 0) {
+  h->update_rank[0] = h->update_rank[1] = -1;
+  const bool rebuild = (coarse == 1 && h->opt.coarse_space != TG_COARSE_RT0 && h->nfaces > 0);
+  if (coarse == 2) {
     rc = galerkin_inverse(h, h->cs);
+  } else if (!rebuild) {
+    rc = galerkin_update(h, h->cs, delta, d_bmask, &h->update_rank[0]);
   } else {
     SpectralBufs sb{};
     rc = alloc_spectral(h, sb);
@@ -1098,7 +1336,7 @@ int update_kappa_impl(tg_handle* h, const double* kappa, int coarse) {
     configure_kernels(std::max(h->cs.D, h->rt.D));
     rc = ctx_alloc(h, &h->ctx);
   }
-  if (!rc) rc = galerkin_inverse(h, h->rt);
+  if (!rc) rc = (coarse == 2) ? galerkin_inverse(h, h->rt) : galerkin_update(h, h->rt, delta, d_bmask, &h->update_rank[1]);
   if (rc) return rc;
   int st = 0;
   if ((rc = read_status(h, &st))) return rc;
@@ -1300,6 +1538,8 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
     tg_destroy(h);
     return rc;
   }
+  cudaStreamSynchronize(h->stream);
+  scratch_release(h);
   *out = h;
   return TG_OK;
 }
@@ -1384,6 +1624,10 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
     rep->fallback_faces = h->fallback_faces;
     rep->smoother_shape = h->shape;
     for (int k = 0; k < kSmootherShapes; ++k) rep->shape_us[k] = h->shape_us[k];
+    rep->refactored_patches = h->refactored_patches;
+    rep->refactored_blocks = h->refactored_blocks;
+    rep->update_rank[0] = h->update_rank[0];
+    rep->update_rank[1] = h->update_rank[1];
     float ms = 0;
     if (h->opt.profile) {
       cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
@@ -1446,7 +1690,7 @@ int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rto
 }
 
 int tg_update_kappa(tg_handle* h, const double* kappa, int coarse) {
-  if (!h || !kappa || (coarse != 0 && coarse != 1)) return TG_ERR_INVALID_ARG;
+  if (!h || !kappa || coarse < 0 || coarse > 2) return TG_ERR_INVALID_ARG;
   return update_kappa_impl(h, kappa, coarse);
 }
 
@@ -1459,6 +1703,7 @@ void tg_destroy(tg_handle* h) {
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);
+  scratch_release(h);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   delete h;
 }

@@ -28,6 +28,7 @@ namespace tg {
 constexpr int kMaxB = 16;                 // largest supported block size b
 constexpr int kMaxOverlap = 2;
 constexpr int kMaxPatchSide = kMaxB + 2 * kMaxOverlap - 1;   // interior nodes per side
+constexpr int kMaxDynSmem = 227 * 1024;   // dynamic shared memory per CTA (opt-in limit)
 constexpr int kMaxPatchNodes = kMaxPatchSide * kMaxPatchSide;
 constexpr int kMaxHist = 4096;            // PCG coefficient history
 constexpr int kRedGrid = 512;             // CTAs of grid-stride reduction kernels
@@ -91,6 +92,7 @@ struct CoarseSpace {
   double* closed = nullptr;  // nslots*(b+1)^2 FP64 tiles (device)
   void* owned = nullptr;     // nslots*b*b tiles in storage precision (device)
   double* Kinv = nullptr;    // D*D inverse of the Galerkin matrix (device)
+  int low_rank_updates = 0;  // low-rank updates of Kinv since it was last inverted in full
   int max_slots_per_block = 0;
 };
 
@@ -303,19 +305,27 @@ void launch_div_error(const double* ux, const double* uy, const double* f, doubl
 // setup (setup.cu)
 void launch_kinv(const double* kappa, double* kinv, float* kinv32, int* status, int n,
                  cudaStream_t s);
+// slot (optional, NULL = identity): the band of rectangle m is band slot
+// slot[m], so a compacted list of rectangles updates bands kept in the full
+// numbering
 void launch_assemble_band(const double* kinv, const int4* rects, double* band, int nmat, int wmax,
-                          int nmax, int n, cudaStream_t s);
+                          int nmax, int n, cudaStream_t s, const int* slot = nullptr);
 void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, int nmax,
-                          int* status, cudaStream_t s);
+                          int* status, cudaStream_t s, const int* slot = nullptr);
 void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax,
-                         int nmax, double* scratch, cudaStream_t s);
+                         int nmax, double* scratch, cudaStream_t s, const int* slot = nullptr);
+// flag[m] = 1 where some cell of rectangle m gets a new 1/kappa (bitwise
+// comparison against kinv_old, computed as launch_kinv computes it)
+void launch_rect_changed(const double* kappa, const double* kinv_old, const int4* rects, int nrect, int n,
+                         unsigned char* flag, cudaStream_t s);
 template <typename TS>
 void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count,
                           int nmax, TS* pinv, cudaStream_t s);
 // FP16 storage: each row scaled by a power of two that puts its largest
-// magnitude in [2^14, 2^15); rscale receives the inverse factor
+// magnitude in [2^14, 2^15); rscale receives the inverse factor.  pidx
+// (optional): patch numbers of a compacted geo list
 void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const int* gofs, int first, int count,
-                              int nmax, __half* pinv, float* rscale, cudaStream_t s);
+                              int nmax, __half* pinv, float* rscale, cudaStream_t s, const int* pidx = nullptr);
 // Snapshot functions of every (block, side): nfn functions per side whose
 // coefficient vectors over {m, d_1..d_{b-1}} are coef[face][fn][0..b-1]
 // (coef NULL: the unit vectors, nfn = b).  Sides with mask[blk*4+side] == 0
@@ -358,9 +368,29 @@ void launch_pred_basis(const float* y, const double* kinv, int k, int n, int b, 
 template <typename TS>
 void launch_build_tiles(const CoarseSpace& cs, const double* psiS, const double* fcoef,
                         const double* zcoef, const int* jeff, int rt_only, int n, int b, cudaStream_t s);
+// bmask (optional): only blocks with bmask[blk] != 0 contribute (the weights
+// kinv are zero on the cells of the others)
 void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b,
-                     double* pairE, const long long* pair_ptr, double* K, cudaStream_t s);
-void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s);  // result in A
+                     double* pairE, const long long* pair_ptr, double* K, cudaStream_t s,
+                     const unsigned char* bmask = nullptr);
+void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s);
+// low-rank update of a Galerkin inverse after a change of 1/kappa on few cells
+// (setup.cu): delta = 1/kappa - kinv_old; row flags of nonzero rows; gathers
+// out[i][a] = K[row(i)][S[a]] (row(i) = i if rows_all, else S[i]); in-place
+// SPD inverse of a small matrix (s <= kGjSmallMax) by one CTA, *bad set on a
+// non-positive pivot; FP64 GEMM C = alpha op(A) op(B) + beta C with element
+// strides (op(A)(i,k) = A[i*ars + k*acs]); (A + A^T)/2; y += x
+constexpr int kGjSmallMax = 1024;
+void launch_kinv_delta(const double* kappa, const double* kinv_old, double* delta, int n, cudaStream_t s);
+void launch_row_nonzero(const double* K, int D, unsigned char* flag, cudaStream_t s);
+void launch_gather_cols(const double* K, int D, const int* S, int s_cnt, int rows, bool rows_all, double* out,
+                        cudaStream_t s);
+void launch_gj_small(double* A, int s_cnt, int* bad, cudaStream_t s);
+void launch_dgemm(int m, int n, int k, double alpha, const double* A, long long ars, long long acs,
+                  const double* B, long long brs, long long bcs, double beta, double* C, long long ldc,
+                  cudaStream_t s);
+void launch_symmetrize(double* A, int s_cnt, cudaStream_t s);
+void launch_add(double* y, const double* x, long long cnt, cudaStream_t s);  // result in A
 
 // learned coarse basis (learned.cu)
 void launch_face_inputs(const double* kappa, int n, int b, __nv_bfloat16* x, cudaStream_t s);

@@ -9,6 +9,8 @@
 // cell origin and interior node counts; local node (a, c) is global node
 // (x0+1+a, y0+1+c), index c*nx + a, and the natural ordering gives band width
 // w = nx + 1.  Band storage: row j holds L_{j, j-d} at j*(wmax+1) + d.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tg {
@@ -33,11 +35,13 @@ __global__ void k_kinv(const double* __restrict__ kappa, double* __restrict__ ki
 }
 
 // lower band rows of the local operator of each rectangle
+// slot (optional): band slot of matrix m (default m), so a compacted list of
+// rectangles can update a band array indexed by the full matrix numbering
 __global__ void k_assemble_band(const double* __restrict__ kinv, const int4* __restrict__ rects,
-                                double* __restrict__ band, int wmax, int nmax, int n) {
+                                const int* __restrict__ slot, double* __restrict__ band, int wmax, int nmax, int n) {
   const int4 r = rects[blockIdx.x];
   const int nx = r.z, nloc = r.z * r.w, ldb = wmax + 1;
-  double* B = band + (long long)blockIdx.x * nmax * ldb;
+  double* B = band + (long long)(slot ? slot[blockIdx.x] : blockIdx.x) * nmax * ldb;
   for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
     const int a = q % nx, c = q / nx;
     const int i = r.x + 1 + a, j = r.y + 1 + c;
@@ -55,72 +59,135 @@ __global__ void k_assemble_band(const double* __restrict__ kinv, const int4* __r
   }
 }
 
-// right-looking band Cholesky, one CTA per matrix, band in shared memory
-__global__ void k_band_cholesky(double* __restrict__ band, const int4* __restrict__ rects, int wmax,
-                                int nmax, int* status) {
+// right-looking band Cholesky, one CTA per matrix, band in shared memory.
+// Column j: every thread takes r = 1/sqrt(K_jj) and, for its pair (d1, d2),
+// 1 <= d2 <= d1 <= w (one pair per thread, w (w + 1) / 2 <= blockDim), the
+// scaled entries l1 = K_{j+d1, j} r, l2 = K_{j+d2, j} r; after a barrier it
+// subtracts l1 l2 from K_{j+d1, j+d2} and the (d1, d1) thread stores l1.  Two
+// barriers per column; the chain of dependent FP64 operations per column is
+// one reciprocal square root, a product and an FMA.
+__global__ void k_band_cholesky(double* __restrict__ band, const int4* __restrict__ rects,
+                                const int* __restrict__ slot, int wmax, int nmax, int* status) {
   extern __shared__ double L[];
   const int4 r = rects[blockIdx.x];
   const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1;
-  double* B = band + (long long)blockIdx.x * nmax * ldb;
+  double* B = band + (long long)(slot ? slot[blockIdx.x] : blockIdx.x) * nmax * ldb;
   for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = B[t];
+  // this thread's pair: t = d1 (d1 - 1) / 2 + (d2 - 1)
+  const int t = threadIdx.x;
+  int d1 = 1;
+  while (d1 * (d1 + 1) / 2 <= t) ++d1;
+  const int d2 = t - d1 * (d1 - 1) / 2 + 1;
+  const bool has_pair = (d1 <= w);
   __syncthreads();
-  const int npair = w * (w + 1) / 2;
   for (int j = 0; j < nloc; ++j) {
-    if (threadIdx.x == 0) {
-      double piv = L[(long long)j * ldb];
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        atomicOr(status, kStNotSpd);
-        piv = 1.0;
-      }
-      L[(long long)j * ldb] = sqrt(piv);
+    double piv = L[(long long)j * ldb];
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      if (threadIdx.x == 0) atomicOr(status, kStNotSpd);
+      piv = 1.0;
+    }
+    const double rj = rsqrt(piv);
+    const bool act = has_pair && (j + d1 < nloc);
+    double l1 = 0.0, l2 = 0.0;
+    if (act) {
+      l1 = L[(long long)(j + d1) * ldb + d1] * rj;
+      l2 = L[(long long)(j + d2) * ldb + d2] * rj;
     }
     __syncthreads();
-    const double ljj = L[(long long)j * ldb];
-    for (int d = 1 + threadIdx.x; d <= w; d += blockDim.x)
-      if (j + d < nloc) L[(long long)(j + d) * ldb + d] /= ljj;
-    __syncthreads();
-    for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-      // t -> (d1, d2), 1 <= d2 <= d1 <= w
-      int d1 = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((d1 + 1) * (d1 + 2) / 2 <= t) ++d1;
-      while (d1 * (d1 + 1) / 2 > t) --d1;
-      const int d2 = t - d1 * (d1 + 1) / 2;  // 0..d1
-      const int D1 = d1 + 1, D2 = d2 + 1;     // 1..w
-      if (j + D1 < nloc)
-        L[(long long)(j + D1) * ldb + (D1 - D2)] -=
-            L[(long long)(j + D1) * ldb + D1] * L[(long long)(j + D2) * ldb + D2];
+    if (act) {
+      L[(long long)(j + d1) * ldb + (d1 - d2)] -= l1 * l2;
+      if (d1 == d2) L[(long long)(j + d1) * ldb + d1] = l1;
     }
+    if (threadIdx.x == 0) L[(long long)j * ldb] = piv * rj;
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) B[t] = L[t];
+  for (int q = threadIdx.x; q < nloc * ldb; q += blockDim.x) B[q] = L[q];
 }
 
 // columns of the inverse from the band factor: thread t solves L L^T x = e_t.
-// scratch (row-major, rows j, columns t) holds nloc x nloc per matrix.
+// CTA (m, y) takes columns c0 .. c0 + blockDim - 1 of matrix m, c0 =
+// y blockDim (further chunks strided by gridDim.y blockDim), so that a few
+// matrices still spread over many SMs.  The rows are swept in the same order
+// by every thread, so the band entries read from shared memory are
+// broadcasts; the reciprocals of the diagonal are formed once; each thread
+// keeps the last w values of its column in a private ring in shared memory
+// (ring[k * blockDim + thread]) and sums the band terms in four partial sums
+// (a short dependent chain: FP64 latency bounds this kernel when it runs on
+// few matrices).  The forward sweep, from row c0 on (y_j = 0 for j < t),
+// leaves y = L^{-1} e_t in scratch; the backward sweep overwrites it with
+// x = L^{-T} y.  scratch (row-major, rows j, columns t)
+// holds nloc x nloc per matrix.
+// sum over d = 1..dmax of c[(d - 1) stride] v_d, v_d the ring entry d slots
+// before pos (ring of rl entries, entry k at my[k T]), in four partial sums
+__device__ __forceinline__ double ring_dot(const double* c, int stride, const double* my, int T, int pos, int rl,
+                                           int dmax) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int q = pos, d = 1;
+  for (; d + 3 <= dmax; d += 4) {
+    const int q1 = (q == 0) ? rl - 1 : q - 1;
+    const int q2 = (q1 == 0) ? rl - 1 : q1 - 1;
+    const int q3 = (q2 == 0) ? rl - 1 : q2 - 1;
+    const int q4 = (q3 == 0) ? rl - 1 : q3 - 1;
+    a0 = fma(c[(d - 1) * stride], my[q1 * T], a0);
+    a1 = fma(c[d * stride], my[q2 * T], a1);
+    a2 = fma(c[(d + 1) * stride], my[q3 * T], a2);
+    a3 = fma(c[(d + 2) * stride], my[q4 * T], a3);
+    q = q4;
+  }
+  for (; d <= dmax; ++d) {
+    q = (q == 0) ? rl - 1 : q - 1;
+    a0 = fma(c[(d - 1) * stride], my[q * T], a0);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
 __global__ void k_band_inverse(const double* __restrict__ band, const int4* __restrict__ rects,
-                               int first, int wmax, int nmax, double* __restrict__ scratch) {
-  extern __shared__ double L[];
+                               const int* __restrict__ slot, int first, int wmax, int nmax,
+                               double* __restrict__ scratch) {
+  extern __shared__ double sh[];
   const int m = first + blockIdx.x;
   const int4 r = rects[m];
-  const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1;
-  const double* B = band + (long long)m * nmax * ldb;
+  const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1, rl = wmax + 1;
+  double* L = sh;
+  double* rd = sh + (long long)nmax * ldb;
+  double* ring = rd + nmax;
+  const double* B = band + (long long)(slot ? slot[m] : m) * nmax * ldb;
   for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = B[t];
   __syncthreads();
+  for (int t = threadIdx.x; t < nloc; t += blockDim.x) rd[t] = 1.0 / L[(long long)t * ldb];
+  __syncthreads();
   double* X = scratch + (long long)blockIdx.x * nmax * nmax;
-  for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-    for (int j = 0; j < t; ++j) X[(long long)j * nloc + t] = 0.0;
-    for (int j = t; j < nloc; ++j) {
-      double acc = (j == t) ? 1.0 : 0.0;
-      const int dmax = min(w, j - t);
-      for (int d = 1; d <= dmax; ++d) acc -= L[(long long)j * ldb + d] * X[(long long)(j - d) * nloc + t];
-      X[(long long)j * nloc + t] = acc / L[(long long)j * ldb];
+  double* my = ring + threadIdx.x;   // my[k * blockDim]
+  const int T = blockDim.x;
+  for (int c0 = blockIdx.y * T; c0 < nloc; c0 += gridDim.y * T) {
+    const int t = c0 + threadIdx.x;
+    const bool col = (t < nloc);
+    for (int q = 0; q < rl; ++q) my[q * T] = 0.0;
+    // forward: y_j = (delta_jt - sum_d L[j][d] y_{j-d}) / L[j][0]
+    int pos = 0;   // ring slot of row j
+    for (int j = c0; j < nloc; ++j) {
+      const double* Lj = L + (long long)j * ldb;
+      double y = 0.0;
+      if (col && j >= t) {
+        const double s4 = ring_dot(Lj + 1, 1, my, T, pos, rl, min(w, j - t));   // L[j][d]
+        y = (((j == t) ? 1.0 : 0.0) - s4) * rd[j];
+      }
+      my[pos * T] = y;
+      if (col) X[(long long)j * nloc + t] = y;
+      pos = (pos + 1 == rl) ? 0 : pos + 1;
     }
+    // backward: x_j = (y_j - sum_d L[j+d][d] x_{j+d}) / L[j][0]
+    pos = 0;
     for (int j = nloc - 1; j >= 0; --j) {
-      double acc = X[(long long)j * nloc + t];
-      const int dmax = min(w, nloc - 1 - j);
-      for (int d = 1; d <= dmax; ++d)
-        acc -= L[(long long)(j + d) * ldb + d] * X[(long long)(j + d) * nloc + t];
-      X[(long long)j * nloc + t] = acc / L[(long long)j * ldb];
+      if (col) {
+        // band entries L[j + d][d] lie ldb + 1 apart
+        const double s4 = ring_dot(L + (long long)(j + 1) * ldb + 1, ldb + 1, my, T, pos, rl, min(w, nloc - 1 - j));
+        const double yj = (j >= t) ? X[(long long)j * nloc + t] : 0.0;   // y_j = 0 above row t
+        const double x = (yj - s4) * rd[j];
+        my[pos * T] = x;
+        X[(long long)j * nloc + t] = x;
+      }
+      pos = (pos + 1 == rl) ? 0 : pos + 1;
     }
   }
 }
@@ -132,7 +199,8 @@ __global__ void k_store_inverse(const double* __restrict__ scratch, const PatchG
   const double* X = scratch + (long long)blockIdx.x * nmax * nmax;
   TS* M = pinv + g.off;
   const long long tot = (long long)g.nloc * g.ld;
-  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+  for (long long t = threadIdx.x + (long long)blockIdx.y * blockDim.x; t < tot;
+       t += (long long)blockDim.x * gridDim.y) {
     const int row = (int)(t / g.ld), col = (int)(t % g.ld);
     const double v = (col < g.nloc) ? X[(long long)row * g.nloc + col] : 0.0;
     M[t] = from_d<TS>(v);
@@ -145,13 +213,15 @@ __global__ void k_store_inverse(const double* __restrict__ scratch, const PatchG
 // limit and the smallest entries keep most of their precision; the power-of-
 // two factor is exact and rscale holds its inverse.  One warp per row.
 __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const PatchGeo* __restrict__ geo,
-                                    const int* __restrict__ gofs, int first, int nmax, __half* __restrict__ pinv,
-                                    float* __restrict__ rscale) {
-  const int p = first + blockIdx.x;
-  const PatchGeo g = geo[p];
+                                    const int* __restrict__ pidx, const int* __restrict__ gofs, int first, int nmax,
+                                    __half* __restrict__ pinv, float* __restrict__ rscale) {
+  const int c = first + blockIdx.x;
+  const PatchGeo g = geo[c];
+  const int p = pidx ? pidx[c] : c;   // patch number (geo may be a compacted list)
   const double* X = scratch + (long long)blockIdx.x * nmax * nmax;
   __half* M = pinv + g.off;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.y;
+  const int warp = (threadIdx.x >> 5) + blockIdx.y * (blockDim.x >> 5);
   for (int row = warp; row < g.nloc; row += nw) {
     const double* xr = X + (long long)row * g.nloc;
     double mx = 0.0;
@@ -165,6 +235,24 @@ __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const Pa
       M[(long long)row * g.ld + col] = __double2half(col < g.nloc ? xr[col] * sc : 0.0);
     if (lane == 0) rscale[(long long)gofs[p] * kRowsPerGroup + row] = (float)ldexp(1.0, e - 15);
   }
+}
+
+// flag[m] = 1 if any cell of rectangle m (cells x0 <= i <= x0 + nx,
+// y0 <= j <= y0 + ny) gets a new inverse permeability: 1/kappa computed as
+// k_kinv does, compared bit for bit with the stored value
+__global__ void k_rect_changed(const double* __restrict__ kappa, const double* __restrict__ kinv_old,
+                               const int4* __restrict__ rects, int n, unsigned char* __restrict__ flag) {
+  const int4 r = rects[blockIdx.x];
+  const int cw = r.z + 1, ch = r.w + 1;
+  int ch_any = 0;
+  for (int t = threadIdx.x; t < cw * ch; t += blockDim.x) {
+    const long long c = (long long)(r.y + t / cw) * n + r.x + t % cw;
+    const double k = kappa[c];
+    const double v = (k > 0.0 && isfinite(k)) ? 1.0 / k : 1.0;
+    if (v != kinv_old[c]) ch_any = 1;
+  }
+  ch_any = __syncthreads_or(ch_any);
+  if (threadIdx.x == 0) flag[blockIdx.x] = (unsigned char)ch_any;
 }
 
 // ---------------------------------------------------------------------------
@@ -789,8 +877,9 @@ __global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __re
 // energies of all slot pairs of a block: int_K kappa^{-1} (C psi_s).(C psi_t)
 __global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __restrict__ closed,
                               const double* __restrict__ kinv, const long long* __restrict__ pair_ptr,
-                              double* __restrict__ pairE, int n, int b) {
+                              const unsigned char* __restrict__ bmask, double* __restrict__ pairE, int n, int b) {
   const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
+  if (bmask && !bmask[blk]) return;
   const int s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
   const int nb1 = b + 1, ncl = nb1 * nb1;
   double* E = pairE + pair_ptr[blk];
@@ -810,18 +899,21 @@ __global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __
       const double bL = Pb[n01] - Pb[n00], bR = Pb[n11] - Pb[n10];
       const double bB = Pb[n00] - Pb[n10], bT = Pb[n01] - Pb[n11];
       const double k = kinv[(long long)(J * b + c) * n + I * b + a];
-      e += k * ((aL * bL + aR * bR + aB * bB + aT * bT) / 3.0 +
-                (aL * bR + aR * bL + aB * bT + aT * bB) / 6.0);
+      // (same-face products) / 3 + (opposite-face products) / 6, times 6
+      e += k * (2.0 * (aL * bL + aR * bR + aB * bB + aT * bT) + (aL * bR + aR * bL + aB * bT + aT * bB));
     }
+    e /= 6.0;
     E[sa * m + sb] = e;
     E[sb * m + sa] = e;
   }
 }
 
-// K[u][*] += pair energies of u's slots (one thread per row: deterministic)
+// K[u][*] += pair energies of u's slots (one thread per row: deterministic);
+// blocks with bmask[blk] == 0 contribute nothing
 __global__ void k_assemble_coarse(const int* __restrict__ slot_ptr, const Slot* __restrict__ slots,
                                   const int* __restrict__ gather, const long long* __restrict__ pair_ptr,
-                                  const double* __restrict__ pairE, double* __restrict__ K, int D) {
+                                  const double* __restrict__ pairE, const unsigned char* __restrict__ bmask,
+                                  double* __restrict__ K, int D) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= D) return;
   double* row = K + (long long)u * D;
@@ -829,6 +921,7 @@ __global__ void k_assemble_coarse(const int* __restrict__ slot_ptr, const Slot* 
     const int s = gather[4 * u + g];
     if (s < 0) continue;
     const int blk = slots[s].block, s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
+    if (bmask && !bmask[blk]) continue;
     const double* E = pairE + pair_ptr[blk] + (long long)(s - s0) * m;
     for (int t = 0; t < m; ++t) row[slots[s0 + t].coef] += E[t];
   }
@@ -855,6 +948,150 @@ __global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, 
   }
 }
 
+// ---- low-rank update of a Galerkin inverse ---------------------------------
+// The Galerkin matrix is linear in 1/kappa, so a change delta of 1/kappa
+// changes it by Delta = Galerkin(delta), nonzero only in the rows and columns
+// S of basis functions whose support meets a changed cell.  With B the old
+// inverse, X = B[:, S], P = B[S, S]^{-1} (the Schur complement of the old
+// matrix on S) and P + Delta[S, S] the new one, the new inverse is
+// B + X M X^T, M = -P (P + Delta[S, S])^{-1} Delta[S, S] (symmetric).
+
+// delta = 1/kappa_new - kinv_old, 1/kappa_new computed as k_kinv computes it
+__global__ void k_kinv_delta(const double* __restrict__ kappa, const double* __restrict__ kinv_old,
+                             double* __restrict__ delta, long long nn) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double k = kappa[t];
+    const double v = (k > 0.0 && isfinite(k)) ? 1.0 / k : 1.0;
+    delta[t] = v - kinv_old[t];
+  }
+}
+
+// flag[i] = 1 if row i of the D x D matrix K has a nonzero (one warp per row)
+__global__ void k_row_nonzero(const double* __restrict__ K, int D, unsigned char* __restrict__ flag) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= D) return;
+  const double* r = K + (long long)warp * D;
+  int nz = 0;
+  for (int j = lane; j < D; j += 32) nz |= (r[j] != 0.0);
+  nz = __any_sync(0xffffffffu, nz);
+  if (lane == 0) flag[warp] = (unsigned char)nz;
+}
+
+// out[i * s + a] = K[row(i) * D + S[a]], row(i) = i (rows_all) or S[i]
+__global__ void k_gather_cols(const double* __restrict__ K, int D, const int* __restrict__ S, int s, int rows,
+                              int rows_all, double* __restrict__ out) {
+  const long long tot = (long long)rows * s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / s), a = (int)(t % s);
+    const int r = rows_all ? i : S[i];
+    out[t] = K[(long long)r * D + S[a]];
+  }
+}
+
+// in-place Gauss-Jordan inverse of an SPD s x s matrix by one CTA (the pivot
+// row and column are staged in shared memory before each elimination step)
+__global__ void k_gj_small(double* __restrict__ A, int s, int* __restrict__ bad) {
+  extern __shared__ double st[];   // 2 s
+  double* rowk = st;
+  double* colk = st + s;
+  const int tot = s * s;
+  for (int k = 0; k < s; ++k) {
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+      rowk[j] = A[(long long)k * s + j];
+      colk[j] = A[(long long)j * s + k];
+    }
+    __syncthreads();
+    double p = rowk[k];
+    if (!(p > 0.0) || !isfinite(p)) {
+      if (threadIdx.x == 0) *bad = 1;
+      p = 1.0;
+    }
+    const double ip = 1.0 / p;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int i = t / s, j = t % s;
+      double v;
+      if (i == k && j == k) v = ip;
+      else if (i == k) v = rowk[j] * ip;
+      else if (j == k) v = -colk[i] * ip;
+      else v = A[t] - colk[i] * rowk[j] * ip;
+      A[t] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// C = alpha op(A) op(B) + beta C, FP64, C m x n row-major with leading
+// dimension ldc; op(A)(i, k) = A[i * ars + k * acs], op(B)(k, j) = B[k * brs + j * bcs].
+// 64 x 64 tiles of C per CTA, 16-deep slices of k staged in shared memory,
+// each of the 256 threads accumulating a 4 x 4 sub-tile
+__global__ void __launch_bounds__(256) k_dgemm(int m, int n, int kdim, double alpha, const double* __restrict__ A,
+                                               long long ars, long long acs, const double* __restrict__ B,
+                                               long long brs, long long bcs, double beta, double* __restrict__ C,
+                                               long long ldc) {
+  __shared__ double sa[16][64 + 1];
+  __shared__ double sb[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < kdim; k0 += 16) {
+    for (int t = threadIdx.x; t < 64 * 16; t += 256) {
+      const int r = t / 16, kk = t % 16;       // A tile element (row r, depth kk)
+      const int gi = i0 + r, gk = k0 + kk;
+      sa[kk][r] = (gi < m && gk < kdim) ? A[gi * ars + gk * acs] : 0.0;
+      const int c = t % 64, kb = t / 64;       // B tile element (depth kb, column c)
+      const int gj = j0 + c, gkb = k0 + kb;
+      sb[kb][c] = (gj < n && gkb < kdim) ? B[gkb * brs + gj * bcs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = sa[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = sb[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+      if (gi < m && gj < n) {
+        double* cp = C + gi * ldc + gj;
+        *cp = alpha * acc[r][c] + (beta != 0.0 ? beta * *cp : 0.0);
+      }
+    }
+}
+
+// A (s x s) = (A + A^T) / 2, one thread per pair i < j
+__global__ void k_symmetrize(double* __restrict__ A, int s) {
+  const long long tot = (long long)s * s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / s), j = (int)(t % s);
+    if (i < j) {
+      const double v = 0.5 * (A[t] + A[(long long)j * s + i]);
+      A[t] = v;
+      A[(long long)j * s + i] = v;
+    }
+  }
+}
+
+// y += x elementwise
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ x, long long cnt) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] += x[t];
+}
+
 }  // namespace
 
 // ---- launchers ---------------------------------------------------------------
@@ -865,25 +1102,55 @@ void launch_kinv(const double* kappa, double* kinv, float* kinv32, int* status, 
   k_kinv<<<g, 256, 0, s>>>(kappa, kinv, kinv32, status, n);
 }
 void launch_assemble_band(const double* kinv, const int4* rects, double* band, int nmat, int wmax, int nmax,
-                          int n, cudaStream_t s) {
-  k_assemble_band<<<nmat, 128, 0, s>>>(kinv, rects, band, wmax, nmax, n);
+                          int n, cudaStream_t s, const int* slot) {
+  if (nmat == 0) return;
+  k_assemble_band<<<nmat, 128, 0, s>>>(kinv, rects, slot, band, wmax, nmax, n);
 }
 void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, int nmax, int* status,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* slot) {
+  if (nmat == 0) return;
   const size_t shm = sizeof(double) * (size_t)nmax * (wmax + 1);
+  // one thread per pair (d1, d2) of the band: w (w + 1) / 2 <= blockDim
+  const int threads = std::max(32, ((wmax * (wmax + 1) / 2 + 31) / 32) * 32);
   cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  k_band_cholesky<<<nmat, 256, shm, s>>>(band, rects, wmax, nmax, status);
+  k_band_cholesky<<<nmat, threads, shm, s>>>(band, rects, slot, wmax, nmax, status);
 }
+// CTAs per matrix so that `count` matrices fill about two waves of the SMs
+// (at most one per 32 columns or rows of a matrix of side nmax)
+static int split_for(int count, int nmax, int granule) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  const int want = (2 * sms + count - 1) / count;
+  return std::max(1, std::min(want, (nmax + granule - 1) / granule));
+}
+
 void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax, int nmax,
-                         double* scratch, cudaStream_t s) {
-  const size_t shm = sizeof(double) * (size_t)nmax * (wmax + 1);
+                         double* scratch, cudaStream_t s, const int* slot) {
+  if (count == 0) return;
+  // one thread per column, the columns of a matrix split over `split` CTAs,
+  // as far as the ring fits beside the band
+  const int split = split_for(count, nmax, 32);
+  const size_t band_b = sizeof(double) * ((size_t)nmax * (wmax + 1) + nmax);
+  int threads = std::min(1024, (((nmax + split - 1) / split + 31) / 32) * 32);
+  while (threads > 32 && band_b + sizeof(double) * (size_t)threads * (wmax + 1) > (size_t)kMaxDynSmem) threads -= 32;
+  const size_t shm = band_b + sizeof(double) * (size_t)threads * (wmax + 1);
   cudaFuncSetAttribute(k_band_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  k_band_inverse<<<count, 128, shm, s>>>(band, rects, first, wmax, nmax, scratch);
+  k_band_inverse<<<dim3(count, split), threads, shm, s>>>(band, rects, slot, first, wmax, nmax, scratch);
+}
+void launch_rect_changed(const double* kappa, const double* kinv_old, const int4* rects, int nrect, int n,
+                         unsigned char* flag, cudaStream_t s) {
+  if (nrect == 0) return;
+  k_rect_changed<<<nrect, 256, 0, s>>>(kappa, kinv_old, rects, n, flag);
 }
 template <typename TS>
 void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first, int count, int nmax,
                           TS* pinv, cudaStream_t s) {
-  k_store_inverse<TS><<<count, 256, 0, s>>>(scratch, geo, first, nmax, pinv);
+  if (count == 0) return;
+  k_store_inverse<TS><<<dim3(count, split_for(count, nmax, 8)), 256, 0, s>>>(scratch, geo, first, nmax, pinv);
 }
 template void launch_store_inverse<double>(const double*, const PatchGeo*, int, int, int, double*,
                                            cudaStream_t);
@@ -893,8 +1160,10 @@ template void launch_store_inverse<__nv_bfloat16>(const double*, const PatchGeo*
                                                   __nv_bfloat16*, cudaStream_t);
 
 void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const int* gofs, int first, int count,
-                              int nmax, __half* pinv, float* rscale, cudaStream_t s) {
-  k_store_inverse_f16<<<count, 256, 0, s>>>(scratch, geo, gofs, first, nmax, pinv, rscale);
+                              int nmax, __half* pinv, float* rscale, cudaStream_t s, const int* pidx) {
+  if (count == 0) return;
+  k_store_inverse_f16<<<dim3(count, split_for(count, nmax, 8)), 256, 0, s>>>(scratch, geo, pidx, gofs, first, nmax,
+                                                                             pinv, rscale);
 }
 void launch_snapshots(const double* kinv, const double* blk_band, const double* coef, int nfn,
                       const unsigned char* mask, double* psiS, double* gram, int n, int b, cudaStream_t s) {
@@ -929,12 +1198,49 @@ template void launch_build_tiles<__nv_bfloat16>(const CoarseSpace&, const double
                                                 const double*, const int*, int, int, int, cudaStream_t);
 
 void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b, double* pairE,
-                     const long long* pair_ptr, double* K, cudaStream_t s) {
+                     const long long* pair_ptr, double* K, cudaStream_t s, const unsigned char* bmask) {
   if (cs.D == 0) return;
-  k_pair_energy<<<nblocks, 128, 0, s>>>(cs.slot_ptr, cs.closed, kinv, pair_ptr, pairE, n, b);
+  k_pair_energy<<<nblocks, 128, 0, s>>>(cs.slot_ptr, cs.closed, kinv, pair_ptr, bmask, pairE, n, b);
   cudaMemsetAsync(K, 0, sizeof(double) * (size_t)cs.D * cs.D, s);
-  k_assemble_coarse<<<(cs.D + 127) / 128, 128, 0, s>>>(cs.slot_ptr, cs.slots, cs.gather, pair_ptr, pairE,
+  k_assemble_coarse<<<(cs.D + 127) / 128, 128, 0, s>>>(cs.slot_ptr, cs.slots, cs.gather, pair_ptr, pairE, bmask,
                                                         K, cs.D);
+}
+static int grid_of(long long cnt, int threads, int cap) {
+  long long g = (cnt + threads - 1) / threads;
+  return (int)std::max<long long>(1, std::min<long long>(g, cap));
+}
+
+void launch_kinv_delta(const double* kappa, const double* kinv_old, double* delta, int n, cudaStream_t s) {
+  const long long nn = (long long)n * n;
+  k_kinv_delta<<<grid_of(nn, 256, 4096), 256, 0, s>>>(kappa, kinv_old, delta, nn);
+}
+void launch_row_nonzero(const double* K, int D, unsigned char* flag, cudaStream_t s) {
+  if (D == 0) return;
+  k_row_nonzero<<<(int)(((long long)D * 32 + 255) / 256), 256, 0, s>>>(K, D, flag);
+}
+void launch_gather_cols(const double* K, int D, const int* S, int s_cnt, int rows, bool rows_all, double* out,
+                        cudaStream_t s) {
+  if (rows == 0 || s_cnt == 0) return;
+  k_gather_cols<<<grid_of((long long)rows * s_cnt, 256, 4096), 256, 0, s>>>(K, D, S, s_cnt, rows,
+                                                                           rows_all ? 1 : 0, out);
+}
+void launch_gj_small(double* A, int s_cnt, int* bad, cudaStream_t s) {
+  if (s_cnt == 0) return;
+  k_gj_small<<<1, 1024, sizeof(double) * 2 * (size_t)s_cnt, s>>>(A, s_cnt, bad);
+}
+void launch_dgemm(int m, int n, int k, double alpha, const double* A, long long ars, long long acs,
+                  const double* B, long long brs, long long bcs, double beta, double* C, long long ldc,
+                  cudaStream_t s) {
+  if (m == 0 || n == 0) return;
+  k_dgemm<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, s>>>(m, n, k, alpha, A, ars, acs, B, brs, bcs, beta, C, ldc);
+}
+void launch_symmetrize(double* A, int s_cnt, cudaStream_t s) {
+  if (s_cnt == 0) return;
+  k_symmetrize<<<grid_of((long long)s_cnt * s_cnt, 256, 1024), 256, 0, s>>>(A, s_cnt);
+}
+void launch_add(double* y, const double* x, long long cnt, cudaStream_t s) {
+  if (cnt == 0) return;
+  k_add<<<grid_of(cnt, 256, 4096), 256, 0, s>>>(y, x, cnt);
 }
 void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s) {
   long long m = (long long)D * D;

@@ -11,15 +11,17 @@ import time
 
 from . import tgms
 
-COARSE_MODES = {"frozen": 0, "rebuild": 1}
+COARSE_MODES = {"frozen": 0, "rebuild": 1, "frozen_full": 2}
 
 
 class Impes:
     """kappa, f: (n, n) torch float64 CUDA tensors (absolute permeability,
     cell source densities: f > 0 injects water, f < 0 produces).  coarse:
-    'frozen' keeps the coarse basis of the first setup (the paper's choice),
-    'rebuild' rebuilds it every step by the handle's method (exact spectral
-    problems, or the learned basis with coarse_space='learned')."""
+    'frozen' keeps the coarse basis of the first setup (the paper's choice)
+    and updates the coarse inverses by low-rank corrections; 'frozen_full'
+    keeps the basis and recomputes the inverses in full; 'rebuild' rebuilds
+    the basis every step by the handle's method (exact spectral problems, or
+    the learned basis with coarse_space='learned')."""
 
     def __init__(self, kappa, f, b, eig_tol=10.0, s0=None, mu_w=1.0, mu_o=5.0, cfl=0.5, rtol=1e-8,
                  coarse="frozen", **solver_opts):
@@ -39,7 +41,8 @@ class Impes:
         self.ux_prev = None
         self.t = 0.0
         self.steps = 0
-        self.history = []    # per step: (dt, PCG iterations, update ms, solve ms, transport ms)
+        self.history = []    # per step: (dt, PCG iterations, update ms, solve ms, transport ms, patches refactored,
+                             #  rank of the coarse-inverse update, -1 = full)
 
     def step(self):
         tg, torch = tgms, self.torch
@@ -59,7 +62,8 @@ class Impes:
         self.ux_prev = self.solver.ux.clone()
         self.t += dt
         self.steps += 1
-        self.history.append((dt, it, 1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2)))
+        self.history.append((dt, it, 1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), rep.refactored_patches,
+                             rep.update_rank[0]))
         return dt, it
 
     def close(self):

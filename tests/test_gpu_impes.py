@@ -93,7 +93,110 @@ def test_update_kappa(tg, coarse):
         fresh.close()
 
 
-@pytest.mark.parametrize("prec,coarse", [("f64", "frozen"), ("f64", "rebuild"), ("bf16", "frozen")])
+def _rect_hits(rects, cells):
+    """Rectangles (x0, y0, x1, y1), cell bounds inclusive, that hold a cell of `cells`."""
+    return sum(any(x0 <= i <= x1 and y0 <= j <= y1 for i, j in cells) for x0, y0, x1, y1 in rects)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_update_kappa_refactors_only_changed(tg, prec):
+    """A permeability change confined to a few cells refactors only the
+    patches and blocks holding one of them (patch K_i^+ of block (I, J) spans
+    cells max(0, Ib - 2) .. min(n, (I + 1) b + 2) - 1 in each direction), and
+    the updated handle's smoother, coarse space and solve agree with a fresh
+    setup on the new permeability."""
+    n, b, ov = 48, 8, 2
+    nc = n // b
+    k1 = inputs.lognormal_field(n, 3, sigma=1.0)
+    k2 = k1.copy()
+    cells = [(6, 0), (6, 1), (20, 33)]          # (i, j)
+    for i, j in cells:
+        k2[j, i] *= 7.0
+    k2[40, 40] = k1[40, 40]                     # rewritten with the same value: no change
+    patches = [(max(0, I * b - ov), max(0, J * b - ov), min(n, (I + 1) * b + ov) - 1, min(n, (J + 1) * b + ov) - 1)
+               for J in range(nc) for I in range(nc)]
+    blocks = [(I * b, J * b, I * b + b - 1, J * b + b - 1) for J in range(nc) for I in range(nc)]
+    f = inputs.quarter_five_spot(n)
+    opts = dict(precision=prec, flexible=int(prec != "f64"), smoother_shape=0)
+    s = tg.Solver(dev(k1), b, 10.0, **opts)
+    fresh = tg.Solver(dev(k2), b, 10.0, **opts)
+    try:
+        s.solve(f, rtol=1e-10)
+        tg.tg_update_kappa(s.h, dev(k2), 1)
+        it, rep = s.solve(f, rtol=1e-12)
+        assert rep.refactored_patches == _rect_hits(patches, cells) == 4
+        assert rep.refactored_blocks == _rect_hits(blocks, cells) == 2
+        it_f, rep_f = fresh.solve(f, rtol=1e-12)
+        assert rep_f.refactored_patches == nc * nc and it == it_f
+        got = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        ref = np.concatenate([fresh.ux.cpu().numpy().ravel(), fresh.uy.cpu().numpy().ravel()])
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+        rng = np.random.default_rng(5)
+        rho = np.zeros((n, n))
+        rho[1:, 1:] = rng.standard_normal((n - 1, n - 1))
+        outs = []
+        for sol in (s, fresh):
+            for fn in (tg.tg_apply_smoother, tg.tg_apply_coarse):
+                z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+                fn(sol.h, dev(rho), z)
+                outs.append(z.cpu().numpy())
+        tol = 1e-13 if prec == "f64" else 1e-6     # same stored inverses; FP32 summation order for FP16
+        for a, r in zip(outs[:2], outs[2:]):
+            assert np.linalg.norm(a - r) <= tol * np.linalg.norm(r)
+        # unchanged permeability: nothing refactored, same iterations
+        tg.tg_update_kappa(s.h, dev(k2), 0)
+        it2, rep2 = s.solve(f, rtol=1e-12)
+        assert rep2.refactored_patches == 0 and rep2.refactored_blocks == 0 and it2 == it
+    finally:
+        s.close()
+        fresh.close()
+
+
+def test_low_rank_coarse_update_matches_full_inverse(tg):
+    """A sequence of local permeability changes: the coarse inverses updated
+    by low-rank corrections (coarse = 0) apply as the ones recomputed in full
+    (coarse = 2), and the solves take the same iterations."""
+    n, b = 64, 8
+    rng = np.random.default_rng(11)
+    k = inputs.channel_field(n, 1e4, 6)
+    f = inputs.quarter_five_spot(n)
+    lo = tg.Solver(dev(k), b, 10.0)
+    full = tg.Solver(dev(k), b, 10.0)
+    try:
+        for step in range(6):
+            k = k.copy()
+            j0, i0 = rng.integers(0, n - 6, size=2)
+            k[j0:j0 + 5, i0:i0 + 5] *= rng.uniform(0.2, 5.0, size=(5, 5))   # a 5 x 5 cell change
+            tg.tg_update_kappa(lo.h, dev(k), 0)
+            tg.tg_update_kappa(full.h, dev(k), 2)
+            it, rep = lo.solve(f, rtol=1e-12)
+            it_f, rep_f = full.solve(f, rtol=1e-12)
+            assert 0 < rep.update_rank[0] and 4 * rep.update_rank[0] <= rep.coarse_unknowns, rep.update_rank
+            assert 0 < rep.update_rank[1], rep.update_rank
+            assert list(rep_f.update_rank) == [-1, -1]
+            assert abs(it - it_f) <= 1
+            rho = np.zeros((n, n))
+            rho[1:, 1:] = rng.standard_normal((n - 1, n - 1))
+            z = [torch.zeros(n, n, dtype=torch.float64, device=DEV) for _ in range(2)]
+            tg.tg_apply_coarse(lo.h, dev(rho), z[0])
+            tg.tg_apply_coarse(full.h, dev(rho), z[1])
+            a, r = z[0].cpu().numpy(), z[1].cpu().numpy()
+            assert np.linalg.norm(a - r) <= 1e-10 * np.linalg.norm(r), step
+            got = np.concatenate([lo.ux.cpu().numpy().ravel(), lo.uy.cpu().numpy().ravel()])
+            ref = np.concatenate([full.ux.cpu().numpy().ravel(), full.uy.cpu().numpy().ravel()])
+            assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+        tg.tg_update_kappa(lo.h, dev(k), 0)                 # no change: nothing to update
+        _, rep = lo.solve(f, rtol=1e-12)
+        assert list(rep.update_rank) == [0, 0]
+        with pytest.raises(tg.TgmsError):
+            tg.tg_update_kappa(lo.h, dev(k), 3)
+    finally:
+        lo.close()
+        full.close()
+
+
+@pytest.mark.parametrize("prec,coarse", [("f64", "frozen"), ("f64", "frozen_full"), ("f64", "rebuild"),
+                                        ("bf16", "frozen")])
 def test_impes_matches_oracle(tg, prec, coarse):
     from paper_1807_07220_gb300.impes import Impes
     n, b, steps = 32, 8, 6
