@@ -486,23 +486,49 @@ def run_learned(args):
 def run_impes(args):
     """Two-phase IMPES (Section 6.2) at 512 x 512 with 16 x 16 blocks:
     channels at 1e5, water injected in cell (0, 0) and produced in
-    (n-1, n-1), mu_w = 1, mu_o = 5, CFL 0.5, args.impes_steps steps, with the
-    coarse basis of the first setup kept (the paper's choice; coarse inverses
-    updated by low-rank corrections, or recomputed in full) and rebuilt
-    exactly every step."""
+    (n-1, n-1), mu_w = 1, mu_o = 5, CFL 0.5, args.impes_steps steps.  Arms:
+    the coarse basis of the first setup kept (the paper's choice) with the
+    coarse inverses updated by low-rank corrections ('frozen', the headline)
+    or recomputed in full ('frozen_full'); the basis rebuilt every step from
+    the exact spectral problems ('rebuild') or from the learned network with
+    per-face exact fallback ('rebuild_learned', network trained beforehand on
+    args.train_fields other seeded channel fields of the same size)."""
     import numpy as np
     import torch
-    from paper_1807_07220_gb300 import inputs
+    from paper_1807_07220_gb300 import inputs, tgms
     from paper_1807_07220_gb300.impes import Impes
     torch.cuda.set_device(0)
-    n, b = args.n, args.b
-    kap = torch.as_tensor(inputs.channel_field(n, 1e5, 77), dtype=torch.float64, device="cuda")
-    f = torch.as_tensor(inputs.quarter_five_spot(n), dtype=torch.float64, device="cuda")
+    n, b, k = args.n, args.b, 4
+    dev = "cuda"
+    stream = torch.cuda.current_stream().cuda_stream
+    kap = torch.as_tensor(inputs.channel_field(n, 1e5, 77), dtype=torch.float64, device=dev)
+    f = torch.as_tensor(inputs.quarter_five_spot(n), dtype=torch.float64, device=dev)
+    # ---- network for the learned rebuild: labels from other channel fields
+    nc = n // b
+    F = 2 * nc * (nc - 1)
+    din, dout, npar = tgms.tg_mlp_shape(b, k, args.hidden)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = torch.empty((args.train_fields * F, din), dtype=torch.bfloat16, device=dev)
+    Q = torch.empty((args.train_fields * F, k, b), dtype=torch.float32, device=dev)
+    for i in range(args.train_fields):
+        kt = torch.as_tensor(inputs.channel_field(n, 1e5, 6000 + i), dtype=torch.float64, device=dev)
+        tgms.tg_face_data(kt, n, b, EIG_TOL, k, X[i * F:(i + 1) * F], Q[i * F:(i + 1) * F], stream=stream)
+    params = torch.as_tensor(inputs.mlp_init_params(din, dout, args.hidden, 17), device=dev)
+    net = tgms.Mlp(b, k, args.hidden, params, stream=stream)
+    order = torch.as_tensor(inputs.sample_order(X.shape[0], args.train_steps, 1024, 23), device=dev)
+    loss = torch.zeros(args.train_steps, dtype=torch.float32, device=dev)
+    net.train(X, Q, order, args.train_steps, 1024, 1e-3, loss)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
     arms = {}
-    for mode in ("frozen", "frozen_full", "rebuild"):
+    modes = (("frozen", dict(coarse="frozen")), ("frozen_full", dict(coarse="frozen_full")),
+             ("rebuild", dict(coarse="rebuild")),
+             ("rebuild_learned", dict(coarse="rebuild", coarse_space="learned", net=net)))
+    for name, kw in modes:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, coarse=mode, precision=args.precision, flexible=1)
+        sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, precision=args.precision, flexible=1, **kw)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         t0 = time.perf_counter()
@@ -512,17 +538,20 @@ def run_impes(args):
         wall = time.perf_counter() - t0
         hist = np.array(sim.history)
         water = float(sim.s.sum()) / n ** 2
-        arms[mode] = {"steps": sim.steps, "t_final": sim.t, "wall_s": wall, "steps_per_s": sim.steps / wall,
+        arms[name] = {"steps": sim.steps, "t_final": sim.t, "wall_s": wall, "steps_per_s": sim.steps / wall,
                       "setup_s": setup_s, "iters_mean": float(hist[:, 1].mean()), "iters_max": int(hist[:, 1].max()),
                       "update_ms_mean": float(hist[:, 2].mean()), "solve_ms_mean": float(hist[:, 3].mean()),
                       "transport_ms_mean": float(hist[:, 4].mean()),
-                      "refactored_patch_frac_mean": float(hist[1:, 5].mean()) / (n // b) ** 2 if sim.steps > 1 else 1.0,
+                      "refactored_patch_frac_mean": float(hist[1:, 5].mean()) / nc ** 2 if sim.steps > 1 else 1.0,
                       "coarse_update_rank_mean": float(hist[1:, 6][hist[1:, 6] >= 0].mean())
                       if (hist[1:, 6] >= 0).any() else None,
                       "coarse_full_inverses": int((hist[1:, 6] < 0).sum()),
+                      "snapshot_solves_per_space": float(hist[1:, 7].mean()) if sim.steps > 1 else 0.0,
+                      "fallback_faces_mean": float(hist[1:, 8].mean()) if sim.steps > 1 else 0.0,
                       "pressure_dof_solves_per_s": dof(n) / (float(hist[:, 3].mean()) / 1e3),
                       "water_volume": water, "s_max": float(sim.s.max())}
         sim.close()
+    net.close()
     line = {
         "metric": "IMPES steps/s (pressure update + warm-started solve + transport)",
         "value": arms["frozen"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.impes_steps,
@@ -530,7 +559,9 @@ def run_impes(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
         "config": {"workload": "%dx%d two-phase IMPES, %dx%d-cell blocks, channels 1e5, quarter five-spot, "
                                "mu_w 1, mu_o 5, CFL 0.5, rtol %g" % (n, n, b, b, RTOL)},
-        "arms": arms,
+        "arms": arms, "faces": F,
+        "training": {"fields": args.train_fields, "samples": int(X.shape[0]), "steps": args.train_steps,
+                     "seconds": train_s, "loss_last": float(loss[-50:].mean())},
     }
     print(json.dumps(line), flush=True)
 

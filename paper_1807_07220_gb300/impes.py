@@ -42,7 +42,8 @@ class Impes:
         self.t = 0.0
         self.steps = 0
         self.history = []    # per step: (dt, PCG iterations, update ms, solve ms, transport ms, patches refactored,
-                             #  rank of the coarse-inverse update, -1 = full)
+                             #  rank of the coarse-inverse update (-1 = full), snapshot solves of the
+                             #  current coarse space, its faces that fell back to the exact problem)
 
     def step(self):
         tg, torch = tgms, self.torch
@@ -63,7 +64,7 @@ class Impes:
         self.t += dt
         self.steps += 1
         self.history.append((dt, it, 1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), rep.refactored_patches,
-                             rep.update_rank[0]))
+                             rep.update_rank[0], rep.snapshot_solves, rep.fallback_faces))
         return dt, it
 
     def close(self):

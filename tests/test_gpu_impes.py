@@ -196,20 +196,34 @@ def test_low_rank_coarse_update_matches_full_inverse(tg):
 
 
 @pytest.mark.parametrize("prec,coarse", [("f64", "frozen"), ("f64", "frozen_full"), ("f64", "rebuild"),
-                                        ("bf16", "frozen")])
+                                        ("f64", "rebuild_learned"), ("bf16", "frozen")])
 def test_impes_matches_oracle(tg, prec, coarse):
+    """IMPES on the GPU against the oracle's IMPES on direct solves; the
+    learned rebuild uses an untrained network (seeded initial weights), so
+    its faces mostly fall back to the exact problem."""
     from paper_1807_07220_gb300.impes import Impes
     n, b, steps = 32, 8, 6
     g = Grid(n, b)
     kap = inputs.channel_field(n, 1e3, 4)
     f = inputs.quarter_five_spot(n)
     hist, dts = M.impes(g, kap, f, np.zeros((n, n)), steps, cfl=0.5)
-    sim = Impes(dev(kap), dev(f), b, rtol=1e-12, coarse=coarse, precision=prec, flexible=int(prec != "f64"))
+    net = None
+    opts = dict(coarse=coarse)
+    if coarse == "rebuild_learned":
+        din, dout, _ = tg.tg_mlp_shape(b, 4, 64)
+        params = torch.as_tensor(inputs.mlp_init_params(din, dout, 64, 3), dtype=torch.float32, device=DEV)
+        net = tg.Mlp(b, 4, 64, params, stream=stream())
+        opts = dict(coarse="rebuild", coarse_space="learned", net=net)
+    sim = Impes(dev(kap), dev(f), b, rtol=1e-12, precision=prec, flexible=int(prec != "f64"), **opts)
     try:
         for k in range(steps):
             dt, it = sim.step()
             assert abs(dt - dts[k]) <= 1e-9 * dts[k]
             np.testing.assert_allclose(sim.s.cpu().numpy(), hist[k + 1], rtol=0, atol=1e-9)
         assert sim.s.cpu().numpy().max() > 0.1       # water has entered
+        if net is not None:
+            assert all(h[7] > 0 for h in sim.history)   # the space was rebuilt every step
     finally:
         sim.close()
+        if net is not None:
+            net.close()
