@@ -46,14 +46,19 @@ class TwoGridSolver:
     L_H = R_0 L_h R_0^T factored once; oversampled local matrices L_i^+
     factored once (direct solvers for all subdomain and coarse problems,
     Section 5).  ``coarse`` selects the comparator coarse spaces ('rt0',
-    'msfem') instead of 'gmsfem'."""
+    'msfem') instead of 'gmsfem'.  ``cycle`` = 'multiplicative' is the
+    two-grid cycle of Section 5; 'additive' is the two-level Schwarz
+    preconditioner S + P that Section 5 contrasts it with (no residual
+    recomputed between the two parts; m1 and m2 unused)."""
 
     def __init__(self, n, b, kappa, tol=10.0, eta=0.2, overlap=2, m1=1, m2=1,
-                 coarse="gmsfem", cap=None, profiles=None):
+                 coarse="gmsfem", cap=None, profiles=None, cycle="multiplicative"):
         from .fine import Grid
+        if cycle not in ("multiplicative", "additive"):
+            raise ValueError("cycle must be 'multiplicative' or 'additive'")
         self.g = g = Grid(n, b, overlap)
         self.kappa = np.asarray(kappa, float).reshape(n, n)
-        self.eta, self.m1, self.m2 = eta, m1, m2
+        self.eta, self.m1, self.m2, self.cycle = eta, m1, m2, cycle
         self.A, self.B = assemble(g, self.kappa)
         self.If = g.interior_faces()
         self.pos = -np.ones(g.nf, dtype=np.int64)
@@ -119,7 +124,10 @@ class TwoGridSolver:
 
     def precondition(self, r):
         """Two-grid cycle: m1 smoothing steps, one coarse step, m2 smoothing
-        steps, recomputing the residual after every step (Section 5)."""
+        steps, recomputing the residual after every step (Section 5).  The
+        additive cycle applies both parts to r itself: S r + P r."""
+        if self.cycle == "additive":
+            return self.smoother(r) + self.coarse_correction(r)
         x = np.zeros_like(r)
         for _ in range(self.m1):
             x = x + self.smoother(r - self.AII @ x)

@@ -246,13 +246,27 @@ def test_kappa_one_spectrum_identical_on_all_faces():
 
 
 # --------------------------------------------------------------------- two-grid
-def test_preconditioner_symmetric_positive_and_lanczos_cond():
+def _on_divfree(s, M):
+    """Eigenvalues of M A restricted to the divergence-free space (range of C)."""
+    C = s.C.toarray()
+    T = np.linalg.solve(C.T @ C, C.T @ M @ s.AII.toarray() @ C)
+    ev = np.linalg.eigvals(T)
+    assert np.abs(ev.imag).max() <= 1e-8 * np.abs(ev).max()
+    return np.sort(ev.real)
+
+
+def _dense(s, fn):
+    return np.column_stack([fn(e) for e in np.eye(s.If.size)])
+
+
+@pytest.mark.parametrize("cycle", ["multiplicative", "additive"])
+def test_preconditioner_symmetric_positive_and_lanczos_cond(cycle):
     """Dense preconditioner on an 8 x 8 grid: symmetric, maps into the
     divergence-free space, and the Lanczos Cond of a converged PCG equals the
     extreme eigenvalue ratio of M A on that space."""
     n, b = 8, 4
     kappa = lognormal_field(n, 13, sigma=2.0)
-    s = TwoGridSolver(n, b, kappa, tol=50.0)
+    s = TwoGridSolver(n, b, kappa, tol=50.0, cycle=cycle)
     m = s.If.size
     M = np.column_stack([s.precondition(e) for e in np.eye(m)])
     assert np.abs(M - M.T).max() <= 1e-11 * np.abs(M).max()
@@ -265,6 +279,37 @@ def test_preconditioner_symmetric_positive_and_lanczos_cond():
     assert ev[0] > 0
     out = s.solve(random_pairs(n, 2, 14), rtol=1e-14)
     assert abs(out["cond"] / (ev[-1] / ev[0]) - 1) < 0.02
+
+
+def test_cycles_against_operator_algebra():
+    """On a 12 x 12 grid with 4 x 4 blocks, as dense operators on the
+    divergence-free space: the coarse correction P A is the A-orthogonal
+    projection onto the coarse divergence-free space (eigenvalues 0 and 1, as
+    many 1s as the coarse space's divergence-free dimension); the additive
+    cycle's spectrum lies in (0, lambda_max(S A) + 1] (sum of two operators
+    self-adjoint in the A inner product); and the multiplicative cycle with
+    m1 = 1, m2 = 0 is S + P - P A S (residual recomputed between the two
+    steps, eq. smooth then eq. coarsepre)."""
+    n, b = 12, 4
+    kappa = lognormal_field(n, 21, sigma=1.5)
+    add = TwoGridSolver(n, b, kappa, tol=50.0, cycle="additive")
+    mul = TwoGridSolver(n, b, kappa, tol=50.0, m1=1, m2=0)
+    S = _dense(add, add.smoother)
+    P = _dense(add, add.coarse_correction)
+    A = add.AII.toarray()
+    evP = _on_divfree(add, P)
+    assert np.all(np.minimum(np.abs(evP), np.abs(evP - 1)) < 1e-9)
+    # coarse divergence-free dimension: basis functions minus the rank of the coarse divergence
+    Phi = add.Phi.toarray()
+    BH = (add.PH.T @ add.BI @ add.Phi).toarray()
+    dim = Phi.shape[1] - np.linalg.matrix_rank(BH)
+    assert int(np.sum(evP > 0.5)) == dim
+    evS = _on_divfree(add, S)
+    evA = _on_divfree(add, _dense(add, add.precondition))
+    assert evA[0] > 0 and evA[-1] <= evS[-1] + 1 + 1e-9
+    assert evA[-1] >= max(evS[-1], 1.0) - 1e-9
+    Mm = _dense(mul, mul.precondition)
+    np.testing.assert_allclose(Mm, S + P - P @ A @ S, atol=1e-10 * np.abs(Mm).max())
 
 
 def test_model1_kappa_one_paper_pin():
