@@ -503,38 +503,45 @@ def run_impes(args):
     stream = torch.cuda.current_stream().cuda_stream
     kap = torch.as_tensor(inputs.channel_field(n, 1e5, 77), dtype=torch.float64, device=dev)
     f = torch.as_tensor(inputs.quarter_five_spot(n), dtype=torch.float64, device=dev)
-    # ---- network for the learned rebuild: labels from other channel fields
+    arm_names = args.impes_arms.split(",")
     nc = n // b
     F = 2 * nc * (nc - 1)
-    din, dout, npar = tgms.tg_mlp_shape(b, k, args.hidden)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    X = torch.empty((args.train_fields * F, din), dtype=torch.bfloat16, device=dev)
-    Q = torch.empty((args.train_fields * F, k, b), dtype=torch.float32, device=dev)
-    for i in range(args.train_fields):
-        kt = torch.as_tensor(inputs.channel_field(n, 1e5, 6000 + i), dtype=torch.float64, device=dev)
-        tgms.tg_face_data(kt, n, b, EIG_TOL, k, X[i * F:(i + 1) * F], Q[i * F:(i + 1) * F], stream=stream)
-    params = torch.as_tensor(inputs.mlp_init_params(din, dout, args.hidden, 17), device=dev)
-    net = tgms.Mlp(b, k, args.hidden, params, stream=stream)
-    order = torch.as_tensor(inputs.sample_order(X.shape[0], args.train_steps, 1024, 23), device=dev)
-    loss = torch.zeros(args.train_steps, dtype=torch.float32, device=dev)
-    net.train(X, Q, order, args.train_steps, 1024, 1e-3, loss)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    net, training = None, None
+    if "rebuild_learned" in arm_names:
+        # ---- network for the learned rebuild: labels from other channel fields
+        din, dout, npar = tgms.tg_mlp_shape(b, k, args.hidden)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X = torch.empty((args.train_fields * F, din), dtype=torch.bfloat16, device=dev)
+        Q = torch.empty((args.train_fields * F, k, b), dtype=torch.float32, device=dev)
+        for i in range(args.train_fields):
+            kt = torch.as_tensor(inputs.channel_field(n, 1e5, 6000 + i), dtype=torch.float64, device=dev)
+            tgms.tg_face_data(kt, n, b, EIG_TOL, k, X[i * F:(i + 1) * F], Q[i * F:(i + 1) * F], stream=stream)
+        params = torch.as_tensor(inputs.mlp_init_params(din, dout, args.hidden, 17), device=dev)
+        net = tgms.Mlp(b, k, args.hidden, params, stream=stream)
+        order = torch.as_tensor(inputs.sample_order(X.shape[0], args.train_steps, 1024, 23), device=dev)
+        loss = torch.zeros(args.train_steps, dtype=torch.float32, device=dev)
+        net.train(X, Q, order, args.train_steps, 1024, 1e-3, loss)
+        torch.cuda.synchronize()
+        training = {"fields": args.train_fields, "samples": int(X.shape[0]), "steps": args.train_steps,
+                    "seconds": time.perf_counter() - t0, "loss_last": float(loss[-50:].mean())}
     arms = {}
-    modes = (("frozen", dict(coarse="frozen")), ("frozen_full", dict(coarse="frozen_full")),
-             ("rebuild", dict(coarse="rebuild")),
-             ("rebuild_learned", dict(coarse="rebuild", coarse_space="learned", net=net)))
-    for name, kw in modes:
+    modes = {"frozen": dict(coarse="frozen"), "frozen_full": dict(coarse="frozen_full"),
+             "rebuild": dict(coarse="rebuild"),
+             "rebuild_learned": dict(coarse="rebuild", coarse_space="learned", net=net)}
+    for name in arm_names:
+        kw = modes[name]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, precision=args.precision, flexible=1, **kw)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("impes_steps")
         for _ in range(args.impes_steps):
             sim.step()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         wall = time.perf_counter() - t0
         hist = np.array(sim.history)
         water = float(sim.s.sum()) / n ** 2
@@ -551,17 +558,84 @@ def run_impes(args):
                       "pressure_dof_solves_per_s": dof(n) / (float(hist[:, 3].mean()) / 1e3),
                       "water_volume": water, "s_max": float(sim.s.max())}
         sim.close()
-    net.close()
+    if net is not None:
+        net.close()
+    head = "frozen" if "frozen" in arms else arm_names[0]
     line = {
         "metric": "IMPES steps/s (pressure update + warm-started solve + transport)",
-        "value": arms["frozen"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.impes_steps,
-        "warmup": 0, "ms_per_step": 1e3 / arms["frozen"]["steps_per_s"], "higher_is_better": True,
+        "value": arms[head]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.impes_steps,
+        "warmup": 0, "ms_per_step": 1e3 / arms[head]["steps_per_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
         "config": {"workload": "%dx%d two-phase IMPES, %dx%d-cell blocks, channels 1e5, quarter five-spot, "
                                "mu_w 1, mu_o 5, CFL 0.5, rtol %g" % (n, n, b, b, RTOL)},
-        "arms": arms, "faces": F,
-        "training": {"fields": args.train_fields, "samples": int(X.shape[0]), "steps": args.train_steps,
-                     "seconds": train_s, "loss_last": float(loss[-50:].mean())},
+        "arms": arms, "faces": F, "headline_arm": head, "training": training,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ablations
+def run_ablation(args):
+    """Robustness and parameter study at args.n x args.n with b x b blocks,
+    quarter five-spot, rtol 1e-8, plain FP64 (standard CG, so N_iter and Cond
+    are those of the method itself): (1) N_iter, Cond and Dim against the
+    channel contrast (background 1, channels at 1, 1e2, 1e4, 1e6) for the
+    GMsFEM, MsFEM and RT0 coarse spaces (the paper's Tables 1-6 experiment on
+    synthetic channels); (2) at contrast 1e6 with GMsFEM, the smoother weight
+    eta, the oversampling, the smoothing counts m1/m2 and the additive
+    two-level Schwarz cycle against the two-grid cycle.  Each row times
+    args.steps solves after args.warmup, L2 flushed before each."""
+    import torch
+    from paper_1807_07220_gb300 import inputs, tgms
+    torch.cuda.set_device(0)
+    n, b = args.n, args.b
+    f = inputs.quarter_five_spot(n)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def row(kappa, overlap=2, **opts):
+        kd = torch.as_tensor(kappa, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        s = tgms.Solver(kd, b, EIG_TOL, overlap=overlap, precision="f64", flexible=0, max_iter=4000, **opts)
+        setup_s = time.perf_counter() - t0
+        try:
+            for _ in range(args.warmup):
+                s.solve(f, rtol=RTOL, allow_maxiter=True)
+            times = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
+                it, r = s.solve(f, rtol=RTOL, allow_maxiter=True)
+                e1.record(s.stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        finally:
+            s.close()
+        return {"iters": r.iters, "cond": r.cond_estimate, "dim": r.coarse_dim, "velocity_basis": r.velocity_basis,
+                "ms_per_solve": statistics.mean(times), "setup_s": setup_s, "converged": r.converged}
+
+    contrast = {}
+    for c in (1.0, 1e2, 1e4, 1e6):
+        kappa = inputs.channel_field(n, c, 31)
+        contrast["%g" % c] = {cs: row(kappa, coarse_space=cs) for cs in ("gmsfem", "msfem", "rt0")}
+    kappa = inputs.channel_field(n, 1e6, 31)
+    params = {}
+    for eta in (0.1, 0.2, 0.3, 0.5):
+        params["eta=%g" % eta] = row(kappa, eta=eta)
+    for ov in (1, 2):   # overlap 0 leaves the coarse grid lines in no patch: singular, rejected
+        params["overlap=%d" % ov] = row(kappa, overlap=ov)
+    for m1, m2 in ((1, 0), (1, 1), (2, 1), (2, 2)):
+        params["m1=%d,m2=%d" % (m1, m2)] = row(kappa, m1=m1, m2=m2)
+    params["additive"] = row(kappa, cycle="additive")
+    head = contrast["1e+06"]["gmsfem"]
+    line = {
+        "metric": "PCG iterations to 1e-8 (robustness to contrast; preconditioner ablations)",
+        "value": head["iters"], "unit": "PCG iterations", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_solve"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%dx%d RT0/P0, %dx%d-cell blocks, channel fields (background 1, seed 31), "
+                               "quarter five-spot, eig tol 10, rtol 1e-8, plain FP64" % (n, n, b, b),
+                   "l2": "flushed between solves"},
+        "contrast": contrast, "params_at_1e6": params,
     }
     print(json.dumps(line), flush=True)
 
@@ -665,8 +739,10 @@ def main():
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned", "impes"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned", "impes", "ablation"])
     ap.add_argument("--impes-steps", type=int, default=200)
+    ap.add_argument("--impes-arms", default="frozen,frozen_full,rebuild,rebuild_learned",
+                    help="comma-separated IMPES arms (frozen, frozen_full, rebuild, rebuild_learned)")
     ap.add_argument("--train-fields", type=int, default=25)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--hidden", type=int, default=512)
@@ -690,6 +766,8 @@ def main():
         run_learned(args)
     elif args.workload == "impes":
         run_impes(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     else:
         run_ours(args)
 

@@ -71,6 +71,9 @@ extern "C" {
 #define TG_PTR_HOST   0
 #define TG_PTR_DEVICE 1
 
+#define TG_CYCLE_TWO_GRID 0
+#define TG_CYCLE_ADDITIVE 1
+
 #define TG_COARSE_GMSFEM 0   /* adaptive spectral space, Section 4.2 */
 #define TG_COARSE_MSFEM  1   /* one MsFEM function per coarse face, eq. msfem */
 #define TG_COARSE_RT0    2   /* coarse RT0 space */
@@ -83,7 +86,10 @@ typedef struct tg_mlp tg_mlp;
 typedef struct tg_grid {
   int nx, ny;     /* fine cells per side; this release requires nx == ny */
   int bx, by;     /* fine cells per coarse block side; bx == by, 2 <= b <= 16 */
-  int overlap;    /* oversampling of K_i^+ in fine cells (Section 6: 2), 0..2 */
+  int overlap;    /* oversampling of K_i^+ in fine cells (Section 6: 2), 1..2.  0 is
+                     rejected (TG_ERR_INVALID_ARG): without oversampling the nodes on
+                     the coarse grid lines lie in no patch, and the preconditioner
+                     is singular on the divergence-free space */
 } tg_grid;
 
 typedef struct tg_options {
@@ -125,6 +131,12 @@ typedef struct tg_options {
    * overlap measured slower (+14 % per solve at 256^2, +22 % at 1024^2),
    * the early-launched CTAs competing with the one-wave grids. */
   int launch_overlap;
+  /* TG_CYCLE_TWO_GRID: the two-grid cycle of Section 5 (m1 smoothing steps,
+   * the coarse correction, m2 smoothing steps, the residual recomputed after
+   * each); TG_CYCLE_ADDITIVE: the two-level Schwarz preconditioner
+   * z = S r + P r (eqs. smooth, coarsepre) that Section 5 contrasts with it,
+   * both parts applied to r itself (m1, m2 unused).  Default two-grid. */
+  int cycle;
 } tg_options;
 
 typedef struct tg_report {
@@ -158,7 +170,7 @@ typedef struct tg_report {
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
  * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0, no
  * network or profiles, learned_k 4, learned_max_iter 0, smoother_shape -1,
- * launch_overlap 0. */
+ * launch_overlap 0, cycle TG_CYCLE_TWO_GRID. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything

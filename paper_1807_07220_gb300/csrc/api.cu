@@ -449,7 +449,8 @@ int validate_grid(const tg_grid* g) {
   if (g->nx != g->ny || g->bx != g->by) return TG_ERR_UNSUPPORTED;
   if (g->nx < 2 || g->bx < 2 || g->nx % g->bx != 0) return TG_ERR_INVALID_ARG;
   if (g->bx > kMaxB) return TG_ERR_UNSUPPORTED;
-  if (g->overlap < 0 || g->overlap > kMaxOverlap) return TG_ERR_UNSUPPORTED;
+  if (g->overlap < 1) return TG_ERR_INVALID_ARG;   // singular preconditioner (no patch covers the coarse lines)
+  if (g->overlap > kMaxOverlap) return TG_ERR_UNSUPPORTED;
   if ((long long)g->nx * g->nx > (1LL << 30)) return TG_ERR_UNSUPPORTED;
   return TG_OK;
 }
@@ -529,6 +530,18 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
   TC* rin = (TC*)c->rin;
   const TS* pinv = (const TS*)h->pinv;
   const double eta = h->opt.eta;
+  if (h->opt.cycle == TG_CYCLE_ADDITIVE) {
+    // z = S r + P r: both parts from r
+    prof_mark(c, s);
+    launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s,
+                                    h->shape, h->rscale);
+    prof_mark(c, s);
+    if (h->cs.D > 0) {
+      launch_restrict<double, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, st, s);
+      launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, zacc, st, s);
+    }
+    return;
+  }
   for (int k = 0; k < h->opt.m1; ++k) {
     if (k == 0) {
       prof_mark(c, s);
@@ -633,7 +646,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   const TS* pinv = (const TS*)h->pinv;
   const double eta = h->opt.eta;
   PcgState* st = c->st;
-  if (h->opt.m1 == 1 && h->opt.m2 == 1) {
+  if (h->opt.m1 == 1 && h->opt.m2 == 1 && h->opt.cycle == TG_CYCLE_TWO_GRID) {
     // The cycle of Section 6 (m1 = m2 = 1) in five kernels.  z ends every
     // iteration in zacc (A); zacc2 (B) holds the intermediate z.  The first
     // sweep accumulates into B and clears A (dead once p is formed), the
@@ -664,6 +677,15 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
                                  p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale);
   prof_mark(c, s);
+  if (h->opt.cycle == TG_CYCLE_ADDITIVE) {
+    // z = S r + P r: the coarse part restricts r itself
+    if (h->cs.D > 0) {
+      launch_restrict<double, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, st, s);
+      launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, z_cur, st, s);
+    }
+    launch_pcg_dots<TC>(r_new, z_cur, c->q, c->part, st, n, s);
+    return;
+  }
   for (int k = 1; k < h->opt.m1; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
@@ -1480,6 +1502,7 @@ int tg_default_options(tg_options* opt) {
   opt->learned_max_iter = 0;
   opt->smoother_shape = -1;
   opt->launch_overlap = 0;
+  opt->cycle = TG_CYCLE_TWO_GRID;
   return TG_OK;
 }
 
@@ -1510,7 +1533,8 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
       opt->precision < 0 || opt->precision > 3 || opt->coarse_space < 0 || opt->coarse_space > 3 ||
       !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
     return TG_ERR_INVALID_ARG;
-  if (opt->m1 < 1) return TG_ERR_UNSUPPORTED;
+  if (opt->cycle != TG_CYCLE_TWO_GRID && opt->cycle != TG_CYCLE_ADDITIVE) return TG_ERR_INVALID_ARG;
+  if (opt->cycle == TG_CYCLE_TWO_GRID && opt->m1 < 1) return TG_ERR_UNSUPPORTED;
   if (opt->smoother_shape < -1 || opt->smoother_shape >= kSmootherShapes) return TG_ERR_INVALID_ARG;
   if (opt->coarse_space == TG_COARSE_LEARNED) {
     if (!opt->face_profiles && !opt->net) return TG_ERR_INVALID_ARG;

@@ -1580,6 +1580,10 @@ template void launch_restrict<float, float>(const CoarseSpace&, double*, int, in
                                             const PcgState*, cudaStream_t);
 template void launch_restrict<float, __nv_bfloat16>(const CoarseSpace&, double*, int, int, int, int, const float*,
                                                     const PcgState*, cudaStream_t);
+template void launch_restrict<double, float>(const CoarseSpace&, double*, int, int, int, int, const double*,
+                                             const PcgState*, cudaStream_t);
+template void launch_restrict<double, __nv_bfloat16>(const CoarseSpace&, double*, int, int, int, int, const double*,
+                                                     const PcgState*, cudaStream_t);
 template void launch_prolong<double, double>(const CoarseSpace&, const double*, int, int, int, int, double*,
                                              const PcgState*, cudaStream_t);
 template void launch_prolong<float, float>(const CoarseSpace&, const double*, int, int, int, int, float*,

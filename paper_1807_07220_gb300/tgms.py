@@ -22,6 +22,7 @@ ERRORS = {
 }
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2, "learned": 3}
+CYCLE = {"two_grid": 0, "additive": 1}
 PTR_HOST, PTR_DEVICE = 0, 1
 
 c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -37,7 +38,8 @@ class tg_options(ctypes.Structure):
                 ("flexible", c_int), ("max_iter", c_int), ("pointer_mode", c_int),
                 ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
                 ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
-                ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int)]
+                ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int),
+                ("cycle", c_int)]
 
 
 class tg_report(ctypes.Structure):
@@ -155,6 +157,8 @@ def default_options(**kw):
             v = PREC[v]
         if k == "coarse_space" and isinstance(v, str):
             v = COARSE[v]
+        if k == "cycle" and isinstance(v, str):
+            v = CYCLE[v]
         if k == "net":
             v = getattr(v, "handle", v)
             v = v.value if isinstance(v, ctypes.c_void_p) else v

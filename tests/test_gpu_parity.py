@@ -103,6 +103,69 @@ def test_preconditioner_parts(case, tg, which):
     assert rel(got, ref) < 1e-9, (case["name"], which, rel(got, ref))
 
 
+VARIANTS = {
+    "msfem": dict(coarse_space="msfem"),
+    "rt0": dict(coarse_space="rt0"),
+    "m1_2_m2_1": dict(m1=2, m2=1),
+    "m1_1_m2_0": dict(m1=1, m2=0),
+    "m1_1_m2_2": dict(m1=1, m2=2),
+    "eta_0.3": dict(eta=0.3),
+    "overlap_1": dict(overlap=1),
+    "additive": dict(cycle="additive"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+def test_preconditioner_variants(tg, name):
+    """The comparator coarse spaces (RT0, MsFEM), other smoothing counts,
+    smoother weight and oversampling, and the additive two-level Schwarz
+    cycle against the oracle: the preconditioner applied to one residual,
+    PCG iterations and Cond at rtol 1e-8, and the solution against the direct
+    solve."""
+    n, b = 32, 8
+    kappa = inputs.channel_field(n, 1e4, 3)
+    v = dict(VARIANTS[name])
+    overlap = v.pop("overlap", 2)
+    okw = {("coarse" if k == "coarse_space" else k): val for k, val in v.items()}
+    o = TwoGridSolver(n, b, kappa, tol=10.0, overlap=overlap, **okw)
+    s = tg.Solver(kappa, b, 10.0, overlap=overlap, **v)
+    try:
+        rng = np.random.default_rng(4)
+        r = o.project(rng.standard_normal(o.If.size))
+        z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+        tg.tg_apply_preconditioner(s.h, dev(psi_from_interior(n, o.C.T @ r)), z)
+        got = o.C @ interior_from_psi(n, z.cpu().numpy())
+        assert rel(got, o.precondition(r)) < 1e-9, (name, rel(got, o.precondition(r)))
+        f = inputs.quarter_five_spot(n)
+        it8, rep8 = s.solve(f, rtol=1e-8)
+        ora = o.solve(f, rtol=1e-8)
+        assert abs(it8 - ora["iters"]) <= 1, (name, it8, ora["iters"])
+        assert abs(rep8.cond_estimate / ora["cond"] - 1) < 0.05, (name, rep8.cond_estimate, ora["cond"])
+        u_ref, p_ref = solve_direct(Grid(n, b, overlap), kappa, f)
+        s.solve(f, rtol=1e-12)
+        got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert rel(got_u, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+    finally:
+        s.close()
+
+
+def test_additive_cycle_mixed_precision(tg):
+    """The additive cycle with BF16 and row-scaled FP16 patch inverses
+    (flexible CG) reaches the direct solution."""
+    n, b = 32, 8
+    kappa = inputs.channel_field(n, 1e4, 3)
+    f = inputs.quarter_five_spot(n)
+    u_ref, p_ref = solve_direct(Grid(n, b), kappa, f)
+    for prec in ("bf16", "f16"):
+        s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=1, cycle="additive")
+        try:
+            it, rep = s.solve(f, rtol=1e-12)
+            got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+            assert rep.converged == 1 and rel(got_u, u_ref) < 1e-8, (prec, rel(got_u, u_ref))
+        finally:
+            s.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f16"])
 def test_smoother_tile_shapes(tg, prec):
     """Every smoother tile shape (16- or 8-byte loads, 2 or 4 rows per pass,
@@ -290,6 +353,12 @@ def test_error_codes(tg):
     assert e.value.code == -1
     with pytest.raises(tg.TgmsError) as e:
         tg.Solver(np.ones((18, 18)), 4, 10.0)
+    assert e.value.code == -1
+    with pytest.raises(tg.TgmsError) as e:           # no oversampling: singular preconditioner
+        tg.Solver(kappa, 4, 10.0, overlap=0)
+    assert e.value.code == -1
+    with pytest.raises(tg.TgmsError) as e:
+        tg.Solver(kappa, 4, 10.0, cycle=2)
     assert e.value.code == -1
     s = tg.Solver(kappa, 4, 10.0)
     try:

@@ -312,6 +312,20 @@ def test_cycles_against_operator_algebra():
     np.testing.assert_allclose(Mm, S + P - P @ A @ S, atol=1e-10 * np.abs(Mm).max())
 
 
+def test_no_oversampling_gives_a_singular_preconditioner():
+    """With K_i^+ = K_i (no oversampling) the local zero-flux problems never
+    touch the fine faces on the coarse grid lines, and the coarse space holds
+    only a few functions per coarse face: M A has zero eigenvalues on the
+    divergence-free space (the library rejects overlap 0).  One cell of
+    oversampling removes them."""
+    n, b = 12, 4
+    kappa = lognormal_field(n, 21, sigma=1.5)
+    for ov, singular in ((0, True), (1, False)):
+        s = TwoGridSolver(n, b, kappa, tol=50.0, overlap=ov)
+        ev = _on_divfree(s, _dense(s, s.precondition))
+        assert (abs(ev[0]) < 1e-12 * ev[-1]) == singular, (ov, ev[0])
+
+
 def test_model1_kappa_one_paper_pin():
     """Section 6, Model 1 with k_1 = 1 (kappa == 1 needs no figure): 100 x 100
     fine, 10 x 10 coarse, eta = 0.2, K_i^+ = K_i + 2, m1 = m2 = 1, tolerance 10.
