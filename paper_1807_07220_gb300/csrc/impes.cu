@@ -73,40 +73,59 @@ __global__ void k_transport_outflow(const double* __restrict__ ux, const double*
     last = (atomicAdd(&g_tr_count, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
+  // the last CTA reduces the partial maxima with all its threads
   __threadfence();
   double fmx = 0.0;
-  for (int k = 0; k < (int)gridDim.x; ++k) fmx = fmax(fmx, __ldcg(g_tr_part + k));
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) fmx = fmax(fmx, __ldcg(g_tr_part + k));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmx = fmax(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = fmx;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  fmx = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fmx = fmax(fmx, sh[w]);
   g_tr_count = 0;
   g_tr_dt = (dt_fixed > 0.0) ? dt_fixed : ((fmx > 0.0) ? cfl * h * h / (fmx * sigma) : 0.0);
 }
 
-// s_out = s + dt / h^2 (q+ - sum of upstream-weighted water fluxes out + f_w(s) q-)
-__global__ void k_transport(const double* __restrict__ s, const double* __restrict__ ux,
-                            const double* __restrict__ uy, const double* __restrict__ f, int n, double mw,
-                            double mo, double* __restrict__ s_out) {
+// s_out = s + dt / h^2 (q+ - sum of upstream-weighted water fluxes out + f_w(s) q-).
+// One CTA per kTx x kTy tile of cells: f_w of the tile and its one-cell halo
+// is formed once in shared memory (one division per cell instead of five).
+constexpr int kTx = 32, kTy = 8;
+__global__ void __launch_bounds__(kTx * kTy) k_transport(const double* __restrict__ s, const double* __restrict__ ux,
+                                                        const double* __restrict__ uy, const double* __restrict__ f,
+                                                        int n, double mw, double mo, double* __restrict__ s_out) {
   pdl_entry();
+  __shared__ double fw[kTy + 2][kTx + 2];
   const double h = 1.0 / n, dt = g_tr_dt;
-  const long long nn = (long long)n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)(t / n);
-    const double fc = frac_flow(s[t], mw, mo);
-    const double ul = ux[(long long)j * (n + 1) + i], ur = ux[(long long)j * (n + 1) + i + 1];
-    const double ub = uy[(long long)j * n + i], ut = uy[(long long)(j + 1) * n + i];
-    double upl, upr, upb, upt;   // fraction carried by each face: the cell the flow leaves; water from outside
-    if (i == 0) upl = (ul > 0.0) ? 1.0 : fc;
-    else upl = (ul >= 0.0) ? frac_flow(s[t - 1], mw, mo) : fc;
-    if (i == n - 1) upr = (ur >= 0.0) ? fc : 1.0;
-    else upr = (ur >= 0.0) ? fc : frac_flow(s[t + 1], mw, mo);
-    if (j == 0) upb = (ub > 0.0) ? 1.0 : fc;
-    else upb = (ub >= 0.0) ? frac_flow(s[t - n], mw, mo) : fc;
-    if (j == n - 1) upt = (ut >= 0.0) ? fc : 1.0;
-    else upt = (ut >= 0.0) ? fc : frac_flow(s[t + n], mw, mo);
-    const double net = (ur * h * upr - ul * h * upl) + (ut * h * upt - ub * h * upb);
-    const double qp = h * h * fmax(f[t], 0.0), qm = h * h * fmin(f[t], 0.0);
-    s_out[t] = s[t] + dt / (h * h) * ((qp - net) + fc * qm);
+  const int i0 = blockIdx.x * kTx, j0 = blockIdx.y * kTy;
+  for (int t = threadIdx.x; t < (kTx + 2) * (kTy + 2); t += blockDim.x) {
+    const int a = t % (kTx + 2), c = t / (kTx + 2);
+    const int i = i0 + a - 1, j = j0 + c - 1;
+    fw[c][a] = (i >= 0 && i < n && j >= 0 && j < n) ? frac_flow(s[(long long)j * n + i], mw, mo) : 0.0;
   }
+  __syncthreads();
+  const int a = threadIdx.x % kTx, c = threadIdx.x / kTx;
+  const int i = i0 + a, j = j0 + c;
+  if (i >= n || j >= n) return;
+  const long long t = (long long)j * n + i;
+  const double fc = fw[c + 1][a + 1];
+  const double ul = ux[(long long)j * (n + 1) + i], ur = ux[(long long)j * (n + 1) + i + 1];
+  const double ub = uy[(long long)j * n + i], ut = uy[(long long)(j + 1) * n + i];
+  double upl, upr, upb, upt;   // fraction carried by each face: the cell the flow leaves; water from outside
+  if (i == 0) upl = (ul > 0.0) ? 1.0 : fc;
+  else upl = (ul >= 0.0) ? fw[c + 1][a] : fc;
+  if (i == n - 1) upr = (ur >= 0.0) ? fc : 1.0;
+  else upr = (ur >= 0.0) ? fc : fw[c + 1][a + 2];
+  if (j == 0) upb = (ub > 0.0) ? 1.0 : fc;
+  else upb = (ub >= 0.0) ? fw[c][a + 1] : fc;
+  if (j == n - 1) upt = (ut >= 0.0) ? fc : 1.0;
+  else upt = (ut >= 0.0) ? fc : fw[c + 2][a + 1];
+  const double net = (ur * h * upr - ul * h * upl) + (ut * h * upt - ub * h * upb);
+  const double qp = h * h * fmax(f[t], 0.0), qm = h * h * fmin(f[t], 0.0);
+  s_out[t] = s[t] + dt / (h * h) * ((qp - net) + fc * qm);
 }
 
 int cuda_rc(cudaError_t e) {
@@ -170,7 +189,8 @@ int tg_transport_step(const double* s, const double* ux, const double* uy, const
   }
   const int grid = grid_for_cells(nn);
   launch(k_transport_outflow, dim3(grid), dim3(kTrThreads), 0, st, ux, uy, f, n, cfl, sigma, dt_fixed);
-  launch(k_transport, dim3(grid), dim3(kTrThreads), 0, st, s, ux, uy, f, n, mu_w, mu_o, s_out);
+  launch(k_transport, dim3((n + kTx - 1) / kTx, (n + kTy - 1) / kTy), dim3(kTx * kTy), 0, st, s, ux, uy, f, n, mu_w,
+         mu_o, s_out);
   TG_COUNT(2);
   int rc = TG_OK;
   if (dt) rc = cuda_rc(cudaMemcpyFromSymbolAsync(dt, g_tr_dt, sizeof(double), 0, cudaMemcpyDeviceToHost, st));

@@ -104,43 +104,20 @@ __global__ void k_band_cholesky(double* __restrict__ band, const int4* __restric
   for (int q = threadIdx.x; q < nloc * ldb; q += blockDim.x) B[q] = L[q];
 }
 
-// columns of the inverse from the band factor: thread t solves L L^T x = e_t.
-// CTA (m, y) takes columns c0 .. c0 + blockDim - 1 of matrix m, c0 =
-// y blockDim (further chunks strided by gridDim.y blockDim), so that a few
-// matrices still spread over many SMs.  The rows are swept in the same order
-// by every thread, so the band entries read from shared memory are
-// broadcasts; the reciprocals of the diagonal are formed once; each thread
-// keeps the last w values of its column in a private ring in shared memory
-// (ring[k * blockDim + thread]) and sums the band terms in four partial sums
-// (a short dependent chain: FP64 latency bounds this kernel when it runs on
-// few matrices).  The forward sweep, from row c0 on (y_j = 0 for j < t),
-// leaves y = L^{-1} e_t in scratch; the backward sweep overwrites it with
-// x = L^{-T} y.  scratch (row-major, rows j, columns t)
-// holds nloc x nloc per matrix.
-// sum over d = 1..dmax of c[(d - 1) stride] v_d, v_d the ring entry d slots
-// before pos (ring of rl entries, entry k at my[k T]), in four partial sums
-__device__ __forceinline__ double ring_dot(const double* c, int stride, const double* my, int T, int pos, int rl,
-                                           int dmax) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int q = pos, d = 1;
-  for (; d + 3 <= dmax; d += 4) {
-    const int q1 = (q == 0) ? rl - 1 : q - 1;
-    const int q2 = (q1 == 0) ? rl - 1 : q1 - 1;
-    const int q3 = (q2 == 0) ? rl - 1 : q2 - 1;
-    const int q4 = (q3 == 0) ? rl - 1 : q3 - 1;
-    a0 = fma(c[(d - 1) * stride], my[q1 * T], a0);
-    a1 = fma(c[d * stride], my[q2 * T], a1);
-    a2 = fma(c[(d + 1) * stride], my[q3 * T], a2);
-    a3 = fma(c[(d + 2) * stride], my[q4 * T], a3);
-    q = q4;
-  }
-  for (; d <= dmax; ++d) {
-    q = (q == 0) ? rl - 1 : q - 1;
-    a0 = fma(c[(d - 1) * stride], my[q * T], a0);
-  }
-  return (a0 + a1) + (a2 + a3);
-}
-
+// Entries of the dense inverse from the band factor: thread t solves
+// L L^T x = e_t for column t, and only rows j >= t are formed (the inverse is
+// symmetric: entry (r, c) is read from scratch at row max(r, c), column
+// min(r, c)).  CTA (m, y) takes columns c0 .. c0 + blockDim - 1 of matrix m,
+// c0 = y blockDim (further chunks strided by gridDim.y blockDim), so that a
+// few matrices still spread over many SMs.  Both triangular solves are
+// right-looking: once a value is known its band column is added at once to
+// the pending sums of the next w rows, which a private ring per thread in
+// shared memory holds (ring[k * blockDim + thread]).  The chain of dependent
+// FP64 operations from one row to the next is then a subtraction and a
+// product (FP64 latency bounds this kernel when it runs on few matrices);
+// the w updates per row are independent.  Every thread sweeps the rows in
+// the same order, so band entries read from shared memory are broadcasts.
+// scratch (row-major, rows j, columns t) holds nloc x nloc per matrix.
 __global__ void k_band_inverse(const double* __restrict__ band, const int4* __restrict__ rects,
                                const int* __restrict__ slot, int first, int wmax, int nmax,
                                double* __restrict__ scratch) {
@@ -157,35 +134,46 @@ __global__ void k_band_inverse(const double* __restrict__ band, const int4* __re
   for (int t = threadIdx.x; t < nloc; t += blockDim.x) rd[t] = 1.0 / L[(long long)t * ldb];
   __syncthreads();
   double* X = scratch + (long long)blockIdx.x * nmax * nmax;
-  double* my = ring + threadIdx.x;   // my[k * blockDim]
+  double* my = ring + threadIdx.x;   // my[k * blockDim]: pending sum of the row in ring slot k
   const int T = blockDim.x;
   for (int c0 = blockIdx.y * T; c0 < nloc; c0 += gridDim.y * T) {
     const int t = c0 + threadIdx.x;
     const bool col = (t < nloc);
     for (int q = 0; q < rl; ++q) my[q * T] = 0.0;
-    // forward: y_j = (delta_jt - sum_d L[j][d] y_{j-d}) / L[j][0]
+    // forward, L y = e_t: y_j = (delta_jt - sum_{i<j} L_ji y_i) / L_jj (y_j = 0 for j < t)
     int pos = 0;   // ring slot of row j
     for (int j = c0; j < nloc; ++j) {
-      const double* Lj = L + (long long)j * ldb;
-      double y = 0.0;
-      if (col && j >= t) {
-        const double s4 = ring_dot(Lj + 1, 1, my, T, pos, rl, min(w, j - t));   // L[j][d]
-        y = (((j == t) ? 1.0 : 0.0) - s4) * rd[j];
+      const double y = (col && j >= t) ? (((j == t) ? 1.0 : 0.0) - my[pos * T]) * rd[j] : 0.0;
+      my[pos * T] = 0.0;
+      if (col && j >= t) X[(long long)j * nloc + t] = y;
+      // L_{j+d, j} = L[(j + d) ldb + d]: add y_j's terms to the next rows
+      const int dmax = min(w, nloc - 1 - j);
+      const double* Lc = L + (long long)(j + 1) * ldb + 1;
+      int q = pos;
+      for (int d = 1; d <= dmax; ++d) {
+        q = (q + 1 == rl) ? 0 : q + 1;
+        my[q * T] = fma(Lc[(d - 1) * (ldb + 1)], y, my[q * T]);
       }
-      my[pos * T] = y;
-      if (col) X[(long long)j * nloc + t] = y;
       pos = (pos + 1 == rl) ? 0 : pos + 1;
     }
-    // backward: x_j = (y_j - sum_d L[j+d][d] x_{j+d}) / L[j][0]
-    pos = 0;
-    for (int j = nloc - 1; j >= 0; --j) {
-      if (col) {
-        // band entries L[j + d][d] lie ldb + 1 apart
-        const double s4 = ring_dot(L + (long long)(j + 1) * ldb + 1, ldb + 1, my, T, pos, rl, min(w, nloc - 1 - j));
-        const double yj = (j >= t) ? X[(long long)j * nloc + t] : 0.0;   // y_j = 0 above row t
-        const double x = (yj - s4) * rd[j];
-        my[pos * T] = x;
+    // backward, L^T x = y for rows j >= t: x_j = (y_j - sum_{i>j} L_ij x_i) / L_jj
+    for (int q = 0; q < rl; ++q) my[q * T] = 0.0;
+    pos = 0;       // ring slot of row j, counted from the last row
+    for (int j = nloc - 1; j >= c0; --j) {
+      const bool act = col && j >= t;
+      double x = 0.0;
+      if (act) {
+        x = (X[(long long)j * nloc + t] - my[pos * T]) * rd[j];
         X[(long long)j * nloc + t] = x;
+      }
+      my[pos * T] = 0.0;
+      // L_{j, j-d} = L[j ldb + d]: add x_j's terms to the rows above
+      const int dmax = min(w, j);
+      const double* Lr = L + (long long)j * ldb;
+      int q = pos;
+      for (int d = 1; d <= dmax; ++d) {
+        q = (q + 1 == rl) ? 0 : q + 1;
+        my[q * T] = fma(Lr[d], x, my[q * T]);
       }
       pos = (pos + 1 == rl) ? 0 : pos + 1;
     }
@@ -202,7 +190,8 @@ __global__ void k_store_inverse(const double* __restrict__ scratch, const PatchG
   for (long long t = threadIdx.x + (long long)blockIdx.y * blockDim.x; t < tot;
        t += (long long)blockDim.x * gridDim.y) {
     const int row = (int)(t / g.ld), col = (int)(t % g.ld);
-    const double v = (col < g.nloc) ? X[(long long)row * g.nloc + col] : 0.0;
+    // lower triangle formed (rows >= columns): symmetric read
+    const double v = (col < g.nloc) ? X[(long long)max(row, col) * g.nloc + min(row, col)] : 0.0;
     M[t] = from_d<TS>(v);
   }
 }
@@ -222,17 +211,18 @@ __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const Pa
   __half* M = pinv + g.off;
   const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.y;
   const int warp = (threadIdx.x >> 5) + blockIdx.y * (blockDim.x >> 5);
+  // lower triangle formed (rows >= columns): entry (row, col) read symmetrically
+  auto at = [&](int row, int col) { return X[(long long)max(row, col) * g.nloc + min(row, col)]; };
   for (int row = warp; row < g.nloc; row += nw) {
-    const double* xr = X + (long long)row * g.nloc;
     double mx = 0.0;
-    for (int col = lane; col < g.nloc; col += 32) mx = fmax(mx, fabs(xr[col]));
+    for (int col = lane; col < g.nloc; col += 32) mx = fmax(mx, fabs(at(row, col)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
     const double sc = ldexp(1.0, 15 - e);
     for (int col = lane; col < g.ld; col += 32)
-      M[(long long)row * g.ld + col] = __double2half(col < g.nloc ? xr[col] * sc : 0.0);
+      M[(long long)row * g.ld + col] = __double2half(col < g.nloc ? at(row, col) * sc : 0.0);
     if (lane == 0) rscale[(long long)gofs[p] * kRowsPerGroup + row] = (float)ldexp(1.0, e - 15);
   }
 }
@@ -874,8 +864,14 @@ __global__ void k_build_tiles(const Slot* __restrict__ slots, const double* __re
   }
 }
 
-// energies of all slot pairs of a block: int_K kappa^{-1} (C psi_s).(C psi_t)
-__global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __restrict__ closed,
+// Energies a(phi_sa, phi_sb) restricted to block blk for every pair of the
+// block's slots (closed (b+1)^2 node tiles, stream-function form: per cell
+// the four face fluxes of each function, weighted by kinv, with the exact
+// RT0 cell mass: same-face products / 3 + opposite-face products / 6).
+// One warp per pair, lanes over the cells (fixed shuffle order: the result
+// is the same on every call); pairs spread over gridDim.y CTAs per block;
+// blocks with bmask[blk] == 0 are skipped.
+__global__ void __launch_bounds__(256) k_pair_energy(const int* __restrict__ slot_ptr, const double* __restrict__ closed,
                               const double* __restrict__ kinv, const long long* __restrict__ pair_ptr,
                               const unsigned char* __restrict__ bmask, double* __restrict__ pairE, int n, int b) {
   const int nc = n / b, blk = blockIdx.x, I = blk % nc, J = blk / nc;
@@ -884,14 +880,15 @@ __global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __
   const int nb1 = b + 1, ncl = nb1 * nb1;
   double* E = pairE + pair_ptr[blk];
   const int npair = m * (m + 1) / 2;
-  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = blockIdx.y * nw + warp; t < npair; t += gridDim.y * nw) {
     int sa = 0, rem = t;
     while (rem >= m - sa) { rem -= m - sa; ++sa; }
     const int sb = sa + rem;
     const double* Pa = closed + (long long)(s0 + sa) * ncl;
     const double* Pb = closed + (long long)(s0 + sb) * ncl;
     double e = 0.0;
-    for (int cell = 0; cell < b * b; ++cell) {
+    for (int cell = lane; cell < b * b; cell += 32) {
       const int a = cell % b, c = cell / b;
       const int n00 = c * nb1 + a, n10 = n00 + 1, n01 = n00 + nb1, n11 = n01 + 1;
       const double aL = Pa[n01] - Pa[n00], aR = Pa[n11] - Pa[n10];
@@ -902,9 +899,13 @@ __global__ void k_pair_energy(const int* __restrict__ slot_ptr, const double* __
       // (same-face products) / 3 + (opposite-face products) / 6, times 6
       e += k * (2.0 * (aL * bL + aR * bR + aB * bB + aT * bT) + (aL * bR + aR * bL + aB * bT + aT * bB));
     }
-    e /= 6.0;
-    E[sa * m + sb] = e;
-    E[sb * m + sa] = e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) {
+      e /= 6.0;
+      E[sa * m + sb] = e;
+      E[sb * m + sa] = e;
+    }
   }
 }
 
@@ -1200,7 +1201,10 @@ template void launch_build_tiles<__nv_bfloat16>(const CoarseSpace&, const double
 void launch_galerkin(const CoarseSpace& cs, const double* kinv, int nblocks, int n, int b, double* pairE,
                      const long long* pair_ptr, double* K, cudaStream_t s, const unsigned char* bmask) {
   if (cs.D == 0) return;
-  k_pair_energy<<<nblocks, 128, 0, s>>>(cs.slot_ptr, cs.closed, kinv, pair_ptr, bmask, pairE, n, b);
+  // one warp per pair of slots: enough CTAs per block for its pairs
+  const int mx = std::max(1, cs.max_slots_per_block), pairs = mx * (mx + 1) / 2;
+  const int ysplit = std::max(1, std::min(64, (pairs + 7) / 8));
+  k_pair_energy<<<dim3(nblocks, ysplit), 256, 0, s>>>(cs.slot_ptr, cs.closed, kinv, pair_ptr, bmask, pairE, n, b);
   cudaMemsetAsync(K, 0, sizeof(double) * (size_t)cs.D * cs.D, s);
   k_assemble_coarse<<<(cs.D + 127) / 128, 128, 0, s>>>(cs.slot_ptr, cs.slots, cs.gather, pair_ptr, pairE, bmask,
                                                         K, cs.D);
