@@ -39,10 +39,11 @@ sys.path.insert(0, ROOT)
 METRIC = "fine DOF-solves/s to 1e-8 rel. residual vs plain FP64; PCG iters; HBM %"
 N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
 # DRAM bytes (read + write) per smoother launch at the default workload, mean of
-# the fused and plain sweeps, from the ncu capture summarised in
+# the two sweeps of an iteration (r - alpha q and r - K z formed at gather time),
+# from the ncu capture summarised in
 # profiles/k_smoother_256x256.md, keyed by (storage precision, tile shape);
 # valid only for the kernel version and shape profiled there
-SMOOTHER_TRAFFIC = {("f32", 0): 134.42e6, ("bf16", 0): 66.24e6, ("bf16", 2): 66.10e6}
+SMOOTHER_TRAFFIC = {("bf16", 2): 67.18e6}
 
 
 def dof(n):

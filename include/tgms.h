@@ -243,6 +243,18 @@ void tg_destroy(tg_handle* h);
 /* Static message for an error code. */
 const char* tg_strerror(int code);
 
+/* Failure detection (no counterpart in the paper).  Every wait of a kernel of
+ * this library on device-side state (the TMA smoother's mbarriers) is bounded;
+ * when a bound expires the kernel raises a device flag, drains its own copies
+ * (bounded again) and returns, and the call returns TG_ERR_DEVICE_TIMEOUT with
+ * the context still usable.  This probe exercises that path without a fault:
+ * one warp waits, for at most 2^limit_log2 polls (0 <= limit_log2 <= 22), on
+ * an mbarrier in shared memory that it completes itself first (complete != 0:
+ * returns TG_OK) or that nothing completes (complete == 0: the bound expires,
+ * returns TG_ERR_DEVICE_TIMEOUT).  stream: cudaStream_t; synchronises it.
+ * Shares the flag with running solves: call it with no solve in flight. */
+int tg_probe_bounded_wait(int complete, int limit_log2, void* stream);
+
 /* ---- operator-level entry points (device pointers, psi vectors) ----------
  * These expose single steps of the PCG iteration for verification; they run
  * exactly the kernels tg_solve runs. */

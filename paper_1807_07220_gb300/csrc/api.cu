@@ -1506,6 +1506,17 @@ int tg_default_options(tg_options* opt) {
   return TG_OK;
 }
 
+int tg_probe_bounded_wait(int complete, int limit_log2, void* stream) {
+  if (limit_log2 < 0 || limit_log2 > 22) return TG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  read_and_clear_timeout();   // start from a clear flag
+  launch_wait_probe(complete, limit_log2, s);
+  int rc = cuda_err(cudaStreamSynchronize(s));
+  if (!rc) rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  return read_and_clear_timeout() ? TG_ERR_DEVICE_TIMEOUT : TG_OK;
+}
+
 const char* tg_strerror(int code) {
   switch (code) {
     case TG_OK: return "success";

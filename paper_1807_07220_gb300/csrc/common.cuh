@@ -202,6 +202,9 @@ void launch_copy_table(const double* const* src, double* const* dst, const long 
 void launch_fill_scalars(const double* v, double* const* dst, int m, cudaStream_t s);
 void launch_gather_states(PcgState* const* st, int* out, int m, cudaStream_t s);
 int read_and_clear_timeout();   // 1 if a bounded device wait expired since the last call
+// one warp waits (at most 2^limit_log2 polls) on an mbarrier it completes
+// first (complete != 0) or that nothing completes (the wait expires)
+void launch_wait_probe(int complete, int limit_log2, cudaStream_t s);
 void launch_pcg_reset(PcgState* st, const double* rtol, int maxit, int flexible, cudaStream_t s);
 // warm start: r = rho - K x, rr = |r|^2, rr0 = |rho|^2 (stopping reference)
 void launch_pcg_init_warm(const double* x, const double* rho, const double* kinv, double* r, double* part,

@@ -801,6 +801,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// Failure-detection probe: one warp waits, bounded by 2^limit_log2 polls, on
+// an mbarrier that it completes first (complete != 0) or that nothing ever
+// completes; an expired wait raises g_timeout_flag exactly as the smoother's
+// waits do.
+__global__ void k_wait_probe(int complete, long long limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned b = smem_addr(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  if (threadIdx.x == 0 && complete)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+  __syncwarp();
+  bool ok = false;
+  for (long long i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(b, 0);
+  if (!ok && threadIdx.x == 0) atomicOr(&g_timeout_flag, 1);
+}
+
 __device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
@@ -1486,6 +1504,10 @@ void launch_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, i
 }
 int sm_count();
 template <typename TC, typename TS, typename TR, int kFused> void smoother_prepare();
+void launch_wait_probe(int complete, int limit_log2, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(complete, 1LL << limit_log2);
+}
+
 int read_and_clear_timeout() {
   int v = 0;
   cudaMemcpyFromSymbol(&v, g_timeout_flag, sizeof(int));

@@ -88,6 +88,7 @@ SIGNATURES = {
     "tg_solve_warm": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_int_p, ctypes.POINTER(tg_report)]),
     "tg_strerror": (ctypes.c_char_p, [c_int]),
+    "tg_probe_bounded_wait": (c_int, [c_int, c_int, c_void_p]),
     "tg_apply_operator": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "tg_apply_smoother": (c_int, [c_void_p, c_void_p, c_void_p]),
     "tg_apply_coarse": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -220,6 +221,11 @@ def tg_transport_step(s, ux, uy, f, n, cfl, mu_w, mu_o, s_out, dt_fixed=0.0, str
 def tg_destroy(h):
     if h is not None:
         lib().tg_destroy(h)
+
+
+def tg_probe_bounded_wait(complete, limit_log2, stream=0):
+    """TG_OK (0) or TG_ERR_DEVICE_TIMEOUT (-5): see include/tgms.h."""
+    return lib().tg_probe_bounded_wait(int(complete), int(limit_log2), ctypes.c_void_p(stream))
 
 
 def tg_strerror(code):

@@ -373,6 +373,23 @@ def test_error_codes(tg):
         s.close()
 
 
+def test_bounded_wait_expires_and_context_survives(tg):
+    """Failure detection without a fault: a bounded device wait on an
+    mbarrier that nothing completes returns TG_ERR_DEVICE_TIMEOUT; one that
+    completes returns TG_OK; a solve afterwards still works."""
+    stream = torch.cuda.current_stream().cuda_stream
+    assert tg.tg_probe_bounded_wait(0, 12, stream) == -5
+    assert tg.tg_probe_bounded_wait(1, 12, stream) == 0
+    assert tg.tg_probe_bounded_wait(0, 12, stream) == -5
+    n = 16
+    s = tg.Solver(np.ones((n, n)), 4, 10.0)
+    try:
+        it, rep = s.solve(inputs.quarter_five_spot(n), rtol=1e-8)
+        assert rep.converged == 1
+    finally:
+        s.close()
+
+
 def test_host_pointer_mode(tg):
     n, b = 16, 4
     kappa = inputs.lognormal_field(n, 2)
