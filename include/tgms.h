@@ -137,6 +137,13 @@ typedef struct tg_options {
    * z = S r + P r (eqs. smooth, coarsepre) that Section 5 contrasts with it,
    * both parts applied to r itself (m1, m2 unused).  Default two-grid. */
   int cycle;
+  /* tg_setup_batch only: 1 (default) = the right-hand sides of an instance
+   * advance in lock step, in groups of up to 4 that share every read of the
+   * patch inverses in the two smoothing sweeps (each chain keeps its own PCG
+   * scalars and stops on its own; iteration counts are those of separate
+   * solves); used with m1 = m2 = 1 and the two-grid cycle.  0 = every
+   * right-hand side an independent chain. */
+  int batch_lockstep;
 } tg_options;
 
 typedef struct tg_report {
@@ -170,7 +177,7 @@ typedef struct tg_report {
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
  * standard CG, max_iter 1000, TG_PTR_DEVICE, GMsFEM, no cap, profile 0, no
  * network or profiles, learned_k 4, learned_max_iter 0, smoother_shape -1,
- * launch_overlap 0, cycle TG_CYCLE_TWO_GRID. */
+ * launch_overlap 0, cycle TG_CYCLE_TWO_GRID, batch_lockstep 1. */
 int tg_default_options(tg_options* opt);
 
 /* Step 2 of Section 5 (and the setup half of Section 3): builds everything

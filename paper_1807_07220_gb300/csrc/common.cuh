@@ -202,6 +202,36 @@ void launch_copy_table(const double* const* src, double* const* dst, const long 
 void launch_fill_scalars(const double* v, double* const* dst, int m, cudaStream_t s);
 void launch_gather_states(PcgState* const* st, int* out, int m, cudaStream_t s);
 int read_and_clear_timeout();   // 1 if a bounded device wait expired since the last call
+// Lock-step groups of right-hand sides (batched solves): up to kGroup PCG
+// chains of one instance share each read of the patch inverses.  Per chain:
+// mode 1 (first sweep) reads r_old, q, x, p, part, st, zclear and writes into
+// zacc; mode 2 (last sweep) reads r, zin, kin, st and writes into zacc.
+constexpr int kGroup = 4;
+struct ChainPtrs {
+  const double* r_old;
+  double* r_new;
+  const double* q;
+  double* x;
+  const double* p;
+  double* part;
+  PcgState* st;
+  void* zclear;
+  const void* zin;
+  const void* kin;
+  const double* r;
+  void* zacc;
+};
+struct StateSet {
+  const PcgState* st[kGroup];
+  int k;
+};
+template <typename TC, typename TS>
+void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                           const ChainPtrs* chains, int k, double eta, int n, int nc, int b, cudaStream_t s, int shape,
+                           const float* rscale);
+// graph loop condition: 1 while any of the k chains is not done
+void launch_set_condition_any(cudaGraphConditionalHandle cond, const PcgState* const* st, int k, cudaStream_t s);
+
 // one warp waits (at most 2^limit_log2 polls) on an mbarrier it completes
 // first (complete != 0) or that nothing completes (the wait expires)
 void launch_wait_probe(int complete, int limit_log2, cudaStream_t s);

@@ -605,6 +605,18 @@ struct FuseArgs {
   const void* kin;      // mode 2: inverse permeabilities (TC)
 };
 
+// the chains of a lock-step group (k_smoother_multi): per chain the vector
+// gathered (mode 2: r; mode 1 reads fa.r_old), the output z, the PCG state
+// and the fused-update arguments; slots k .. kGroup-1 are absent
+template <typename TC>
+struct ChainSet {
+  const double* r[kGroup];
+  TC* zacc[kGroup];
+  const PcgState* st[kGroup];
+  FuseArgs fa[kGroup];
+  int k;
+};
+
 // kFused: 0 plain sweep z += eta S r; 1 first sweep of an iteration (r - alpha q
 // formed at gather time, r, x updated and (r, r) reduced by the block
 // owners); 2 last sweep with the residual formed at gather time,
@@ -763,6 +775,165 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
           S->done = 1;
         }
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lock-step variant for several right-hand sides of one instance: one read of
+// every patch inverse serves up to kGroup PCG chains that run the same
+// five-kernel iteration (each chain its own vectors, scalars and state).
+// Each chain's rows are reduced exactly as k_smoother reduces them (same
+// lanes, same order), so a chain's results do not depend on its group.
+// Chains whose PCG has finished (or that are absent, slot >= k) are skipped.
+template <typename TC, typename TS, int kFused, int kCB, int kR>
+__global__ void __launch_bounds__(kThreads) k_smoother_multi(const PatchGeo* __restrict__ geo,
+                                                             const int* __restrict__ gofs, int npatch,
+                                                             const TS* __restrict__ pinv, TC eta, int n,
+                                                             ChainSet<TC> cs, const float* __restrict__ rscale) {
+  pdl_entry();
+  __shared__ __align__(16) TC xs[kGroup][kPatchLd];
+  __shared__ double shr[32];
+  bool act[kGroup];
+  int any = 0;
+#pragma unroll
+  for (int c = 0; c < kGroup; ++c) {
+    act[c] = (c < cs.k) && !cs.st[c]->done;
+    any |= act[c];
+  }
+  if (!any) return;
+  double alpha[kGroup], rr[kGroup];
+#pragma unroll
+  for (int c = 0; c < kGroup; ++c) {
+    alpha[c] = (kFused == 1 && act[c]) ? cs.fa[c].st->alpha : 0.0;
+    rr[c] = 0.0;
+  }
+  const int G = gofs[npatch];
+  const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
+  const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
+  __shared__ int sp;
+  if (threadIdx.x == 0) sp = npatch - 1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < npatch; t += blockDim.x)
+    if (gofs[t] <= g0 && gofs[t + 1] > g0) sp = t;
+  __syncthreads();
+  int p = sp;
+  constexpr int W = kCB / (int)sizeof(TS);
+  constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
+    const PatchGeo g = geo[p];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kGroup; ++c) {
+      if (!act[c]) continue;
+      const FuseArgs& fa = cs.fa[c];
+      for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
+        TC v = (TC)0;
+        if (q < g.nloc) {
+          const int a = q % g.nx, cc = q / g.nx;
+          const long long id = (long long)(g.y0 + 1 + cc) * n + (g.x0 + 1 + a);
+          if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha[c] * fa.q[id]);
+          else if constexpr (kFused == 2)
+            v = (TC)cs.r[c][id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
+                                                            g.y0 + 1 + cc);
+          else v = (TC)cs.r[c][id];
+        }
+        xs[c][q] = v;
+      }
+      if (kFused == 1 && gofs[p] >= g0) {   // this CTA owns block p
+        const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+        for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+          const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+          const double rv = fa.r_old[id] - alpha[c] * fa.q[id];
+          fa.r_new[id] = rv;
+          fa.x[id] += alpha[c] * fa.p[id];
+          rr[c] += rv * rv;
+          if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
+        }
+      }
+      if (kFused == 2 && gofs[p] >= g0) {   // the owner seeds the output with z_in
+        const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+        for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+          const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+          atomicAdd(cs.zacc[c] + id, ((const TC*)fa.zin)[id]);
+        }
+      }
+    }
+    __syncthreads();
+    const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
+    const TS* M = pinv + g.off;
+    constexpr int R = kR;
+    constexpr int P = kRowsPerWarp / R;
+    using V = typename LdChunk<TS, kCB>::T;
+    for (int grp = ga + warp; grp < gb; grp += nw) {
+#pragma unroll
+      for (int pass = 0; pass < P; ++pass) {
+        const int row0 = grp * kRowsPerWarp + pass * R;
+        V buf[R][kIter];
+#pragma unroll
+        for (int it = 0; it < kIter; ++it) {
+          const int col = (it * 32 + lane) * W;
+#pragma unroll
+          for (int k = 0; k < R; ++k) {
+            if (col < g.ld && row0 + k < g.nloc) buf[k][it] = load_tile<TS, kCB>(M + (long long)(row0 + k) * g.ld + col);
+            else buf[k][it] = V{};
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kGroup; ++c) {
+          if (!act[c]) continue;
+          TC acc[R];
+#pragma unroll
+          for (int k = 0; k < R; ++k) acc[k] = (TC)0;
+#pragma unroll
+          for (int it = 0; it < kIter; ++it) {
+            const int col = (it * 32 + lane) * W;
+            if (col < g.ld) {
+#pragma unroll
+              for (int k = 0; k < R; ++k) acc[k] += dot_tile<TS, TC>(buf[k][it], &xs[c][col]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < R; ++k) acc[k] = warp_sum(acc[k]);
+          if (lane < R && row0 + lane < g.nloc) {
+            TC v = acc[0];
+#pragma unroll
+            for (int k = 1; k < R; ++k)
+              if (lane == k) v = acc[k];
+            const int q = row0 + lane, a = q % g.nx, cc = q / g.nx;
+            if constexpr (std::is_same<TS, __half>::value) v *= (TC)rscale[(long long)gofs[p] * kRowsPerWarp + q];
+            atomicAdd(cs.zacc[c] + (long long)(g.y0 + 1 + cc) * n + (g.x0 + 1 + a), eta * v);
+          }
+        }
+      }
+    }
+  }
+  if (kFused == 1) {
+#pragma unroll
+    for (int c = 0; c < kGroup; ++c) {
+      if (!act[c]) continue;
+      const FuseArgs& fa = cs.fa[c];
+      const double tot_cta = block_sum(rr[c], shr);
+      if (arrive_last(tot_cta, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
+        const double tot = sum_partials(fa.part, gridDim.x);
+        if (threadIdx.x == 0) {
+          PcgState* S = fa.st;
+          S->counter[1] = 0;
+          S->rr = tot;
+          S->iter += 1;
+          if (tot <= S->rtol2 * S->rr0) {
+            S->done = 1;
+          } else if (!isfinite(tot)) {
+            S->status |= kStBreakdown;
+            S->done = 1;
+          } else if (S->iter >= S->maxit) {
+            S->status |= kStMaxIter;
+            S->done = 1;
+          }
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -1425,6 +1596,90 @@ void launch_smoother_resid(const PatchGeo* geo, const int* gofs, int npatch, int
   FuseArgs fa{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nc, b, nullptr, zin, kin};
   smoother_shape<TC, TS, double, 2>(shape, geo, gofs, npatch, ngroups, pinv, r, zout, eta, n, st, fa, rscale, s);
 }
+template <typename TC, typename TS, int kFused, int kCB, int kR>
+int smoother_multi_per_sm() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother_multi<TC, TS, kFused, kCB, kR>, kThreads, 0);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  return per_sm;
+}
+
+template <typename TC, typename TS, int kFused, int kCB, int kR>
+void smoother_multi_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, double eta,
+                       int n, const ChainSet<TC>& cs, const float* rscale, cudaStream_t s) {
+  const int grid = wave_grid(smoother_multi_per_sm<TC, TS, kFused, kCB, kR>(), ngroups);
+  launch(k_smoother_multi<TC, TS, kFused, kCB, kR>, dim3(grid), dim3(kThreads), 0, s, geo, gofs, npatch, pinv,
+         (TC)eta, n, cs, rscale);
+}
+
+// tile shapes of the lock-step sweep: the non-pipelined register shapes
+// (TMA and pipelined shapes map to 0, 3 and 1 as in the single-chain sweep's
+// families; FP64 storage uses 16-byte loads, 2 rows)
+template <typename TC, typename TS, int kFused>
+void smoother_multi_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                          double eta, int n, const ChainSet<TC>& cs, const float* rscale, cudaStream_t s) {
+  TG_COUNT(1);
+  if constexpr (std::is_same<TS, double>::value) {
+    smoother_multi_go<TC, TS, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s);
+  } else {
+    switch (shape) {
+      case 1: case 6: smoother_multi_go<TC, TS, kFused, 16, 2>(geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s); break;
+      case 2: smoother_multi_go<TC, TS, kFused, 8, 4>(geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s); break;
+      case 3: case 5: smoother_multi_go<TC, TS, kFused, 8, 2>(geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s); break;
+      default: smoother_multi_go<TC, TS, kFused, 16, 4>(geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s); break;
+    }
+  }
+}
+
+template <typename TC, typename TS>
+void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
+                           const ChainPtrs* chains, int k, double eta, int n, int nc, int b, cudaStream_t s, int shape,
+                           const float* rscale) {
+  ChainSet<TC> cs{};
+  cs.k = k;
+  for (int c = 0; c < kGroup; ++c) {
+    const ChainPtrs& q = chains[c < k ? c : 0];   // absent slots repeat chain 0's pointers (never used)
+    cs.r[c] = q.r;
+    cs.zacc[c] = (TC*)q.zacc;
+    cs.st[c] = q.st;
+    cs.fa[c] = FuseArgs{q.r_old, q.r_new, q.q, q.x, q.p, q.part, q.st, nc, b, q.zclear, q.zin, q.kin};
+  }
+  if (mode == 1)
+    smoother_multi_shape<TC, TS, 1>(shape, geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s);
+  else
+    smoother_multi_shape<TC, TS, 2>(shape, geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s);
+}
+template void launch_smoother_multi<double, double>(int, const PatchGeo*, const int*, int, int, const double*,
+                                                    const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
+                                                    const float*);
+template void launch_smoother_multi<float, float>(int, const PatchGeo*, const int*, int, int, const float*,
+                                                  const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
+                                                  const float*);
+template void launch_smoother_multi<float, __nv_bfloat16>(int, const PatchGeo*, const int*, int, int,
+                                                          const __nv_bfloat16*, const ChainPtrs*, int, double, int,
+                                                          int, int, cudaStream_t, int, const float*);
+template void launch_smoother_multi<float, __half>(int, const PatchGeo*, const int*, int, int, const __half*,
+                                                   const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
+                                                   const float*);
+
+// set the graph's loop condition: continue while any chain of a group runs
+__global__ void k_set_condition_any(cudaGraphConditionalHandle cond, StateSet ss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned go = 0u;
+    for (int c = 0; c < ss.k; ++c) go |= ss.st[c]->done ? 0u : 1u;
+    cudaGraphSetConditional(cond, go);
+  }
+}
+void launch_set_condition_any(cudaGraphConditionalHandle cond, const PcgState* const* st, int k, cudaStream_t s) {
+  StateSet ss{};
+  ss.k = k;
+  for (int c = 0; c < k && c < kGroup; ++c) ss.st[c] = st[c];
+  TG_COUNT(1);
+  launch(k_set_condition_any, dim3(1), dim3(32), 0, s, cond, ss);
+}
+
 template void launch_smoother_resid<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                     const double*, const double*, const double*, double*, double,
                                                     int, int, int, const PcgState*, cudaStream_t, int, const float*);

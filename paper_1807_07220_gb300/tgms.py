@@ -39,7 +39,7 @@ class tg_options(ctypes.Structure):
                 ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
                 ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
                 ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int),
-                ("cycle", c_int)]
+                ("cycle", c_int), ("batch_lockstep", c_int)]
 
 
 class tg_report(ctypes.Structure):

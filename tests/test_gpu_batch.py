@@ -70,3 +70,46 @@ def test_batch_matches_direct_and_single_solves(tg, prec):
                 s.close()
     finally:
         tg.tg_destroy_batch(batch)
+
+
+def _run_batch(tg, kd, specs, fs, nrhs, prec, lockstep, rtol):
+    dev = "cuda"
+    opts = tg.default_options(precision=prec, flexible=int(prec != "f64"), batch_lockstep=lockstep)
+    stream = torch.cuda.current_stream().cuda_stream
+    batch = tg.tg_setup_batch(kd, [s[0] for s in specs], [s[1] for s in specs], 10.0, nrhs, options=opts,
+                              stream=stream)
+    try:
+        outs = [(torch.zeros(n, n + 1, dtype=torch.float64, device=dev),
+                 torch.zeros(n + 1, n, dtype=torch.float64, device=dev),
+                 torch.zeros(n, n, dtype=torch.float64, device=dev)) for (n, b, c, seed) in specs for _ in range(nrhs)]
+        fd = [torch.as_tensor(f, dtype=torch.float64, device=dev).contiguous() for f in fs]
+        iters, status = tg.tg_solve_batch(batch, fd, None, rtol, [o[0] for o in outs], [o[1] for o in outs],
+                                          [o[2] for o in outs])
+        assert (status == 0).all()
+        return iters, [np.concatenate([o[0].cpu().numpy().ravel(), o[1].cpu().numpy().ravel()]) for o in outs]
+    finally:
+        tg.tg_destroy_batch(batch)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_lockstep_groups_match_independent_chains(tg, prec):
+    """Right-hand sides of an instance in lock step (groups of up to 4 sharing
+    the smoother sweeps; 5 per instance makes a group of 4 and a lone chain)
+    give the iteration counts and solutions of independent chains, and the
+    direct solution; their different source pairs make the chains of a group
+    stop at different iterations."""
+    specs = [(32, 8, 1e4, 1), (48, 16, 1e5, 3)]
+    nrhs = 5
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device="cuda").contiguous() for k in kappas]
+    fs = [inputs.random_pairs(n, 1 + r % 3, 50 * seed + r) for (n, b, c, seed) in specs for r in range(nrhs)]
+    it_l, u_l = _run_batch(tg, kd, specs, fs, nrhs, prec, 1, 1e-12)
+    it_i, u_i = _run_batch(tg, kd, specs, fs, nrhs, prec, 0, 1e-12)
+    assert len(set(it_l.tolist())) > 1                 # the chains stop at different iterations
+    assert np.abs(it_l - it_i).max() <= 1, (it_l, it_i)
+    j = 0
+    for (n, b, c, seed), k in zip(specs, kappas):
+        for r in range(nrhs):
+            u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
+            assert rel(u_l[j], u_ref) < 1e-8 and rel(u_i[j], u_ref) < 1e-8, (j, rel(u_l[j], u_ref))
+            j += 1
