@@ -414,6 +414,7 @@ void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t 
 // non-positive pivot; FP64 GEMM C = alpha op(A) op(B) + beta C with element
 // strides (op(A)(i,k) = A[i*ars + k*acs]); (A + A^T)/2; y += x
 constexpr int kGjSmallMax = 1024;
+constexpr int kGjBlock = 64;       // pivots per block of the blocked Gauss-Jordan inverse
 void launch_kinv_delta(const double* kappa, const double* kinv_old, double* delta, int n, cudaStream_t s);
 void launch_row_nonzero(const double* K, int D, unsigned char* flag, cudaStream_t s);
 void launch_gather_cols(const double* K, int D, const int* S, int s_cnt, int rows, bool rows_all, double* out,

@@ -1072,6 +1072,46 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int kdim, double al
     }
 }
 
+// in-place Gauss-Jordan inverse of the kb x kb SPD diagonal block at A
+// (leading dimension lda) by one CTA; a non-positive pivot raises status
+__global__ void k_gj_block(double* __restrict__ A, long long lda, int kb, int* status) {
+  __shared__ double rowk[kGjBlock], colk[kGjBlock];
+  const int tot = kb * kb;
+  for (int k = 0; k < kb; ++k) {
+    for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+      rowk[j] = A[(long long)k * lda + j];
+      colk[j] = A[(long long)j * lda + k];
+    }
+    __syncthreads();
+    double p = rowk[k];
+    if (!(p > 0.0) || !isfinite(p)) {
+      if (threadIdx.x == 0) atomicOr(status, kStNotSpd);
+      p = 1.0;
+    }
+    const double ip = 1.0 / p;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int i = t / kb, j = t % kb;
+      double* a = A + (long long)i * lda + j;
+      if (i == k && j == k) *a = ip;
+      else if (i == k) *a = rowk[j] * ip;
+      else if (j == k) *a = -colk[i] * ip;
+      else *a = *a - colk[i] * rowk[j] * ip;
+    }
+    __syncthreads();
+  }
+}
+
+// dst (rows x cols, leading dimension ldd) = src (leading dimension lds)
+__global__ void k_copy2d(double* __restrict__ dst, long long ldd, const double* __restrict__ src, long long lds,
+                         int rows, int cols) {
+  const long long tot = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / cols), j = (int)(t % cols);
+    dst[(long long)i * ldd + j] = src[(long long)i * lds + j];
+  }
+}
+
 // A (s x s) = (A + A^T) / 2, one thread per pair i < j
 __global__ void k_symmetrize(double* __restrict__ A, int s) {
   const long long tot = (long long)s * s;
@@ -1246,15 +1286,41 @@ void launch_add(double* y, const double* x, long long cnt, cudaStream_t s) {
   if (cnt == 0) return;
   k_add<<<grid_of(cnt, 256, 4096), 256, 0, s>>>(y, x, cnt);
 }
+// Inverse of an SPD D x D matrix in place.  Small matrices: D pivot steps of
+// k_gj_step (ping-pong with B).  Larger ones: Gauss-Jordan by blocks of kb =
+// kGjBlock pivots, so that the bulk of the work is one rank-kb update of the
+// whole matrix per block (a GEMM) instead of D passes over it.  With P the
+// inverse of the pivot block, C = A[:, blk] and R = P A[blk, :] (taken before
+// the update):  A -= C R;  A[:, blk] = -C P;  A[blk, :] = R;  A[blk, blk] = P,
+// which is the scalar step of k_gj_step applied to kb pivots at once.  B holds
+// P, C and R (kb (kb + 2 D) doubles <= D^2).
 void launch_gauss_jordan(double* A, double* B, int D, int* status, cudaStream_t s) {
-  long long m = (long long)D * D;
-  int g = (int)((m + 255) / 256);
-  if (g > 2048) g = 2048;
-  for (int k = 0; k < D; ++k) {
-    if (k % 2 == 0) k_gj_step<<<g, 256, 0, s>>>(A, B, D, k, status);
-    else k_gj_step<<<g, 256, 0, s>>>(B, A, D, k, status);
+  const long long m = (long long)D * D;
+  if (D < 3 * kGjBlock) {
+    int g = (int)((m + 255) / 256);
+    if (g > 2048) g = 2048;
+    for (int k = 0; k < D; ++k) {
+      if (k % 2 == 0) k_gj_step<<<g, 256, 0, s>>>(A, B, D, k, status);
+      else k_gj_step<<<g, 256, 0, s>>>(B, A, D, k, status);
+    }
+    if (D % 2 == 1) cudaMemcpyAsync(A, B, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s);
+    return;
   }
-  if (D % 2 == 1) cudaMemcpyAsync(A, B, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s);
+  double* P = B;
+  double* C = B + (long long)kGjBlock * kGjBlock;
+  double* R = C + (long long)D * kGjBlock;
+  for (int k0 = 0; k0 < D; k0 += kGjBlock) {
+    const int kb = std::min(kGjBlock, D - k0);
+    double* Akk = A + (long long)k0 * D + k0;
+    k_gj_block<<<1, 1024, 0, s>>>(Akk, D, kb, status);                                   // P in place
+    k_copy2d<<<grid_of((long long)kb * kb, 256, 64), 256, 0, s>>>(P, kb, Akk, D, kb, kb);
+    k_copy2d<<<grid_of((long long)D * kb, 256, 2048), 256, 0, s>>>(C, kb, A + k0, D, D, kb);   // C = A[:, blk]
+    launch_dgemm(kb, D, kb, 1.0, P, kb, 1, A + (long long)k0 * D, D, 1, 0.0, R, D, s);    // R = P A[blk, :]
+    launch_dgemm(D, D, kb, -1.0, C, kb, 1, R, D, 1, 1.0, A, D, s);                       // A -= C R
+    launch_dgemm(D, kb, kb, -1.0, C, kb, 1, P, kb, 1, 0.0, A + k0, D, s);                // A[:, blk] = -C P
+    k_copy2d<<<grid_of((long long)kb * D, 256, 2048), 256, 0, s>>>(A + (long long)k0 * D, D, R, D, kb, D);
+    k_copy2d<<<grid_of((long long)kb * kb, 256, 64), 256, 0, s>>>(Akk, D, P, kb, kb, kb);
+  }
 }
 
 }  // namespace tg
