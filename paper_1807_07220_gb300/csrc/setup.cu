@@ -60,12 +60,14 @@ __global__ void k_assemble_band(const double* __restrict__ kinv, const int4* __r
 }
 
 // right-looking band Cholesky, one CTA per matrix, band in shared memory.
-// Column j: every thread takes r = 1/sqrt(K_jj) and, for its pair (d1, d2),
-// 1 <= d2 <= d1 <= w (one pair per thread, w (w + 1) / 2 <= blockDim), the
-// scaled entries l1 = K_{j+d1, j} r, l2 = K_{j+d2, j} r; after a barrier it
-// subtracts l1 l2 from K_{j+d1, j+d2} and the (d1, d1) thread stores l1.  Two
-// barriers per column; the chain of dependent FP64 operations per column is
-// one reciprocal square root, a product and an FMA.
+// Column j: r = 1/sqrt(K_jj) comes from shared memory; every thread takes,
+// for its pair (d1, d2), 1 <= d2 <= d1 <= w (one pair per thread,
+// w (w + 1) / 2 <= blockDim), the scaled entries l1 = K_{j+d1, j} r,
+// l2 = K_{j+d2, j} r; after a barrier it subtracts l1 l2 from K_{j+d1, j+d2}
+// and the (d1, d1) thread stores l1.  The (1, 1) thread makes the last update
+// of the next pivot, so it forms the next r at once (one reciprocal square
+// root per column, not one per thread: FP64 is scarce on this GPU).  Two
+// barriers per column.
 __global__ void k_band_cholesky(double* __restrict__ band, const int4* __restrict__ rects,
                                 const int* __restrict__ slot, int wmax, int nmax, int* status) {
   extern __shared__ double L[];
@@ -79,14 +81,21 @@ __global__ void k_band_cholesky(double* __restrict__ band, const int4* __restric
   while (d1 * (d1 + 1) / 2 <= t) ++d1;
   const int d2 = t - d1 * (d1 - 1) / 2 + 1;
   const bool has_pair = (d1 <= w);
+  __shared__ double rsh;   // 1/sqrt of the current pivot
   __syncthreads();
-  for (int j = 0; j < nloc; ++j) {
+  auto pivot_rsqrt = [&](int j) {
     double piv = L[(long long)j * ldb];
     if (!(piv > 0.0) || !isfinite(piv)) {
-      if (threadIdx.x == 0) atomicOr(status, kStNotSpd);
+      atomicOr(status, kStNotSpd);
       piv = 1.0;
+      L[(long long)j * ldb] = 1.0;
     }
-    const double rj = rsqrt(piv);
+    rsh = rsqrt(piv);
+  };
+  if (threadIdx.x == 0 && nloc > 0) pivot_rsqrt(0);
+  __syncthreads();
+  for (int j = 0; j < nloc; ++j) {
+    const double rj = rsh;
     const bool act = has_pair && (j + d1 < nloc);
     double l1 = 0.0, l2 = 0.0;
     if (act) {
@@ -98,7 +107,10 @@ __global__ void k_band_cholesky(double* __restrict__ band, const int4* __restric
       L[(long long)(j + d1) * ldb + (d1 - d2)] -= l1 * l2;
       if (d1 == d2) L[(long long)(j + d1) * ldb + d1] = l1;
     }
-    if (threadIdx.x == 0) L[(long long)j * ldb] = piv * rj;
+    if (threadIdx.x == 0) {
+      L[(long long)j * ldb] *= rj;                // sqrt(K_jj) = K_jj / sqrt(K_jj)
+      if (j + 1 < nloc) pivot_rsqrt(j + 1);       // pair (1, 1) just updated K_{j+1, j+1}
+    }
     __syncthreads();
   }
   for (int q = threadIdx.x; q < nloc * ldb; q += blockDim.x) B[q] = L[q];
@@ -932,11 +944,14 @@ __global__ void k_assemble_coarse(const int* __restrict__ slot_ptr, const Slot* 
 __global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int D, int k,
                           int* status) {
   const long long m = (long long)D * D;
-  const double p = A[(long long)k * D + k];
-  if (!(p > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStNotSpd);
+  __shared__ double ipk;   // the pivot's reciprocal, once per CTA
+  if (threadIdx.x == 0) {
+    const double p = A[(long long)k * D + k];
+    if (!(p > 0.0) && blockIdx.x == 0) atomicOr(status, kStNotSpd);
+    ipk = 1.0 / p;
   }
-  const double ip = 1.0 / p;
+  __syncthreads();
+  const double ip = ipk;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / D), j = (int)(t % D);
@@ -995,28 +1010,33 @@ __global__ void k_gather_cols(const double* __restrict__ K, int D, const int* __
 // row and column are staged in shared memory before each elimination step)
 __global__ void k_gj_small(double* __restrict__ A, int s, int* __restrict__ bad) {
   extern __shared__ double st[];   // 2 s
-  double* rowk = st;
+  __shared__ double ipk;
+  double* rows = st;
   double* colk = st + s;
   const int tot = s * s;
   for (int k = 0; k < s; ++k) {
+    if (threadIdx.x == 0) {   // the reciprocal once per step
+      double p = A[(long long)k * s + k];
+      if (!(p > 0.0) || !isfinite(p)) {
+        *bad = 1;
+        p = 1.0;
+      }
+      ipk = 1.0 / p;
+    }
+    __syncthreads();
+    const double ip = ipk;
     for (int j = threadIdx.x; j < s; j += blockDim.x) {
-      rowk[j] = A[(long long)k * s + j];
+      rows[j] = A[(long long)k * s + j] * ip;
       colk[j] = A[(long long)j * s + k];
     }
     __syncthreads();
-    double p = rowk[k];
-    if (!(p > 0.0) || !isfinite(p)) {
-      if (threadIdx.x == 0) *bad = 1;
-      p = 1.0;
-    }
-    const double ip = 1.0 / p;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int i = t / s, j = t % s;
       double v;
       if (i == k && j == k) v = ip;
-      else if (i == k) v = rowk[j] * ip;
+      else if (i == k) v = rows[j];
       else if (j == k) v = -colk[i] * ip;
-      else v = A[t] - colk[i] * rowk[j] * ip;
+      else v = fma(-colk[i], rows[j], A[t]);
       A[t] = v;
     }
     __syncthreads();
@@ -1074,28 +1094,34 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int kdim, double al
 
 // in-place Gauss-Jordan inverse of the kb x kb SPD diagonal block at A
 // (leading dimension lda) by one CTA; a non-positive pivot raises status
+// (the pivot's reciprocal is formed once per step and the pivot row scaled
+// by it, so each entry costs one FMA: FP64 throughput bounds this kernel)
 __global__ void k_gj_block(double* __restrict__ A, long long lda, int kb, int* status) {
-  __shared__ double rowk[kGjBlock], colk[kGjBlock];
+  __shared__ double rows[kGjBlock], colk[kGjBlock], ipk;
   const int tot = kb * kb;
   for (int k = 0; k < kb; ++k) {
+    if (threadIdx.x == 0) {
+      double p = A[(long long)k * lda + k];
+      if (!(p > 0.0) || !isfinite(p)) {
+        atomicOr(status, kStNotSpd);
+        p = 1.0;
+      }
+      ipk = 1.0 / p;
+    }
+    __syncthreads();
+    const double ip = ipk;
     for (int j = threadIdx.x; j < kb; j += blockDim.x) {
-      rowk[j] = A[(long long)k * lda + j];
+      rows[j] = A[(long long)k * lda + j] * ip;   // pivot row / p
       colk[j] = A[(long long)j * lda + k];
     }
     __syncthreads();
-    double p = rowk[k];
-    if (!(p > 0.0) || !isfinite(p)) {
-      if (threadIdx.x == 0) atomicOr(status, kStNotSpd);
-      p = 1.0;
-    }
-    const double ip = 1.0 / p;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int i = t / kb, j = t % kb;
       double* a = A + (long long)i * lda + j;
       if (i == k && j == k) *a = ip;
-      else if (i == k) *a = rowk[j] * ip;
+      else if (i == k) *a = rows[j];
       else if (j == k) *a = -colk[i] * ip;
-      else *a = *a - colk[i] * rowk[j] * ip;
+      else *a = fma(-colk[i], rows[j], *a);
     }
     __syncthreads();
   }
