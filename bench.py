@@ -153,6 +153,21 @@ def smoother_bytes(n, b, ov, ts_bytes, tc_bytes):
     return total
 
 
+def whole_job_rate(ms_list, dof_per_solve, world, distributed, device):
+    """Whole-job DOF-solves/s of `world` replicas that each timed len(ms_list)
+    solves: every rank's solves over the slowest rank's summed time (the max
+    over ranks, one all-reduce of the initialised default process group when
+    `distributed`).  Returns (DOF-solves/s, ms per step of the slowest rank)."""
+    total_ms = sum(ms_list)
+    if distributed:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * len(ms_list) * dof_per_solve / (total_ms / 1e3), total_ms / len(ms_list)
+
+
 def run_ncu_target(args):
     """Setup, warm-up and timed solves of the headline arm only (the command
     profiled by ncu; prints the solver report of the last solve)."""
@@ -256,13 +271,7 @@ def run_ours(args):
     tgms.tg_destroy(h)
 
     def agg(ms_list):
-        """Whole-job DOF-solves/s: all ranks' solves over the slowest rank's time."""
-        total_ms = sum(ms_list)
-        if dist:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        return world * len(ms_list) * dof(n) / (total_ms / 1e3), total_ms / len(ms_list)
+        return whole_job_rate(ms_list, dof(n), world, dist is not None, "cuda")
 
     value, ms_step = agg(times)
     p_value, p_ms = agg(p_times)

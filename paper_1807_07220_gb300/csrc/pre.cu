@@ -317,13 +317,14 @@ __global__ void k_block_particular(const double* __restrict__ f, double* __restr
   const int c = threadIdx.x;
   if (c < b) {
     // vertical flux through y-face (I b, J b + c), c >= 1, column 0 of the block
-    if (c >= 1) uy[(long long)(J * b + c) * n + I * b] += up[c] / h;
+    // flux / h = flux * n (products, not FP64 divisions, in the loop)
+    if (c >= 1) uy[(long long)(J * b + c) * n + I * b] += up[c] * (double)n;
     double run = 0.0;
     for (int a = 0; a + 1 < b; ++a) {
       double v = s[c * b + a];
       if (a == 0) v -= (up[c + 1] - up[c]);
       run += v;
-      ux[(long long)(J * b + c) * (n + 1) + I * b + a + 1] += run / h;
+      ux[(long long)(J * b + c) * (n + 1) + I * b + a + 1] += run * (double)n;
     }
   }
 }
