@@ -1174,26 +1174,23 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const int* __restri
                                                              int n, const PcgState* st) {
   pdl_entry();
   if (st && st->done) return;
-  __shared__ TC sh[32];
+  __shared__ TC vals[kMaxB * kMaxB];
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int bb = b * b, t = threadIdx.x;
-  TC val = (TC)0;
   if (t < bb) {
     const int i = I * b + t % b, j = J * b + t / b;
-    if (i != 0 && j != 0) val = (TC)r[(long long)j * n + i] - stencil_apply<TC, TC, TC>(z, kinv, n, i, j);
+    vals[t] = (i != 0 && j != 0) ? (TC)r[(long long)j * n + i] - stencil_apply<TC, TC, TC>(z, kinv, n, i, j)
+                                 : (TC)0;
   }
+  __syncthreads();
+  // one warp per slot: no barrier per slot
   const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
-  for (int s = s0; s < s1; ++s) {
-    TC prod = (t < bb) ? val * (TC)to_f(owned[(long long)s * bb + t]) : (TC)0;
-    prod = warp_sum(prod);
-    if ((t & 31) == 0) sh[t >> 5] = prod;
-    __syncthreads();
-    if (t < 32) {
-      TC x = (t < (int)(blockDim.x >> 5)) ? sh[t] : (TC)0;
-      x = warp_sum(x);
-      if (t == 0) part[s] = (double)x;
-    }
-    __syncthreads();
+  const int warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+  for (int s = s0 + warp; s < s1; s += nw) {
+    TC acc = (TC)0;
+    for (int e = lane; e < bb; e += 32) acc += vals[e] * (TC)to_f(owned[(long long)s * bb + e]);
+    acc = warp_sum(acc);
+    if (lane == 0) part[s] = (double)acc;
   }
 }
 
@@ -1208,23 +1205,19 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const int* __restrict__ s
                                                        int n, const PcgState* st) {
   pdl_entry();
   if (st && st->done) return;
-  __shared__ TC sh[32];
+  __shared__ TC vals[kMaxB * kMaxB];
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int bb = b * b, t = threadIdx.x;
-  TC val = (TC)0;
-  if (t < bb) val = v[(long long)(J * b + t / b) * n + I * b + t % b];
+  if (t < bb) vals[t] = v[(long long)(J * b + t / b) * n + I * b + t % b];
+  __syncthreads();
+  // one warp per slot: no barrier per slot
   const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
-  for (int s = s0; s < s1; ++s) {
-    TC prod = (t < bb) ? val * (TC)to_f(owned[(long long)s * bb + t]) : (TC)0;
-    prod = warp_sum(prod);
-    if ((t & 31) == 0) sh[t >> 5] = prod;
-    __syncthreads();
-    if (t < 32) {
-      TC x = (t < (int)(blockDim.x >> 5)) ? sh[t] : (TC)0;
-      x = warp_sum(x);
-      if (t == 0) part[s] = (double)x;
-    }
-    __syncthreads();
+  const int warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+  for (int s = s0 + warp; s < s1; s += nw) {
+    TC acc = (TC)0;
+    for (int e = lane; e < bb; e += 32) acc += vals[e] * (TC)to_f(owned[(long long)s * bb + e]);
+    acc = warp_sum(acc);
+    if (lane == 0) part[s] = (double)acc;
   }
 }
 
