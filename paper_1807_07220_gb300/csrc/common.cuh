@@ -251,16 +251,9 @@ template <typename TC>
 void launch_residual(const double* r, const TC* z, const TC* kinv, TC* out, int n, const PcgState* st,
                      cudaStream_t s);
 
-void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part,
-                          PcgState* st, int n, cudaStream_t s);
-template <typename TC>
-void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
-                          double* part, PcgState* st, int n, cudaStream_t s);
 template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st,
                      int n, cudaStream_t s);
-template <typename TC>
-void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s);
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s);
 template <typename TC>
 void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, PcgState* st, int n,

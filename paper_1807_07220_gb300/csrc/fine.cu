@@ -113,43 +113,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double* __restrict_
   }
 }
 
-// q = K p, alpha = rz / (p, q)
-__global__ void __launch_bounds__(kThreads) k_pcg_apply_dot(const double* __restrict__ p,
-                                                            const double* __restrict__ kinv,
-                                                            double* __restrict__ q,
-                                                            double* part, PcgState* st, int n) {
-  pdl_entry();
-  if (st->done) return;
-  __shared__ double sh[32];
-  const long long nn = (long long)n * n;
-  double acc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)(t / n);
-    double v = 0.0;
-    if (i != 0 && j != 0) v = stencil_apply<double, double, double>(p, kinv, n, i, j);
-    q[t] = v;
-    acc += v * p[t];
-  }
-  acc = block_sum(acc, sh);
-  if (arrive_last(acc, part, &st->counter[0]) && threadIdx.x < 32) {
-    const double pq = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-      st->counter[0] = 0;
-      st->pq = pq;
-      const double alpha = st->rz / pq;
-      if (!(pq > 0.0) || !isfinite(alpha)) {
-        st->status |= kStBreakdown;
-        st->done = 1;
-        st->alpha = 0.0;
-      } else {
-        st->alpha = alpha;
-        if (st->iter < kMaxHist) st->alphas[st->iter] = alpha;
-      }
-    }
-  }
-}
-
 // q = K p_new with p_new = z_prev + beta p_old formed on the fly in a shared
 // (32+2) x (8+2) halo tile (each p_new value computed once), p_new and q
 // written, z_next zeroed for the coming smoother accumulation, and
@@ -230,49 +193,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
   }
 }
 
-// x += alpha p, r -= alpha q, zacc = 0, rr = (r, r); convergence decision
-template <typename TC>
-__global__ void __launch_bounds__(kThreads) k_pcg_update_xr(double* __restrict__ x,
-                                                            double* __restrict__ r,
-                                                            const double* __restrict__ p,
-                                                            const double* __restrict__ q,
-                                                            TC* __restrict__ zacc, double* part,
-                                                            PcgState* st, int n) {
-  pdl_entry();
-  if (st->done) return;
-  __shared__ double sh[32];
-  const double alpha = st->alpha;
-  const long long nn = (long long)n * n;
-  double acc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    x[t] += alpha * p[t];
-    const double rv = r[t] - alpha * q[t];
-    r[t] = rv;
-    zacc[t] = (TC)0;
-    acc += rv * rv;
-  }
-  acc = block_sum(acc, sh);
-  if (arrive_last(acc, part, &st->counter[1]) && threadIdx.x < 32) {
-    const double rr = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-      st->counter[1] = 0;
-      st->rr = rr;
-      st->iter += 1;
-      if (rr <= st->rtol2 * st->rr0) {
-        st->done = 1;
-      } else if (!isfinite(rr)) {
-        st->status |= kStBreakdown;
-        st->done = 1;
-      } else if (st->iter >= st->maxit) {
-        st->status |= kStMaxIter;
-        st->done = 1;
-      }
-    }
-  }
-}
-
-// (r, z) and (z, q); beta
+// (r, r), (r, z) and (z, q) of the iteration's new residual r and
+// preconditioned residual z: the last CTA counts the iteration and tests
+// convergence on (r, r) (the stopping rule), then forms beta
 template <typename TC>
 __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict__ r,
                                                        const TC* __restrict__ z,
@@ -282,22 +205,42 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
   if (st->done) return;
   __shared__ double sh[32];
   const long long nn = (long long)n * n;
-  double a = 0.0, b = 0.0;
+  double a = 0.0, b = 0.0, c = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
        t += (long long)gridDim.x * blockDim.x) {
-    const double zv = (double)z[t];
-    a += r[t] * zv;
+    const double zv = (double)z[t], rv = r[t];
+    a += rv * zv;
     b += zv * q[t];
+    c += rv * rv;
   }
   a = block_sum(a, sh);
   b = block_sum(b, sh);
-  // two partial arrays: part[0..grid) and part[grid..2 grid)
-  if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = b;
+  c = block_sum(c, sh);
+  // three partial arrays: part[0..grid), part[grid..2 grid), part[2 grid..3 grid)
+  if (threadIdx.x == 0) {
+    part[gridDim.x + blockIdx.x] = b;
+    part[2 * gridDim.x + blockIdx.x] = c;
+  }
   if (arrive_last(a, part, &st->counter[2]) && threadIdx.x < 32) {
     const double rz = sum_partials(part, gridDim.x);
     const double zq = sum_partials(part + gridDim.x, gridDim.x);
+    const double rr = sum_partials(part + 2 * gridDim.x, gridDim.x);
     if (threadIdx.x == 0) {
       st->counter[2] = 0;
+      st->rr = rr;
+      st->iter += 1;
+      if (rr <= st->rtol2 * st->rr0) {
+        st->done = 1;
+        return;
+      } else if (!isfinite(rr)) {
+        st->status |= kStBreakdown;
+        st->done = 1;
+        return;
+      } else if (st->iter >= st->maxit) {
+        st->status |= kStMaxIter;
+        st->done = 1;
+        return;
+      }
       const double beta = st->flexible ? (-st->alpha * zq / st->rz) : (rz / st->rz);
       if (!(rz > 0.0) || !isfinite(beta)) {
         st->status |= kStBreakdown;
@@ -310,19 +253,6 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
       st->rz = rz;
     }
   }
-}
-
-template <typename TC>
-__global__ void __launch_bounds__(kThreads) k_pcg_update_p(double* __restrict__ p,
-                                                           const TC* __restrict__ z,
-                                                           const PcgState* st, int n) {
-  pdl_entry();
-  if (st->done) return;
-  const double beta = st->beta;
-  const long long nn = (long long)n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x)
-    p[t] = (double)z[t] + beta * p[t];
 }
 
 // scalar state at the start of a solve (rtol read from device memory so that
@@ -589,8 +519,9 @@ constexpr int kRowsPerWarp = kRowsPerGroup;
 // With kFused the sweep also performs the PCG update: the residual it
 // smooths is r_new = r_old - alpha q, formed at gather time; the CTA that owns
 // the first row group of patch p writes r_new and x += alpha p on the nodes of
-// block p (blocks partition the nodes, and r_old is never written here), and
-// the last CTA takes (r_new, r_new) and decides convergence.
+// block p (blocks partition the nodes, and r_old is never written here).
+// (r_new, r_new) and the stopping test are left to k_pcg_dots, which reads
+// r_new anyway.
 struct FuseArgs {
   const double* r_old;
   double* r_new;
@@ -618,8 +549,8 @@ struct ChainSet {
 };
 
 // kFused: 0 plain sweep z += eta S r; 1 first sweep of an iteration (r - alpha q
-// formed at gather time, r, x updated and (r, r) reduced by the block
-// owners); 2 last sweep with the residual formed at gather time,
+// formed at gather time, r and x updated by the block owners); 2 last sweep
+// with the residual formed at gather time,
 // r_in = r - K z_in, into a z buffer that the owners seed with z_in.
 template <typename TC, typename TS, typename TR, int kFused, int kCB, int kR, bool kPipe>
 __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restrict__ geo,
@@ -634,7 +565,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
   __shared__ __align__(16) TC xs[kPatchLd];
   __shared__ double shr[32];
   const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
-  double rr = 0.0;
   const int G = gofs[npatch];
   const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
   const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
@@ -675,7 +605,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
         const double rv = fa.r_old[id] - alpha * fa.q[id];
         fa.r_new[id] = rv;
         fa.x[id] += alpha * fa.p[id];
-        rr += rv * rv;
         if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
       }
     }
@@ -756,27 +685,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
       }
     }
   }
-  if (kFused == 1) {
-    rr = block_sum(rr, shr);
-    if (arrive_last(rr, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
-      const double tot = sum_partials(fa.part, gridDim.x);
-      if (threadIdx.x == 0) {
-        PcgState* S = fa.st;
-        S->counter[1] = 0;
-        S->rr = tot;
-        S->iter += 1;
-        if (tot <= S->rtol2 * S->rr0) {
-          S->done = 1;
-        } else if (!isfinite(tot)) {
-          S->status |= kStBreakdown;
-          S->done = 1;
-        } else if (S->iter >= S->maxit) {
-          S->status |= kStMaxIter;
-          S->done = 1;
-        }
-      }
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -802,12 +710,9 @@ __global__ void __launch_bounds__(kThreads) k_smoother_multi(const PatchGeo* __r
     any |= act[c];
   }
   if (!any) return;
-  double alpha[kGroup], rr[kGroup];
+  double alpha[kGroup];
 #pragma unroll
-  for (int c = 0; c < kGroup; ++c) {
-    alpha[c] = (kFused == 1 && act[c]) ? cs.fa[c].st->alpha : 0.0;
-    rr[c] = 0.0;
-  }
+  for (int c = 0; c < kGroup; ++c) alpha[c] = (kFused == 1 && act[c]) ? cs.fa[c].st->alpha : 0.0;
   const int G = gofs[npatch];
   const long long per = ((long long)G + gridDim.x - 1) / gridDim.x;
   const int g0 = (int)min((long long)G, blockIdx.x * per), g1 = (int)min((long long)G, g0 + per);
@@ -848,7 +753,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother_multi(const PatchGeo* __r
           const double rv = fa.r_old[id] - alpha[c] * fa.q[id];
           fa.r_new[id] = rv;
           fa.x[id] += alpha[c] * fa.p[id];
-          rr[c] += rv * rv;
           if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
         }
       }
@@ -907,33 +811,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother_multi(const PatchGeo* __r
           }
         }
       }
-    }
-  }
-  if (kFused == 1) {
-#pragma unroll
-    for (int c = 0; c < kGroup; ++c) {
-      if (!act[c]) continue;
-      const FuseArgs& fa = cs.fa[c];
-      const double tot_cta = block_sum(rr[c], shr);
-      if (arrive_last(tot_cta, fa.part, &fa.st->counter[1]) && threadIdx.x < 32) {
-        const double tot = sum_partials(fa.part, gridDim.x);
-        if (threadIdx.x == 0) {
-          PcgState* S = fa.st;
-          S->counter[1] = 0;
-          S->rr = tot;
-          S->iter += 1;
-          if (tot <= S->rtol2 * S->rr0) {
-            S->done = 1;
-          } else if (!isfinite(tot)) {
-            S->status |= kStBreakdown;
-            S->done = 1;
-          } else if (S->iter >= S->maxit) {
-            S->status |= kStMaxIter;
-            S->done = 1;
-          }
-        }
-      }
-      __syncthreads();
     }
   }
 }
@@ -1127,7 +1004,6 @@ __global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __res
   }
   if (kFused) {
     // block owners: r_new = r_old - alpha q and x += alpha p on their block's nodes
-    double rr = 0.0;
     for (int p = p0; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
       if (gofs[p] < g0) continue;
       const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
@@ -1136,27 +1012,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother_tma(const PatchGeo* __res
         const double rv = fa.r_old[id] - alpha * fa.q[id];
         fa.r_new[id] = rv;
         fa.x[id] += alpha * fa.p[id];
-        rr += rv * rv;
         if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
-      }
-    }
-    rr = block_sum(rr, shr);
-    if (arrive_last(rr, fa.part, &fa.st->counter[1]) && tid < 32) {
-      const double tot = sum_partials(fa.part, gridDim.x);
-      if (tid == 0) {
-        PcgState* S = fa.st;
-        S->counter[1] = 0;
-        S->rr = tot;
-        S->iter += 1;
-        if (tot <= S->rtol2 * S->rr0) {
-          S->done = 1;
-        } else if (!isfinite(tot)) {
-          S->status |= kStBreakdown;
-          S->done = 1;
-        } else if (S->iter >= S->maxit) {
-          S->status |= kStMaxIter;
-          S->done = 1;
-        }
       }
     }
   }
@@ -1414,27 +1270,11 @@ template void launch_residual<double>(const double*, const double*, const double
 template void launch_residual<float>(const double*, const float*, const float*, float*, int,
                                      const PcgState*, cudaStream_t);
 
-void launch_pcg_apply_dot(const double* p, const double* kinv, double* q, double* part, PcgState* st,
-                          int n, cudaStream_t s) {
-  TG_COUNT(1);
-  launch(k_pcg_apply_dot, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, p, kinv, q, part, st, n);
-}
-template <typename TC>
-void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, TC* zacc,
-                          double* part, PcgState* st, int n, cudaStream_t s) {
-  TG_COUNT(1);
-  launch(k_pcg_update_xr<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, x, r, p, q, zacc, part, st, n);
-}
 template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
                      cudaStream_t s) {
   TG_COUNT(1);
   launch(k_pcg_dots<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, q, part, st, n);
-}
-template <typename TC>
-void launch_pcg_update_p(double* p, const TC* z, const PcgState* st, int n, cudaStream_t s) {
-  TG_COUNT(1);
-  launch(k_pcg_update_p<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, p, z, st, n);
 }
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
@@ -1447,11 +1287,8 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
   launch(k_pcg_init_rz<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, p, part, st, n);
 }
 #define TG_INST_TC(TC)                                                                              \
-  template void launch_pcg_update_xr<TC>(double*, double*, const double*, const double*, TC*,      \
-                                         double*, PcgState*, int, cudaStream_t);                    \
   template void launch_pcg_dots<TC>(const double*, const TC*, const double*, double*, PcgState*,   \
                                     int, cudaStream_t);                                             \
-  template void launch_pcg_update_p<TC>(double*, const TC*, const PcgState*, int, cudaStream_t);   \
   template void launch_pcg_init_rz<TC>(const double*, const TC*, double*, double*, PcgState*, int, \
                                        cudaStream_t);
 TG_INST_TC(double)
