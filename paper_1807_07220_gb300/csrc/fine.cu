@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
                                                        double* part, PcgState* st, int n) {
   pdl_entry();
   if (st->done) return;
-  __shared__ double sh[32];
   const long long nn = (long long)n * n;
   double a = 0.0, b = 0.0, c = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -213,9 +212,25 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
     b += zv * q[t];
     c += rv * rv;
   }
-  a = block_sum(a, sh);
-  b = block_sum(b, sh);
-  c = block_sum(c, sh);
+  // the three CTA sums in one pass (one barrier instead of three block sums)
+  {
+    __shared__ double sh3[3][32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+      sh3[0][w] = a;
+      sh3[1][w] = b;
+      sh3[2][w] = c;
+    }
+    __syncthreads();
+    if (w == 0) {
+      a = warp_sum(l < nw ? sh3[0][l] : 0.0);
+      b = warp_sum(l < nw ? sh3[1][l] : 0.0);
+      c = warp_sum(l < nw ? sh3[2][l] : 0.0);
+    }
+  }
   // three partial arrays: part[0..grid), part[grid..2 grid), part[2 grid..3 grid)
   if (threadIdx.x == 0) {
     part[gridDim.x + blockIdx.x] = b;
