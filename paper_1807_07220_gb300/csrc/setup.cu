@@ -192,6 +192,89 @@ __global__ void k_band_inverse(const double* __restrict__ band, const int4* __re
   }
 }
 
+// The same inverse for few matrices, with G lanes per column: the pending
+// sums of a column's rows are split among its G lanes by row (row r belongs to
+// lane r mod G), so each lane makes about w / G of the w updates per row, and
+// the lane owning row j forms y_j (x_j in the backward sweep) and passes it to
+// the others by a shuffle.  This cuts the FP64 instructions a warp issues per
+// row about G-fold (FP64 issue bounds the first columns' long sweeps when one
+// matrix is refactored alone).  CTA (m, y) takes blockDim / G columns; ring of
+// pending sums per column in shared memory, slot of row r = r mod (wmax + 1).
+template <int G>
+__global__ void k_band_inverse_grp(const double* __restrict__ band, const int4* __restrict__ rects,
+                                   const int* __restrict__ slot, int first, int wmax, int nmax,
+                                   double* __restrict__ scratch) {
+  extern __shared__ double sh[];
+  const int m = first + blockIdx.x;
+  const int4 r = rects[m];
+  const int nx = r.z, nloc = r.z * r.w, w = nx + 1, ldb = wmax + 1, rl = wmax + 1;
+  const int C = blockDim.x / G;   // columns per CTA
+  double* L = sh;
+  double* rd = sh + (long long)nmax * ldb;
+  double* ring = rd + nmax;   // ring[col * rl + slot]
+  const double* B = band + (long long)(slot ? slot[m] : m) * nmax * ldb;
+  for (int t = threadIdx.x; t < nloc * ldb; t += blockDim.x) L[t] = B[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nloc; t += blockDim.x) rd[t] = 1.0 / L[(long long)t * ldb];
+  __syncthreads();
+  double* X = scratch + (long long)blockIdx.x * nmax * nmax;
+  const int cl = threadIdx.x / G, sub = threadIdx.x % G;
+  const int lane = threadIdx.x & 31, base = lane - sub;   // first lane of this column's group
+  double* my = ring + (long long)cl * rl;
+  for (int c0 = blockIdx.y * C; c0 < nloc; c0 += gridDim.y * C) {
+    const int t = c0 + cl;
+    const bool col = (t < nloc);
+    for (int q = sub; q < rl; q += G) my[q] = 0.0;
+    __syncwarp();
+    // forward, L y = e_t, rows j >= t (y_j = 0 above)
+    for (int j = c0; j < nloc; ++j) {
+      const int o = j % G;
+      double y = 0.0;
+      if (sub == o && col && j >= t) {
+        const int q = j % rl;
+        y = (((j == t) ? 1.0 : 0.0) - my[q]) * rd[j];
+        my[q] = 0.0;
+        X[(long long)j * nloc + t] = y;
+      }
+      y = __shfl_sync(0xffffffffu, y, base + o);
+      if (col && j >= t) {
+        const int dmax = min(w, nloc - 1 - j);
+        // rows j + d owned by this lane: (j + d) % G == sub
+        for (int d = (sub - j % G + G) % G; d <= dmax; d += G) {
+          if (d == 0) continue;
+          const int rr = j + d;
+          my[rr % rl] = fma(L[(long long)rr * ldb + d], y, my[rr % rl]);
+        }
+      }
+      __syncwarp();
+    }
+    for (int q = sub; q < rl; q += G) my[q] = 0.0;
+    __syncwarp();
+    // backward, L^T x = y for rows j >= t
+    for (int j = nloc - 1; j >= c0; --j) {
+      const int o = j % G;
+      double x = 0.0;
+      if (sub == o && col && j >= t) {
+        const int q = j % rl;
+        x = (X[(long long)j * nloc + t] - my[q]) * rd[j];
+        my[q] = 0.0;
+        X[(long long)j * nloc + t] = x;
+      }
+      x = __shfl_sync(0xffffffffu, x, base + o);
+      if (col && j >= t) {
+        const int dmax = min(w, j);
+        // rows j - d owned by this lane: (j - d) % G == sub
+        for (int d = (j % G - sub + G) % G; d <= dmax; d += G) {
+          if (d == 0) continue;
+          const int rr = j - d;
+          my[rr % rl] = fma(L[(long long)j * ldb + d], x, my[rr % rl]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <typename TS>
 __global__ void k_store_inverse(const double* __restrict__ scratch, const PatchGeo* __restrict__ geo,
                                 int first, int nmax, TS* __restrict__ pinv) {
@@ -1182,6 +1265,16 @@ void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, i
   cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   k_band_cholesky<<<nmat, threads, shm, s>>>(band, rects, slot, wmax, nmax, status);
 }
+static int sm_count_setup() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
 // CTAs per matrix so that `count` matrices fill about two waves of the SMs
 // (at most one per 32 columns or rows of a matrix of side nmax)
 static int split_for(int count, int nmax, int granule) {
@@ -1198,6 +1291,15 @@ static int split_for(int count, int nmax, int granule) {
 void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax, int nmax,
                          double* scratch, cudaStream_t s, const int* slot) {
   if (count == 0) return;
+  if (count * ((nmax + 31) / 32) < sm_count_setup()) {
+    // few matrices: 8 lanes per column, 16 columns per CTA
+    constexpr int G = 8, kThr = 128;
+    const int C = kThr / G, split = (nmax + C - 1) / C;
+    const size_t shm = sizeof(double) * ((size_t)nmax * (wmax + 1) + nmax + (size_t)C * (wmax + 1));
+    cudaFuncSetAttribute(k_band_inverse_grp<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_band_inverse_grp<G><<<dim3(count, split), kThr, shm, s>>>(band, rects, slot, first, wmax, nmax, scratch);
+    return;
+  }
   // one thread per column, the columns of a matrix split over `split` CTAs,
   // as far as the ring fits beside the band
   const int split = split_for(count, nmax, 32);
