@@ -396,7 +396,8 @@ int galerkin_update(tg_handle* h, CoarseSpace& c, const double* delta, const uns
     rc = cuda_err(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
     if (!rc && !bad) {
-      launch_dgemm(D, D, m, 1.0, T, m, 1, X, 1, m, 1.0, c.Kinv, D, s);   // B += T X^T
+      if (m <= 8) launch_rank_update(c.Kinv, D, T, X, m, s);             // B += T X^T
+      else launch_dgemm(D, D, m, 1.0, T, m, 1, X, 1, m, 1.0, c.Kinv, D, s);
       rc = cuda_err(cudaStreamSynchronize(s));
     }
   }

@@ -417,6 +417,8 @@ void launch_dgemm(int m, int n, int k, double alpha, const double* A, long long 
                   const double* B, long long brs, long long bcs, double beta, double* C, long long ldc,
                   cudaStream_t s);
 void launch_symmetrize(double* A, int s_cnt, cudaStream_t s);
+// B (D x D) += T X^T, T and X D x m row-major (small m: one thread per entry)
+void launch_rank_update(double* B, int D, const double* T, const double* X, int m, cudaStream_t s);
 void launch_add(double* y, const double* x, long long cnt, cudaStream_t s);  // result in A
 
 // learned coarse basis (learned.cu)

@@ -1221,6 +1221,20 @@ __global__ void k_copy2d(double* __restrict__ dst, long long ldd, const double* 
   }
 }
 
+// B (D x D) += T X^T for a small rank m (T, X: D x m row-major), one thread
+// per entry: the rank-|S| correction of a coarse inverse when |S| is small
+__global__ void k_rank_update(double* __restrict__ B, int D, const double* __restrict__ T,
+                              const double* __restrict__ X, int m) {
+  const long long tot = (long long)D * D;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / D), j = (int)(t % D);
+    double acc = B[t];
+    for (int a = 0; a < m; ++a) acc = fma(T[(long long)i * m + a], X[(long long)j * m + a], acc);
+    B[t] = acc;
+  }
+}
+
 // A (s x s) = (A + A^T) / 2, one thread per pair i < j
 __global__ void k_symmetrize(double* __restrict__ A, int s) {
   const long long tot = (long long)s * s;
@@ -1406,6 +1420,10 @@ void launch_dgemm(int m, int n, int k, double alpha, const double* A, long long 
                   cudaStream_t s) {
   if (m == 0 || n == 0) return;
   k_dgemm<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, s>>>(m, n, k, alpha, A, ars, acs, B, brs, bcs, beta, C, ldc);
+}
+void launch_rank_update(double* B, int D, const double* T, const double* X, int m, cudaStream_t s) {
+  if (D == 0 || m == 0) return;
+  k_rank_update<<<grid_of((long long)D * D, 256, 4096), 256, 0, s>>>(B, D, T, X, m);
 }
 void launch_symmetrize(double* A, int s_cnt, cudaStream_t s) {
   if (s_cnt == 0) return;
