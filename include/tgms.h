@@ -120,9 +120,12 @@ typedef struct tg_options {
    * per pass (2 for FP64 storage); 1 = 16-byte loads, 2 rows; 2 = 8-byte
    * loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
    * shared-memory ring; 5 = shape 3 and 6 = shape 1 software-pipelined (the
-   * next pass's rows are loaded while the current pass is reduced).  FP64
-   * storage runs shape 0 for 1..3, 5, 6; FP16 storage shape 0 for 4.  Same
-   * arithmetic in every shape. */
+   * next pass's rows are loaded while the current pass is reduced); 7 =
+   * the band form: each local problem solved from its band Cholesky factor by
+   * two triangular solves (the paper's direct subdomain solver), one warp per
+   * patch, in the arithmetic precision (FP64 handles FP64, the others FP32).
+   * FP64 storage runs shape 0 for 1..3, 5, 6; FP16 storage shape 0 for 4.
+   * Shapes 0..6 compute the same arithmetic; shape 7 the same operator. */
   int smoother_shape;
   /* 1: launch the kernels of a solve with programmatic dependent launch
    * (each kernel's launch overlaps the tail of the one before it; it waits
@@ -166,7 +169,7 @@ typedef struct tg_report {
   int fallback_faces;     /* TG_COARSE_LEARNED: faces that took the exact spectral problem */
   int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
   int smoother_shape;     /* smoother tile shape in use */
-  float shape_us[7];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
+  float shape_us[8];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
   int refactored_patches; /* patch inverses computed by the handle's last setup or tg_update_kappa */
   int refactored_blocks;  /* coarse-block factors computed by the same call */
   int update_rank[2];     /* last tg_update_kappa: rank of the low-rank update of the

@@ -45,6 +45,8 @@ struct tg_handle {
   int* d_gofs = nullptr;    // first row group of each patch (+ total)
   int ngroups = 0;
   void* pinv = nullptr;
+  void* pband = nullptr;    // band factors of the patches in the arithmetic type (tile shape kShapeBand)
+  BandRef band;
   float* rscale = nullptr;  // FP16 storage: inverse row scales
   // block factors (snapshots) and dense block inverses (preprocessing)
   double* blk_band = nullptr;
@@ -535,7 +537,7 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
     // z = S r + P r: both parts from r
     prof_mark(c, s);
     launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s,
-                                    h->shape, h->rscale);
+                                    h->shape, h->rscale, h->band);
     prof_mark(c, s);
     if (h->cs.D > 0) {
       launch_restrict<double, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r, st, s);
@@ -547,12 +549,13 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
     if (k == 0) {
       prof_mark(c, s);
       launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r, zacc, eta, n, st, s,
-                                      h->shape, h->rscale);
+                                      h->shape, h->rscale, h->band);
       prof_mark(c, s);
     } else {
       launch_residual<TC>(r, zacc, kin, rin, n, st, s);
       prof_mark(c, s);
-      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape, h->rscale);
+      launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape,
+                                  h->rscale, h->band);
       prof_mark(c, s);
     }
   }
@@ -563,7 +566,8 @@ void precondition(Ctx* c, const double* r, TC* zacc, const PcgState* st, cudaStr
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r, zacc, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape, h->rscale);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, zacc, eta, n, st, s, h->shape,
+                                h->rscale, h->band);
     prof_mark(c, s);
   }
 }
@@ -658,7 +662,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
     launch_pcg_apply_p<TC>(zA, p_old, p_new, c->q, zB, h->kcoef, c->part, st, n, s);
     prof_mark(c, s);
     launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
-                                   p_new, zB, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, zA);
+                                   p_new, zB, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, zA, h->band);
     prof_mark(c, s);
     if (h->cs.D > 0) {
       launch_resid_restrict<TC, tile_t<TS>>(h->cs, c->cs_part, h->nblocks, h->nc, h->b, n, r_new, zB, kin, st, s);
@@ -666,7 +670,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
     }
     prof_mark(c, s);
     launch_smoother_resid<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_new, zB, kin, zA, eta, n,
-                                  h->nc, h->b, st, s, h->shape, h->rscale);
+                                  h->nc, h->b, st, s, h->shape, h->rscale, h->band);
     prof_mark(c, s);
     launch_pcg_dots<TC>(r_new, zA, c->q, c->part, st, n, s);
     return;
@@ -676,7 +680,8 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
   prof_mark(c, s);
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
-                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale);
+                                 p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, nullptr,
+                                 h->band);
   prof_mark(c, s);
   if (h->opt.cycle == TG_CYCLE_ADDITIVE) {
     // z = S r + P r: the coarse part restricts r itself
@@ -690,7 +695,8 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   for (int k = 1; k < h->opt.m1; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape, h->rscale);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape,
+                                h->rscale, h->band);
     prof_mark(c, s);
   }
   if (h->cs.D > 0) {
@@ -700,7 +706,8 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   for (int k = 0; k < h->opt.m2; ++k) {
     launch_residual<TC>(r_new, z_cur, kin, rin, n, st, s);
     prof_mark(c, s);
-    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape, h->rscale);
+    launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, rin, z_cur, eta, n, st, s, h->shape,
+                                h->rscale, h->band);
     prof_mark(c, s);
   }
   launch_pcg_dots<TC>(r_new, z_cur, c->q, c->part, st, n, s);
@@ -778,8 +785,17 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
     m1[i] = ChainPtrs{r_old, r_new, c->q, c->x, p_new, c->part, c->st, zA, nullptr, nullptr, r_old, zB};
     m2[i] = ChainPtrs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->st, nullptr, zB, kin, r_new, zA};
   }
-  launch_smoother_multi<TC, TS>(1, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1, k, h->opt.eta, n, h->nc,
-                                h->b, s, h->shape, h->rscale);
+  // the band sweep has no lock-step form: one band sweep per chain
+  const bool band = (h->shape == kShapeBand);
+  if (band) {
+    for (int i = 0; i < k; ++i)
+      launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1[i].r_old, m1[i].r_new,
+                                     m1[i].q, m1[i].x, m1[i].p, (TC*)m1[i].zacc, h->opt.eta, n, h->nc, h->b,
+                                     m1[i].part, m1[i].st, s, h->shape, h->rscale, (TC*)m1[i].zclear, h->band);
+  } else {
+    launch_smoother_multi<TC, TS>(1, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1, k, h->opt.eta, n, h->nc,
+                                  h->b, s, h->shape, h->rscale);
+  }
   if (h->cs.D > 0) {
     for (int i = 0; i < k; ++i) {
       Ctx* c = cs[i];
@@ -789,8 +805,15 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
       launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, zB, c->st, s);
     }
   }
-  launch_smoother_multi<TC, TS>(2, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2, k, h->opt.eta, n, h->nc,
-                                h->b, s, h->shape, h->rscale);
+  if (band) {
+    for (int i = 0; i < k; ++i)
+      launch_smoother_resid<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2[i].r, (const TC*)m2[i].zin,
+                                    kin, (TC*)m2[i].zacc, h->opt.eta, n, h->nc, h->b, m2[i].st, s, h->shape,
+                                    h->rscale, h->band);
+  } else {
+    launch_smoother_multi<TC, TS>(2, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2, k, h->opt.eta, n, h->nc,
+                                  h->b, s, h->shape, h->rscale);
+  }
   for (int i = 0; i < k; ++i) {
     Ctx* c = cs[i];
     const double* r_new = parity ? c->r : c->r2;
@@ -989,6 +1012,12 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
     TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)L.off * ts_size(h->opt.precision))));
     if (h->opt.precision == TG_PREC_F16 && dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup))
       return TG_ERR_OOM;
+    // band factors for the band smoother: FP64 handles in FP64, the others in FP32
+    h->band.ldb = kBandLd;
+    h->band.stride = 2LL * (nmax + 2 * kBandPad) * kBandLd;   // column and row layouts
+    const size_t esz = (h->opt.precision == TG_PREC_F64) ? sizeof(double) : sizeof(float);
+    TG_CK(cudaMalloc(&h->pband, std::max<size_t>(1, (size_t)h->npatch * h->band.stride * esz)));
+    h->band.p = h->pband;
   }
   // the patches to factor, as a compact list: rectangles, layouts, numbers
   const std::vector<int> ids = selected(h->npatch, update ? changed : nullptr);
@@ -1016,6 +1045,10 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
   if (!rc) {
     launch_assemble_band(h->kinv, d_rect, band, cnt, wmax, nmax, n, s);
     launch_band_cholesky(band, d_rect, cnt, wmax, nmax, h->d_status, s);
+    if (h->opt.precision == TG_PREC_F64)
+      launch_store_band<double>(band, d_rect, d_ids, cnt, wmax, nmax, h->band.stride, (double*)h->pband, s);
+    else
+      launch_store_band<float>(band, d_rect, d_ids, cnt, wmax, nmax, h->band.stride, (float*)h->pband, s);
     for (int first = 0; first < cnt; first += batch) {
       const int m = std::min(batch, cnt - first);
       launch_band_inverse(band, d_rect, first, m, wmax, nmax, inv, s);
@@ -1282,16 +1315,16 @@ int autotune_smoother_t(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaMemsetAsync(rin, 0, sizeof(TC) * nn, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
   const bool f64 = std::is_same<TS, double>::value, f16 = std::is_same<TS, __half>::value;
-  const int cand_all[] = {0, 1, 2, 3, 4, 5, 6}, cand_f64[] = {0, 4}, cand_f16[] = {0, 1, 2, 3, 5, 6};
+  const int cand_all[] = {0, 1, 2, 3, 4, 5, 6, 7}, cand_f64[] = {0, 4, 7}, cand_f16[] = {0, 1, 2, 3, 5, 6, 7};
   const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : cand_all;   // FP16: no TMA ring
-  const int ncand = f64 ? 2 : f16 ? 6 : 7;
+  const int ncand = f64 ? 3 : f16 ? 7 : 8;
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {
     const int shape = cand[i];
     auto go = [&]() {
       launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rin, z,
-                                  h->opt.eta, h->n, nullptr, s, shape, h->rscale);
+                                  h->opt.eta, h->n, nullptr, s, shape, h->rscale, h->band);
     };
     go();
     cudaEventRecord(e0, s);
@@ -1495,7 +1528,7 @@ int hook_precond(tg_handle* h, const double* rho, double* z, int which) {
   TG_CK(cudaMemsetAsync(zacc, 0, sizeof(TC) * nn, h->stream));
   if (which == 0) {
     launch_smoother<TC, TS, double>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rho, zacc,
-                                    h->opt.eta, n, nullptr, h->stream, h->shape, h->rscale);
+                                    h->opt.eta, n, nullptr, h->stream, h->shape, h->rscale, h->band);
   } else if (which == 1) {
     if (h->cs.D > 0) {
       TC* rin = (TC*)c->rin;
@@ -1825,7 +1858,7 @@ void tg_destroy(tg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   ctx_free(h->ctx);
-  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->rscale, h->blk_band, h->lam,
+  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->pband, h->rscale, h->blk_band, h->lam,
                   h->d_bgeo, h->d_bgofs, h->binv, h->binv32, h->kcoef};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);

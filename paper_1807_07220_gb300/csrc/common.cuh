@@ -265,24 +265,41 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 // shared-memory ring; 5 = shape 3 and 6 = shape 1, software-pipelined (the
 // next pass's rows in flight while the current one is reduced).  FP64 storage
 // uses shape 0 for 1..3, 5, 6; FP16 storage uses shape 0 for 4.
-constexpr int kSmootherShapes = 7;
+constexpr int kSmootherShapes = 8;
+constexpr int kShapeBand = 7;   // smoother from the patches' band Cholesky factors (two triangular solves)
+// band factors of the oversampled patches in the arithmetic type, two
+// layouts per patch (patch p at p * stride, the second at + stride / 2):
+// column layout, entry (j, d) = L_{j+d, j} (the column below the diagonal;
+// read by the forward sweep), and row layout, entry (j, d) = L_{j, j-d} (the
+// row left of the diagonal; read by the backward sweep); d = 0 holds 1 / L_jj
+// in both, entry (j, d) sits at (j + kBandPad) * kBandLd + d.  Rows -kBandPad ..
+// nmax + kBandPad - 1 are stored, zero outside the matrix and the band, so
+// the sweeps read them without bounds checks and every read is coalesced.
+constexpr int kBandLd = 24;    // entries per row (the band is at most kMaxPatchSide + 1 = 20 wide)
+constexpr int kBandPad = 16;   // >= the sweeps' read-ahead (8 rows) plus the row rounding (< 8)
+struct BandRef {
+  const void* p = nullptr;
+  int ldb = 0;
+  long long stride = 0;
+};
 // rscale: FP16 storage only, one power-of-two factor per stored row (index
 // gofs[p] * kRowsPerGroup + row) that undoes the row's scaling.
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                      TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape = 0,
-                     const float* rscale = nullptr);
+                     const float* rscale = nullptr, BandRef band = {});
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape = 0, const float* rscale = nullptr, TC* zclear = nullptr);
+                            cudaStream_t s, int shape = 0, const float* rscale = nullptr, TC* zclear = nullptr,
+                            BandRef band = {});
 // last smoothing sweep with the residual formed at gather time:
 // zout (zeroed beforehand) = zin + eta sum_i E_i M_i E_i^T (r - K zin)
 template <typename TC, typename TS>
 void launch_smoother_resid(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                            const double* r, const TC* zin, const TC* kin, TC* zout, double eta, int n, int nc, int b,
-                           const PcgState* st, cudaStream_t s, int shape, const float* rscale);
+                           const PcgState* st, cudaStream_t s, int shape, const float* rscale, BandRef band = {});
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s);
@@ -340,6 +357,11 @@ void launch_band_cholesky(double* band, const int4* rects, int nmat, int wmax, i
                           int* status, cudaStream_t s, const int* slot = nullptr);
 void launch_band_inverse(const double* band, const int4* rects, int first, int count, int wmax,
                          int nmax, double* scratch, cudaStream_t s, const int* slot = nullptr);
+// band factors (Cholesky bands of compact patches c, rows L[j][d] =
+// L_{j,j-d}) into the smoother's band layout (BandRef) of patches ids[c]
+template <typename TB>
+void launch_store_band(const double* band, const int4* rects, const int* ids, int count, int wmax, int nmax,
+                       long long stride, TB* out, cudaStream_t s);
 // flag[m] = 1 where some cell of rectangle m gets a new 1/kappa (bitwise
 // comparison against kinv_old, computed as launch_kinv computes it)
 void launch_rect_changed(const double* kappa, const double* kinv_old, const int4* rects, int nrect, int n,

@@ -703,6 +703,124 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Band variant (tile shape kShapeBand): each local problem is solved from its
+// band Cholesky factor by the two triangular solves, as the paper's direct
+// subdomain solvers do, instead of a product with the stored dense inverse.
+// One warp per patch: the residual is gathered into shared memory, then both
+// sweeps are right-looking: lane 0 forms the row's value from its pending
+// sum, broadcasts it, and lane d adds its band entry's term to the pending
+// sum of row j + d (forward) or j - d (backward), held in its registers.  Lane d's band entries are loaded kBandPF rows ahead (they
+// do not depend on the sweep), so the chain from row to row is a
+// subtraction, a product and two shuffles.  The factor is read once per sweep:
+// n_loc (w + 1) values against n_loc^2 for the dense inverse.
+constexpr int kBandWarps = 4;   // patches per CTA
+constexpr int kBandPF = 8;      // rows of band entries in flight per lane
+template <typename TC, typename TR, int kFused>
+__global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGeo* __restrict__ geo, int npatch,
+                                                                   const TC* __restrict__ band, int ldb,
+                                                                   long long pstride, const TR* __restrict__ r,
+                                                                   TC* __restrict__ zacc, TC eta, int n,
+                                                                   const PcgState* st, FuseArgs fa) {
+  pdl_entry();
+  if (st && st->done) return;
+  __shared__ TC xs_all[kBandWarps][kPatchLd];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kBandWarps + warp;
+  if (p >= npatch) return;   // warp-uniform; no block-wide barrier below
+  TC* xs = xs_all[warp];
+  const PatchGeo g = geo[p];
+  const int nloc = g.nloc, w = g.nx + 1;
+  const TC* Lc = band + (long long)p * pstride;
+  const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
+  for (int q = lane; q < nloc; q += 32) {
+    const int a = q % g.nx, c = q / g.nx;
+    const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
+    TC v;
+    if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+    else if constexpr (kFused == 2)
+      v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a, g.y0 + 1 + c);
+    else v = (TC)r[id];
+    xs[q] = v;
+  }
+  if (kFused == 1) {   // block p's owner work
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = lane; t < b * b; t += 32) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      fa.r_new[id] = fa.r_old[id] - alpha * fa.q[id];
+      fa.x[id] += alpha * fa.p[id];
+      if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
+    }
+  }
+  if (kFused == 2) {   // the owner seeds the output with z_in
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = lane; t < b * b; t += 32) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      atomicAdd(zacc + id, ((const TC*)fa.zin)[id]);
+    }
+  }
+  // rows past the matrix up to a multiple of kBandPF: zero right-hand side,
+  // zero band entries (padding), so they add nothing
+  const int nrow = ((nloc + kBandPF - 1) / kBandPF) * kBandPF;
+  for (int q = nloc + lane; q < nrow; q += 32) xs[q] = (TC)0;
+  __syncwarp();
+  // pending sums live in registers: after row j, lane d holds the pending sum
+  // of row j + 1 + d (forward) or j - 1 - d (backward); a shuffle down by one
+  // lane moves them along as the sweep advances.  Lane d reads entry (j, d) of
+  // the column layout (L_{j+d, j}) in the forward sweep and of the row layout
+  // (L_{j, j-d}) in the backward one: one coalesced row per step; the padded
+  // layouts make every read in range and zero outside the band.
+  const bool ln = (lane < ldb);   // lanes past the stored band read nothing
+  const TC* L0 = Lc + (long long)kBandPad * ldb + (ln ? lane : 0);   // entry (0, lane)
+  {
+    TC pf[kBandPF];
+#pragma unroll
+    for (int k = 0; k < kBandPF; ++k) pf[k] = ln ? L0[(long long)k * ldb] : (TC)0;
+    TC acc = (TC)0;
+    for (int j0 = 0; j0 < nrow; j0 += kBandPF) {
+      const TC* lp = L0 + (long long)(j0 + kBandPF) * ldb;
+#pragma unroll
+      for (int k = 0; k < kBandPF; ++k) {
+        const int j = j0 + k;
+        const TC cj = pf[k];
+        pf[k] = ln ? lp[(long long)k * ldb] : (TC)0;
+        TC y = (xs[j] - acc) * cj;             // meaningful in lane 0
+        y = __shfl_sync(0xffffffffu, y, 0);
+        if (lane == 0) xs[j] = y;
+        else acc = fma(cj, y, acc);
+        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      }
+    }
+  }
+  __syncwarp();
+  {
+    const TC* Lb = L0 + pstride / 2;   // row layout: entry (j, lane) = L_{j, j-lane} at Lb[j ldb]
+    TC pf[kBandPF];
+#pragma unroll
+    for (int k = 0; k < kBandPF; ++k) pf[k] = ln ? Lb[(long long)(nrow - 1 - k) * ldb] : (TC)0;
+    TC acc = (TC)0;
+    for (int j0 = nrow - 1; j0 >= 0; j0 -= kBandPF) {
+      const TC* lp = Lb + (long long)(j0 - kBandPF) * ldb;
+#pragma unroll
+      for (int k = 0; k < kBandPF; ++k) {
+        const int j = j0 - k;
+        const TC cj = pf[k];
+        pf[k] = ln ? lp[-(long long)k * ldb] : (TC)0;
+        TC x = (xs[j] - acc) * cj;             // meaningful in lane 0
+        x = __shfl_sync(0xffffffffu, x, 0);
+        if (lane == 0) xs[j] = x;
+        else acc = fma(cj, x, acc);
+        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      }
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < nloc; q += 32) {
+    const int a = q % g.nx, c = q / g.nx;
+    atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * xs[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Lock-step variant for several right-hand sides of one instance: one read of
 // every patch inverse serves up to kGroup PCG chains that run the same
 // five-kernel iteration (each chain its own vectors, scalars and state).
@@ -1372,8 +1490,14 @@ void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, 
 template <typename TC, typename TS, typename TR, int kFused>
 void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                     const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
-                    const float* rscale, cudaStream_t s) {
+                    const float* rscale, cudaStream_t s, BandRef band = {}) {
   TG_COUNT(1);
+  if (shape == kShapeBand && band.p) {
+    launch(k_smoother_band<TC, TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps), 0,
+           s, geo, npatch, (const TC*)band.p, band.ldb, band.stride, r, zacc, (TC)eta, n, st, fa);
+    return;
+  }
+  if (shape == kShapeBand) shape = 0;
   constexpr bool kHalf = std::is_same<TS, __half>::value;
   // the TMA ring has no row scaling and no residual-fused mode
   if ((kHalf || kFused == 2) && shape == 4) shape = 0;
@@ -1419,27 +1543,28 @@ void smoother_prepare() {
 template <typename TC, typename TS, typename TR>
 void launch_smoother(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv, const TR* r,
                      TC* zacc, double eta, int n, const PcgState* st, cudaStream_t s, int shape,
-                     const float* rscale) {
+                     const float* rscale, BandRef band) {
   smoother_shape<TC, TS, TR, false>(shape, geo, gofs, npatch, ngroups, pinv, r, zacc, eta, n, st, FuseArgs{},
-                                    rscale, s);
+                                    rscale, s, band);
 }
 
 template <typename TC, typename TS>
 void launch_smoother_update(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                             const double* r_old, double* r_new, const double* q, double* x, const double* p,
                             TC* zacc, double eta, int n, int nc, int b, double* part, PcgState* st,
-                            cudaStream_t s, int shape, const float* rscale, TC* zclear) {
+                            cudaStream_t s, int shape, const float* rscale, TC* zclear, BandRef band) {
   FuseArgs fa{r_old, r_new, q, x, p, part, st, nc, b, zclear, nullptr, nullptr};
   smoother_shape<TC, TS, double, 1>(shape, geo, gofs, npatch, ngroups, pinv, r_old, zacc, eta, n, st, fa,
-                                    rscale, s);
+                                    rscale, s, band);
 }
 
 template <typename TC, typename TS>
 void launch_smoother_resid(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                            const double* r, const TC* zin, const TC* kin, TC* zout, double eta, int n, int nc, int b,
-                           const PcgState* st, cudaStream_t s, int shape, const float* rscale) {
+                           const PcgState* st, cudaStream_t s, int shape, const float* rscale, BandRef band) {
   FuseArgs fa{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nc, b, nullptr, zin, kin};
-  smoother_shape<TC, TS, double, 2>(shape, geo, gofs, npatch, ngroups, pinv, r, zout, eta, n, st, fa, rscale, s);
+  smoother_shape<TC, TS, double, 2>(shape, geo, gofs, npatch, ngroups, pinv, r, zout, eta, n, st, fa, rscale, s,
+                                    band);
 }
 template <typename TC, typename TS, int kFused, int kCB, int kR>
 int smoother_multi_per_sm() {
@@ -1527,34 +1652,34 @@ void launch_set_condition_any(cudaGraphConditionalHandle cond, const PcgState* c
 
 template void launch_smoother_resid<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                     const double*, const double*, const double*, double*, double,
-                                                    int, int, int, const PcgState*, cudaStream_t, int, const float*);
+                                                    int, int, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother_resid<float, float>(const PatchGeo*, const int*, int, int, const float*, const double*,
                                                   const float*, const float*, float*, double, int, int, int,
-                                                  const PcgState*, cudaStream_t, int, const float*);
+                                                  const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother_resid<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
                                                           const __nv_bfloat16*, const double*, const float*,
                                                           const float*, float*, double, int, int, int,
-                                                          const PcgState*, cudaStream_t, int, const float*);
+                                                          const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother_resid<float, __half>(const PatchGeo*, const int*, int, int, const __half*,
                                                    const double*, const float*, const float*, float*, double, int,
-                                                   int, int, const PcgState*, cudaStream_t, int, const float*);
+                                                   int, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother_update<double, double>(const PatchGeo*, const int*, int, int, const double*,
                                                      const double*, double*, const double*, double*,
                                                      const double*, double*, double, int, int, int, double*,
-                                                     PcgState*, cudaStream_t, int, const float*, double*);
+                                                     PcgState*, cudaStream_t, int, const float*, double*, BandRef);
 template void launch_smoother_update<float, float>(const PatchGeo*, const int*, int, int, const float*,
                                                    const double*, double*, const double*, double*,
                                                    const double*, float*, double, int, int, int, double*,
-                                                   PcgState*, cudaStream_t, int, const float*, float*);
+                                                   PcgState*, cudaStream_t, int, const float*, float*, BandRef);
 template void launch_smoother_update<float, __nv_bfloat16>(const PatchGeo*, const int*, int, int,
                                                            const __nv_bfloat16*, const double*, double*,
                                                            const double*, double*, const double*, float*, double,
                                                            int, int, int, double*, PcgState*, cudaStream_t, int,
-                                                           const float*, float*);
+                                                           const float*, float*, BandRef);
 template void launch_smoother_update<float, __half>(const PatchGeo*, const int*, int, int, const __half*,
                                                     const double*, double*, const double*, double*, const double*,
                                                     float*, double, int, int, int, double*, PcgState*, cudaStream_t,
-                                                    int, const float*, float*);
+                                                    int, const float*, float*, BandRef);
 
 template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
@@ -1569,19 +1694,19 @@ template void launch_pcg_apply_p<float>(const float*, const double*, double*, do
                                         double*, PcgState*, int, cudaStream_t);
 
 template void launch_smoother<double, double, double>(const PatchGeo*, const int*, int, int, const double*, const double*, double*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, float, double>(const PatchGeo*, const int*, int, int, const float*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, float, float>(const PatchGeo*, const int*, int, int, const float*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, __nv_bfloat16, double>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, __nv_bfloat16, float>(const PatchGeo*, const int*, int, int, const __nv_bfloat16*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, __half, double>(const PatchGeo*, const int*, int, int, const __half*, const double*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 template void launch_smoother<float, __half, float>(const PatchGeo*, const int*, int, int, const __half*, const float*, float*,
-                                      double, int, const PcgState*, cudaStream_t, int, const float*);
+                                      double, int, const PcgState*, cudaStream_t, int, const float*, BandRef);
 
 template <typename TC, typename TS>
 void launch_resid_restrict(const CoarseSpace& cs, double* part, int nblocks, int nc, int b, int n, const double* r,

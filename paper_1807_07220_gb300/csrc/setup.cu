@@ -322,6 +322,35 @@ __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const Pa
   }
 }
 
+// band factor of compact patch c (band rows L[j][d] = L_{j, j-d}) in the
+// smoother's two padded band layouts at out + ids[c] * stride: column layout
+// (entry (j, d >= 1) = L_{j+d, j}) then row layout (entry (j, d >= 1) =
+// L_{j, j-d}); entry (j, 0) = 1 / L_jj in both, zero outside the matrix
+template <typename TB>
+__global__ void k_store_band(const double* __restrict__ band, const int4* __restrict__ rects,
+                             const int* __restrict__ ids, int wmax, int nmax, long long stride, TB* __restrict__ out) {
+  const int c = blockIdx.x;
+  const int4 r = rects[c];
+  const int nloc = r.z * r.w, ldb = wmax + 1;
+  const double* B = band + (long long)c * nmax * ldb;
+  TB* O = out + (long long)(ids ? ids[c] : c) * stride;
+  const long long tot = (long long)(nmax + 2 * kBandPad) * kBandLd;
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int j = (int)(t / kBandLd) - kBandPad, d = (int)(t % kBandLd);
+    double vc = 0.0, vr = 0.0;
+    if (j >= 0 && j < nloc && d < ldb) {
+      if (d == 0) {
+        vc = vr = 1.0 / B[(long long)j * ldb];
+      } else {
+        if (j + d < nloc) vc = B[(long long)(j + d) * ldb + d];   // L_{j+d, j}
+        if (j - d >= 0) vr = B[(long long)j * ldb + d];           // L_{j, j-d}
+      }
+    }
+    O[t] = (TB)vc;
+    O[tot + t] = (TB)vr;
+  }
+}
+
 // flag[m] = 1 if any cell of rectangle m (cells x0 <= i <= x0 + nx,
 // y0 <= j <= y0 + ny) gets a new inverse permeability: 1/kappa computed as
 // k_kinv does, compared bit for bit with the stored value
@@ -1325,6 +1354,16 @@ void launch_band_inverse(const double* band, const int4* rects, int first, int c
   cudaFuncSetAttribute(k_band_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   k_band_inverse<<<dim3(count, split), threads, shm, s>>>(band, rects, slot, first, wmax, nmax, scratch);
 }
+template <typename TB>
+void launch_store_band(const double* band, const int4* rects, const int* ids, int count, int wmax, int nmax,
+                       long long stride, TB* out, cudaStream_t s) {
+  if (count == 0) return;
+  k_store_band<TB><<<count, 256, 0, s>>>(band, rects, ids, wmax, nmax, stride, out);
+}
+template void launch_store_band<double>(const double*, const int4*, const int*, int, int, int, long long, double*,
+                                        cudaStream_t);
+template void launch_store_band<float>(const double*, const int4*, const int*, int, int, int, long long, float*,
+                                       cudaStream_t);
 void launch_rect_changed(const double* kappa, const double* kinv_old, const int4* rects, int nrect, int n,
                          unsigned char* flag, cudaStream_t s) {
   if (nrect == 0) return;

@@ -72,9 +72,9 @@ def test_batch_matches_direct_and_single_solves(tg, prec):
         tg.tg_destroy_batch(batch)
 
 
-def _run_batch(tg, kd, specs, fs, nrhs, prec, lockstep, rtol):
+def _run_batch(tg, kd, specs, fs, nrhs, prec, lockstep, rtol, **extra):
     dev = "cuda"
-    opts = tg.default_options(precision=prec, flexible=int(prec != "f64"), batch_lockstep=lockstep)
+    opts = tg.default_options(precision=prec, flexible=int(prec != "f64"), batch_lockstep=lockstep, **extra)
     stream = torch.cuda.current_stream().cuda_stream
     batch = tg.tg_setup_batch(kd, [s[0] for s in specs], [s[1] for s in specs], 10.0, nrhs, options=opts,
                               stream=stream)
@@ -112,4 +112,21 @@ def test_lockstep_groups_match_independent_chains(tg, prec):
         for r in range(nrhs):
             u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
             assert rel(u_l[j], u_ref) < 1e-8 and rel(u_i[j], u_ref) < 1e-8, (j, rel(u_l[j], u_ref))
+            j += 1
+
+
+def test_lockstep_batch_with_band_smoother(tg):
+    """Lock-step groups whose handles use the band smoother (tile shape 7,
+    one band sweep per chain inside the group) reach the direct solution."""
+    specs = [(32, 8, 1e4, 1), (48, 16, 1e5, 3)]
+    nrhs = 3
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device="cuda").contiguous() for k in kappas]
+    fs = [inputs.random_pairs(n, 1, 70 * seed + r) for (n, b, c, seed) in specs for r in range(nrhs)]
+    it, u = _run_batch(tg, kd, specs, fs, nrhs, "f32", 1, 1e-12, smoother_shape=7)
+    j = 0
+    for (n, b, c, seed), k in zip(specs, kappas):
+        for r in range(nrhs):
+            u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
+            assert rel(u[j], u_ref) < 1e-8, (j, rel(u[j], u_ref))
             j += 1

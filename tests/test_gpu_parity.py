@@ -169,10 +169,13 @@ def test_additive_cycle_mixed_precision(tg):
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f16"])
 def test_smoother_tile_shapes(tg, prec):
     """Every smoother tile shape (16- or 8-byte loads, 2 or 4 rows per pass,
-    TMA ring, software-pipelined passes) computes the same smoother: against shape 0 to FP32 summation
-    order (same stored inverses), against the oracle to the storage
-    precision; a solve with each shape matches the direct solve; the
-    autotuner reports a timed shape."""
+    TMA ring, software-pipelined passes) computes the same smoother: against
+    shape 0 to FP32 summation order (same stored inverses), against the
+    oracle to the storage precision.  The band shape (7: triangular solves
+    with the band Cholesky factors in the arithmetic precision) matches the
+    oracle to FP64 rounding (FP64 handles) or FP32 rounding amplified by the
+    factor's condition (the others).  A solve with each shape matches the
+    direct solve; the autotuner reports a timed shape."""
     n, b, kf = CASES["32x32_b8_channels"]
     kappa = kf(n)
     o = TwoGridSolver(n, b, kappa, tol=10.0)
@@ -183,14 +186,16 @@ def test_smoother_tile_shapes(tg, prec):
     f = inputs.quarter_five_spot(n)
     u_ref, _ = solve_direct(Grid(n, b), kappa, f)
     tol_oracle = {"f64": 1e-9, "f32": 2e-5, "bf16": 2e-2, "f16": 5e-3}[prec]
+    tol_band = 1e-9 if prec == "f64" else 1e-4
     outs = {}
-    for shape in range(7):
+    for shape in range(8):
         s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), smoother_shape=shape)
         try:
             z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
             tg.tg_apply_smoother(s.h, rho, z)
             outs[shape] = o.C @ interior_from_psi(n, z.cpu().numpy())
-            assert rel(outs[shape], ref) < tol_oracle, (prec, shape, rel(outs[shape], ref))
+            tol = tol_band if shape == 7 else tol_oracle
+            assert rel(outs[shape], ref) < tol, (prec, shape, rel(outs[shape], ref))
             it, rep = s.solve(f, rtol=1e-12)
             got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
             ran = 0 if (prec == "f16" and shape == 4) else shape       # FP16 has no TMA ring
@@ -203,7 +208,7 @@ def test_smoother_tile_shapes(tg, prec):
     try:
         it, rep = s.solve(f, rtol=1e-8)
         times = rep.shape_times()
-        tried = {"f64": [0, 4], "f16": [0, 1, 2, 3, 5, 6]}.get(prec, [0, 1, 2, 3, 4, 5, 6])
+        tried = {"f64": [0, 4, 7], "f16": [0, 1, 2, 3, 5, 6, 7]}.get(prec, [0, 1, 2, 3, 4, 5, 6, 7])
         assert all(times[k] > 0 for k in tried)
         assert rep.smoother_shape in tried and times[rep.smoother_shape] == min(times[k] for k in tried)
     finally:
