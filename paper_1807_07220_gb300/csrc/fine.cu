@@ -715,6 +715,11 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
 // n_loc (w + 1) values against n_loc^2 for the dense inverse.
 constexpr int kBandWarps = 4;   // patches per CTA
 constexpr int kBandPF = 8;      // rows of band entries in flight per lane
+// the sweeps round n_loc up to a multiple of kBandPF and read kBandPF rows
+// ahead: the rows they touch must stay inside the shared residual and the
+// padded band layouts
+static_assert(kPatchLd % kBandPF == 0, "row rounding must stay inside the shared residual");
+static_assert(kBandPad >= 2 * kBandPF, "read-ahead plus rounding must stay inside the band padding");
 template <typename TC, typename TR, int kFused>
 __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGeo* __restrict__ geo, int npatch,
                                                                    const TC* __restrict__ band, int ldb,
