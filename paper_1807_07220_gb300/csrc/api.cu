@@ -651,7 +651,10 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   const TS* pinv = (const TS*)h->pinv;
   const double eta = h->opt.eta;
   PcgState* st = c->st;
-  if (h->opt.m1 == 1 && h->opt.m2 == 1 && h->opt.cycle == TG_CYCLE_TWO_GRID) {
+  // the five-kernel form gathers r - K z per patch node inside the last
+  // sweep; the band sweep (one warp per patch) gathers better from a
+  // separately formed residual, so band handles take the general form
+  if (h->opt.m1 == 1 && h->opt.m2 == 1 && h->opt.cycle == TG_CYCLE_TWO_GRID && h->shape != kShapeBand) {
     // The cycle of Section 6 (m1 = m2 = 1) in five kernels.  z ends every
     // iteration in zacc (A); zacc2 (B) holds the intermediate z.  The first
     // sweep accumulates into B and clears A (dead once p is formed), the
@@ -769,6 +772,10 @@ int add_chain_t(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
 template <typename TC, typename TS>
 void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) {
   tg_handle* h = cs[0]->h;
+  if (h->shape == kShapeBand) {   // no lock-step band sweep: each chain's own iteration
+    for (int i = 0; i < k; ++i) enqueue_iteration<TC, TS>(cs[i], parity, s);
+    return;
+  }
   const int n = h->n;
   const TC* kin = std::is_same<TC, double>::value ? (const TC*)h->kinv : (const TC*)h->kinv32;
   const TS* pinv = (const TS*)h->pinv;
@@ -785,17 +792,8 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
     m1[i] = ChainPtrs{r_old, r_new, c->q, c->x, p_new, c->part, c->st, zA, nullptr, nullptr, r_old, zB};
     m2[i] = ChainPtrs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->st, nullptr, zB, kin, r_new, zA};
   }
-  // the band sweep has no lock-step form: one band sweep per chain
-  const bool band = (h->shape == kShapeBand);
-  if (band) {
-    for (int i = 0; i < k; ++i)
-      launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1[i].r_old, m1[i].r_new,
-                                     m1[i].q, m1[i].x, m1[i].p, (TC*)m1[i].zacc, h->opt.eta, n, h->nc, h->b,
-                                     m1[i].part, m1[i].st, s, h->shape, h->rscale, (TC*)m1[i].zclear, h->band);
-  } else {
-    launch_smoother_multi<TC, TS>(1, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1, k, h->opt.eta, n, h->nc,
-                                  h->b, s, h->shape, h->rscale);
-  }
+  launch_smoother_multi<TC, TS>(1, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1, k, h->opt.eta, n, h->nc,
+                                h->b, s, h->shape, h->rscale);
   if (h->cs.D > 0) {
     for (int i = 0; i < k; ++i) {
       Ctx* c = cs[i];
@@ -805,15 +803,8 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
       launch_coarse_correct<TC, tile_t<TS>>(h->cs, c->cs_part, c->cs_coefs, h->nblocks, h->nc, h->b, n, zB, c->st, s);
     }
   }
-  if (band) {
-    for (int i = 0; i < k; ++i)
-      launch_smoother_resid<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2[i].r, (const TC*)m2[i].zin,
-                                    kin, (TC*)m2[i].zacc, h->opt.eta, n, h->nc, h->b, m2[i].st, s, h->shape,
-                                    h->rscale, h->band);
-  } else {
-    launch_smoother_multi<TC, TS>(2, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2, k, h->opt.eta, n, h->nc,
-                                  h->b, s, h->shape, h->rscale);
-  }
+  launch_smoother_multi<TC, TS>(2, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2, k, h->opt.eta, n, h->nc,
+                                h->b, s, h->shape, h->rscale);
   for (int i = 0; i < k; ++i) {
     Ctx* c = cs[i];
     const double* r_new = parity ? c->r : c->r2;
@@ -1323,6 +1314,11 @@ int autotune_smoother_t(tg_handle* h) {
   for (int i = 0; i < ncand && !rc; ++i) {
     const int shape = cand[i];
     auto go = [&]() {
+      // the band form runs from a separately formed residual: time that launch with it
+      if (shape == kShapeBand)
+        launch_residual<TC>(h->kinv, z, (const TC*)(std::is_same<TC, double>::value ? (const void*)h->kinv
+                                                                                     : (const void*)h->kinv32),
+                            rin, h->n, nullptr, s);
       launch_smoother<TC, TS, TC>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, (const TS*)h->pinv, rin, z,
                                   h->opt.eta, h->n, nullptr, s, shape, h->rscale, h->band);
     };
