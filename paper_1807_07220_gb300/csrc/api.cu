@@ -1005,7 +1005,7 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
       return TG_ERR_OOM;
     // band factors for the band smoother: FP64 handles in FP64, the others in FP32
     h->band.ldb = kBandLd;
-    h->band.stride = 2LL * (nmax + 2 * kBandPad) * kBandLd;   // column and row layouts
+    h->band.stride = 2LL * band_rows(nmax) * kBandLd;   // column and row layouts
     const size_t esz = (h->opt.precision == TG_PREC_F64) ? sizeof(double) : sizeof(float);
     TG_CK(cudaMalloc(&h->pband, std::max<size_t>(1, (size_t)h->npatch * h->band.stride * esz)));
     h->band.p = h->pband;

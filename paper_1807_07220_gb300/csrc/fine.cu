@@ -709,17 +709,41 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
 // One warp per patch: the residual is gathered into shared memory, then both
 // sweeps are right-looking: lane 0 forms the row's value from its pending
 // sum, broadcasts it, and lane d adds its band entry's term to the pending
-// sum of row j + d (forward) or j - d (backward), held in its registers.  Lane d's band entries are loaded kBandPF rows ahead (they
-// do not depend on the sweep), so the chain from row to row is a
-// subtraction, a product and two shuffles.  The factor is read once per sweep:
-// n_loc (w + 1) values against n_loc^2 for the dense inverse.
+// sum of row j + d (forward) or j - d (backward), held in its registers.
+// Lane d loads entry d of four rows at once (the layouts interleave rows in
+// groups of four) and keeps 16 rows in flight (8 for FP64, whose wider
+// registers would otherwise cost the single wave of patches; the entries do
+// not depend on the sweep), so the chain from row to row is a subtraction, a product and
+// two shuffles.  The factor is read once per sweep: n_loc (w + 1) values
+// against n_loc^2 for the dense inverse.
 constexpr int kBandWarps = 4;   // patches per CTA
-constexpr int kBandPF = 8;      // rows of band entries in flight per lane
-// the sweeps round n_loc up to a multiple of kBandPF and read kBandPF rows
-// ahead: the rows they touch must stay inside the shared residual and the
-// padded band layouts
+template <typename TC>
+constexpr int kBandGroupsOf = sizeof(TC) == 8 ? kBandPF / 8 : kBandPF / 4;   // row groups in flight per lane
+// the sweeps round n_loc up to a multiple of kBandPF: the rows they touch
+// must stay inside the shared residual
 static_assert(kPatchLd % kBandPF == 0, "row rounding must stay inside the shared residual");
-static_assert(kBandPad >= 2 * kBandPF, "read-ahead plus rounding must stay inside the band padding");
+template <typename TC>
+struct BandQuad {
+  TC v[4];
+};
+__device__ __forceinline__ BandQuad<float> band_quad(const float* p) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ BandQuad<double> band_quad(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+// lanes past the stored band load nothing and hold zeros
+template <typename TC>
+__device__ __forceinline__ void band_quad_if(bool ln, const TC* p, BandQuad<TC>& q) {
+  if (ln) {
+    q = band_quad(p);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q.v[k] = (TC)0;
+  }
+}
 template <typename TC, typename TR, int kFused>
 __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGeo* __restrict__ geo, int npatch,
                                                                    const TC* __restrict__ band, int ldb,
@@ -772,49 +796,62 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGe
   // of row j + 1 + d (forward) or j - 1 - d (backward); a shuffle down by one
   // lane moves them along as the sweep advances.  Lane d reads entry (j, d) of
   // the column layout (L_{j+d, j}) in the forward sweep and of the row layout
-  // (L_{j, j-d}) in the backward one: one coalesced row per step; the padded
-  // layouts make every read in range and zero outside the band.
+  // (L_{j, j-d}) in the backward one, four rows per load; the padded layouts
+  // make every read in range and zero outside the band.
   const bool ln = (lane < ldb);   // lanes past the stored band read nothing
-  const TC* L0 = Lc + (long long)kBandPad * ldb + (ln ? lane : 0);   // entry (0, lane)
+  const long long gs = 4LL * ldb; // one group of four rows
+  constexpr int kG = kBandGroupsOf<TC>, kRows = 4 * kG;   // nrow is a multiple of kRows
+  static_assert(kBandPF % kRows == 0, "rows per pass must divide the row rounding");
   {
-    TC pf[kBandPF];
+    // group holding rows 0..3, lane's entries
+    const TC* G0 = Lc + (long long)(kBandPad / 4) * gs + (ln ? 4 * lane : 0);
+    BandQuad<TC> pf[kG];
 #pragma unroll
-    for (int k = 0; k < kBandPF; ++k) pf[k] = ln ? L0[(long long)k * ldb] : (TC)0;
+    for (int i = 0; i < kG; ++i) band_quad_if(ln, G0 + i * gs, pf[i]);
     TC acc = (TC)0;
-    for (int j0 = 0; j0 < nrow; j0 += kBandPF) {
-      const TC* lp = L0 + (long long)(j0 + kBandPF) * ldb;
+    for (int j0 = 0; j0 < nrow; j0 += kRows) {
+      const TC* gp = G0 + (long long)(j0 / 4 + kG) * gs;
 #pragma unroll
-      for (int k = 0; k < kBandPF; ++k) {
-        const int j = j0 + k;
-        const TC cj = pf[k];
-        pf[k] = ln ? lp[(long long)k * ldb] : (TC)0;
-        TC y = (xs[j] - acc) * cj;             // meaningful in lane 0
-        y = __shfl_sync(0xffffffffu, y, 0);
-        if (lane == 0) xs[j] = y;
-        else acc = fma(cj, y, acc);
-        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      for (int i = 0; i < kG; ++i) {
+        const BandQuad<TC> cur = pf[i];
+        band_quad_if(ln, gp + i * gs, pf[i]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int j = j0 + 4 * i + k;
+          const TC cj = cur.v[k];
+          TC y = (xs[j] - acc) * cj;             // meaningful in lane 0
+          y = __shfl_sync(0xffffffffu, y, 0);
+          if (lane == 0) xs[j] = y;
+          else acc = fma(cj, y, acc);
+          acc = __shfl_down_sync(0xffffffffu, acc, 1);
+        }
       }
     }
   }
   __syncwarp();
   {
-    const TC* Lb = L0 + pstride / 2;   // row layout: entry (j, lane) = L_{j, j-lane} at Lb[j ldb]
-    TC pf[kBandPF];
+    // row layout, group holding rows nrow - 4 .. nrow - 1 (row j at v[j % 4])
+    const TC* H0 = Lc + pstride / 2 + (long long)((kBandPad + nrow) / 4 - 1) * gs + (ln ? 4 * lane : 0);
+    BandQuad<TC> pf[kG];
 #pragma unroll
-    for (int k = 0; k < kBandPF; ++k) pf[k] = ln ? Lb[(long long)(nrow - 1 - k) * ldb] : (TC)0;
+    for (int i = 0; i < kG; ++i) band_quad_if(ln, H0 - i * gs, pf[i]);
     TC acc = (TC)0;
-    for (int j0 = nrow - 1; j0 >= 0; j0 -= kBandPF) {
-      const TC* lp = Lb + (long long)(j0 - kBandPF) * ldb;
+    for (int j0 = nrow - 1; j0 >= 0; j0 -= kRows) {
+      const TC* gp = H0 - (long long)((nrow - 1 - j0) / 4 + kG) * gs;
 #pragma unroll
-      for (int k = 0; k < kBandPF; ++k) {
-        const int j = j0 - k;
-        const TC cj = pf[k];
-        pf[k] = ln ? lp[-(long long)k * ldb] : (TC)0;
-        TC x = (xs[j] - acc) * cj;             // meaningful in lane 0
-        x = __shfl_sync(0xffffffffu, x, 0);
-        if (lane == 0) xs[j] = x;
-        else acc = fma(cj, x, acc);
-        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      for (int i = 0; i < kG; ++i) {
+        const BandQuad<TC> cur = pf[i];
+        band_quad_if(ln, gp - i * gs, pf[i]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int j = j0 - 4 * i - k;
+          const TC cj = cur.v[3 - k];
+          TC x = (xs[j] - acc) * cj;             // meaningful in lane 0
+          x = __shfl_sync(0xffffffffu, x, 0);
+          if (lane == 0) xs[j] = x;
+          else acc = fma(cj, x, acc);
+          acc = __shfl_down_sync(0xffffffffu, acc, 1);
+        }
       }
     }
   }

@@ -325,7 +325,8 @@ __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const Pa
 // band factor of compact patch c (band rows L[j][d] = L_{j, j-d}) in the
 // smoother's two padded band layouts at out + ids[c] * stride: column layout
 // (entry (j, d >= 1) = L_{j+d, j}) then row layout (entry (j, d >= 1) =
-// L_{j, j-d}); entry (j, 0) = 1 / L_jj in both, zero outside the matrix
+// L_{j, j-d}); entry (j, 0) = 1 / L_jj in both, zero outside the matrix;
+// rows in groups of four, interleaved by entry (the order the sweeps load)
 template <typename TB>
 __global__ void k_store_band(const double* __restrict__ band, const int4* __restrict__ rects,
                              const int* __restrict__ ids, int wmax, int nmax, long long stride, TB* __restrict__ out) {
@@ -334,9 +335,10 @@ __global__ void k_store_band(const double* __restrict__ band, const int4* __rest
   const int nloc = r.z * r.w, ldb = wmax + 1;
   const double* B = band + (long long)c * nmax * ldb;
   TB* O = out + (long long)(ids ? ids[c] : c) * stride;
-  const long long tot = (long long)(nmax + 2 * kBandPad) * kBandLd;
+  const long long tot = stride / 2;   // one layout: band_rows(nmax) rows in groups of four
   for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int j = (int)(t / kBandLd) - kBandPad, d = (int)(t % kBandLd);
+    const int e = (int)(t % (4 * kBandLd));
+    const int j = (int)(t / (4 * kBandLd)) * 4 + (e & 3) - kBandPad, d = e >> 2;
     double vc = 0.0, vr = 0.0;
     if (j >= 0 && j < nloc && d < ldb) {
       if (d == 0) {
