@@ -63,10 +63,42 @@ __device__ __forceinline__ bool arrive_last_linear(double partial, double* part,
   return last;
 }
 
-__device__ __forceinline__ double sum_partials(const double* part, int m) {
-  double s = 0.0;
-  for (int k = threadIdx.x & 31; k < m; k += 32) s += __ldcg(part + k);
-  return warp_sum(s);
+// Sums K arrays of m partials (array k at part + k m) in the CTA that
+// arrived last, with all of its threads: thread t adds entries t, t + T, ...
+// of every array (the loads of one pass issued before its adds), then one
+// block-wide tree.  The order is fixed by m and the block size, so the sums
+// are reproducible.  Every thread of the CTA must call it; out is valid in
+// thread 0.
+template <int K>
+__device__ __forceinline__ void block_sum_partials(const double* part, int m, double (&out)[K]) {
+  __shared__ double shp[K][32];
+  double s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.0;
+  int t = threadIdx.x;
+  for (; t + 3 * (int)blockDim.x < m; t += 4 * blockDim.x) {
+    double v[K][4];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[k][u] = __ldcg(part + (long long)k * m + t + u * blockDim.x);
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+  }
+  for (; t < m; t += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] += __ldcg(part + (long long)k * m + t);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    s[k] = warp_sum(s[k]);
+    if (l == 0) shp[k][w] = s[k];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = warp_sum(l < nw ? shp[k][l] : 0.0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -114,11 +146,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double* __restrict_
 }
 
 // q = K p_new with p_new = z_prev + beta p_old formed on the fly in a shared
-// (32+2) x (8+2) halo tile (each p_new value computed once), p_new and q
+// (32+2) x (8R+2) halo tile (each p_new value computed once), p_new and q
 // written, z_next zeroed for the coming smoother accumulation, and
-// alpha = rz / (p_new, q) by the last CTA.
+// alpha = rz / (p_new, q) by the last CTA.  Each thread takes R nodes of a
+// column (rows ty, ty + 8, ...): on GB300 the kernel is bound by the FP64
+// pipe, and R > 1 spreads the CTA's FP64 sum and the halo over more nodes.
 constexpr int kTx = 32, kTy = 8;
-template <typename TC>
+template <typename TC, int R>
 __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__ zprev,
                                                           const double* __restrict__ pold,
                                                           double* __restrict__ pnew, double* __restrict__ q,
@@ -127,11 +161,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
                                                           PcgState* st, int n) {
   pdl_entry();
   if (st->done) return;
-  __shared__ double P[kTy + 2][kTx + 2];
+  constexpr int kRows = kTy * R;
+  __shared__ double P[kRows + 2][kTx + 2];
   __shared__ double sh[32];
   const double beta = st->beta;
-  const int i0 = blockIdx.x * kTx, j0 = blockIdx.y * kTy;
-  for (int t = threadIdx.x; t < (kTx + 2) * (kTy + 2); t += blockDim.x) {
+  const int i0 = blockIdx.x * kTx, j0 = blockIdx.y * kRows;
+  for (int t = threadIdx.x; t < (kTx + 2) * (kRows + 2); t += blockDim.x) {
     const int a = t % (kTx + 2), c = t / (kTx + 2);
     const int i = i0 - 1 + a, j = j0 - 1 + c;
     double v = 0.0;
@@ -142,41 +177,48 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
     P[c][a] = v;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTx, ty = threadIdx.x / kTx;
-  const int i = i0 + tx, j = j0 + ty;
+  const int tx = threadIdx.x % kTx, ty0 = threadIdx.x / kTx;
+  const int i = i0 + tx;
+  const long long nn = (long long)n * n;
+  // K p with the node coefficients (c0, cE, cN, cNE, cNW); the west, south,
+  // south-west and south-east couplings are the neighbours' east, north,
+  // north-east and north-west ones (K is symmetric)
+  const double* c0 = kcoef;
+  const double* cE = kcoef + nn;
+  const double* cN = kcoef + 2 * nn;
+  const double* cNE = kcoef + 3 * nn;
+  const double* cNW = kcoef + 4 * nn;
   double acc = 0.0;
-  if (i < n && j < n) {
-    const long long id = (long long)j * n + i, nn = (long long)n * n;
-    const double p0 = P[ty + 1][tx + 1];
-    double qv = 0.0;
-    if (i >= 1 && j >= 1) {
-      // K p with the node coefficients (c0, cE, cN, cNE, cNW); the west, south,
-      // south-west and south-east couplings are the neighbours' east, north,
-      // north-east and north-west ones (K is symmetric)
-      const double* c0 = kcoef;
-      const double* cE = kcoef + nn;
-      const double* cN = kcoef + 2 * nn;
-      const double* cNE = kcoef + 3 * nn;
-      const double* cNW = kcoef + 4 * nn;
-      qv = c0[id] * p0;
-      qv = fma(cE[id], P[ty + 1][tx + 2], qv);
-      qv = fma(cN[id], P[ty + 2][tx + 1], qv);
-      qv = fma(cNE[id], P[ty + 2][tx + 2], qv);
-      qv = fma(cNW[id], P[ty + 2][tx], qv);
-      qv = fma(cE[id - 1], P[ty + 1][tx], qv);
-      qv = fma(cN[id - n], P[ty][tx + 1], qv);
-      qv = fma(cNE[id - n - 1], P[ty][tx], qv);
-      qv = fma(cNW[id - n + 1], P[ty][tx + 2], qv);
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int ty = ty0 + kTy * u, j = j0 + ty;
+    if (i < n && j < n) {
+      const long long id = (long long)j * n + i;
+      const double p0 = P[ty + 1][tx + 1];
+      double qv = 0.0;
+      if (i >= 1 && j >= 1) {
+        qv = c0[id] * p0;
+        qv = fma(cE[id], P[ty + 1][tx + 2], qv);
+        qv = fma(cN[id], P[ty + 2][tx + 1], qv);
+        qv = fma(cNE[id], P[ty + 2][tx + 2], qv);
+        qv = fma(cNW[id], P[ty + 2][tx], qv);
+        qv = fma(cE[id - 1], P[ty + 1][tx], qv);
+        qv = fma(cN[id - n], P[ty][tx + 1], qv);
+        qv = fma(cNE[id - n - 1], P[ty][tx], qv);
+        qv = fma(cNW[id - n + 1], P[ty][tx + 2], qv);
+      }
+      pnew[id] = p0;
+      q[id] = qv;
+      znext[id] = (TC)0;
+      acc = fma(p0, qv, acc);
     }
-    pnew[id] = p0;
-    q[id] = qv;
-    znext[id] = (TC)0;
-    acc = p0 * qv;
   }
   acc = block_sum(acc, sh);
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-  if (arrive_last_linear(acc, part, &st->counter[0], bid, nblk) && threadIdx.x < 32) {
-    const double pq = sum_partials(part, nblk);
+  if (arrive_last_linear(acc, part, &st->counter[0], bid, nblk)) {
+    double sum[1];
+    block_sum_partials<1>(part, nblk, sum);
+    const double pq = sum[0];
     if (threadIdx.x == 0) {
       st->counter[0] = 0;
       st->pq = pq;
@@ -205,8 +247,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
   if (st->done) return;
   const long long nn = (long long)n * n;
   double a = 0.0, b = 0.0, c = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // four grid strides per pass, all loads issued before the sums (same
+  // order of the sums as one stride at a time)
+  for (; t + 3 * stride < nn; t += 4 * stride) {
+    double zv[4], rv[4], qv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zv[u] = (double)z[t + u * stride];
+      rv[u] = r[t + u * stride];
+      qv[u] = q[t + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a += rv[u] * zv[u];
+      b += zv[u] * qv[u];
+      c += rv[u] * rv[u];
+    }
+  }
+  for (; t < nn; t += stride) {
     const double zv = (double)z[t], rv = r[t];
     a += rv * zv;
     b += zv * q[t];
@@ -236,10 +296,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
     part[gridDim.x + blockIdx.x] = b;
     part[2 * gridDim.x + blockIdx.x] = c;
   }
-  if (arrive_last(a, part, &st->counter[2]) && threadIdx.x < 32) {
-    const double rz = sum_partials(part, gridDim.x);
-    const double zq = sum_partials(part + gridDim.x, gridDim.x);
-    const double rr = sum_partials(part + 2 * gridDim.x, gridDim.x);
+  if (arrive_last(a, part, &st->counter[2])) {
+    double sum[3];
+    block_sum_partials<3>(part, gridDim.x, sum);
+    const double rz = sum[0], zq = sum[1], rr = sum[2];
     if (threadIdx.x == 0) {
       st->counter[2] = 0;
       st->rr = rr;
@@ -306,8 +366,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x,
     acc += r[t] * r[t];
   }
   acc = block_sum(acc, sh);
-  if (arrive_last(acc, part, &st->counter[3]) && threadIdx.x < 32) {
-    const double rr = sum_partials(part, gridDim.x);
+  if (arrive_last(acc, part, &st->counter[3])) {
+    double sum[1];
+    block_sum_partials<1>(part, gridDim.x, sum);
+    const double rr = sum[0];
     if (threadIdx.x == 0) {
       st->counter[3] = 0;
       st->rr0 = rr;
@@ -346,9 +408,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init_warm(const double* __rest
   a = block_sum(a, sh);
   b = block_sum(b, sh);
   if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = b;
-  if (arrive_last(a, part, &st->counter[3]) && threadIdx.x < 32) {
-    const double rr = sum_partials(part, gridDim.x);
-    const double rr0 = sum_partials(part + gridDim.x, gridDim.x);
+  if (arrive_last(a, part, &st->counter[3])) {
+    double sum[2];
+    block_sum_partials<2>(part, gridDim.x, sum);
+    const double rr = sum[0], rr0 = sum[1];
     if (threadIdx.x == 0) {
       st->counter[3] = 0;
       st->rr0 = rr0;
@@ -381,8 +444,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restri
     acc += r[t] * zv;
   }
   acc = block_sum(acc, sh);
-  if (arrive_last(acc, part, &st->counter[3]) && threadIdx.x < 32) {
-    const double rz = sum_partials(part, gridDim.x);
+  if (arrive_last(acc, part, &st->counter[3])) {
+    double sum[1];
+    block_sum_partials<1>(part, gridDim.x, sum);
+    const double rz = sum[0];
     if (threadIdx.x == 0) {
       st->counter[3] = 0;
       st->rz = rz;
@@ -1727,8 +1792,20 @@ template <typename TC>
 void launch_pcg_apply_p(const TC* zprev, const double* pold, double* pnew, double* q, TC* znext,
                         const double* kcoef, double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
-  dim3 grid((n + kTx - 1) / kTx, (n + kTy - 1) / kTy);
-  launch(k_pcg_apply_p<TC>, dim3(grid), dim3(kThreads), 0, s, zprev, pold, pnew, q, znext, kcoef, part, st, n);
+  // rows per thread: the most that still leaves at least two CTAs per SM
+  const int gx = (n + kTx - 1) / kTx;
+  auto ctas = [&](int r) { return (long long)gx * ((n + kTy * r - 1) / (kTy * r)); };
+  const int sms = sm_count();
+  if (ctas(4) >= 2LL * sms) {
+    launch(k_pcg_apply_p<TC, 4>, dim3(gx, (n + 4 * kTy - 1) / (4 * kTy)), dim3(kThreads), 0, s, zprev, pold, pnew, q,
+           znext, kcoef, part, st, n);
+  } else if (ctas(2) >= 2LL * sms) {
+    launch(k_pcg_apply_p<TC, 2>, dim3(gx, (n + 2 * kTy - 1) / (2 * kTy)), dim3(kThreads), 0, s, zprev, pold, pnew, q,
+           znext, kcoef, part, st, n);
+  } else {
+    launch(k_pcg_apply_p<TC, 1>, dim3(gx, (n + kTy - 1) / kTy), dim3(kThreads), 0, s, zprev, pold, pnew, q, znext,
+           kcoef, part, st, n);
+  }
 }
 template void launch_pcg_apply_p<double>(const double*, const double*, double*, double*, double*, const double*,
                                          double*, PcgState*, int, cudaStream_t);
