@@ -63,6 +63,20 @@ __device__ __forceinline__ bool arrive_last_linear(double partial, double* part,
   return last;
 }
 
+// Exact float -> double from the IEEE 754 fields (sign kept, exponent
+// rebiased from 127 to 1023, the 23 fraction bits moved to the top of the 52)
+// on the integer pipe: the FP64 pipe, the bound of the kernels that widen a
+// preconditioned vector, stays free.  Zeros, subnormals, infinities and NaNs
+// take the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Sums K arrays of m partials (array k at part + k m) in the CTA that
 // arrived last, with all of its threads: thread t adds entries t, t + T, ...
 // of every array (the loads of one pass issued before its adds), then one
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
     double v = 0.0;
     if (i >= 1 && j >= 1 && i < n && j < n) {
       const long long id = (long long)j * n + i;
-      v = (double)zprev[id] + beta * pold[id];
+      v = widen(zprev[id]) + beta * pold[id];
     }
     P[c][a] = v;
   }
@@ -255,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
     double zv[4], rv[4], qv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      zv[u] = (double)z[t + u * stride];
+      zv[u] = widen(z[t + u * stride]);
       rv[u] = r[t + u * stride];
       qv[u] = q[t + u * stride];
     }
@@ -267,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
     }
   }
   for (; t < nn; t += stride) {
-    const double zv = (double)z[t], rv = r[t];
+    const double zv = widen(z[t]), rv = r[t];
     a += rv * zv;
     b += zv * q[t];
     c += rv * rv;
@@ -439,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init_rz(const double* __restri
   double acc = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
        t += (long long)gridDim.x * blockDim.x) {
-    const double zv = (double)z[t];
+    const double zv = widen(z[t]);
     p[t] = zv;
     acc += r[t] * zv;
   }
@@ -1510,11 +1524,14 @@ template void launch_residual<double>(const double*, const double*, const double
 template void launch_residual<float>(const double*, const float*, const float*, float*, int,
                                      const PcgState*, cudaStream_t);
 
+int sm_count();
 template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
                      cudaStream_t s) {
   TG_COUNT(1);
-  launch(k_pcg_dots<TC>, dim3(grid_for((long long)n * n)), dim3(kThreads), 0, s, r, z, q, part, st, n);
+  // FP64-pipe bound: two CTAs per SM, so fewer per-CTA FP64 tree sums
+  launch(k_pcg_dots<TC>, dim3(std::min(grid_for((long long)n * n), 2 * sm_count())), dim3(kThreads), 0, s, r, z, q,
+         part, st, n);
 }
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
   TG_COUNT(1);
