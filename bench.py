@@ -154,6 +154,33 @@ def band_smoother_bytes(n, b, ov, tc_bytes):
     return total
 
 
+FP64_PEAK_GFLOPS = 1250.0   # nominal dense FP64 rate of the part
+
+
+def operator_roofline(n, tc_bytes, op_ms, op_n, peaks, peak_src):
+    """Roofline of the PCG operator kernel (p = z + beta p, q = K p, (p, q),
+    alpha), timed with events around each launch.  On this part it is bound
+    by the FP64 pipe, so its arithmetic is reported against the nominal FP64
+    rate and its bytes against the measured copy bandwidth.  Algorithmic
+    FP64 work: 9 FMAs of K p per interior node, plus one FMA for p and one for
+    (p, q) per node; bytes: z (TC), p_old, five coefficient arrays read,
+    p_new, q (FP64) and the cleared z_next (TC) written, per node."""
+    if not op_n:
+        return None
+    sec = op_ms / op_n / 1e3
+    flops = 2.0 * (9 * (n - 1) ** 2 + 2 * n * n)
+    nbytes = float(n * n * (2 * tc_bytes + 8 + 40 + 16))
+    gflops = flops / sec / 1e9
+    gbs = nbytes / sec / 1e9
+    return {"kernel": "k_pcg_apply_p", "bound": "fp64", "achieved": gflops, "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": gflops / FP64_PEAK_GFLOPS,
+            "peak_source": "nominal FP64 rate (1.25 TFLOP/s)",
+            "hbm_achieved": gbs, "hbm_peak": peaks.get("hbm_gbs"),
+            "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "hbm_peak_source": peak_src,
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+            "avg_launch_us": sec * 1e6, "launches_timed": op_n}
+
+
 def smoother_bytes(n, b, ov, ts_bytes, tc_bytes):
     """Algorithmic bytes of one smoother launch: every patch inverse read once
     (nloc^2 entries), the residual gathered (FP64 or TC) and the correction
@@ -265,6 +292,8 @@ def run_ours(args):
     prof.close()
     sm_ms = sum(r.smoother_ms for r in prof_reps)
     sm_n = sum(r.smoother_launches for r in prof_reps)
+    op_ms = sum(r.operator_ms for r in prof_reps)
+    op_n = sum(r.operator_launches for r in prof_reps)
     ts_bytes = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[prec]
     tc_bytes = 8 if prec == "f64" else 4
     band = (shape == 7)
@@ -328,6 +357,7 @@ def run_ours(args):
                      "tile_shape": shape, "autotuner_us_per_shape": reps[-1].shape_times(),
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None,
                      "launches_timed": sm_n, "peak_source": peak_src},
+        "operator_roofline": operator_roofline(n, tc_bytes, op_ms, op_n, peaks, peak_src),
         "e2e": {"value": e_value, "unit": "DOF-solves/s", "ms_per_step": e_ms,
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * (n + 1) + n * n)},
         "clocks": clk,

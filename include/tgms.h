@@ -175,6 +175,9 @@ typedef struct tg_report {
   int update_rank[2];     /* last tg_update_kappa: rank of the low-rank update of the
                              coarse inverse ([0]) and of the coarse RT0 inverse ([1]);
                              -1: recomputed in full */
+  int operator_launches;  /* profile == 1: launches of the PCG operator kernel (p = z + beta p,
+                             q = K p, alpha) timed ... */
+  double operator_ms;     /* ... and their summed device time */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,

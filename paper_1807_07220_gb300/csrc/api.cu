@@ -100,6 +100,8 @@ struct Ctx {
   // profiling: events around smoother launches (profile == 1)
   std::vector<cudaEvent_t> prof_ev;
   int prof_used = 0;
+  std::vector<cudaEvent_t> prof_op_ev;   // and around the operator launches
+  int prof_op_used = 0;
 };
 
 int cuda_err(cudaError_t e) {
@@ -475,6 +477,8 @@ void ctx_free(Ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->prof_ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->prof_op_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -510,6 +514,9 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
     c->prof_ev.resize(2048);
     for (auto& e : c->prof_ev)
       if (!rc) rc = cuda_err(cudaEventCreate(&e));
+    c->prof_op_ev.resize(1024);
+    for (auto& e : c->prof_op_ev)
+      if (!rc) rc = cuda_err(cudaEventCreate(&e));
   }
   if (!rc) rc = cuda_err(cudaMemsetAsync(c->st, 0, sizeof(PcgState), h->stream));
   if (rc) {
@@ -523,6 +530,10 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
 // ---- the two-grid preconditioner (Section 5), zacc must be zero on entry ----
 void prof_mark(Ctx* c, cudaStream_t s) {
   if (c->h->opt.profile && c->prof_used < (int)c->prof_ev.size()) cudaEventRecord(c->prof_ev[c->prof_used++], s);
+}
+void prof_op_mark(Ctx* c, cudaStream_t s) {
+  if (c->h->opt.profile && c->prof_op_used < (int)c->prof_op_ev.size())
+    cudaEventRecord(c->prof_op_ev[c->prof_op_used++], s);
 }
 
 template <typename TC, typename TS>
@@ -662,7 +673,9 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
     // time and accumulates z_B + S(r - K z_B) into A.
     TC* zA = (TC*)c->zacc;
     TC* zB = (TC*)c->zacc2;
+    prof_op_mark(c, s);
     launch_pcg_apply_p<TC>(zA, p_old, p_new, c->q, zB, h->kcoef, c->part, st, n, s);
+    prof_op_mark(c, s);
     prof_mark(c, s);
     launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
                                    p_new, zB, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, zA, h->band);
@@ -680,7 +693,9 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   }
   TC* z_prev = (TC*)(parity ? c->zacc2 : c->zacc);
   TC* z_cur = (TC*)(parity ? c->zacc : c->zacc2);
+  prof_op_mark(c, s);
   launch_pcg_apply_p<TC>(z_prev, p_old, p_new, c->q, z_cur, h->kcoef, c->part, st, n, s);
+  prof_op_mark(c, s);
   prof_mark(c, s);
   launch_smoother_update<TC, TS>(h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, r_old, r_new, c->q, c->x,
                                  p_new, z_cur, eta, n, h->nc, h->b, c->part, st, s, h->shape, h->rscale, nullptr,
@@ -1729,6 +1744,7 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
   cudaEventRecord(c->ev[0], s);
   if (h->opt.profile) {
     c->prof_used = 0;
+    c->prof_op_used = 0;
     rc = run_loop(c, &launches);
   } else {
     cudaGraphExec_t& ex = c->warm ? c->exec_warm : c->exec;
@@ -1799,6 +1815,13 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
       }
       rep->smoother_ms = sm;
       rep->smoother_launches = c->prof_used / 2;
+      double om = 0.0;
+      for (int k = 0; k + 1 < c->prof_op_used; k += 2) {
+        cudaEventElapsedTime(&ms, c->prof_op_ev[k], c->prof_op_ev[k + 1]);
+        om += ms;
+      }
+      rep->operator_ms = om;
+      rep->operator_launches = c->prof_op_used / 2;
     } else {
       cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
       rep->pcg_ms = ms;  // whole graph

@@ -51,7 +51,7 @@ class tg_report(ctypes.Structure):
                 ("graph", c_int), ("snapshot_solves", c_int), ("fallback_faces", c_int),
                 ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 8),
                 ("refactored_patches", c_int), ("refactored_blocks", c_int),
-                ("update_rank", c_int * 2)]
+                ("update_rank", c_int * 2), ("operator_launches", c_int), ("operator_ms", c_double)]
 
     def shape_times(self):
         return [float(v) for v in self.shape_us]

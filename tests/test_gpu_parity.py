@@ -309,7 +309,10 @@ def test_warm_start(tg, prec, profile):
     u_ref, p_ref = solve_direct(g, kappa, f)
     s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), profile=profile)
     try:
-        it_cold, _ = s.solve(f, rtol=1e-10)
+        it_cold, rep_cold = s.solve(f, rtol=1e-10)
+        if profile:   # the host loop times every smoother and operator launch it enqueued
+            assert rep_cold.operator_launches in (it_cold, it_cold + 1) and rep_cold.operator_ms > 0
+            assert rep_cold.smoother_launches >= 2 * it_cold and rep_cold.smoother_ms > 0
         exact_x = dev(u_ref[: g.nxf].reshape(n, n + 1))
         it0, rep0 = s.solve(f, rtol=1e-10, ux0=exact_x)
         got = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
