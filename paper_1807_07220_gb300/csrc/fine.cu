@@ -174,7 +174,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
                                                           const double* __restrict__ kcoef, double* part,
                                                           PcgState* st, int n) {
   pdl_entry();
-  if (st->done) return;
+  // the stop flag is tested once the halo tile is loaded, so its load is not
+  // a round trip of its own (the vectors stay valid after convergence, and
+  // nothing global is written before the test)
+  const int done = st->done;
   constexpr int kRows = kTy * R;
   __shared__ double P[kRows + 2][kTx + 2];
   __shared__ double sh[32];
@@ -191,6 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_apply_p(const TC* __restrict__
     P[c][a] = v;
   }
   __syncthreads();
+  if (done) return;
   const int tx = threadIdx.x % kTx, ty0 = threadIdx.x / kTx;
   const int i = i0 + tx;
   const long long nn = (long long)n * n;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
                                                        const double* __restrict__ q,
                                                        double* part, PcgState* st, int n) {
   pdl_entry();
-  if (st->done) return;
+  const int done = st->done;   // tested after the loads (see k_pcg_apply_p)
   const long long nn = (long long)n * n;
   double a = 0.0, b = 0.0, c = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -286,6 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dots(const double* __restrict_
     b += zv * q[t];
     c += rv * rv;
   }
+  if (done) return;
   // the three CTA sums in one pass (one barrier instead of three block sums)
   {
     __shared__ double sh3[3][32];
@@ -655,7 +660,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
                                                        const PcgState* st, FuseArgs fa,
                                                        const float* __restrict__ rscale) {
   pdl_entry();
-  if (st && st->done) return;
+  const int done = st ? st->done : 0;   // tested after the first loads (see k_pcg_apply_p)
   __shared__ __align__(16) TC xs[kPatchLd];
   __shared__ double shr[32];
   const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
@@ -672,6 +677,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
   for (int t = threadIdx.x; t < npatch; t += blockDim.x)
     if (gofs[t] <= g0 && gofs[t + 1] > g0) sp = t;
   __syncthreads();
+  if (done) return;
   int p = sp;
   constexpr int W = kCB / (int)sizeof(TS);
   constexpr int kIter = (kPatchLd + 32 * W - 1) / (32 * W);
@@ -1283,7 +1289,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const int* __restri
                                                              double* __restrict__ part, int nc, int b,
                                                              int n, const PcgState* st) {
   pdl_entry();
-  if (st && st->done) return;
+  const int done = st ? st->done : 0;   // tested after the loads (see k_pcg_apply_p)
   __shared__ TC vals[kMaxB * kMaxB];
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int bb = b * b, t = threadIdx.x;
@@ -1293,6 +1299,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(const int* __restri
                                  : (TC)0;
   }
   __syncthreads();
+  if (done) return;
   // one warp per slot: no barrier per slot
   const int s0 = slot_ptr[blk], s1 = slot_ptr[blk + 1];
   const int warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
@@ -1438,7 +1445,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_prolong(const double* __res
                                                              const TS* __restrict__ owned, TC* __restrict__ v,
                                                              int nc, int b, int n, const PcgState* st) {
   pdl_entry();
-  if (st && st->done) return;
+  const int done = st ? st->done : 0;   // tested after the loads (see k_pcg_apply_p)
   __shared__ double cvec[kCoarseSplit];
   __shared__ double dloc[kFuseSlots];
   for (int u = threadIdx.x; u < D; u += blockDim.x) {
@@ -1451,6 +1458,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_prolong(const double* __res
     cvec[u] = sum;
   }
   __syncthreads();
+  if (done) return;
   const int blk = blockIdx.x, I = blk % nc, J = blk / nc;
   const int s0 = slot_ptr[blk], m = slot_ptr[blk + 1] - s0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
