@@ -11,11 +11,11 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle.fine import Grid, assemble, solve_direct, split_faces, curl_matrix, boundary_lift
+from oracle.fine import Grid, assemble, solve_direct, solve_direct_pinned, split_faces, curl_matrix, boundary_lift
 from oracle.coarse import (BlockSolvers, coarse_faces, face_blocks, fine_faces_on, jacobi_eigh,
                            snapshots, spectral_problem, solve_spectral)
 from oracle.twogrid import TwoGridSolver
-from paper_1807_07220_gb300.inputs import lognormal_field, random_pairs, quarter_five_spot
+from paper_1807_07220_gb300.inputs import channel_field, lognormal_field, random_pairs, quarter_five_spot
 
 
 # --------------------------------------------------------------------- fine system
@@ -151,6 +151,53 @@ def test_brute_force_dense_saddle():
     u, p = solve_direct(g, kappa, f)
     np.testing.assert_allclose(u[I], v, rtol=1e-10, atol=1e-14)
     np.testing.assert_allclose(p, p_phys, rtol=1e-10, atol=1e-14)
+
+
+def test_pinned_direct_solve():
+    """solve_direct_pinned (pressure constant fixed by a pinned cell, then
+    mean zero) reproduces the layered closed form with prescribed boundary
+    flux, the dense least-squares solution of the unbordered system, and the
+    bordered solve on a high-contrast channel field with a source pair."""
+    n, b = 16, 4
+    g = Grid(n, b)
+    kappa, bflux, krow = _layered_case(n, np.random.default_rng(1))
+    xc = (np.arange(n) + 0.5) / n
+    u, p = solve_direct_pinned(g, kappa, np.zeros((n, n)), bflux)
+    ux, uy = split_faces(g, u)
+    np.testing.assert_allclose(ux, -np.repeat(krow[:, None], n + 1, axis=1), rtol=1e-11)
+    assert np.abs(uy).max() < 1e-11 * krow.max()
+    np.testing.assert_allclose(p.reshape(n, n), np.tile(xc - xc.mean(), (n, 1)), atol=1e-11)
+    # brute force: dense least squares of the singular saddle system
+    n4 = 4
+    g4 = Grid(n4, 2)
+    k4 = lognormal_field(n4, 5, sigma=1.5)
+    f4 = random_pairs(n4, 2, 6)
+    A, B = assemble(g4, k4)
+    I = g4.interior_faces()
+    K = np.block([[A[I][:, I].toarray(), B[:, I].toarray().T], [B[:, I].toarray(), np.zeros((n4 * n4, n4 * n4))]])
+    x = np.linalg.lstsq(K, np.concatenate([np.zeros(I.size), g4.h ** 2 * f4.ravel()]), rcond=None)[0]
+    u4, p4 = solve_direct_pinned(g4, k4, f4)
+    np.testing.assert_allclose(u4[I], x[: I.size], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(p4, -(x[I.size:] - x[I.size:].mean()), rtol=1e-10, atol=1e-14)
+    # channels with point sources: exact mass balance, the reduced residual
+    # C^T A u at rounding level, and the bordered solve's solution (velocity
+    # compared at contrast 1e4; at 1e6 the two factorisations' velocities
+    # differ by conditioning, ~3e-9 here, while both residuals stay ~1e-14)
+    g32 = Grid(32, 8)
+    f32 = random_pairs(32, 3, 11)
+    F32 = g32.h ** 2 * f32.ravel()
+    C32, I32 = curl_matrix(g32), g32.interior_faces()
+    for contrast, utol in ((1e4, 1e-9), (1e6, 1e-7)):
+        k32 = channel_field(32, contrast, 9)
+        u1, p1 = solve_direct(g32, k32, f32)
+        u2, p2 = solve_direct_pinned(g32, k32, f32)
+        A32, B32 = assemble(g32, k32)
+        Au = (A32 @ u2)[I32]
+        assert np.abs(B32 @ u2 - F32).max() <= 1e-12 * np.abs(F32).max()
+        assert np.linalg.norm(C32.T @ Au) <= 1e-12 * np.linalg.norm(abs(C32.T) @ np.abs(Au))
+        assert np.linalg.norm(u2 - u1) <= utol * np.linalg.norm(u1)
+        assert np.linalg.norm(p2 - p1) <= 1e-12 * np.linalg.norm(p1)
+        assert abs(p2.sum()) <= 1e-12 * np.abs(p2).sum()
 
 
 def test_superconvergence_second_order():
