@@ -1,0 +1,131 @@
+"""Full-size checks of the CUDA solve, in the launch configurations that
+bench.py times (headline 256 x 256 BF16 arm; 512 x 512 BF16, where the
+operator kernel takes two rows per thread; 1024 x 1024 FP16, where the band
+smoother and four operator rows per thread are in use).
+
+The discrete solution (u, p) of the RT0/P0 system (Section 2) is fixed by
+  * mass balance B u = F on every cell,
+  * a vanishing reduced residual C^T A u on the interior faces (C the
+    discrete curl, so C^T B^T = 0: the momentum equation up to a gradient),
+  * the momentum equation A u = B^T p on the interior faces, with sum(p) = 0.
+Each is evaluated with the oracle's own matrices.  The reduced residual is
+measured against that of a particular solution built here (the source routed
+along the bottom row and the right column), which is independent of the CUDA
+path.  At 256 x 256 the solution is also compared with the oracle's sparse
+direct solve.  Bars: the FP64 oracle PCG at rtol 1e-12 on the 256 x 256
+workload reaches 9e-11 (velocity, energy norm), 7e-13 (pressure), 4e-13
+(momentum), 4e-14 (reduced residual over the particular solution's); the
+bars below leave about two orders of magnitude for the mixed-precision
+preconditioner and the GPU's rounding order.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.fine import Grid, assemble, curl_matrix, solve_direct_pinned  # noqa: E402
+from paper_1807_07220_gb300 import inputs  # noqa: E402
+
+CONTRAST, EIG_TOL, FIELD_SEED = 1e6, 10.0, 5
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import os
+    from paper_1807_07220_gb300 import build, tgms
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(tgms.LIB_PATH):
+        build.build_library()
+    tgms.lib()
+    return tgms
+
+
+def path_flow(g, F):
+    """A face field with B v = F for the quarter five-spot (source in cell
+    (0, 0), sink in cell (n-1, n-1)): the source's flux carried along the
+    bottom row of x-faces and up the right column of y-faces."""
+    q = F[0]
+    v = np.zeros(g.nf)
+    v[g.xface(np.arange(1, g.n), 0)] = q / g.h
+    v[g.yface(g.n - 1, np.arange(1, g.n))] = q / g.h
+    return v
+
+
+class Checks:
+    def __init__(self, n, b, kappa, f):
+        self.g = g = Grid(n, b)
+        self.A, self.B = assemble(g, kappa)
+        self.C = curl_matrix(g)
+        self.I = g.interior_faces()
+        self.F = g.h ** 2 * np.asarray(f, dtype=np.float64).ravel()
+        vp = path_flow(g, self.F)
+        assert np.abs(self.B @ vp - self.F).max() <= 1e-15 * np.abs(self.F).max()
+        self.path_res = np.linalg.norm(self.C.T @ (self.A @ vp)[self.I])
+
+    def measure(self, u, p):
+        Au = (self.A @ u)[self.I]
+        return {
+            "mass": np.abs(self.B @ u - self.F).max() / np.abs(self.F).max(),
+            "reduced": np.linalg.norm(self.C.T @ Au) / self.path_res,
+            "momentum": np.linalg.norm(Au - (self.B.T @ p)[self.I]) / np.linalg.norm(Au),
+            "mean_p": abs(p.sum()) / np.abs(p).sum(),
+        }
+
+
+def gpu_solve(tg, kappa, b, f, rtol, **opts):
+    s = tg.Solver(kappa, b, EIG_TOL, **opts)
+    try:
+        it, rep = s.solve(f, rtol=rtol)
+        torch.cuda.synchronize()
+        u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        p = s.p.cpu().numpy().ravel()
+        shape = rep.smoother_shape
+    finally:
+        s.close()
+    return it, rep, u, p, shape
+
+
+def check_tight(m):
+    assert m["mass"] <= 1e-12, m
+    assert m["reduced"] <= 1e-11, m
+    assert m["momentum"] <= 1e-10, m
+    assert m["mean_p"] <= 1e-12, m
+
+
+def test_headline_256_against_direct_solve(tg):
+    """256 x 256, b = 16, BF16 preconditioner, flexible CG (the headline
+    arm): at the benchmark's rtol 1e-8 converged and mass-exact; at rtol
+    1e-12 equal to the sparse direct solve."""
+    n, b = 256, 16
+    kappa = inputs.grf_channel_field(n, CONTRAST, FIELD_SEED)
+    f = inputs.quarter_five_spot(n)
+    chk = Checks(n, b, kappa, f)
+    it, rep, u, p, _ = gpu_solve(tg, kappa, b, f, 1e-8, precision="bf16", flexible=1)
+    m = chk.measure(u, p)
+    assert rep.converged == 1 and m["mass"] <= 1e-12 and m["reduced"] <= 1e-8, m
+    it, rep, u, p, _ = gpu_solve(tg, kappa, b, f, 1e-12, precision="bf16", flexible=1)
+    assert rep.converged == 1
+    m = chk.measure(u, p)
+    check_tight(m)
+    us, ps = solve_direct_pinned(chk.g, kappa, f)
+    e = u - us
+    err_a = np.sqrt(e @ (chk.A @ e)) / np.sqrt(us @ (chk.A @ us))
+    err_p = np.linalg.norm(p - ps) / np.linalg.norm(ps)
+    assert err_a <= 1e-8 and err_p <= 1e-8, (err_a, err_p, m)
+
+
+@pytest.mark.parametrize("n,prec", [(512, "bf16"), (1024, "f16")])
+def test_large_grids_properties(tg, n, prec):
+    """512 x 512 (operator at two rows per thread) and 1024 x 1024 (band
+    smoother where the autotuner picks it, operator at four rows per
+    thread): the properties that fix the discrete solution, at rtol 1e-12."""
+    b = 16
+    kappa = inputs.grf_channel_field(n, CONTRAST, FIELD_SEED)
+    f = inputs.quarter_five_spot(n)
+    chk = Checks(n, b, kappa, f)
+    it, rep, u, p, shape = gpu_solve(tg, kappa, b, f, 1e-12, precision=prec, flexible=1)
+    assert rep.converged == 1, (it, shape)
+    check_tight(chk.measure(u, p))
