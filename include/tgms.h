@@ -85,7 +85,9 @@ typedef struct tg_mlp tg_mlp;
 
 typedef struct tg_grid {
   int nx, ny;     /* fine cells per side; this release requires nx == ny */
-  int bx, by;     /* fine cells per coarse block side; bx == by, 2 <= b <= 16 */
+  int bx, by;     /* fine cells per coarse block side; bx == by, 2 <= b <= 16, b divides
+                     n and n / b >= 2 (a single coarse block has no coarse faces, so
+                     the coarse space of Section 4 would be empty: TG_ERR_INVALID_ARG) */
   int overlap;    /* oversampling of K_i^+ in fine cells (Section 6: 2), 1..2.  0 is
                      rejected (TG_ERR_INVALID_ARG): without oversampling the nodes on
                      the coarse grid lines lie in no patch, and the preconditioner

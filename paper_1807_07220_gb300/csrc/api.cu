@@ -453,6 +453,7 @@ int validate_grid(const tg_grid* g) {
   if (!g) return TG_ERR_INVALID_ARG;
   if (g->nx != g->ny || g->bx != g->by) return TG_ERR_UNSUPPORTED;
   if (g->nx < 2 || g->bx < 2 || g->nx % g->bx != 0) return TG_ERR_INVALID_ARG;
+  if (g->nx / g->bx < 2) return TG_ERR_INVALID_ARG;   // one coarse block: no coarse faces, empty coarse space
   if (g->bx > kMaxB) return TG_ERR_UNSUPPORTED;
   if (g->overlap < 1) return TG_ERR_INVALID_ARG;   // singular preconditioner (no patch covers the coarse lines)
   if (g->overlap > kMaxOverlap) return TG_ERR_UNSUPPORTED;

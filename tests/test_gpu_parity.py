@@ -362,6 +362,9 @@ def test_error_codes(tg):
     with pytest.raises(tg.TgmsError) as e:
         tg.Solver(np.ones((18, 18)), 4, 10.0)
     assert e.value.code == -1
+    with pytest.raises(tg.TgmsError) as e:           # one coarse block: no coarse faces
+        tg.Solver(np.ones((16, 16)), 16, 10.0)
+    assert e.value.code == -1
     with pytest.raises(tg.TgmsError) as e:           # no oversampling: singular preconditioner
         tg.Solver(kappa, 4, 10.0, overlap=0)
     assert e.value.code == -1
@@ -377,6 +380,48 @@ def test_error_codes(tg):
         assert e.value.code == -2
         it, rep = s.solve(inputs.quarter_five_spot(n), rtol=1e-8)
         assert rep.converged == 1
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16"])
+def test_zero_source(tg, prec):
+    """f = 0 with no boundary flux: the zero solution, reached with no PCG
+    iteration (the oracle's PCG also stops at once)."""
+    n, b, kf = CASES["32x32_b8_channels"]
+    s = tg.Solver(kf(n), b, 10.0, precision=prec, flexible=int(prec != "f64"))
+    try:
+        it, rep = s.solve(np.zeros((n, n)), rtol=1e-8)
+        assert it == 0 and rep.converged == 1
+        assert float(s.ux.abs().max()) == 0.0 and float(s.uy.abs().max()) == 0.0
+        assert float(s.p.abs().max()) == 0.0
+        it, rep = s.solve(inputs.quarter_five_spot(n), rtol=1e-8)   # the handle still solves
+        assert rep.converged == 1 and it > 0
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("tol", [1e-12, 1e12])
+def test_eigenvalue_tolerance_extremes(tg, tol):
+    """Spectral selection at its extremes (reading 7): a tolerance below
+    every eigenvalue keeps the one required function per coarse face, one
+    above every eigenvalue keeps all b of them.  Coarse dimension as the
+    oracle's; solution as the direct solve's."""
+    n, b, kf = CASES["32x32_b8_channels"]
+    kappa = kf(n)
+    f = inputs.quarter_five_spot(n)
+    o = TwoGridSolver(n, b, kappa, tol=tol)
+    u_ref, p_ref = solve_direct(Grid(n, b), kappa, f)
+    s = tg.Solver(kappa, b, tol)
+    try:
+        it, rep = s.solve(f, rtol=1e-12)
+        u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+        assert rep.converged == 1
+        nc = n // b
+        faces = 2 * nc * (nc - 1)
+        assert sum(o.info["nsel"]) == (faces if tol < 1 else b * faces)
+        assert rep.velocity_basis == sum(o.info["nsel"]) and rep.coarse_dim == rep.velocity_basis + nc * nc + 1
+        assert rel(u, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
     finally:
         s.close()
 
