@@ -43,7 +43,10 @@ N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
 # from the ncu capture summarised in
 # profiles/k_smoother_256x256.md, keyed by (storage precision, tile shape);
 # valid only for the kernel version and shape profiled there
-SMOOTHER_TRAFFIC = {("bf16", 2): 67.18e6}
+# DRAM bytes per smoother launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the captured launches of both sweeps) of the current kernels:
+# 256 x 256 BF16 dense shape 2, and 1024 x 1024 FP16 handle with the band form
+SMOOTHER_TRAFFIC = {("bf16", 2): 66.51e6, ("f16", 7): 335.3e6}
 
 
 def dof(n):
