@@ -797,10 +797,10 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
 // sum of row j + d (forward) or j - d (backward), held in its registers.
 // Lane d loads entry d of four rows at once (the layouts interleave rows in
 // groups of four) and keeps 16 rows in flight (8 for FP64, whose wider
-// registers would otherwise cost the single wave of patches; the entries do
-// not depend on the sweep), so the chain from row to row is a subtraction, a product and
-// two shuffles.  The factor is read once per sweep: n_loc (w + 1) values
-// against n_loc^2 for the dense inverse.
+// registers would otherwise cost the single wave of patches).  The entries do
+// not depend on the sweep, so the chain from row to row is a subtraction, a
+// product and two shuffles.  The factor is read once per sweep: n_loc (w + 1)
+// values against n_loc^2 for the dense inverse.
 constexpr int kBandWarps = 4;   // patches per CTA
 template <typename TC>
 constexpr int kBandGroupsOf = sizeof(TC) == 8 ? kBandPF / 8 : kBandPF / 4;   // row groups in flight per lane
