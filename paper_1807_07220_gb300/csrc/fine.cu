@@ -1537,8 +1537,12 @@ template <typename TC>
 void launch_pcg_dots(const double* r, const TC* z, const double* q, double* part, PcgState* st, int n,
                      cudaStream_t s) {
   TG_COUNT(1);
-  // FP64-pipe bound: two CTAs per SM, so fewer per-CTA FP64 tree sums
-  launch(k_pcg_dots<TC>, dim3(std::min(grid_for((long long)n * n), 2 * sm_count())), dim3(kThreads), 0, s, r, z, q,
+  // FP64-pipe bound at large n: two CTAs per SM, so fewer per-CTA FP64 tree
+  // sums; at small n at least four elements per thread (one pass of loads),
+  // so fewer CTAs arrive at the reduction
+  const long long nn = (long long)n * n;
+  const long long g4 = std::max<long long>(1, (nn + 4LL * kThreads - 1) / (4LL * kThreads));
+  launch(k_pcg_dots<TC>, dim3((unsigned)std::min<long long>(g4, 2LL * sm_count())), dim3(kThreads), 0, s, r, z, q,
          part, st, n);
 }
 void launch_pcg_init(double* x, const double* r, double* part, PcgState* st, int n, cudaStream_t s) {
