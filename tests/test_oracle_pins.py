@@ -292,6 +292,26 @@ def test_kappa_one_spectrum_identical_on_all_faces():
     np.testing.assert_allclose(spectra, np.tile(spectra[0], (len(spectra), 1)), rtol=1e-10)
 
 
+def test_kappa_one_eigenfunctions_mirror_symmetric():
+    """kappa = 1: the neighbourhood of a coarse face (its two blocks) is
+    symmetric under reflection about the face midpoint, and the spectrum is
+    simple, so each eigenfunction's coefficient vector over the face's
+    snapshots (ordered along the face) is even or odd under reversal; the
+    first (smallest lambda) is even and the parities alternate."""
+    n, b = 16, 4
+    g = Grid(n, b)
+    kappa = np.ones((n, n))
+    A, B = assemble(g, kappa)
+    blocks = BlockSolvers(g, A, B)
+    for face in coarse_faces(g):
+        sup, val = snapshots(g, A, B, blocks, face)
+        lam, c = solve_spectral(*spectral_problem(g, A, B, 1 / kappa, face, sup, val), 1e12)
+        assert np.all(np.diff(lam) > 1e-6 * lam[-1])
+        for k in range(c.shape[1]):
+            v = c[:, k]
+            np.testing.assert_allclose(v[::-1], (-1) ** k * v, atol=1e-12 * np.abs(v).max())
+
+
 # --------------------------------------------------------------------- two-grid
 def _on_divfree(s, M):
     """Eigenvalues of M A restricted to the divergence-free space (range of C)."""
