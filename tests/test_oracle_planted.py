@@ -23,10 +23,12 @@ import oracle.coarse as oc
 import oracle.fine as of
 import oracle.learned as ol
 import oracle.twogrid as otg
+import oracle.impes as oi
+import tests.test_oracle_impes as ipins
 import tests.test_oracle_pins as pins
 from paper_1807_07220_gb300.inputs import quarter_five_spot
 
-MODULES = (of, oc, otg, ol, oracle, pins)
+MODULES = (of, oc, otg, ol, oi, oracle, pins, ipins)
 
 
 def plant(monkeypatch, name, fn):
@@ -180,3 +182,26 @@ def test_planted_mistake_fails_its_pins(monkeypatch, case):
 def test_model1_cond_check_holds_unplanted():
     """Control: the capped Model-1 check passes on the oracle as it is."""
     model1_cond()
+
+
+IMPES_CASES = {
+    # downwind instead of upwind fractional flow on the x-faces
+    "downwind": ("transport_step", "upx = np.where(ux >= 0, left, right)", "upx = np.where(ux >= 0, right, left)",
+                 [ipins.test_maximum_principle_under_cfl, ipins.test_buckley_leverett_front]),
+    # the CFL limit with h in place of h^2
+    "cfl_scale": ("transport_step", "dt = cfl * h * h / (fmax * max_slope(mu_w, mu_o))",
+                  "dt = cfl * h / (fmax * max_slope(mu_w, mu_o))", [ipins.test_maximum_principle_under_cfl]),
+    # a sink producing water only, not the cell's fractional flow
+    "sink_fraction": ("transport_step", "+ fw * qminus)", "+ qminus)", [ipins.test_transport_conserves_water_exactly]),
+    # the viscosities exchanged in the fractional flow
+    "fractional_flow": ("frac_flow", "(s * s / mu_w)", "(s * s / mu_o)", [ipins.test_mobility_closed_forms]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(IMPES_CASES))
+def test_planted_transport_mistake_fails_its_pins(monkeypatch, case):
+    name, old, new, targets = IMPES_CASES[case]
+    plant(monkeypatch, name, function_with(oi, name, old, new))
+    for pin in targets:
+        with pytest.raises(Exception):
+            pin()
