@@ -24,11 +24,12 @@ import oracle.fine as of
 import oracle.learned as ol
 import oracle.twogrid as otg
 import oracle.impes as oi
+import tests.test_oracle_learned as lpins
 import tests.test_oracle_impes as ipins
 import tests.test_oracle_pins as pins
 from paper_1807_07220_gb300.inputs import quarter_five_spot
 
-MODULES = (of, oc, otg, ol, oi, oracle, pins, ipins)
+MODULES = (of, oc, otg, ol, oi, oracle, pins, ipins, lpins)
 
 
 def plant(monkeypatch, name, fn):
@@ -202,6 +203,30 @@ IMPES_CASES = {
 def test_planted_transport_mistake_fails_its_pins(monkeypatch, case):
     name, old, new, targets = IMPES_CASES[case]
     plant(monkeypatch, name, function_with(oi, name, old, new))
+    for pin in targets:
+        with pytest.raises(Exception):
+            pin()
+
+
+LEARNED_CASES = {
+    # bfloat16 by truncation instead of round-to-nearest-even
+    "bf16_truncation": ("bf16", "u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = u & 0xFFFF0000",
+                        [lpins.test_bf16_rounding_matches_torch]),
+    # the hidden-to-hidden weight gradient transposed (same shape: hidden x hidden)
+    "w2_gradient_transposed": ("backward", 'g["W2"], g["b2"] = dH2.T @ H1, dH2.sum(0)',
+                               'g["W2"], g["b2"] = H1.T @ dH2, dH2.sum(0)', [lpins.test_gradient_by_central_differences]),
+    # the subspace loss gradient with 2 for 4
+    "loss_gradient_factor": ("subspace_loss", "dG = (4.0 / B) * (E @ G)", "dG = (2.0 / B) * (E @ G)",
+                             [lpins.test_gradient_by_central_differences]),
+    # Adam without the bias corrections
+    "adam_bias_correction": ("adam_step", "mhat = m / (1 - beta1 ** t)", "mhat = m", [lpins.test_adam_matches_torch]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(LEARNED_CASES))
+def test_planted_network_mistake_fails_its_pins(monkeypatch, case):
+    name, old, new, targets = LEARNED_CASES[case]
+    plant(monkeypatch, name, function_with(ol, name, old, new))
     for pin in targets:
         with pytest.raises(Exception):
             pin()
