@@ -138,7 +138,9 @@ def spectral_problem(g, A, B, kinv, face, sup, val):
     a(v, w) = int_{E_i} kappa^{-1} (v.n)(w.n) evaluated as the fine-face trace
     product sum_l kappa_e^{-1} (v.n)_l (w.n)_l, i.e. diagonal kappa_e^{-1} in
     the snapshot basis, with kappa_e^{-1} the mean of the two adjacent cells'
-    kappa^{-1} (the trace of kappa on E_i is not defined by the text).
+    kappa^{-1} (the trace of kappa on E_i is not defined by the text: this
+    choice is parity unpinned; the scale of both forms is pinned by
+    quadrature of the snapshot fields).
     Reading: the face length h is left out.  With it, kappa == 1 gives
     lambda_2 = pi/2 on every face at any resolution, so tolerance 10 would keep
     eight functions per face, against the single one (Dim 282, the RT0 count)

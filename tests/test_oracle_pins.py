@@ -278,6 +278,76 @@ def test_spectral_problem_against_generalized_lapack(small_problem):
             assert abs(rq - lam[k]) <= 1e-10 * lam[k]
 
 
+def _spectral_forms_by_quadrature(n, b, kappa, face, sup, val):
+    """a and s of eq. spectral_eqn for the snapshots ``val`` (on faces
+    ``sup``), integrated from the velocity fields themselves, without the
+    oracle's A and B.  Each snapshot is rebuilt cell by cell as an RT0 field
+    (v_x linear in x between the cell's two x-face values, v_y linear in y),
+    kappa^{-1} v.w is integrated with a 3 x 3 Gauss rule (exact for these
+    quadratics), and div v div w with div v = (sum of outflow values) / h,
+    constant per cell, times the cell area.  s = (that sum over omega) / H
+    with H = b / n, the coarse block side in domain units.  a is the trace
+    product sum_l kappa_e^{-1} (v.n)_l (w.n)_l over the fine faces of E, with
+    kappa_e^{-1} the mean of the two adjacent cells' kappa^{-1}."""
+    h = 1.0 / n
+    H = b * h
+    J = val.shape[1]
+    nxf = (n + 1) * n
+    full = np.zeros((2 * nxf, J))
+    full[sup] = val
+    ux = full[:nxf].reshape(n, n + 1, J)          # [j, i]: x-face at x = i h
+    uy = full[nxf:].reshape(n + 1, n, J)          # [j, i]: y-face at y = j h
+    kind, I, Jc = face
+    blocks = ((I - 1, Jc), (I, Jc)) if kind == 0 else ((I, Jc - 1), (I, Jc))
+    gx, gw = np.polynomial.legendre.leggauss(3)
+    t, w = (gx + 1) / 2, gw / 2                   # nodes and weights on [0, 1]
+    s = np.zeros((J, J))
+    for (bI, bJ) in blocks:
+        for j in range(bJ * b, (bJ + 1) * b):
+            for i in range(bI * b, (bI + 1) * b):
+                kinv = 1.0 / kappa[j, i]
+                for tx, wx in zip(t, w):
+                    for ty, wy in zip(t, w):
+                        vx = ux[j, i] * (1 - tx) + ux[j, i + 1] * tx
+                        vy = uy[j, i] * (1 - ty) + uy[j + 1, i] * ty
+                        s += wx * wy * h * h * kinv * (np.outer(vx, vx) + np.outer(vy, vy))
+                div = (ux[j, i + 1] - ux[j, i] + uy[j + 1, i] - uy[j, i]) / h
+                s += h * h * np.outer(div, div)
+    s /= H
+    l = np.arange(b)
+    if kind == 0:
+        vn = ux[Jc * b + l, I * b]
+        kinv_e = 0.5 * (1 / kappa[Jc * b + l, I * b - 1] + 1 / kappa[Jc * b + l, I * b])
+    else:
+        vn = uy[Jc * b, I * b + l]
+        kinv_e = 0.5 * (1 / kappa[Jc * b - 1, I * b + l] + 1 / kappa[Jc * b, I * b + l])
+    a = vn.T @ (kinv_e[:, None] * vn)
+    return a, s
+
+
+def test_spectral_forms_by_quadrature():
+    """The scale of the spectral problem (eqs. spectral_1 and spectral_eqn of
+    Section 4.2): the oracle's a and s against the same forms integrated
+    from the snapshot velocity fields by quadrature.  This fixes the H^{-1}
+    factor with H in domain units (reading 7), the h^{-2} of the divergence
+    term, and kappa_e^{-1} as the mean of the two cells' kappa^{-1} with no
+    face length (readings 5 and 6), which the selection count at kappa = 1
+    constrains only within a factor of about 20."""
+    for n, b, kappa in ((16, 4, lognormal_field(16, 11, sigma=2.0)),
+                        (24, 8, channel_field(24, 1e4, 3))):
+        g = Grid(n, b)
+        A, B = assemble(g, kappa)
+        blocks = BlockSolvers(g, A, B)
+        faces = coarse_faces(g)
+        for face in (faces[0], faces[len(faces) // 2 + 1], faces[-1]):
+            sup, val = snapshots(g, A, B, blocks, face)
+            a, s = spectral_problem(g, A, B, 1 / kappa, face, sup, val)
+            aq, sq = _spectral_forms_by_quadrature(n, b, kappa, face, sup, val)
+            np.testing.assert_allclose(a, np.diag(aq), rtol=1e-12)   # the oracle keeps a's diagonal
+            assert np.abs(aq - np.diag(np.diag(aq))).max() == 0.0       # snapshots: v.n = delta_l on E
+            np.testing.assert_allclose(s, sq, rtol=0, atol=1e-12 * np.abs(sq).max())
+
+
 def test_kappa_one_spectrum_identical_on_all_faces():
     n, b = 16, 4
     g = Grid(n, b)

@@ -5,10 +5,11 @@ flipped sign, a broken rotation, a dropped term, two indices swapped) and
 checks that the pins named beside it fail: by a failed assertion, or by the
 breakdown the mistake causes inside the pin.  The mistakes are planted with
 monkeypatch in every module that holds the patched name, so nothing outside
-this test changes.  Known gaps stay documented instead of tested: the
-face-length and H scalings of the spectral problem (readings 4 and 6) are
-pinned only through the selection count at kappa = 1, and kappa on a coarse
-face (reading 5) has no pin.
+this test changes.  The scale of the spectral problem (H in domain units,
+the h^{-2} of its divergence term, kappa_e^{-1} as a mean, no face length)
+is fixed by the quadrature pin; which trace of kappa on a fine face is meant
+(reading 5) and the omitted face length (reading 6) are readings that the
+quadrature restates, not facts it derives.
 """
 
 import inspect
@@ -168,6 +169,24 @@ CASES = {
                                  [pins.test_layered_medium_closed_form]),
     "snapshot_order": (lambda: ("snapshots", snapshots_swapped(oc.snapshots)),
                        [pins.test_kappa_one_eigenfunctions_mirror_symmetric]),
+    # H counted in fine cells (b) instead of domain units (b / n)
+    "spectral_H_in_cells": (lambda: ("spectral_problem", function_with(oc, "spectral_problem", "h, H = g.h, g.H",
+                                                                         "h, H = g.h, float(g.b)")),
+                            [pins.test_spectral_forms_by_quadrature]),
+    # the divergence term of s over h instead of h^2
+    "spectral_div_over_h": (lambda: ("spectral_problem", function_with(oc, "spectral_problem",
+                                                                         "(Bv.T @ Bv) / h ** 2", "(Bv.T @ Bv) / h")),
+                            [pins.test_spectral_forms_by_quadrature]),
+    # kappa_e^{-1} as the sum of the two cells' kappa^{-1}, not their mean
+    "spectral_kappa_e_sum": (lambda: ("spectral_problem", function_with(oc, "spectral_problem",
+                                                                          "a = 0.5 * (kflat[cL] + kflat[cR])",
+                                                                          "a = kflat[cL] + kflat[cR]")),
+                             [pins.test_spectral_forms_by_quadrature]),
+    # the a-form with the face length h
+    "spectral_face_length": (lambda: ("spectral_problem", function_with(oc, "spectral_problem",
+                                                                          "a = 0.5 * (kflat[cL] + kflat[cR])",
+                                                                          "a = 0.5 * h * (kflat[cL] + kflat[cR])")),
+                             [pins.test_spectral_forms_by_quadrature]),
 }
 
 
