@@ -149,6 +149,13 @@ typedef struct tg_options {
    * solves); used with m1 = m2 = 1 and the two-grid cycle.  0 = every
    * right-hand side an independent chain. */
   int batch_lockstep;
+  /* tg_setup_batch with TG_COARSE_LEARNED only: candidate networks (host
+   * array of nnets handles, NULL entries skipped); each instance takes the
+   * first whose block size equals its own (a network is trained for one
+   * block size), TG_ERR_INVALID_ARG when none does.  NULL: every instance
+   * takes `net`. */
+  const tg_mlp* const* batch_nets;
+  int batch_nnets;
 } tg_options;
 
 typedef struct tg_report {
@@ -428,9 +435,9 @@ int tg_transport_step(const double* s, const double* ux, const double* uy, const
 
 /* ---- allocation-free entry point --------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot
- * allocate device memory -- code recorded inside a CUDA stream capture
- * (cudaMalloc is not capturable), processes whose device memory is owned by
- * another allocator (a framework's caching allocator or a fixed arena), and
+ * allocate device memory -- processes whose device memory is owned by another
+ * allocator (a framework's caching allocator or a fixed arena reserved at
+ * start-up, where an outside cudaMalloc can fail or fragment it), and
  * latency-critical paths that must not take cudaMalloc's implicit device
  * synchronisation.  It needs no handle and calls no cudaMalloc, cudaFree or
  * allocating library routine.
@@ -441,7 +448,9 @@ int tg_transport_step(const double* s, const double* ux, const double* uy, const
  * law A u = B^T p along grid rows and fitting one offset per row to the
  * y-face equations in least squares.  All pointers are device pointers;
  * work runs on `stream` (cudaStream_t, NULL = legacy default stream) and the
- * call returns after synchronising it.
+ * call returns after synchronising it.  TG_ERR_CUDA reports a failed launch,
+ * copy or synchronisation of this call; a launch error already pending in
+ * the calling thread is left pending and not reported.
  *
  * Scratch: one statically sized device array compiled into the library
  * (about 20 MiB, held by every GPU that loads the library until the process

@@ -1640,6 +1640,8 @@ int tg_default_options(tg_options* opt) {
   opt->launch_overlap = 0;
   opt->cycle = TG_CYCLE_TWO_GRID;
   opt->batch_lockstep = 1;
+  opt->batch_nets = nullptr;
+  opt->batch_nnets = 0;
   return TG_OK;
 }
 
@@ -1946,7 +1948,22 @@ int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, 
   int rc = TG_OK;
   for (int i = 0; i < ninst && !rc; ++i) {
     tg_handle* h = nullptr;
-    rc = tg_setup(kappa[i], &grids[i], eig_tol, opt, stream, &h);
+    tg_options oi = *opt;
+    if (opt->coarse_space == TG_COARSE_LEARNED && opt->batch_nets) {
+      // the network trained for this instance's block size
+      oi.net = nullptr;
+      for (int k = 0; k < opt->batch_nnets && !oi.net; ++k) {
+        if (!opt->batch_nets[k]) continue;
+        int nb = 0, nk = 0, hid = 0, din = 0, dout = 0;
+        mlp_dims(opt->batch_nets[k], &nb, &nk, &hid, &din, &dout);
+        if (nb == grids[i].bx) oi.net = opt->batch_nets[k];
+      }
+      if (!oi.net) {
+        rc = TG_ERR_INVALID_ARG;
+        break;
+      }
+    }
+    rc = tg_setup(kappa[i], &grids[i], eig_tol, &oi, stream, &h);
     if (!rc) B->handles.push_back(h);
   }
   // contexts: the handle's own context serves its first right-hand side

@@ -3,11 +3,14 @@
 // row-integrated pressures and the row offsets) in one file-scope device
 // array instead of handle-owned buffers.
 //
-// Who needs it: code that may not call cudaMalloc -- work recorded inside a
-// CUDA stream capture (allocation calls are not capturable), processes whose
+// Who needs it: callers that may not call cudaMalloc -- processes whose
 // device memory is owned entirely by another allocator (a framework's caching
-// allocator or a fixed arena), and latency-critical paths that must not take
-// the implicit device synchronisation of cudaMalloc / cudaFree.
+// allocator or a fixed arena reserved at start-up, where a stray cudaMalloc
+// can fail or fragment that arena), and latency-critical paths that must not
+// take the implicit device synchronisation of cudaMalloc / cudaFree.
+//
+// The first call on a device looks up the array's device address (one-time
+// set-up per device); that first call should come before any stream capture.
 #include <mutex>
 
 #include "../../include/tgms.h"
@@ -64,13 +67,18 @@ extern "C" int tg_pressure_noalloc(const double* kappa, const double* ux, const 
   int* status = reinterpret_cast<int*>(s8 + kOffStatus);
   double* work = reinterpret_cast<double*>(s8 + kOffWork);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // A launch error already pending in this thread belongs to the caller's
+  // earlier work: it is neither reported here nor cleared.
+  const cudaError_t pending = cudaPeekAtLastError();
   // the status word keeps the previous call's value: clear it
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return TG_ERR_CUDA;
   tg::launch_kinv(kappa, kinv, kinv32, status, n, s);
   tg::launch_pressure(ux, uy, kinv, p, work, n, s);
+  const cudaError_t launched = cudaPeekAtLastError();
+  if (launched != cudaSuccess && launched != pending) return TG_ERR_CUDA;
   int h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return TG_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return TG_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TG_ERR_CUDA;
   return h_status ? TG_ERR_INVALID_ARG : TG_OK;
 }

@@ -39,7 +39,7 @@ class tg_options(ctypes.Structure):
                 ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
                 ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
                 ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int),
-                ("cycle", c_int), ("batch_lockstep", c_int)]
+                ("cycle", c_int), ("batch_lockstep", c_int), ("batch_nets", c_void_p), ("batch_nnets", c_int)]
 
 
 class tg_report(ctypes.Structure):
@@ -165,6 +165,13 @@ def default_options(**kw):
             v = v.value if isinstance(v, ctypes.c_void_p) else v
         if k == "face_profiles":
             v = _ptr(v).value if v is not None else None
+        if k == "batch_nets":
+            # a host array of network handles, kept alive with the options
+            hs = [getattr(x, "handle", x) for x in v]
+            arr = (c_void_p * len(hs))(*[x.value if isinstance(x, ctypes.c_void_p) else x for x in hs])
+            o._batch_nets_keep = arr
+            o.batch_nnets = len(hs)
+            v = ctypes.cast(arr, c_void_p).value
         setattr(o, k, v)
     return o
 

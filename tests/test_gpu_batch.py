@@ -130,3 +130,35 @@ def test_lockstep_batch_with_band_smoother(tg):
             u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
             assert rel(u[j], u_ref) < 1e-8, (j, rel(u[j], u_ref))
             j += 1
+
+
+def test_learned_batch_takes_the_network_of_each_block_size(tg):
+    """A learned-coarse-space batch over instances of two block sizes takes,
+    per instance, the network trained for its block size (batch_nets); the
+    solutions reach the direct solve.  With no network for one of the block
+    sizes the setup is rejected."""
+    specs = [(32, 8, 1e4, 1), (48, 16, 1e5, 3), (32, 16, 1e6, 4)]
+    nrhs = 2
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device="cuda").contiguous() for k in kappas]
+    fs = [inputs.random_pairs(n, 1, 90 * seed + r) for (n, b, c, seed) in specs for r in range(nrhs)]
+    stream = torch.cuda.current_stream().cuda_stream
+    nets = []
+    try:
+        for b in (16, 8):
+            din, dout, npar = tg.tg_mlp_shape(b, 4, 64)
+            params = torch.as_tensor(inputs.mlp_init_params(din, dout, 64, 17 + b), device="cuda")
+            nets.append(tg.Mlp(b, 4, 64, params, stream=stream))
+        it, u = _run_batch(tg, kd, specs, fs, nrhs, "f16", 1, 1e-12, coarse_space="learned", batch_nets=nets)
+        j = 0
+        for (n, b, c, seed), k in zip(specs, kappas):
+            for r in range(nrhs):
+                u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
+                assert rel(u[j], u_ref) < 1e-8, (j, rel(u[j], u_ref))
+                j += 1
+        with pytest.raises(tg.TgmsError) as e:
+            _run_batch(tg, kd, specs, fs, nrhs, "f16", 1, 1e-12, coarse_space="learned", batch_nets=nets[:1])
+        assert e.value.code == -1
+    finally:
+        for net in nets:
+            net.close()

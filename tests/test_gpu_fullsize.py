@@ -113,8 +113,9 @@ def test_headline_256_against_direct_solve(tg):
     us, ps = solve_direct_pinned(chk.g, kappa, f)
     e = u - us
     err_a = np.sqrt(e @ (chk.A @ e)) / np.sqrt(us @ (chk.A @ us))
+    err_u = np.linalg.norm(e) / np.linalg.norm(us)
     err_p = np.linalg.norm(p - ps) / np.linalg.norm(ps)
-    assert err_a <= 1e-8 and err_p <= 1e-8, (err_a, err_p, m)
+    assert err_a <= 1e-8 and err_u <= 1e-8 and err_p <= 1e-8, (err_a, err_u, err_p, m)
 
 
 @pytest.mark.parametrize("n,prec", [(512, "bf16"), (1024, "f16")])

@@ -70,7 +70,7 @@ def test_structs_match_header_layout():
     text = open(HEADER).read()
     for struct in (tgms.tg_grid, tgms.tg_options, tgms.tg_report):
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct.__name__, struct.__name__), text, re.S)
-        fields = re.findall(r"\b(?:const\s+)?(?:int|double|float|tg_mlp)\s*\*?\s*([A-Za-z_][^;]*);",
+        fields = re.findall(r"\b(?:const\s+)?(?:int|double|float|tg_mlp)\s*\*?\s*(?:const\s*\*\s*)?([A-Za-z_][^;]*);",
                             re.sub(r"/\*.*?\*/", "", body.group(1), flags=re.S))
         names = [re.sub(r"\[.*\]", "", x).strip() for f in fields for x in f.split(",")]
         assert names == [f for f, _ in struct._fields_], struct.__name__
