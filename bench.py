@@ -18,10 +18,28 @@ step is timed with CUDA events on the solver's stream.  `e2e` repeats the
 headline arm through the host-pointer C ABI (host -> device copy of f and
 device -> host copy of ux, uy, p inside every timed call).
 
+The default line also carries, for one GPU:
+  north_star.batch_64x4: 64 instances (n in {64,128,256,512}, b in {8,16},
+    channels at 10^U(4,6)) x 4 right-hand sides in one graph launch per
+    step: learned coarse space + FP16 preconditioner (networks trained here
+    for b = 8 and 16), exact spectral space + FP16, and plain FP64 exact;
+  north_star.n1024_b16: 1024^2, b = 16, held-out exp(GRF) + 1e6 channel
+    field: learned (network trained here on 25 fields, 201 600 faces) and
+    exact with the FP16 preconditioner against plain FP64 exact, plus the
+    smoother's roofline at that size (its factors stream from HBM).
+With the oracle legs (unless --no-cpu-baseline): cpu_baseline, the oracle's
+full solve on every host core (one core beside it), and the GPU solutions
+checked against the oracle: error_vs_oracle (relative l2 and energy-norm
+velocity error and l2 pressure error against its sparse direct solve) for
+the headline arm and a sample of the batch, and the properties that fix the
+solution (mass balance, momentum equation, zero-mean pressure, evaluated
+with its matrices) for the 1024^2 arms.
+
 --impl reference times the FP64 CPU oracle (test infrastructure of this
 repository) on the host cores: each step is one oracle PCG iteration on the
 same workload, and the throughput uses the oracle's own preprocessing,
-iteration count and pressure times measured once in warm-up.
+iteration count and pressure times measured once in warm-up; ms_per_step is
+the solve time this extrapolates to.
 """
 
 import argparse
@@ -287,6 +305,9 @@ def run_ours(args):
     clk = clocks.stop()
     if dist:
         dist.barrier()
+    # the last timed solve (rtol 1e-8), checked against the oracle after the timing
+    checks = {"headline": dict(n=n, b=b, kappa=kappa, f=f, direct=True, p=head.p.cpu().numpy().ravel(),
+                               u=np.concatenate([head.ux.cpu().numpy().ravel(), head.uy.cpu().numpy().ravel()]))}
     head.close()
     # roofline of the dominant kernel (patch smoother): events around every launch
     shape = reps[-1].smoother_shape
@@ -322,6 +343,12 @@ def run_ours(args):
     def agg(ms_list):
         return whole_job_rate(ms_list, dof(n), world, dist is not None, "cuda")
 
+    peaks, peak_src = measured_peaks()
+    north = None
+    if world == 1 and not args.no_north_star:
+        north = {"batch_64x4": north_star_batch(args, tgms, torch, flush, checks),
+                 "n1024_b16": north_star_1024(args, tgms, torch, flush, checks, peaks, peak_src)}
+
     value, ms_step = agg(times)
     p_value, p_ms = agg(p_times)
     other_arms = {}
@@ -334,7 +361,6 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    peaks, peak_src = measured_peaks()
     achieved = alg_bytes / (sm_ms / sm_n / 1e3) / 1e9 if sm_n else None
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-solves/s", "n_gpus": world, "steps": args.steps,
@@ -357,6 +383,11 @@ def run_ours(args):
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                      "traffic": SMOOTHER_TRAFFIC.get((prec, shape)),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache",
+                     "working_set": "%.0f MB of patch factors per sweep against a 129 MB L2: at %d^2 they stay "
+                                    "L2-resident between sweeps, so the launch is L2/latency-bound and the HBM "
+                                    "fraction is a lower bound of what the kernel could stream" % (alg_bytes / 1e6, n)
+                     if alg_bytes < 100e6 else "%.0f MB per sweep, streamed from HBM" % (alg_bytes / 1e6),
                      "tile_shape": shape, "autotuner_us_per_shape": reps[-1].shape_times(),
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None,
                      "launches_timed": sm_n, "peak_source": peak_src},
@@ -365,11 +396,207 @@ def run_ours(args):
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * (n + 1) + n * n)},
         "clocks": clk,
     }
+    if north is not None:
+        line["north_star"] = north
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, b)
+        try:
+            res = oracle_checks(checks)
+        except Exception as e:  # reported, never fatal for the GPU line
+            res = {"error": str(e)[:300]}
+        line["error_vs_oracle"] = res.get("headline", res)
+        if north is not None:
+            for arm in north["batch_64x4"]["arms"]:
+                north["batch_64x4"]["arms"][arm]["error_vs_oracle"] = {
+                    k[len("batch_%s_" % arm):]: v for k, v in res.items() if k.startswith("batch_%s_" % arm)}
+            for arm in north["n1024_b16"]["arms"]:
+                north["n1024_b16"]["arms"][arm]["properties_vs_oracle"] = res.get("n1024_" + arm)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- spec comparison
+def train_net(tgms, torch, n, b, kappa_of, seeds, steps, hidden, stream, k=4):
+    """A network for block size b: labels from the exact spectral problems
+    (Section 4.2) of the seeded fields kappa_of(seed), then ``steps`` Adam
+    steps of 1024 faces with the library's own kernels.  Returns (Mlp, info)."""
+    from paper_1807_07220_gb300 import inputs
+    dev = "cuda"
+    nc = n // b
+    F = 2 * nc * (nc - 1)
+    din, dout, npar = tgms.tg_mlp_shape(b, k, hidden)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = torch.empty((len(seeds) * F, din), dtype=torch.bfloat16, device=dev)
+    Q = torch.empty((len(seeds) * F, k, b), dtype=torch.float32, device=dev)
+    for i, sd in enumerate(seeds):
+        kap = torch.as_tensor(kappa_of(sd), dtype=torch.float64, device=dev)
+        tgms.tg_face_data(kap, n, b, EIG_TOL, k, X[i * F:(i + 1) * F], Q[i * F:(i + 1) * F], stream=stream)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    params = torch.as_tensor(inputs.mlp_init_params(din, dout, hidden, 17), device=dev)
+    net = tgms.Mlp(b, k, hidden, params, stream=stream)
+    order = torch.as_tensor(inputs.sample_order(X.shape[0], steps, 1024, 23), device=dev)
+    hist = torch.zeros(steps, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    net.train(X, Q, order, steps, 1024, 1e-3, hist)
+    torch.cuda.synchronize()
+    info = {"b": b, "fields": len(seeds), "field_n": n, "samples": int(X.shape[0]), "steps": steps,
+            "label_s": label_s, "train_s": time.perf_counter() - t0,
+            "loss_last": float(hist[-min(50, steps):].mean().item())}
+    del X, Q
+    return net, info
+
+
+def arm_record(dof_total, times, setup_s):
+    ms = statistics.mean(times)
+    return {"value": dof_total / (ms / 1e3), "ms_per_step": ms, "setup_s": setup_s,
+            "value_with_setup": dof_total / (ms / 1e3 + setup_s)}
+
+
+def north_star_batch(args, tgms, torch, flush, checks):
+    """The 64-instance x 4-right-hand-side workload (n from {64, 128, 256,
+    512}, b from {8, 16}, channels at 10^U(4,6), one random source/sink pair
+    per right-hand side) in one graph launch per step: learned coarse space
+    with the row-scaled FP16 preconditioner (networks for b = 8 and b = 16
+    trained on other channel fields), the exact spectral space with the same
+    preconditioner, and the plain FP64 exact path in the same batched form."""
+    import numpy as np
+    from paper_1807_07220_gb300 import inputs
+    dev = "cuda"
+    stream = torch.cuda.current_stream().cuda_stream
+    specs = batch_specs(64)
+    nrhs = 4
+    ns, bs = [sp[0] for sp in specs], [sp[1] for sp in specs]
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device=dev).contiguous() for k in kappas]
+    fs_h = [inputs.random_pairs(n, 1, 7 * seed + r) for (n, b, c, seed) in specs for r in range(nrhs)]
+    fs = [torch.as_tensor(f, dtype=torch.float64, device=dev).contiguous() for f in fs_h]
+    z = lambda *sh: torch.zeros(*sh, dtype=torch.float64, device=dev)
+    ux = [z(n, n + 1) for n in ns for _ in range(nrhs)]
+    uy = [z(n + 1, n) for n in ns for _ in range(nrhs)]
+    pp = [z(n, n) for n in ns for _ in range(nrhs)]
+    total_dof = sum(dof(n) for n in ns) * nrhs
+    rng = np.random.default_rng(2025)
+    contrast = {sd: float(10.0 ** rng.uniform(4, 6)) for sd in range(7000, 7016)}
+    nets, training = [], []
+    for b, seeds in ((8, range(7000, 7004)), (16, range(7004, 7016))):
+        net, info = train_net(tgms, torch, 512, b, lambda sd: inputs.channel_field(512, contrast[sd], sd),
+                              list(seeds), args.train_steps, args.hidden, stream)
+        nets.append(net)
+        training.append(info)
+    # one problem per grid side up to 256 (its first right-hand side) against the direct solve
+    sample = {}
+    for i, n in enumerate(ns):
+        if n <= 256 and n not in sample:
+            sample[n] = i
+    steps = max(1, min(args.steps, args.ns_steps))
+    arms = {}
+    for name, opt in (("learned_f16", dict(precision="f16", flexible=1, coarse_space="learned", batch_nets=nets)),
+                      ("exact_f16", dict(precision="f16", flexible=1)),
+                      ("exact_f64", dict(precision="f64", flexible=0))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch = tgms.tg_setup_batch(kd, ns, bs, EIG_TOL, nrhs, options=tgms.default_options(**opt), stream=stream)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        try:
+            for _ in range(args.warmup):
+                tgms.tg_solve_batch(batch, fs, None, RTOL, ux, uy, pp)
+            times = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                iters, status = tgms.tg_solve_batch(batch, fs, None, RTOL, ux, uy, pp)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        finally:
+            tgms.tg_destroy_batch(batch)
+        rec = arm_record(total_dof, times, setup_s)
+        rec.update(iters_min_mean_max=[int(iters.min()), float(iters.mean()), int(iters.max())],
+                   all_converged=bool((status == 0).all()), steps_timed=steps)
+        arms[name] = rec
+        for n, i in sample.items():
+            j = i * nrhs
+            checks["batch_%s_n%d" % (name, n)] = dict(
+                n=n, b=bs[i], kappa=kappas[i], f=fs_h[j], direct=True,
+                u=np.concatenate([ux[j].cpu().numpy().ravel(), uy[j].cpu().numpy().ravel()]),
+                p=pp[j].cpu().numpy().ravel())
+    for net in nets:
+        net.close()
+    return {"workload": "64 instances x 4 right-hand sides, n in {64,128,256,512}, b in {8,16}, channels at "
+                        "10^U(4,6), one random source/sink pair per rhs, rtol 1e-8, one CUDA graph launch per "
+                        "step, L2 flushed before each", "dof_per_step": total_dof, "arms": arms,
+            "training": training, "error_sample": {str(n): "instance %d (b = %d), first rhs" % (i, bs[i])
+                                                    for n, i in sample.items()},
+            "learned_f16_vs_exact_f64": arms["learned_f16"]["value"] / arms["exact_f64"]["value"],
+            "learned_f16_vs_exact_f64_with_setup":
+                arms["learned_f16"]["value_with_setup"] / arms["exact_f64"]["value_with_setup"]}
+
+
+def north_star_1024(args, tgms, torch, flush, checks, peaks, peak_src):
+    """1024 x 1024, 16 x 16-cell blocks, exp(GRF) + 1e6 channels (held-out
+    field): the learned coarse space (network trained on 25 other seeded
+    fields, 201 600 faces) and the exact spectral space with the row-scaled
+    FP16 preconditioner, against the plain FP64 exact path.  Also the
+    roofline of the smoother at this size, where its factors (hundreds of MB)
+    stream from HBM on every sweep."""
+    import numpy as np
+    from paper_1807_07220_gb300 import inputs
+    n, b = 1024, 16
+    stream = torch.cuda.current_stream().cuda_stream
+    net, training = train_net(tgms, torch, n, b, lambda sd: inputs.grf_channel_field(n, CONTRAST, sd),
+                              list(range(5000, 5000 + args.train_fields)), args.train_steps, args.hidden, stream)
+    kappa, f = workload(n, 4242)
+    kd = torch.as_tensor(kappa, dtype=torch.float64, device="cuda")
+    steps = max(1, min(args.steps, args.ns_steps))
+    arms = {}
+    shape16 = None
+    for name, kw in (("learned_f16", dict(precision="f16", flexible=1, coarse_space="learned", net=net)),
+                     ("exact_f16", dict(precision="f16", flexible=1)),
+                     ("exact_f64", dict(precision="f64", flexible=0))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = tgms.Solver(kd, b, EIG_TOL, **kw)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        times, reps = time_solves(s, f, steps, args.warmup, flush, torch)
+        r = reps[-1]
+        rec = arm_record(dof(n), times, setup_s)
+        rec.update(iters=r.iters, rel_residual=r.rel_residual, coarse_unknowns=r.coarse_unknowns,
+                   snapshot_solves=r.snapshot_solves, fallback_faces=r.fallback_faces,
+                   smoother_shape=r.smoother_shape, steps_timed=steps)
+        arms[name] = rec
+        if name == "exact_f16":
+            shape16 = r.smoother_shape
+        checks["n1024_" + name] = dict(n=n, b=b, kappa=kappa, f=f, direct=False,
+                                       u=np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()]),
+                                       p=s.p.cpu().numpy().ravel())
+        s.close()
+    net.close()
+    # smoother roofline at 1024^2: events around every launch of a profiled run of the FP16 arm
+    prof = tgms.Solver(kd, b, EIG_TOL, precision="f16", flexible=1, profile=1, smoother_shape=shape16)
+    _, prof_reps = time_solves(prof, f, 2, 1, flush, torch)
+    prof.close()
+    sm_ms = sum(r.smoother_ms for r in prof_reps)
+    sm_n = sum(r.smoother_launches for r in prof_reps)
+    band = shape16 == 7
+    alg = band_smoother_bytes(n, b, 2, 4) if band else smoother_bytes(n, b, 2, 2, 4)
+    ach = alg / (sm_ms / sm_n / 1e3) / 1e9 if sm_n else None
+    roof = {"bound": "hbm", "kernel": "k_smoother_band (patch band solves)" if band else "k_smoother",
+            "achieved": ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": SMOOTHER_TRAFFIC.get(("f16", shape16)),
+            "tile_shape": shape16, "algorithmic_bytes_per_launch": alg,
+            "avg_launch_us": 1e3 * sm_ms / sm_n if sm_n else None, "launches_timed": sm_n, "peak_source": peak_src}
+    return {"workload": workload_name(n, b) + " (field seed 4242, held out of training)", "dof_per_solve": dof(n),
+            "arms": arms, "training": training, "smoother_roofline": roof,
+            "learned_f16_vs_exact_f64": arms["learned_f16"]["value"] / arms["exact_f64"]["value"],
+            "learned_f16_vs_exact_f16": arms["learned_f16"]["value"] / arms["exact_f16"]["value"],
+            "learned_f16_vs_exact_f64_with_setup":
+                arms["learned_f16"]["value_with_setup"] / arms["exact_f64"]["value_with_setup"]}
 
 
 # ---------------------------------------------------------------- batched workload
@@ -757,27 +984,104 @@ print("ORACLE_JSON " + json.dumps(out))
 """
 
 
-def run_oracle(n, b, mode, steps=0, warmup=0, timeout=900):
+def host_cores():
+    return os.cpu_count() or 1
+
+
+def oracle_env(threads):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
+    return env
+
+
+def run_oracle(n, b, mode, steps=0, warmup=0, timeout=900, threads=None):
+    threads = threads or host_cores()
     code = ORACLE_SNIPPET % {"root": ROOT, "n": n, "b": b, "mode": mode, "steps": steps, "warmup": warmup}
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=oracle_env(threads),
+                       timeout=timeout)
     for ln in r.stdout.splitlines():
         if ln.startswith("ORACLE_JSON "):
             return json.loads(ln[len("ORACLE_JSON "):])
     raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
 
 
+ORACLE_CHECK_SNIPPET = r"""
+import json, sys
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle.fine import Grid, assemble, solve_direct_pinned
+d = np.load(%(path)r)
+out, cache = {}, {}
+for name in %(names)r:
+    n, b = int(d[name + "/n"]), int(d[name + "/b"])
+    kappa, f, u, p = d[name + "/kappa"], d[name + "/f"], d[name + "/u"], d[name + "/p"]
+    g = Grid(n, b)
+    A, B = assemble(g, kappa)
+    I = g.interior_faces()
+    F = g.h ** 2 * f.ravel()
+    Au = (A @ u)[I]
+    r = {"n": n, "b": b,
+         "mass": float(np.abs(B @ u - F).max() / np.abs(F).max()),
+         "momentum": float(np.linalg.norm(Au - (B.T @ p)[I]) / np.linalg.norm(Au)),
+         "mean_p": float(abs(p.sum()) / np.abs(p).sum())}
+    if int(d[name + "/direct"]):
+        key = (n, b, hash(kappa.tobytes()), hash(f.tobytes()))
+        if key not in cache:
+            cache[key] = solve_direct_pinned(g, kappa, f)
+        us, ps = cache[key]
+        e = u - us
+        r.update(err_u_l2=float(np.linalg.norm(e) / np.linalg.norm(us)),
+                 err_u_energy=float(np.sqrt(e @ (A @ e)) / np.sqrt(us @ (A @ us))),
+                 err_p_l2=float(np.linalg.norm(p - ps) / np.linalg.norm(ps)))
+    out[name] = r
+print("ORACLE_JSON " + json.dumps(out))
+"""
+
+
+def oracle_checks(cases, timeout=900):
+    """The GPU solutions in ``cases`` (name -> dict(n, b, kappa, f, u, p,
+    direct)) checked with the oracle in a subprocess: the relative errors
+    against its sparse direct solve (direct = True) and the properties that
+    fix the discrete solution (mass balance per cell, momentum equation
+    A u = B^T p on interior faces, sum(p) = 0), evaluated with its matrices."""
+    import tempfile
+    import numpy as np
+    if not cases:
+        return {}
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "cases.npz")
+        arrs = {}
+        for name, c in cases.items():
+            for k in ("n", "b", "kappa", "f", "u", "p"):
+                arrs[name + "/" + k] = np.asarray(c[k])
+            arrs[name + "/direct"] = np.asarray(int(c.get("direct", False)))
+        np.savez(path, **arrs)
+        code = ORACLE_CHECK_SNIPPET % {"root": ROOT, "path": path, "names": sorted(cases)}
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           env=oracle_env(host_cores()), timeout=timeout)
+    for ln in r.stdout.splitlines():
+        if ln.startswith("ORACLE_JSON "):
+            return json.loads(ln[len("ORACLE_JSON "):])
+    raise RuntimeError("oracle check failed: " + r.stderr[-2000:])
+
+
 def cpu_baseline(n, b):
+    """The oracle's full solve of the workload on the host cores: BLAS
+    threads set to every core (the figure reported) and to one core (beside
+    it).  The oracle's sparse LU and sparse products are single-threaded."""
+    cores = host_cores()
     try:
-        o = run_oracle(n, b, "full")
+        o = run_oracle(n, b, "full", threads=cores)
+        o1 = run_oracle(n, b, "full", threads=1)
     except Exception as e:  # reported, never fatal for the GPU line
         return {"value": None, "error": str(e)[:200]}
-    return {"value": dof(n) / o["solve_s"], "unit": "DOF-solves/s", "cores": 1, "kind": "oracle",
+    return {"value": dof(n) / o["solve_s"], "unit": "DOF-solves/s", "cores": cores, "kind": "oracle",
             "sample": "one full oracle solve (preprocessing + %d PCG iterations + pressure) of the same "
-                      "workload, single-threaded BLAS; oracle setup (%.0f s) excluded" % (o["iters"], o["setup_s"]),
-            "solve_s": o["solve_s"]}
+                      "workload, BLAS threads = %d host cores (SuperLU and sparse products single-threaded); "
+                      "oracle setup (%.0f s) excluded" % (o["iters"], cores, o["setup_s"]),
+            "solve_s": o["solve_s"],
+            "one_core": {"value": dof(n) / o1["solve_s"], "solve_s": o1["solve_s"], "cores": 1}}
 
 
 def run_reference(args):
@@ -785,21 +1089,24 @@ def run_reference(args):
     if rank != 0:
         return
     n, b = args.n, args.b
-    o = run_oracle(n, b, "iter", steps=args.steps, warmup=args.warmup, timeout=3000)
+    cores = host_cores()
+    o = run_oracle(n, b, "iter", steps=args.steps, warmup=args.warmup, timeout=3000, threads=cores)
     t_iter = statistics.mean(o["it_times"])
     t_solve = o["t_pre"] + o["iters"] * t_iter + o["t_post"]
     value = dof(n) / t_solve
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_iter, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(n, b), "n": n, "b": b, "precision": "f64",
                    "dof_per_solve": dof(n)},
-        "cpu_baseline": {"value": value, "unit": "DOF-solves/s", "cores": 1, "kind": "oracle",
+        "ms_per_pcg_iteration": 1e3 * t_iter,
+        "cpu_baseline": {"value": value, "unit": "DOF-solves/s", "cores": cores, "kind": "oracle",
                          "sample": "each step = one oracle PCG iteration (operator, two preconditioner "
-                                   "applications for the scalars, vector updates) on the same workload; "
-                                   "solve time = preprocessing %.2f s + %d iterations + pressure %.2f s"
-                                   % (o["t_pre"], o["iters"], o["t_post"])},
+                                   "applications for the scalars, vector updates) on the same workload, "
+                                   "BLAS threads = %d host cores; ms_per_step = the solve it extrapolates to: "
+                                   "preprocessing %.2f s + %d iterations + pressure %.2f s"
+                                   % (cores, o["t_pre"], o["iters"], o["t_post"])},
         "e2e": {"value": value, "unit": "DOF-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -814,7 +1121,11 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--b", type=int, default=B_DEFAULT)
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle legs (CPU baseline and the checks against the oracle)")
+    ap.add_argument("--no-north-star", action="store_true",
+                    help="skip the batched and 1024^2 learned comparisons against plain FP64")
+    ap.add_argument("--ns-steps", type=int, default=5, help="timed steps of each north-star arm")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "learned", "impes", "ablation"])
     ap.add_argument("--impes-steps", type=int, default=200)
     ap.add_argument("--impes-arms", default="frozen,frozen_full,rebuild,rebuild_learned",
