@@ -46,6 +46,8 @@ struct tg_handle {
   int ngroups = 0;
   void* pinv = nullptr;
   void* pband = nullptr;    // band factors of the patches in the arithmetic type (tile shape kShapeBand)
+  void* ptiles = nullptr;   // 2-byte storage: the inverses in the tensor-core tile layout (kShapeTensor)
+  int* d_tofs = nullptr;    // first 16-row tile of each patch (+ total)
   BandRef band;
   float* rscale = nullptr;  // FP16 storage: inverse row scales
   // block factors (snapshots) and dense block inverses (preprocessing)
@@ -938,6 +940,8 @@ struct PatchLayout {
   std::vector<int4> rect;
   std::vector<PatchGeo> geo;
   long long off = 0;   // total stored elements
+  long long toff = 0;  // total elements of the tile layout
+  std::vector<int> tofs;   // first 16-row tile of each patch (+ total)
   int wmax = 0, nmax = 0;
 };
 
@@ -957,11 +961,16 @@ PatchLayout patch_layout(const tg_handle* h) {
       g.ld = ((g.nloc + 7) / 8) * 8;
       g.off = L.off;
       L.off += (long long)g.nloc * g.ld;
+      const int T = tiles_per_side(g.nloc);
+      g.toff = L.toff;
+      L.toff += (long long)T * T * kTile * kTile;
       L.geo[k] = g;
       L.rect[k] = make_int4(x0, y0, g.nx, g.ny);
       L.wmax = std::max(L.wmax, g.nx + 1);
       L.nmax = std::max(L.nmax, g.nloc);
     }
+  L.tofs.assign(h->npatch + 1, 0);
+  for (int k = 0; k < h->npatch; ++k) L.tofs[k + 1] = L.tofs[k] + tiles_per_side(L.geo[k].nloc);
   return L;
 }
 
@@ -1025,6 +1034,15 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
     const size_t esz = (h->opt.precision == TG_PREC_F64) ? sizeof(double) : sizeof(float);
     TG_CK(cudaMalloc(&h->pband, std::max<size_t>(1, (size_t)h->npatch * h->band.stride * esz)));
     h->band.p = h->pband;
+    // 2-byte storage: the same inverses in the tensor-core tile layout
+    if (h->opt.precision == TG_PREC_BF16 || h->opt.precision == TG_PREC_F16) {
+      TG_CK(cudaMalloc(&h->ptiles, std::max<size_t>(1, (size_t)L.toff * 2)));
+      if (dalloc(&h->d_tofs, L.tofs.size())) return TG_ERR_OOM;
+      TG_CK(cudaMemcpyAsync(h->d_tofs, L.tofs.data(), sizeof(int) * L.tofs.size(), cudaMemcpyHostToDevice, s));
+      h->band.tp = h->ptiles;
+      h->band.tofs = h->d_tofs;
+      h->band.ntiles = L.tofs.back();
+    }
   }
   // the patches to factor, as a compact list: rectangles, layouts, numbers
   const std::vector<int> ids = selected(h->npatch, update ? changed : nullptr);
@@ -1063,10 +1081,15 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
         launch_store_inverse<double>(inv, d_geo, first, m, nmax, (double*)h->pinv, s);
       else if (h->opt.precision == TG_PREC_F32)
         launch_store_inverse<float>(inv, d_geo, first, m, nmax, (float*)h->pinv, s);
-      else if (h->opt.precision == TG_PREC_F16)
+      else if (h->opt.precision == TG_PREC_F16) {
         launch_store_inverse_f16(inv, d_geo, h->d_gofs, first, m, nmax, (__half*)h->pinv, h->rscale, s, d_ids);
-      else
+        launch_store_inverse_tiles<__half>(inv, d_geo, h->d_gofs, d_ids, first, m, nmax, (__half*)h->ptiles,
+                                           h->rscale, s);
+      } else {
         launch_store_inverse<__nv_bfloat16>(inv, d_geo, first, m, nmax, (__nv_bfloat16*)h->pinv, s);
+        launch_store_inverse_tiles<__nv_bfloat16>(inv, d_geo, h->d_gofs, d_ids, first, m, nmax,
+                                                  (__nv_bfloat16*)h->ptiles, nullptr, s);
+      }
     }
     rc = cuda_err(cudaStreamSynchronize(s));
   }
@@ -1322,9 +1345,12 @@ int autotune_smoother_t(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaMemsetAsync(rin, 0, sizeof(TC) * nn, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
   const bool f64 = std::is_same<TS, double>::value, f16 = std::is_same<TS, __half>::value;
-  const int cand_all[] = {0, 1, 2, 3, 4, 5, 6, 7}, cand_f64[] = {0, 4, 7}, cand_f16[] = {0, 1, 2, 3, 5, 6, 7};
-  const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : cand_all;   // FP16: no TMA ring
-  const int ncand = f64 ? 3 : f16 ? 7 : 8;
+  const bool bf16 = std::is_same<TS, __nv_bfloat16>::value;
+  const int cand_bf16[] = {0, 1, 2, 3, 4, 5, 6, 7, 8}, cand_f32[] = {0, 1, 2, 3, 4, 5, 6, 7}, cand_f64[] = {0, 4, 7},
+            cand_f16[] = {0, 1, 2, 3, 5, 6, 7, 8};
+  // FP16: no TMA ring; the tensor-core tiles exist for 2-byte storage only
+  const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : bf16 ? cand_bf16 : cand_f32;
+  const int ncand = f64 ? 3 : f16 ? 8 : bf16 ? 9 : 8;
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {
@@ -1364,6 +1390,7 @@ int choose_smoother_shape(tg_handle* h) {
   if (h->opt.smoother_shape >= 0) {
     h->shape = h->opt.smoother_shape;
     if (h->opt.precision == TG_PREC_F16 && h->shape == 4) h->shape = 0;   // no TMA ring for FP16
+    if (h->shape == kShapeTensor && !h->ptiles) h->shape = 0;            // tiles exist for 2-byte storage only
     return TG_OK;
   }
   if (h->opt.precision == TG_PREC_F64) return autotune_smoother_t<double, double>(h);
@@ -1880,8 +1907,8 @@ void tg_destroy(tg_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   ctx_free(h->ctx);
-  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->pband, h->rscale, h->blk_band, h->lam,
-                  h->d_bgeo, h->d_bgofs, h->binv, h->binv32, h->kcoef};
+  void* ptrs[] = {h->kinv, h->kinv32, h->d_status, h->d_pgeo, h->d_gofs, h->pinv, h->pband, h->ptiles, h->d_tofs,
+                  h->rscale, h->blk_band, h->lam, h->d_bgeo, h->d_bgofs, h->binv, h->binv32, h->kcoef};
   for (void* ptr : ptrs) cudaFree(ptr);
   free_space(h->cs);
   free_space(h->rt);

@@ -51,6 +51,7 @@ struct PatchGeo {
   int nloc;        // nx * ny
   int ld;          // row stride of the stored inverse (multiple of 8)
   long long off;   // element offset of the stored inverse
+  long long toff;  // element offset of the inverse in the tensor-core tile layout (2-byte storage)
 };
 
 // Scalars of the PCG iteration, updated only by the last CTA of a
@@ -107,6 +108,7 @@ template <> __device__ __forceinline__ float from_d<float>(double x) { return (f
 template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double x) {
   return __float2bfloat16_rn((float)x);
 }
+template <> __device__ __forceinline__ __half from_d<__half>(double x) { return __double2half(x); }
 
 // Coarse basis tiles are stored in the preconditioner precision, except with
 // FP16 patch inverses, whose tiles stay FP32 (they are a small fraction of the
@@ -265,8 +267,20 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 // shared-memory ring; 5 = shape 3 and 6 = shape 1, software-pipelined (the
 // next pass's rows in flight while the current one is reduced).  FP64 storage
 // uses shape 0 for 1..3, 5, 6; FP16 storage uses shape 0 for 4.
-constexpr int kSmootherShapes = 8;
+constexpr int kSmootherShapes = 9;
 constexpr int kShapeBand = 7;   // smoother from the patches' band Cholesky factors (two triangular solves)
+// The patch inverses applied on the tensor cores (2-byte storage; FP32 and
+// FP64 storage use shape 0): 16 x 16 tiles stored in the A-fragment order
+// of mma.m16n8k16, the residual split into three 2-byte parts as the
+// columns of B.  Tile layout of patch p at toff (elements): T = ceil(nloc /
+// 16) tiles per side, tile (i, j) (rows 16 i.., columns 16 j..) at
+// toff + (i T + j) 256, lane l's eight entries at + 8 l: entries e = 0..7 are
+// (row 16 i + l / 4 + 8 ((e >> 1) & 1), column 16 j + 2 (l % 4) + (e & 1) +
+// 8 (e >> 2)), zero outside the matrix; FP16 rows carry the row scaling of
+// the row layout.
+constexpr int kShapeTensor = 8;
+constexpr int kTile = 16;
+__host__ __device__ inline int tiles_per_side(int nloc) { return (nloc + kTile - 1) / kTile; }
 // band factors of the oversampled patches in the arithmetic type, two
 // layouts per patch (patch p at p * stride, the second at + stride / 2):
 // column layout, entry (j, d) = L_{j+d, j} (the column below the diagonal;
@@ -287,10 +301,17 @@ static_assert(kBandPad >= kBandPF && kBandPad % 4 == 0 && kBandPF % 4 == 0,
 inline long long band_rows(int nmax) {
   return (long long)(nmax + kBandPF - 1) / kBandPF * kBandPF + 2 * kBandPad;
 }
+// the patch factors in the layouts other than the dense rows: band factors
+// (shape kShapeBand) and tensor-core tiles (shape kShapeTensor; tofs[p] the
+// first 16-row tile of patch p in the global tile order, tofs[npatch] their
+// total, as gofs is for 4-row groups)
 struct BandRef {
   const void* p = nullptr;
   int ldb = 0;
   long long stride = 0;
+  const void* tp = nullptr;
+  const int* tofs = nullptr;
+  int ntiles = 0;
 };
 // rscale: FP16 storage only, one power-of-two factor per stored row (index
 // gofs[p] * kRowsPerGroup + row) that undoes the row's scaling.
@@ -384,6 +405,12 @@ void launch_store_inverse(const double* scratch, const PatchGeo* geo, int first,
 // (optional): patch numbers of a compacted geo list
 void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const int* gofs, int first, int count,
                               int nmax, __half* pinv, float* rscale, cudaStream_t s, const int* pidx = nullptr);
+// The same inverses in the tensor-core tile layout (kShapeTensor; TS 2-byte).
+// FP16: each row scaled as the row layout scales it (rscale, written by
+// launch_store_inverse_f16 before, indexed through gofs and pidx).
+template <typename TS>
+void launch_store_inverse_tiles(const double* scratch, const PatchGeo* geo, const int* gofs, const int* pidx,
+                                int first, int count, int nmax, TS* tiles, const float* rscale, cudaStream_t s);
 // Snapshot functions of every (block, side): nfn functions per side whose
 // coefficient vectors over {m, d_1..d_{b-1}} are coef[face][fn][0..b-1]
 // (coef NULL: the unit vectors, nfn = b).  Sides with mask[blk*4+side] == 0

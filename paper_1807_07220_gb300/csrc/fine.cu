@@ -647,6 +647,47 @@ struct ChainSet {
   int k;
 };
 
+// The residual of patch p gathered into xs[0 .. fill) (zero past nloc), with
+// the fused work of kFused (see k_smoother): mode 1 forms r - alpha q and,
+// where this CTA owns block p, writes r and x += alpha p there and clears
+// the other z buffer; mode 2 forms r - K z_in and the owner seeds the output
+// with z_in.
+template <typename TC, typename TR, int kFused>
+__device__ __forceinline__ void smoother_gather(const PatchGeo& g, int p, bool owner, const TR* __restrict__ r,
+                                                TC* __restrict__ zacc, int n, const FuseArgs& fa, double alpha,
+                                                TC* xs, int fill) {
+  for (int q = threadIdx.x; q < fill; q += blockDim.x) {
+    TC v = (TC)0;
+    if (q < g.nloc) {
+      const int a = q % g.nx, c = q / g.nx;
+      const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
+      if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+      else if constexpr (kFused == 2)
+        v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
+                                                  g.y0 + 1 + c);
+      else v = (TC)r[id];
+    }
+    xs[q] = v;
+  }
+  if (kFused == 1 && owner) {   // this CTA owns block p
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      const double rv = fa.r_old[id] - alpha * fa.q[id];
+      fa.r_new[id] = rv;
+      fa.x[id] += alpha * fa.p[id];
+      if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
+    }
+  }
+  if (kFused == 2 && owner) {   // the owner seeds the output with z_in
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      atomicAdd(zacc + id, ((const TC*)fa.zin)[id]);
+    }
+  }
+}
+
 // kFused: 0 plain sweep z += eta S r; 1 first sweep of an iteration (r - alpha q
 // formed at gather time, r and x updated by the block owners); 2 last sweep
 // with the residual formed at gather time,
@@ -685,36 +726,7 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
   for (; g0 < g1 && p < npatch && gofs[p] < g1; ++p) {
     const PatchGeo g = geo[p];
     __syncthreads();
-    for (int q = threadIdx.x; q < g.ld; q += blockDim.x) {
-      TC v = (TC)0;
-      if (q < g.nloc) {
-        const int a = q % g.nx, c = q / g.nx;
-        const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
-        if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
-        else if constexpr (kFused == 2)
-          v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
-                                                    g.y0 + 1 + c);
-        else v = (TC)r[id];
-      }
-      xs[q] = v;
-    }
-    if (kFused == 1 && gofs[p] >= g0) {   // this CTA owns block p
-      const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
-      for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
-        const double rv = fa.r_old[id] - alpha * fa.q[id];
-        fa.r_new[id] = rv;
-        fa.x[id] += alpha * fa.p[id];
-        if (fa.zclear) ((TC*)fa.zclear)[id] = (TC)0;
-      }
-    }
-    if (kFused == 2 && gofs[p] >= g0) {   // the owner seeds the output with z_in
-      const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
-      for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
-        atomicAdd(zacc + id, ((const TC*)fa.zin)[id]);
-      }
-    }
+    smoother_gather<TC, TR, kFused>(g, p, gofs[p] >= g0, r, zacc, n, fa, alpha, xs, g.ld);
     __syncthreads();
     const int ga = max(g0, gofs[p]) - gofs[p], gb = min(g1, gofs[p + 1]) - gofs[p];
     const TS* M = pinv + g.off;
@@ -781,6 +793,168 @@ __global__ void __launch_bounds__(kThreads) k_smoother(const PatchGeo* __restric
         if (t + 1 < nseq) {
           if (t + 2 < nseq) load_rows(bA, row_at(t + 2));
           reduce_rows(bB, row_at(t + 1));
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core variant (tile shape kShapeTensor, BF16 / FP16 storage).  The
+// CUDA-core sweep spends two instructions per stored 2-byte entry (unpack,
+// FMA) plus a warp reduction per row, and at grids whose inverses stay in L2
+// that instruction stream, not the bytes, bounds it.  Here a warp takes
+// 16-row tiles of a patch inverse: per 16 x 16 tile one 16-byte load per lane
+// (the tiles are stored in A-fragment order) and one mma.m16n8k16 against
+// B = [x_hi x_mid x_lo 0 ...], the residual split into three 2-byte parts
+// (x = x_hi + x_mid + x_lo to 2^-24 relative), FP32 accumulation.  The row
+// result is the sum of the first three accumulator columns.  FP16 storage
+// scales the residual by a per-patch power of two (its largest magnitude in
+// [2^14, 2^15)) before the split and undoes it with the row scale.  Gather
+// and fused modes are those of k_smoother, with 16-row tiles (tofs) in place
+// of 4-row groups.  When the wave holds at least one CTA per patch, each
+// patch's tiles are cut evenly among k = grid / npatch CTAs (one gather per
+// CTA, no search); otherwise CTAs take equal contiguous tile ranges, as
+// k_smoother takes row groups.
+static_assert((kMaxPatchNodes + kTile - 1) / kTile * kTile <= kPatchLd, "the tile rows must fit the shared residual");
+constexpr int kTileBatch = 8;   // tiles of a row in flight per lane
+
+template <typename TS> struct MmaTile;
+template <> struct MmaTile<__nv_bfloat16> {
+  static __device__ __forceinline__ unsigned short to16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+  static __device__ __forceinline__ float from16(unsigned short v) {
+    return __bfloat162float(__ushort_as_bfloat16(v));
+  }
+  static __device__ __forceinline__ void mma(float (&d)[4], const uint4& a, const uint2& b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  }
+};
+template <> struct MmaTile<__half> {
+  static __device__ __forceinline__ unsigned short to16(float x) { return __half_as_ushort(__float2half_rn(x)); }
+  static __device__ __forceinline__ float from16(unsigned short v) { return __half2float(__ushort_as_half(v)); }
+  static __device__ __forceinline__ void mma(float (&d)[4], const uint4& a, const uint2& b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  }
+};
+// part k (0, 1, 2) of x: each part is the 2-byte rounding of what the
+// previous parts leave (each difference is exact in FP32)
+template <typename TS>
+__device__ __forceinline__ unsigned part16(float x, int k) {
+  unsigned short v = MmaTile<TS>::to16(x);
+  for (int t = 0; t < k; ++t) {
+    x -= MmaTile<TS>::from16(v);
+    v = MmaTile<TS>::to16(x);
+  }
+  return v;
+}
+
+template <typename TC, typename TS, typename TR, int kFused>
+__global__ void __launch_bounds__(kThreads, 4) k_smoother_mma(const PatchGeo* __restrict__ geo,
+                                                           const int* __restrict__ tofs,
+                                                           const int* __restrict__ gofs, int npatch,
+                                                           const TS* __restrict__ tiles,
+                                                           const TR* __restrict__ r,
+                                                           TC* __restrict__ zacc, TC eta, int n,
+                                                           const PcgState* st, FuseArgs fa,
+                                                           const float* __restrict__ rscale) {
+  pdl_entry();
+  const int done = st ? st->done : 0;   // tested after the first loads (see k_pcg_apply_p)
+  constexpr bool kHalf = std::is_same<TS, __half>::value;
+  __shared__ __align__(16) TC xs[kPatchLd];
+  __shared__ __align__(16) uint2 xb[(kPatchLd / kTile) * 12];
+  const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
+  int t0, t1;
+  __shared__ int sp;
+  if (gridDim.x >= (unsigned)npatch && gridDim.x % npatch == 0) {
+    const int k = gridDim.x / npatch, pp = blockIdx.x / k, piece = blockIdx.x % k;
+    const int base = tofs[pp], nt = tofs[pp + 1] - base;
+    t0 = base + piece * nt / k;
+    t1 = base + (piece + 1) * nt / k;
+    if (threadIdx.x == 0) sp = pp;
+    __syncthreads();
+  } else {
+    const int RT = tofs[npatch];
+    const long long per = ((long long)RT + gridDim.x - 1) / gridDim.x;
+    t0 = (int)min((long long)RT, blockIdx.x * per);
+    t1 = (int)min((long long)RT, t0 + per);
+    // the patch holding tile t0 (tofs strictly increasing; see k_smoother)
+    if (threadIdx.x == 0) sp = npatch - 1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < npatch; t += blockDim.x)
+      if (tofs[t] <= t0 && tofs[t + 1] > t0) sp = t;
+    __syncthreads();
+  }
+  if (done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = sp; t0 < t1 && p < npatch && tofs[p] < t1; ++p) {
+    const PatchGeo g = geo[p];
+    const int T = tiles_per_side(g.nloc);
+    __syncthreads();
+    smoother_gather<TC, TR, kFused>(g, p, tofs[p] >= t0, r, zacc, n, fa, alpha, xs, T * kTile);
+    __syncthreads();
+    float sx = 1.0f, unscale = 1.0f;
+    if constexpr (kHalf) {   // every warp forms the patch's residual scale
+      float m = 0.0f;
+      for (int q = lane; q < g.nloc; q += 32) m = fmaxf(m, fabsf((float)xs[q]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (m > 0.0f) {
+        int e = 0;
+        frexpf(m, &e);
+        sx = ldexpf(1.0f, 15 - e);
+        unscale = ldexpf(1.0f, e - 15);
+      }
+    }
+    // B fragments: lane l < 12 of k-tile j holds part l / 4 of x at columns
+    // 16 j + 2 (l % 4) + {0, 1} and the same + 8; lanes 12..31 hold zeros
+    for (int e = threadIdx.x; e < T * 12; e += blockDim.x) {
+      const int j = e / 12, l = e % 12, k = l >> 2, c0 = kTile * j + 2 * (l & 3);
+      auto pk = [&](int q) { return part16<TS>((float)xs[q] * sx, k); };
+      xb[e] = make_uint2(pk(c0) | (pk(c0 + 1) << 16), pk(c0 + 8) | (pk(c0 + 9) << 16));
+    }
+    __syncthreads();
+    const int ta = max(t0, tofs[p]) - tofs[p], tb = min(t1, tofs[p + 1]) - tofs[p];
+    const uint4* A = reinterpret_cast<const uint4*>(tiles + g.toff) + lane;
+    for (int i = ta + warp; i < tb; i += nw) {
+      // two accumulators (even and odd k-tiles), so consecutive mma do not wait on each other
+      float d[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const uint4* Ai = A + (long long)i * T * 32;
+      for (int j0 = 0; j0 < T; j0 += kTileBatch) {
+        uint4 a[kTileBatch];
+#pragma unroll
+        for (int u = 0; u < kTileBatch; ++u) a[u] = (j0 + u < T) ? __ldg(Ai + (j0 + u) * 32) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < kTileBatch; ++u) {
+          if (j0 + u < T) {   // uniform over the warp
+            const uint2 bv = (lane < 12) ? xb[(j0 + u) * 12 + lane] : make_uint2(0u, 0u);
+            if (u & 1) MmaTile<TS>::mma(d2, a[u], bv);
+            else MmaTile<TS>::mma(d, a[u], bv);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d[k] += d2[k];
+      // lane 4 g holds columns 0 and 1 (hi, mid) of rows g and g + 8, lane 4 g + 1 column 2 (lo)
+      const float lo0 = __shfl_down_sync(0xffffffffu, d[0], 1), lo1 = __shfl_down_sync(0xffffffffu, d[2], 1);
+      if ((lane & 3) == 0) {
+        const float y[2] = {d[0] + d[1] + lo0, d[2] + d[3] + lo1};
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int q = kTile * i + (lane >> 2) + 8 * hh;
+          if (q < g.nloc) {
+            TC v = (TC)y[hh];
+            if constexpr (kHalf) v *= (TC)(rscale[(long long)gofs[p] * kRowsPerWarp + q] * unscale);
+            const int a2 = q % g.nx, c2 = q / g.nx;
+            atomicAdd(zacc + (long long)(g.y0 + 1 + c2) * n + (g.x0 + 1 + a2), eta * v);
+          }
         }
       }
     }
@@ -1624,6 +1798,30 @@ void smoother_go(const PatchGeo* geo, const int* gofs, int npatch, int ngroups, 
 }
 
 template <typename TC, typename TS, typename TR, int kFused>
+int smoother_mma_per_sm() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother_mma<TC, TS, TR, kFused>, kThreads, 0);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  return per_sm;
+}
+
+// tensor-core sweep: one wave of CTAs, at least one 16-row tile per warp
+template <typename TC, typename TS, typename TR, int kFused>
+void smoother_mma_go(const PatchGeo* geo, const int* gofs, int npatch, const TR* r, TC* zacc, double eta, int n,
+                     const PcgState* st, const FuseArgs& fa, const float* rscale, const BandRef& band,
+                     cudaStream_t s) {
+  int grid = smoother_mma_per_sm<TC, TS, TR, kFused>() * sm_count();
+  const int min_tiles_per_cta = kThreads / 32;
+  if (grid * min_tiles_per_cta > band.ntiles) grid = (band.ntiles + min_tiles_per_cta - 1) / min_tiles_per_cta;
+  if (grid >= npatch) grid = grid / npatch * npatch;
+  if (grid < 1) grid = 1;
+  launch(k_smoother_mma<TC, TS, TR, kFused>, dim3(grid), dim3(kThreads), 0, s, geo, band.tofs, gofs, npatch,
+         (const TS*)band.tp, r, zacc, (TC)eta, n, st, fa, rscale);
+}
+
+template <typename TC, typename TS, typename TR, int kFused>
 void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                     const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
                     const float* rscale, cudaStream_t s, BandRef band = {}) {
@@ -1634,6 +1832,15 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
     return;
   }
   if (shape == kShapeBand) shape = 0;
+  if (shape == kShapeTensor) {
+    if constexpr (sizeof(TS) == 2) {
+      if (band.tp) {
+        smoother_mma_go<TC, TS, TR, kFused>(geo, gofs, npatch, r, zacc, eta, n, st, fa, rscale, band, s);
+        return;
+      }
+    }
+    shape = 0;
+  }
   constexpr bool kHalf = std::is_same<TS, __half>::value;
   // the TMA ring has no row scaling and no residual-fused mode
   if ((kHalf || kFused == 2) && shape == 4) shape = 0;
@@ -1674,6 +1881,7 @@ void smoother_prepare() {
     smoother_per_sm<TC, TS, TR, kFused, 8, 2, true>();
     smoother_per_sm<TC, TS, TR, kFused, 16, 2, true>();
   }
+  if constexpr (sizeof(TS) == 2) smoother_mma_per_sm<TC, TS, TR, kFused>();
 }
 
 template <typename TC, typename TS, typename TR>

@@ -322,6 +322,38 @@ __global__ void k_store_inverse_f16(const double* __restrict__ scratch, const Pa
   }
 }
 
+// Patch inverses in the tensor-core tile layout (see kShapeTensor): entry e
+// of lane l of tile (i, j) is M(16 i + l / 4 + 8 ((e >> 1) & 1),
+// 16 j + 2 (l % 4) + (e & 1) + 8 (e >> 2)), the A-fragment order of
+// mma.m16n8k16, zero outside the matrix.  FP16 rows are divided by their
+// rscale (a power of two, so the stored value equals the row layout's).
+template <typename TS>
+__global__ void k_store_inverse_tiles(const double* __restrict__ scratch, const PatchGeo* __restrict__ geo,
+                                      const int* __restrict__ gofs, const int* __restrict__ pidx, int first, int nmax,
+                                      TS* __restrict__ tiles, const float* __restrict__ rscale) {
+  const int c = first + blockIdx.x;
+  const PatchGeo g = geo[c];
+  const int p = pidx ? pidx[c] : c;
+  const double* X = scratch + (long long)blockIdx.x * nmax * nmax;
+  TS* out = tiles + g.toff;
+  const int T = tiles_per_side(g.nloc);
+  const long long tot = (long long)T * T * kTile * kTile;
+  for (long long t = threadIdx.x + (long long)blockIdx.y * blockDim.x; t < tot;
+       t += (long long)blockDim.x * gridDim.y) {
+    const int tile = (int)(t >> 8), w = (int)(t & 255);
+    const int lane = w >> 3, e = w & 7;
+    const int i = tile / T, j = tile % T;
+    const int row = kTile * i + (lane >> 2) + 8 * ((e >> 1) & 1);
+    const int col = kTile * j + 2 * (lane & 3) + (e & 1) + 8 * (e >> 2);
+    double v = 0.0;
+    if (row < g.nloc && col < g.nloc) {
+      v = X[(long long)max(row, col) * g.nloc + min(row, col)];   // lower triangle formed: symmetric read
+      if (rscale) v /= (double)rscale[(long long)gofs[p] * kRowsPerGroup + row];
+    }
+    out[t] = from_d<TS>(v);
+  }
+}
+
 // band factor of compact patch c (band rows L[j][d] = L_{j, j-d}) in the
 // smoother's two padded band layouts at out + ids[c] * stride: column layout
 // (entry (j, d >= 1) = L_{j+d, j}) then row layout (entry (j, d >= 1) =
@@ -1390,6 +1422,17 @@ void launch_store_inverse_f16(const double* scratch, const PatchGeo* geo, const 
   k_store_inverse_f16<<<dim3(count, split_for(count, nmax, 8)), 256, 0, s>>>(scratch, geo, pidx, gofs, first, nmax,
                                                                              pinv, rscale);
 }
+template <typename TS>
+void launch_store_inverse_tiles(const double* scratch, const PatchGeo* geo, const int* gofs, const int* pidx,
+                                int first, int count, int nmax, TS* tiles, const float* rscale, cudaStream_t s) {
+  if (count == 0) return;
+  k_store_inverse_tiles<TS><<<dim3(count, split_for(count, nmax, 8)), 256, 0, s>>>(scratch, geo, gofs, pidx, first,
+                                                                                   nmax, tiles, rscale);
+}
+template void launch_store_inverse_tiles<__nv_bfloat16>(const double*, const PatchGeo*, const int*, const int*, int,
+                                                        int, int, __nv_bfloat16*, const float*, cudaStream_t);
+template void launch_store_inverse_tiles<__half>(const double*, const PatchGeo*, const int*, const int*, int, int,
+                                                 int, __half*, const float*, cudaStream_t);
 void launch_snapshots(const double* kinv, const double* blk_band, const double* coef, int nfn,
                       const unsigned char* mask, double* psiS, double* gram, int n, int b, cudaStream_t s) {
   const int nc = n / b, nloc = (b - 1) * (b - 1), threads = 256;

@@ -170,7 +170,9 @@ def test_additive_cycle_mixed_precision(tg):
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f16"])
 def test_smoother_tile_shapes(tg, prec):
     """Every smoother tile shape (16- or 8-byte loads, 2 or 4 rows per pass,
-    TMA ring, software-pipelined passes) computes the same smoother: against
+    TMA ring, software-pipelined passes, tensor-core tiles for 2-byte storage
+    with the residual split into three 2-byte parts) computes the same
+    smoother: against
     shape 0 to FP32 summation order (same stored inverses), against the
     oracle to the storage precision.  The band shape (7: triangular solves
     with the band Cholesky factors in the arithmetic precision) matches the
@@ -189,7 +191,7 @@ def test_smoother_tile_shapes(tg, prec):
     tol_oracle = {"f64": 1e-9, "f32": 2e-5, "bf16": 2e-2, "f16": 5e-3}[prec]
     tol_band = 1e-9 if prec == "f64" else 1e-4
     outs = {}
-    for shape in range(8):
+    for shape in range(9):
         s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"), smoother_shape=shape)
         try:
             z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
@@ -199,17 +201,20 @@ def test_smoother_tile_shapes(tg, prec):
             assert rel(outs[shape], ref) < tol, (prec, shape, rel(outs[shape], ref))
             it, rep = s.solve(f, rtol=1e-12)
             got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
-            ran = 0 if (prec == "f16" and shape == 4) else shape       # FP16 has no TMA ring
+            ran = shape
+            if (prec == "f16" and shape == 4) or (prec in ("f32", "f64") and shape == 8):
+                ran = 0        # FP16 has no TMA ring; the tensor-core tiles exist for 2-byte storage
             assert rel(got_u, u_ref) < 1e-8 and rep.smoother_shape == ran
         finally:
             s.close()
-    for shape in range(1, 7):
-        assert rel(outs[shape], outs[0]) < (1e-12 if prec == "f64" else 2e-6), (prec, shape)
+    for shape in (1, 2, 3, 4, 5, 6, 8):
+        assert rel(outs[shape], outs[0]) < (1e-12 if prec == "f64" else 2e-6), (prec, shape, rel(outs[shape], outs[0]))
     s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"))
     try:
         it, rep = s.solve(f, rtol=1e-8)
         times = rep.shape_times()
-        tried = {"f64": [0, 4, 7], "f16": [0, 1, 2, 3, 5, 6, 7]}.get(prec, [0, 1, 2, 3, 4, 5, 6, 7])
+        tried = {"f64": [0, 4, 7], "f16": [0, 1, 2, 3, 5, 6, 7, 8], "f32": [0, 1, 2, 3, 4, 5, 6, 7]}.get(
+            prec, [0, 1, 2, 3, 4, 5, 6, 7, 8])
         assert all(times[k] > 0 for k in tried)
         assert rep.smoother_shape in tried and times[rep.smoother_shape] == min(times[k] for k in tried)
     finally:
@@ -252,6 +257,45 @@ def test_band_smoother_at_block_16(tg, prec):
             (prec, rel(got_u, u_ref), rel(s.p.cpu().numpy().ravel(), p_ref))
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_tensor_smoother_at_block_16(tg, prec):
+    """The tensor-core smoother (tile shape 8) at b = 16 on 64 x 64, where the
+    wave holds several CTAs per patch (the patch-aligned split): against the
+    dense row shape 0 on the same stored inverses to FP32 summation order
+    (the residual split into three 2-byte parts keeps 24 bits), against the
+    oracle to the storage precision, linear in the residual's scale over 24
+    decades (the FP16 path scales each patch's residual by a power of two),
+    and a solve with it against the direct solve."""
+    n, b = 64, 16
+    kappa = inputs.grf_channel_field(n, 1e6, 5)
+    o = TwoGridSolver(n, b, kappa, tol=10.0)
+    rng = np.random.default_rng(3)
+    r = o.project(rng.standard_normal(o.If.size))
+    ref = o.smoother(r)
+    rho = psi_from_interior(n, o.C.T @ r)
+    outs = {}
+    for shape in (0, 8):
+        s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=1, smoother_shape=shape)
+        try:
+            for scale in (1.0, 1e-12, 1e12):
+                z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+                tg.tg_apply_smoother(s.h, dev(scale * rho), z)
+                outs[(shape, scale)] = o.C @ interior_from_psi(n, z.cpu().numpy()) / scale
+            if shape == 8:
+                f = inputs.quarter_five_spot(n)
+                it, rep = s.solve(f, rtol=1e-12)
+                assert rep.converged == 1 and rep.smoother_shape == 8
+                u_ref, p_ref = solve_direct(Grid(n, b), kappa, f)
+                got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+                assert rel(got_u, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+        finally:
+            s.close()
+    tol_oracle = {"bf16": 2e-2, "f16": 5e-3}[prec]
+    for scale in (1.0, 1e-12, 1e12):
+        assert rel(outs[(8, scale)], outs[(0, 1.0)]) < 2e-6, (prec, scale, rel(outs[(8, scale)], outs[(0, 1.0)]))
+        assert rel(outs[(8, scale)], ref) < tol_oracle
 
 
 def test_spectra_and_selection(case, tg):
