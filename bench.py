@@ -56,15 +56,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fine DOF-solves/s to 1e-8 rel. residual vs plain FP64; PCG iters; HBM %"
 N_DEFAULT, B_DEFAULT, CONTRAST, EIG_TOL, RTOL = 256, 16, 1e6, 10.0, 1e-8
-# DRAM bytes (read + write) per smoother launch at the default workload, mean of
-# the two sweeps of an iteration (r - alpha q and r - K z formed at gather time),
-# from the ncu capture summarised in
-# profiles/k_smoother_256x256.md, keyed by (storage precision, tile shape);
-# valid only for the kernel version and shape profiled there
 # DRAM bytes per smoother launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the captured launches of both sweeps) of the current kernels:
-# 256 x 256 BF16 dense shape 2, and 1024 x 1024 FP16 handle with the band form
-SMOOTHER_TRAFFIC = {("bf16", 2): 66.51e6, ("f16", 7): 335.3e6}
+# 256 x 256 BF16 dense shape 2 and tensor-core shape 8, and 1024 x 1024 FP16
+# handle with the band form
+SMOOTHER_TRAFFIC = {("bf16", 2): 66.51e6, ("bf16", 8): 68.44e6, ("f16", 7): 335.3e6}
 
 
 def dof(n):
@@ -379,7 +375,9 @@ def run_ours(args):
         "gpu_launches": sum(r.kernel_launches for r in reps),
         "gpu_launches_per_step": reps[-1].kernel_launches,
         "roofline": {"bound": "hbm",
-                     "kernel": "k_smoother_band (patch band solves)" if band else "k_smoother (patch inverse apply)",
+                     "kernel": "k_smoother_band (patch band solves)" if band else
+                     "k_smoother_mma (patch inverse apply, tensor-core tiles)" if shape == 8 else
+                     "k_smoother (patch inverse apply)",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                      "traffic": SMOOTHER_TRAFFIC.get((prec, shape)),
