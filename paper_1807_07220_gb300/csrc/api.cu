@@ -178,6 +178,7 @@ void free_space(CoarseSpace& c) {
   cudaFree(c.closed);
   cudaFree(c.owned);
   cudaFree(c.Kinv);
+  cudaFree(c.Kdf);
   c = CoarseSpace{};
 }
 
@@ -315,6 +316,17 @@ int assemble_galerkin(tg_handle* h, const CoarseSpace& c, const double* kinv, do
   return rc ? rc : cuda_err(cudaGetLastError());
 }
 
+// The double-float copy of the preconditioner's coarse inverse, formed again
+// after every change of Kinv (mixed-precision handles whose coarse solve is a
+// separate GEMV, D > kCoarseSplit; FP64 handles and the preprocessing's RT0
+// space keep the FP64 GEMV)
+int refresh_coarse_df(tg_handle* h, CoarseSpace& c) {
+  if (&c != &h->cs || h->opt.precision == TG_PREC_F64 || c.D <= kCoarseSplit) return TG_OK;
+  if (!c.Kdf && dalloc(&c.Kdf, (size_t)c.D * c.D)) return TG_ERR_OOM;
+  launch_split_df(c.Kinv, c.Kdf, (long long)c.D * c.D, h->stream);
+  return cuda_err(cudaStreamSynchronize(h->stream));
+}
+
 // Galerkin matrix of a coarse space with the handle's current kappa, and its
 // inverse (dense Gauss-Jordan)
 int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
@@ -327,6 +339,7 @@ int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
     rc = cuda_err(cudaStreamSynchronize(h->stream));
   }
   c.low_rank_updates = 0;
+  if (rc == TG_OK) rc = refresh_coarse_df(h, c);
   if (rc == TG_OK) rc = cuda_err(cudaGetLastError());
   return rc;
 }
@@ -411,7 +424,8 @@ int galerkin_update(tg_handle* h, CoarseSpace& c, const double* delta, const uns
   if (bad) return galerkin_inverse(h, c);
   ++c.low_rank_updates;
   *rank = m;
-  return cuda_err(cudaGetLastError());
+  rc = refresh_coarse_df(h, c);
+  return rc ? rc : cuda_err(cudaGetLastError());
 }
 
 // extreme eigenvalues of the Lanczos tridiagonal by Sturm bisection (report only)

@@ -93,9 +93,16 @@ struct CoarseSpace {
   double* closed = nullptr;  // nslots*(b+1)^2 FP64 tiles (device)
   void* owned = nullptr;     // nslots*b*b tiles in storage precision (device)
   double* Kinv = nullptr;    // D*D inverse of the Galerkin matrix (device)
+  // mixed-precision handles with D > kCoarseSplit: Kinv as double-float
+  // pairs (hi, lo: FP32, hi + lo = Kinv to ~2^-48), applied on the FP32 pipe
+  float2* Kdf = nullptr;
   int low_rank_updates = 0;  // low-rank updates of Kinv since it was last inverted in full
   int max_slots_per_block = 0;
 };
+
+constexpr int kCoarseSplit = 1024;   // coarse systems larger than this form their right-hand side once
+// Kinv (m entries) into double-float pairs: hi = fl32(x), lo = fl32(x - hi)
+void launch_split_df(const double* a, float2* b, long long m, cudaStream_t s);
 
 // ---- small device helpers --------------------------------------------------
 __device__ __forceinline__ float to_f(float x) { return x; }

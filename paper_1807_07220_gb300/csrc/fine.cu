@@ -18,7 +18,6 @@ namespace tg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCoarseSplit = 1024;   // coarse systems larger than this form their right-hand side once
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -1559,6 +1558,85 @@ __global__ void k_coarse_rhs(const double* __restrict__ part, const int* __restr
   }
 }
 
+// Double-float GEMV (mixed-precision handles): d = Kinv c with Kinv and c
+// as FP32 pairs (hi + lo), each product formed exactly by TwoProduct (the FMA
+// residual of hi * hi) plus the two cross terms, and accumulated by
+// compensated summation (Knuth's TwoSum), per lane and in the warp
+// reduction; about 48 significant bits, on the FP32 pipe.  The FP64 GEMV
+// reads the same 8 bytes per entry but is bound by this part's FP64 rate.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_fma(float& h, float& l, float2 k, float2 c) {
+  const float p = k.x * c.x;
+  float pe = fmaf(k.x, c.x, -p);   // the exact rounding error of k.x * c.x
+  pe = fmaf(k.x, c.y, fmaf(k.y, c.x, pe));
+  float sum, err;
+  two_sum(h, p, sum, err);
+  h = sum;
+  l += err + pe;
+}
+__global__ void k_coarse_rhs_df(const double* __restrict__ part, const int* __restrict__ gather,
+                                float2* __restrict__ c, int D, const PcgState* st) {
+  pdl_entry();
+  if (st && st->done) return;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < D; u += gridDim.x * blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int g = gather[4 * u + k];
+      if (g >= 0) v += part[g];
+    }
+    const float hi = (float)v;
+    c[u] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_coarse_gemv_df(const float2* __restrict__ c,
+                                                             const float2* __restrict__ Kdf,
+                                                             double* __restrict__ d, int D, const PcgState* st) {
+  pdl_entry();
+  if (st && st->done) return;
+  extern __shared__ float2 cdf[];
+  for (int u = threadIdx.x; u < D; u += blockDim.x) cdf[u] = c[u];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = blockIdx.x * nw + warp; row < D; row += gridDim.x * nw) {
+    const float2* kr = Kdf + (long long)row * D;
+    // sixteen loads in flight per lane, four independent accumulator pairs
+    float hh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ll[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int col = lane;
+    for (; col + 480 < D; col += 512) {
+      float2 kk[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) kk[u] = __ldg(kr + col + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) df_fma(hh[u & 3], ll[u & 3], kk[u], cdf[col + 32 * u]);
+    }
+    for (; col < D; col += 32) df_fma(hh[0], ll[0], __ldg(kr + col), cdf[col]);
+    float h, l, e, h2, e2;
+    two_sum(hh[0], hh[1], h, e);
+    two_sum(hh[2], hh[3], h2, e2);
+    l = (ll[0] + ll[1]) + (ll[2] + ll[3]) + e + e2;
+    two_sum(h, h2, h, e);
+    l += e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      two_sum(h, oh, h, e);
+      l += ol + e;
+    }
+    if (lane == 0) d[row] = (double)h + (double)l;
+  }
+}
+__global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const double x = a[i];
+    const float hi = (float)x;
+    b[i] = make_float2(hi, (float)(x - (double)hi));
+  }
+}
 __global__ void __launch_bounds__(kThreads) k_coarse_gemv(const double* __restrict__ c,
                                                           const double* __restrict__ Kinv,
                                                           double* __restrict__ d, int D, const PcgState* st) {
@@ -2141,9 +2219,18 @@ void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coef
   if (cs.D > kCoarseSplit) {
     double* rhs = coefs + cs.D;
     TG_COUNT(2);
-    launch(k_coarse_rhs, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rhs, cs.D, st);
     int grid = (cs.D + 7) / 8;
     if (grid > 2 * sm_count()) grid = 2 * sm_count();
+    if (cs.Kdf) {   // double-float copy (mixed precision): rhs as FP32 pairs in the same space
+      float2* rdf = reinterpret_cast<float2*>(rhs);
+      grid = std::min((cs.D + 7) / 8, 4 * sm_count());
+      launch(k_coarse_rhs_df, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rdf,
+             cs.D, st);
+      launch(k_coarse_gemv_df, dim3(grid), dim3(kThreads), sizeof(float2) * (size_t)cs.D, s, (const float2*)rdf,
+             (const float2*)cs.Kdf, coefs, cs.D, st);
+      return;
+    }
+    launch(k_coarse_rhs, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rhs, cs.D, st);
     launch(k_coarse_gemv, dim3(grid), dim3(kThreads), shm, s, rhs, cs.Kinv, coefs, cs.D, st);
     return;
   }
@@ -2193,6 +2280,11 @@ template void launch_prolong<float, float>(const CoarseSpace&, const double*, in
                                            const PcgState*, cudaStream_t);
 template void launch_prolong<float, __nv_bfloat16>(const CoarseSpace&, const double*, int, int, int, int, float*,
                                                    const PcgState*, cudaStream_t);
+
+void launch_split_df(const double* a, float2* b, long long m, cudaStream_t s) {
+  TG_COUNT(1);
+  launch(k_split_df, dim3(grid_for(m)), dim3(kThreads), 0, s, a, b, m);
+}
 
 void launch_stencil_coefs(const double* kinv, double* kcoef, int n, cudaStream_t s) {
   TG_COUNT(1);

@@ -298,6 +298,39 @@ def test_tensor_smoother_at_block_16(tg, prec):
         assert rel(outs[(8, scale)], ref) < tol_oracle
 
 
+def test_double_float_coarse_gemv(tg):
+    """A coarse system above the fused size (D > 1024): 136 x 136 with 4 x 4
+    blocks.  Mixed-precision handles apply the FP64 coarse inverse as
+    double-float pairs (about 48 bits) on the FP32 pipe; the coarse
+    correction matches the oracle's to the precision of the FP32 basis tiles
+    and the FP64 handle's to 1e-6, and a solve reaches the direct solution."""
+    n, b = 136, 4   # 33^2 = 1089 coarse nodes
+    kappa = inputs.channel_field(n, 1e4, 7)
+    o = TwoGridSolver(n, b, kappa, tol=10.0)
+    rng = np.random.default_rng(5)
+    r = o.project(rng.standard_normal(o.If.size))
+    ref = o.coarse_correction(r)
+    rho = dev(psi_from_interior(n, o.C.T @ r))
+    outs = {}
+    for prec in ("f64", "f32"):
+        s = tg.Solver(kappa, b, 10.0, precision=prec, flexible=int(prec != "f64"))
+        try:
+            z = torch.zeros(n, n, dtype=torch.float64, device=DEV)
+            tg.tg_apply_coarse(s.h, rho, z)
+            outs[prec] = o.C @ interior_from_psi(n, z.cpu().numpy())
+            f = inputs.quarter_five_spot(n)
+            it, rep = s.solve(f, rtol=1e-12)
+            assert rep.coarse_unknowns > 1024, rep.coarse_unknowns
+            u_ref, p_ref = solve_direct(Grid(n, b), kappa, f)
+            got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+            assert rel(got_u, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+        finally:
+            s.close()
+    assert rel(outs["f64"], ref) < 1e-9
+    assert rel(outs["f32"], ref) < 2e-5, rel(outs["f32"], ref)
+    assert rel(outs["f32"], outs["f64"]) < 1e-6 * 20, rel(outs["f32"], outs["f64"])
+
+
 def test_spectra_and_selection(case, tg):
     o, s, b = case["oracle"], case["solver"], case["b"]
     nsel, lam, vb = tg.tg_coarse_info(s.h, b)
