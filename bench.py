@@ -810,6 +810,72 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- network GEMMs
+def run_mlp(args):
+    """The learned basis's network on the tensor cores (tcgen05 GEMMs): the
+    forward pass over the faces of one 1024 x 1024 grid with 16 x 16 blocks
+    (8 064 faces, 612 -> 512 -> 512 -> 64) and training steps of 1 024 faces,
+    on random inputs of that shape, timed with CUDA events.  Work: 2 M (din h
+    + h h + h dout) flops per forward pass over M faces, 2 B (2 din h + 3 h h
+    + 3 h dout) per training step of B faces (forward plus the five backward
+    GEMMs).  Each call includes its operand packing (row gathers, transposes,
+    padding to the 16-byte TMA stride)."""
+    import numpy as np
+    import torch
+    from paper_1807_07220_gb300 import inputs, tgms
+    torch.cuda.set_device(0)
+    dev = "cuda"
+    b, k, hidden, F, batch = 16, 4, args.hidden, 8064, 1024
+    din, dout, npar = tgms.tg_mlp_shape(b, k, hidden)
+    g = torch.Generator(device="cpu").manual_seed(29)
+    X = (torch.rand((F, din), generator=g) * 2 - 1).to(torch.bfloat16).to(dev)
+    Q = torch.linalg.qr(torch.randn((F, b, k), generator=g))[0].transpose(1, 2).contiguous().to(dev,
+                                                                                              torch.float32)
+    params = torch.as_tensor(inputs.mlp_init_params(din, dout, hidden, 17), device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    net = tgms.Mlp(b, k, hidden, params, stream=stream)
+    y = torch.zeros((F, dout), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        net.forward(X, y)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.forward(X, y)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.mean(times)
+    fwd_flops = 2.0 * F * (din * hidden + hidden * hidden + hidden * dout)
+    nsteps = 200
+    order = torch.as_tensor(inputs.sample_order(F, nsteps * (args.steps + 1), batch, 23), device=dev)
+    net.train(X, Q, order, nsteps, batch, 1e-3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.train(X, Q, order[nsteps * batch:], nsteps * args.steps, batch, 1e-3)
+    e1.record()
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / (nsteps * args.steps)
+    step_flops = 2.0 * batch * (2 * din * hidden + 3 * hidden * hidden + 3 * hidden * dout)
+    net.close()
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    fwd_tf = fwd_flops / (fwd_ms / 1e3) / 1e12
+    line = {
+        "metric": "network forward TFLOP/s (bf16 tcgen05 GEMMs, FP32 accumulation)", "value": fwd_tf,
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "%d faces x %d-%d-%d-%d perceptron (1024^2 grid, 16x16 blocks); training steps of "
+                               "%d faces" % (F, din, hidden, hidden, dout, batch)},
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (3 GEMMs + operand packing per forward pass)",
+                     "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fwd_tf / peak if peak else None, "peak_source": src + " bf16 burst"},
+        "train_step_ms": step_ms, "train_tflops": step_flops / (step_ms / 1e3) / 1e12,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- two-phase IMPES
 def run_impes(args):
     """Two-phase IMPES (Section 6.2) at 512 x 512 with 16 x 16 blocks:
@@ -1151,7 +1217,8 @@ def main():
     ap.add_argument("--no-north-star", action="store_true",
                     help="skip the batched and 1024^2 learned comparisons against plain FP64")
     ap.add_argument("--ns-steps", type=int, default=5, help="timed steps of each north-star arm")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "learned", "impes", "ablation"])
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "learned", "impes", "ablation", "mlp"])
     ap.add_argument("--impes-steps", type=int, default=200)
     ap.add_argument("--impes-arms", default="frozen,frozen_full,rebuild,rebuild_learned",
                     help="comma-separated IMPES arms (frozen, frozen_full, rebuild, rebuild_learned)")
@@ -1180,6 +1247,8 @@ def main():
         run_impes(args)
     elif args.workload == "ablation":
         run_ablation(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_ours(args)
 

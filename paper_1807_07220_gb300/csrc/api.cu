@@ -1264,7 +1264,7 @@ int spectral_learned(tg_handle* h, const double* kd, SpectralBufs& sb) {
       rc = TG_ERR_OOM;
     if (!rc) {
       launch_face_inputs(kd, n, b, x, s);
-      mlp_forward(h->opt.net, F, x, ybuf, h1, h2, s);
+      rc = mlp_forward(h->opt.net, F, x, ybuf, h1, h2, s);
       Y = ybuf;
     }
   }
@@ -1285,6 +1285,7 @@ int spectral_learned(tg_handle* h, const double* kd, SpectralBufs& sb) {
     launch_face_spectral(A, F, s);
     rc = cuda_err(cudaMemcpyAsync(hfb.data(), fb, sizeof(int) * F, cudaMemcpyDeviceToHost, s));
     if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+    if (!rc && read_and_clear_gemm_timeout()) rc = TG_ERR_DEVICE_TIMEOUT;   // the network's GEMMs
   }
   int nfb = 0;
   for (int v : hfb) nfb += v;

@@ -491,7 +491,22 @@ void launch_add(double* y, const double* x, long long cnt, cudaStream_t s);  // 
 void launch_face_inputs(const double* kappa, int n, int b, __nv_bfloat16* x, cudaStream_t s);
 // network dimensions; y (batch x dout) = net(x) with caller scratch h1, h2 (batch x hidden)
 void mlp_dims(const tg_mlp* net, int* b, int* k, int* hidden, int* din, int* dout);
-void mlp_forward(const tg_mlp* net, int batch, const __nv_bfloat16* x, float* y, __nv_bfloat16* h1,
+
+// Tensor-core GEMM of the network (gemm_tc.cu): C (M x N) = A (M x K) B (N x K)^T,
+// bfloat16 operands K-major (rows x K, row stride ld entries, ld a multiple of
+// 8 and the base 16-byte aligned), FP32 accumulation, fused epilogue.
+enum : int { kEpiF32 = 0, kEpiReluBf16 = 1, kEpiMaskBf16 = 2 };
+struct TcOperand {
+  const __nv_bfloat16* p;
+  int rows, K, ld;
+};
+int gemm_tc(const TcOperand& a, const TcOperand& b, int M, int N, int K, const float* bias, int epi, float* outf,
+            __nv_bfloat16* outh, long long som, const __nv_bfloat16* mask, cudaStream_t s);
+// dst[r * ld + k] = src[(rmap ? rmap[r] : r) * s_row + (kmap ? kmap[k] : k) * s_k], zero for K <= k < ld
+void pack_kmajor(const __nv_bfloat16* src, long long s_row, long long s_k, const int* rmap, const int* kmap, int R,
+                 int K, int ld, __nv_bfloat16* dst, cudaStream_t s);
+int read_and_clear_gemm_timeout();   // 1 if a bounded wait of the GEMM expired since the last call
+int mlp_forward(const tg_mlp* net, int batch, const __nv_bfloat16* x, float* y, __nv_bfloat16* h1,
                  __nv_bfloat16* h2, cudaStream_t s);
 
 }  // namespace tg

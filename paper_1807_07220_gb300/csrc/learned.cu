@@ -1,7 +1,8 @@
 // Learned coarse basis: the network's face inputs, a three-layer perceptron
-// evaluated and trained with bfloat16 tensor-core GEMMs (mma.sync m16n8k16,
-// FP32 accumulation), its subspace loss and Adam, and the training-data entry
-// point (labels from the exact spectral problems of Section 4.2).
+// evaluated and trained with bfloat16 tensor-core GEMMs (tcgen05.mma with TMA
+// operand loads and TMEM accumulators, gemm_tc.cu; FP32 accumulation), its
+// subspace loss and Adam, and the training-data entry point (labels from the
+// exact spectral problems of Section 4.2).
 //
 // Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3.  Master parameters are
 // FP32 (one vector: W1 | b1 | W2 | b2 | W3 | b3, weights row-major out x in);
@@ -30,6 +31,9 @@ struct tg_mlp {
   __nv_bfloat16 *h1 = nullptr, *h2 = nullptr, *dy = nullptr, *dh1 = nullptr, *dh2 = nullptr;
   float* y = nullptr;
   double* lacc = nullptr;         // loss accumulator
+  // K-major, 16-byte-strided GEMM operands (gathered, transposed or padded)
+  __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+  long long pack_cap = 0;         // entries of pa and of pb
 };
 
 namespace tg {
@@ -56,131 +60,6 @@ __global__ void k_face_inputs(const double* __restrict__ kappa, int n, int b, __
     const double kv = (kind == 0) ? kappa[(long long)al * n + ac] : kappa[(long long)ac * n + al];
     x[(long long)f * R * C + t] = __float2bfloat16_rn((float)(log10(kv) / 3.0));
   }
-}
-
-// ---------------------------------------------------------------------------
-// C (M x N) = A (M x K) B (K x N) on bfloat16 tensor cores, FP32 accumulation.
-// A(m, k) = A[row(m) * sam + k * sak], B(k, n) = B[krow(k) * sbk + n * sbn]
-// (row / krow: optional gathers); out(m, n) at m * som + n.
-enum : int { kEpiF32 = 0, kEpiReluBf16 = 1, kEpiMaskBf16 = 2 };
-
-struct GemmArgs {
-  int M, N, K;
-  const __nv_bfloat16* A;
-  long long sam, sak;
-  const int* arow;
-  const __nv_bfloat16* B;
-  long long sbk, sbn;
-  const int* brow;
-  const float* bias;           // [N] or NULL
-  int epi;
-  float* outf;                 // kEpiF32
-  __nv_bfloat16* outh;         // kEpiReluBf16 / kEpiMaskBf16
-  long long som;
-  const __nv_bfloat16* mask;   // kEpiMaskBf16: out *= (mask(m, n) > 0), same layout as out
-};
-
-constexpr int kBM = 64, kBN = 64, kBK = 32, kLds = kBK + 8;
-
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// 64 x 64 tile per CTA, four warps of 32 x 32, K in steps of 32 staged in
-// shared memory (A row-major, B column-major: k contiguous for both).
-__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[kBM][kLds];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kLds];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += kBK) {
-#pragma unroll 4
-    for (int i = 0; i < (kBM * kBK) / 128; ++i) {
-      const int e = tid + i * 128;
-      int r, kk;
-      if (g.sak == 1) { r = e / kBK; kk = e % kBK; }
-      else { r = e % kBM; kk = e / kBM; }
-      const int gm = m0 + r, gk = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (gm < g.M && gk < g.K) {
-        const long long row = g.arow ? (long long)g.arow[gm] : (long long)gm;
-        v = g.A[row * g.sam + (long long)gk * g.sak];
-      }
-      As[r][kk] = v;
-    }
-#pragma unroll 4
-    for (int i = 0; i < (kBN * kBK) / 128; ++i) {
-      const int e = tid + i * 128;
-      int nn, kk;
-      if (g.sbk == 1) { nn = e / kBK; kk = e % kBK; }
-      else { nn = e % kBN; kk = e / kBN; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (gn < g.N && gk < g.K) {
-        const long long krow = g.brow ? (long long)g.brow[gk] : (long long)gk;
-        v = g.B[krow * g.sbk + (long long)gn * g.sbn];
-      }
-      Bs[nn][kk] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kBK; ks += 16) {
-      const int kq = ks + (lane & 3) * 2;
-      uint32_t a[2][4], bq[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = wm * 32 + mt * 16 + (lane >> 2);
-        a[mt][0] = *reinterpret_cast<const uint32_t*>(&As[r0][kq]);
-        a[mt][1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kq]);
-        a[mt][2] = *reinterpret_cast<const uint32_t*>(&As[r0][kq + 8]);
-        a[mt][3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kq + 8]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = wn * 32 + nt * 8 + (lane >> 2);
-        bq[nt][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kq]);
-        bq[nt][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kq + 8]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt], bq[nt]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = m0 + wm * 32 + mt * 16 + (lane >> 2) + (q >> 1) * 8;
-        const int c = n0 + wn * 32 + nt * 8 + (lane & 3) * 2 + (q & 1);
-        if (r >= g.M || c >= g.N) continue;
-        float v = acc[mt][nt][q];
-        if (g.bias) v += g.bias[c];
-        const long long o = (long long)r * g.som + c;
-        if (g.epi == kEpiF32) {
-          g.outf[o] = v;
-        } else if (g.epi == kEpiReluBf16) {
-          g.outh[o] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-        } else {
-          g.outh[o] = __float2bfloat16_rn(__bfloat162float(g.mask[o]) > 0.0f ? v : 0.0f);
-        }
-      }
 }
 
 // Subspace loss, one warp per sample: E = G G^T - Q Q^T (b x b, G the b x k
@@ -272,44 +151,70 @@ __global__ void k_loss_out(double* __restrict__ acc, float* __restrict__ out) {
   }
 }
 
-void gemm(const GemmArgs& a, cudaStream_t s) {
-  if (a.M <= 0 || a.N <= 0) return;
-  dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(a);
-  TG_COUNT(1);
+inline int pad8(int x) { return (x + 7) / 8 * 8; }
+
+// entries each pack buffer needs for batches of up to `rows` samples
+long long pack_need(const tg_mlp* net, int rows) {
+  const long long M = std::max({rows, net->hidden, net->din, net->dout});
+  const long long K = std::max({pad8(net->din), pad8(rows), pad8(net->hidden), pad8(net->dout)});
+  return M * K;
 }
 
-GemmArgs gemm_args(int M, int N, int K) {
-  GemmArgs a{};
-  a.M = M; a.N = N; a.K = K;
-  return a;
+int ensure_pack(tg_mlp* net, int rows) {
+  const long long need = pack_need(net, rows);
+  if (need <= net->pack_cap) return TG_OK;
+  cudaFree(net->pa);
+  cudaFree(net->pb);
+  net->pa = net->pb = nullptr;
+  net->pack_cap = 0;
+  if (cudaMalloc(&net->pa, sizeof(__nv_bfloat16) * need) != cudaSuccess ||
+      cudaMalloc(&net->pb, sizeof(__nv_bfloat16) * need) != cudaSuccess)
+    return TG_ERR_OOM;
+  net->pack_cap = need;
+  return TG_OK;
+}
+
+// a row-major (rows x K, stride ld) operand as the GEMM takes it: in place when
+// its base and stride meet the TMA rules, else copied (padded) into buf
+TcOperand operand(const __nv_bfloat16* p, int rows, int K, int ld, __nv_bfloat16* buf, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0) return TcOperand{p, rows, K, ld};
+  pack_kmajor(p, ld, 1, nullptr, nullptr, rows, K, pad8(K), buf, s);
+  return TcOperand{buf, rows, K, pad8(K)};
+}
+// the transpose of a row-major (K x rows, stride ld) matrix, with its rows
+// optionally gathered through kmap, as a K-major (rows x K) operand in buf
+TcOperand transposed(const __nv_bfloat16* p, int rows, int K, int ld, const int* kmap, __nv_bfloat16* buf,
+                     cudaStream_t s) {
+  pack_kmajor(p, 1, ld, nullptr, kmap, rows, K, pad8(K), buf, s);
+  return TcOperand{buf, rows, K, pad8(K)};
 }
 
 // forward pass over `batch` rows of x (gathered through rows when not NULL)
-void forward_rows(const tg_mlp* net, int batch, const __nv_bfloat16* x, const int* rows, float* y,
-                  __nv_bfloat16* h1, __nv_bfloat16* h2, cudaStream_t s) {
-  GemmArgs a = gemm_args(batch, net->hidden, net->din);
-  a.A = x; a.sam = net->din; a.sak = 1; a.arow = rows;
-  a.B = net->wb + net->oW1; a.sbk = 1; a.sbn = net->din;
-  a.bias = net->p + net->ob1; a.epi = kEpiReluBf16; a.outh = h1; a.som = net->hidden;
-  gemm(a, s);
-  a = gemm_args(batch, net->hidden, net->hidden);
-  a.A = h1; a.sam = net->hidden; a.sak = 1;
-  a.B = net->wb + net->oW2; a.sbk = 1; a.sbn = net->hidden;
-  a.bias = net->p + net->ob2; a.epi = kEpiReluBf16; a.outh = h2; a.som = net->hidden;
-  gemm(a, s);
-  a = gemm_args(batch, net->dout, net->hidden);
-  a.A = h2; a.sam = net->hidden; a.sak = 1;
-  a.B = net->wb + net->oW3; a.sbk = 1; a.sbn = net->hidden;
-  a.bias = net->p + net->ob3; a.epi = kEpiF32; a.outf = y; a.som = net->dout;
-  gemm(a, s);
+int forward_rows(tg_mlp* net, int batch, const __nv_bfloat16* x, const int* rows, float* y, __nv_bfloat16* h1,
+                 __nv_bfloat16* h2, cudaStream_t s) {
+  const int hid = net->hidden, din = net->din, dout = net->dout;
+  const __nv_bfloat16 *W1 = net->wb + net->oW1, *W2 = net->wb + net->oW2, *W3 = net->wb + net->oW3;
+  // H1 = relu(X W1^T + b1)
+  pack_kmajor(x, din, 1, rows, nullptr, batch, din, pad8(din), net->pa, s);
+  int rc = gemm_tc(TcOperand{net->pa, batch, din, pad8(din)}, operand(W1, hid, din, din, net->pb, s), batch, hid,
+                   din, net->p + net->ob1, kEpiReluBf16, nullptr, h1, hid, nullptr, s);
+  // H2 = relu(H1 W2^T + b2)
+  if (!rc)
+    rc = gemm_tc(operand(h1, batch, hid, hid, net->pa, s), operand(W2, hid, hid, hid, net->pb, s), batch, hid, hid,
+                 net->p + net->ob2, kEpiReluBf16, nullptr, h2, hid, nullptr, s);
+  // Y = H2 W3^T + b3
+  if (!rc)
+    rc = gemm_tc(operand(h2, batch, hid, hid, net->pa, s), operand(W3, dout, hid, hid, net->pb, s), batch, dout,
+                 hid, net->p + net->ob3, kEpiF32, y, nullptr, dout, nullptr, s);
+  return rc;
 }
 
 // loss and gradient (into net->g) of `batch` rows; loss added to net->lacc
-void loss_backward(tg_mlp* net, int batch, const __nv_bfloat16* x, const float* q, const int* rows,
-                   cudaStream_t s) {
+int loss_backward(tg_mlp* net, int batch, const __nv_bfloat16* x, const float* q, const int* rows, cudaStream_t s) {
   const int hid = net->hidden, din = net->din, dout = net->dout;
-  forward_rows(net, batch, x, rows, net->y, net->h1, net->h2, s);
+  const __nv_bfloat16 *W2 = net->wb + net->oW2, *W3 = net->wb + net->oW3;
+  int rc = forward_rows(net, batch, x, rows, net->y, net->h1, net->h2, s);
+  if (rc) return rc;
   {
     const int warps = 4;
     const size_t shm = sizeof(float) * warps * (2 * net->b * net->k + net->b * net->b);
@@ -317,35 +222,33 @@ void loss_backward(tg_mlp* net, int batch, const __nv_bfloat16* x, const float* 
                                                                           net->lacc, net->dy);
     TG_COUNT(1);
   }
-  GemmArgs a = gemm_args(dout, hid, batch);           // dW3 = dY^T H2
-  a.A = net->dy; a.sam = 1; a.sak = dout;
-  a.B = net->h2; a.sbk = hid; a.sbn = 1;
-  a.epi = kEpiF32; a.outf = net->g + net->oW3; a.som = hid;
-  gemm(a, s);
+  // dW3 = dY^T H2 (contraction over the batch)
+  rc = gemm_tc(transposed(net->dy, dout, batch, dout, nullptr, net->pa, s),
+               transposed(net->h2, hid, batch, hid, nullptr, net->pb, s), dout, hid, batch, nullptr, kEpiF32,
+               net->g + net->oW3, nullptr, hid, nullptr, s);
   k_colsum<<<(dout + 127) / 128, 128, 0, s>>>(net->dy, batch, dout, net->g + net->ob3);
-  a = gemm_args(batch, hid, dout);                    // dH2 = (dY W3) * [H2 > 0]
-  a.A = net->dy; a.sam = dout; a.sak = 1;
-  a.B = net->wb + net->oW3; a.sbk = hid; a.sbn = 1;
-  a.epi = kEpiMaskBf16; a.outh = net->dh2; a.som = hid; a.mask = net->h2;
-  gemm(a, s);
-  a = gemm_args(hid, hid, batch);                     // dW2 = dH2^T H1
-  a.A = net->dh2; a.sam = 1; a.sak = hid;
-  a.B = net->h1; a.sbk = hid; a.sbn = 1;
-  a.epi = kEpiF32; a.outf = net->g + net->oW2; a.som = hid;
-  gemm(a, s);
+  // dH2 = (dY W3) * [H2 > 0]
+  if (!rc)
+    rc = gemm_tc(operand(net->dy, batch, dout, dout, net->pa, s), transposed(W3, hid, dout, hid, nullptr, net->pb, s),
+                 batch, hid, dout, nullptr, kEpiMaskBf16, nullptr, net->dh2, hid, net->h2, s);
+  // dW2 = dH2^T H1
+  if (!rc)
+    rc = gemm_tc(transposed(net->dh2, hid, batch, hid, nullptr, net->pa, s),
+                 transposed(net->h1, hid, batch, hid, nullptr, net->pb, s), hid, hid, batch, nullptr, kEpiF32,
+                 net->g + net->oW2, nullptr, hid, nullptr, s);
   k_colsum<<<(hid + 127) / 128, 128, 0, s>>>(net->dh2, batch, hid, net->g + net->ob2);
-  a = gemm_args(batch, hid, hid);                     // dH1 = (dH2 W2) * [H1 > 0]
-  a.A = net->dh2; a.sam = hid; a.sak = 1;
-  a.B = net->wb + net->oW2; a.sbk = hid; a.sbn = 1;
-  a.epi = kEpiMaskBf16; a.outh = net->dh1; a.som = hid; a.mask = net->h1;
-  gemm(a, s);
-  a = gemm_args(hid, din, batch);                     // dW1 = dH1^T X
-  a.A = net->dh1; a.sam = 1; a.sak = hid;
-  a.B = x; a.sbk = din; a.sbn = 1; a.brow = rows;
-  a.epi = kEpiF32; a.outf = net->g + net->oW1; a.som = din;
-  gemm(a, s);
+  // dH1 = (dH2 W2) * [H1 > 0]
+  if (!rc)
+    rc = gemm_tc(operand(net->dh2, batch, hid, hid, net->pa, s), transposed(W2, hid, hid, hid, nullptr, net->pb, s),
+                 batch, hid, hid, nullptr, kEpiMaskBf16, nullptr, net->dh1, hid, net->h1, s);
+  // dW1 = dH1^T X (the batch's rows of x)
+  if (!rc)
+    rc = gemm_tc(transposed(net->dh1, hid, batch, hid, nullptr, net->pa, s),
+                 transposed(x, din, batch, din, rows, net->pb, s), hid, din, batch, nullptr, kEpiF32,
+                 net->g + net->oW1, nullptr, din, nullptr, s);
   k_colsum<<<(hid + 127) / 128, 128, 0, s>>>(net->dh1, batch, hid, net->g + net->ob1);
   TG_COUNT(3);
+  return rc;
 }
 
 int cuda_rc(cudaError_t e) {
@@ -385,9 +288,16 @@ void mlp_dims(const tg_mlp* net, int* b, int* k, int* hidden, int* din, int* dou
   *b = net->b; *k = net->k; *hidden = net->hidden; *din = net->din; *dout = net->dout;
 }
 
-void mlp_forward(const tg_mlp* net, int batch, const __nv_bfloat16* x, float* y, __nv_bfloat16* h1,
-                 __nv_bfloat16* h2, cudaStream_t s) {
-  forward_rows(net, batch, x, nullptr, y, h1, h2, s);
+int mlp_forward(const tg_mlp* cnet, int batch, const __nv_bfloat16* x, float* y, __nv_bfloat16* h1,
+                __nv_bfloat16* h2, cudaStream_t s) {
+  tg_mlp* net = const_cast<tg_mlp*>(cnet);   // the parameters stay; only the pack scratch may grow
+  int rc = ensure_pack(net, std::min(batch, kMaxBatch));
+  for (int r0 = 0; r0 < batch && !rc; r0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, batch - r0);
+    rc = forward_rows(net, cnt, x + (long long)r0 * net->din, nullptr, y + (long long)r0 * net->dout,
+                      h1 + (long long)r0 * net->hidden, h2 + (long long)r0 * net->hidden, s);
+  }
+  return rc;
 }
 
 }  // namespace tg
@@ -410,7 +320,7 @@ void tg_mlp_destroy(tg_mlp* net) {
   if (!net) return;
   cudaFree(net->p); cudaFree(net->g); cudaFree(net->m); cudaFree(net->v); cudaFree(net->wb);
   cudaFree(net->h1); cudaFree(net->h2); cudaFree(net->dy); cudaFree(net->dh1); cudaFree(net->dh2);
-  cudaFree(net->y); cudaFree(net->lacc);
+  cudaFree(net->y); cudaFree(net->lacc); cudaFree(net->pa); cudaFree(net->pb);
   delete net;
 }
 
@@ -470,27 +380,33 @@ int tg_mlp_forward(tg_mlp* net, int batch, const uint16_t* x, float* y) {
   for (int r0 = 0; r0 < batch; r0 += kMaxBatch) {
     const int cnt = std::min(kMaxBatch, batch - r0);
     int rc = ensure_capacity(net, cnt);
+    if (!rc) rc = ensure_pack(net, cnt);
+    if (!rc)
+      rc = forward_rows(net, cnt, xb + (long long)r0 * net->din, nullptr, y + (long long)r0 * net->dout, net->h1,
+                        net->h2, s);
     if (rc) return rc;
-    forward_rows(net, cnt, xb + (long long)r0 * net->din, nullptr, y + (long long)r0 * net->dout, net->h1, net->h2,
-                 s);
   }
   int rc = cuda_rc(cudaStreamSynchronize(s));
-  return rc ? rc : cuda_rc(cudaGetLastError());
+  if (!rc) rc = cuda_rc(cudaGetLastError());
+  if (!rc && read_and_clear_gemm_timeout()) rc = TG_ERR_DEVICE_TIMEOUT;
+  return rc;
 }
 
 int tg_mlp_loss_grad(tg_mlp* net, int batch, const uint16_t* x, const float* q, double* loss, float* grad) {
   if (!net || !x || !q || batch < 1 || batch > kMaxBatch) return TG_ERR_INVALID_ARG;
   int rc = ensure_capacity(net, batch);
+  if (!rc) rc = ensure_pack(net, batch);
   if (rc) return rc;
   cudaStream_t s = net->stream;
   cudaMemsetAsync(net->lacc, 0, sizeof(double), s);
-  loss_backward(net, batch, reinterpret_cast<const __nv_bfloat16*>(x), q, nullptr, s);
+  if ((rc = loss_backward(net, batch, reinterpret_cast<const __nv_bfloat16*>(x), q, nullptr, s))) return rc;
   double h_loss = 0.0;
   if ((rc = cuda_rc(cudaMemcpyAsync(&h_loss, net->lacc, sizeof(double), cudaMemcpyDeviceToHost, s)))) return rc;
   if (grad && (rc = cuda_rc(cudaMemcpyAsync(grad, net->g, sizeof(float) * net->np, cudaMemcpyDeviceToDevice, s))))
     return rc;
   if ((rc = cuda_rc(cudaStreamSynchronize(s)))) return rc;
   if ((rc = cuda_rc(cudaGetLastError()))) return rc;
+  if (read_and_clear_gemm_timeout()) return TG_ERR_DEVICE_TIMEOUT;
   if (loss) *loss = h_loss;
   return TG_OK;
 }
@@ -500,6 +416,7 @@ int tg_mlp_train(tg_mlp* net, int nsamples, const uint16_t* x, const float* q, c
   if (!net || !x || !q || !order || nsamples < 1 || nsteps < 0 || batch < 1 || batch > kMaxBatch || !(lr > 0))
     return TG_ERR_INVALID_ARG;
   int rc = ensure_capacity(net, batch);
+  if (!rc) rc = ensure_pack(net, batch);
   if (rc) return rc;
   cudaStream_t s = net->stream;
   const __nv_bfloat16* xb = reinterpret_cast<const __nv_bfloat16*>(x);
@@ -521,7 +438,7 @@ int tg_mlp_train(tg_mlp* net, int nsamples, const uint16_t* x, const float* q, c
   cudaMemsetAsync(net->lacc, 0, sizeof(double), s);
   const int agrid = (int)std::min<long long>((net->np + 255) / 256, 2048);
   for (int st = 0; st < nsteps; ++st) {
-    loss_backward(net, batch, xb, q, order + (long long)st * batch, s);
+    if ((rc = loss_backward(net, batch, xb, q, order + (long long)st * batch, s))) return rc;
     net->t += 1;
     const double c1 = 1.0 / (1.0 - std::pow(0.9, net->t)), c2 = 1.0 / (1.0 - std::pow(0.999, net->t));
     k_adam<<<agrid, 256, 0, s>>>(net->p, net->g, net->m, net->v, net->wb, net->np, lr, (float)c1, (float)c2);
@@ -529,7 +446,9 @@ int tg_mlp_train(tg_mlp* net, int nsamples, const uint16_t* x, const float* q, c
     TG_COUNT(2);
   }
   rc = cuda_rc(cudaStreamSynchronize(s));
-  return rc ? rc : cuda_rc(cudaGetLastError());
+  if (!rc) rc = cuda_rc(cudaGetLastError());
+  if (!rc && read_and_clear_gemm_timeout()) rc = TG_ERR_DEVICE_TIMEOUT;
+  return rc;
 }
 
 }  // extern "C"
