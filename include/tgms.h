@@ -129,9 +129,12 @@ typedef struct tg_options {
    * 8 = the tensor cores: BF16 / FP16 inverses stored a second time as
    * 16 x 16 tiles in mma operand order, applied by mma.m16n8k16 to the
    * residual split into three BF16 / FP16 parts (24 significant bits), FP32
-   * accumulation.  FP64 storage runs shape 0 for 1..3, 5, 6, 8; FP32 storage
-   * shape 0 for 8; FP16 storage shape 0 for 4.  Shapes 0..6 and 8 compute
-   * the same product of the stored inverses; shape 7 the same operator. */
+   * accumulation; 9 = the band form with FP32 factors read ahead through a
+   * shared-memory ring (cp.async, 44 rows ahead instead of 16 in registers:
+   * faster where fewer patches leave HBM bandwidth to spare).  FP64 storage
+   * runs shape 0 for 1..3, 5, 6, 8 and shape 7 for 9; FP32 storage shape 0
+   * for 8; FP16 storage shape 0 for 4.  Shapes 0..6 and 8 compute the same
+   * product of the stored inverses; shapes 7 and 9 the same operator. */
   int smoother_shape;
   /* 1: launch the kernels of a solve with programmatic dependent launch
    * (each kernel's launch overlaps the tail of the one before it; it waits
@@ -182,7 +185,7 @@ typedef struct tg_report {
   int fallback_faces;     /* TG_COARSE_LEARNED: faces that took the exact spectral problem */
   int learned_fallback;   /* 1 if this call rebuilt the space exactly (learned_max_iter) */
   int smoother_shape;     /* smoother tile shape in use */
-  float shape_us[9];      /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
+  float shape_us[10];     /* autotuner: microseconds per smoother launch of each shape (0: not tried) */
   int refactored_patches; /* patch inverses computed by the handle's last setup or tg_update_kappa */
   int refactored_blocks;  /* coarse-block factors computed by the same call */
   int update_rank[2];     /* last tg_update_kappa: rank of the low-rank update of the

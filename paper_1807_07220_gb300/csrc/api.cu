@@ -682,7 +682,7 @@ void enqueue_iteration(Ctx* c, int parity, cudaStream_t s) {
   // the five-kernel form gathers r - K z per patch node inside the last
   // sweep; the band sweep (one warp per patch) gathers better from a
   // separately formed residual, so band handles take the general form
-  if (h->opt.m1 == 1 && h->opt.m2 == 1 && h->opt.cycle == TG_CYCLE_TWO_GRID && h->shape != kShapeBand) {
+  if (h->opt.m1 == 1 && h->opt.m2 == 1 && h->opt.cycle == TG_CYCLE_TWO_GRID && !is_band_shape(h->shape)) {
     // The cycle of Section 6 (m1 = m2 = 1) in five kernels.  z ends every
     // iteration in zacc (A); zacc2 (B) holds the intermediate z.  The first
     // sweep accumulates into B and clears A (dead once p is formed), the
@@ -804,7 +804,7 @@ int add_chain_t(Ctx* c, cudaGraph_t graph, cudaStream_t cs) {
 template <typename TC, typename TS>
 void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) {
   tg_handle* h = cs[0]->h;
-  if (h->shape == kShapeBand) {   // no lock-step band sweep: each chain's own iteration
+  if (is_band_shape(h->shape)) {   // no lock-step band sweep: each chain's own iteration
     for (int i = 0; i < k; ++i) enqueue_iteration<TC, TS>(cs[i], parity, s);
     return;
   }
@@ -1361,18 +1361,19 @@ int autotune_smoother_t(tg_handle* h) {
   if (!rc) rc = cuda_err(cudaMemsetAsync(z, 0, sizeof(TC) * nn, s));
   const bool f64 = std::is_same<TS, double>::value, f16 = std::is_same<TS, __half>::value;
   const bool bf16 = std::is_same<TS, __nv_bfloat16>::value;
-  const int cand_bf16[] = {0, 1, 2, 3, 4, 5, 6, 7, 8}, cand_f32[] = {0, 1, 2, 3, 4, 5, 6, 7}, cand_f64[] = {0, 4, 7},
-            cand_f16[] = {0, 1, 2, 3, 5, 6, 7, 8};
-  // FP16: no TMA ring; the tensor-core tiles exist for 2-byte storage only
+  const int cand_bf16[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9}, cand_f32[] = {0, 1, 2, 3, 4, 5, 6, 7, 9},
+            cand_f64[] = {0, 4, 7}, cand_f16[] = {0, 1, 2, 3, 5, 6, 7, 8, 9};
+  // FP16: no TMA ring; the tensor-core tiles exist for 2-byte storage only;
+  // FP64 factors have one band form
   const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : bf16 ? cand_bf16 : cand_f32;
-  const int ncand = f64 ? 3 : f16 ? 8 : bf16 ? 9 : 8;
+  const int ncand = f64 ? 3 : f16 ? 9 : bf16 ? 10 : 9;
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {
     const int shape = cand[i];
     auto go = [&]() {
       // the band form runs from a separately formed residual: time that launch with it
-      if (shape == kShapeBand)
+      if (is_band_shape(shape))
         launch_residual<TC>(h->kinv, z, (const TC*)(std::is_same<TC, double>::value ? (const void*)h->kinv
                                                                                      : (const void*)h->kinv32),
                             rin, h->n, nullptr, s);
@@ -1406,6 +1407,7 @@ int choose_smoother_shape(tg_handle* h) {
     h->shape = h->opt.smoother_shape;
     if (h->opt.precision == TG_PREC_F16 && h->shape == 4) h->shape = 0;   // no TMA ring for FP16
     if (h->shape == kShapeTensor && !h->ptiles) h->shape = 0;            // tiles exist for 2-byte storage only
+    if (h->shape == kShapeBandRing && h->opt.precision == TG_PREC_F64) h->shape = kShapeBand;   // FP64 factors
     return TG_OK;
   }
   if (h->opt.precision == TG_PREC_F64) return autotune_smoother_t<double, double>(h);

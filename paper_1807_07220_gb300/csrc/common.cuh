@@ -274,8 +274,13 @@ void launch_pcg_init_rz(const double* r, const TC* z, double* p, double* part, P
 // shared-memory ring; 5 = shape 3 and 6 = shape 1, software-pipelined (the
 // next pass's rows in flight while the current one is reduced).  FP64 storage
 // uses shape 0 for 1..3, 5, 6; FP16 storage uses shape 0 for 4.
-constexpr int kSmootherShapes = 9;
+constexpr int kSmootherShapes = 10;
 constexpr int kShapeBand = 7;   // smoother from the patches' band Cholesky factors (two triangular solves)
+// The band form with FP32 factors read ahead through a shared-memory ring
+// (cp.async, 44 rows ahead instead of 16 in registers); FP64 factors run
+// shape 7.  The autotuner keeps whichever band form is faster per handle.
+constexpr int kShapeBandRing = 9;
+__host__ __device__ inline bool is_band_shape(int shape) { return shape == kShapeBand || shape == kShapeBandRing; }
 // The patch inverses applied on the tensor cores (2-byte storage; FP32 and
 // FP64 storage use shape 0): 16 x 16 tiles stored in the A-fragment order
 // of mma.m16n8k16, the residual split into three 2-byte parts as the

@@ -1120,6 +1120,146 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGe
   }
 }
 
+// FP32 band sweeps with a deeper read-ahead (the handles with FP32 factors).
+// The sweep's per-row dependency chain (a broadcast and a shift by
+// shuffles, a subtraction, a product, an FMA) takes far less than an HBM
+// round trip per 16 rows, so the register read-ahead of k_smoother_band
+// leaves the warp waiting on loads.  Here each lane copies its own 16-byte
+// entry quads (entry d of four rows, the grouped layout) with cp.async into
+// a per-warp shared-memory ring of kBandRing row groups, kBandRing - 1
+// groups (44 rows) ahead of the row being solved; a lane reads only what it
+// copied, so no cross-lane synchronisation is needed, and copies are issued
+// only for stored row groups.  Same arithmetic and order as k_smoother_band.
+constexpr int kBandRing = 12;
+__device__ __forceinline__ void band_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void band_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void band_cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename TR, int kFused>
+__global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const PatchGeo* __restrict__ geo, int npatch,
+                                                                        const float* __restrict__ band,
+                                                                        long long pstride,
+                                                                        const TR* __restrict__ r,
+                                                                        float* __restrict__ zacc, float eta, int n,
+                                                                        const PcgState* st, FuseArgs fa) {
+  pdl_entry();
+  if (st && st->done) return;
+  __shared__ float xs_all[kBandWarps][kPatchLd];
+  __shared__ __align__(16) float4 ring_all[kBandWarps][kBandRing][kBandLd];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kBandWarps + warp;
+  if (p >= npatch) return;   // warp-uniform; no block-wide barrier below
+  float* xs = xs_all[warp];
+  float4(*ring)[kBandLd] = ring_all[warp];
+  const PatchGeo g = geo[p];
+  const int nloc = g.nloc;
+  const float* Lc = band + (long long)p * pstride;
+  const bool ln = (lane < kBandLd);   // lanes past the stored band copy and read nothing
+  const long long gs = 4LL * kBandLd; // one group of four rows
+  const int nrow = ((nloc + kBandPF - 1) / kBandPF) * kBandPF;
+  const int ngrp = nrow / 4;
+  // the first groups of the forward sweep are in flight during the gather
+  const float* G0 = Lc + (long long)(kBandPad / 4) * gs + (ln ? 4 * lane : 0);
+#pragma unroll
+  for (int i = 0; i < kBandRing - 1; ++i) {
+    if (ln && i < ngrp) band_cp_async16(&ring[i][lane], G0 + i * gs);
+    band_cp_commit();
+  }
+  const double alpha = (kFused == 1) ? fa.st->alpha : 0.0;
+  for (int q = lane; q < nloc; q += 32) {
+    const int a = q % g.nx, c = q / g.nx;
+    const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
+    float v;
+    if constexpr (kFused == 1) v = (float)(fa.r_old[id] - alpha * fa.q[id]);
+    else if constexpr (kFused == 2)
+      v = (float)r[id] - stencil_apply<float, float, float>((const float*)fa.zin, (const float*)fa.kin, n,
+                                                           g.x0 + 1 + a, g.y0 + 1 + c);
+    else v = (float)r[id];
+    xs[q] = v;
+  }
+  if (kFused == 1) {   // block p's owner work
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = lane; t < b * b; t += 32) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      fa.r_new[id] = fa.r_old[id] - alpha * fa.q[id];
+      fa.x[id] += alpha * fa.p[id];
+      if (fa.zclear) ((float*)fa.zclear)[id] = 0.0f;
+    }
+  }
+  if (kFused == 2) {   // the owner seeds the output with z_in
+    const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
+    for (int t = lane; t < b * b; t += 32) {
+      const long long id = (long long)(J * b + t / b) * n + I * b + t % b;
+      atomicAdd(zacc + id, ((const float*)fa.zin)[id]);
+    }
+  }
+  for (int q = nloc + lane; q < nrow; q += 32) xs[q] = 0.0f;
+  __syncwarp();
+  // forward sweep, column layout: group k of rows 4k .. 4k + 3 in slot k % kBandRing
+  {
+    float acc = 0.0f;
+    for (int k = 0; k < ngrp; ++k) {
+      // group k + kBandRing - 1 into the slot read in the previous step
+      if (ln && k + kBandRing - 1 < ngrp)
+        band_cp_async16(&ring[(k + kBandRing - 1) % kBandRing][lane], G0 + (long long)(k + kBandRing - 1) * gs);
+      band_cp_commit();
+      band_cp_wait<kBandRing - 1>();   // group k has landed
+      const float4 cur = ln ? ring[k % kBandRing][lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = 4 * k + t;
+        const float cj = cv[t];
+        float y = (xs[j] - acc) * cj;             // meaningful in lane 0
+        y = __shfl_sync(0xffffffffu, y, 0);
+        if (lane == 0) xs[j] = y;
+        else acc = fmaf(cj, y, acc);
+        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      }
+    }
+  }
+  band_cp_wait<0>();
+  __syncwarp();
+  // backward sweep, row layout: group holding rows nrow - 4 - 4k .. nrow - 1 - 4k
+  {
+    const float* H0 = Lc + pstride / 2 + (long long)((kBandPad + nrow) / 4 - 1) * gs + (ln ? 4 * lane : 0);
+#pragma unroll
+    for (int i = 0; i < kBandRing - 1; ++i) {
+      if (ln && i < ngrp) band_cp_async16(&ring[i][lane], H0 - i * gs);
+      band_cp_commit();
+    }
+    float acc = 0.0f;
+    for (int k = 0; k < ngrp; ++k) {
+      if (ln && k + kBandRing - 1 < ngrp)
+        band_cp_async16(&ring[(k + kBandRing - 1) % kBandRing][lane], H0 - (long long)(k + kBandRing - 1) * gs);
+      band_cp_commit();
+      band_cp_wait<kBandRing - 1>();
+      const float4 cur = ln ? ring[k % kBandRing][lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = nrow - 1 - 4 * k - t;
+        const float cj = cv[3 - t];
+        float x = (xs[j] - acc) * cj;             // meaningful in lane 0
+        x = __shfl_sync(0xffffffffu, x, 0);
+        if (lane == 0) xs[j] = x;
+        else acc = fmaf(cj, x, acc);
+        acc = __shfl_down_sync(0xffffffffu, acc, 1);
+      }
+    }
+  }
+  band_cp_wait<0>();
+  __syncwarp();
+  for (int q = lane; q < nloc; q += 32) {
+    const int a = q % g.nx, c = q / g.nx;
+    atomicAdd(zacc + (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a), eta * xs[q]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Lock-step variant for several right-hand sides of one instance: one read of
 // every patch inverse serves up to kGroup PCG chains that run the same
@@ -1904,12 +2044,23 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
                     const TR* r, TC* zacc, double eta, int n, const PcgState* st, const FuseArgs& fa,
                     const float* rscale, cudaStream_t s, BandRef band = {}) {
   TG_COUNT(1);
-  if (shape == kShapeBand && band.p) {
-    launch(k_smoother_band<TC, TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps), 0,
-           s, geo, npatch, (const TC*)band.p, band.ldb, band.stride, r, zacc, (TC)eta, n, st, fa);
+  if (is_band_shape(shape) && band.p) {
+    if constexpr (std::is_same<TC, float>::value) {
+      if (shape == kShapeBand) {
+        launch(k_smoother_band<TC, TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps),
+               dim3(32 * kBandWarps), 0, s, geo, npatch, (const TC*)band.p, band.ldb, band.stride, r, zacc, (TC)eta,
+               n, st, fa);
+        return;
+      }
+      launch(k_smoother_band_ring<TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps),
+             0, s, geo, npatch, (const float*)band.p, band.stride, r, zacc, (float)eta, n, st, fa);
+    } else {
+      launch(k_smoother_band<TC, TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps), 0,
+             s, geo, npatch, (const TC*)band.p, band.ldb, band.stride, r, zacc, (TC)eta, n, st, fa);
+    }
     return;
   }
-  if (shape == kShapeBand) shape = 0;
+  if (is_band_shape(shape)) shape = 0;
   if (shape == kShapeTensor) {
     if constexpr (sizeof(TS) == 2) {
       if (band.tp) {

@@ -49,7 +49,7 @@ class tg_report(ctypes.Structure):
                 ("preprocess_ms", c_double), ("pcg_ms", c_double), ("epilogue_ms", c_double),
                 ("kernel_launches", c_int), ("smoother_launches", c_int), ("smoother_ms", c_double),
                 ("graph", c_int), ("snapshot_solves", c_int), ("fallback_faces", c_int),
-                ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 9),
+                ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 10),
                 ("refactored_patches", c_int), ("refactored_blocks", c_int),
                 ("update_rank", c_int * 2), ("operator_launches", c_int), ("operator_ms", c_double)]
 
