@@ -1043,8 +1043,9 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
     if (h->opt.precision == TG_PREC_F16 && dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup))
       return TG_ERR_OOM;
     // band factors for the band smoother: FP64 handles in FP64, the others in FP32
-    h->band.ldb = kBandLd;
-    h->band.stride = 2LL * band_rows(nmax) * kBandLd;   // column and row layouts
+    h->band.ldb = wmax + 1;   // stored row width: the widest band plus the reciprocal diagonal
+    if (h->band.ldb > kBandLd) return TG_ERR_UNSUPPORTED;
+    h->band.stride = 2LL * band_rows(nmax) * h->band.ldb;   // column and row layouts
     const size_t esz = (h->opt.precision == TG_PREC_F64) ? sizeof(double) : sizeof(float);
     TG_CK(cudaMalloc(&h->pband, std::max<size_t>(1, (size_t)h->npatch * h->band.stride * esz)));
     h->band.p = h->pband;
@@ -1344,7 +1345,10 @@ int setup_coarse(tg_handle* h, SpectralBufs& sb) {
 
 // Smoother autotuner: times every tile shape on this handle's own patch
 // inverses (one warm-up and five timed launches each, CUDA events on the
-// handle's stream, scratch vectors of its own) and keeps the fastest.
+// handle's stream, scratch vectors of its own) and keeps the fastest.  When
+// that is a band form, the two band forms are compared again from an
+// evicted L2, as they run in a solve.
+constexpr size_t kAutotuneFlushBytes = 256ull << 20;   // twice the 129 MB L2
 template <typename TC, typename TS>
 int autotune_smoother_t(tg_handle* h) {
   const long long nn = (long long)h->n * h->n;
@@ -1353,6 +1357,13 @@ int autotune_smoother_t(tg_handle* h) {
   if (dalloc(&rin, nn) || dalloc(&z, nn)) {
     cudaFree(rin);
     return TG_ERR_OOM;
+  }
+  // L2 eviction buffer for the band candidates (absent without band factors)
+  float band_cold[2] = {0.0f, 0.0f};   // shapes kShapeBand, kShapeBandRing, from an evicted L2
+  unsigned char* flush = nullptr;
+  if (h->band.p && cudaMalloc(&flush, kAutotuneFlushBytes) != cudaSuccess) {
+    cudaGetLastError();   // no eviction buffer: the band candidates are timed warm
+    flush = nullptr;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = cuda_err(cudaEventCreate(&e0));
@@ -1381,14 +1392,33 @@ int autotune_smoother_t(tg_handle* h) {
                                   h->opt.eta, h->n, nullptr, s, shape, h->rscale, h->band);
     };
     go();
+    float ms = 0.0f;
     cudaEventRecord(e0, s);
     for (int k = 0; k < 5; ++k) go();
     cudaEventRecord(e1, s);
     rc = cuda_err(cudaEventSynchronize(e1));
     if (!rc) rc = cuda_err(cudaGetLastError());
-    float ms = 0.0f;
     if (!rc) cudaEventElapsedTime(&ms, e0, e1);
     h->shape_us[shape] = ms * 1000.0f / 5.0f;
+    if (is_band_shape(shape) && flush && !rc) {
+      // the two band forms differ only in how far they read ahead, which
+      // matters where the factors stream from HBM, as they do in a solve (the
+      // iteration's other kernels pass through L2 between two sweeps): they
+      // are also timed each from an evicted L2
+      float cold = 0.0f;
+      for (int k = 0; k < 5 && !rc; ++k) {
+        cudaMemsetAsync(flush, 0, kAutotuneFlushBytes, s);
+        cudaEventRecord(e0, s);
+        go();
+        cudaEventRecord(e1, s);
+        rc = cuda_err(cudaEventSynchronize(e1));
+        float one = 0.0f;
+        if (!rc) cudaEventElapsedTime(&one, e0, e1);
+        cold += one;
+      }
+      if (!rc) rc = cuda_err(cudaGetLastError());
+      band_cold[shape == kShapeBand ? 0 : 1] = cold * 1000.0f / 5.0f;
+    }
     if (!rc && h->shape_us[shape] < best) {
       best = h->shape_us[shape];
       best_shape = shape;
@@ -1398,6 +1428,11 @@ int autotune_smoother_t(tg_handle* h) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(rin);
   cudaFree(z);
+  cudaFree(flush);
+  // dense against band on the warm times; between the two band forms, the
+  // one faster from an evicted L2
+  if (!rc && is_band_shape(best_shape) && band_cold[0] > 0.0f && band_cold[1] > 0.0f)
+    best_shape = band_cold[1] < band_cold[0] ? kShapeBandRing : kShapeBand;
   if (!rc) h->shape = best_shape;
   return rc;
 }

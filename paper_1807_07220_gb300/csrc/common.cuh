@@ -299,13 +299,15 @@ __host__ __device__ inline int tiles_per_side(int nloc) { return (nloc + kTile -
 // read by the forward sweep), and row layout, entry (j, d) = L_{j, j-d} (the
 // row left of the diagonal; read by the backward sweep); d = 0 holds 1 / L_jj
 // in both.  Rows are stored in groups of four, interleaved by entry: with
-// R = j + kBandPad, entry (j, d) sits at (R / 4) * 4 kBandLd + 4 d + R % 4, so
+// R = j + kBandPad, entry (j, d) sits at (R / 4) * 4 ldb + 4 d + R % 4, so
 // lane d of a warp loads entries (j..j+3, d) of a group as one 16-byte vector
-// (two for FP64) and a group is one contiguous, 128-byte aligned block.
+// (two for FP64) and a group is one contiguous, 16-byte aligned block.
 // band_rows(nmax) rows, -kBandPad .. roundup(nmax, kBandPF) + kBandPad - 1,
 // are stored, zero outside the matrix and the band, so the sweeps read them
 // without bounds checks.
-constexpr int kBandLd = 24;    // entries per row (the band is at most kMaxPatchSide + 1 = 20 wide)
+// ldb (BandRef): entries per stored row, the handle's widest band plus the
+// reciprocal diagonal (21 at b = 16, 13 at b = 8); kBandLd bounds it
+constexpr int kBandLd = 24;    // the band is at most kMaxPatchSide + 1 = 20 wide
 constexpr int kBandPF = 16;    // row rounding of the sweeps, and at most the rows they keep in flight per lane
 constexpr int kBandPad = 16;   // rows of zeros before and after: the read-ahead runs past the last row
 static_assert(kBandPad >= kBandPF && kBandPad % 4 == 0 && kBandPF % 4 == 0,

@@ -1141,7 +1141,7 @@ __device__ __forceinline__ void band_cp_wait() { asm volatile("cp.async.wait_gro
 
 template <typename TR, int kFused>
 __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const PatchGeo* __restrict__ geo, int npatch,
-                                                                        const float* __restrict__ band,
+                                                                        const float* __restrict__ band, int ldb,
                                                                         long long pstride,
                                                                         const TR* __restrict__ r,
                                                                         float* __restrict__ zacc, float eta, int n,
@@ -1158,8 +1158,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const Pa
   const PatchGeo g = geo[p];
   const int nloc = g.nloc;
   const float* Lc = band + (long long)p * pstride;
-  const bool ln = (lane < kBandLd);   // lanes past the stored band copy and read nothing
-  const long long gs = 4LL * kBandLd; // one group of four rows
+  const bool ln = (lane < ldb);   // lanes past the stored band copy and read nothing (ldb <= kBandLd)
+  const long long gs = 4LL * ldb; // one group of four rows
   const int nrow = ((nloc + kBandPF - 1) / kBandPF) * kBandPF;
   const int ngrp = nrow / 4;
   // the first groups of the forward sweep are in flight during the gather
@@ -2053,7 +2053,7 @@ void smoother_shape(int shape, const PatchGeo* geo, const int* gofs, int npatch,
         return;
       }
       launch(k_smoother_band_ring<TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps),
-             0, s, geo, npatch, (const float*)band.p, band.stride, r, zacc, (float)eta, n, st, fa);
+             0, s, geo, npatch, (const float*)band.p, band.ldb, band.stride, r, zacc, (float)eta, n, st, fa);
     } else {
       launch(k_smoother_band<TC, TR, kFused>, dim3((npatch + kBandWarps - 1) / kBandWarps), dim3(32 * kBandWarps), 0,
              s, geo, npatch, (const TC*)band.p, band.ldb, band.stride, r, zacc, (TC)eta, n, st, fa);

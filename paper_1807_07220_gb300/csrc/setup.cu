@@ -367,10 +367,10 @@ __global__ void k_store_band(const double* __restrict__ band, const int4* __rest
   const int nloc = r.z * r.w, ldb = wmax + 1;
   const double* B = band + (long long)c * nmax * ldb;
   TB* O = out + (long long)(ids ? ids[c] : c) * stride;
-  const long long tot = stride / 2;   // one layout: band_rows(nmax) rows in groups of four
+  const long long tot = stride / 2;   // one layout: band_rows(nmax) rows in groups of four, ldb wide
   for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int e = (int)(t % (4 * kBandLd));
-    const int j = (int)(t / (4 * kBandLd)) * 4 + (e & 3) - kBandPad, d = e >> 2;
+    const int e = (int)(t % (4 * ldb));
+    const int j = (int)(t / (4 * ldb)) * 4 + (e & 3) - kBandPad, d = e >> 2;
     double vc = 0.0, vr = 0.0;
     if (j >= 0 && j < nloc && d < ldb) {
       if (d == 0) {
