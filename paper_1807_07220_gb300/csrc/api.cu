@@ -825,7 +825,7 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
     m2[i] = ChainPtrs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->st, nullptr, zB, kin, r_new, zA};
   }
   launch_smoother_multi<TC, TS>(1, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m1, k, h->opt.eta, n, h->nc,
-                                h->b, s, h->shape, h->rscale);
+                                h->b, s, h->shape, h->rscale, &h->band);
   if (h->cs.D > 0) {
     for (int i = 0; i < k; ++i) {
       Ctx* c = cs[i];
@@ -836,7 +836,7 @@ void enqueue_group_iteration(Ctx* const* cs, int k, int parity, cudaStream_t s) 
     }
   }
   launch_smoother_multi<TC, TS>(2, h->d_pgeo, h->d_gofs, h->npatch, h->ngroups, pinv, m2, k, h->opt.eta, n, h->nc,
-                                h->b, s, h->shape, h->rscale);
+                                h->b, s, h->shape, h->rscale, &h->band);
   for (int i = 0; i < k; ++i) {
     Ctx* c = cs[i];
     const double* r_new = parity ? c->r : c->r2;

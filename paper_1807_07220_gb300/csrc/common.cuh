@@ -234,10 +234,13 @@ struct StateSet {
   const PcgState* st[kGroup];
   int k;
 };
+struct BandRef;
+// tiles (optional): the tensor-core tile layout of the same inverses, used
+// when shape is kShapeTensor (2-byte storage)
 template <typename TC, typename TS>
 void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                            const ChainPtrs* chains, int k, double eta, int n, int nc, int b, cudaStream_t s, int shape,
-                           const float* rscale);
+                           const float* rscale, const BandRef* tiles = nullptr);
 // graph loop condition: 1 while any of the k chains is not done
 void launch_set_condition_any(cudaGraphConditionalHandle cond, const PcgState* const* st, int k, cudaStream_t s);
 

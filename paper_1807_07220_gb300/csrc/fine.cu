@@ -960,6 +960,160 @@ __global__ void __launch_bounds__(kThreads, 4) k_smoother_mma(const PatchGeo* __
   }
 }
 
+// Lock-step tensor-core sweep (k_smoother_multi on the tile layout): up to
+// kGroup chains share every A-fragment load; chains 0 and 1 are the columns
+// 0-2 and 3-5 of one B operand, chains 2 and 3 of a second, so a tile costs
+// one load per lane and one or two mma.  Each chain keeps its own gather,
+// fused updates and (FP16) residual scale, and its row sums follow the
+// single-chain order ((hi + mid) + lo).
+template <typename TC, typename TS, int kFused>
+__global__ void __launch_bounds__(kThreads, 4) k_smoother_mma_multi(const PatchGeo* __restrict__ geo,
+                                                                    const int* __restrict__ tofs,
+                                                                    const int* __restrict__ gofs, int npatch,
+                                                                    const TS* __restrict__ tiles, TC eta, int n,
+                                                                    ChainSet<TC> cs,
+                                                                    const float* __restrict__ rscale) {
+  pdl_entry();
+  constexpr bool kHalf = std::is_same<TS, __half>::value;
+  constexpr int kPairs = kGroup / 2;
+  __shared__ __align__(16) TC xs[kGroup][kPatchLd];
+  __shared__ __align__(16) uint2 xb[kPairs][(kPatchLd / kTile) * 24];
+  bool act[kGroup];
+  int any = 0;
+#pragma unroll
+  for (int c = 0; c < kGroup; ++c) {
+    act[c] = (c < cs.k) && !cs.st[c]->done;
+    any |= act[c];
+  }
+  if (!any) return;
+  const bool pair_act[kPairs] = {act[0] || act[1], act[2] || act[3]};
+  double alpha[kGroup];
+#pragma unroll
+  for (int c = 0; c < kGroup; ++c) alpha[c] = (kFused == 1 && act[c]) ? cs.fa[c].st->alpha : 0.0;
+  int t0, t1;
+  __shared__ int sp;
+  if (gridDim.x >= (unsigned)npatch && gridDim.x % npatch == 0) {
+    const int k = gridDim.x / npatch, pp = blockIdx.x / k, piece = blockIdx.x % k;
+    const int base = tofs[pp], nt = tofs[pp + 1] - base;
+    t0 = base + piece * nt / k;
+    t1 = base + (piece + 1) * nt / k;
+    if (threadIdx.x == 0) sp = pp;
+    __syncthreads();
+  } else {
+    const int RT = tofs[npatch];
+    const long long per = ((long long)RT + gridDim.x - 1) / gridDim.x;
+    t0 = (int)min((long long)RT, blockIdx.x * per);
+    t1 = (int)min((long long)RT, t0 + per);
+    if (threadIdx.x == 0) sp = npatch - 1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < npatch; t += blockDim.x)
+      if (tofs[t] <= t0 && tofs[t + 1] > t0) sp = t;
+    __syncthreads();
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = sp; t0 < t1 && p < npatch && tofs[p] < t1; ++p) {
+    const PatchGeo g = geo[p];
+    const int T = tiles_per_side(g.nloc);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kGroup; ++c)
+      if (act[c])
+        smoother_gather<TC, double, kFused>(g, p, tofs[p] >= t0, cs.r[c], cs.zacc[c], n, cs.fa[c], alpha[c], xs[c],
+                                            T * kTile);
+    __syncthreads();
+    float sx[kGroup], unscale[kGroup];
+#pragma unroll
+    for (int c = 0; c < kGroup; ++c) {
+      sx[c] = 1.0f;
+      unscale[c] = 1.0f;
+      if constexpr (kHalf) {
+        if (act[c]) {
+          float m = 0.0f;
+          for (int q = lane; q < g.nloc; q += 32) m = fmaxf(m, fabsf((float)xs[c][q]));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          if (m > 0.0f) {
+            int e = 0;
+            frexpf(m, &e);
+            sx[c] = ldexpf(1.0f, 15 - e);
+            unscale[c] = ldexpf(1.0f, e - 15);
+          }
+        }
+      }
+    }
+    // B fragments: lane l < 24 of k-tile j of pair P holds part (l / 4) % 3 of
+    // chain 2 P + l / 12 at columns 16 j + 2 (l % 4) + {0, 1} and + 8
+    for (int e = threadIdx.x; e < kPairs * T * 24; e += blockDim.x) {
+      const int P = e / (T * 24), r2 = e % (T * 24), j = r2 / 24, l = r2 % 24;
+      const int c = 2 * P + l / 12, k = (l >> 2) % 3, c0 = kTile * j + 2 * (l & 3);
+      uint2 w = make_uint2(0u, 0u);
+      if (act[c]) {
+        auto pk = [&](int q) { return part16<TS>((float)xs[c][q] * sx[c], k); };
+        w = make_uint2(pk(c0) | (pk(c0 + 1) << 16), pk(c0 + 8) | (pk(c0 + 9) << 16));
+      }
+      xb[P][j * 24 + l] = w;
+    }
+    __syncthreads();
+    const int ta = max(t0, tofs[p]) - tofs[p], tb = min(t1, tofs[p + 1]) - tofs[p];
+    const uint4* A = reinterpret_cast<const uint4*>(tiles + g.toff) + lane;
+    for (int i = ta + warp; i < tb; i += nw) {
+      float d[kPairs][4] = {}, d2[kPairs][4] = {};
+      const uint4* Ai = A + (long long)i * T * 32;
+      for (int j0 = 0; j0 < T; j0 += 6) {
+        uint4 a[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) a[u] = (j0 + u < T) ? __ldg(Ai + (j0 + u) * 32) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          if (j0 + u < T) {   // uniform over the warp
+#pragma unroll
+            for (int P = 0; P < kPairs; ++P) {
+              if (!pair_act[P]) continue;
+              const uint2 bv = (lane < 24) ? xb[P][(j0 + u) * 24 + lane] : make_uint2(0u, 0u);
+              if (u & 1) MmaTile<TS>::mma(d2[P], a[u], bv);
+              else MmaTile<TS>::mma(d[P], a[u], bv);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int P = 0; P < kPairs; ++P) {
+        if (!pair_act[P]) continue;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[P][k] += d2[P][k];
+        // chain 2P: columns 0, 1 on lane 4g, column 2 on lane 4g + 1; chain
+        // 2P + 1: column 3 on lane 4g + 1, columns 4, 5 on lane 4g + 2
+        float y[2][2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float c0v = d[P][2 * hh], c1v = d[P][2 * hh + 1];
+          const float n0 = __shfl_down_sync(0xffffffffu, c0v, 1), n1 = __shfl_down_sync(0xffffffffu, c1v, 1);
+          const float m0 = __shfl_down_sync(0xffffffffu, c0v, 2), m1 = __shfl_down_sync(0xffffffffu, c1v, 2);
+          y[0][hh] = (c0v + c1v) + n0;
+          y[1][hh] = (n1 + m0) + m1;
+        }
+        if ((lane & 3) == 0) {
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = 2 * P + cc;
+            if (!act[c]) continue;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int q = kTile * i + (lane >> 2) + 8 * hh;
+              if (q < g.nloc) {
+                TC v = (TC)y[cc][hh];
+                if constexpr (kHalf) v *= (TC)(rscale[(long long)gofs[p] * kRowsPerWarp + q] * unscale[c]);
+                const int a2 = q % g.nx, c2 = q / g.nx;
+                atomicAdd(cs.zacc[c] + (long long)(g.y0 + 1 + c2) * n + (g.x0 + 1 + a2), eta * v);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Band variant (tile shape kShapeBand): each local problem is solved from its
 // band Cholesky factor by the two triangular solves, as the paper's direct
@@ -2176,10 +2330,28 @@ void smoother_multi_shape(int shape, const PatchGeo* geo, const int* gofs, int n
   }
 }
 
+template <typename TC, typename TS, int kFused>
+void smoother_mma_multi_go(const PatchGeo* geo, const int* gofs, int npatch, double eta, int n,
+                           const ChainSet<TC>& cs, const float* rscale, const BandRef& t, cudaStream_t s) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smoother_mma_multi<TC, TS, kFused>, kThreads, 0);
+    if (per_sm <= 0) per_sm = 1;
+  }
+  int grid = per_sm * sm_count();
+  const int min_tiles_per_cta = kThreads / 32;
+  if (grid * min_tiles_per_cta > t.ntiles) grid = (t.ntiles + min_tiles_per_cta - 1) / min_tiles_per_cta;
+  if (grid >= npatch) grid = grid / npatch * npatch;
+  if (grid < 1) grid = 1;
+  TG_COUNT(1);
+  launch(k_smoother_mma_multi<TC, TS, kFused>, dim3(grid), dim3(kThreads), 0, s, geo, t.tofs, gofs, npatch,
+         (const TS*)t.tp, (TC)eta, n, cs, rscale);
+}
+
 template <typename TC, typename TS>
 void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int npatch, int ngroups, const TS* pinv,
                            const ChainPtrs* chains, int k, double eta, int n, int nc, int b, cudaStream_t s, int shape,
-                           const float* rscale) {
+                           const float* rscale, const BandRef* tiles) {
   ChainSet<TC> cs{};
   cs.k = k;
   for (int c = 0; c < kGroup; ++c) {
@@ -2189,6 +2361,13 @@ void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int n
     cs.st[c] = q.st;
     cs.fa[c] = FuseArgs{q.r_old, q.r_new, q.q, q.x, q.p, q.part, q.st, nc, b, q.zclear, q.zin, q.kin};
   }
+  if constexpr (sizeof(TS) == 2) {
+    if (shape == kShapeTensor && tiles && tiles->tp) {   // the tensor-core tiles, one A load for every chain
+      if (mode == 1) smoother_mma_multi_go<TC, TS, 1>(geo, gofs, npatch, eta, n, cs, rscale, *tiles, s);
+      else smoother_mma_multi_go<TC, TS, 2>(geo, gofs, npatch, eta, n, cs, rscale, *tiles, s);
+      return;
+    }
+  }
   if (mode == 1)
     smoother_multi_shape<TC, TS, 1>(shape, geo, gofs, npatch, ngroups, pinv, eta, n, cs, rscale, s);
   else
@@ -2196,16 +2375,16 @@ void launch_smoother_multi(int mode, const PatchGeo* geo, const int* gofs, int n
 }
 template void launch_smoother_multi<double, double>(int, const PatchGeo*, const int*, int, int, const double*,
                                                     const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
-                                                    const float*);
+                                                    const float*, const BandRef*);
 template void launch_smoother_multi<float, float>(int, const PatchGeo*, const int*, int, int, const float*,
                                                   const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
-                                                  const float*);
+                                                  const float*, const BandRef*);
 template void launch_smoother_multi<float, __nv_bfloat16>(int, const PatchGeo*, const int*, int, int,
                                                           const __nv_bfloat16*, const ChainPtrs*, int, double, int,
-                                                          int, int, cudaStream_t, int, const float*);
+                                                          int, int, cudaStream_t, int, const float*, const BandRef*);
 template void launch_smoother_multi<float, __half>(int, const PatchGeo*, const int*, int, int, const __half*,
                                                    const ChainPtrs*, int, double, int, int, int, cudaStream_t, int,
-                                                   const float*);
+                                                   const float*, const BandRef*);
 
 // set the graph's loop condition: continue while any chain of a group runs
 __global__ void k_set_condition_any(cudaGraphConditionalHandle cond, StateSet ss) {

@@ -162,3 +162,25 @@ def test_learned_batch_takes_the_network_of_each_block_size(tg):
     finally:
         for net in nets:
             net.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_lockstep_tensor_core_smoother(tg, prec):
+    """Lock-step groups on the tensor-core tiles (tile shape 8: one A load per
+    tile for up to four chains, two chains per B operand): the iteration
+    counts of independent chains and the direct solution, with five
+    right-hand sides per instance (a group of four and a lone chain)."""
+    specs = [(32, 8, 1e4, 1), (48, 16, 1e5, 3), (64, 16, 1e6, 5)]
+    nrhs = 5
+    kappas = [inputs.channel_field(n, c, seed) for n, b, c, seed in specs]
+    kd = [torch.as_tensor(k, dtype=torch.float64, device="cuda").contiguous() for k in kappas]
+    fs = [inputs.random_pairs(n, 1 + r % 3, 60 * seed + r) for (n, b, c, seed) in specs for r in range(nrhs)]
+    it_l, u_l = _run_batch(tg, kd, specs, fs, nrhs, prec, 1, 1e-12, smoother_shape=8)
+    it_i, u_i = _run_batch(tg, kd, specs, fs, nrhs, prec, 0, 1e-12, smoother_shape=8)
+    assert np.abs(it_l - it_i).max() <= 1, (it_l, it_i)
+    j = 0
+    for (n, b, c, seed), k in zip(specs, kappas):
+        for r in range(nrhs):
+            u_ref, _ = solve_direct(Grid(n, b), k, fs[j])
+            assert rel(u_l[j], u_ref) < 1e-8 and rel(u_i[j], u_ref) < 1e-8, (j, rel(u_l[j], u_ref))
+            j += 1
