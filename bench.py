@@ -370,6 +370,11 @@ def run_ours(args):
     if world == 1 and not args.no_north_star:
         north = {"batch_64x4": north_star_batch(args, tgms, torch, flush, checks),
                  "n1024_b16": north_star_1024(args, tgms, torch, flush, checks, peaks, peak_src)}
+        # two-phase flow: 512^2, 200 steps, the paper's frozen coarse space (low-rank inverse updates) and
+        # the coarse space rebuilt every step by the learned network with exact fallback
+        rec = impes_record(args, 512, 16, ["frozen", "rebuild_learned"], 200, prec="f16")
+        north["impes_512"] = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "arms",
+                                                  "headline_arm", "training")}
 
     value, ms_step = agg(times)
     p_value, p_ms = agg(p_times)
@@ -887,17 +892,23 @@ def run_impes(args):
     the exact spectral problems ('rebuild') or from the learned network with
     per-face exact fallback ('rebuild_learned', network trained beforehand on
     args.train_fields other seeded channel fields of the same size)."""
+    line = impes_record(args, args.n, args.b, args.impes_arms.split(","), args.impes_steps)
+    print(json.dumps(line), flush=True)
+
+
+def impes_record(args, n, b, arm_names, nsteps, prec=None):
+    """The IMPES line (see run_impes) as a dict, for the given arms."""
+    prec = prec or args.precision
     import numpy as np
     import torch
     from paper_1807_07220_gb300 import inputs, tgms
     from paper_1807_07220_gb300.impes import Impes
     torch.cuda.set_device(0)
-    n, b, k = args.n, args.b, 4
+    k = 4
     dev = "cuda"
     stream = torch.cuda.current_stream().cuda_stream
     kap = torch.as_tensor(inputs.channel_field(n, 1e5, 77), dtype=torch.float64, device=dev)
     f = torch.as_tensor(inputs.quarter_five_spot(n), dtype=torch.float64, device=dev)
-    arm_names = args.impes_arms.split(",")
     nc = n // b
     F = 2 * nc * (nc - 1)
     net, training = None, None
@@ -927,12 +938,12 @@ def run_impes(args):
         kw = modes[name]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, precision=args.precision, flexible=1, **kw)
+        sim = Impes(kap, f, b, EIG_TOL, rtol=RTOL, precision=prec, flexible=1, **kw)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         t0 = time.perf_counter()
         torch.cuda.nvtx.range_push("impes_steps")
-        for _ in range(args.impes_steps):
+        for _ in range(nsteps):
             sim.step()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -955,16 +966,15 @@ def run_impes(args):
     if net is not None:
         net.close()
     head = "frozen" if "frozen" in arms else arm_names[0]
-    line = {
+    return {
         "metric": "IMPES steps/s (pressure update + warm-started solve + transport)",
-        "value": arms[head]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.impes_steps,
+        "value": arms[head]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": nsteps,
         "warmup": 0, "ms_per_step": 1e3 / arms[head]["steps_per_s"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + prec, "data": "synthetic",
         "config": {"workload": "%dx%d two-phase IMPES, %dx%d-cell blocks, channels 1e5, quarter five-spot, "
                                "mu_w 1, mu_o 5, CFL 0.5, rtol %g" % (n, n, b, b, RTOL)},
         "arms": arms, "faces": F, "headline_arm": head, "training": training,
     }
-    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- ablations

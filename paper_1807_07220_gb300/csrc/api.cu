@@ -1499,6 +1499,7 @@ int setup_impl(tg_handle* h, const double* kappa) {
   if (st) return status_to_err(st);
 
   configure_kernels(std::max(h->cs.D, h->rt.D));
+  if (configure_rt_particular(h->nc, h->nblocks)) return TG_ERR_UNSUPPORTED;   // coarse grid beyond one CTA's memory
   if ((rc = choose_smoother_shape(h))) return rc;
   if ((rc = ctx_alloc(h, &h->ctx))) return rc;
   TG_CK(cudaStreamSynchronize(s));

@@ -103,6 +103,8 @@ struct CoarseSpace {
 constexpr int kCoarseSplit = 1024;   // coarse systems larger than this form their right-hand side once
 // Kinv (m entries) into double-float pairs: hi = fl32(x), lo = fl32(x - hi)
 void launch_split_df(const double* a, float2* b, long long m, cudaStream_t s);
+// shared memory of the RT0 particular-flux kernel for nc x nc blocks; -1 if the device cannot hold it
+int configure_rt_particular(int nc, int nblocks);
 
 // ---- small device helpers --------------------------------------------------
 __device__ __forceinline__ float to_f(float x) { return x; }

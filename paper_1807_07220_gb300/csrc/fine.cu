@@ -1887,14 +1887,22 @@ __global__ void k_coarse_rhs_df(const double* __restrict__ part, const int* __re
     c[u] = make_float2(hi, (float)(v - (double)hi));
   }
 }
+// kStage: the right-hand side staged in shared memory (D * 8 bytes, up to
+// kCoarseStageMax); above that it is read from global memory (L1/L2)
+constexpr int kCoarseStageMax = 24 * 1024;
+template <bool kStage>
 __global__ void __launch_bounds__(kThreads) k_coarse_gemv_df(const float2* __restrict__ c,
                                                              const float2* __restrict__ Kdf,
                                                              double* __restrict__ d, int D, const PcgState* st) {
   pdl_entry();
   if (st && st->done) return;
-  extern __shared__ float2 cdf[];
-  for (int u = threadIdx.x; u < D; u += blockDim.x) cdf[u] = c[u];
-  __syncthreads();
+  extern __shared__ float2 cdf_sh[];
+  const float2* cdf = c;
+  if constexpr (kStage) {
+    for (int u = threadIdx.x; u < D; u += blockDim.x) cdf_sh[u] = c[u];
+    __syncthreads();
+    cdf = cdf_sh;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int row = blockIdx.x * nw + warp; row < D; row += gridDim.x * nw) {
     const float2* kr = Kdf + (long long)row * D;
@@ -1931,14 +1939,19 @@ __global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b,
     b[i] = make_float2(hi, (float)(x - (double)hi));
   }
 }
+template <bool kStage>
 __global__ void __launch_bounds__(kThreads) k_coarse_gemv(const double* __restrict__ c,
                                                           const double* __restrict__ Kinv,
                                                           double* __restrict__ d, int D, const PcgState* st) {
   pdl_entry();
   if (st && st->done) return;
-  extern __shared__ double cvec[];
-  for (int u = threadIdx.x; u < D; u += blockDim.x) cvec[u] = c[u];
-  __syncthreads();
+  extern __shared__ double cvec_sh[];
+  const double* cvec = c;
+  if constexpr (kStage) {
+    for (int u = threadIdx.x; u < D; u += blockDim.x) cvec_sh[u] = c[u];
+    __syncthreads();
+    cvec = cvec_sh;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int row = blockIdx.x * nw + warp; row < D; row += gridDim.x * nw) {
     const double* kr = Kinv + (long long)row * D;
@@ -2526,8 +2539,9 @@ void configure_kernels(int max_coarse_dim) {
   smoother_prepare<float, __half, double, 2>();
   const size_t shm = sizeof(double) * (size_t)(max_coarse_dim > 0 ? max_coarse_dim : 1);
   if (shm > 48 * 1024) {
-    cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    cudaFuncSetAttribute(k_coarse_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const int stage = (int)std::min(shm, sizeof(double) * (size_t)kCoarseStageMax);
+    cudaFuncSetAttribute(k_coarse_gemv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage);
+    cudaFuncSetAttribute(k_coarse_gemv_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage);   // float2: 8 B
   }
 }
 void launch_pcg_init_warm(const double* x, const double* rho, const double* kinv, double* r, double* part,
@@ -2551,17 +2565,23 @@ void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coef
     TG_COUNT(2);
     int grid = (cs.D + 7) / 8;
     if (grid > 2 * sm_count()) grid = 2 * sm_count();
+    const bool stage = cs.D <= kCoarseStageMax;
     if (cs.Kdf) {   // double-float copy (mixed precision): rhs as FP32 pairs in the same space
       float2* rdf = reinterpret_cast<float2*>(rhs);
       grid = std::min((cs.D + 7) / 8, 4 * sm_count());
       launch(k_coarse_rhs_df, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rdf,
              cs.D, st);
-      launch(k_coarse_gemv_df, dim3(grid), dim3(kThreads), sizeof(float2) * (size_t)cs.D, s, (const float2*)rdf,
-             (const float2*)cs.Kdf, coefs, cs.D, st);
+      if (stage)
+        launch(k_coarse_gemv_df<true>, dim3(grid), dim3(kThreads), sizeof(float2) * (size_t)cs.D, s,
+               (const float2*)rdf, (const float2*)cs.Kdf, coefs, cs.D, st);
+      else
+        launch(k_coarse_gemv_df<false>, dim3(grid), dim3(kThreads), 0, s, (const float2*)rdf, (const float2*)cs.Kdf,
+               coefs, cs.D, st);
       return;
     }
     launch(k_coarse_rhs, dim3((cs.D + kThreads - 1) / kThreads), dim3(kThreads), 0, s, part, cs.gather, rhs, cs.D, st);
-    launch(k_coarse_gemv, dim3(grid), dim3(kThreads), shm, s, rhs, cs.Kinv, coefs, cs.D, st);
+    if (stage) launch(k_coarse_gemv<true>, dim3(grid), dim3(kThreads), shm, s, rhs, cs.Kinv, coefs, cs.D, st);
+    else launch(k_coarse_gemv<false>, dim3(grid), dim3(kThreads), 0, s, rhs, cs.Kinv, coefs, cs.D, st);
     return;
   }
   int grid = (cs.D + 7) / 8;

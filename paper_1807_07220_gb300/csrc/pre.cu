@@ -481,6 +481,21 @@ void launch_block_sources(const double* f, const double* ux, const double* uy, d
   TG_COUNT(1);
   launch(k_block_sources, dim3(nc * nc), dim3(kThreads), 0, s, f, ux, uy, FH, absF, n, b);
 }
+// The RT0 particular flux runs in one CTA with (nc + nblocks) FP64 values in
+// dynamic shared memory; grids whose values exceed the default 48 KB get the
+// larger carve-out here, before any capture (0 when they exceed the device).
+int configure_rt_particular(int nc, int nblocks) {
+  const size_t shm = sizeof(double) * (size_t)(nc + nblocks);
+  if (shm <= 48 * 1024) return 0;
+  int dev = 0, maxopt = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      shm > (size_t)maxopt)
+    return -1;
+  return cudaFuncSetAttribute(k_rt_particular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) == cudaSuccess
+             ? 0
+             : -1;
+}
 void launch_rt_particular(const double* FH, const double* absF, double* gx, double* gy, int nc, double H,
                           int nblocks, PcgState* st, cudaStream_t s) {
   TG_COUNT(1);

@@ -130,3 +130,18 @@ def test_large_grids_properties(tg, n, prec):
     it, rep, u, p, shape = gpu_solve(tg, kappa, b, f, 1e-12, precision=prec, flexible=1)
     assert rep.converged == 1, (it, shape)
     check_tight(chk.measure(u, p))
+
+
+def test_many_coarse_blocks_properties(tg):
+    """640 x 640 with 8 x 8 blocks: 80 x 80 coarse blocks, whose RT0
+    particular flux (one CTA holding a value per block and per coarse row)
+    needs more than the default 48 KB of shared memory, and a coarse system
+    above the fused size.  The properties that fix the discrete solution, at
+    rtol 1e-12."""
+    n, b = 640, 8
+    kappa = inputs.grf_channel_field(n, CONTRAST, FIELD_SEED)
+    f = inputs.quarter_five_spot(n)
+    chk = Checks(n, b, kappa, f)
+    it, rep, u, p, shape = gpu_solve(tg, kappa, b, f, 1e-12, precision="f16", flexible=1)
+    assert rep.converged == 1 and rep.coarse_unknowns > 6000, (it, rep.coarse_unknowns)
+    check_tight(chk.measure(u, p))
