@@ -646,28 +646,50 @@ struct ChainSet {
   int k;
 };
 
+// q / nx for a patch node q < kPatchLd and a patch side nx <= kMaxPatchSide:
+// q * ceil(2^16 / nx) / 2^16 exceeds q / nx by less than kPatchLd / 2^16 < 1 / nx,
+// so the shift gives the exact quotient with two integer operations
+__device__ __forceinline__ int patch_row(int q, int mul16) { return (q * mul16) >> 16; }
+__device__ __forceinline__ int patch_mul16(int nx) { return (65536 + nx - 1) / nx; }
+static_assert(kMaxPatchSide * kPatchLd < 65536 && kPatchLd * 65536LL < (1LL << 31),
+              "the multiply-shift quotient stays exact and q * mul16 fits an int");
+
 // The residual of patch p gathered into xs[0 .. fill) (zero past nloc), with
 // the fused work of kFused (see k_smoother): mode 1 forms r - alpha q and,
 // where this CTA owns block p, writes r and x += alpha p there and clears
 // the other z buffer; mode 2 forms r - K z_in and the owner seeds the output
 // with z_in.
+// the residual at patch node q (zero past nloc), as the sweep of kFused forms it
+template <typename TC, typename TR, int kFused>
+__device__ __forceinline__ TC smoother_value(const PatchGeo& g, int q, const TR* __restrict__ r, int n,
+                                             const FuseArgs& fa, double alpha, int mul16) {
+  TC v = (TC)0;
+  if (q < g.nloc) {
+    const int c = patch_row(q, mul16), a = q - c * g.nx;
+    const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
+    if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
+    else if constexpr (kFused == 2)
+      v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
+                                                g.y0 + 1 + c);
+    else v = (TC)r[id];
+  }
+  return v;
+}
+template <typename TC, int kFused>
+__device__ __forceinline__ void smoother_owner(int p, bool owner, TC* __restrict__ zacc, int n, const FuseArgs& fa,
+                                               double alpha);
 template <typename TC, typename TR, int kFused>
 __device__ __forceinline__ void smoother_gather(const PatchGeo& g, int p, bool owner, const TR* __restrict__ r,
                                                 TC* __restrict__ zacc, int n, const FuseArgs& fa, double alpha,
                                                 TC* xs, int fill) {
-  for (int q = threadIdx.x; q < fill; q += blockDim.x) {
-    TC v = (TC)0;
-    if (q < g.nloc) {
-      const int a = q % g.nx, c = q / g.nx;
-      const long long id = (long long)(g.y0 + 1 + c) * n + (g.x0 + 1 + a);
-      if constexpr (kFused == 1) v = (TC)(fa.r_old[id] - alpha * fa.q[id]);
-      else if constexpr (kFused == 2)
-        v = (TC)r[id] - stencil_apply<TC, TC, TC>((const TC*)fa.zin, (const TC*)fa.kin, n, g.x0 + 1 + a,
-                                                  g.y0 + 1 + c);
-      else v = (TC)r[id];
-    }
-    xs[q] = v;
-  }
+  const int mul16 = patch_mul16(g.nx);
+  for (int q = threadIdx.x; q < fill; q += blockDim.x)
+    xs[q] = smoother_value<TC, TR, kFused>(g, q, r, n, fa, alpha, mul16);
+  smoother_owner<TC, kFused>(p, owner, zacc, n, fa, alpha);
+}
+template <typename TC, int kFused>
+__device__ __forceinline__ void smoother_owner(int p, bool owner, TC* __restrict__ zacc, int n, const FuseArgs& fa,
+                                               double alpha) {
   if (kFused == 1 && owner) {   // this CTA owns block p
     const int I = p % fa.nc, J = p / fa.nc, b = fa.b;
     for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
@@ -897,10 +919,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_smoother_mma(const PatchGeo* __
     const PatchGeo g = geo[p];
     const int T = tiles_per_side(g.nloc);
     __syncthreads();
-    smoother_gather<TC, TR, kFused>(g, p, tofs[p] >= t0, r, zacc, n, fa, alpha, xs, T * kTile);
-    __syncthreads();
     float sx = 1.0f, unscale = 1.0f;
-    if constexpr (kHalf) {   // every warp forms the patch's residual scale
+    if constexpr (!kHalf) {
+      // BF16 needs no scale: each thread gathers a pair of adjacent nodes and
+      // writes its three parts straight into the B fragments (lane 4 k + c of
+      // k-tile j holds columns 16 j + 2 c + {0, 1} in its first word, + 8 in
+      // its second)
+      const int mul16 = patch_mul16(g.nx);
+      for (int t = threadIdx.x; t < T * (kTile / 2); t += blockDim.x) {
+        const int q0 = 2 * t, j = q0 / kTile, w = q0 % kTile, c = (w & 7) >> 1, half = w >> 3;
+        const float v0 = (float)smoother_value<TC, TR, kFused>(g, q0, r, n, fa, alpha, mul16);
+        const float v1 = (float)smoother_value<TC, TR, kFused>(g, q0 + 1, r, n, fa, alpha, mul16);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          reinterpret_cast<unsigned*>(&xb[j * 12 + 4 * k + c])[half] = part16<TS>(v0, k) | (part16<TS>(v1, k) << 16);
+      }
+      smoother_owner<TC, kFused>(p, tofs[p] >= t0, zacc, n, fa, alpha);
+    } else {
+      smoother_gather<TC, TR, kFused>(g, p, tofs[p] >= t0, r, zacc, n, fa, alpha, xs, T * kTile);
+      __syncthreads();
+      // every warp forms the patch's residual scale
       float m = 0.0f;
       for (int q = lane; q < g.nloc; q += 32) m = fmaxf(m, fabsf((float)xs[q]));
 #pragma unroll
@@ -911,13 +949,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_smoother_mma(const PatchGeo* __
         sx = ldexpf(1.0f, 15 - e);
         unscale = ldexpf(1.0f, e - 15);
       }
-    }
-    // B fragments: lane l < 12 of k-tile j holds part l / 4 of x at columns
-    // 16 j + 2 (l % 4) + {0, 1} and the same + 8; lanes 12..31 hold zeros
-    for (int e = threadIdx.x; e < T * 12; e += blockDim.x) {
-      const int j = e / 12, l = e % 12, k = l >> 2, c0 = kTile * j + 2 * (l & 3);
-      auto pk = [&](int q) { return part16<TS>((float)xs[q] * sx, k); };
-      xb[e] = make_uint2(pk(c0) | (pk(c0 + 1) << 16), pk(c0 + 8) | (pk(c0 + 9) << 16));
+      // B fragments: lane l < 12 of k-tile j holds part l / 4 of x at columns
+      // 16 j + 2 (l % 4) + {0, 1} and the same + 8; lanes 12..31 hold zeros
+      for (int e = threadIdx.x; e < T * 12; e += blockDim.x) {
+        const int j = e / 12, l = e % 12, k = l >> 2, c0 = kTile * j + 2 * (l & 3);
+        auto pk = [&](int q) { return part16<TS>((float)xs[q] * sx, k); };
+        xb[e] = make_uint2(pk(c0) | (pk(c0 + 1) << 16), pk(c0 + 8) | (pk(c0 + 9) << 16));
+      }
     }
     __syncthreads();
     const int ta = max(t0, tofs[p]) - tofs[p], tb = min(t1, tofs[p + 1]) - tofs[p];
@@ -951,7 +989,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_smoother_mma(const PatchGeo* __
           if (q < g.nloc) {
             TC v = (TC)y[hh];
             if constexpr (kHalf) v *= (TC)(rscale[(long long)gofs[p] * kRowsPerWarp + q] * unscale);
-            const int a2 = q % g.nx, c2 = q / g.nx;
+            const int c2 = patch_row(q, patch_mul16(g.nx)), a2 = q - c2 * g.nx;
             atomicAdd(zacc + (long long)(g.y0 + 1 + c2) * n + (g.x0 + 1 + a2), eta * v);
           }
         }
@@ -1103,7 +1141,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_smoother_mma_multi(const PatchG
               if (q < g.nloc) {
                 TC v = (TC)y[cc][hh];
                 if constexpr (kHalf) v *= (TC)(rscale[(long long)gofs[p] * kRowsPerWarp + q] * unscale[c]);
-                const int a2 = q % g.nx, c2 = q / g.nx;
+                const int c2 = patch_row(q, patch_mul16(g.nx)), a2 = q - c2 * g.nx;
                 atomicAdd(cs.zacc[c] + (long long)(g.y0 + 1 + c2) * n + (g.x0 + 1 + a2), eta * v);
               }
             }
