@@ -267,7 +267,7 @@ def run_ncu_target(args):
     n, b = args.n, args.b
     kappa, f = workload(n, 5)
     s = tgms.Solver(kappa, b, EIG_TOL, precision=args.precision, flexible=int(args.precision != "f64"),
-                    profile=int(args.profile_loop), smoother_shape=args.shape)
+                    profile=int(args.profile_loop), smoother_shape=args.shape, coarse_solver=args.coarse_solver)
     for _ in range(args.warmup + args.steps):
         it, rep = s.solve(f, rtol=RTOL)
     torch.cuda.synchronize()
@@ -302,7 +302,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = tgms.Solver(kappa, b, EIG_TOL, precision=precision, flexible=flexible, profile=profile,
-                        pointer_mode=pointer_mode, **kw)
+                        pointer_mode=pointer_mode, coarse_solver=args.coarse_solver, **kw)
         torch.cuda.synchronize()
         return s, (time.perf_counter() - t0) * 1e3
 
@@ -352,7 +352,8 @@ def run_ours(args):
     # end to end through the host-pointer ABI (copies inside the timed call)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h = tgms.tg_setup(pin(kappa), n, b, EIG_TOL, 2,
-                      tgms.default_options(precision=prec, flexible=1, pointer_mode=tgms.PTR_HOST),
+                      tgms.default_options(precision=prec, flexible=1, pointer_mode=tgms.PTR_HOST,
+                                           coarse_solver=args.coarse_solver),
                       torch.cuda.current_stream().cuda_stream)
     hf = pin(f)
     hux, huy, hp = pin(np.zeros((n, n + 1))), pin(np.zeros((n + 1, n))), pin(np.zeros((n, n)))
@@ -1242,6 +1243,8 @@ def main():
     ap.add_argument("--hidden", type=int, default=512)
     ap.add_argument("--learned-precision", default="f16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--shape", type=int, default=-1, help="smoother tile shape (-1: autotune)")
+    ap.add_argument("--coarse-solver", default="auto", choices=["auto", "dense", "nd"],
+                    help="solver of the FP64 coarse system (auto: nested dissection above 2048 unknowns)")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--ncu-target", action="store_true", help="headline solves only (for ncu)")

@@ -80,6 +80,19 @@ extern "C" {
 #define TG_COARSE_LEARNED 3  /* spectral problem of Section 4.2 restricted to predicted
                                 flux profiles (see "learned coarse basis" below) */
 
+/* solver of the FP64 coarse system (Section 5: the coarse problem is solved
+ * by a direct method).  Both are exact up to rounding. */
+#define TG_COARSE_SOLVER_AUTO  0   /* nested dissection above 2048 coarse unknowns, else dense */
+#define TG_COARSE_SOLVER_DENSE 1   /* explicit dense inverse: one GEMV of D^2 entries per solve */
+#define TG_COARSE_SOLVER_ND    2   /* one level of nested dissection by coarse block rows: rows of
+                                      coarse nodes separate strips of block rows; interior blocks and
+                                      the separator Schur complement kept as dense FP64 inverses, so a
+                                      solve reads sum_t (n_t^2 + 2 n_t m_t) + NS^2 entries (n_t interior
+                                      and m_t adjacent separator unknowns of strip t, NS separator
+                                      unknowns) in four launches.  Needs at least 4 coarse blocks per
+                                      side (else the dense inverse is used); with tg_update_kappa the
+                                      factor is formed again instead of updated by low rank */
+
 typedef struct tg_handle tg_handle;
 typedef struct tg_mlp tg_mlp;
 
@@ -163,6 +176,8 @@ typedef struct tg_options {
    * takes `net`. */
   const tg_mlp* const* batch_nets;
   int batch_nnets;
+  int coarse_solver;   /* TG_COARSE_SOLVER_*, for the preconditioner's coarse space and the coarse
+                          RT0 system of the preprocessing alike */
 } tg_options;
 
 typedef struct tg_report {
@@ -194,6 +209,8 @@ typedef struct tg_report {
   int operator_launches;  /* profile == 1: launches of the PCG operator kernel (p = z + beta p,
                              q = K p, alpha) timed ... */
   double operator_ms;     /* ... and their summed device time */
+  int coarse_solver;      /* TG_COARSE_SOLVER_DENSE or _ND: the solver of the preconditioner's coarse system */
+  double coarse_solve_mb; /* matrix megabytes (1e6 B) that one coarse solve reads */
 } tg_report;
 
 /* Fills *opt with the parameters of Section 6 (eta 0.2, m1 = m2 = 1), FP64,
@@ -258,6 +275,8 @@ int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rto
  *     applied in O(D^2 |S|) (Sherman-Morrison-Woodbury), or the inverse is
  *     recomputed in full when |S| > min(1024, D/4), after 64 updates in a row
  *     or on a non-positive pivot (tg_report's update_rank: |S|, -1 = full);
+ *     a nested-dissection factor (TG_COARSE_SOLVER_ND) is always formed
+ *     again in full;
  *   coarse = 1: rebuilds the coarse space by the handle's method (spectral
  *     problems, MsFEM or the learned basis); the coarse RT0 inverse of the
  *     preprocessing is updated as for 0;

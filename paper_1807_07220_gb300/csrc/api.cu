@@ -179,6 +179,7 @@ void free_space(CoarseSpace& c) {
   cudaFree(c.owned);
   cudaFree(c.Kinv);
   cudaFree(c.Kdf);
+  nd_free(c.nd);
   c = CoarseSpace{};
 }
 
@@ -245,6 +246,11 @@ int build_space(tg_handle* h, CoarseSpace& c, const std::vector<int>& nsel, bool
   }
   ptr[h->nblocks] = (int)slots.size();
   c.nslots = (int)slots.size();
+  // coarse row keys (nested-dissection ordering of the coarse system)
+  c.key.assign(c.D, 0);
+  for (int u = 0; u < ntheta; ++u) c.key[u] = 2 * (u / (nc - 1) + 1);
+  for (int f = 0; f < nfaces; ++f)
+    for (int u = zbase[f]; u < zbase[f + 1]; ++u) c.key[u] = f < nV ? 2 * (f / (nc - 1)) + 1 : 2 * ((f - nV) / nc + 1);
   std::vector<int> gather((size_t)std::max(c.D, 1) * 4, -1);
   for (int s = 0; s < c.nslots; ++s) {
     int* g = &gather[(size_t)slots[s].coef * 4];
@@ -321,16 +327,39 @@ int assemble_galerkin(tg_handle* h, const CoarseSpace& c, const double* kinv, do
 // separate GEMV, D > kCoarseSplit; FP64 handles and the preprocessing's RT0
 // space keep the FP64 GEMV)
 int refresh_coarse_df(tg_handle* h, CoarseSpace& c) {
-  if (&c != &h->cs || h->opt.precision == TG_PREC_F64 || c.D <= kCoarseSplit) return TG_OK;
+  if (&c != &h->cs || h->opt.precision == TG_PREC_F64 || c.D <= kCoarseSplit || c.solver == 2) return TG_OK;
   if (!c.Kdf && dalloc(&c.Kdf, (size_t)c.D * c.D)) return TG_ERR_OOM;
   launch_split_df(c.Kinv, c.Kdf, (long long)c.D * c.D, h->stream);
   return cuda_err(cudaStreamSynchronize(h->stream));
 }
 
+// Which solver a coarse space of this handle takes (1 dense inverse, 2 nested
+// dissection; the latter needs at least 4 coarse blocks per side)
+int coarse_solver_for(const tg_handle* h, const CoarseSpace& c) {
+  if (h->nc < 4) return 1;
+  if (h->opt.coarse_solver == TG_COARSE_SOLVER_ND) return 2;
+  if (h->opt.coarse_solver == TG_COARSE_SOLVER_AUTO && c.D > kNdAutoMin) return 2;
+  return 1;
+}
+
 // Galerkin matrix of a coarse space with the handle's current kappa, and its
-// inverse (dense Gauss-Jordan)
+// inverse (dense Gauss-Jordan) or nested-dissection factor
 int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
   if (c.D == 0) return cuda_err(cudaGetLastError());
+  c.low_rank_updates = 0;
+  if (coarse_solver_for(h, c) == 2) {
+    int rc = assemble_galerkin(h, c, h->kinv, c.Kinv);   // Kinv holds the matrix itself
+    if (!rc) rc = nd_build(c.Kinv, c.D, c.key, h->nc, c.gather, c.nd, h->d_status, h->stream);
+    if (rc == TG_OK) {
+      c.solver = 2;
+      cudaFree(c.Kdf);
+      c.Kdf = nullptr;
+      return cuda_err(cudaGetLastError());
+    }
+    if (rc != TG_ERR_UNSUPPORTED) return rc;
+  }
+  c.solver = 1;
+  nd_free(c.nd);
   double* tmp = nullptr;
   if (scratch(h, kScrDense, (size_t)c.D * c.D, &tmp)) return TG_ERR_OOM;
   int rc = assemble_galerkin(h, c, h->kinv, c.Kinv);
@@ -338,7 +367,6 @@ int galerkin_inverse(tg_handle* h, CoarseSpace& c) {
     launch_gauss_jordan(c.Kinv, tmp, c.D, h->d_status, h->stream);
     rc = cuda_err(cudaStreamSynchronize(h->stream));
   }
-  c.low_rank_updates = 0;
   if (rc == TG_OK) rc = refresh_coarse_df(h, c);
   if (rc == TG_OK) rc = cuda_err(cudaGetLastError());
   return rc;
@@ -360,7 +388,9 @@ int galerkin_update(tg_handle* h, CoarseSpace& c, const double* delta, const uns
   constexpr int kMaxLowRankUpdates = 64;
   *rank = -1;
   if (c.D == 0) return cuda_err(cudaGetLastError());
-  if (c.low_rank_updates >= kMaxLowRankUpdates) return galerkin_inverse(h, c);
+  // a nested-dissection factor is formed again in full (it costs far less
+  // than a dense Gauss-Jordan inverse)
+  if (c.solver == 2 || c.low_rank_updates >= kMaxLowRankUpdates) return galerkin_inverse(h, c);
   cudaStream_t s = h->stream;
   const int D = c.D;
   double* dK = nullptr;
@@ -516,8 +546,8 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
       dalloc(&c->fd, nn) || dalloc(&c->bd, 4 * n) || dalloc(&c->pd, nn) || dalloc(&c->pw, nn + 2 * n + 2) ||
       dalloc(&c->part, npart) || dalloc(&c->gx, (nc + 1) * nc) || dalloc(&c->gy, (nc + 1) * nc) ||
       dalloc(&c->FH, h->nblocks) || dalloc(&c->absF, h->nblocks) || dalloc(&c->diverr, 2) ||
-      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, 2 * (size_t)h->cs.D) ||
-      dalloc(&c->rt_part, h->rt.nslots) || dalloc(&c->rt_coefs, 2 * (size_t)h->rt.D) || dalloc(&c->st, 1) ||
+      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, 5 * (size_t)h->cs.D) ||
+      dalloc(&c->rt_part, h->rt.nslots) || dalloc(&c->rt_coefs, 5 * (size_t)h->rt.D) || dalloc(&c->st, 1) ||
       dalloc(&c->d_rtol, 1))
     rc = TG_ERR_OOM;
   if (!rc) rc = cuda_err(cudaMalloc(&c->zacc, tc * nn));
@@ -1722,6 +1752,7 @@ int tg_default_options(tg_options* opt) {
   opt->batch_lockstep = 1;
   opt->batch_nets = nullptr;
   opt->batch_nnets = 0;
+  opt->coarse_solver = TG_COARSE_SOLVER_AUTO;
   return TG_OK;
 }
 
@@ -1764,6 +1795,8 @@ int tg_setup(const double* kappa, const tg_grid* grid, double eig_tol, const tg_
       !(eig_tol > 0) || (opt->pointer_mode != TG_PTR_HOST && opt->pointer_mode != TG_PTR_DEVICE))
     return TG_ERR_INVALID_ARG;
   if (opt->cycle != TG_CYCLE_TWO_GRID && opt->cycle != TG_CYCLE_ADDITIVE) return TG_ERR_INVALID_ARG;
+  if (opt->coarse_solver < TG_COARSE_SOLVER_AUTO || opt->coarse_solver > TG_COARSE_SOLVER_ND)
+    return TG_ERR_INVALID_ARG;
   if (opt->cycle == TG_CYCLE_TWO_GRID && opt->m1 < 1) return TG_ERR_UNSUPPORTED;
   if (opt->smoother_shape < -1 || opt->smoother_shape >= kSmootherShapes) return TG_ERR_INVALID_ARG;
   if (opt->coarse_space == TG_COARSE_LEARNED) {
@@ -1883,6 +1916,8 @@ int solve_impl(tg_handle* h, const double* f, const double* bflux, double rtol, 
     rep->refactored_blocks = h->refactored_blocks;
     rep->update_rank[0] = h->update_rank[0];
     rep->update_rank[1] = h->update_rank[1];
+    rep->coarse_solver = h->cs.solver == 2 ? TG_COARSE_SOLVER_ND : TG_COARSE_SOLVER_DENSE;
+    rep->coarse_solve_mb = (h->cs.solver == 2 ? h->cs.nd.bytes : 8.0 * (double)h->cs.D * h->cs.D) * 1e-6;
     float ms = 0;
     if (h->opt.profile) {
       cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);

@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 struct tg_mlp;   // network of the learned coarse basis (learned.cu)
 
@@ -83,6 +84,37 @@ struct Slot {
   int coef;        // coarse unknown
 };
 
+// One row of a ragged batch of dense GEMVs: out = sum_j M[m + j] * x[x0 + j], j < len.
+struct NdRow {
+  long long m;
+  int x0, len, out;
+};
+
+// Nested-dissection factor of an SPD coarse system (coarse_nd.cu), one level:
+// the coarse unknowns are split by coarse block rows into S strips whose
+// interiors do not couple to each other, and S - 1 separators (the unknowns
+// of one row of coarse nodes: the nodal functions of that row and the
+// zero-flux functions of its horizontal coarse faces).  With the unknowns
+// ordered interiors first (strip by strip), separators last, A_t the
+// interior blocks, X_t = A_t^{-1} A_{t,S} and Sigma = A_SS - sum_t A_{S,t} X_t
+// the separator Schur complement, the solve of K y = c is
+//   w_t = A_t^{-1} c_t,  g = c_S - sum_t X_t^T c_t,  y_S = Sigma^{-1} g,
+//   y_t = w_t - X_t y_S,
+// each a batch of dense FP64 GEMVs with blocks stored as explicit inverses.
+struct NdFactor {
+  int D = 0, DI = 0, NS = 0;   // unknowns, interior unknowns, separator unknowns
+  int strips = 0;
+  int* perm = nullptr;         // D: unknown at each position of the interiors-then-separators order (device)
+  int* gatherp = nullptr;      // 4 D: slot ids of the unknown at each position (device)
+  double* M = nullptr;         // per strip [A_t^{-1}; X_t^T] (rows of width n_t), then the X_t, then Sigma^{-1}
+  NdRow* rows_a = nullptr;     // rows of the [A_t^{-1}; X_t^T] blocks (device)
+  NdRow* rows_b = nullptr;     // rows of the X_t blocks (device)
+  int nrows_a = 0, nrows_b = 0;
+  long long y_off = 0;         // element offset of Sigma^{-1} in M
+  long long total = 0;         // entries of M
+  double bytes = 0;            // matrix bytes read by one solve
+};
+
 // Coarse space in per-block slot form.
 struct CoarseSpace {
   int D = 0;                 // coarse unknowns
@@ -98,7 +130,33 @@ struct CoarseSpace {
   float2* Kdf = nullptr;
   int low_rank_updates = 0;  // low-rank updates of Kinv since it was last inverted in full
   int max_slots_per_block = 0;
+  // coarse row key of every unknown (host): 2 j for the nodal functions of
+  // coarse node row j and the zero-flux functions of the horizontal faces at
+  // y = j H (support in block rows j - 1 and j), 2 J + 1 for the zero-flux
+  // functions of the vertical faces in block row J (support in row J only)
+  std::vector<int> key;
+  // solver of the coarse system: 1 = dense inverse Kinv, 2 = nested
+  // dissection (nd; Kinv then holds the Galerkin matrix itself)
+  int solver = 1;
+  NdFactor nd;
 };
+
+// Nested-dissection coarse solver (coarse_nd.cu)
+constexpr int kNdSepMax = 16384;   // separator unknowns staged in shared memory by the separator GEMV
+constexpr int kNdAutoMin = 2048;   // TG_COARSE_SOLVER_AUTO takes nested dissection above this many unknowns
+// Factor of the SPD matrix K (D x D, device, row-major) with row keys `key`
+// and nc coarse blocks per side; gather (device, 4 D) gives the slots of each
+// unknown.  Returns TG_ERR_UNSUPPORTED when fewer than 2 strips of at least 2
+// block rows exist; sets kStNotSpd in *status on a non-positive pivot.  A
+// factor of the same structure (same keys and slots, e.g. after a change of
+// kappa with the coarse basis kept) is formed again in the buffers it already
+// has, so CUDA graphs that captured its solve stay valid.
+int nd_build(const double* K, int D, const std::vector<int>& key, int nc, const int* gather, NdFactor& f,
+             int* status, cudaStream_t s);
+void nd_free(NdFactor& f);
+// d = K^{-1} c, c[u] = sum of the partials of u's slots; work: 4 D doubles
+// after d (device).  Four launches.
+void launch_nd_solve(const NdFactor& f, const double* part, double* d, const PcgState* st, cudaStream_t s);
 
 constexpr int kCoarseSplit = 1024;   // coarse systems larger than this form their right-hand side once
 // Kinv (m entries) into double-float pairs: hi = fl32(x), lo = fl32(x - hi)

@@ -2597,6 +2597,10 @@ void launch_set_condition(cudaGraphConditionalHandle cond, const PcgState* st, c
 }
 void launch_coarse_solve(const CoarseSpace& cs, const double* part, double* coefs, const PcgState* st,
                          cudaStream_t s) {
+  if (cs.solver == 2) {   // nested-dissection factor (coarse_nd.cu)
+    launch_nd_solve(cs.nd, part, coefs, st, s);
+    return;
+  }
   const size_t shm = sizeof(double) * (size_t)cs.D;
   if (cs.D > kCoarseSplit) {
     double* rhs = coefs + cs.D;
@@ -2637,7 +2641,7 @@ void launch_prolong(const CoarseSpace& cs, const double* coefs, int nblocks, int
 template <typename TC, typename TS>
 void launch_coarse_correct(const CoarseSpace& cs, const double* part, double* coefs, int nblocks, int nc, int b, int n,
                            TC* v, const PcgState* st, cudaStream_t s) {
-  if (cs.D <= kCoarseSplit && cs.max_slots_per_block <= kFuseSlots && b * b <= kThreads) {
+  if (cs.solver == 1 && cs.D <= kCoarseSplit && cs.max_slots_per_block <= kFuseSlots && b * b <= kThreads) {
     TG_COUNT(1);
     launch(k_coarse_prolong<TC, TS>, dim3(nblocks), dim3(kThreads), 0, s, part, cs.gather, cs.Kinv, cs.D, cs.slot_ptr,
            cs.slots, (const TS*)cs.owned, v, nc, b, n, st);

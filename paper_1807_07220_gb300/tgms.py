@@ -23,6 +23,7 @@ ERRORS = {
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 COARSE = {"gmsfem": 0, "msfem": 1, "rt0": 2, "learned": 3}
 CYCLE = {"two_grid": 0, "additive": 1}
+COARSE_SOLVER = {"auto": 0, "dense": 1, "nd": 2}
 PTR_HOST, PTR_DEVICE = 0, 1
 
 c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -39,7 +40,8 @@ class tg_options(ctypes.Structure):
                 ("coarse_space", c_int), ("max_basis", c_int), ("profile", c_int),
                 ("net", c_void_p), ("face_profiles", c_void_p), ("learned_k", c_int),
                 ("learned_max_iter", c_int), ("smoother_shape", c_int), ("launch_overlap", c_int),
-                ("cycle", c_int), ("batch_lockstep", c_int), ("batch_nets", c_void_p), ("batch_nnets", c_int)]
+                ("cycle", c_int), ("batch_lockstep", c_int), ("batch_nets", c_void_p), ("batch_nnets", c_int),
+                ("coarse_solver", c_int)]
 
 
 class tg_report(ctypes.Structure):
@@ -51,7 +53,8 @@ class tg_report(ctypes.Structure):
                 ("graph", c_int), ("snapshot_solves", c_int), ("fallback_faces", c_int),
                 ("learned_fallback", c_int), ("smoother_shape", c_int), ("shape_us", ctypes.c_float * 10),
                 ("refactored_patches", c_int), ("refactored_blocks", c_int),
-                ("update_rank", c_int * 2), ("operator_launches", c_int), ("operator_ms", c_double)]
+                ("update_rank", c_int * 2), ("operator_launches", c_int), ("operator_ms", c_double),
+                ("coarse_solver", c_int), ("coarse_solve_mb", c_double)]
 
     def shape_times(self):
         return [float(v) for v in self.shape_us]
@@ -160,6 +163,8 @@ def default_options(**kw):
             v = COARSE[v]
         if k == "cycle" and isinstance(v, str):
             v = CYCLE[v]
+        if k == "coarse_solver" and isinstance(v, str):
+            v = COARSE_SOLVER[v]
         if k == "net":
             v = getattr(v, "handle", v)
             v = v.value if isinstance(v, ctypes.c_void_p) else v
