@@ -82,7 +82,9 @@ extern "C" {
 
 /* solver of the FP64 coarse system (Section 5: the coarse problem is solved
  * by a direct method).  Both are exact up to rounding. */
-#define TG_COARSE_SOLVER_AUTO  0   /* nested dissection above 2048 coarse unknowns, else dense */
+#define TG_COARSE_SOLVER_AUTO  0   /* nested dissection above 768 coarse unknowns, else dense; a
+                                      space whose kappa tg_update_kappa changes with its basis kept
+                                      turns to the dense inverse (low-rank updates) at that call */
 #define TG_COARSE_SOLVER_DENSE 1   /* explicit dense inverse: one GEMV of D^2 entries per solve */
 #define TG_COARSE_SOLVER_ND    2   /* one level of nested dissection by coarse block rows: rows of
                                       coarse nodes separate strips of block rows; interior blocks and
@@ -275,8 +277,9 @@ int tg_solve_warm(tg_handle* h, const double* f, const double* bflux, double rto
  *     applied in O(D^2 |S|) (Sherman-Morrison-Woodbury), or the inverse is
  *     recomputed in full when |S| > min(1024, D/4), after 64 updates in a row
  *     or on a non-positive pivot (tg_report's update_rank: |S|, -1 = full);
- *     a nested-dissection factor (TG_COARSE_SOLVER_ND) is always formed
- *     again in full;
+ *     a nested-dissection factor is formed again in full under
+ *     TG_COARSE_SOLVER_ND, and replaced by the dense inverse (formed in
+ *     full once, then updated as above) under TG_COARSE_SOLVER_AUTO;
  *   coarse = 1: rebuilds the coarse space by the handle's method (spectral
  *     problems, MsFEM or the learned basis); the coarse RT0 inverse of the
  *     preprocessing is updated as for 0;

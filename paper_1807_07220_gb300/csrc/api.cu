@@ -66,6 +66,7 @@ struct tg_handle {
   int fallback_faces = 0;    // learned space: faces that took the exact problem
   int refactored_patches = 0, refactored_blocks = 0;   // factored by the last setup or update
   int update_rank[2] = {-1, -1};   // last update: rows of the low-rank Galerkin-inverse update (cs, rt); -1 full
+  bool regraph = false;      // a coarse space changed solver: the solve context (and its graph) is re-created
   int shape = 0;             // smoother tile shape (autotuned or from the options)
   float shape_us[kSmootherShapes] = {};   // autotuner: time per smoother launch of each shape (0: not tried)
   // coarse spaces: preconditioner and coarse RT0 (preprocessing)
@@ -338,7 +339,7 @@ int refresh_coarse_df(tg_handle* h, CoarseSpace& c) {
 int coarse_solver_for(const tg_handle* h, const CoarseSpace& c) {
   if (h->nc < 4) return 1;
   if (h->opt.coarse_solver == TG_COARSE_SOLVER_ND) return 2;
-  if (h->opt.coarse_solver == TG_COARSE_SOLVER_AUTO && c.D > kNdAutoMin) return 2;
+  if (h->opt.coarse_solver == TG_COARSE_SOLVER_AUTO && c.D > kNdAutoMin && !c.updated_dense) return 2;
   return 1;
 }
 
@@ -388,8 +389,13 @@ int galerkin_update(tg_handle* h, CoarseSpace& c, const double* delta, const uns
   constexpr int kMaxLowRankUpdates = 64;
   *rank = -1;
   if (c.D == 0) return cuda_err(cudaGetLastError());
-  // a nested-dissection factor is formed again in full (it costs far less
-  // than a dense Gauss-Jordan inverse)
+  // a nested-dissection factor is formed again in full; under
+  // TG_COARSE_SOLVER_AUTO the space turns to the dense inverse instead, so
+  // that the next changes are low-rank updates
+  if (c.solver == 2 && h->opt.coarse_solver == TG_COARSE_SOLVER_AUTO) {
+    c.updated_dense = true;
+    h->regraph = true;
+  }
   if (c.solver == 2 || c.low_rank_updates >= kMaxLowRankUpdates) return galerkin_inverse(h, c);
   cudaStream_t s = h->stream;
   const int D = c.D;
@@ -1605,6 +1611,12 @@ int update_kappa_impl(tg_handle* h, const double* kappa, int coarse) {
     rc = ctx_alloc(h, &h->ctx);
   }
   if (!rc) rc = (coarse == 2) ? galerkin_inverse(h, h->rt) : galerkin_update(h, h->rt, delta, d_bmask, &h->update_rank[1]);
+  if (!rc && h->regraph) {   // the solve graph captured the other coarse solver
+    h->regraph = false;
+    ctx_free(h->ctx);
+    h->ctx = nullptr;
+    rc = ctx_alloc(h, &h->ctx);
+  }
   if (rc) return rc;
   int st = 0;
   if ((rc = read_status(h, &st))) return rc;

@@ -139,11 +139,15 @@ struct CoarseSpace {
   // dissection (nd; Kinv then holds the Galerkin matrix itself)
   int solver = 1;
   NdFactor nd;
+  // TG_COARSE_SOLVER_AUTO: set at the first low-rank update request (a
+  // change of kappa with the basis kept); the space keeps the dense inverse
+  // from then on, whose low-rank updates cost far less than new factors
+  bool updated_dense = false;
 };
 
 // Nested-dissection coarse solver (coarse_nd.cu)
 constexpr int kNdSepMax = 16384;   // separator unknowns staged in shared memory by the separator GEMV
-constexpr int kNdAutoMin = 2048;   // TG_COARSE_SOLVER_AUTO takes nested dissection above this many unknowns
+constexpr int kNdAutoMin = 768;    // TG_COARSE_SOLVER_AUTO takes nested dissection above this many unknowns
 // Factor of the SPD matrix K (D x D, device, row-major) with row keys `key`
 // and nc coarse blocks per side; gather (device, 4 D) gives the slots of each
 // unknown.  Returns TG_ERR_UNSUPPORTED when fewer than 2 strips of at least 2

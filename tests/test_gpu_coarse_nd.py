@@ -203,3 +203,44 @@ def test_invalid_coarse_solver_is_rejected(tg):
     with pytest.raises(tg.TgmsError) as e:
         tg.tg_setup(dev(kappa), 32, 8, 10.0, options=o, stream=torch.cuda.current_stream().cuda_stream)
     assert e.value.code == -1
+
+
+def test_auto_choice_and_switch_to_dense_under_kappa_updates(tg):
+    """TG_COARSE_SOLVER_AUTO: the dense inverse for at most 768 coarse
+    unknowns, nested dissection above; a handle whose kappa is changed with
+    its basis kept turns to the dense inverse at that call (formed in full)
+    and takes low-rank updates after it, solving like a fresh dense handle
+    updated the same way."""
+    small = tg.Solver(inputs.channel_field(64, 1e4, 2), 16, 10.0)
+    try:
+        _, rep = small.solve(inputs.quarter_five_spot(64), rtol=1e-8)
+        assert rep.coarse_solver == 1 and rep.coarse_unknowns <= 768
+    finally:
+        small.close()
+    n, b = 256, 8
+    k0 = inputs.channel_field(n, 1e5, 4)
+    f = inputs.quarter_five_spot(n)
+    s = tg.Solver(k0, b, 10.0, precision="f16", flexible=1)
+    t = tg.Solver(k0, b, 10.0, precision="f16", flexible=1, coarse_solver="dense")
+    try:
+        _, rep = s.solve(f, rtol=1e-8)
+        assert rep.coarse_solver == 2 and rep.coarse_unknowns > 768
+        k = k0.copy()
+        for step, (i0, j0) in enumerate(((130, 130), (50, 200))):
+            k[j0:j0 + 4, i0:i0 + 4] *= 0.1
+            for h in (s, t):
+                tg.tg_update_kappa(h.h, dev(k), 0)
+            it, rep = s.solve(f, rtol=1e-12)
+            it2, rep2 = t.solve(f, rtol=1e-12)
+            assert rep.coarse_solver == 1
+            if step == 0:
+                assert rep.update_rank[0] == -1 and rep.update_rank[1] == -1
+            else:
+                assert rep.update_rank[0] > 0 and rep.update_rank[1] > 0
+            assert abs(it - it2) <= 1, (it, it2)
+            u_ref, p_ref = solve_direct(Grid(n, b), k, f)
+            got_u = np.concatenate([s.ux.cpu().numpy().ravel(), s.uy.cpu().numpy().ravel()])
+            assert rel(got_u, u_ref) < 1e-8 and rel(s.p.cpu().numpy().ravel(), p_ref) < 1e-8
+    finally:
+        s.close()
+        t.close()
