@@ -1194,6 +1194,24 @@ __device__ __forceinline__ void band_quad_if(bool ln, const TC* p, BandQuad<TC>&
     for (int k = 0; k < 4; ++k) q.v[k] = (TC)0;
   }
 }
+// four consecutive right-hand sides / solution values of the shared patch
+// vector (16-byte aligned quads): one shared-memory access per four rows
+// instead of one per row
+__device__ __forceinline__ void xs_ld4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void xs_ld4(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void xs_st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void xs_st4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 template <typename TC, typename TR, int kFused>
 __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGeo* __restrict__ geo, int npatch,
                                                                    const TC* __restrict__ band, int ldb,
@@ -1202,7 +1220,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGe
                                                                    const PcgState* st, FuseArgs fa) {
   pdl_entry();
   if (st && st->done) return;
-  __shared__ TC xs_all[kBandWarps][kPatchLd];
+  __shared__ __align__(16) TC xs_all[kBandWarps][kPatchLd];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * kBandWarps + warp;
   if (p >= npatch) return;   // warp-uniform; no block-wide barrier below
@@ -1265,16 +1283,18 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGe
       for (int i = 0; i < kG; ++i) {
         const BandQuad<TC> cur = pf[i];
         band_quad_if(ln, gp + i * gs, pf[i]);
+        TC xv[4], yv[4];
+        xs_ld4(xs + j0 + 4 * i, xv);              // rows j0 + 4 i .. + 3
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int j = j0 + 4 * i + k;
           const TC cj = cur.v[k];
-          TC y = (xs[j] - acc) * cj;             // meaningful in lane 0
+          TC y = (xv[k] - acc) * cj;             // meaningful in lane 0
           y = __shfl_sync(0xffffffffu, y, 0);
-          if (lane == 0) xs[j] = y;
-          else acc = fma(cj, y, acc);
+          yv[k] = y;
+          if (lane != 0) acc = fma(cj, y, acc);
           acc = __shfl_down_sync(0xffffffffu, acc, 1);
         }
+        if (lane == 0) xs_st4(xs + j0 + 4 * i, yv);
       }
     }
   }
@@ -1292,16 +1312,18 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band(const PatchGe
       for (int i = 0; i < kG; ++i) {
         const BandQuad<TC> cur = pf[i];
         band_quad_if(ln, gp - i * gs, pf[i]);
+        TC xv[4], yv[4];
+        xs_ld4(xs + j0 - 4 * i - 3, xv);          // rows j0 - 4 i - 3 .. j0 - 4 i
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int j = j0 - 4 * i - k;
           const TC cj = cur.v[3 - k];
-          TC x = (xs[j] - acc) * cj;             // meaningful in lane 0
+          TC x = (xv[3 - k] - acc) * cj;         // meaningful in lane 0
           x = __shfl_sync(0xffffffffu, x, 0);
-          if (lane == 0) xs[j] = x;
-          else acc = fma(cj, x, acc);
+          yv[3 - k] = x;
+          if (lane != 0) acc = fma(cj, x, acc);
           acc = __shfl_down_sync(0xffffffffu, acc, 1);
         }
+        if (lane == 0) xs_st4(xs + j0 - 4 * i - 3, yv);
       }
     }
   }
@@ -1340,7 +1362,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const Pa
                                                                         const PcgState* st, FuseArgs fa) {
   pdl_entry();
   if (st && st->done) return;
-  __shared__ float xs_all[kBandWarps][kPatchLd];
+  __shared__ __align__(16) float xs_all[kBandWarps][kPatchLd];
   __shared__ __align__(16) float4 ring_all[kBandWarps][kBandRing][kBandLd];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * kBandWarps + warp;
@@ -1402,16 +1424,18 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const Pa
       band_cp_wait<kBandRing - 1>();   // group k has landed
       const float4 cur = ln ? ring[k % kBandRing][lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+      float xv[4], yv[4];
+      xs_ld4(xs + 4 * k, xv);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int j = 4 * k + t;
         const float cj = cv[t];
-        float y = (xs[j] - acc) * cj;             // meaningful in lane 0
+        float y = (xv[t] - acc) * cj;             // meaningful in lane 0
         y = __shfl_sync(0xffffffffu, y, 0);
-        if (lane == 0) xs[j] = y;
-        else acc = fmaf(cj, y, acc);
+        yv[t] = y;
+        if (lane != 0) acc = fmaf(cj, y, acc);
         acc = __shfl_down_sync(0xffffffffu, acc, 1);
       }
+      if (lane == 0) xs_st4(xs + 4 * k, yv);
     }
   }
   band_cp_wait<0>();
@@ -1432,16 +1456,18 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_smoother_band_ring(const Pa
       band_cp_wait<kBandRing - 1>();
       const float4 cur = ln ? ring[k % kBandRing][lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+      float xv[4], yv[4];
+      xs_ld4(xs + nrow - 4 - 4 * k, xv);            // rows nrow - 4 - 4 k .. nrow - 1 - 4 k
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int j = nrow - 1 - 4 * k - t;
         const float cj = cv[3 - t];
-        float x = (xs[j] - acc) * cj;             // meaningful in lane 0
+        float x = (xv[3 - t] - acc) * cj;         // meaningful in lane 0
         x = __shfl_sync(0xffffffffu, x, 0);
-        if (lane == 0) xs[j] = x;
-        else acc = fmaf(cj, x, acc);
+        yv[3 - t] = x;
+        if (lane != 0) acc = fmaf(cj, x, acc);
         acc = __shfl_down_sync(0xffffffffu, acc, 1);
       }
+      if (lane == 0) xs_st4(xs + nrow - 4 - 4 * k, yv);
     }
   }
   band_cp_wait<0>();
