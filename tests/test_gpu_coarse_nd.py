@@ -217,7 +217,7 @@ def test_auto_choice_and_switch_to_dense_under_kappa_updates(tg):
         assert rep.coarse_solver == 1 and rep.coarse_unknowns <= 768
     finally:
         small.close()
-    n, b = 256, 8
+    n, b = 128, 4   # 32 blocks per side: 961 nodal functions
     k0 = inputs.channel_field(n, 1e5, 4)
     f = inputs.quarter_five_spot(n)
     s = tg.Solver(k0, b, 10.0, precision="f16", flexible=1)
@@ -226,7 +226,7 @@ def test_auto_choice_and_switch_to_dense_under_kappa_updates(tg):
         _, rep = s.solve(f, rtol=1e-8)
         assert rep.coarse_solver == 2 and rep.coarse_unknowns > 768
         k = k0.copy()
-        for step, (i0, j0) in enumerate(((130, 130), (50, 200))):
+        for step, (i0, j0) in enumerate(((62, 62), (25, 100))):
             k[j0:j0 + 4, i0:i0 + 4] *= 0.1
             for h in (s, t):
                 tg.tg_update_kappa(h.h, dev(k), 0)
