@@ -62,7 +62,7 @@ extern "C" {
  * the coarse matrix are always FP64. */
 #define TG_PREC_F64  0
 #define TG_PREC_F32  1
-#define TG_PREC_BF16 2   /* BF16 storage, FP32 arithmetic */
+#define TG_PREC_BF16 2   /* BF16 patch inverses, FP32 coarse tiles, FP32 arithmetic */
 #define TG_PREC_F16  3   /* FP16 patch inverses, each row scaled by a power of two that puts its
                             largest magnitude in [2^14, 2^15) (the factor is undone after the row's
                             FP32 dot product); FP32 coarse tiles; FP32 arithmetic.  Same bytes as

@@ -189,7 +189,7 @@ size_t ts_size(int precision) {
   return precision == TG_PREC_F64 ? 8 : precision == TG_PREC_F32 ? 4 : 2;
 }
 size_t tile_size(int precision) {
-  return precision == TG_PREC_F64 ? 8 : precision == TG_PREC_BF16 ? 2 : 4;
+  return precision == TG_PREC_F64 ? 8 : 4;
 }
 
 int status_to_err(int st) {
@@ -288,10 +288,8 @@ int finish_space(tg_handle* h, CoarseSpace& c, const double* psiS, const double*
   if (c.nslots > 0) {
     if (rt_only || h->opt.precision == TG_PREC_F64)
       launch_build_tiles<double>(c, psiS, fcoef, zcoef, jeff, rt_only ? 1 : 0, n, b, h->stream);
-    else if (h->opt.precision == TG_PREC_F32 || h->opt.precision == TG_PREC_F16)
-      launch_build_tiles<float>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
     else
-      launch_build_tiles<__nv_bfloat16>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
+      launch_build_tiles<float>(c, psiS, fcoef, zcoef, jeff, 0, n, b, h->stream);
   }
   return galerkin_inverse(h, c);
 }

@@ -123,7 +123,7 @@ struct CoarseSpace {
   Slot* slots = nullptr;     // device
   int* gather = nullptr;     // D*4 global slot ids (-1 = none) (device)
   double* closed = nullptr;  // nslots*(b+1)^2 FP64 tiles (device)
-  void* owned = nullptr;     // nslots*b*b tiles in storage precision (device)
+  void* owned = nullptr;     // nslots*b*b tiles: FP64 (FP64 handles), else FP32 (device)
   double* Kinv = nullptr;    // D*D inverse of the Galerkin matrix (device)
   // mixed-precision handles with D > kCoarseSplit: Kinv as double-float
   // pairs (hi, lo: FP32, hi + lo = Kinv to ~2^-48), applied on the FP32 pipe
@@ -182,10 +182,12 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(doubl
 template <> __device__ __forceinline__ __half from_d<__half>(double x) { return __double2half(x); }
 
 // Coarse basis tiles are stored in the preconditioner precision, except with
-// FP16 patch inverses, whose tiles stay FP32 (they are a small fraction of the
-// bytes and carry no row scale).
+// 2-byte patch inverses (BF16, FP16), whose tiles stay FP32: they are a small
+// fraction of the bytes, and BF16 tiles (8 significant bits) cost PCG
+// iterations at large grids.
 template <typename TS> struct TileOf { using T = TS; };
 template <> struct TileOf<__half> { using T = float; };
+template <> struct TileOf<__nv_bfloat16> { using T = float; };
 template <typename TS> using tile_t = typename TileOf<TS>::T;
 
 template <typename T>
