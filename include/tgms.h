@@ -133,7 +133,10 @@ typedef struct tg_options {
   int learned_k;
   int learned_max_iter;
   /* smoother tile shape: -1 = autotune at setup (time every shape on the
-   * handle's own patch inverses, keep the fastest); 0 = 16-byte loads, 4 rows
+   * handle's own patch inverses, keep the fastest; where the dense inverses,
+   * counted at two bytes an entry, exceed 1.5 times the L2, a mixed-precision
+   * handle forms no dense inverses and picks between the band forms 7 and 9
+   * only); 0 = 16-byte loads, 4 rows
    * per pass (2 for FP64 storage); 1 = 16-byte loads, 2 rows; 2 = 8-byte
    * loads, 4 rows; 3 = 8-byte loads, 2 rows; 4 = TMA bulk copies into a
    * shared-memory ring; 5 = shape 3 and 6 = shape 1 software-pipelined (the

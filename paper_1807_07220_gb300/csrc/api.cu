@@ -46,6 +46,7 @@ struct tg_handle {
   int ngroups = 0;
   void* pinv = nullptr;
   void* pband = nullptr;    // band factors of the patches in the arithmetic type (tile shape kShapeBand)
+  bool dense = true;        // the dense patch inverses (and tiles) are formed (dense_inverses_needed)
   void* ptiles = nullptr;   // 2-byte storage: the inverses in the tensor-core tile layout (kShapeTensor)
   int* d_tofs = nullptr;    // first 16-row tile of each patch (+ total)
   BandRef band;
@@ -1058,6 +1059,28 @@ std::vector<int> selected(int count, const std::vector<unsigned char>* sel) {
   return ids;
 }
 
+// Whether the dense patch inverses (and their tensor-core tiles) are formed:
+// FP64 handles and handles given a dense tile shape always; handles whose
+// shape the autotuner picks only while the inverses, counted at two bytes an
+// entry, stay within 1.5 times the L2.  Above that the band form was the
+// faster one at every size measured (the autotuner's warm per-launch times,
+// FP16: 448^2 / b = 16, 208 MB, 39.4 against 41.1 us; 512^2 / 16, 272 MB,
+// 39.4 against 51.7; 768^2 / 8, 285 MB, 57.8 against 87.8; 1024^2 / 16, 1.1
+// GB, 80 against 186), while at 384^2 / 16 (153 MB) the dense tensor-core
+// form still won (28.8 against 37.4 us).  The inverses cost most of the
+// patch setup and of the handle's memory.
+bool dense_inverses_needed(const tg_handle* h, long long entries) {
+  if (h->opt.precision == TG_PREC_F64) return true;
+  if (h->opt.smoother_shape >= 0) return !is_band_shape(h->opt.smoother_shape);
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+      l2 <= 0) {
+    cudaGetLastError();
+    return true;
+  }
+  return 2.0 * (double)entries <= 1.5 * (double)l2;
+}
+
 // oversampled patches K_i^+: local operators, band Cholesky, dense inverses.
 // update: the storage exists and only the patches in `changed` (NULL: all)
 // are factored again
@@ -1073,9 +1096,12 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
     if (dalloc(&h->d_gofs, gofs.size()) || dalloc(&h->d_pgeo, L.geo.size())) return TG_ERR_OOM;
     TG_CK(cudaMemcpyAsync(h->d_gofs, gofs.data(), sizeof(int) * gofs.size(), cudaMemcpyHostToDevice, s));
     TG_CK(cudaMemcpyAsync(h->d_pgeo, L.geo.data(), sizeof(PatchGeo) * L.geo.size(), cudaMemcpyHostToDevice, s));
-    TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)L.off * ts_size(h->opt.precision))));
-    if (h->opt.precision == TG_PREC_F16 && dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup))
-      return TG_ERR_OOM;
+    h->dense = dense_inverses_needed(h, L.off);
+    if (h->dense) {
+      TG_CK(cudaMalloc(&h->pinv, std::max<size_t>(1, (size_t)L.off * ts_size(h->opt.precision))));
+      if (h->opt.precision == TG_PREC_F16 && dalloc(&h->rscale, (size_t)h->ngroups * kRowsPerGroup))
+        return TG_ERR_OOM;
+    }
     // band factors for the band smoother: FP64 handles in FP64, the others in FP32
     h->band.ldb = wmax + 1;   // stored row width: the widest band plus the reciprocal diagonal
     if (h->band.ldb > kBandLd) return TG_ERR_UNSUPPORTED;
@@ -1084,7 +1110,7 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
     TG_CK(cudaMalloc(&h->pband, std::max<size_t>(1, (size_t)h->npatch * h->band.stride * esz)));
     h->band.p = h->pband;
     // 2-byte storage: the same inverses in the tensor-core tile layout
-    if (h->opt.precision == TG_PREC_BF16 || h->opt.precision == TG_PREC_F16) {
+    if (h->dense && (h->opt.precision == TG_PREC_BF16 || h->opt.precision == TG_PREC_F16)) {
       TG_CK(cudaMalloc(&h->ptiles, std::max<size_t>(1, (size_t)L.toff * 2)));
       if (dalloc(&h->d_tofs, L.tofs.size())) return TG_ERR_OOM;
       TG_CK(cudaMemcpyAsync(h->d_tofs, L.tofs.data(), sizeof(int) * L.tofs.size(), cudaMemcpyHostToDevice, s));
@@ -1111,7 +1137,7 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
   const int batch = std::max(1, std::min(cnt, (int)((256LL << 20) / (8LL * nmax * nmax))));
   int rc = (scratch(h, kScrRect, cnt, &d_rect) || scratch(h, kScrGeo, cnt, &d_geo) ||
             scratch(h, kScrIds, cnt, &d_ids) || scratch(h, kScrBand, (size_t)cnt * nmax * (wmax + 1), &band) ||
-            scratch(h, kScrInv, (size_t)batch * nmax * nmax, &inv))
+            (h->dense && scratch(h, kScrInv, (size_t)batch * nmax * nmax, &inv)))
                ? TG_ERR_OOM : TG_OK;
   if (!rc) rc = cuda_err(cudaMemcpyAsync(d_rect, crect.data(), sizeof(int4) * cnt, cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_err(cudaMemcpyAsync(d_geo, cgeo.data(), sizeof(PatchGeo) * cnt, cudaMemcpyHostToDevice, s));
@@ -1123,7 +1149,7 @@ int setup_patches(tg_handle* h, bool update = false, const std::vector<unsigned 
       launch_store_band<double>(band, d_rect, d_ids, cnt, wmax, nmax, h->band.stride, (double*)h->pband, s);
     else
       launch_store_band<float>(band, d_rect, d_ids, cnt, wmax, nmax, h->band.stride, (float*)h->pband, s);
-    for (int first = 0; first < cnt; first += batch) {
+    for (int first = 0; h->dense && first < cnt; first += batch) {
       const int m = std::min(batch, cnt - first);
       launch_band_inverse(band, d_rect, first, m, wmax, nmax, inv, s);
       if (h->opt.precision == TG_PREC_F64)
@@ -1410,8 +1436,9 @@ int autotune_smoother_t(tg_handle* h) {
             cand_f64[] = {0, 4, 7}, cand_f16[] = {0, 1, 2, 3, 5, 6, 7, 8, 9};
   // FP16: no TMA ring; the tensor-core tiles exist for 2-byte storage only;
   // FP64 factors have one band form
-  const int* cand = f64 ? cand_f64 : f16 ? cand_f16 : bf16 ? cand_bf16 : cand_f32;
-  const int ncand = f64 ? 3 : f16 ? 9 : bf16 ? 10 : 9;
+  const int cand_band[] = {7, 9};   // handles without dense inverses (dense_inverses_needed)
+  const int* cand = !h->dense ? cand_band : f64 ? cand_f64 : f16 ? cand_f16 : bf16 ? cand_bf16 : cand_f32;
+  const int ncand = !h->dense ? 2 : f64 ? 3 : f16 ? 9 : bf16 ? 10 : 9;
   float best = 1e30f;
   int best_shape = 0;
   for (int i = 0; i < ncand && !rc; ++i) {

@@ -122,13 +122,18 @@ def test_headline_256_against_direct_solve(tg):
 def test_large_grids_properties(tg, n, prec):
     """512 x 512 (operator at two rows per thread) and 1024 x 1024 (band
     smoother where the autotuner picks it, operator at four rows per
-    thread): the properties that fix the discrete solution, at rtol 1e-12."""
+    thread): the properties that fix the discrete solution, at rtol 1e-12.
+    At both sizes the 2-byte dense inverses exceed 1.5 times the L2, so
+    the handle forms none and the autotuner times the two band forms only."""
     b = 16
     kappa = inputs.grf_channel_field(n, CONTRAST, FIELD_SEED)
     f = inputs.quarter_five_spot(n)
     chk = Checks(n, b, kappa, f)
     it, rep, u, p, shape = gpu_solve(tg, kappa, b, f, 1e-12, precision=prec, flexible=1)
     assert rep.converged == 1, (it, shape)
+    times = rep.shape_times()
+    assert shape in (7, 9) and times[7] > 0 and times[9] > 0, (shape, times)
+    assert all(times[k] == 0 for k in (0, 1, 2, 3, 4, 5, 6, 8)), times
     check_tight(chk.measure(u, p))
 
 
