@@ -617,8 +617,9 @@ __global__ void k_snapshots(const double* __restrict__ kinv, const double* __res
 //       of E_i (fine-face trace product, kappa_e^{-1} the mean of the two
 //       adjacent cells).
 // Solved as L_a^{-1} s L_a^{-T} y = mu y (a = L_a L_a^T, mu = 1/lambda) by
-// cyclic Jacobi, so the selected (small lambda = large mu) pairs carry full
-// relative accuracy.  Then the selected span is split into one function with
+// Jacobi rotations (jacobi_warp on the face's warp; jacobi_serial for the
+// small Ritz problems), so the selected (small lambda = large mu) pairs carry
+// full relative accuracy.  Then the selected span is split into one function with
 // unit m-coefficient (unit flux through E_i, min-norm combination) and
 // nsel-1 zero-flux functions (a Householder complement of the m-coefficients).
 constexpr int kJ = kMaxB;
@@ -669,6 +670,79 @@ __device__ void jacobi_serial(double (*A)[kJ], double (*V)[kJ], int m) {
   }
 }
 
+// The same Jacobi iteration on one warp (all 32 lanes call it): the m
+// indices, padded to an even count m2, meet in m2 - 1 rounds of m2 / 2
+// disjoint pairs per sweep (round-robin ordering).  Each round, one lane per
+// pair forms its rotation from the current A (the formula of jacobi_serial);
+// the rotations, which commute, are then applied to the columns of A, to its
+// rows and to the columns of V with the work spread over the warp.  Same
+// stopping test.
+__device__ void jacobi_warp(double (*A)[kJ], double (*V)[kJ], int m, int lane) {
+  __shared__ double rc[kJ / 2], rs[kJ / 2];
+  __shared__ int rp[kJ / 2], rq[kJ / 2], rot[kJ / 2];
+  for (int t = lane; t < m * m; t += 32) V[t / m][t % m] = (t / m == t % m) ? 1.0 : 0.0;
+  const int m2 = m + (m & 1), np = m2 / 2;
+  double loc = 0.0;
+  for (int t = lane; t < m * m; t += 32) loc += A[t / m][t % m] * A[t / m][t % m];
+  const double scale = sqrt(warp_sum(loc));
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int t = lane; t < m * m; t += 32)
+      if (t / m != t % m) off += A[t / m][t % m] * A[t / m][t % m];
+    off = warp_sum(off);   // the same value in every lane
+    if (sqrt(off) <= 1e-15 * scale) break;
+    for (int r = 0; r < m2 - 1; ++r) {
+      if (lane < np) {
+        int p = lane == 0 ? r : (r + lane) % (m2 - 1);
+        int q = lane == 0 ? m2 - 1 : (r - lane + (m2 - 1)) % (m2 - 1);
+        if (p > q) { const int x = p; p = q; q = x; }
+        double c = 1.0, sn = 0.0;
+        int did = 0;
+        if (q < m && A[p][q] != 0.0) {   // the padding index rotates nothing
+          const double apq = A[p][q], diff = A[q][q] - A[p][p];
+          double t;
+          if (fabs(diff) > 1e150 * fabs(apq)) {
+            t = apq / diff;
+          } else {
+            const double tau = diff / (2.0 * apq);
+            t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+          }
+          c = 1.0 / sqrt(1.0 + t * t);
+          sn = t * c;
+          did = 1;
+        }
+        rp[lane] = p; rq[lane] = q; rc[lane] = c; rs[lane] = sn; rot[lane] = did;
+      }
+      __syncwarp();
+      for (int t = lane; t < m * np; t += 32) {   // columns of A: (row i, pair k)
+        const int i = t / np, k = t % np;
+        if (!rot[k]) continue;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], sn = rs[k], aip = A[i][p], aiq = A[i][q];
+        A[i][p] = c * aip - sn * aiq;
+        A[i][q] = sn * aip + c * aiq;
+      }
+      __syncwarp();
+      for (int t = lane; t < m * np; t += 32) {   // rows of A and columns of V: (index j, pair k)
+        const int j = t / np, k = t % np;
+        if (!rot[k]) continue;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], sn = rs[k];
+        const double apj = A[p][j], aqj = A[q][j];
+        A[p][j] = c * apj - sn * aqj;
+        A[q][j] = sn * apj + c * aqj;
+        const double vjp = V[j][p], vjq = V[j][q];
+        V[j][p] = c * vjp - sn * vjq;
+        V[j][q] = sn * vjp + c * vjq;
+      }
+      __syncwarp();
+      if (lane < np && rot[lane]) A[rp[lane]][rq[lane]] = A[rq[lane]][rp[lane]] = 0.0;
+      __syncwarp();
+    }
+  }
+}
+
 __device__ bool cholesky_serial(double (*A)[kJ], int m) {  // lower factor in place
   for (int j = 0; j < m; ++j) {
     double d = A[j][j];
@@ -711,10 +785,13 @@ __device__ __forceinline__ void normal_values(int kind, int l, int b, double h, 
 }
 
 __global__ void k_face_spectral(SpectralArgs A) {
-  if (threadIdx.x != 0) return;
+  // one warp per face: lane 0 assembles the problem and selects the
+  // functions, the warp runs the Jacobi iteration
+  const int lane = threadIdx.x;
   __shared__ double S[kJ][kJ], Aa[kJ][kJ], V[kJ][kJ], C[kJ][kJ];
   __shared__ double mu[kJ], lamv[kJ], wv[kJ];
   __shared__ int ord[kJ];
+  __shared__ int go;
   const int n = A.n, b = A.b, nc = n / b;
   const int f = blockIdx.x;
   if (A.fmask && !A.fmask[f]) return;
@@ -726,56 +803,64 @@ __global__ void k_face_spectral(SpectralArgs A) {
   const double h = 1.0 / n, H = b * h;
   const bool learned = (A.prof != nullptr);
   const int m_fn = learned ? A.jpred[f] : b;    // functions of the face
-  if (A.jeff) A.jeff[f] = m_fn;
-  for (int k = 0; k < b; ++k) A.lam[(long long)f * b + k] = INFINITY;
-  if (learned && m_fn < 1) {                     // nothing predicted: exact problem
-    A.fallback[f] = 1;
-    return;
-  }
-  // flux weights: coefficient of m in each function
-  for (int i = 0; i < m_fn; ++i) wv[i] = learned ? A.ccoef[((long long)f * A.kmax + i) * b] : (i == 0 ? 1.0 : 0.0);
-  const double* G1 = A.gram + ((long long)blk1 * 4 + side1) * b * b;
-  const double* G2 = A.gram + ((long long)blk2 * 4 + side2) * b * b;
-  // s = H^{-1} (Gram_{K1} + Gram_{K2} + div term), div term 2 w_i w_j
-  for (int i = 0; i < m_fn; ++i)
-    for (int j = 0; j < m_fn; ++j) S[i][j] = (G1[i * b + j] + G2[i * b + j] + 2.0 * wv[i] * wv[j]) / H;
-  // a = N diag(kappa_e^{-1}) N^T, N the normal values of the functions on E_i
-  for (int i = 0; i < m_fn; ++i)
-    for (int j = 0; j < m_fn; ++j) Aa[i][j] = 0.0;
-  for (int l = 0; l < b; ++l) {
-    const double ke = face_kinv(A.kinv, n, b, kind, I, J, l);
-    double Nl[kJ];
-    if (learned) {
-      for (int i = 0; i < m_fn; ++i) Nl[i] = A.prof[((long long)f * A.kmax + i) * b + l];
+  if (lane == 0) {
+    go = 0;
+    if (A.jeff) A.jeff[f] = m_fn;
+    for (int k = 0; k < b; ++k) A.lam[(long long)f * b + k] = INFINITY;
+    if (learned && m_fn < 1) {                     // nothing predicted: exact problem
+      A.fallback[f] = 1;
     } else {
-      normal_values(kind, l, b, h, Nl);
-    }
-    for (int i = 0; i < m_fn; ++i)
-      for (int j = 0; j < m_fn; ++j) Aa[i][j] += ke * Nl[i] * Nl[j];
-  }
-  if (!cholesky_serial(Aa, m_fn)) {
-    atomicOr(A.status, kStNotSpd);
-    return;
-  }
-  // S <- L^{-1} S L^{-T}
-  for (int col = 0; col < m_fn; ++col)
-    for (int i = 0; i < m_fn; ++i) {
-      double v = S[i][col];
-      for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[k][col];
-      S[i][col] = v / Aa[i][i];
-    }
-  for (int row = 0; row < m_fn; ++row)
-    for (int i = 0; i < m_fn; ++i) {
-      double v = S[row][i];
-      for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[row][k];
-      S[row][i] = v / Aa[i][i];
-    }
-  for (int i = 0; i < m_fn; ++i)
-    for (int j = 0; j < i; ++j) {
-      const double v = 0.5 * (S[i][j] + S[j][i]);
-      S[i][j] = S[j][i] = v;
-    }
-  jacobi_serial(S, V, m_fn);
+      // flux weights: coefficient of m in each function
+      for (int i = 0; i < m_fn; ++i) wv[i] = learned ? A.ccoef[((long long)f * A.kmax + i) * b] : (i == 0 ? 1.0 : 0.0);
+      const double* G1 = A.gram + ((long long)blk1 * 4 + side1) * b * b;
+      const double* G2 = A.gram + ((long long)blk2 * 4 + side2) * b * b;
+      // s = H^{-1} (Gram_{K1} + Gram_{K2} + div term), div term 2 w_i w_j
+      for (int i = 0; i < m_fn; ++i)
+        for (int j = 0; j < m_fn; ++j) S[i][j] = (G1[i * b + j] + G2[i * b + j] + 2.0 * wv[i] * wv[j]) / H;
+      // a = N diag(kappa_e^{-1}) N^T, N the normal values of the functions on E_i
+      for (int i = 0; i < m_fn; ++i)
+        for (int j = 0; j < m_fn; ++j) Aa[i][j] = 0.0;
+      for (int l = 0; l < b; ++l) {
+        const double ke = face_kinv(A.kinv, n, b, kind, I, J, l);
+        double Nl[kJ];
+        if (learned) {
+          for (int i = 0; i < m_fn; ++i) Nl[i] = A.prof[((long long)f * A.kmax + i) * b + l];
+        } else {
+          normal_values(kind, l, b, h, Nl);
+        }
+        for (int i = 0; i < m_fn; ++i)
+          for (int j = 0; j < m_fn; ++j) Aa[i][j] += ke * Nl[i] * Nl[j];
+      }
+      if (!cholesky_serial(Aa, m_fn)) {
+        atomicOr(A.status, kStNotSpd);
+      } else {
+        // S <- L^{-1} S L^{-T}
+        for (int col = 0; col < m_fn; ++col)
+          for (int i = 0; i < m_fn; ++i) {
+            double v = S[i][col];
+            for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[k][col];
+            S[i][col] = v / Aa[i][i];
+          }
+        for (int row = 0; row < m_fn; ++row)
+          for (int i = 0; i < m_fn; ++i) {
+            double v = S[row][i];
+            for (int k = 0; k < i; ++k) v -= Aa[i][k] * S[row][k];
+            S[row][i] = v / Aa[i][i];
+          }
+        for (int i = 0; i < m_fn; ++i)
+          for (int j = 0; j < i; ++j) {
+            const double v = 0.5 * (S[i][j] + S[j][i]);
+            S[i][j] = S[j][i] = v;
+          }
+        go = 1;
+      }   // Cholesky of a
+    }   // functions to solve for
+  }   // lane 0
+  __syncwarp();
+  if (!go) return;
+  jacobi_warp(S, V, m_fn, lane);
+  __syncwarp();
+  if (lane != 0) return;
   for (int k = 0; k < m_fn; ++k) { mu[k] = S[k][k]; ord[k] = k; }
   // descending mu = ascending lambda (stable insertion sort)
   for (int i = 1; i < m_fn; ++i) {
