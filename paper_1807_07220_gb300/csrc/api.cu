@@ -2173,8 +2173,11 @@ int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, 
     const bool lockstep = opt->batch_lockstep && nrhs > 1 && opt->m1 == 1 && opt->m2 == 1 &&
                           opt->cycle == TG_CYCLE_TWO_GRID;
     for (int i = 0; i < ninst && !rc; ++i) {
-      for (int k0 = 0; k0 < nrhs && !rc; k0 += lockstep ? kGroup : 1) {
-        const int k = lockstep ? std::min(kGroup, nrhs - k0) : 1;
+      // a band smoother has no lock-step sweep: its right-hand sides run as
+      // independent branches (in a group they would follow one another)
+      const bool ls = lockstep && !is_band_shape(B->handles[i]->shape);
+      for (int k0 = 0; k0 < nrhs && !rc; k0 += ls ? kGroup : 1) {
+        const int k = ls ? std::min(kGroup, nrhs - k0) : 1;
         Ctx* const* cs = &B->ctx[(size_t)i * nrhs + k0];
         rc = (k > 1) ? add_group(cs, k, g, B->cap) : add_chain(cs[0], g, B->cap);
       }
