@@ -19,15 +19,15 @@ headline arm through the host-pointer C ABI (host -> device copy of f and
 device -> host copy of ux, uy, p inside every timed call).
 
 The default line also carries, for one GPU:
-  north_star.batch_64x4: 64 instances (n in {64,128,256,512}, b in {8,16},
+  comparisons.batch_64x4: 64 instances (n in {64,128,256,512}, b in {8,16},
     channels at 10^U(4,6)) x 4 right-hand sides in one graph launch per
     step: learned coarse space + FP16 preconditioner (networks trained here
     for b = 8 and 16), exact spectral space + FP16, and plain FP64 exact;
-  north_star.n1024_b16: 1024^2, b = 16, held-out exp(GRF) + 1e6 channel
+  comparisons.n1024_b16: 1024^2, b = 16, held-out exp(GRF) + 1e6 channel
     field: learned (network trained here on 25 fields, 201 600 faces) and
     exact with the FP16 preconditioner against plain FP64 exact, plus the
     smoother's roofline at that size (its factors stream from HBM);
-  north_star.impes_512: two-phase IMPES at 512^2 (b = 16, channels 1e5),
+  comparisons.impes_512: two-phase IMPES at 512^2 (b = 16, channels 1e5),
     200 steps with the FP16 preconditioner: the coarse space of the first
     setup kept with low-rank inverse updates (the paper's choice) against
     the space rebuilt every step by the learned network (trained here on
@@ -372,14 +372,14 @@ def run_ours(args):
         return whole_job_rate(ms_list, dof(n), world, dist is not None, "cuda")
 
     peaks, peak_src = measured_peaks()
-    north = None
-    if world == 1 and not args.no_north_star:
-        north = {"batch_64x4": north_star_batch(args, tgms, torch, flush, checks),
-                 "n1024_b16": north_star_1024(args, tgms, torch, flush, checks, peaks, peak_src)}
+    comp = None
+    if world == 1 and not args.no_comparisons:
+        comp = {"batch_64x4": compare_batch(args, tgms, torch, flush, checks),
+                 "n1024_b16": compare_1024(args, tgms, torch, flush, checks, peaks, peak_src)}
         # two-phase flow: 512^2, 200 steps, the paper's frozen coarse space (low-rank inverse updates) and
         # the coarse space rebuilt every step by the learned network with exact fallback
         rec = impes_record(args, 512, 16, ["frozen", "rebuild_learned"], 200, prec="f16")
-        north["impes_512"] = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "arms",
+        comp["impes_512"] = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "arms",
                                                   "headline_arm", "training")}
 
     value, ms_step = agg(times)
@@ -432,8 +432,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * (n + 1) + n * n)},
         "clocks": clk,
     }
-    if north is not None:
-        line["north_star"] = north
+    if comp is not None:
+        line["comparisons"] = comp
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, b)
         try:
@@ -441,18 +441,18 @@ def run_ours(args):
         except Exception as e:  # reported, never fatal for the GPU line
             res = {"error": str(e)[:300]}
         line["error_vs_oracle"] = res.get("headline", res)
-        if north is not None:
-            for arm in north["batch_64x4"]["arms"]:
-                north["batch_64x4"]["arms"][arm]["error_vs_oracle"] = {
+        if comp is not None:
+            for arm in comp["batch_64x4"]["arms"]:
+                comp["batch_64x4"]["arms"][arm]["error_vs_oracle"] = {
                     k[len("batch_%s_" % arm):]: v for k, v in res.items() if k.startswith("batch_%s_" % arm)}
-            for arm in north["n1024_b16"]["arms"]:
-                north["n1024_b16"]["arms"][arm]["properties_vs_oracle"] = res.get("n1024_" + arm)
+            for arm in comp["n1024_b16"]["arms"]:
+                comp["n1024_b16"]["arms"][arm]["properties_vs_oracle"] = res.get("n1024_" + arm)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-# ---------------------------------------------------------------- spec comparison
+# ---------------------------------------------------------------- comparisons against plain FP64
 def train_net(tgms, torch, n, b, kappa_of, seeds, steps, hidden, stream, k=4):
     """A network for block size b: labels from the exact spectral problems
     (Section 4.2) of the seeded fields kappa_of(seed), then ``steps`` Adam
@@ -491,7 +491,7 @@ def arm_record(dof_total, times, setup_s):
             "value_with_setup": dof_total / (ms / 1e3 + setup_s)}
 
 
-def north_star_batch(args, tgms, torch, flush, checks):
+def compare_batch(args, tgms, torch, flush, checks):
     """The 64-instance x 4-right-hand-side workload (n from {64, 128, 256,
     512}, b from {8, 16}, channels at 10^U(4,6), one random source/sink pair
     per right-hand side) in one graph launch per step: learned coarse space
@@ -573,7 +573,7 @@ def north_star_batch(args, tgms, torch, flush, checks):
                 arms["learned_f16"]["value_with_setup"] / arms["exact_f64"]["value_with_setup"]}
 
 
-def north_star_1024(args, tgms, torch, flush, checks, peaks, peak_src):
+def compare_1024(args, tgms, torch, flush, checks, peaks, peak_src):
     """1024 x 1024, 16 x 16-cell blocks, exp(GRF) + 1e6 channels (held-out
     field): the learned coarse space (network trained on 25 other seeded
     fields, 201 600 faces) and the exact spectral space with the row-scaled
@@ -1230,9 +1230,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle legs (CPU baseline and the checks against the oracle)")
-    ap.add_argument("--no-north-star", action="store_true",
+    ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the batched and 1024^2 learned comparisons against plain FP64")
-    ap.add_argument("--ns-steps", type=int, default=5, help="timed steps of each north-star arm")
+    ap.add_argument("--ns-steps", type=int, default=5, help="timed steps of each comparison arm")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch", "learned", "impes", "ablation", "mlp"])
     ap.add_argument("--impes-steps", type=int, default=200)
