@@ -483,6 +483,7 @@ __device__ __forceinline__ int face_of_side(int side, int I, int J, int nc) {
 // RT_s forcing, interior solved with the block's band factor.
 // Dynamic shared memory: L[(b-1)^2 (b+1)] | psi[nfn (b+1)^2] | kloc[b^2] |
 // coefficient rows [nfn b] | solve lines [warps (b-1)^2]
+constexpr int kGramChunk = 8;   // cells per pass of the snapshot Gram
 __global__ void k_snapshots(const double* __restrict__ kinv, const double* __restrict__ blk_band,
                             const double* __restrict__ coef, int nfn, const unsigned char* __restrict__ mask,
                             double* __restrict__ psiS, double* __restrict__ gram, int n, int b) {
@@ -572,37 +573,65 @@ __global__ void k_snapshots(const double* __restrict__ kinv, const double* __res
   __syncthreads();
   double* outp = psiS + ((long long)blk * 4 + side) * b * ncl;
   for (int t = threadIdx.x; t < nfn * ncl; t += blockDim.x) outp[t] = psi[t];
-  // Gram: thread per pair (fa <= fb), energy summed over the block's cells;
-  // the velocity of function f is coef_{f,0} RT_s + C psi_f
+  // Gram: G[fa][fb] = sum over the block's cells of u_a^T (kappa^{-1} M) u_b,
+  // with u_f the cell's four face values (h times the normal velocity of
+  // coef_{f,0} RT_s + C psi_f on the left, right, bottom and top faces) and
+  // M the RT0 mass pattern (1/3 on a face, 1/6 between opposite faces).  The
+  // cells go in chunks of kGramChunk: the chunk's u and kappa^{-1} M u of every
+  // function are formed once in shared memory, then one thread per pair
+  // (fa <= fb) adds their inner products.
+  double* Ug = cf + nfn * b + (blockDim.x >> 5) * nloc;   // [nfn][kGramChunk][4]
+  double* Wg = Ug + nfn * kGramChunk * 4;                  // [nfn][kGramChunk][4]
   double* G = gram + ((long long)blk * 4 + side) * b * b;
   const int npair = nfn * (nfn + 1) / 2;
-  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-    int fa = 0, rem = t;
+  int fa = -1, fb = -1;
+  if ((int)threadIdx.x < npair) {
+    int rem = threadIdx.x;
+    fa = 0;
     while (rem >= nfn - fa) { rem -= nfn - fa; ++fa; }
-    const int fb = fa + rem;
-    const double* Pa = psi + fa * ncl;
-    const double* Pb = psi + fb * ncl;
-    const double ca = cf[fa * b], cb = cf[fb * b];
-    double e = 0.0;
-    for (int cell = 0; cell < b * b; ++cell) {
-      const int a = cell % b, c = cell / b;
-      const int n00 = c * nb1 + a, n10 = n00 + 1, n01 = n00 + nb1, n11 = n01 + 1;
-      // w = h * normal velocity: x-faces left/right, y-faces bottom/top
-      double aL = Pa[n01] - Pa[n00], aR = Pa[n11] - Pa[n10];
-      double aB = -(Pa[n10] - Pa[n00]), aT = -(Pa[n11] - Pa[n01]);
-      double bL = Pb[n01] - Pb[n00], bR = Pb[n11] - Pb[n10];
-      double bB = -(Pb[n10] - Pb[n00]), bT = -(Pb[n11] - Pb[n01]);
-      if (side <= 1) {
-        aL += ca * h * rt_value(side, a, b); aR += ca * h * rt_value(side, a + 1, b);
-        bL += cb * h * rt_value(side, a, b); bR += cb * h * rt_value(side, a + 1, b);
-      } else {
-        aB += ca * h * rt_value(side, c, b); aT += ca * h * rt_value(side, c + 1, b);
-        bB += cb * h * rt_value(side, c, b); bT += cb * h * rt_value(side, c + 1, b);
+    fb = fa + rem;
+  }
+  double e = 0.0;
+  for (int c0 = 0; c0 < b * b; c0 += kGramChunk) {
+    for (int t = threadIdx.x; t < nfn * kGramChunk; t += blockDim.x) {
+      const int fn = t / kGramChunk, cell = c0 + t % kGramChunk;
+      double u[4] = {0.0, 0.0, 0.0, 0.0}, k = 0.0;
+      if (cell < b * b) {
+        const int a = cell % b, c = cell / b;
+        const int n00 = c * nb1 + a, n10 = n00 + 1, n01 = n00 + nb1, n11 = n01 + 1;
+        const double* P = psi + fn * ncl;
+        const double cfn = cf[fn * b];
+        u[0] = P[n01] - P[n00];
+        u[1] = P[n11] - P[n10];
+        u[2] = -(P[n10] - P[n00]);
+        u[3] = -(P[n11] - P[n01]);
+        if (side <= 1) {
+          u[0] += cfn * h * rt_value(side, a, b);
+          u[1] += cfn * h * rt_value(side, a + 1, b);
+        } else {
+          u[2] += cfn * h * rt_value(side, c, b);
+          u[3] += cfn * h * rt_value(side, c + 1, b);
+        }
+        k = kl[cell];
       }
-      const double k = kl[cell];
-      e += k * ((aL * bL + aR * bR + aB * bB + aT * bT) / 3.0 +
-                (aL * bR + aR * bL + aB * bT + aT * bB) / 6.0);
+      double* Uc = Ug + (long long)t * 4;
+      double* Wc = Wg + (long long)t * 4;
+      Uc[0] = u[0]; Uc[1] = u[1]; Uc[2] = u[2]; Uc[3] = u[3];
+      Wc[0] = k * (u[0] / 3.0 + u[1] / 6.0);
+      Wc[1] = k * (u[0] / 6.0 + u[1] / 3.0);
+      Wc[2] = k * (u[2] / 3.0 + u[3] / 6.0);
+      Wc[3] = k * (u[2] / 6.0 + u[3] / 3.0);
     }
+    __syncthreads();
+    if (fa >= 0) {
+      const double* Ua = Ug + fa * kGramChunk * 4;
+      const double* Wb = Wg + fb * kGramChunk * 4;
+#pragma unroll 4
+      for (int i = 0; i < kGramChunk * 4; ++i) e = fma(Ua[i], Wb[i], e);
+    }
+    __syncthreads();
+  }
+  if (fa >= 0) {
     G[fa * b + fb] = e;
     G[fb * b + fa] = e;
   }
@@ -1523,7 +1552,8 @@ void launch_snapshots(const double* kinv, const double* blk_band, const double* 
   const int nc = n / b, nloc = (b - 1) * (b - 1), threads = 256;
   if (!coef) nfn = b;
   const size_t shm = sizeof(double) * ((size_t)nloc * (b + 1) + (size_t)nfn * (b + 1) * (b + 1) +
-                                       (size_t)b * b + (size_t)nfn * b + (size_t)(threads / 32) * nloc);
+                                       (size_t)b * b + (size_t)nfn * b + (size_t)(threads / 32) * nloc +
+                                       2 * (size_t)nfn * kGramChunk * 4);
   cudaFuncSetAttribute(k_snapshots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   k_snapshots<<<nc * nc * 4, threads, shm, s>>>(kinv, blk_band, coef, nfn, mask, psiS, gram, n, b);
 }
