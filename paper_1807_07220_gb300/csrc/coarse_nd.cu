@@ -238,15 +238,12 @@ int nd_build(const double* K, int D, const std::vector<int>& key, int nc, const 
   std::vector<long long> offa(S), offe(S);
   std::vector<int> nt(S), st0(S), mt(S);
   long long total = 0;
-  size_t max_t = 1, max_g = (size_t)NS * NS;
   for (int t = 0; t < S; ++t) {
     nt[t] = o[t + 1] - o[t];
     st0[t] = sepoff[std::max(t - 1, 0)];
     mt[t] = sepoff[std::min(t + 1, S - 1)] - st0[t];
     offa[t] = total;
     total += (long long)(nt[t] + mt[t]) * nt[t];
-    max_t = std::max(max_t, (size_t)nt[t] * mt[t]);
-    max_g = std::max(max_g, (size_t)nt[t] * nt[t]);
   }
   for (int t = 0; t < S; ++t) {
     offe[t] = total;
@@ -284,39 +281,99 @@ int nd_build(const double* K, int D, const std::vector<int>& key, int nc, const 
     if (!rc) rc = ck(cudaMalloc(&f.rows_a, sizeof(NdRow) * std::max<size_t>(1, ra.size())));
     if (!rc) rc = ck(cudaMalloc(&f.rows_b, sizeof(NdRow) * std::max<size_t>(1, rb.size())));
   }
-  double *T = nullptr, *G = nullptr;
-  if (!rc) rc = ck(cudaMalloc(&T, sizeof(double) * max_t));
-  if (!rc) rc = ck(cudaMalloc(&G, sizeof(double) * max_g));
+  // Per-strip work (the interior block, its inverse, X_t and X_t^T) runs on
+  // up to kNdStreams streams; strips of fewer than 3 kGjBlock unknowns are
+  // inverted by one CTA (k_gj_small) rather than one launch per pivot.  The
+  // Schur updates of Sigma follow in two colours (even strips, then odd:
+  // strips of one colour touch disjoint separator blocks), then Sigma^{-1}.
+  constexpr int kNdStreams = 8;
+  const int nss = std::min(S, kNdStreams);
+  std::vector<cudaStream_t> ss(nss, nullptr);
+  std::vector<cudaEvent_t> ev(nss + 1, nullptr);
+  std::vector<double*> G(nss, nullptr);
+  double *T = nullptr, *GS = nullptr;
+  int* bad = nullptr;
+  size_t max_n2 = 1, sum_t = 1;
+  for (int t = 0; t < S; ++t) {
+    max_n2 = std::max(max_n2, (size_t)nt[t] * nt[t]);
+    sum_t += (size_t)nt[t] * mt[t];
+  }
+  std::vector<long long> toff(S + 1, 0);   // per strip A_{t,S} (kept for the Schur updates)
+  for (int t = 0; t < S; ++t) toff[t + 1] = toff[t] + (long long)nt[t] * mt[t];
+  for (int k = 0; k < nss && !rc; ++k) {
+    rc = ck(cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking));
+    if (!rc) rc = ck(cudaMalloc(&G[k], sizeof(double) * max_n2));
+  }
+  for (int k = 0; k <= nss && !rc; ++k) rc = ck(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+  if (!rc) rc = ck(cudaMalloc(&T, sizeof(double) * sum_t));
+  if (!rc) rc = ck(cudaMalloc(&GS, sizeof(double) * std::max<size_t>(1, (size_t)NS * NS)));
+  if (!rc) rc = ck(cudaMalloc(&bad, sizeof(int)));
+  if (!rc) rc = ck(cudaMemsetAsync(bad, 0, sizeof(int), s));
   if (!rc) rc = ck(cudaMemcpyAsync(f.perm, perm.data(), sizeof(int) * D, cudaMemcpyHostToDevice, s));
   if (!rc) rc = ck(cudaMemcpyAsync(f.gatherp, gp.data(), sizeof(int) * gp.size(), cudaMemcpyHostToDevice, s));
   if (!rc && !ra.empty())
     rc = ck(cudaMemcpyAsync(f.rows_a, ra.data(), sizeof(NdRow) * ra.size(), cudaMemcpyHostToDevice, s));
   if (!rc && !rb.empty())
     rc = ck(cudaMemcpyAsync(f.rows_b, rb.data(), sizeof(NdRow) * rb.size(), cudaMemcpyHostToDevice, s));
+  // the streams start after what s has enqueued, and s continues after all of them
+  auto fork = [&]() {
+    cudaEventRecord(ev[nss], s);
+    for (int k = 0; k < nss; ++k) cudaStreamWaitEvent(ss[k], ev[nss], 0);
+  };
+  auto join = [&]() {
+    for (int k = 0; k < nss; ++k) {
+      cudaEventRecord(ev[k], ss[k]);
+      cudaStreamWaitEvent(s, ev[k], 0);
+    }
+  };
   if (!rc) {
     const int* ps = f.perm + DI;
     double* Y = f.M + y_off;
     // Sigma starts as A_SS
     k_nd_gather<<<grid_cap((long long)NS * NS, 256, 4096), 256, 0, s>>>(K, D, ps, NS, ps, NS, Y, NS);
+    fork();
     for (int t = 0; t < S; ++t) {
       const int n = nt[t], m = mt[t];
       if (n == 0) continue;
+      cudaStream_t st = ss[t % nss];
       const int* pt = f.perm + o[t];
       double* Ai = f.M + offa[t];
       double* X = f.M + offe[t];
-      k_nd_gather<<<grid_cap((long long)n * n, 256, 4096), 256, 0, s>>>(K, D, pt, n, pt, n, Ai, n);
-      launch_gauss_jordan(Ai, G, n, status, s);                                        // A_t^{-1}
+      double* Tt = T + toff[t];
+      k_nd_gather<<<grid_cap((long long)n * n, 256, 4096), 256, 0, st>>>(K, D, pt, n, pt, n, Ai, n);
+      if (n < 3 * kGjBlock) launch_gj_small(Ai, n, bad, st);                           // A_t^{-1}
+      else launch_gauss_jordan(Ai, G[t % nss], n, status, st);
       if (m == 0) continue;
-      k_nd_gather<<<grid_cap((long long)n * m, 256, 4096), 256, 0, s>>>(K, D, pt, n, ps + st0[t], m, T, m);
-      launch_dgemm(n, m, n, 1.0, Ai, n, 1, T, m, 1, 0.0, X, m, s);                     // X_t = A_t^{-1} A_{t,S}
-      k_nd_transpose<<<grid_cap((long long)n * m, 256, 4096), 256, 0, s>>>(X, n, m, m, Ai + (long long)n * n, n);
-      launch_dgemm(m, m, n, -1.0, T, 1, m, X, m, 1, 1.0, Y + (long long)st0[t] * NS + st0[t], NS, s);   // Sigma
+      k_nd_gather<<<grid_cap((long long)n * m, 256, 4096), 256, 0, st>>>(K, D, pt, n, ps + st0[t], m, Tt, m);
+      launch_dgemm(n, m, n, 1.0, Ai, n, 1, Tt, m, 1, 0.0, X, m, st);                   // X_t = A_t^{-1} A_{t,S}
+      k_nd_transpose<<<grid_cap((long long)n * m, 256, 4096), 256, 0, st>>>(X, n, m, m, Ai + (long long)n * n, n);
     }
-    launch_gauss_jordan(Y, G, NS, status, s);                                          // Sigma^{-1}
+    join();
+    for (int colour = 0; colour < 2; ++colour) {   // Sigma -= A_{S,t} X_t
+      fork();
+      for (int t = colour, q = 0; t < S; t += 2, ++q) {
+        const int n = nt[t], m = mt[t];
+        if (n == 0 || m == 0) continue;
+        launch_dgemm(m, m, n, -1.0, T + toff[t], 1, m, f.M + offe[t], m, 1, 1.0,
+                     Y + (long long)st0[t] * NS + st0[t], NS, ss[q % nss]);
+      }
+      join();
+    }
+    launch_gauss_jordan(Y, GS, NS, status, s);                                         // Sigma^{-1}
     rc = ck(cudaStreamSynchronize(s));
   }
+  int h_bad = 0;
+  if (!rc) rc = ck(cudaMemcpy(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!rc && h_bad) rc = TG_ERR_BREAKDOWN;   // a strip block with a non-positive pivot: not SPD
+  for (int k = 0; k < nss; ++k) {
+    if (ss[k]) cudaStreamDestroy(ss[k]);
+    cudaFree(G[k]);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(T);
-  cudaFree(G);
+  cudaFree(GS);
+  cudaFree(bad);
   if (!rc) rc = ck(cudaGetLastError());
   if (!rc && NS * sizeof(double) > 48 * 1024)
     rc = ck(cudaFuncSetAttribute(k_nd_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(NS * sizeof(double))));
