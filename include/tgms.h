@@ -352,7 +352,10 @@ int tg_preprocess(tg_handle* h, const double* f, const double* bflux, double* ux
 typedef struct tg_batch tg_batch;
 
 /* Step 2 of Section 5 for every instance: kappa[i] (device, n_i * n_i) on
- * grids[i]; nrhs right-hand sides per instance.  The batch owns the handles. */
+ * grids[i]; nrhs right-hand sides per instance.  The batch owns the handles.
+ * With smoother_shape -1, the autotuner runs for the first instance of each
+ * (nx, bx, overlap); the later ones take the tile shape it chose (the same
+ * patches give the same launches), so their reports' shape_us stay 0. */
 int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, double eig_tol,
                    const tg_options* opt, int nrhs, void* stream, tg_batch** out);
 

@@ -2098,9 +2098,20 @@ int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, 
   B->nrhs = nrhs;
   B->stream = (cudaStream_t)stream;
   int rc = TG_OK;
+  // Instances of one grid size, block size and oversampling have the same
+  // patches, hence the same smoother launches: the tile shape the autotuner
+  // picks for the first of them is given to the others, which skip the
+  // autotuner (and, when it is a band shape, the dense patch inverses).
+  struct Tuned {
+    int nx, bx, overlap, shape;
+  };
+  std::vector<Tuned> tuned;
   for (int i = 0; i < ninst && !rc; ++i) {
     tg_handle* h = nullptr;
     tg_options oi = *opt;
+    if (opt->smoother_shape < 0)
+      for (const Tuned& t : tuned)
+        if (t.nx == grids[i].nx && t.bx == grids[i].bx && t.overlap == grids[i].overlap) oi.smoother_shape = t.shape;
     if (opt->coarse_space == TG_COARSE_LEARNED && opt->batch_nets) {
       // the network trained for this instance's block size
       oi.net = nullptr;
@@ -2116,7 +2127,10 @@ int tg_setup_batch(int ninst, const double* const* kappa, const tg_grid* grids, 
       }
     }
     rc = tg_setup(kappa[i], &grids[i], eig_tol, &oi, stream, &h);
-    if (!rc) B->handles.push_back(h);
+    if (!rc) {
+      B->handles.push_back(h);
+      if (oi.smoother_shape < 0) tuned.push_back(Tuned{grids[i].nx, grids[i].bx, grids[i].overlap, h->shape});
+    }
   }
   // contexts: the handle's own context serves its first right-hand side
   for (int i = 0; i < ninst && !rc; ++i) {
