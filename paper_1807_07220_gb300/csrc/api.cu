@@ -93,6 +93,7 @@ struct Ctx {
   double *cs_part = nullptr, *cs_coefs = nullptr, *rt_part = nullptr, *rt_coefs = nullptr;
   PcgState* st = nullptr;
   double* d_rtol = nullptr;
+  void* slab = nullptr;       // the device memory of every vector above (one allocation)
   double* h_rtol = nullptr;   // pinned
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // one-chain graphs of tg_solve (zero initial guess) and tg_solve_warm
@@ -520,10 +521,7 @@ void ctx_free(Ctx* c) {
   if (c->exec_warm) cudaGraphExecDestroy(c->exec_warm);
   if (c->cap) cudaStreamDestroy(c->cap);
   cudaFree(c->ux0);
-  void* ptrs[] = {c->x, c->r, c->p, c->q, c->rho, c->phi, c->p2, c->r2, c->zacc, c->zacc2, c->rin, c->ux, c->uy,
-                  c->fd, c->bd, c->pd, c->pw, c->part, c->gx, c->gy, c->FH, c->absF, c->diverr, c->cs_part,
-                  c->cs_coefs, c->rt_part, c->rt_coefs, c->st, c->d_rtol};
-  for (void* ptr : ptrs) cudaFree(ptr);
+  cudaFree(c->slab);
   if (c->h_rtol) cudaFreeHost(c->h_rtol);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -545,19 +543,42 @@ int ctx_alloc(tg_handle* h, Ctx** out) {
   // partials: reductions over up to max(kRedGrid, stencil tiles) CTAs, and the
   // last smoothing sweep's two dot products over its one-wave grid
   const long long npart = 4 * std::max<long long>(2048, (long long)((n + 31) / 32) * ((n + 7) / 8));
-  int rc = TG_OK;
-  if (dalloc(&c->x, nn) || dalloc(&c->r, nn) || dalloc(&c->p, nn) || dalloc(&c->q, nn) || dalloc(&c->rho, nn) ||
-      dalloc(&c->phi, nn) || dalloc(&c->p2, nn) || dalloc(&c->r2, nn) || dalloc(&c->ux, nf) || dalloc(&c->uy, nf) ||
-      dalloc(&c->fd, nn) || dalloc(&c->bd, 4 * n) || dalloc(&c->pd, nn) || dalloc(&c->pw, nn + 2 * n + 2) ||
-      dalloc(&c->part, npart) || dalloc(&c->gx, (nc + 1) * nc) || dalloc(&c->gy, (nc + 1) * nc) ||
-      dalloc(&c->FH, h->nblocks) || dalloc(&c->absF, h->nblocks) || dalloc(&c->diverr, 2) ||
-      dalloc(&c->cs_part, h->cs.nslots) || dalloc(&c->cs_coefs, 5 * (size_t)h->cs.D) ||
-      dalloc(&c->rt_part, h->rt.nslots) || dalloc(&c->rt_coefs, 5 * (size_t)h->rt.D) || dalloc(&c->st, 1) ||
-      dalloc(&c->d_rtol, 1))
-    rc = TG_ERR_OOM;
-  if (!rc) rc = cuda_err(cudaMalloc(&c->zacc, tc * nn));
-  if (!rc) rc = cuda_err(cudaMalloc(&c->zacc2, tc * nn));
-  if (!rc) rc = cuda_err(cudaMalloc(&c->rin, tc * nn));
+  // Every device vector of the context is carved from one allocation (a
+  // batch creates nrhs + 1 contexts per instance: one cudaMalloc each instead
+  // of 29).  Each vector starts on a 256-byte boundary and is followed by a
+  // gap of at least 512 bytes.
+  struct Part {
+    void** ptr;
+    size_t bytes;
+  };
+  const size_t d8 = sizeof(double);
+  auto cnt = [](long long v) { return (size_t)std::max<long long>(v, 1); };   // empty vectors get one element
+  const Part parts[] = {
+      {(void**)&c->x, d8 * cnt(nn)},          {(void**)&c->r, d8 * cnt(nn)},
+      {(void**)&c->p, d8 * cnt(nn)},          {(void**)&c->q, d8 * cnt(nn)},
+      {(void**)&c->rho, d8 * cnt(nn)},        {(void**)&c->phi, d8 * cnt(nn)},
+      {(void**)&c->p2, d8 * cnt(nn)},         {(void**)&c->r2, d8 * cnt(nn)},
+      {(void**)&c->ux, d8 * cnt(nf)},         {(void**)&c->uy, d8 * cnt(nf)},
+      {(void**)&c->fd, d8 * cnt(nn)},         {(void**)&c->bd, d8 * cnt(4LL * n)},
+      {(void**)&c->pd, d8 * cnt(nn)},         {(void**)&c->pw, d8 * cnt(nn + 2LL * n + 2)},
+      {(void**)&c->part, d8 * cnt(npart)},    {(void**)&c->gx, d8 * cnt((nc + 1LL) * nc)},
+      {(void**)&c->gy, d8 * cnt((nc + 1LL) * nc)}, {(void**)&c->FH, d8 * cnt(h->nblocks)},
+      {(void**)&c->absF, d8 * cnt(h->nblocks)}, {(void**)&c->diverr, d8 * 2},
+      {(void**)&c->cs_part, d8 * cnt(h->cs.nslots)}, {(void**)&c->cs_coefs, d8 * cnt(5LL * h->cs.D)},
+      {(void**)&c->rt_part, d8 * cnt(h->rt.nslots)}, {(void**)&c->rt_coefs, d8 * cnt(5LL * h->rt.D)},
+      {(void**)&c->st, sizeof(PcgState)},     {(void**)&c->d_rtol, d8},
+      {(void**)&c->zacc, tc * cnt(nn)},       {(void**)&c->zacc2, tc * cnt(nn)},
+      {(void**)&c->rin, tc * cnt(nn)},
+  };
+  constexpr size_t kAlign = 256, kGap = 512;
+  size_t off[sizeof(parts) / sizeof(parts[0])], total = 0;
+  for (size_t k = 0; k < sizeof(parts) / sizeof(parts[0]); ++k) {
+    total = (total + kAlign - 1) / kAlign * kAlign;
+    off[k] = total;
+    total += parts[k].bytes + kGap;
+  }
+  int rc = cuda_err(cudaMalloc(&c->slab, total));
+  for (size_t k = 0; !rc && k < sizeof(parts) / sizeof(parts[0]); ++k) *parts[k].ptr = (char*)c->slab + off[k];
   if (!rc) rc = cuda_err(cudaMallocHost(&c->h_rtol, sizeof(double)));
   for (auto& e : c->ev)
     if (!rc) rc = cuda_err(cudaEventCreate(&e));
