@@ -494,8 +494,11 @@ int tg_transport_step(const double* s, const double* ux, const double* uy, const
  * TG_ERR_INVALID_ARG (p is then unspecified).  Every call on a device shares
  * that array: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The first call on a
- * device looks up the array's device address (a one-time set-up per device);
- * make that first call before any stream capture. */
+ * device looks up the array's device address (a one-time set-up per device).
+ * The call cannot be recorded in a stream capture (it reads its status on
+ * the host and synchronises the stream): on a stream that is being captured
+ * it returns TG_ERR_UNSUPPORTED before enqueuing anything, and the capture
+ * stays valid. */
 int tg_pressure_noalloc(const double* kappa, const double* ux, const double* uy, double* p, int n,
                         void* stream);
 

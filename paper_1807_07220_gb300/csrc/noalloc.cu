@@ -10,7 +10,9 @@
 // take the implicit device synchronisation of cudaMalloc / cudaFree.
 //
 // The first call on a device looks up the array's device address (one-time
-// set-up per device); that first call should come before any stream capture.
+// set-up per device).  The call reads its status on the host and synchronises
+// its stream, which a stream capture cannot record: on a capturing stream it
+// returns TG_ERR_UNSUPPORTED without enqueuing anything.
 #include <mutex>
 
 #include "../../include/tgms.h"
@@ -58,6 +60,10 @@ extern "C" int tg_pressure_noalloc(const double* kappa, const double* ux, const 
                                    void* stream) {
   if (!kappa || !ux || !uy || !p || n < 2) return TG_ERR_INVALID_ARG;
   if (n > kNoAllocMaxN) return TG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) return TG_ERR_CUDA;
+  if (capture != cudaStreamCaptureStatusNone) return TG_ERR_UNSUPPORTED;
   void* base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;
@@ -66,7 +72,6 @@ extern "C" int tg_pressure_noalloc(const double* kappa, const double* ux, const 
   float* kinv32 = reinterpret_cast<float*>(s8 + kOffKinv32);
   int* status = reinterpret_cast<int*>(s8 + kOffStatus);
   double* work = reinterpret_cast<double*>(s8 + kOffWork);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // A launch error already pending in this thread belongs to the caller's
   // earlier work: it is neither reported here nor cleared.
   const cudaError_t pending = cudaPeekAtLastError();

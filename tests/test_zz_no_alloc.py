@@ -7,8 +7,9 @@ arena, and paths that must avoid cudaMalloc's implicit synchronisation.  It
 keeps its scratch in a static device array shared by all calls, so this test
 calls it twice in a row on the same device and checks both results against
 the existing entry point, checks that the calls leave the device's memory
-use unchanged, and that an invalid permeability is reported without
-poisoning the next call.  The file sorts last so that a run stopping at the
+use unchanged, that an invalid permeability is reported without
+poisoning the next call, and that a call on a stream being captured is
+refused without invalidating the capture.  The file sorts last so that a run stopping at the
 first failure has already run every other test; it also passes alone in a
 fresh process."""
 
@@ -96,6 +97,37 @@ def test_noalloc_invalid_kappa_then_valid_call(tg):
             tg.tg_pressure_noalloc(bad, s.ux, s.uy, p, n, stream)
         assert e.value.code == -1
         tg.tg_pressure_noalloc(s.kappa, s.ux, s.uy, p, n, stream)
+        assert _rel(p, s.p) < 1e-12
+    finally:
+        s.close()
+
+
+def test_noalloc_refuses_a_capturing_stream(tg):
+    """The call reads its status on the host and synchronises its stream, so
+    it cannot be recorded in a graph: on a capturing stream it returns
+    TG_ERR_UNSUPPORTED before enqueuing anything, the capture still ends in a
+    graph that replays, and the next call on an ordinary stream succeeds."""
+    n, b = 32, 8
+    s = _solved(tg, n, b)
+    try:
+        p = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        x = torch.arange(64, dtype=torch.float64, device="cuda")
+        side = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        code = None
+        with torch.cuda.graph(graph, stream=side):
+            y = 2.0 * x
+            try:
+                tg.tg_pressure_noalloc(s.kappa, s.ux, s.uy, p, n, side.cuda_stream)
+            except tg.TgmsError as e:
+                code = e.code
+        assert code == -8
+        y.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, 2.0 * x)
+        assert not p.any()   # nothing of the refused call ran
+        tg.tg_pressure_noalloc(s.kappa, s.ux, s.uy, p, n, torch.cuda.current_stream().cuda_stream)
         assert _rel(p, s.p) < 1e-12
     finally:
         s.close()
