@@ -61,8 +61,12 @@ extern "C" int tg_pressure_noalloc(const double* kappa, const double* ux, const 
   if (!kappa || !ux || !uy || !p || n < 2) return TG_ERR_INVALID_ARG;
   if (n > kNoAllocMaxN) return TG_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // (the legacy stream answers cudaErrorStreamCaptureImplicit while a
+  // blocking stream captures: work on it would join that capture)
   cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) return TG_ERR_CUDA;
+  const cudaError_t query = cudaStreamIsCapturing(s, &capture);
+  if (query == cudaErrorStreamCaptureImplicit) return TG_ERR_UNSUPPORTED;
+  if (query != cudaSuccess) return TG_ERR_CUDA;
   if (capture != cudaStreamCaptureStatusNone) return TG_ERR_UNSUPPORTED;
   void* base = nullptr;
   int rc = scratch_address(&base);
