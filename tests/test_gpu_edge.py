@@ -107,3 +107,68 @@ def test_edge_mixed_precision(tg, case, prec):
     assert _rel(u, case["u_ref"]) < 1e-8, _rel(u, case["u_ref"])
     assert _rel(p, case["p_ref"]) < 1e-8, _rel(p, case["p_ref"])
     assert rep.max_div_error < 1e-12
+
+
+def _batch_solve(tg, specs, fs, nrhs, prec, rtol):
+    dev = "cuda"
+    kd = [torch.as_tensor(field(n), dtype=torch.float64, device=dev).contiguous() for n, b, field in specs]
+    opts = tg.default_options(precision=prec, flexible=int(prec != "f64"))
+    stream = torch.cuda.current_stream().cuda_stream
+    batch = tg.tg_setup_batch(kd, [s[0] for s in specs], [s[1] for s in specs], 10.0, nrhs, options=opts,
+                              stream=stream)
+    try:
+        assert tg.tg_batch_size(batch) == (len(specs), nrhs)
+        outs = [(torch.full((n, n + 1), 7.0, dtype=torch.float64, device=dev),
+                 torch.full((n + 1, n), 7.0, dtype=torch.float64, device=dev),
+                 torch.full((n, n), 7.0, dtype=torch.float64, device=dev)) for (n, b, _) in specs for _ in range(nrhs)]
+        fd = [torch.as_tensor(f, dtype=torch.float64, device=dev).contiguous() for f in fs]
+        iters, status = tg.tg_solve_batch(batch, fd, None, rtol, [o[0] for o in outs], [o[1] for o in outs],
+                                          [o[2] for o in outs])
+        torch.cuda.synchronize()
+        return iters, status, [tuple(t.cpu().numpy() for t in o) for o in outs]
+    finally:
+        tg.tg_destroy_batch(batch)
+
+
+def test_batch_of_one_problem(tg):
+    """One instance with one right-hand side: the batch graph holds a single
+    chain, and its result is the direct solution."""
+    n, b = 4, 2
+    f = inputs.quarter_five_spot(n)
+    iters, status, outs = _batch_solve(tg, [(n, b, _channels)], [f], 1, "f64", 1e-12)
+    assert (status == 0).all() and iters.shape == (1,)
+    u_ref, p_ref = solve_direct(Grid(n, b), _channels(n), f)
+    u = np.concatenate([outs[0][0].ravel(), outs[0][1].ravel()])
+    assert _rel(u, u_ref) < 1e-8 and _rel(outs[0][2].ravel(), p_ref) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16"])
+def test_batch_of_smallest_grids_with_a_zero_source(tg, prec):
+    """The smallest grids, each size twice (the later instance of a size
+    takes the smoother shape tuned for the first), three right-hand sides per
+    instance in lock step, the middle one of every instance zero.  The zero
+    chains stop at once with the exact zero solution while the others of
+    their group iterate on; every other chain reaches the direct solution."""
+    specs = [(4, 2, _channels), (32, 16, _lognormal), (12, 2, _channels), (4, 2, _lognormal),
+             (8, 4, _channels), (32, 16, _channels), (12, 2, _lognormal)]
+    nrhs = 3
+    fs = []
+    for i, (n, b, _) in enumerate(specs):
+        for r in range(nrhs):
+            fs.append(np.zeros((n, n)) if r == 1 else inputs.random_pairs(n, 1, 10 * i + r))
+    iters, status, outs = _batch_solve(tg, specs, fs, nrhs, prec, 1e-12)
+    assert (status == 0).all(), status
+    j = 0
+    for i, (n, b, field) in enumerate(specs):
+        for r in range(nrhs):
+            ux, uy, p = outs[j]
+            if r == 1:
+                assert iters[j] == 0
+                assert not ux.any() and not uy.any() and not p.any()
+            else:
+                assert iters[j] > 0
+                u_ref, p_ref = solve_direct(Grid(n, b), field(n), fs[j])
+                u = np.concatenate([ux.ravel(), uy.ravel()])
+                assert _rel(u, u_ref) < 1e-8, (i, r, _rel(u, u_ref))
+                assert _rel(p.ravel(), p_ref) < 1e-8, (i, r)
+            j += 1
